@@ -1,0 +1,357 @@
+"""Plain FP64 restatement of S3TTV denoising / destriping (Takemoto, Naganuma, Ono).
+
+TEST INFRASTRUCTURE ONLY: the oracle the CUDA path is checked against.  Nothing
+in the product imports this module.
+
+Everything follows the paper's notation and the order of its steps:
+
+* Sec. II-A: forward differences D_v, D_h, D_s with periodic boundaries.
+* Sec. II-B: prox, conjugate prox (Moreau, eq. ProxConjugate), projections.
+* Sec. II-C: P-PDS and Lemma 1 (diagonal preconditioners, eq. Preconditioners).
+* Sec. III-A: spatio-spectral structure tensors (eq. SSST, eq. rewrite_Lu).
+* Sec. III-C: Alg. 1 and the proximity operators it uses (eq. prox_box_constraint,
+  eq. prox_zeroset, eq. prox_l2ball_constraint, eq. prox_nuclear_norm, the
+  l1-ball projection) and the step sizes (eq. stepsize_denoising).
+* Sec. IV-A: radii rule (eq. RadiusSet), stopping rule (eq. StopCri_simulated),
+  MPSNR (eq. MPSNR).
+
+Readings of passages the paper leaves open:
+D_v differences along the first (vertical, i) axis and D_h along the second (j);
+blocks are all N1*N2 stride-1 k x k windows with periodic wrap, one per anchor
+(p, q) covering pixels (p+a, q+c), a, c in [0, k); block row r = a*k + c; column
+2b is the vertical and 2b+1 the horizontal difference of band b; initial values
+u = v, s = t = 0, all duals 0; the stop test uses ||u^(t)|| of the previous
+iterate (||u+ - u|| alone when ||u|| = 0).
+
+Arrays are (N1, N2, N3) float64, element (i, j, b).
+"""
+from __future__ import annotations
+
+import math
+import numpy as np
+
+__all__ = [
+    "AXIS_V", "AXIS_H", "AXIS_S", "diff", "diff_adj", "structure_tensors",
+    "structure_tensors_adjoint", "structure_tensor_block", "linear_op_adjoint_u",
+    "prox_nuclear", "block_dual_update", "proj_box", "proj_l2_ball",
+    "proj_l1_ball", "step_sizes", "assemble_operator", "lemma1_step_sizes",
+    "radii", "init_state", "iterate", "solve", "mpsnr", "objective",
+]
+
+AXIS_V, AXIS_H, AXIS_S = 0, 1, 2
+
+
+# ----------------------------------------------------------------------------
+# Sec. II-A: difference operators (forward, periodic boundary).
+# ----------------------------------------------------------------------------
+def diff(x: np.ndarray, axis: int) -> np.ndarray:
+    """Forward difference with periodic boundary: (D x)[i] = x[i+1] - x[i] (Sec. II-A)."""
+    return np.roll(x, -1, axis=axis) - x
+
+
+def diff_adj(y: np.ndarray, axis: int) -> np.ndarray:
+    """Adjoint of :func:`diff`: (D^T y)[i] = y[i-1] - y[i] (periodic)."""
+    return np.roll(y, 1, axis=axis) - y
+
+
+# ----------------------------------------------------------------------------
+# Sec. III-A: spatio-spectral structure tensors T_u^(l) = P_l D D_s u.
+# ----------------------------------------------------------------------------
+def structure_tensors(u: np.ndarray, k: int) -> np.ndarray:
+    """All structure tensors of eq. (SSST) / eq. (rewrite_Lu), shape (L, k*k, 2*N3).
+
+    Block l = p*N2 + q holds the second-order differences D_v D_s u and D_h D_s u
+    of the k x k window whose pixels are ((p+a) mod N1, (q+c) mod N2) (the
+    footnote of Sec. III-A pads a window at the border with pixels from the
+    opposite side).  Row r = a*k + c; columns [v_1 h_1 ... v_N3 h_N3].
+    """
+    N1, N2, N3 = u.shape
+    Ds = diff(u, AXIS_S)
+    Fv = diff(Ds, AXIS_V)
+    Fh = diff(Ds, AXIS_H)
+    X = np.empty((N1, N2, k * k, 2 * N3))
+    for a in range(k):
+        for c in range(k):
+            r = a * k + c
+            X[:, :, r, 0::2] = np.roll(Fv, shift=(-a, -c), axis=(0, 1))
+            X[:, :, r, 1::2] = np.roll(Fh, shift=(-a, -c), axis=(0, 1))
+    return X.reshape(N1 * N2, k * k, 2 * N3)
+
+
+def structure_tensor_block(u: np.ndarray, k: int, p: int, q: int) -> np.ndarray:
+    """One structure tensor T_u^(l) of eq. (SSST), anchor (p, q); shape (k*k, 2*N3)."""
+    N1, N2, N3 = u.shape
+    X = np.empty((k * k, 2 * N3))
+    for a in range(k):
+        for c in range(k):
+            i, j = (p + a) % N1, (q + c) % N2
+            i1, j1 = (i + 1) % N1, (j + 1) % N2
+            ds = lambda ii, jj: np.roll(u[ii, jj], -1) - u[ii, jj]  # D_s along bands
+            X[a * k + c, 0::2] = ds(i1, j) - ds(i, j)
+            X[a * k + c, 1::2] = ds(i, j1) - ds(i, j)
+    return X
+
+
+def structure_tensors_adjoint(Y: np.ndarray, k: int, shape) -> tuple[np.ndarray, np.ndarray]:
+    """sum_l P_l^T Y_l split into its vertical and horizontal parts (Zv, Zh)."""
+    N1, N2, N3 = shape
+    Y = Y.reshape(N1, N2, k * k, 2 * N3)
+    Zv = np.zeros((N1, N2, N3))
+    Zh = np.zeros((N1, N2, N3))
+    for a in range(k):
+        for c in range(k):
+            r = a * k + c
+            Zv += np.roll(Y[:, :, r, 0::2], shift=(a, c), axis=(0, 1))
+            Zh += np.roll(Y[:, :, r, 1::2], shift=(a, c), axis=(0, 1))
+    return Zv, Zh
+
+
+def linear_op_adjoint_u(Y: np.ndarray, k: int, shape) -> np.ndarray:
+    """sum_l D_s^T D^T P_l^T Y_l, the dual-to-primal term of Alg. 1 step 2."""
+    Zv, Zh = structure_tensors_adjoint(Y, k, shape)
+    return diff_adj(diff_adj(Zv, AXIS_V) + diff_adj(Zh, AXIS_H), AXIS_S)
+
+
+# ----------------------------------------------------------------------------
+# Sec. II-B / III-C: proximity operators and projections.
+# ----------------------------------------------------------------------------
+def prox_nuclear(A: np.ndarray, gamma: float) -> np.ndarray:
+    """prox of gamma*||.||_* by eq. (prox_nuclear_norm): U diag(max(s - gamma, 0)) V^T.
+
+    ``A`` may be a stack (..., m, n); the SVD is numpy's (LAPACK gesdd).
+    """
+    U, s, Vt = np.linalg.svd(A, full_matrices=False)
+    return U @ (np.maximum(s - gamma, 0.0)[..., :, None] * Vt)
+
+
+def block_dual_update(Y: np.ndarray, X: np.ndarray, gamma_Y: float) -> np.ndarray:
+    """Alg. 1 steps 9-10 for a stack of blocks.
+
+    Y' = Y + gamma_Y X, then Y+ = Y' - gamma_Y prox_{gamma_Y^-1 ||.||_*}(gamma_Y^-1 Y'),
+    which is the conjugate prox of eq. (ProxConjugate) applied to the nuclear norm.
+    """
+    Yp = Y + gamma_Y * X
+    return Yp - gamma_Y * prox_nuclear(Yp / gamma_Y, 1.0 / gamma_Y)
+
+
+def proj_box(x: np.ndarray, lo: float, hi: float) -> np.ndarray:
+    """Projection onto [mu_min, mu_max]^N, eq. (prox_box_constraint)."""
+    return np.minimum(np.maximum(x, lo), hi)
+
+
+def proj_l2_ball(x: np.ndarray, center: np.ndarray, eps: float) -> np.ndarray:
+    """Projection onto {x : ||x - v||_2 <= eps}, eq. (prox_l2ball_constraint)."""
+    d = x - center
+    nrm = math.sqrt(float(np.sum(d * d)))
+    if nrm <= eps:
+        return x.copy()
+    return center + eps * d / nrm
+
+
+def proj_l1_ball(x: np.ndarray, radius: float) -> np.ndarray:
+    """Projection onto {x : ||x||_1 <= radius} (Sec. III-C, the l1-ball projection
+    the paper cites from Condat 2016, in its sort-based form, O(N log N) as in
+    Table II).
+
+    With a_1 >= a_2 >= ... the sorted |x|: rho = max{j : a_j > (sum_{i<=j} a_i - r)/j},
+    tau = (sum_{i<=rho} a_i - r)/rho, result sign(x) max(|x| - tau, 0).
+    """
+    a = np.abs(x).ravel()
+    if a.sum() <= radius:
+        return x.copy()
+    if radius <= 0.0:
+        return np.zeros_like(x)
+    srt = np.sort(a)[::-1]
+    cs = np.cumsum(srt)
+    j = np.arange(1, srt.size + 1)
+    rho = int(np.nonzero(srt > (cs - radius) / j)[0][-1]) + 1
+    tau = (cs[rho - 1] - radius) / rho
+    return np.sign(x) * np.maximum(np.abs(x) - tau, 0.0)
+
+
+# ----------------------------------------------------------------------------
+# Step sizes: eq. (stepsize_denoising) and Lemma 1 (eq. Preconditioners).
+# ----------------------------------------------------------------------------
+def step_sizes(N1: int, N2: int, k: int, policy: str = "paper") -> dict:
+    """Step sizes of Alg. 1.
+
+    ``policy="paper"``: eq. (stepsize_denoising) as printed, gamma_u = 1/(8L + 1)
+    with L = N1*N2 blocks.  ``policy="pc_exact"``: gamma_u = 1/(8k^2 + 1), the exact
+    column abs-sum of Lemma 1 when every entry of D D_s u lies in k^2 blocks.
+    The other five are the same in both (Lemma 1 reproduces them exactly).
+    """
+    L = N1 * N2
+    if policy == "paper":
+        gu = 1.0 / (8.0 * L + 1.0)
+    elif policy == "pc_exact":
+        gu = 1.0 / (8.0 * k * k + 1.0)
+    else:
+        raise ValueError(policy)
+    return {"u": gu, "s": 1.0, "t": 1.0 / 3.0, "Y": 0.25, "y2": 0.5, "y3": 1.0 / 3.0}
+
+
+def assemble_operator(N1: int, N2: int, N3: int, k: int):
+    """The linear operator of Prob. (denoising2PPDS) as scipy.sparse blocks.
+
+    Built entry by entry from the index definitions (not from :func:`diff`), so it
+    is an independent construction.  Returns a dict of blocks A[(dual, primal)]
+    with duals 'Y' (all L blocks stacked, row order (l, r, column) of eq. SSST),
+    'y2', 'y3' and primals 'u', 's', 't'.
+    """
+    import scipy.sparse as sp
+
+    N = N1 * N2 * N3
+
+    def idx(i, j, b):
+        return ((i % N1) * N2 + (j % N2)) * N3 + (b % N3)
+
+    def dmat(axis):
+        rows, cols, vals = [], [], []
+        for i in range(N1):
+            for j in range(N2):
+                for b in range(N3):
+                    r = idx(i, j, b)
+                    nxt = [(i + 1, j, b), (i, j + 1, b), (i, j, b + 1)][axis]
+                    rows += [r, r]
+                    cols += [idx(*nxt), r]
+                    vals += [1.0, -1.0]
+        return sp.csr_matrix((vals, (rows, cols)), shape=(N, N))
+
+    Dv, Dh, Ds = dmat(0), dmat(1), dmat(2)
+    DvDs = (Dv @ Ds).tocsr()
+    DhDs = (Dh @ Ds).tocsr()
+    L = N1 * N2
+    rows, cols, vals = [], [], []
+    for p in range(N1):
+        for q in range(N2):
+            l = p * N2 + q
+            for a in range(k):
+                for c in range(k):
+                    r = a * k + c
+                    for b in range(N3):
+                        for o, M in ((0, DvDs), (1, DhDs)):
+                            row = (l * k * k + r) * 2 * N3 + 2 * b + o
+                            src = M.getrow(idx(p + a, q + c, b))
+                            rows += [row] * src.nnz
+                            cols += list(src.indices)
+                            vals += list(src.data)
+    AY = sp.csr_matrix((vals, (rows, cols)), shape=(L * k * k * 2 * N3, N))
+    I = sp.identity(N, format="csr")
+    Z = sp.csr_matrix((N, N))
+    return {
+        ("Y", "u"): AY, ("Y", "s"): sp.csr_matrix((AY.shape[0], N)),
+        ("Y", "t"): sp.csr_matrix((AY.shape[0], N)),
+        ("y2", "u"): Z, ("y2", "s"): Z, ("y2", "t"): Dv,
+        ("y3", "u"): I, ("y3", "s"): I, ("y3", "t"): I,
+    }
+
+
+def lemma1_step_sizes(blocks) -> dict:
+    """Lemma 1 (eq. Preconditioners): primal gamma = 1 / column abs-sum, dual
+    gamma = 1 / row abs-sum, of the stacked operator; returns the per-variable
+    value together with whether every column (row) of the variable agrees."""
+    out = {}
+    for prim in ("u", "s", "t"):
+        colsum = sum(np.asarray(abs(blocks[(d, prim)]).sum(axis=0)).ravel() for d in ("Y", "y2", "y3"))
+        out[prim] = (1.0 / colsum.max(), bool(np.allclose(colsum, colsum[0])))
+    for dual in ("Y", "y2", "y3"):
+        rowsum = sum(np.asarray(abs(blocks[(dual, p)]).sum(axis=1)).ravel() for p in ("u", "s", "t"))
+        out[dual] = (1.0 / rowsum.max(), bool(np.allclose(rowsum, rowsum[0])))
+    return out
+
+
+def radii(N: int, sigma: float, p_s: float, p_t: float, rho: float = 0.95):
+    """eq. (RadiusSet): alpha = rho N p_s / 2, beta = rho 0.5 N p_t (1 - p_s) / 2,
+    eps = rho sqrt(sigma^2 N (1 - p_s)); with sigma = 0 the paper fixes eps = 0.01."""
+    alpha = rho * N * p_s / 2.0
+    beta = rho * 0.5 * N * p_t * (1.0 - p_s) / 2.0
+    eps = rho * math.sqrt(sigma * sigma * N * (1.0 - p_s)) if sigma > 0 else 0.01
+    return eps, alpha, beta
+
+
+# ----------------------------------------------------------------------------
+# Alg. 1: the P-PDS solver.
+# ----------------------------------------------------------------------------
+def init_state(v: np.ndarray, k: int) -> dict:
+    """Initial values (Alg. 1 leaves them open): u = v, s = t = 0, duals 0."""
+    v = np.asarray(v, dtype=np.float64)
+    N1, N2, N3 = v.shape
+    z = np.zeros_like(v)
+    return {"u": v.copy(), "s": z.copy(), "t": z.copy(), "y2": z.copy(), "y3": z.copy(),
+            "Y": np.zeros((N1 * N2, k * k, 2 * N3))}
+
+
+def iterate(state: dict, v: np.ndarray, k: int, eps: float, alpha: float, beta: float,
+            mu_min: float, mu_max: float, gammas: dict) -> tuple[dict, float]:
+    """One pass of Alg. 1 (steps 2-14); returns (new state, relative change).
+
+    The relative change is eq. (StopCri_simulated): ||u+ - u||_2 / ||u||_2.
+    """
+    v = np.asarray(v, dtype=np.float64)
+    u, s, t, y2, y3, Y = (state[n] for n in ("u", "s", "t", "y2", "y3", "Y"))
+    g = gammas
+    # Step 2: u update, box projection.
+    u_new = proj_box(u - g["u"] * (linear_op_adjoint_u(Y, k, u.shape) + y3), mu_min, mu_max)
+    # Step 3: sparse noise, l1 ball of radius alpha.
+    s_new = proj_l1_ball(s - g["s"] * y3, alpha)
+    # Step 4: stripe noise, l1 ball of radius beta.
+    t_new = proj_l1_ball(t - g["t"] * (diff_adj(y2, AXIS_V) + y3), beta)
+    # Steps 5-7: extrapolation.
+    ub, sb, tb = 2.0 * u_new - u, 2.0 * s_new - s, 2.0 * t_new - t
+    # Steps 8-11: every block dual, through the nuclear-norm conjugate prox.
+    Y_new = block_dual_update(Y, structure_tensors(ub, k), g["Y"])
+    # Step 12: prox of the conjugate of iota_{0} is the identity (eq. prox_zeroset).
+    y2_new = y2 + g["y2"] * diff(tb, AXIS_V)
+    # Steps 13-14: fidelity dual through the l2-ball projection.
+    y3p = y3 + g["y3"] * (ub + sb + tb)
+    y3_new = y3p - g["y3"] * proj_l2_ball(y3p / g["y3"], v, eps)
+    du = math.sqrt(float(np.sum((u_new - u) ** 2)))
+    nu = math.sqrt(float(np.sum(u * u)))
+    rel = du / nu if nu > 0 else du
+    return {"u": u_new, "s": s_new, "t": t_new, "y2": y2_new, "y3": y3_new, "Y": Y_new}, rel
+
+
+def solve(v: np.ndarray, k: int, eps: float, alpha: float, beta: float, mu_min: float = 0.0,
+          mu_max: float = 1.0, max_iter: int = 5000, tol: float = 1e-5, policy: str = "paper",
+          state: dict | None = None, trace: list | None = None):
+    """Run Alg. 1 until the relative change is below ``tol`` or ``max_iter`` passes.
+
+    Returns (state, iterations completed, last relative change).
+    """
+    v = np.asarray(v, dtype=np.float64)
+    N1, N2, _ = v.shape
+    gam = step_sizes(N1, N2, k, policy)
+    st = init_state(v, k) if state is None else state
+    rel = float("inf")
+    it = 0
+    while it < max_iter:
+        st, rel = iterate(st, v, k, eps, alpha, beta, mu_min, mu_max, gam)
+        it += 1
+        if trace is not None:
+            trace.append(rel)
+        if rel < tol:
+            break
+    return st, it, rel
+
+
+# ----------------------------------------------------------------------------
+# Sec. IV-A: evaluation.
+# ----------------------------------------------------------------------------
+def mpsnr(u: np.ndarray, ref: np.ndarray, trim: int = 3) -> float:
+    """eq. (MPSNR) with peak 1, averaged over bands, the first and last ``trim``
+    bands dropped (the paper cuts three because of the circulant boundary)."""
+    u = np.asarray(u, np.float64)
+    ref = np.asarray(ref, np.float64)
+    N1, N2, N3 = u.shape
+    bands = range(trim, N3 - trim) if N3 > 2 * trim else range(N3)
+    vals = []
+    for b in bands:
+        err = float(np.sum((u[:, :, b] - ref[:, :, b]) ** 2))
+        vals.append(10.0 * math.log10(N1 * N2 / err) if err > 0 else float("inf"))
+    return float(np.mean(vals))
+
+
+def objective(u: np.ndarray, k: int) -> float:
+    """S3TTV(u) = sum_l ||T_u^(l)||_*, eq. (S3TTV_Lu)."""
+    X = structure_tensors(np.asarray(u, np.float64), k)
+    return float(np.linalg.svd(X, compute_uv=False).sum())

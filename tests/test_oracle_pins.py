@@ -1,0 +1,447 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each oracle function is checked against something other than itself: brute force
+on tiny inputs built from the index definitions, optimality conditions of the
+proximity operators, closed forms, invariances, and values the paper prints
+(``tests/golden/``).  A plausible mistake (a dropped term, a wrong sign or index,
+a transposed operand) fails at least one of these.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+# ---------------------------------------------------------------------------
+# Sec. II-A difference operators.
+# ---------------------------------------------------------------------------
+def _brute_diff(x, axis):
+    N1, N2, N3 = x.shape
+    y = np.zeros_like(x)
+    for i in range(N1):
+        for j in range(N2):
+            for b in range(N3):
+                nxt = [((i + 1) % N1, j, b), (i, (j + 1) % N2, b), (i, j, (b + 1) % N3)][axis]
+                y[i, j, b] = x[nxt] - x[i, j, b]
+    return y
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_diff_matches_brute_force_and_adjoint(axis):
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((3, 4, 5))
+    y = rng.standard_normal((3, 4, 5))
+    np.testing.assert_allclose(O.diff(x, axis), _brute_diff(x, axis), rtol=0, atol=1e-14)
+    lhs = np.sum(O.diff(x, axis) * y)
+    rhs = np.sum(x * O.diff_adj(y, axis))
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + 1)
+    # a constant has no differences
+    assert np.all(O.diff(np.full((3, 4, 5), 0.7), axis) == 0)
+
+
+def test_vertical_stripe_has_no_vertical_difference():
+    """C1 reading: a vertical stripe (constant down a column i) has D_v t = 0 (Sec. III-B)."""
+    t = np.zeros((6, 7, 3))
+    t[:, 2, :] = 0.4
+    t[:, 5, 1] = -0.3
+    assert np.all(O.diff(t, O.AXIS_V) == 0)
+    assert np.any(O.diff(t, O.AXIS_H) != 0)
+
+
+# ---------------------------------------------------------------------------
+# Sec. III-A structure tensors.
+# ---------------------------------------------------------------------------
+def _brute_tensors(u, k):
+    """Expanded second-order difference, element by element (no composition)."""
+    N1, N2, N3 = u.shape
+    X = np.zeros((N1 * N2, k * k, 2 * N3))
+    for p in range(N1):
+        for q in range(N2):
+            for a in range(k):
+                for c in range(k):
+                    i, j = (p + a) % N1, (q + c) % N2
+                    for b in range(N3):
+                        b1, i1, j1 = (b + 1) % N3, (i + 1) % N1, (j + 1) % N2
+                        fv = u[i1, j, b1] - u[i1, j, b] - u[i, j, b1] + u[i, j, b]
+                        fh = u[i, j1, b1] - u[i, j1, b] - u[i, j, b1] + u[i, j, b]
+                        X[p * N2 + q, a * k + c, 2 * b] = fv
+                        X[p * N2 + q, a * k + c, 2 * b + 1] = fh
+    return X
+
+
+@pytest.mark.parametrize("shape,k", [((4, 5, 3), 2), ((3, 3, 4), 3), ((5, 4, 2), 1), ((4, 4, 3), 4)])
+def test_structure_tensors_brute_force(shape, k):
+    rng = np.random.default_rng(2)
+    u = rng.standard_normal(shape)
+    Xb = _brute_tensors(u, k)
+    np.testing.assert_allclose(O.structure_tensors(u, k), Xb, rtol=0, atol=1e-13)
+    N1, N2, _ = shape
+    for p, q in [(0, 0), (N1 - 1, N2 - 1), (1 % N1, 2 % N2)]:
+        np.testing.assert_allclose(O.structure_tensor_block(u, k, p, q), Xb[p * N2 + q], atol=1e-13)
+
+
+@pytest.mark.parametrize("shape,k", [((4, 5, 3), 2), ((6, 5, 4), 3), ((5, 5, 2), 5)])
+def test_structure_tensor_adjoint_identity(shape, k):
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal(shape)
+    Y = rng.standard_normal((shape[0] * shape[1], k * k, 2 * shape[2]))
+    lhs = np.sum(O.structure_tensors(u, k) * Y)
+    rhs = np.sum(u * O.linear_op_adjoint_u(Y, k, shape))
+    assert abs(lhs - rhs) <= 1e-11 * (abs(lhs) + 1)
+
+
+def test_assembled_operator_agrees_with_oracle_operators():
+    """The sparse operator built from index definitions equals the oracle's
+    forward map and its transpose equals the oracle's adjoint (Alg. 1 step 2)."""
+    shape, k = (4, 3, 3), 2
+    A = O.assemble_operator(*shape, k)
+    rng = np.random.default_rng(4)
+    u = rng.standard_normal(shape)
+    Y = rng.standard_normal((12, k * k, 2 * shape[2]))
+    np.testing.assert_allclose(A[("Y", "u")] @ u.ravel(), O.structure_tensors(u, k).ravel(), atol=1e-13)
+    np.testing.assert_allclose(A[("Y", "u")].T @ Y.ravel(),
+                               O.linear_op_adjoint_u(Y, k, shape).ravel(), atol=1e-12)
+    t = rng.standard_normal(shape)
+    np.testing.assert_allclose(A[("y2", "t")] @ t.ravel(), O.diff(t, O.AXIS_V).ravel(), atol=1e-14)
+
+
+def test_low_rank_spectra_give_low_rank_tensors():
+    """Appendix A direction: a cube whose spectra span r vectors has structure
+    tensors of rank <= r (the differences are linear in the spectra)."""
+    rng = np.random.default_rng(5)
+    N1, N2, N3, k, r = 7, 6, 12, 3, 2
+    A = rng.standard_normal((N1, N2, r))
+    E = rng.standard_normal((r, N3))
+    u = A @ E
+    X = O.structure_tensors(u, k)
+    rk = lambda M: np.linalg.matrix_rank(M, tol=1e-9)
+    # the vertical and the horizontal halves each lie in the span of the r
+    # differenced spectra; side by side (eq. SSST) at most 2r
+    assert max(rk(X[l][:, 0::2]) for l in range(X.shape[0])) == r
+    assert max(rk(X[l][:, 1::2]) for l in range(X.shape[0])) == r
+    assert max(rk(X[l]) for l in range(X.shape[0])) <= 2 * r
+
+
+def test_appendix_a_rank_inequality():
+    """Appendix A: rank(U) <= rank(D'_v U D'_s) + 2 for a block U (k^2 x N3), with
+    D' the (non-periodic) difference matrices; checked on random low-rank U."""
+    rng = np.random.default_rng(6)
+    k2, N3 = 9, 10
+    Dv = np.eye(k2, k=1)[:-1] - np.eye(k2)[:-1]       # (k2-1) x k2, rank k2-1
+    Ds = (np.eye(N3, k=1)[:-1] - np.eye(N3)[:-1]).T    # N3 x (N3-1), rank N3-1
+    for r in range(1, 6):
+        U = rng.standard_normal((k2, r)) @ rng.standard_normal((r, N3))
+        assert np.linalg.matrix_rank(U) <= np.linalg.matrix_rank(Dv @ U @ Ds) + 2
+
+
+# ---------------------------------------------------------------------------
+# Step sizes: eq. (stepsize_denoising), Lemma 1, convergence condition.
+# ---------------------------------------------------------------------------
+def test_lemma1_reproduces_printed_step_sizes():
+    g = _gold("stepsizes.json")
+    N1, N2, N3, k = 4, 5, 3, 2
+    lem = O.lemma1_step_sizes(O.assemble_operator(N1, N2, N3, k))
+    for key, gold in (("s", g["gamma_s"]), ("t", g["gamma_t"]), ("Y", g["gamma_Y"]),
+                      ("y2", g["gamma_y2"]), ("y3", g["gamma_y3"])):
+        val, uniform = lem[key]
+        assert uniform
+        assert val == pytest.approx(gold, rel=1e-15)
+    # u: Lemma 1 gives 1/(8k^2+1) exactly; the printed 1/(8L+1) is never larger
+    val, uniform = lem["u"]
+    assert uniform and val == pytest.approx(1.0 / (8 * k * k + 1), rel=1e-15)
+    gp = O.step_sizes(N1, N2, k, "paper")
+    ge = O.step_sizes(N1, N2, k, "pc_exact")
+    assert gp["u"] == pytest.approx(1.0 / (8 * N1 * N2 + 1)) and gp["u"] <= val
+    assert ge["u"] == pytest.approx(val)
+    for key, gkey in (("s", "gamma_s"), ("t", "gamma_t"), ("Y", "gamma_Y"), ("y2", "gamma_y2"), ("y3", "gamma_y3")):
+        assert gp[key] == pytest.approx(g[gkey]) and ge[key] == pytest.approx(g[gkey])
+
+
+@pytest.mark.parametrize("policy", ["paper", "pc_exact"])
+def test_convergence_condition_holds(policy):
+    """Theorem 1 condition: ||Gamma_2^1/2 A Gamma_1^1/2||_op^2 < 1."""
+    import scipy.sparse as sp
+    N1, N2, N3, k = 4, 4, 3, 2
+    B = O.assemble_operator(N1, N2, N3, k)
+    A = sp.bmat([[B[(d, p)] for p in ("u", "s", "t")] for d in ("Y", "y2", "y3")]).toarray()
+    g = O.step_sizes(N1, N2, k, policy)
+    N = N1 * N2 * N3
+    g1 = np.concatenate([np.full(N, g["u"]), np.full(N, g["s"]), np.full(N, g["t"])])
+    nY = B[("Y", "u")].shape[0]
+    g2 = np.concatenate([np.full(nY, g["Y"]), np.full(N, g["y2"]), np.full(N, g["y3"])])
+    M = np.sqrt(g2)[:, None] * A * np.sqrt(g1)[None, :]
+    nrm2 = np.linalg.norm(M, 2) ** 2
+    assert nrm2 < 1.0
+
+
+# ---------------------------------------------------------------------------
+# Proximity operators.
+# ---------------------------------------------------------------------------
+def test_prox_nuclear_hand_examples():
+    for case in _gold("nuclear_prox_hand.json")["cases"]:
+        out = O.prox_nuclear(np.array(case["A"]), case["gamma"])
+        np.testing.assert_allclose(out, np.array(case["out"]), atol=1e-14)
+
+
+@pytest.mark.parametrize("m,n", [(4, 7), (9, 4), (5, 5), (1, 6)])
+def test_prox_nuclear_optimality(m, n):
+    """P = prox_{g||.||_*}(A) iff (A-P)/g is a subgradient of ||.||_* at P:
+    ||(A-P)/g||_2 <= 1 and <(A-P)/g, P> = ||P||_*."""
+    rng = np.random.default_rng(7)
+    for g in (0.1, 1.0, 3.0):
+        A = rng.standard_normal((m, n))
+        P = O.prox_nuclear(A, g)
+        W = (A - P) / g
+        assert np.linalg.norm(W, 2) <= 1 + 1e-12
+        assert np.sum(W * P) == pytest.approx(np.linalg.svd(P, compute_uv=False).sum(), rel=1e-12, abs=1e-12)
+
+
+def _is_spectral_projection(Yp, Yn, rng, trials=200):
+    """Yn = argmin_{||Z||_2 <= 1} ||Z - Yp||_F: feasible, and the variational
+    inequality <Yp - Yn, Z - Yn> <= 0 holds for every feasible Z."""
+    assert np.linalg.norm(Yn, 2) <= 1 + 1e-12
+    for _ in range(trials):
+        Z = rng.standard_normal(Yp.shape)
+        Z /= max(1.0, np.linalg.norm(Z, 2)) * rng.uniform(1.0, 3.0)
+        assert np.sum((Yp - Yn) * (Z - Yn)) <= 1e-10
+
+
+@pytest.mark.parametrize("k2,cols", [(9, 32), (25, 16), (9, 4), (4, 40)])
+def test_block_dual_update_is_projection_on_spectral_ball(k2, cols):
+    """Steps 9-10 through Moreau's identity (eq. ProxConjugate) equal the
+    projection onto the spectral-norm unit ball: clip singular values at 1."""
+    rng = np.random.default_rng(8)
+    for scale in (0.05, 0.5, 3.0):
+        Y = scale * rng.standard_normal((k2, cols))
+        X = scale * rng.standard_normal((k2, cols))
+        Yn = O.block_dual_update(Y, X, 0.25)
+        _is_spectral_projection(Y + 0.25 * X, Yn, rng)
+        # idempotent
+        np.testing.assert_allclose(O.block_dual_update(Yn, np.zeros_like(X), 0.25), Yn, atol=1e-12)
+
+
+def test_block_dual_update_special_cases():
+    rng = np.random.default_rng(9)
+    # all singular values below 1: identity
+    Y = rng.standard_normal((9, 20))
+    Y *= 0.9 / np.linalg.norm(Y, 2)
+    np.testing.assert_allclose(O.block_dual_update(Y, np.zeros_like(Y), 0.25), Y, atol=1e-13)
+    # k = 1: each block is one row, projected onto the unit l2 ball (textbook)
+    rows = rng.standard_normal((50, 1, 12)) * rng.uniform(0.1, 3.0, size=(50, 1, 1))
+    out = O.block_dual_update(rows, np.zeros_like(rows), 0.25)
+    nrm = np.linalg.norm(rows, axis=2, keepdims=True)
+    np.testing.assert_allclose(out, rows / np.maximum(nrm, 1.0), atol=1e-13)
+    # rank-deficient block with one singular value exactly 1 and one at 2
+    u1, u2 = np.eye(5)[0], np.eye(5)[3]
+    v1, v2 = np.eye(8)[1], np.eye(8)[6]
+    B = 1.0 * np.outer(u1, v1) + 2.0 * np.outer(u2, v2)
+    np.testing.assert_allclose(O.block_dual_update(B, np.zeros_like(B), 0.25),
+                               np.outer(u1, v1) + np.outer(u2, v2), atol=1e-13)
+    # non-expansive
+    A1, A2 = rng.standard_normal((2, 9, 10)) * 2
+    P1 = O.block_dual_update(A1, 0 * A1, 0.25)
+    P2 = O.block_dual_update(A2, 0 * A2, 0.25)
+    assert np.linalg.norm(P1 - P2) <= np.linalg.norm(A1 - A2) + 1e-12
+
+
+def test_gram_route_equals_svd_route():
+    """The reading used by the GPU path: with G = Y'Y'^T = V diag(lam) V^T,
+    clip(Y') = V diag(min(1, lam^-1/2)) V^T Y'.  Pinned here in FP64."""
+    rng = np.random.default_rng(10)
+    for _ in range(20):
+        Yp = rng.standard_normal((25, 64)) * rng.uniform(0.01, 0.5)
+        lam, V = np.linalg.eigh(Yp @ Yp.T)
+        f = np.where(lam > 1, 1.0 / np.sqrt(np.maximum(lam, 1e-300)), 1.0)
+        np.testing.assert_allclose((V * f) @ V.T @ Yp, O.block_dual_update(Yp, 0 * Yp, 0.25), atol=1e-12)
+
+
+def _bisect_tau(a, r):
+    lo, hi = 0.0, float(a.max())
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if np.maximum(a - mid, 0).sum() > r:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def test_l1_ball_hand_examples():
+    for case in _gold("l1_ball_hand.json")["cases"]:
+        out = O.proj_l1_ball(np.array(case["x"]), case["radius"])
+        np.testing.assert_allclose(out, np.array(case["out"]), atol=1e-15)
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 100, 5000])
+def test_l1_ball_vs_bisection_and_kkt(n):
+    rng = np.random.default_rng(11 + n)
+    x = rng.standard_normal(n) * rng.uniform(0.1, 5, size=n)
+    x[rng.uniform(size=n) < 0.1] = 0.0
+    l1 = np.abs(x).sum()
+    for r in (0.0, 1e-3 * l1, 0.3 * l1, 0.999 * l1, l1, 2 * l1):
+        y = O.proj_l1_ball(x, r)
+        if r >= l1:
+            np.testing.assert_array_equal(y, x)
+            continue
+        if r == 0:
+            assert np.all(y == 0)
+            continue
+        tau = _bisect_tau(np.abs(x), r)
+        np.testing.assert_allclose(y, np.sign(x) * np.maximum(np.abs(x) - tau, 0), atol=1e-9 * (1 + np.abs(x).max()))
+        # KKT: on the sphere, signs kept, one common shrink tau on the support
+        assert np.abs(y).sum() == pytest.approx(r, rel=1e-12)
+        assert np.all(np.sign(y[y != 0]) == np.sign(x[y != 0]))
+        sup = y != 0
+        shr = np.abs(x[sup]) - np.abs(y[sup])
+        assert np.ptp(shr) <= 1e-9 * (1 + np.abs(x).max())
+        assert np.all(np.abs(x[~sup]) <= shr[0] + 1e-9)
+
+
+def test_l1_ball_enumeration_tiny():
+    """Brute force over supports and sign patterns for n <= 5."""
+    import itertools
+    rng = np.random.default_rng(12)
+    for _ in range(40):
+        n = int(rng.integers(1, 6))
+        x = rng.standard_normal(n) * 2
+        r = float(rng.uniform(0.05, np.abs(x).sum()))
+        best, bestd = None, np.inf
+        # candidates: for each support S, y_S = sign(x_S)(|x_S| - tau) with tau = (sum|x_S| - r)/|S|
+        for m in range(1, n + 1):
+            for S in itertools.combinations(range(n), m):
+                S = list(S)
+                tau = (np.abs(x[S]).sum() - r) / m
+                y = np.zeros(n)
+                y[S] = np.sign(x[S]) * (np.abs(x[S]) - tau)
+                if np.any(np.abs(x[S]) - tau < -1e-15):
+                    continue
+                d = np.sum((y - x) ** 2)
+                if d < bestd and np.abs(y).sum() <= r + 1e-12:
+                    best, bestd = y, d
+        np.testing.assert_allclose(O.proj_l1_ball(x, r), best, atol=1e-12)
+
+
+def test_box_and_l2_ball():
+    x = np.array([-0.5, 0.25, 1.5, 1.0, 0.0])
+    np.testing.assert_array_equal(O.proj_box(x, 0.0, 1.0), [0.0, 0.25, 1.0, 1.0, 0.0])
+    v = np.array([1.0, 2.0])
+    np.testing.assert_allclose(O.proj_l2_ball(np.array([4.0, 6.0]), v, 2.5), [2.5, 4.0])  # 3-4-5 triangle
+    np.testing.assert_array_equal(O.proj_l2_ball(np.array([1.5, 2.0]), v, 2.5), [1.5, 2.0])
+    rng = np.random.default_rng(13)
+    for _ in range(20):
+        c = rng.standard_normal(30)
+        z = rng.standard_normal(30) * 3
+        eps = float(rng.uniform(0.1, 5))
+        p = O.proj_l2_ball(z, c, eps)
+        assert np.linalg.norm(p - c) <= eps * (1 + 1e-14)
+        for _ in range(20):
+            w = c + rng.standard_normal(30)
+            w = c + (w - c) * min(1.0, eps / np.linalg.norm(w - c)) * rng.uniform(0, 1)
+            assert np.dot(z - p, w - p) <= 1e-10
+
+
+# ---------------------------------------------------------------------------
+# Experiment rules and metrics (Sec. IV-A).
+# ---------------------------------------------------------------------------
+def test_radii_parity_cube():
+    g = _gold("radii_parity_cube.json")
+    eps, alpha, beta = O.radii(g["N"], g["sigma"], g["p_s"], g["p_t"], g["rho"])
+    assert alpha == pytest.approx(g["alpha"], rel=1e-14)
+    assert beta == pytest.approx(g["beta"], rel=1e-14)
+    assert eps == pytest.approx(g["eps"], rel=1e-14)
+    assert O.radii(100, 0.0, 0.0, 0.0)[0] == 0.01
+
+
+def test_mpsnr_hand():
+    g = _gold("mpsnr_hand.json")
+    ref = np.random.default_rng(14).uniform(size=g["shape"])
+    u = ref + np.array(g["band_delta"])[None, None, :]
+    assert O.mpsnr(u, ref) == pytest.approx(g["mpsnr"], abs=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Alg. 1 as a whole: fixed points, invariances, convergence.
+# ---------------------------------------------------------------------------
+def _run(v, k, iters, policy="paper", eps=1.0, alpha=2.0, beta=1.0, **kw):
+    st, it, rel = O.solve(v, k, eps, alpha, beta, max_iter=iters, tol=0.0, policy=policy, **kw)
+    return st
+
+
+@pytest.mark.parametrize("kind", ["constant", "spectrally_flat"])
+def test_fixed_points(kind):
+    """v inside the box with D_s v = 0 is a solution (objective 0, feasible);
+    Alg. 1 started there stays there: u = v, s = t = 0, all duals 0."""
+    rng = np.random.default_rng(15)
+    if kind == "constant":
+        v = np.full((5, 6, 4), 0.37)
+    else:
+        v = np.repeat(rng.uniform(0.1, 0.9, size=(5, 6, 1)), 4, axis=2)
+    st = _run(v, 2, 7)
+    np.testing.assert_allclose(st["u"], v, atol=1e-15)
+    for key in ("s", "t", "y2", "y3", "Y"):
+        assert np.abs(st[key]).max() <= 1e-15
+
+
+def test_zero_radii_keep_noise_components_zero():
+    from synthetic import CubeSpec, make_cube
+    _, v = make_cube(CubeSpec(8, 8, 6, regions=3, endmembers=2, seed=3))
+    st = _run(v, 2, 10, alpha=0.0, beta=0.0)
+    assert np.all(st["s"] == 0) and np.all(st["t"] == 0)
+
+
+@pytest.mark.parametrize("shift", [(2, 0, 0), (0, 3, 0), (0, 0, 1), (1, -2, 2)])
+def test_circular_shift_equivariance(shift):
+    """All boundaries are periodic, so shifting v circularly shifts u, s, t."""
+    from synthetic import CubeSpec, make_cube
+    _, v = make_cube(CubeSpec(8, 7, 6, regions=3, endmembers=2, seed=4))
+    v = v.astype(np.float64)
+    a = _run(v, 3, 6)
+    b = _run(np.roll(v, shift, axis=(0, 1, 2)), 3, 6)
+    for key in ("u", "s", "t", "y2", "y3"):
+        np.testing.assert_allclose(b[key], np.roll(a[key], shift, axis=(0, 1, 2)), atol=1e-11)
+
+
+def test_convergence_feasibility_and_residuals():
+    """P-PDS converges (Theorem 1): at the end the constraints of Prob.
+    (S3TTV_denoising) hold and successive differences vanish."""
+    from synthetic import CubeSpec, make_cube
+    spec = CubeSpec(8, 8, 6, regions=3, endmembers=2, sigma=0.05, p_s=0.05, p_t=0.1, seed=5)
+    clean, v = make_cube(spec)
+    v = v.astype(np.float64)
+    eps, alpha, beta = O.radii(v.size, spec.sigma, spec.p_s, spec.p_t)
+    trace = []
+    st, it, rel = O.solve(v, 2, eps, alpha, beta, max_iter=3000, tol=0.0, policy="pc_exact", trace=trace)
+    assert st["u"].min() >= 0.0 and st["u"].max() <= 1.0
+    assert np.abs(st["s"]).sum() <= alpha * (1 + 1e-12)
+    assert np.abs(st["t"]).sum() <= beta * (1 + 1e-12)
+    assert np.linalg.norm(O.diff(st["t"], O.AXIS_V)) <= 1e-3 * (1 + np.linalg.norm(st["t"]))
+    assert np.linalg.norm(st["u"] + st["s"] + st["t"] - v) <= eps * (1 + 1e-3)
+    assert trace[-1] < 1e-4 * max(trace[:10])
+    # one more pass barely moves anything
+    st2, _ = O.iterate(st, v, 2, eps, alpha, beta, 0.0, 1.0, O.step_sizes(8, 8, 2, "pc_exact"))
+    assert np.linalg.norm(st2["u"] - st["u"]) <= 1e-4 * np.linalg.norm(st["u"])
+
+
+def test_parity_cube_improves_mpsnr():
+    """Fig. 11 behaviour on the 32x32x16 parity cube: the restored cube is
+    closer to the clean one than the observation after 300 passes."""
+    from synthetic import WORKLOADS, make_cube
+    spec = WORKLOADS["parity_32x32x16_k3"]
+    clean, v = make_cube(spec)
+    eps, alpha, beta = O.radii(v.size, spec.sigma, spec.p_s, spec.p_t)
+    trace = []
+    st, it, rel = O.solve(v, spec.k, eps, alpha, beta, max_iter=300, tol=0.0, trace=trace)
+    assert it == 300
+    assert O.mpsnr(st["u"], clean) > O.mpsnr(v, clean) + 1.0
+    assert np.median(trace[-20:]) < np.median(trace[1:21])
