@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Throughput of the S3TTV P-PDS solver (Alg. 1) on GB300.
+
+One "step" is one full pass of Alg. 1 (steps 2-14: primal update, both l1-ball
+projections, every block dual with its singular-value clip, both dual updates,
+the fidelity projection and the stop test) over the whole cube.  The headline
+workload is the seeded synthetic 256x256x128 cube with k = 5 blocks.
+
+``value``  P-PDS passes per second over all ranks, inputs resident in HBM, timed
+           with CUDA events on the solver's stream (max over ranks).
+``e2e``    the same rate through the public C ABI call s3ttv_solve with pinned
+           HOST buffers: setup, host->device copy of v, the passes and the
+           device->host copy of u, s, t inside the timed region.
+``roofline`` the dominant kernel (block dual, steps 8-11): algorithmic bytes per
+           launch / its average CUDA-event duration in the timed region.
+``cpu_baseline`` the FP64 oracle timed on this host on a bounded crop, scaled to
+           the full cube (a reported baseline, not a target).
+Also reported: seconds and passes to the paper's stop rule (||u+ - u||/||u|| <
+1e-5, cap 5000) and the restored cube's MPSNR.
+
+``--impl reference`` times the FP64 oracle instead (host cores, rank 0 only).
+Multi-GPU: the method has no exchange step at one cube, so N ranks run N
+independent replicas (weak scaling); only the timing is reduced over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "S3TTV seconds-to-tol at 256×256×128; P-PDS iters/s; % of roofline"
+UNIT = "iter/s"
+DEFAULT_WORKLOAD = "s3ttv_256x256x128_k5"
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (replicas only)
+# ---------------------------------------------------------------------------
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def dist_init(backend):
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def dist_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def dist_max(x, world, device=None):
+    """Max of a float over ranks (identity at world size 1)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu_id)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def nvsmi_id(device_index):
+    import torch
+    try:
+        props = torch.cuda.get_device_properties(device_index)
+        bus = getattr(props, "pci_bus_id", None)
+        dom = getattr(props, "pci_domain_id", None)
+        dev = getattr(props, "pci_device_id", None)
+        if bus is not None and dom is not None and dev is not None:
+            return f"{dom:08x}:{bus:02x}:{dev:02x}.0"
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [x for x in vis.split(",") if x.strip()]
+    if ids and all(x.strip().isdigit() for x in ids) and device_index < len(ids):
+        return ids[device_index].strip()
+    return str(device_index)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded crop of the same workload
+# ---------------------------------------------------------------------------
+def oracle_rate(spec, crop, seconds_budget, min_steps=2, max_steps=None, warmup=0, policy="paper"):
+    """Time oracle passes on the top-left crop x crop x N3 of the workload cube
+    (same generator, same noise model).  Returns (full-cube passes/s, passes,
+    seconds, threads, sample text)."""
+    import numpy as np
+    import oracle as O
+    from synthetic import CubeSpec, make_cube
+    sub = CubeSpec(crop, crop, spec.N3, regions=max(2, spec.regions * crop * crop // (spec.N1 * spec.N2)),
+                   endmembers=spec.endmembers, sigma=spec.sigma, p_s=spec.p_s, p_t=spec.p_t, k=spec.k,
+                   seed=spec.seed)
+    _, v = make_cube(sub)
+    v = v.astype(np.float64)
+    eps, alpha, beta = O.radii(v.size, sub.sigma, sub.p_s, sub.p_t)
+    g = O.step_sizes(spec.N1, spec.N2, spec.k, policy)  # the full cube's step sizes
+    st = O.init_state(v, spec.k)
+    for _ in range(warmup):
+        st, _ = O.iterate(st, v, spec.k, eps, alpha, beta, 0.0, 1.0, g)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        st, _ = O.iterate(st, v, spec.k, eps, alpha, beta, 0.0, 1.0, g)
+        n += 1
+        el = time.perf_counter() - t0
+        if max_steps is not None and n >= max_steps:
+            break
+        if max_steps is None and n >= min_steps and el >= seconds_budget:
+            break
+    per_pass_full = el / n * (spec.N1 * spec.N2) / (crop * crop)
+    try:
+        threads = len(os.sched_getaffinity(0))
+    except AttributeError:
+        threads = os.cpu_count()
+    sample = (f"{n} oracle passes (FP64, numpy/LAPACK SVD per block) on a {crop}x{crop}x{spec.N3} crop, "
+              f"k={spec.k}, scaled by {spec.N1 * spec.N2}/{crop * crop} pixels to one full-cube pass")
+    return 1.0 / per_pass_full, n, el, threads, sample
+
+
+def run_reference(args, spec):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    total = args.steps + args.warmup
+    crop = 32 if total > 40 else 64
+    rate, n, el, threads, sample = oracle_rate(spec, crop, 0.0, max_steps=args.steps, warmup=args.warmup,
+                                               policy=args.policy)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / rate, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "N1": spec.N1, "N2": spec.N2, "N3": spec.N3, "k": spec.k,
+                   "policy": args.policy},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def mpsnr(u, ref, trim=3):
+    import numpy as np
+    u = np.asarray(u, np.float64)
+    ref = np.asarray(ref, np.float64)
+    N1, N2, N3 = u.shape
+    bands = range(trim, N3 - trim) if N3 > 2 * trim else range(N3)
+    err = ((u - ref) ** 2).sum(axis=(0, 1))
+    return float(np.mean([10 * math.log10(N1 * N2 / err[b]) for b in bands]))
+
+
+def run_ours(args, spec):
+    import numpy as np
+    import torch
+    import paper_2404_03313_gb300 as P
+    from synthetic import make_cube
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        dist_init("nccl")
+    dev = local_rank if world > 1 else 0
+    torch.cuda.set_device(dev)
+    P.library()
+    clean, v = make_cube(spec)
+    N = v.size
+    eps, alpha, beta = P.radii(N, spec.sigma, spec.p_s, spec.p_t, 0.95)
+    policy = P.STEP_PC_EXACT if args.policy == "pc_exact" else P.STEP_PAPER
+    stream = torch.cuda.Stream(device=dev)
+    solver = P.Solver(dev, stream=stream)
+    solver.set_option(P.OPT_STEP_POLICY, policy)
+    vd = torch.from_numpy(v).to(f"cuda:{dev}")
+    torch.cuda.synchronize()
+
+    # ---- device-resident timing ----
+    solver.setup(vd, eps, alpha, beta, spec.k)
+    solver.set_option(P.OPT_CHECK_EVERY, max(args.steps, args.warmup, 1))
+    solver.iterate(args.warmup)
+    solver.set_option(P.OPT_PROFILE, 1)
+    launches0 = solver.launch_count()
+    sampler = ClockSampler(nvsmi_id(dev)).start()
+    time.sleep(0.3)
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    info = solver.iterate(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = dist_max(ms, world, device=f"cuda:{dev}")
+    launches = solver.launch_count() - launches0
+    stats = solver.kernel_stats()
+    solver.set_option(P.OPT_PROFILE, 0)
+    value = world * args.steps / (ms_max / 1000.0)
+
+    # ---- roofline of the dominant kernel (block dual, steps 8-11) ----
+    k2 = spec.k * spec.k
+    bd_ms, bd_n = stats["block_dual"]
+    bd_avg_s = bd_ms / max(bd_n, 1) / 1000.0
+    bytes_per_voxel = 16 * k2 + 4 + 8  # Y read + write, ubar read, Z written once
+    alg_bytes = bytes_per_voxel * N
+    peak, peak_src = measured_peaks()
+    achieved = alg_bytes / bd_avg_s / 1e9 if bd_avg_s > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "block_dual_kernel<5>", "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": bd_avg_s * 1000.0}
+    pass_bytes = (16 * k2 + 120) * N
+    kernel_ms = {name: (t / max(c, 1)) for name, (t, c) in stats.items()}
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    vh = torch.from_numpy(v).pin_memory()
+    outs = [torch.empty(v.shape, dtype=torch.float32).pin_memory() for _ in range(3)]
+    dist_barrier(world)
+    t0 = time.perf_counter()
+    solver.solve(vh.numpy(), eps, alpha, beta, spec.k, max_iter=args.steps, tol=0.0,
+                 out=[o.numpy() for o in outs])
+    e2e_s = time.perf_counter() - t0
+    e2e_s = dist_max(e2e_s, world, device=f"cuda:{dev}")
+    e2e = {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * N / args.steps,
+           "d2h_bytes_per_step": 12 * N / args.steps, "seconds": e2e_s}
+
+    # ---- seconds to the paper's stop rule ----
+    tol_run = None
+    if not args.no_tol_run:
+        solver.set_option(P.OPT_CHECK_EVERY, 16)
+        u, s, t, inf = solver.solve(vd, eps, alpha, beta, spec.k, max_iter=5000, tol=1e-5)
+        torch.cuda.synchronize()
+        tol_run = {"seconds": inf["seconds"], "iters": inf["iters"], "converged": bool(inf["converged"]),
+                   "rel_change": inf["rel_change"], "mpsnr_restored": mpsnr(u.cpu().numpy(), clean),
+                   "mpsnr_observed": mpsnr(v, clean), "stop_tol": 1e-5, "max_iter": 5000}
+
+    # ---- CPU baseline (oracle), rank 0 at N = 1 only ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, n, el, threads, sample = oracle_rate(spec, 64, args.cpu_seconds, policy=args.policy)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+               "seconds": el}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "N1": spec.N1, "N2": spec.N2, "N3": spec.N3, "k": spec.k,
+                       "policy": args.policy, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (block duals Y: %.2f GB, read and written every pass)"
+                             % (8 * k2 * N / 1e9)},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "cpu_baseline": cpu,
+            "pass_roofline": {"bound": "hbm", "algorithmic_bytes": pass_bytes,
+                              "achieved": pass_bytes / (ms_max / args.steps / 1000.0) / 1e9, "peak": peak,
+                              "unit": "GB/s"},
+            "kernel_avg_ms": kernel_ms, "jacobi_nonconverged_last_pass_batch": info["jacobi_nonconverged"],
+            "to_tol": tol_run,
+        }
+        out["pass_roofline"]["frac"] = out["pass_roofline"]["achieved"] / peak
+        print(json.dumps(out), flush=True)
+    solver.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--policy", choices=("paper", "pc_exact"), default="paper")
+    ap.add_argument("--no-tol-run", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    from synthetic import WORKLOADS
+    spec = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, spec)
+    return run_ours(args, spec)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,209 @@
+/*
+ * s3ttv.h - C ABI of a GB300 (sm_103a) solver for S3TTV hyperspectral
+ * denoising and destriping (Takemoto, Naganuma, Ono, "Spatio-Spectral Structure
+ * Tensor Total Variation for Hyperspectral Image Denoising and Destriping").
+ *
+ * The solver runs the preconditioned primal-dual splitting of Alg. 1 (Sec. III-C)
+ * on Prob. (S3TTV_denoising) (Sec. III-B):
+ *
+ *     min_{u,s,t}  sum_l || P_l D D_s u ||_*
+ *     s.t.  ||s||_1 <= alpha,  ||t||_1 <= beta,  D_v t = 0,
+ *           ||u + s + t - v||_2 <= eps,  mu_min <= u <= mu_max,
+ *
+ * where D_v, D_h, D_s are forward differences with periodic boundaries along the
+ * vertical (first), horizontal (second) and spectral (third) axes (Sec. II-A),
+ * and P_l extracts the k x k x N3 block anchored at pixel l (eq. rewrite_Lu).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Cube layout: FP32, C-contiguous [N1][N2][N3], band fastest: element (i, j, b)
+ *   is at offset (i*N2 + j)*N3 + b (a torch tensor of shape (N1, N2, N3)).
+ * Blocks: one per anchor pixel l = p*N2 + q (all N1*N2 stride-1 windows, wrapped
+ *   periodically as the footnote of Sec. III-A describes), covering pixels
+ *   ((p+a) mod N1, (q+c) mod N2), a, c in [0, k).  A block matrix has k*k rows
+ *   (row r = a*k + c) and 2*N3 columns in the order of eq. (SSST): column 2b holds
+ *   D_v D_s, column 2b+1 holds D_h D_s of band b.  The block dual "Y" is stored
+ *   [N1*N2][k*k][2*N3] in that order.
+ * Pointers: unless an entry point says otherwise, a data pointer may point to
+ *   device memory of the context's GPU or to host memory (pageable or pinned);
+ *   the library asks the CUDA runtime which it is and stages host buffers through
+ *   its own device workspace.  The caller owns every buffer it passes; the library
+ *   never keeps a pointer past the call and never writes to an input.
+ * Streams: all work runs on the context's stream; every entry point returns after
+ *   that stream has finished the call's work (synchronous semantics).
+ * Errors: each call returns an s3ttv_status; negative values are failures and
+ *   leave the outputs untouched (argument errors are detected on the host before
+ *   any launch).  s3ttv_last_error(ctx) gives a one-line description.  After
+ *   S3TTV_ECUDA the context should be destroyed.  No C++ exception crosses the ABI.
+ * Threads: a context must not be used by two host threads at the same time.
+ */
+#ifndef S3TTV_H
+#define S3TTV_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct s3ttv_ctx s3ttv_ctx;
+
+typedef enum s3ttv_status {
+  S3TTV_OK = 0,            /* finished: the stop rule fired                          */
+  S3TTV_MAXITER = 1,       /* finished: iteration cap reached first (results valid)  */
+  S3TTV_EINVAL = -1,       /* invalid argument                                       */
+  S3TTV_ENOMEM = -2,       /* device allocation failed                               */
+  S3TTV_ECUDA = -3,        /* CUDA runtime error                                     */
+  S3TTV_ENUMERIC = -4,     /* NaN or Inf appeared in the iterates                    */
+  S3TTV_EUNSUPPORTED = -5, /* valid but outside what this build supports (see each call) */
+  S3TTV_ESTATE = -6        /* call made before s3ttv_setup                           */
+} s3ttv_status;
+
+/* Per-call report.  Filled by the calls that take it (may be NULL). */
+typedef struct s3ttv_info {
+  int status;              /* the call's return value                                */
+  int iters;               /* P-PDS passes completed by this call                    */
+  int converged;           /* 1 if ||u+ - u|| / ||u|| < tol fired                    */
+  int jacobi_nonconverged; /* blocks whose eigen-solve reached the sweep cap         */
+  double rel_change;       /* ||u+ - u||_2 / ||u||_2 of the last pass (eq. StopCri)  */
+  double seconds;          /* host wall time of the call                             */
+} s3ttv_info;
+
+/* Step-size policies (option S3TTV_OPT_STEP_POLICY).
+ * PAPER: eq. (stepsize_denoising) as printed: gamma_u = 1/(8L+1), L = N1*N2 blocks,
+ *   gamma_s = 1, gamma_t = 1/3, gamma_Y = 1/4, gamma_y2 = 1/2, gamma_y3 = 1/3.
+ * PC_EXACT: the same except gamma_u = 1/(8k^2+1), the exact column abs-sum of
+ *   Lemma 1 (eq. Preconditioners) when every entry of D D_s u lies in k^2 blocks. */
+enum { S3TTV_STEP_PAPER = 0, S3TTV_STEP_PC_EXACT = 1 };
+
+/* Option keys for s3ttv_set_option. */
+enum {
+  S3TTV_OPT_STEP_POLICY = 1,       /* S3TTV_STEP_PAPER (default) or S3TTV_STEP_PC_EXACT  */
+  S3TTV_OPT_CHECK_EVERY = 2,       /* passes between host reads of the stop flag (default 16) */
+  S3TTV_OPT_JACOBI_MAX_SWEEPS = 3, /* sweep cap of the block eigen-solve (default 24, 1..64) */
+  S3TTV_OPT_JACOBI_TOL = 4,        /* relative orthogonality tolerance (default 2e-6)    */
+  S3TTV_OPT_PROFILE = 5            /* 1: time each kernel class of every pass with CUDA
+                                      events on the context stream (resets the totals);
+                                      0: off (default)                                    */
+};
+
+/* Kernel classes reported by s3ttv_kernel_stats. */
+enum {
+  S3TTV_KERNEL_PRIMAL = 0,     /* steps 2-7 for u, arguments of steps 3-4           */
+  S3TTV_KERNEL_L1_SEARCH = 1,  /* l1-ball thresholds of steps 3-4 (5 launches/pass) */
+  S3TTV_KERNEL_BLOCK_DUAL = 2, /* steps 8-11: block duals and their singular values */
+  S3TTV_KERNEL_DUAL = 3,       /* steps 3-4 finish, 12, 13                          */
+  S3TTV_KERNEL_FINALIZE = 4,   /* step 14 scalar and the stop rule                  */
+  S3TTV_KERNEL_CLASSES = 5
+};
+
+/* Which part of the solver state s3ttv_get_state / s3ttv_set_state address. */
+enum {
+  S3TTV_STATE_U = 0,   /* primal u,  cube                                     */
+  S3TTV_STATE_S = 1,   /* primal s,  cube                                     */
+  S3TTV_STATE_T = 2,   /* primal t,  cube                                     */
+  S3TTV_STATE_Y2 = 3,  /* dual y2 (of D_v t = 0), cube                        */
+  S3TTV_STATE_Y3 = 4,  /* dual y3 (of the l2 fidelity ball), cube             */
+  S3TTV_STATE_Y = 5    /* block duals Y_1 .. Y_L, [N1*N2][k*k][2*N3]          */
+};
+
+/* Create a context on CUDA device `device`.  `stream` is a cudaStream_t to run on,
+ * or NULL for a stream the context creates and owns.  Allocates nothing on the
+ * device until a problem is set up.  Returns S3TTV_EINVAL if out is NULL or the
+ * device does not exist, S3TTV_ECUDA on a runtime failure. */
+int s3ttv_create(s3ttv_ctx **out, int device, void *stream);
+
+/* Free the context and all its device workspace.  NULL is allowed. */
+void s3ttv_destroy(s3ttv_ctx *ctx);
+
+/* Static text for a status code. */
+const char *s3ttv_strerror(int status);
+
+/* Text of the last failure seen by this context ("" if none). */
+const char *s3ttv_last_error(const s3ttv_ctx *ctx);
+
+/* Set an option (keys above).  Takes effect at the next setup/iterate. */
+int s3ttv_set_option(s3ttv_ctx *ctx, int key, double value);
+
+/* Bytes of device workspace the context holds now. */
+long long s3ttv_workspace_bytes(const s3ttv_ctx *ctx);
+
+/* Number of kernels the passes of Alg. 1 (s3ttv_iterate, s3ttv_solve) have
+ * launched on this context since it was created (9 per pass, plus one per call). */
+long long s3ttv_launch_count(const s3ttv_ctx *ctx);
+
+/* With S3TTV_OPT_PROFILE on: total device milliseconds (ms[c]) and launches
+ * (launches[c]) of each kernel class c < S3TTV_KERNEL_CLASSES accumulated by
+ * s3ttv_iterate / s3ttv_solve since profiling was switched on.  Host arrays of
+ * S3TTV_KERNEL_CLASSES entries; either may be NULL. */
+int s3ttv_kernel_stats(const s3ttv_ctx *ctx, double *ms, long long *launches);
+
+/* Solve Prob. (S3TTV_denoising) for the observation v with Alg. 1 (Sec. III-C).
+ *
+ * v        observed cube [N1][N2][N3] (host or device).
+ * eps      radius of the l2 fidelity ball (eq. constraint_fidel), >= 0.
+ * alpha    radius of the l1 ball of the sparse noise s (eq. constraint_sparse), >= 0.
+ * beta     radius of the l1 ball of the stripe noise t (eq. constraint_stripe), >= 0.
+ * mu_min, mu_max  box of u (eq. constraint_box), mu_min < mu_max.
+ * k        block side (k x k x N3 blocks), 1 <= k <= min(N1, N2); this build supports k <= 5.
+ * max_iter iteration cap, >= 1.
+ * tol      stop when ||u+ - u||_2 / ||u||_2 < tol (eq. StopCri_simulated), >= 0;
+ *          0 runs exactly max_iter passes.
+ * u        output clean cube (required); s, t: output sparse / stripe noise (NULL skips).
+ * info     optional report.
+ * Initial values: u = v, s = t = 0, every dual 0.  Requires N3 >= 2.
+ * Returns S3TTV_OK, S3TTV_MAXITER, or a negative status. */
+int s3ttv_solve(s3ttv_ctx *ctx, const float *v, int N1, int N2, int N3,
+                float eps, float alpha, float beta, float mu_min, float mu_max,
+                int k, int max_iter, float tol,
+                float *u, float *s, float *t, s3ttv_info *info);
+
+/* Stepping interface (the same solver, split so a caller can time passes,
+ * inspect or replace the state).  s3ttv_setup loads a problem (same arguments and
+ * checks as s3ttv_solve) and sets the initial values; s3ttv_iterate runs up to n
+ * passes of Alg. 1, stopping early when the relative change drops below tol
+ * (tol = 0: exactly n passes); info->iters counts the passes it ran. */
+int s3ttv_setup(s3ttv_ctx *ctx, const float *v, int N1, int N2, int N3,
+                float eps, float alpha, float beta, float mu_min, float mu_max, int k);
+int s3ttv_iterate(s3ttv_ctx *ctx, int n, float tol, s3ttv_info *info);
+
+/* Copy one state variable out of / into the context (after s3ttv_setup).
+ * `which` is an S3TTV_STATE_* value; cubes have N1*N2*N3 floats, Y has
+ * N1*N2*k*k*2*N3 floats in the layout described at the top.  Setting Y also
+ * rebuilds the context's sum_l P_l^T Y_l.  Returns S3TTV_ESTATE before setup. */
+int s3ttv_get_state(s3ttv_ctx *ctx, int which, float *dst);
+int s3ttv_set_state(s3ttv_ctx *ctx, int which, const float *src);
+
+/* Projection onto the l1 ball {x : ||x||_1 <= radius} (the prox of Alg. 1
+ * steps 3-4; Sec. III-C), with the same threshold search the solver uses.
+ * x, out: n floats (host or device; may alias).  radius >= 0.  tau_out (host,
+ * may be NULL) receives the soft threshold (0 when ||x||_1 <= radius, +inf when
+ * radius = 0).  n may be 0. */
+int s3ttv_l1_ball(s3ttv_ctx *ctx, const float *x, float *out, long long n,
+                  double radius, double *tau_out);
+
+/* Block dual update of Alg. 1 steps 8-11 for every block, as the solver runs it:
+ * Y_l <- Y'_l - gamma_Y prox_{gamma_Y^-1 ||.||_*}(Y'_l / gamma_Y) with
+ * Y'_l = Y_l + gamma_Y P_l D D_s ubar, which by Moreau's identity
+ * (eq. ProxConjugate) clips the singular values of Y'_l at 1; then
+ * Z = sum_l P_l^T Y_l is returned split into Zv (column 2b parts) and Zh.
+ * Y: [N1*N2][k*k][2*N3], updated in place; ubar: cube; Zv, Zh: output cubes.
+ * All host or device.  info (may be NULL) reports jacobi_nonconverged.
+ * Uses the context's workspace (replaces any problem set up before). */
+int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, float *Zh,
+                     int N1, int N2, int N3, int k, float gamma_Y, s3ttv_info *info);
+
+/* Radii of eq. (RadiusSet) (Sec. IV-A): alpha = rho N p_s / 2,
+ * beta = rho 0.5 N p_t (1 - p_s) / 2, eps = rho sqrt(sigma^2 N (1 - p_s)), and
+ * eps = 0.01 when sigma = 0 (the paper's choice for its stripe-only case).
+ * All output pointers are host pointers and required. */
+int s3ttv_radii(long long N, double sigma, double p_s, double p_t, double rho,
+                double *eps, double *alpha, double *beta);
+
+/* Step sizes (u, s, t, Y, y2, y3) of a policy for an N1 x N2 image and block k,
+ * written to gammas[6] (host). */
+int s3ttv_step_sizes(int N1, int N2, int k, int policy, double gammas[6]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* S3TTV_H */

@@ -33,6 +33,7 @@ import numpy as np
 __all__ = [
     "AXIS_V", "AXIS_H", "AXIS_S", "diff", "diff_adj", "structure_tensors",
     "structure_tensors_adjoint", "structure_tensor_block", "linear_op_adjoint_u",
+    "linear_op_adjoint_u_at",
     "prox_nuclear", "block_dual_update", "proj_box", "proj_l2_ball",
     "proj_l1_ball", "step_sizes", "assemble_operator", "lemma1_step_sizes",
     "radii", "init_state", "iterate", "solve", "mpsnr", "objective",
@@ -110,6 +111,30 @@ def linear_op_adjoint_u(Y: np.ndarray, k: int, shape) -> np.ndarray:
     """sum_l D_s^T D^T P_l^T Y_l, the dual-to-primal term of Alg. 1 step 2."""
     Zv, Zh = structure_tensors_adjoint(Y, k, shape)
     return diff_adj(diff_adj(Zv, AXIS_V) + diff_adj(Zh, AXIS_H), AXIS_S)
+
+
+def linear_op_adjoint_u_at(Y: np.ndarray, k: int, shape, i: int, j: int, b: int) -> float:
+    """One entry (i, j, b) of sum_l D_s^T D^T P_l^T Y_l, from the definitions.
+
+    (D^T z)(i, j) = z_v(i-1, j) - z_v(i, j) + z_h(i, j-1) - z_h(i, j), then
+    (D_s^T w)(b) = w(b-1) - w(b); z = sum_l P_l^T Y_l gathers, for pixel (x, y),
+    row a*k + c of the block anchored at (x - a, y - c).  ``Y`` may be any array
+    indexable as Y[l, r, col] (for example a GPU tensor moved block by block).
+    """
+    N1, N2, N3 = shape
+
+    def z(x, y, o, bb):
+        tot = 0.0
+        for a in range(k):
+            for c in range(k):
+                l = ((x - a) % N1) * N2 + (y - c) % N2
+                tot += float(Y[l, a * k + c, 2 * (bb % N3) + o])
+        return tot
+
+    def w(bb):
+        return (z(i - 1, j, 0, bb) - z(i, j, 0, bb)) + (z(i, j - 1, 1, bb) - z(i, j, 1, bb))
+
+    return w(b - 1) - w(b)
 
 
 # ----------------------------------------------------------------------------

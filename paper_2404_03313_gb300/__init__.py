@@ -1,0 +1,13 @@
+"""GB300-native S3TTV hyperspectral denoising and destriping.
+
+The solver (Alg. 1 of the paper, P-PDS) runs in hand-written sm_103a CUDA kernels
+behind the C ABI of ``include/s3ttv.h`` (``libs3ttv.so``); this package is the
+thin ctypes binding over it plus the build script.  Nothing here computes on the
+CPU: if the library is not built, calls raise ``S3TTVError``.
+"""
+from ._binding import (  # noqa: F401
+    Info, S3TTVError, Solver, library, radii, step_sizes, LIB_PATH, SIGNATURES, STATE,
+    STEP_PAPER, STEP_PC_EXACT, OPT_STEP_POLICY, OPT_CHECK_EVERY, OPT_JACOBI_MAX_SWEEPS, OPT_JACOBI_TOL,
+    OPT_PROFILE, KERNEL_CLASSES,
+    OK, MAXITER, EINVAL, ENOMEM, ECUDA, ENUMERIC, EUNSUPPORTED, ESTATE,
+)

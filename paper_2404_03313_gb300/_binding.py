@@ -1,0 +1,268 @@
+"""ctypes binding of libs3ttv.so (include/s3ttv.h): argument marshalling only.
+
+Every step of the solver runs in the library's CUDA kernels.  Arrays may be torch
+tensors (CUDA or CPU) or numpy arrays; they must be float32 and C-contiguous.
+If the shared library is missing, every call raises S3TTVError: there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libs3ttv.so")
+
+# status codes (s3ttv_status)
+OK, MAXITER, EINVAL, ENOMEM, ECUDA, ENUMERIC, EUNSUPPORTED, ESTATE = 0, 1, -1, -2, -3, -4, -5, -6
+STEP_PAPER, STEP_PC_EXACT = 0, 1
+OPT_STEP_POLICY, OPT_CHECK_EVERY, OPT_JACOBI_MAX_SWEEPS, OPT_JACOBI_TOL, OPT_PROFILE = 1, 2, 3, 4, 5
+KERNEL_CLASSES = ("primal", "l1_search", "block_dual", "dual", "finalize")
+STATE = {"u": 0, "s": 1, "t": 2, "y2": 3, "y3": 4, "Y": 5}
+
+# Every symbol include/s3ttv.h declares, with (restype, argtypes).
+_c_int, _c_ll, _c_f, _c_d, _vp = ctypes.c_int, ctypes.c_longlong, ctypes.c_float, ctypes.c_double, ctypes.c_void_p
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("converged", ctypes.c_int),
+                ("jacobi_nonconverged", ctypes.c_int), ("rel_change", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.POINTER
+SIGNATURES = {
+    "s3ttv_create": (_c_int, [_P(_vp), _c_int, _vp]),
+    "s3ttv_destroy": (None, [_vp]),
+    "s3ttv_strerror": (ctypes.c_char_p, [_c_int]),
+    "s3ttv_last_error": (ctypes.c_char_p, [_vp]),
+    "s3ttv_set_option": (_c_int, [_vp, _c_int, _c_d]),
+    "s3ttv_workspace_bytes": (_c_ll, [_vp]),
+    "s3ttv_launch_count": (_c_ll, [_vp]),
+    "s3ttv_kernel_stats": (_c_int, [_vp, _P(_c_d), _P(_c_ll)]),
+    "s3ttv_solve": (_c_int, [_vp, _vp, _c_int, _c_int, _c_int, _c_f, _c_f, _c_f, _c_f, _c_f, _c_int, _c_int,
+                             _c_f, _vp, _vp, _vp, _P(Info)]),
+    "s3ttv_setup": (_c_int, [_vp, _vp, _c_int, _c_int, _c_int, _c_f, _c_f, _c_f, _c_f, _c_f, _c_int]),
+    "s3ttv_iterate": (_c_int, [_vp, _c_int, _c_f, _P(Info)]),
+    "s3ttv_get_state": (_c_int, [_vp, _c_int, _vp]),
+    "s3ttv_set_state": (_c_int, [_vp, _c_int, _vp]),
+    "s3ttv_l1_ball": (_c_int, [_vp, _vp, _vp, _c_ll, _c_d, _P(_c_d)]),
+    "s3ttv_block_dual": (_c_int, [_vp, _vp, _vp, _vp, _vp, _c_int, _c_int, _c_int, _c_int, _c_f, _P(Info)]),
+    "s3ttv_radii": (_c_int, [_c_ll, _c_d, _c_d, _c_d, _c_d, _P(_c_d), _P(_c_d), _P(_c_d)]),
+    "s3ttv_step_sizes": (_c_int, [_c_int, _c_int, _c_int, _c_int, _P(_c_d)]),
+}
+
+
+class S3TTVError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"s3ttv status {status}: {msg}")
+        self.status = status
+
+
+_LIB = None
+
+
+def library():
+    """Load libs3ttv.so (once) and declare its signatures."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise S3TTVError(ECUDA, f"{LIB_PATH} is not built; run paper_2404_03313_gb300.build.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, n=None, name="array"):
+    """Device or host address of a float32 C-contiguous array (torch or numpy)."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        import torch
+        if x.dtype != torch.float32 or not x.is_contiguous():
+            raise S3TTVError(EINVAL, f"{name} must be a contiguous float32 tensor")
+        if n is not None and x.numel() != n:
+            raise S3TTVError(EINVAL, f"{name} has {x.numel()} elements, expected {n}")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float32 or not x.flags["C_CONTIGUOUS"]:
+            raise S3TTVError(EINVAL, f"{name} must be a C-contiguous float32 array")
+        if n is not None and x.size != n:
+            raise S3TTVError(EINVAL, f"{name} has {x.size} elements, expected {n}")
+        return x.ctypes.data
+    raise S3TTVError(EINVAL, f"{name}: unsupported array type {type(x)}")
+
+
+def _empty_like(x, shape):
+    if _is_torch(x):
+        import torch
+        return torch.empty(shape, dtype=torch.float32, device=x.device)
+    return np.empty(shape, dtype=np.float32)
+
+
+def _sync_torch(*arrays):
+    """Make torch's pending work on CUDA inputs visible to the library's stream."""
+    for x in arrays:
+        if x is not None and _is_torch(x) and x.is_cuda:
+            import torch
+            torch.cuda.current_stream(x.device).synchronize()
+            return
+
+
+def radii(N, sigma, p_s, p_t, rho=0.95):
+    """eq. (RadiusSet) as implemented by the library: returns (eps, alpha, beta)."""
+    e, a, b = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    rc = library().s3ttv_radii(int(N), float(sigma), float(p_s), float(p_t), float(rho),
+                               ctypes.byref(e), ctypes.byref(a), ctypes.byref(b))
+    if rc:
+        raise S3TTVError(rc, "s3ttv_radii")
+    return e.value, a.value, b.value
+
+
+def step_sizes(N1, N2, k, policy=STEP_PAPER):
+    g = (ctypes.c_double * 6)()
+    rc = library().s3ttv_step_sizes(N1, N2, k, policy, g)
+    if rc:
+        raise S3TTVError(rc, "s3ttv_step_sizes")
+    return dict(zip(("u", "s", "t", "Y", "y2", "y3"), list(g)))
+
+
+class Solver:
+    """One s3ttv_ctx: a device, a stream, and the workspace of one problem."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._lib = library()
+        h = ctypes.c_void_p()
+        st = None
+        if stream is not None:
+            st = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        rc = self._lib.s3ttv_create(ctypes.byref(h), int(device), st)
+        if rc:
+            raise S3TTVError(rc, f"s3ttv_create(device={device}) failed")
+        self._h = h
+        self.device = device
+        self.shape = None
+        self.k = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.s3ttv_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc, what):
+        if rc < 0:
+            msg = self._lib.s3ttv_last_error(self._h).decode(errors="replace")
+            raise S3TTVError(rc, f"{what}: {msg}")
+        return rc
+
+    def set_option(self, key, value):
+        self._check(self._lib.s3ttv_set_option(self._h, key, float(value)), "set_option")
+
+    def workspace_bytes(self):
+        return int(self._lib.s3ttv_workspace_bytes(self._h))
+
+    def launch_count(self):
+        return int(self._lib.s3ttv_launch_count(self._h))
+
+    def kernel_stats(self):
+        """{class: (total ms, launches)} since profiling was switched on."""
+        ms = (ctypes.c_double * len(KERNEL_CLASSES))()
+        n = (ctypes.c_longlong * len(KERNEL_CLASSES))()
+        self._check(self._lib.s3ttv_kernel_stats(self._h, ms, n), "kernel_stats")
+        return {name: (ms[i], n[i]) for i, name in enumerate(KERNEL_CLASSES)}
+
+    def solve(self, v, eps, alpha, beta, k, mu_min=0.0, mu_max=1.0, max_iter=5000, tol=1e-5,
+              out=None):
+        """Run Alg. 1 on v (N1, N2, N3); returns (u, s, t, info dict)."""
+        N1, N2, N3 = v.shape
+        n = N1 * N2 * N3
+        u, s, t = out if out is not None else (_empty_like(v, v.shape) for _ in range(3))
+        info = Info()
+        _sync_torch(v)
+        rc = self._lib.s3ttv_solve(self._h, _ptr(v, n, "v"), N1, N2, N3, eps, alpha, beta, mu_min, mu_max, k,
+                                   max_iter, tol, _ptr(u, n, "u"), _ptr(s, n, "s"), _ptr(t, n, "t"),
+                                   ctypes.byref(info))
+        self._check(rc, "s3ttv_solve")
+        self.shape, self.k = (N1, N2, N3), k
+        return u, s, t, info.as_dict()
+
+    def setup(self, v, eps, alpha, beta, k, mu_min=0.0, mu_max=1.0):
+        N1, N2, N3 = v.shape
+        _sync_torch(v)
+        rc = self._lib.s3ttv_setup(self._h, _ptr(v, N1 * N2 * N3, "v"), N1, N2, N3, eps, alpha, beta,
+                                   mu_min, mu_max, k)
+        self._check(rc, "s3ttv_setup")
+        self.shape, self.k = (N1, N2, N3), k
+
+    def iterate(self, n, tol=0.0):
+        info = Info()
+        rc = self._lib.s3ttv_iterate(self._h, int(n), float(tol), ctypes.byref(info))
+        self._check(rc, "s3ttv_iterate")
+        return info.as_dict()
+
+    def _state_size(self, which):
+        N1, N2, N3 = self.shape
+        if which == "Y":
+            return (N1 * N2, self.k * self.k, 2 * N3)
+        return (N1, N2, N3)
+
+    def get_state(self, which, like=None):
+        shp = self._state_size(which)
+        dst = _empty_like(like, shp) if like is not None else np.empty(shp, np.float32)
+        self._check(self._lib.s3ttv_get_state(self._h, STATE[which], _ptr(dst, int(np.prod(shp)), which)),
+                    "get_state")
+        return dst
+
+    def set_state(self, which, src):
+        shp = self._state_size(which)
+        _sync_torch(src)
+        self._check(self._lib.s3ttv_set_state(self._h, STATE[which], _ptr(src, int(np.prod(shp)), which)),
+                    "set_state")
+
+    def l1_ball(self, x, radius, out=None):
+        """Projection onto the l1 ball of the given radius; returns (out, tau)."""
+        n = int(np.prod(x.shape))
+        out = _empty_like(x, x.shape) if out is None else out
+        tau = ctypes.c_double()
+        _sync_torch(x)
+        self._check(self._lib.s3ttv_l1_ball(self._h, _ptr(x, n, "x"), _ptr(out, n, "out"), n, float(radius),
+                                            ctypes.byref(tau)), "s3ttv_l1_ball")
+        return out, tau.value
+
+    def block_dual(self, Y, ubar, k, gamma_Y=0.25):
+        """Alg. 1 steps 8-11 on every block; Y (L, k*k, 2*N3) is updated in place.
+        Returns (Zv, Zh, info)."""
+        N1, N2, N3 = ubar.shape
+        n = N1 * N2 * N3
+        Zv, Zh = _empty_like(ubar, ubar.shape), _empty_like(ubar, ubar.shape)
+        info = Info()
+        _sync_torch(Y, ubar)
+        rc = self._lib.s3ttv_block_dual(self._h, _ptr(Y, N1 * N2 * k * k * 2 * N3, "Y"), _ptr(ubar, n, "ubar"),
+                                        _ptr(Zv, n, "Zv"), _ptr(Zh, n, "Zh"), N1, N2, N3, k, gamma_Y,
+                                        ctypes.byref(info))
+        self._check(rc, "s3ttv_block_dual")
+        return Zv, Zh, info.as_dict()

@@ -1,0 +1,852 @@
+// Host side of libs3ttv: argument checks, device workspace, the per-pass launch
+// sequence of Alg. 1 and the C ABI declared in include/s3ttv.h.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "s3ttv.h"
+#include "s3ttv_internal.cuh"
+
+using namespace s3ttv;
+
+struct s3ttv_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 0;
+  char err[512] = {0};
+  // options
+  int step_policy = S3TTV_STEP_PAPER;
+  int check_every = 16;
+  int jacobi_max_sweeps = 24;
+  float jacobi_tol = 2e-6f;
+  // problem
+  bool ready = false;
+  Dims dm{};
+  int k = 0;
+  float eps = 0.f, alpha = 0.f, beta = 0.f, mu_min = 0.f, mu_max = 1.f;
+  double gam[6] = {0, 0, 0, 0, 0, 0};
+  int parity = 0;  // which of t[2], Zv[2], Zh[2] holds the current value
+  // device workspace
+  size_t cap_np = 0, cap_y = 0, cap_stage = 0;
+  float *v = nullptr, *u = nullptr, *s = nullptr, *t[2] = {nullptr, nullptr}, *y2 = nullptr, *d = nullptr;
+  float *ubar = nullptr, *zs = nullptr, *zt = nullptr, *Zv[2] = {nullptr, nullptr}, *Zh[2] = {nullptr, nullptr};
+  float *Y = nullptr, *stage = nullptr;
+  Scalars *sc = nullptr;
+  double *part = nullptr;  // [3][kMaxGrid]
+  unsigned *hcnt = nullptr;
+  double *hsum = nullptr;
+  size_t bytes = 0;
+  // launch accounting and optional per-class event timing
+  long long launches = 0;
+  bool profile = false;
+  cudaEvent_t *ev = nullptr;  // [6 * ev_passes]
+  int ev_passes = 0;
+  double prof_ms[S3TTV_KERNEL_CLASSES] = {0, 0, 0, 0, 0};
+  long long prof_n[S3TTV_KERNEL_CLASSES] = {0, 0, 0, 0, 0};
+};
+
+namespace {
+
+constexpr int kMaxGrid = 4096;
+constexpr int kMaxK = 5;
+
+int fail(s3ttv_ctx *c, int status, const char *fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return status;
+}
+
+#define CU(call)                                                                            \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(ctx, S3TTV_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));         \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int round4(int x) { return (x + 3) & ~3; }
+
+int elementwise_grid(const s3ttv_ctx *c, long long n) {
+  long long g = (n + 255) / 256;
+  long long cap = (long long)c->num_sms * 8;
+  if (cap > kMaxGrid) cap = kMaxGrid;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+void free_all(s3ttv_ctx *c) {
+  float **bufs[] = {&c->v, &c->u, &c->s, &c->t[0], &c->t[1], &c->y2, &c->d, &c->ubar, &c->zs,
+                    &c->zt, &c->Zv[0], &c->Zv[1], &c->Zh[0], &c->Zh[1], &c->Y, &c->stage};
+  for (float **b : bufs) {
+    if (*b) cudaFree(*b);
+    *b = nullptr;
+  }
+  if (c->sc) cudaFree(c->sc);
+  if (c->part) cudaFree(c->part);
+  if (c->hcnt) cudaFree(c->hcnt);
+  if (c->hsum) cudaFree(c->hsum);
+  c->sc = nullptr;
+  c->part = nullptr;
+  c->hcnt = nullptr;
+  c->hsum = nullptr;
+  c->cap_np = c->cap_y = c->cap_stage = 0;
+  c->bytes = 0;
+  c->ready = false;
+}
+
+int dmalloc(s3ttv_ctx *ctx, void **p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(ctx, S3TTV_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  ctx->bytes += bytes;
+  return S3TTV_OK;
+}
+
+// Small buffers every entry point needs.
+int ensure_common(s3ttv_ctx *ctx) {
+  if (ctx->sc) return S3TTV_OK;
+  int rc;
+  if ((rc = dmalloc(ctx, (void **)&ctx->sc, sizeof(Scalars)))) return rc;
+  if ((rc = dmalloc(ctx, (void **)&ctx->part, sizeof(double) * 3 * kMaxGrid))) return rc;
+  if ((rc = dmalloc(ctx, (void **)&ctx->hcnt, sizeof(unsigned) * 2 * kHistBins))) return rc;
+  if ((rc = dmalloc(ctx, (void **)&ctx->hsum, sizeof(double) * 2 * kHistBins))) return rc;
+  CU(cudaMemsetAsync(ctx->hcnt, 0, sizeof(unsigned) * 2 * kHistBins, ctx->stream));
+  CU(cudaMemsetAsync(ctx->hsum, 0, sizeof(double) * 2 * kHistBins, ctx->stream));
+  return S3TTV_OK;
+}
+
+int ensure_stage(s3ttv_ctx *ctx, size_t elems) {
+  if (elems <= ctx->cap_stage) return S3TTV_OK;
+  if (ctx->stage) {
+    cudaFree(ctx->stage);
+    ctx->bytes -= ctx->cap_stage * sizeof(float);
+    ctx->stage = nullptr;
+    ctx->cap_stage = 0;
+  }
+  int rc = dmalloc(ctx, (void **)&ctx->stage, elems * sizeof(float));
+  if (rc) return rc;
+  ctx->cap_stage = elems;
+  return S3TTV_OK;
+}
+
+// Problem-sized buffers; reuses them when they are large enough.
+int ensure_problem_buffers(s3ttv_ctx *ctx, const Dims &dm, int k) {
+  const size_t np = (size_t)dm.Np;
+  const size_t ny = (size_t)dm.P * k * k * 2 * dm.N3p;
+  if (np <= ctx->cap_np && ny <= ctx->cap_y && ctx->sc) return S3TTV_OK;
+  free_all(ctx);
+  int rc = ensure_common(ctx);
+  if (rc) return rc;
+  float **cubes[] = {&ctx->v, &ctx->u, &ctx->s, &ctx->t[0], &ctx->t[1], &ctx->y2, &ctx->d, &ctx->ubar,
+                     &ctx->zs, &ctx->zt, &ctx->Zv[0], &ctx->Zv[1], &ctx->Zh[0], &ctx->Zh[1]};
+  for (float **b : cubes) {
+    if ((rc = dmalloc(ctx, (void **)b, np * sizeof(float)))) {
+      free_all(ctx);
+      return rc;
+    }
+  }
+  if ((rc = dmalloc(ctx, (void **)&ctx->Y, ny * sizeof(float)))) {
+    free_all(ctx);
+    return rc;
+  }
+  ctx->cap_np = np;
+  ctx->cap_y = ny;
+  return S3TTV_OK;
+}
+
+Dims make_dims(int N1, int N2, int N3) {
+  Dims dm;
+  dm.N1 = N1;
+  dm.N2 = N2;
+  dm.N3 = N3;
+  dm.N3p = round4(N3);
+  dm.P = (long long)N1 * N2;
+  dm.Np = dm.P * dm.N3p;
+  return dm;
+}
+
+// Block-dual launch shape: warps per CTA limited by shared memory.
+int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, int *warps, int *rs, size_t *smem, int *grid) {
+  *rs = block_dual_row_stride(dm.N3p);
+  const size_t per = block_dual_smem_per_warp(k, *rs);
+  int dev_max = 0;
+  cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+  if (dev_max <= 0) dev_max = 227 * 1024;
+  int w = (int)((size_t)dev_max / per);
+  if (w > 8) w = 8;
+  if (w < 1)
+    return fail(ctx, S3TTV_EUNSUPPORTED,
+                "a %dx%dx%d block needs %zu bytes of shared memory per warp (device limit %d)", k, k, dm.N3,
+                per, dev_max);
+  *warps = w;
+  *smem = per * w;
+  long long g = (dm.P + w - 1) / w;
+  if (g > 1 << 30) g = 1 << 30;
+  *grid = (int)g;
+  cudaError_t e = block_dual_prepare(k, *smem);
+  if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+  return S3TTV_OK;
+}
+
+int check_problem(s3ttv_ctx *ctx, const float *v, int N1, int N2, int N3, float eps, float alpha, float beta,
+                  float mu_min, float mu_max, int k) {
+  if (!ctx) return S3TTV_EINVAL;
+  if (!v) return fail(ctx, S3TTV_EINVAL, "v is NULL");
+  if (k < 1) return fail(ctx, S3TTV_EINVAL, "k = %d must be >= 1", k);
+  if (N1 < k || N2 < k) return fail(ctx, S3TTV_EINVAL, "N1 = %d and N2 = %d must be >= k = %d", N1, N2, k);
+  if (N3 < 2) return fail(ctx, S3TTV_EINVAL, "N3 = %d must be >= 2", N3);
+  if (!(std::isfinite(eps) && eps >= 0.f)) return fail(ctx, S3TTV_EINVAL, "eps must be finite and >= 0");
+  if (!(std::isfinite(alpha) && alpha >= 0.f)) return fail(ctx, S3TTV_EINVAL, "alpha must be finite and >= 0");
+  if (!(std::isfinite(beta) && beta >= 0.f)) return fail(ctx, S3TTV_EINVAL, "beta must be finite and >= 0");
+  if (!(std::isfinite(mu_min) && std::isfinite(mu_max) && mu_min < mu_max))
+    return fail(ctx, S3TTV_EINVAL, "need finite mu_min < mu_max");
+  if ((long long)N1 * N2 * (long long)N3 > (1ll << 40)) return fail(ctx, S3TTV_EINVAL, "cube too large");
+  if (k > kMaxK) return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: this build supports k <= %d", k, kMaxK);
+  return S3TTV_OK;
+}
+
+void step_sizes(int N1, int N2, int k, int policy, double g[6]) {
+  const double L = (double)N1 * (double)N2;
+  g[0] = policy == S3TTV_STEP_PC_EXACT ? 1.0 / (8.0 * k * k + 1.0) : 1.0 / (8.0 * L + 1.0);
+  g[1] = 1.0;
+  g[2] = 1.0 / 3.0;
+  g[3] = 0.25;
+  g[4] = 0.5;
+  g[5] = 1.0 / 3.0;
+}
+
+// Copy a caller cube (host or device, [N1][N2][N3]) into an internal padded cube.
+int load_cube(s3ttv_ctx *ctx, const float *src, float *dst, float scale) {
+  const Dims &dm = ctx->dm;
+  const float *from = src;
+  if (!is_device_ptr(src)) {
+    int rc = ensure_stage(ctx, (size_t)dm.P * dm.N3);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(ctx->stage, src, sizeof(float) * dm.P * dm.N3, cudaMemcpyHostToDevice, ctx->stream));
+    from = ctx->stage;
+  }
+  CU(launch_pad_cube(from, dst, dm, scale, ctx->stream));
+  return S3TTV_OK;
+}
+
+int store_cube(s3ttv_ctx *ctx, const float *src, float *dst, const double *scale_dev) {
+  const Dims &dm = ctx->dm;
+  if (is_device_ptr(dst)) {
+    CU(launch_unpad_cube(src, dst, dm, scale_dev, ctx->stream));
+    return S3TTV_OK;
+  }
+  int rc = ensure_stage(ctx, (size_t)dm.P * dm.N3);
+  if (rc) return rc;
+  CU(launch_unpad_cube(src, ctx->stage, dm, scale_dev, ctx->stream));
+  CU(cudaMemcpyAsync(dst, ctx->stage, sizeof(float) * dm.P * dm.N3, cudaMemcpyDeviceToHost, ctx->stream));
+  return S3TTV_OK;
+}
+
+int load_Y(s3ttv_ctx *ctx, const float *src) {
+  const Dims &dm = ctx->dm;
+  const size_t ne = (size_t)dm.P * ctx->k * ctx->k * 2 * dm.N3;
+  const float *from = src;
+  if (!is_device_ptr(src)) {
+    int rc = ensure_stage(ctx, ne);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(ctx->stage, src, sizeof(float) * ne, cudaMemcpyHostToDevice, ctx->stream));
+    from = ctx->stage;
+  }
+  CU(launch_Y_to_internal(from, ctx->Y, dm, ctx->k, ctx->stream));
+  return S3TTV_OK;
+}
+
+int store_Y(s3ttv_ctx *ctx, float *dst) {
+  const Dims &dm = ctx->dm;
+  const size_t ne = (size_t)dm.P * ctx->k * ctx->k * 2 * dm.N3;
+  if (is_device_ptr(dst)) {
+    CU(launch_Y_to_external(ctx->Y, dst, dm, ctx->k, ctx->stream));
+    return S3TTV_OK;
+  }
+  int rc = ensure_stage(ctx, ne);
+  if (rc) return rc;
+  CU(launch_Y_to_external(ctx->Y, ctx->stage, dm, ctx->k, ctx->stream));
+  CU(cudaMemcpyAsync(dst, ctx->stage, sizeof(float) * ne, cudaMemcpyDeviceToHost, ctx->stream));
+  return S3TTV_OK;
+}
+
+__global__ void begin_iterate_kernel(Scalars *sc, int n, float tol) {
+  sc->iter_limit = sc->iter + n;
+  sc->done = 0;
+  sc->status = 0;
+  sc->tol = tol;
+  sc->jacobi_fail = 0u;
+}
+
+__global__ void set_c3_kernel(Scalars *sc, double c3) { sc->c3 = c3; }
+
+// One pass of Alg. 1, enqueued on the context stream.  `par` selects the current
+// t / Z buffers; the pass writes the other ones.
+int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, int grid_bd, int warps, int rs, size_t smem,
+                 cudaEvent_t *ev) {
+  const Dims &dm = ctx->dm;
+  cudaStream_t st = ctx->stream;
+  if (ev) CU(cudaEventRecord(ev[0], st));
+  PrimalArgs pa;
+  pa.Zv = ctx->Zv[par];
+  pa.Zh = ctx->Zh[par];
+  pa.Znv = ctx->Zv[par ^ 1];
+  pa.Znh = ctx->Zh[par ^ 1];
+  pa.u = ctx->u;
+  pa.ubar = ctx->ubar;
+  pa.s = ctx->s;
+  pa.t = ctx->t[par];
+  pa.y2 = ctx->y2;
+  pa.d = ctx->d;
+  pa.zs = ctx->zs;
+  pa.zt = ctx->zt;
+  pa.dm = dm;
+  pa.gu = (float)ctx->gam[0];
+  pa.gs = (float)ctx->gam[1];
+  pa.gt = (float)ctx->gam[2];
+  pa.lo = ctx->mu_min;
+  pa.hi = ctx->mu_max;
+  pa.sc = ctx->sc;
+  pa.part = ctx->part;
+  pa.hcnt = ctx->hcnt;
+  pa.hsum = ctx->hsum;
+  CU(launch_primal(pa, grid_e, st));
+  if (ev) CU(cudaEventRecord(ev[1], st));
+
+  L1Args la;
+  la.x[0] = ctx->zs;
+  la.x[1] = ctx->zt;
+  la.n = dm.Np;
+  la.nprob = 2;
+  la.sc = ctx->sc;
+  la.hcnt = ctx->hcnt;
+  la.hsum = ctx->hsum;
+  CU(launch_l1_scan(la, 1, st));
+  CU(launch_l1_hist(la, 2, grid_e, st));
+  CU(launch_l1_scan(la, 2, st));
+  CU(launch_l1_hist(la, 3, grid_e, st));
+  CU(launch_l1_scan(la, 3, st));
+  if (ev) CU(cudaEventRecord(ev[2], st));
+
+  BlockDualArgs ba;
+  ba.Y = ctx->Y;
+  ba.ubar = ctx->ubar;
+  ba.Zv = ctx->Zv[par ^ 1];
+  ba.Zh = ctx->Zh[par ^ 1];
+  ba.dm = dm;
+  ba.gY = (float)ctx->gam[3];
+  ba.rs = rs;
+  ba.warps = warps;
+  ba.max_sweeps = ctx->jacobi_max_sweeps;
+  ba.tol = ctx->jacobi_tol;
+  ba.sc = ctx->sc;
+  CU(launch_block_dual(ba, ctx->k, grid_bd, smem, st));
+  if (ev) CU(cudaEventRecord(ev[3], st));
+
+  DualArgs da;
+  da.zs = ctx->zs;
+  da.zt = ctx->zt;
+  da.s_old = ctx->s;
+  da.t_old = ctx->t[par];
+  da.ubar = ctx->ubar;
+  da.v = ctx->v;
+  da.s_new = ctx->s;
+  da.t_new = ctx->t[par ^ 1];
+  da.y2 = ctx->y2;
+  da.d = ctx->d;
+  da.dm = dm;
+  da.g2 = (float)ctx->gam[4];
+  da.g3 = (float)ctx->gam[5];
+  da.sc = ctx->sc;
+  da.part = ctx->part + 2 * grid_e;
+  CU(launch_dual(da, grid_e, st));
+  if (ev) CU(cudaEventRecord(ev[4], st));
+
+  FinalizeArgs fa;
+  fa.sc = ctx->sc;
+  fa.part_primal = ctx->part;
+  fa.grid_p = grid_e;
+  fa.part_dual = ctx->part + 2 * grid_e;
+  fa.grid_d = grid_e;
+  fa.eps = ctx->eps;
+  fa.g3 = ctx->gam[5];
+  CU(launch_finalize(fa, st));
+  if (ev) CU(cudaEventRecord(ev[5], st));
+  ctx->launches += 9;
+  return S3TTV_OK;
+}
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+constexpr int kEvPerPass = S3TTV_KERNEL_CLASSES + 1;  // boundaries around the five classes
+
+void destroy_events(s3ttv_ctx *c) {
+  for (int i = 0; i < kEvPerPass * c->ev_passes; ++i) cudaEventDestroy(c->ev[i]);
+  delete[] c->ev;
+  c->ev = nullptr;
+  c->ev_passes = 0;
+}
+
+int ensure_events(s3ttv_ctx *ctx, int passes) {
+  if (passes <= ctx->ev_passes) return S3TTV_OK;
+  destroy_events(ctx);
+  ctx->ev = new (std::nothrow) cudaEvent_t[(size_t)kEvPerPass * passes];
+  if (!ctx->ev) return fail(ctx, S3TTV_ENOMEM, "event pool");
+  for (int i = 0; i < kEvPerPass * passes; ++i) {
+    cudaError_t e = cudaEventCreate(&ctx->ev[i]);
+    if (e != cudaSuccess) {
+      for (int j = 0; j < i; ++j) cudaEventDestroy(ctx->ev[j]);
+      delete[] ctx->ev;
+      ctx->ev = nullptr;
+      return fail(ctx, S3TTV_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
+    }
+  }
+  ctx->ev_passes = passes;
+  return S3TTV_OK;
+}
+
+// Add the elapsed times of `passes` recorded passes to the per-class totals.
+int collect_events(s3ttv_ctx *ctx, int passes) {
+  for (int p = 0; p < passes; ++p) {
+    cudaEvent_t *e = ctx->ev + (size_t)kEvPerPass * p;
+    for (int c = 0; c < S3TTV_KERNEL_CLASSES; ++c) {
+      float ms = 0.f;
+      CU(cudaEventElapsedTime(&ms, e[c], e[c + 1]));
+      ctx->prof_ms[c] += ms;
+      ctx->prof_n[c] += c == S3TTV_KERNEL_L1_SEARCH ? 5 : 1;
+    }
+  }
+  return S3TTV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *s3ttv_strerror(int status) {
+  switch (status) {
+    case S3TTV_OK: return "ok (stop rule fired)";
+    case S3TTV_MAXITER: return "iteration cap reached";
+    case S3TTV_EINVAL: return "invalid argument";
+    case S3TTV_ENOMEM: return "device allocation failed";
+    case S3TTV_ECUDA: return "CUDA runtime error";
+    case S3TTV_ENUMERIC: return "NaN or Inf in the iterates";
+    case S3TTV_EUNSUPPORTED: return "not supported by this build";
+    case S3TTV_ESTATE: return "no problem set up";
+    default: return "unknown status";
+  }
+}
+
+const char *s3ttv_last_error(const s3ttv_ctx *ctx) { return ctx ? ctx->err : "null context"; }
+
+long long s3ttv_workspace_bytes(const s3ttv_ctx *ctx) { return ctx ? (long long)ctx->bytes : 0; }
+
+long long s3ttv_launch_count(const s3ttv_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+int s3ttv_kernel_stats(const s3ttv_ctx *ctx, double *ms, long long *launches) {
+  if (!ctx) return S3TTV_EINVAL;
+  for (int c = 0; c < S3TTV_KERNEL_CLASSES; ++c) {
+    if (ms) ms[c] = ctx->prof_ms[c];
+    if (launches) launches[c] = ctx->prof_n[c];
+  }
+  return S3TTV_OK;
+}
+
+int s3ttv_create(s3ttv_ctx **out, int device, void *stream) {
+  if (!out) return S3TTV_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return S3TTV_ECUDA;
+  }
+  if (device < 0 || device >= ndev) return S3TTV_EINVAL;
+  s3ttv_ctx *ctx = new (std::nothrow) s3ttv_ctx();
+  if (!ctx) return S3TTV_ENOMEM;
+  ctx->device = device;
+  DeviceGuard g(device);
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (ctx->num_sms <= 0) ctx->num_sms = 1;
+  if (stream) {
+    ctx->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete ctx;
+      return S3TTV_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  *out = ctx;
+  return S3TTV_OK;
+}
+
+void s3ttv_destroy(s3ttv_ctx *ctx) {
+  if (!ctx) return;
+  {
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    free_all(ctx);
+    destroy_events(ctx);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  }
+  delete ctx;
+}
+
+int s3ttv_set_option(s3ttv_ctx *ctx, int key, double value) {
+  if (!ctx) return S3TTV_EINVAL;
+  switch (key) {
+    case S3TTV_OPT_STEP_POLICY:
+      if (value != S3TTV_STEP_PAPER && value != S3TTV_STEP_PC_EXACT)
+        return fail(ctx, S3TTV_EINVAL, "unknown step policy %g", value);
+      ctx->step_policy = (int)value;
+      if (ctx->ready) step_sizes(ctx->dm.N1, ctx->dm.N2, ctx->k, ctx->step_policy, ctx->gam);
+      return S3TTV_OK;
+    case S3TTV_OPT_CHECK_EVERY:
+      if (!(value >= 1 && value <= 1e6)) return fail(ctx, S3TTV_EINVAL, "check_every must be in [1, 1e6]");
+      ctx->check_every = (int)value;
+      return S3TTV_OK;
+    case S3TTV_OPT_JACOBI_MAX_SWEEPS:
+      if (!(value >= 1 && value <= 64)) return fail(ctx, S3TTV_EINVAL, "jacobi sweeps must be in [1, 64]");
+      ctx->jacobi_max_sweeps = (int)value;
+      return S3TTV_OK;
+    case S3TTV_OPT_JACOBI_TOL:
+      if (!(value > 0 && value < 1)) return fail(ctx, S3TTV_EINVAL, "jacobi tol must be in (0, 1)");
+      ctx->jacobi_tol = (float)value;
+      return S3TTV_OK;
+    case S3TTV_OPT_PROFILE:
+      if (value != 0 && value != 1) return fail(ctx, S3TTV_EINVAL, "profile must be 0 or 1");
+      ctx->profile = value == 1;
+      for (int c = 0; c < S3TTV_KERNEL_CLASSES; ++c) {
+        ctx->prof_ms[c] = 0.0;
+        ctx->prof_n[c] = 0;
+      }
+      return S3TTV_OK;
+    default:
+      return fail(ctx, S3TTV_EINVAL, "unknown option key %d", key);
+  }
+}
+
+int s3ttv_radii(long long N, double sigma, double p_s, double p_t, double rho, double *eps, double *alpha,
+                double *beta) {
+  if (!eps || !alpha || !beta || N < 1 || !(sigma >= 0) || !(p_s >= 0 && p_s <= 1) || !(p_t >= 0 && p_t <= 1) ||
+      !(rho > 0))
+    return S3TTV_EINVAL;
+  *alpha = rho * (double)N * p_s / 2.0;
+  *beta = rho * 0.5 * (double)N * p_t * (1.0 - p_s) / 2.0;
+  *eps = sigma > 0 ? rho * std::sqrt(sigma * sigma * (double)N * (1.0 - p_s)) : 0.01;
+  return S3TTV_OK;
+}
+
+int s3ttv_step_sizes(int N1, int N2, int k, int policy, double gammas[6]) {
+  if (!gammas || N1 < 1 || N2 < 1 || k < 1) return S3TTV_EINVAL;
+  if (policy != S3TTV_STEP_PAPER && policy != S3TTV_STEP_PC_EXACT) return S3TTV_EINVAL;
+  step_sizes(N1, N2, k, policy, gammas);
+  return S3TTV_OK;
+}
+
+int s3ttv_setup(s3ttv_ctx *ctx, const float *v, int N1, int N2, int N3, float eps, float alpha, float beta,
+                float mu_min, float mu_max, int k) {
+  int rc = check_problem(ctx, v, N1, N2, N3, eps, alpha, beta, mu_min, mu_max, k);
+  if (rc) return rc;
+  DeviceGuard g(ctx->device);
+  ctx->ready = false;
+  const Dims dm = make_dims(N1, N2, N3);
+  int warps, rs, grid;
+  size_t smem;
+  if ((rc = block_dual_shape(ctx, dm, k, &warps, &rs, &smem, &grid))) return rc;
+  if ((rc = ensure_problem_buffers(ctx, dm, k))) return rc;
+  ctx->dm = dm;
+  ctx->k = k;
+  ctx->eps = eps;
+  ctx->alpha = alpha;
+  ctx->beta = beta;
+  ctx->mu_min = mu_min;
+  ctx->mu_max = mu_max;
+  step_sizes(N1, N2, k, ctx->step_policy, ctx->gam);
+  const size_t cb = sizeof(float) * dm.Np;
+  if ((rc = load_cube(ctx, v, ctx->v, 1.f))) return rc;
+  CU(cudaMemcpyAsync(ctx->u, ctx->v, cb, cudaMemcpyDeviceToDevice, ctx->stream));  // u0 = v
+  float *zero[] = {ctx->s, ctx->t[0], ctx->t[1], ctx->y2, ctx->d, ctx->ubar, ctx->zs, ctx->zt,
+                   ctx->Zv[0], ctx->Zv[1], ctx->Zh[0], ctx->Zh[1]};
+  for (float *z : zero) CU(cudaMemsetAsync(z, 0, cb, ctx->stream));
+  CU(cudaMemsetAsync(ctx->Y, 0, sizeof(float) * dm.P * k * k * 2 * dm.N3p, ctx->stream));
+  CU(cudaMemsetAsync(ctx->hcnt, 0, sizeof(unsigned) * 2 * kHistBins, ctx->stream));
+  CU(cudaMemsetAsync(ctx->hsum, 0, sizeof(double) * 2 * kHistBins, ctx->stream));
+  CU(launch_init_scalars(ctx->sc, alpha, beta, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  ctx->parity = 0;
+  ctx->ready = true;
+  return S3TTV_OK;
+}
+
+int s3ttv_iterate(s3ttv_ctx *ctx, int n, float tol, s3ttv_info *info) {
+  if (!ctx) return S3TTV_EINVAL;
+  const double t0 = now_s();
+  if (info) memset(info, 0, sizeof(*info));
+  if (!ctx->ready) return fail(ctx, S3TTV_ESTATE, "s3ttv_iterate before s3ttv_setup");
+  if (n < 1) return fail(ctx, S3TTV_EINVAL, "n = %d must be >= 1", n);
+  if (!(tol >= 0.f) || !std::isfinite(tol)) return fail(ctx, S3TTV_EINVAL, "tol must be finite and >= 0");
+  DeviceGuard g(ctx->device);
+  int warps, rs, grid_bd;
+  size_t smem;
+  int rc = block_dual_shape(ctx, ctx->dm, ctx->k, &warps, &rs, &smem, &grid_bd);
+  if (rc) return rc;
+  const int grid_e = elementwise_grid(ctx, ctx->dm.Np);
+  Scalars hs;
+  CU(cudaMemcpyAsync(&hs, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  const int iter0 = hs.iter;
+  const int par0 = ctx->parity;
+  begin_iterate_kernel<<<1, 1, 0, ctx->stream>>>(ctx->sc, n, tol);
+  CU(cudaGetLastError());
+  ctx->launches += 1;
+  int enq = 0, par = par0;
+  while (enq < n) {
+    const int chunk = n - enq < ctx->check_every ? n - enq : ctx->check_every;
+    if (ctx->profile && (rc = ensure_events(ctx, chunk))) return rc;
+    for (int c = 0; c < chunk; ++c) {
+      cudaEvent_t *ev = ctx->profile ? ctx->ev + (size_t)kEvPerPass * c : nullptr;
+      if ((rc = enqueue_pass(ctx, par, grid_e, grid_bd, warps, rs, smem, ev))) return rc;
+      par ^= 1;
+    }
+    enq += chunk;
+    CU(cudaMemcpyAsync(&hs, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (ctx->profile) {
+      // passes skipped after the stop flag are empty launches; count what ran
+      const int ran = hs.iter - iter0 - (enq - chunk);
+      if ((rc = collect_events(ctx, ran < chunk ? (ran > 0 ? ran : 0) : chunk))) return rc;
+    }
+    if (hs.done) break;
+  }
+  const int done_iters = hs.iter - iter0;
+  ctx->parity = (par0 + done_iters) & 1;
+  int status;
+  if (hs.status == -4) {
+    status = fail(ctx, S3TTV_ENUMERIC, "NaN or Inf after %d passes", done_iters);
+  } else {
+    status = hs.status == 1 ? S3TTV_OK : S3TTV_MAXITER;
+  }
+  if (info) {
+    info->status = status;
+    info->iters = done_iters;
+    info->converged = hs.status == 1;
+    info->jacobi_nonconverged = (int)hs.jacobi_fail;
+    info->rel_change = hs.rel;
+    info->seconds = now_s() - t0;
+  }
+  return status;
+}
+
+int s3ttv_get_state(s3ttv_ctx *ctx, int which, float *dst) {
+  if (!ctx) return S3TTV_EINVAL;
+  if (!ctx->ready) return fail(ctx, S3TTV_ESTATE, "no problem set up");
+  if (!dst) return fail(ctx, S3TTV_EINVAL, "dst is NULL");
+  DeviceGuard g(ctx->device);
+  int rc;
+  switch (which) {
+    case S3TTV_STATE_U: rc = store_cube(ctx, ctx->u, dst, nullptr); break;
+    case S3TTV_STATE_S: rc = store_cube(ctx, ctx->s, dst, nullptr); break;
+    case S3TTV_STATE_T: rc = store_cube(ctx, ctx->t[ctx->parity], dst, nullptr); break;
+    case S3TTV_STATE_Y2: rc = store_cube(ctx, ctx->y2, dst, nullptr); break;
+    case S3TTV_STATE_Y3: rc = store_cube(ctx, ctx->d, dst, &ctx->sc->c3); break;
+    case S3TTV_STATE_Y: rc = store_Y(ctx, dst); break;
+    default: return fail(ctx, S3TTV_EINVAL, "unknown state %d", which);
+  }
+  if (rc) return rc;
+  CU(cudaStreamSynchronize(ctx->stream));
+  return S3TTV_OK;
+}
+
+int s3ttv_set_state(s3ttv_ctx *ctx, int which, const float *src) {
+  if (!ctx) return S3TTV_EINVAL;
+  if (!ctx->ready) return fail(ctx, S3TTV_ESTATE, "no problem set up");
+  if (!src) return fail(ctx, S3TTV_EINVAL, "src is NULL");
+  DeviceGuard g(ctx->device);
+  int rc;
+  switch (which) {
+    case S3TTV_STATE_U: rc = load_cube(ctx, src, ctx->u, 1.f); break;
+    case S3TTV_STATE_S: rc = load_cube(ctx, src, ctx->s, 1.f); break;
+    case S3TTV_STATE_T: rc = load_cube(ctx, src, ctx->t[ctx->parity], 1.f); break;
+    case S3TTV_STATE_Y2: rc = load_cube(ctx, src, ctx->y2, 1.f); break;
+    case S3TTV_STATE_Y3:
+      rc = load_cube(ctx, src, ctx->d, 1.f);
+      if (!rc) {
+        set_c3_kernel<<<1, 1, 0, ctx->stream>>>(ctx->sc, 1.0);
+        CU(cudaGetLastError());
+      }
+      break;
+    case S3TTV_STATE_Y:
+      rc = load_Y(ctx, src);
+      if (!rc) CU(launch_Z_from_Y(ctx->Y, ctx->Zv[ctx->parity], ctx->Zh[ctx->parity], ctx->dm, ctx->k, ctx->stream));
+      break;
+    default: return fail(ctx, S3TTV_EINVAL, "unknown state %d", which);
+  }
+  if (rc) return rc;
+  CU(cudaStreamSynchronize(ctx->stream));
+  return S3TTV_OK;
+}
+
+int s3ttv_solve(s3ttv_ctx *ctx, const float *v, int N1, int N2, int N3, float eps, float alpha, float beta,
+                float mu_min, float mu_max, int k, int max_iter, float tol, float *u, float *s, float *t,
+                s3ttv_info *info) {
+  const double t0 = now_s();
+  if (info) memset(info, 0, sizeof(*info));
+  if (!ctx) return S3TTV_EINVAL;
+  if (!u) return fail(ctx, S3TTV_EINVAL, "u is NULL");
+  if (max_iter < 1) return fail(ctx, S3TTV_EINVAL, "max_iter = %d must be >= 1", max_iter);
+  if (!(tol >= 0.f) || !std::isfinite(tol)) return fail(ctx, S3TTV_EINVAL, "tol must be finite and >= 0");
+  int rc = s3ttv_setup(ctx, v, N1, N2, N3, eps, alpha, beta, mu_min, mu_max, k);
+  if (rc) {
+    if (info) info->status = rc;
+    return rc;
+  }
+  s3ttv_info it;
+  const int st = s3ttv_iterate(ctx, max_iter, tol, &it);
+  if (st < 0) {
+    if (info) {
+      *info = it;
+      info->status = st;
+    }
+    return st;
+  }
+  DeviceGuard g(ctx->device);
+  if ((rc = store_cube(ctx, ctx->u, u, nullptr))) return rc;
+  if (s && (rc = store_cube(ctx, ctx->s, s, nullptr))) return rc;
+  if (t && (rc = store_cube(ctx, ctx->t[ctx->parity], t, nullptr))) return rc;
+  CU(cudaStreamSynchronize(ctx->stream));
+  if (info) {
+    *info = it;
+    info->status = st;
+    info->seconds = now_s() - t0;
+  }
+  return st;
+}
+
+int s3ttv_l1_ball(s3ttv_ctx *ctx, const float *x, float *out, long long n, double radius, double *tau_out) {
+  if (!ctx) return S3TTV_EINVAL;
+  if (n < 0) return fail(ctx, S3TTV_EINVAL, "n < 0");
+  if (!(radius >= 0) || !std::isfinite(radius)) return fail(ctx, S3TTV_EINVAL, "radius must be finite and >= 0");
+  if (n > 0 && (!x || !out)) return fail(ctx, S3TTV_EINVAL, "x and out are required");
+  if (n == 0) {
+    if (tau_out) *tau_out = 0.0;
+    return S3TTV_OK;
+  }
+  DeviceGuard g(ctx->device);
+  int rc = ensure_common(ctx);
+  if (rc) return rc;
+  const bool xd = is_device_ptr(x), od = is_device_ptr(out);
+  // stage: [host copy of x][output]
+  const size_t need = (xd ? 0 : (size_t)n) + (od ? 0 : (size_t)n);
+  if (need && (rc = ensure_stage(ctx, need))) return rc;
+  const float *xin = x;
+  float *xout = out;
+  if (!xd) {
+    CU(cudaMemcpyAsync(ctx->stage, x, sizeof(float) * n, cudaMemcpyHostToDevice, ctx->stream));
+    xin = ctx->stage;
+  }
+  if (!od) xout = ctx->stage + (xd ? 0 : n);
+  CU(launch_init_scalars(ctx->sc, radius, 0.0, ctx->stream));
+  L1Args la;
+  la.x[0] = xin;
+  la.x[1] = xin;
+  la.n = n;
+  la.nprob = 1;
+  la.sc = ctx->sc;
+  la.hcnt = ctx->hcnt;
+  la.hsum = ctx->hsum;
+  const int grid = elementwise_grid(ctx, n);
+  for (int level = 1; level <= 3; ++level) {
+    CU(launch_l1_hist(la, level, grid, ctx->stream));
+    CU(launch_l1_scan(la, level, ctx->stream));
+  }
+  CU(launch_soft_threshold(xin, xout, n, ctx->sc, 0, ctx->stream));
+  if (!od) CU(cudaMemcpyAsync(out, xout, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  Scalars hs;
+  CU(cudaMemcpyAsync(&hs, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  if (tau_out) *tau_out = (double)hs.l1[0].tau;
+  ctx->ready = false;  // the scalars of any set-up problem were overwritten
+  return S3TTV_OK;
+}
+
+int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, float *Zh, int N1, int N2, int N3,
+                     int k, float gamma_Y, s3ttv_info *info) {
+  if (info) memset(info, 0, sizeof(*info));
+  if (!ctx) return S3TTV_EINVAL;
+  if (!Y || !ubar || !Zv || !Zh) return fail(ctx, S3TTV_EINVAL, "Y, ubar, Zv and Zh are required");
+  if (k < 1 || N1 < k || N2 < k || N3 < 1) return fail(ctx, S3TTV_EINVAL, "need N1, N2 >= k >= 1 and N3 >= 1");
+  if (!(gamma_Y > 0.f) || !std::isfinite(gamma_Y)) return fail(ctx, S3TTV_EINVAL, "gamma_Y must be > 0");
+  if (k > kMaxK) return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: this build supports k <= %d", k, kMaxK);
+  DeviceGuard g(ctx->device);
+  const Dims dm = make_dims(N1, N2, N3);
+  int warps, rs, grid, rc;
+  size_t smem;
+  if ((rc = block_dual_shape(ctx, dm, k, &warps, &rs, &smem, &grid))) return rc;
+  ctx->ready = false;
+  if ((rc = ensure_problem_buffers(ctx, dm, k))) return rc;
+  ctx->dm = dm;
+  ctx->k = k;
+  if ((rc = load_Y(ctx, Y))) return rc;
+  if ((rc = load_cube(ctx, ubar, ctx->ubar, 1.f))) return rc;
+  CU(cudaMemsetAsync(ctx->Zv[0], 0, sizeof(float) * dm.Np, ctx->stream));
+  CU(cudaMemsetAsync(ctx->Zh[0], 0, sizeof(float) * dm.Np, ctx->stream));
+  CU(launch_init_scalars(ctx->sc, 0.0, 0.0, ctx->stream));
+  BlockDualArgs ba;
+  ba.Y = ctx->Y;
+  ba.ubar = ctx->ubar;
+  ba.Zv = ctx->Zv[0];
+  ba.Zh = ctx->Zh[0];
+  ba.dm = dm;
+  ba.gY = gamma_Y;
+  ba.rs = rs;
+  ba.warps = warps;
+  ba.max_sweeps = ctx->jacobi_max_sweeps;
+  ba.tol = ctx->jacobi_tol;
+  ba.sc = ctx->sc;
+  CU(launch_block_dual(ba, k, grid, smem, ctx->stream));
+  if ((rc = store_Y(ctx, Y))) return rc;
+  if ((rc = store_cube(ctx, ctx->Zv[0], Zv, nullptr))) return rc;
+  if ((rc = store_cube(ctx, ctx->Zh[0], Zh, nullptr))) return rc;
+  Scalars hs;
+  CU(cudaMemcpyAsync(&hs, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  if (info) info->jacobi_nonconverged = (int)hs.jacobi_fail;
+  return S3TTV_OK;
+}
+
+}  // extern "C"

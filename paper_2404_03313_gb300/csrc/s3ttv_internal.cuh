@@ -1,0 +1,138 @@
+// Internal declarations shared by the CUDA translation units of libs3ttv.
+//
+// Internal layout.  Every cube lives as [N1][N2][N3p] with N3p = N3 rounded up to
+// a multiple of 4, so each pixel's spectrum starts on a 16-byte boundary and the
+// kernels can move float4s; the padding bands are kept at exactly zero.  The
+// block dual Y lives as [L][k*k][2][N3p]: per block row, the N3p vertical
+// differences (eq. SSST columns 2b) followed by the N3p horizontal ones (columns
+// 2b+1).  A column permutation of a block does not change its singular values,
+// so this is the same prox.  The fidelity dual is stored as y3 = c3 * d with a
+// device scalar c3 and a cube d (see dual_kernel).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace s3ttv {
+
+constexpr int kHistBins = 2048;  // bins of the widest radix level
+constexpr unsigned kFull = 0xffffffffu;
+
+struct Dims {
+  int N1, N2, N3, N3p;
+  long long P;   // pixels N1*N2 (= number of blocks L)
+  long long Np;  // P * N3p, elements of an internal cube
+};
+
+// One l1-ball projection being solved by radix selection over the bits of |z|.
+struct L1State {
+  double radius;
+  double S_above;               // sum of |z| over bins above the current prefix
+  unsigned long long C_above;   // count of those
+  unsigned prefix;              // bits of |z| fixed so far
+  int mode;                     // 0 searching, 1 inside the ball (tau 0), 2 radius 0, 3 found
+  float tau;                    // soft threshold once mode != 0
+};
+
+// Device-resident scalars of one solve.
+struct Scalars {
+  L1State l1[2];       // [0] sparse noise s, [1] stripe noise t
+  double c3;           // y3 = c3 * d
+  double rel;          // relative change of the last pass
+  int iter;            // passes completed since setup
+  int iter_limit;      // stop when iter reaches this
+  int done;            // set once the stop rule or the cap fired
+  int status;          // 0 running, 1 converged, 2 cap, -4 numeric
+  unsigned jacobi_fail;
+  float tol;
+};
+
+// Radix levels over the 31 magnitude bits of a float.
+__host__ __device__ inline int l1_level_bits(int level) { return level == 3 ? 9 : 11; }
+__host__ __device__ inline int l1_level_shift(int level) { return level == 1 ? 20 : (level == 2 ? 9 : 0); }
+
+// Soft threshold sign(z) max(|z| - tau, 0); tau = +inf gives 0.
+__device__ __forceinline__ float soft_threshold(float z, float tau) {
+  float m = fabsf(z) - tau;
+  return m > 0.f ? copysignf(m, z) : 0.f;
+}
+
+// ---- launch wrappers (each returns the launch error) ----
+struct PrimalArgs {
+  const float *Zv, *Zh;   // sum_l P_l^T Y_l of the current Y
+  float *Znv, *Znh;       // next accumulation target, zeroed here
+  float *u, *ubar;        // u is updated in place, ubar = 2u+ - u
+  const float *s, *t, *y2, *d;
+  float *zs, *zt;         // pre-projection arguments of steps 3 and 4
+  Dims dm;
+  float gu, gs, gt, lo, hi;
+  Scalars *sc;
+  double *part;           // [2][grid]: sum (u+ - u)^2, sum u^2
+  unsigned *hcnt;         // [2][kHistBins]
+  double *hsum;           // [2][kHistBins]
+};
+cudaError_t launch_primal(const PrimalArgs &a, int grid, cudaStream_t st);
+
+struct DualArgs {
+  const float *zs, *zt, *s_old, *t_old, *ubar, *v;
+  float *s_new, *t_new, *y2, *d;
+  Dims dm;
+  float g2, g3;
+  Scalars *sc;
+  double *part;           // [grid]: sum d^2
+};
+cudaError_t launch_dual(const DualArgs &a, int grid, cudaStream_t st);
+
+struct FinalizeArgs {
+  Scalars *sc;
+  const double *part_primal;  // [2][grid_p]
+  int grid_p;
+  const double *part_dual;    // [grid_d]
+  int grid_d;
+  double eps;
+  double g3;
+};
+cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t st);
+
+// l1-ball radix selection: histogram pass over up to two vectors and the scan
+// that narrows the threshold one level.
+struct L1Args {
+  const float *x[2];
+  long long n;            // elements of each vector (both the same length)
+  int nprob;              // 1 or 2
+  Scalars *sc;
+  unsigned *hcnt;         // [2][kHistBins]
+  double *hsum;           // [2][kHistBins]
+};
+cudaError_t launch_l1_hist(const L1Args &a, int level, int grid, cudaStream_t st);
+cudaError_t launch_l1_scan(const L1Args &a, int level, cudaStream_t st);
+cudaError_t launch_soft_threshold(const float *x, float *out, long long n, const Scalars *sc,
+                                  int prob, cudaStream_t st);
+
+// Block dual (Alg. 1 steps 8-11) for all blocks.
+struct BlockDualArgs {
+  float *Y;               // [L][k*k][2][N3p], in place
+  const float *ubar;
+  float *Zv, *Zh;         // accumulated with +=
+  Dims dm;
+  float gY;
+  int rs;                 // shared-memory row stride (floats)
+  int warps;              // warps per CTA (one block per warp at a time)
+  int max_sweeps;
+  float tol;
+  Scalars *sc;            // done flag and the non-convergence counter
+};
+// Returns cudaErrorInvalidValue if k is not supported.
+cudaError_t launch_block_dual(const BlockDualArgs &a, int k, int grid, size_t smem, cudaStream_t st);
+size_t block_dual_smem_per_warp(int k, int rs);
+int block_dual_row_stride(int N3p);
+cudaError_t block_dual_prepare(int k, size_t smem_bytes);
+
+// Layout conversion and small helpers.
+cudaError_t launch_pad_cube(const float *src, float *dst, Dims dm, float scale, cudaStream_t st);
+cudaError_t launch_unpad_cube(const float *src, float *dst, Dims dm, const double *scale_dev, cudaStream_t st);
+cudaError_t launch_Y_to_internal(const float *ext, float *in, Dims dm, int k, cudaStream_t st);
+cudaError_t launch_Y_to_external(const float *in, float *ext, Dims dm, int k, cudaStream_t st);
+cudaError_t launch_Z_from_Y(const float *Y, float *Zv, float *Zh, Dims dm, int k, cudaStream_t st);
+cudaError_t launch_init_scalars(Scalars *sc, double alpha, double beta, cudaStream_t st);
+
+}  // namespace s3ttv

@@ -1,0 +1,272 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: per-operator and one-pass relative L2 error <= 1e-5 (FP32 against
+FP64); after 300 passes of Alg. 1 on the 32x32x16 parity cube the iterates agree
+to relative L2 <= 1e-3 and MPSNR to 0.01 dB.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from synthetic import WORKLOADS, CubeSpec, make_cube, random_state
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+OP_TOL = 1e-5
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2404_03313_gb300 as P
+    P.library()
+    return P
+
+
+@pytest.fixture()
+def solver(P):
+    s = P.Solver(0)
+    yield s
+    s.close()
+
+
+# ---------------------------------------------------------------------------
+# l1-ball projection (steps 3-4)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 7, 1000, 100003, 2_000_001])
+def test_l1_ball_matches_oracle(solver, n):
+    rng = np.random.default_rng(n)
+    x = (rng.standard_normal(n) * rng.uniform(0.01, 3.0, size=n)).astype(np.float32)
+    x[rng.uniform(size=n) < 0.2] = 0.0
+    if n > 10:
+        x[: n // 10] = 0.25  # many equal magnitudes
+        x[n // 10: n // 5] = -0.25
+    l1 = float(np.abs(x.astype(np.float64)).sum())
+    for frac in (0.0, 1e-4, 0.3, 0.9, 1.0, 1.5):
+        r = frac * l1
+        ref = O.proj_l1_ball(x.astype(np.float64), r)
+        xd = torch.from_numpy(x).cuda()
+        out, tau = solver.l1_ball(xd, r)
+        got = out.cpu().numpy()
+        assert rel(got, ref) <= OP_TOL, (frac, rel(got, ref))
+        assert np.abs(got - ref).max() <= 1e-5 * max(1.0, np.abs(x).max())
+        if frac >= 1.0:
+            assert tau == 0.0
+        if frac == 0.0:
+            assert np.all(got == 0)
+
+
+def test_l1_ball_host_and_device_buffers_agree(solver):
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(50_000).astype(np.float32)
+    r = 0.4 * float(np.abs(x).sum())
+    out_h, tau_h = solver.l1_ball(x, r)
+    out_d, tau_d = solver.l1_ball(torch.from_numpy(x).cuda(), r)
+    assert tau_h == tau_d
+    np.testing.assert_array_equal(out_h, out_d.cpu().numpy())
+
+
+def test_l1_ball_empty_and_zero(solver):
+    out, tau = solver.l1_ball(np.zeros(0, np.float32), 1.0)
+    assert out.size == 0
+    out, tau = solver.l1_ball(np.zeros(1000, np.float32), 0.0)
+    assert np.all(out == 0)
+
+
+# ---------------------------------------------------------------------------
+# block dual / SVT (steps 8-11), the dominant kernel
+# ---------------------------------------------------------------------------
+BLOCK_CASES = [
+    ((8, 7, 6), 1), ((6, 6, 5), 2), ((9, 8, 16), 3), ((3, 3, 4), 3), ((5, 5, 3), 5),
+    ((12, 10, 13), 4), ((10, 11, 7), 5), ((32, 32, 16), 3), ((20, 24, 33), 5), ((16, 16, 128), 5),
+]
+
+
+@pytest.mark.parametrize("shape,k", BLOCK_CASES)
+def test_block_dual_matches_oracle(solver, shape, k):
+    N1, N2, N3 = shape
+    rng = np.random.default_rng(N1 * 1000 + N2 * 10 + k)
+    L = N1 * N2
+    scale = rng.uniform(0.02, 3.0, size=(L, 1, 1)) / math.sqrt(k * k + 2 * N3)
+    Y = (rng.standard_normal((L, k * k, 2 * N3)) * scale).astype(np.float32)
+    Y[rng.uniform(size=L) < 0.1] = 0.0  # some empty blocks
+    ubar = rng.uniform(-0.5, 1.5, size=shape).astype(np.float32)
+    Yd = torch.from_numpy(Y).cuda()
+    Zv, Zh, info = solver.block_dual(Yd, torch.from_numpy(ubar).cuda(), k)
+    assert info["jacobi_nonconverged"] == 0
+    X = O.structure_tensors(ubar.astype(np.float64), k)
+    Yref = O.block_dual_update(Y.astype(np.float64), X, 0.25)
+    Zvr, Zhr = O.structure_tensors_adjoint(Yref, k, shape)
+    got = Yd.cpu().numpy()
+    assert rel(got, Yref) <= OP_TOL, rel(got, Yref)
+    assert rel(Zv.cpu().numpy(), Zvr) <= OP_TOL
+    assert rel(Zh.cpu().numpy(), Zhr) <= OP_TOL
+    # every block now lies in the spectral-norm unit ball
+    assert np.linalg.norm(got.astype(np.float64), 2, axis=(1, 2)).max() <= 1 + 1e-5
+
+
+def test_block_dual_identity_when_inside_ball(solver):
+    shape, k = (7, 9, 10), 3
+    rng = np.random.default_rng(5)
+    Y = rng.standard_normal((63, 9, 20))
+    Y *= 0.5 / np.linalg.norm(Y, 2, axis=(1, 2), keepdims=True)
+    Y = Y.astype(np.float32)
+    ubar = np.full(shape, 0.3, np.float32)  # constant: X = 0
+    Yd = torch.from_numpy(Y.copy()).cuda()
+    Zv, Zh, info = solver.block_dual(Yd, torch.from_numpy(ubar).cuda(), k)
+    assert rel(Yd.cpu().numpy(), Y) <= 1e-6
+
+
+# ---------------------------------------------------------------------------
+# one whole pass of Alg. 1 from a random state
+# ---------------------------------------------------------------------------
+def _radii_for_state(st, v, k, g):
+    """Radii that make all three projections of the pass active: half the l1 norms
+    of the projection arguments of steps 3-4, and half the distance of the
+    fidelity argument of step 14 (taken from a probe pass whose ball is inactive;
+    eps does not change u, s, t)."""
+    zs = st["s"] - g["s"] * st["y3"]
+    zt = st["t"] - g["t"] * (O.diff_adj(st["y2"], O.AXIS_V) + st["y3"])
+    alpha, beta = 0.5 * float(np.abs(zs).sum()), 0.5 * float(np.abs(zt).sum())
+    probe, _ = O.iterate(st, v, k, 1e30, alpha, beta, 0.0, 1.0, g)
+    ub, sb, tb = (2 * probe[x] - st[x] for x in ("u", "s", "t"))
+    d = (st["y3"] + g["y3"] * (ub + sb + tb)) / g["y3"] - v
+    return 0.5 * float(np.linalg.norm(d)), alpha, beta
+
+
+@pytest.mark.parametrize("shape,k,policy", [((32, 32, 16), 3, "paper"), ((13, 11, 7), 2, "pc_exact"),
+                                            ((10, 9, 5), 5, "pc_exact"), ((6, 6, 2), 1, "pc_exact")])
+def test_one_pass_matches_oracle(P, solver, shape, k, policy):
+    N1, N2, N3 = shape
+    _, v = make_cube(CubeSpec(N1, N2, N3, regions=4, endmembers=3, seed=7))
+    st32 = random_state(N1, N2, N3, k, seed=11)
+    st = {key: val.astype(np.float64) for key, val in st32.items()}
+    g = O.step_sizes(N1, N2, k, policy)
+    eps, alpha, beta = _radii_for_state(st, v.astype(np.float64), k, g)
+    ref, rel_ref = O.iterate(st, v, k, eps, alpha, beta, 0.0, 1.0, g)
+
+    solver.set_option(P.OPT_STEP_POLICY, P.STEP_PAPER if policy == "paper" else P.STEP_PC_EXACT)
+    solver.setup(v, eps, alpha, beta, k)
+    for key in ("u", "s", "t", "y2", "y3", "Y"):
+        solver.set_state(key, st32[key])
+    info = solver.iterate(1)
+    assert info["iters"] == 1 and info["jacobi_nonconverged"] == 0
+    assert info["rel_change"] == pytest.approx(rel_ref, rel=1e-4)
+    for key in ("u", "s", "t", "y2", "y3", "Y"):
+        got = solver.get_state(key)
+        e = rel(got, ref[key])
+        assert e <= OP_TOL, (key, e)
+
+
+# ---------------------------------------------------------------------------
+# 300 passes on the parity cube
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def parity_run(P):
+    spec = WORKLOADS["parity_32x32x16_k3"]
+    clean, v = make_cube(spec)
+    eps, alpha, beta = O.radii(v.size, spec.sigma, spec.p_s, spec.p_t)
+    ref, it, _ = O.solve(v, spec.k, eps, alpha, beta, max_iter=300, tol=0.0)
+    with P.Solver(0) as s:
+        u, sp, t, info = s.solve(torch.from_numpy(v).cuda(), eps, alpha, beta, spec.k, max_iter=300, tol=0.0)
+    return clean, v, ref, (u.cpu().numpy(), sp.cpu().numpy(), t.cpu().numpy()), info
+
+
+def test_300_pass_iterates_match(parity_run):
+    clean, v, ref, (u, s, t), info = parity_run
+    assert info["iters"] == 300 and info["status"] == 1  # tol = 0: the cap ends the run
+    assert info["jacobi_nonconverged"] == 0
+    assert rel(u, ref["u"]) <= 1e-3
+    assert rel(s, ref["s"]) <= 1e-3
+    assert rel(t, ref["t"]) <= 1e-3
+
+
+def test_300_pass_mpsnr_matches(parity_run):
+    clean, v, ref, (u, s, t), info = parity_run
+    assert abs(O.mpsnr(u, clean) - O.mpsnr(ref["u"], clean)) <= 0.01
+    assert O.mpsnr(u, clean) > O.mpsnr(v, clean)
+
+
+def test_constraints_hold_on_gpu(parity_run):
+    clean, v, ref, (u, s, t), info = parity_run
+    spec = WORKLOADS["parity_32x32x16_k3"]
+    eps, alpha, beta = O.radii(v.size, spec.sigma, spec.p_s, spec.p_t)
+    assert u.min() >= 0.0 and u.max() <= 1.0
+    assert np.abs(s.astype(np.float64)).sum() <= alpha * (1 + 1e-5)
+    assert np.abs(t.astype(np.float64)).sum() <= beta * (1 + 1e-5)
+
+
+# ---------------------------------------------------------------------------
+# stop rule, fixed points, buffers, errors
+# ---------------------------------------------------------------------------
+def test_stop_rule_matches_oracle(P, solver):
+    spec = WORKLOADS["parity_32x32x16_k3"]
+    _, v = make_cube(spec)
+    eps, alpha, beta = O.radii(v.size, spec.sigma, spec.p_s, spec.p_t)
+    trace = []
+    _, it_ref, _ = O.solve(v, spec.k, eps, alpha, beta, max_iter=400, tol=2e-4, policy="pc_exact", trace=trace)
+    solver.set_option(P.OPT_STEP_POLICY, P.STEP_PC_EXACT)
+    solver.set_option(P.OPT_CHECK_EVERY, 7)
+    u, s, t, info = solver.solve(v, eps, alpha, beta, spec.k, max_iter=400, tol=2e-4)
+    assert info["converged"] == 1 and info["rel_change"] < 2e-4
+    assert abs(info["iters"] - it_ref) <= 1
+    assert solver.get_state("u").shape == v.shape
+
+
+def test_fixed_point_constant_cube(solver):
+    v = np.full((9, 10, 6), 0.37, np.float32)
+    u, s, t, info = solver.solve(v, 1.0, 5.0, 5.0, 3, max_iter=20, tol=0.0)
+    np.testing.assert_array_equal(u, v)
+    assert np.all(s == 0) and np.all(t == 0)
+
+
+def test_zero_radii_keep_s_and_t_zero(solver):
+    _, v = make_cube(CubeSpec(16, 12, 8, regions=3, endmembers=2, seed=2))
+    u, s, t, info = solver.solve(v, 2.0, 0.0, 0.0, 3, max_iter=15, tol=0.0)
+    assert np.all(s == 0) and np.all(t == 0)
+
+
+def test_host_and_device_buffers_agree(solver):
+    _, v = make_cube(CubeSpec(20, 18, 11, regions=3, endmembers=2, seed=4))
+    eps, alpha, beta = O.radii(v.size, 0.1, 0.05, 0.05)
+    uh, sh, th, _ = solver.solve(v, eps, alpha, beta, 3, max_iter=25, tol=0.0)
+    ud, sd, td, _ = solver.solve(torch.from_numpy(v).cuda(), eps, alpha, beta, 3, max_iter=25, tol=0.0)
+    np.testing.assert_array_equal(uh, ud.cpu().numpy())
+    np.testing.assert_array_equal(th, td.cpu().numpy())
+
+
+def test_nan_input_reports_numeric_error(P, solver):
+    v = np.random.default_rng(0).uniform(size=(8, 8, 6)).astype(np.float32)
+    v[3, 4, 2] = np.nan
+    with pytest.raises(P.S3TTVError) as e:
+        solver.solve(v, 1.0, 1.0, 1.0, 2, max_iter=10, tol=0.0)
+    assert e.value.status == P.ENUMERIC
+
+
+def test_invalid_arguments(P, solver):
+    v = np.zeros((8, 8, 6), np.float32)
+    bad = [dict(k=0), dict(k=9), dict(eps=-1.0), dict(alpha=float("nan")), dict(mu_min=1.0, mu_max=0.5)]
+    for kw in bad:
+        args = dict(eps=1.0, alpha=1.0, beta=1.0, k=2, mu_min=0.0, mu_max=1.0)
+        args.update(kw)
+        with pytest.raises(P.S3TTVError) as e:
+            solver.solve(v, args["eps"], args["alpha"], args["beta"], args["k"], args["mu_min"], args["mu_max"],
+                         max_iter=3)
+        assert e.value.status == P.EINVAL
+    with pytest.raises(P.S3TTVError) as e:
+        solver.solve(np.zeros((8, 8, 6), np.float32), 1.0, 1.0, 1.0, 6, max_iter=3)
+    assert e.value.status == P.EUNSUPPORTED
+    with pytest.raises(P.S3TTVError) as e:
+        P.Solver(0).iterate(1)
+    assert e.value.status == P.ESTATE

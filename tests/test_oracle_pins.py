@@ -101,6 +101,15 @@ def test_structure_tensor_adjoint_identity(shape, k):
     assert abs(lhs - rhs) <= 1e-11 * (abs(lhs) + 1)
 
 
+def test_pointwise_adjoint_matches_whole_cube():
+    rng = np.random.default_rng(16)
+    shape, k = (5, 6, 4), 3
+    Y = rng.standard_normal((30, 9, 8))
+    full = O.linear_op_adjoint_u(Y, k, shape)
+    for (i, j, b) in [(0, 0, 0), (4, 5, 3), (2, 3, 1), (0, 5, 2)]:
+        assert O.linear_op_adjoint_u_at(Y, k, shape, i, j, b) == pytest.approx(full[i, j, b], abs=1e-12)
+
+
 def test_assembled_operator_agrees_with_oracle_operators():
     """The sparse operator built from index definitions equals the oracle's
     forward map and its transpose equals the oracle's adjoint (Alg. 1 step 2)."""
