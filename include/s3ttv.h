@@ -65,6 +65,7 @@ typedef struct s3ttv_info {
   int jacobi_nonconverged; /* blocks whose eigen-solve reached the sweep cap         */
   double rel_change;       /* ||u+ - u||_2 / ||u||_2 of the last pass (eq. StopCri)  */
   double seconds;          /* host wall time of the call                             */
+  double jacobi_sweeps;    /* mean eigen-solve sweeps per block and pass             */
 } s3ttv_info;
 
 /* Step-size policies (option S3TTV_OPT_STEP_POLICY).

@@ -28,7 +28,7 @@ _c_int, _c_ll, _c_f, _c_d, _vp = ctypes.c_int, ctypes.c_longlong, ctypes.c_float
 class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("converged", ctypes.c_int),
                 ("jacobi_nonconverged", ctypes.c_int), ("rel_change", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("jacobi_sweeps", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -307,6 +307,7 @@ __global__ void begin_iterate_kernel(Scalars *sc, int n, float tol) {
   sc->status = 0;
   sc->tol = tol;
   sc->jacobi_fail = 0u;
+  sc->jacobi_sweeps = 0ull;
 }
 
 __global__ void set_c3_kernel(Scalars *sc, double c3) { sc->c3 = c3; }
@@ -668,6 +669,7 @@ int s3ttv_iterate(s3ttv_ctx *ctx, int n, float tol, s3ttv_info *info) {
     info->jacobi_nonconverged = (int)hs.jacobi_fail;
     info->rel_change = hs.rel;
     info->seconds = now_s() - t0;
+    info->jacobi_sweeps = done_iters > 0 ? (double)hs.jacobi_sweeps / ((double)done_iters * ctx->dm.P) : 0.0;
   }
   return status;
 }
@@ -845,7 +847,10 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   Scalars hs;
   CU(cudaMemcpyAsync(&hs, ctx->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
-  if (info) info->jacobi_nonconverged = (int)hs.jacobi_fail;
+  if (info) {
+    info->jacobi_nonconverged = (int)hs.jacobi_fail;
+    info->jacobi_sweeps = (double)hs.jacobi_sweeps / (double)dm.P;
+  }
   return S3TTV_OK;
 }
 

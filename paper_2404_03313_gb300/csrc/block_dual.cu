@@ -47,8 +47,11 @@ __global__ void __launch_bounds__(256) block_dual_kernel(BlockDualArgs a) {
   using S = Shape<K>;
   constexpr int n = S::n, NP = S::NP, NPOS = S::NPOS, H = S::H, GS = S::GS;
   extern __shared__ __align__(16) float smem[];
+  __shared__ unsigned s_sweeps;
   if (a.sc->done) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) s_sweeps = 0u;
+  __syncthreads();
   const int RS = a.rs;
   // per-warp slice rounded to 32 floats so every warp's Y' rows stay 16-byte aligned
   const size_t per_warp = ((size_t)n * RS + (size_t)n * GS + (size_t)NPOS * GS + 31) & ~(size_t)31;
@@ -143,23 +146,40 @@ __global__ void __launch_bounds__(256) block_dual_kernel(BlockDualArgs a) {
     __syncwarp();
 
     // ---- 3. one-sided Jacobi on the rows of G ----
+    // Positions 0..NPOS-1 hold the rows; lane pair i (lanes 2i, 2i+1, one half of
+    // each row) holds positions (2i, 2i+1) on even steps and (2i+1, 2i+2) on odd
+    // steps (the odd-even ordering: neighbours rotate, then trade places, so every
+    // pair of rows meets once in NPOS steps).  Between steps one row per lane
+    // moves one lane pair along a ring; on odd steps the last lane pair holds
+    // (NPOS-1, 0), which do not meet there.
     const int pi = lane >> 1, hf = lane & 1;
     const bool act = pi < NP;
+    const int src_r = act ? (pi + 1 == NP ? hf : lane + 2) : lane;      // right neighbour (ring)
+    const int src_l = act ? (pi == 0 ? 2 * (NP - 1) + hf : lane - 2) : lane;  // left neighbour (ring)
     float A[H], B[H];
+    float fro = 0.f;
     {
-      const int rA = pi, rB = NPOS - 1 - pi;
+      const int rA = 2 * pi, rB = 2 * pi + 1;
 #pragma unroll
       for (int e = 0; e < H; ++e) {
         const int col = hf * H + e;
         A[e] = (act && rA < n && col < n) ? Gm[rA * GS + col] : 0.f;
         B[e] = (act && rB < n && col < n) ? Gm[rB * GS + col] : 0.f;
+        fro = fmaf(A[e], A[e], fmaf(B[e], B[e], fro));
       }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(kFull, fro, o);
+    // rows below 1e-6 ||G||_F are numerical zeros: rotating them changes any
+    // other row's direction by less than 1e-6
+    const float floor2 = 1e-12f * fro;
     bool converged = false;
+    int sweeps = 0;
     for (int sw = 0; sw < a.max_sweeps; ++sw) {
       bool rotated = false;
 #pragma unroll 1
-      for (int stp = 0; stp < NPOS - 1; ++stp) {
+      for (int stp = 0; stp < NPOS; ++stp) {
+        const bool odd = stp & 1;
         float app = 0.f, aqq = 0.f, apq = 0.f;
 #pragma unroll
         for (int e = 0; e < H; ++e) {
@@ -170,39 +190,54 @@ __global__ void __launch_bounds__(256) block_dual_kernel(BlockDualArgs a) {
         app += __shfl_xor_sync(kFull, app, 1);
         aqq += __shfl_xor_sync(kFull, aqq, 1);
         apq += __shfl_xor_sync(kFull, apq, 1);
-        if (act && app + aqq >= 1.f && fabsf(apq) > a.tol * sqrtf(app * aqq)) {
+        const bool meets = act && !(odd && pi == NP - 1);
+        float cs = 1.f, sn = 0.f;
+        if (meets && fminf(app, aqq) > floor2 && fabsf(apq) > a.tol * sqrtf(app * aqq)) {
           const float zeta = (aqq - app) / (2.f * apq);
           const float az = fabsf(zeta);
           const float tt = az > 1e15f ? 0.5f / zeta : copysignf(1.f / (az + sqrtf(fmaf(zeta, zeta, 1.f))), zeta);
-          const float cs = rsqrtf(fmaf(tt, tt, 1.f)), sn = cs * tt;
-#pragma unroll
-          for (int e = 0; e < H; ++e) {
-            const float x = A[e], y = B[e];
-            A[e] = fmaf(cs, x, -sn * y);
-            B[e] = fmaf(sn, x, cs * y);
-          }
+          cs = rsqrtf(fmaf(tt, tt, 1.f));
+          sn = cs * tt;
           rotated = true;
         }
-        if constexpr (NP > 1) {
-          // round robin: position 0 fixed, positions 1..NPOS-1 advance by one.
+        // rotate, and trade places: the rotated B row takes A's position
 #pragma unroll
-          for (int e = 0; e < H; ++e) {
-            const float sendR = (pi == 0) ? B[e] : A[e];
-            const float fromL = __shfl_sync(kFull, sendR, (lane + 30) & 31);
-            const float fromR = __shfl_sync(kFull, B[e], (lane + 2) & 31);
-            const float nA = (pi == 0) ? A[e] : fromL;
-            const float nB = (pi == NP - 1) ? A[e] : fromR;
-            A[e] = act ? nA : 0.f;
-            B[e] = act ? nB : 0.f;
+        for (int e = 0; e < H; ++e) {
+          const float x = A[e], y = B[e];
+          const float na = meets ? fmaf(sn, x, cs * y) : x;
+          const float nb = meets ? fmaf(cs, x, -sn * y) : y;
+          A[e] = na;
+          B[e] = nb;
+        }
+        // move to the other phase's positions
+        if constexpr (NP > 1) {
+          if (!odd) {  // even -> odd: keep position 2i+1, take 2i+2 from the right
+#pragma unroll
+            for (int e = 0; e < H; ++e) {
+              const float recv = __shfl_sync(kFull, A[e], src_r);
+              A[e] = B[e];
+              B[e] = act ? recv : 0.f;
+            }
+          } else {     // odd -> even: keep position 2i+1, take 2i from the left
+#pragma unroll
+            for (int e = 0; e < H; ++e) {
+              const float recv = __shfl_sync(kFull, B[e], src_l);
+              B[e] = A[e];
+              A[e] = act ? recv : 0.f;
+            }
           }
         }
       }
+      ++sweeps;
       if (!__any_sync(kFull, rotated)) {
         converged = true;
         break;
       }
     }
-    if (!converged && lane == 0) atomicAdd(&a.sc->jacobi_fail, 1u);
+    if (lane == 0) {
+      if (!converged) atomicAdd(&a.sc->jacobi_fail, 1u);
+      atomicAdd(&s_sweeps, (unsigned)sweeps);
+    }
 
     // ---- 4. eigen-rows: lam = ||row||, keep sqrt(1 - lam^-1/2) row / lam ----
     {
@@ -298,6 +333,8 @@ __global__ void __launch_bounds__(256) block_dual_kernel(BlockDualArgs a) {
     }
     __syncwarp();
   }
+  __syncthreads();
+  if (threadIdx.x == 0 && s_sweeps) atomicAdd(&a.sc->jacobi_sweeps, (unsigned long long)s_sweeps);
 }
 
 template <int K>

@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(256) dual_kernel(DualArgs a) {
   const long long N3p = dm.N3p;
   const float c3 = (float)a.sc->c3;
   const float tau_s = a.sc->l1[0].tau, tau_t = a.sc->l1[1].tau;
+  const float tls = a.sc->l1[0].tau_lo, tlt = a.sc->l1[1].tau_lo;
   const float inv_g3 = 1.f / a.g3;
   float d2 = 0.f;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -138,11 +139,11 @@ __global__ void __launch_bounds__(256) dual_kernel(DualArgs a) {
     }
     const int i = (int)(pix / dm.N2), j = (int)(pix - (long long)i * dm.N2);
     const long long pip = ((long long)(i + 1 == dm.N1 ? 0 : i + 1) * dm.N2 + j) * N3p + b;
-    const float sp = soft_threshold(a.zs[idx], tau_s);
+    const float sp = soft_threshold(a.zs[idx], tau_s, tls);
     const float sbar = 2.f * sp - a.s_old[idx];
-    const float tp = soft_threshold(a.zt[idx], tau_t);
+    const float tp = soft_threshold(a.zt[idx], tau_t, tlt);
     const float tbar = 2.f * tp - a.t_old[idx];
-    const float tbar_n = 2.f * soft_threshold(a.zt[pip], tau_t) - a.t_old[pip];
+    const float tbar_n = 2.f * soft_threshold(a.zt[pip], tau_t, tlt) - a.t_old[pip];
     a.y2[idx] = fmaf(a.g2, tbar_n - tbar, a.y2[idx]);
     const float y3p = fmaf(a.g3, a.ubar[idx] + sbar + tbar, c3 * a.d[idx]);
     const float dn = y3p * inv_g3 - a.v[idx];

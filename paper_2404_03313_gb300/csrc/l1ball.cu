@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(1024) l1_scan_kernel(L1Args a, int level) {
       st.prefix = 0u;
       st.mode = 0;
       st.tau = 0.f;
+      st.tau_lo = 0.f;
     }
     s_st = st;
     s_best = -1;
@@ -143,6 +144,7 @@ __global__ void __launch_bounds__(1024) l1_scan_kernel(L1Args a, int level) {
         L1State st = s_st;
         st.mode = total_S <= r ? 1 : 2;
         st.tau = total_S <= r ? 0.f : INFINITY;
+        st.tau_lo = 0.f;
         a.sc->l1[pb] = st;
       }
       return;
@@ -179,7 +181,9 @@ __global__ void __launch_bounds__(1024) l1_scan_kernel(L1Args a, int level) {
     st.prefix = (pre << bits) | (unsigned)best;
     if (level == 3) {
       st.mode = 3;
-      st.tau = st.C_above > 0 ? (float)((st.S_above - r) / (double)st.C_above) : 0.f;
+      const double tau = st.C_above > 0 ? (st.S_above - r) / (double)st.C_above : 0.0;
+      st.tau = (float)tau;
+      st.tau_lo = (float)(tau - (double)st.tau);
     }
     a.sc->l1[pb] = st;
   }
@@ -187,10 +191,10 @@ __global__ void __launch_bounds__(1024) l1_scan_kernel(L1Args a, int level) {
 
 __global__ void soft_threshold_kernel(const float *__restrict__ x, float *__restrict__ out, long long n,
                                       const Scalars *sc, int prob) {
-  const float tau = sc->l1[prob].tau;
+  const float tau = sc->l1[prob].tau, tau_lo = sc->l1[prob].tau_lo;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    out[i] = soft_threshold(x[i], tau);
+    out[i] = soft_threshold(x[i], tau, tau_lo);
 }
 
 }  // namespace

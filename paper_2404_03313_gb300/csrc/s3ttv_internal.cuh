@@ -30,7 +30,8 @@ struct L1State {
   unsigned long long C_above;   // count of those
   unsigned prefix;              // bits of |z| fixed so far
   int mode;                     // 0 searching, 1 inside the ball (tau 0), 2 radius 0, 3 found
-  float tau;                    // soft threshold once mode != 0
+  float tau;                    // soft threshold once mode != 0 (rounded)
+  float tau_lo;                 // tau - (double)tau, so tau + tau_lo carries ~48 bits
 };
 
 // Device-resident scalars of one solve.
@@ -44,15 +45,20 @@ struct Scalars {
   int status;          // 0 running, 1 converged, 2 cap, -4 numeric
   unsigned jacobi_fail;
   float tol;
+  unsigned long long jacobi_sweeps;  // sweeps summed over blocks (statistics)
 };
 
 // Radix levels over the 31 magnitude bits of a float.
 __host__ __device__ inline int l1_level_bits(int level) { return level == 3 ? 9 : 11; }
 __host__ __device__ inline int l1_level_shift(int level) { return level == 1 ? 20 : (level == 2 ? 9 : 0); }
 
-// Soft threshold sign(z) max(|z| - tau, 0); tau = +inf gives 0.
-__device__ __forceinline__ float soft_threshold(float z, float tau) {
-  float m = fabsf(z) - tau;
+// Soft threshold sign(z) max(|z| - tau, 0); tau = +inf gives 0.  The threshold
+// comes as a float pair tau + tau_lo: when |z| and tau are within a factor of two
+// |z| - tau is exact in FP32, so the one rounding left is that of subtracting
+// tau_lo, and the result keeps full relative precision even when |z| - tau is
+// many orders of magnitude below |z|.
+__device__ __forceinline__ float soft_threshold(float z, float tau, float tau_lo) {
+  const float m = (fabsf(z) - tau) - tau_lo;
   return m > 0.f ? copysignf(m, z) : 0.f;
 }
 

@@ -61,8 +61,10 @@ def test_l1_ball_matches_oracle(solver, n):
         got = out.cpu().numpy()
         assert rel(got, ref) <= OP_TOL, (frac, rel(got, ref))
         assert np.abs(got - ref).max() <= 1e-5 * max(1.0, np.abs(x).max())
-        if frac >= 1.0:
+        if frac > 1.0:
             assert tau == 0.0
+        if frac == 1.0:  # on the sphere: the FP32-accumulated norm decides, tau ~ 0
+            assert tau <= 1e-6 * float(np.abs(x).max())
         if frac == 0.0:
             assert np.all(got == 0)
 
@@ -214,13 +216,19 @@ def test_stop_rule_matches_oracle(P, solver):
     spec = WORKLOADS["parity_32x32x16_k3"]
     _, v = make_cube(spec)
     eps, alpha, beta = O.radii(v.size, spec.sigma, spec.p_s, spec.p_t)
+    tol = 2e-4
     trace = []
-    _, it_ref, _ = O.solve(v, spec.k, eps, alpha, beta, max_iter=400, tol=2e-4, policy="pc_exact", trace=trace)
+    O.solve(v, spec.k, eps, alpha, beta, max_iter=400, tol=0.0, policy="pc_exact", trace=trace)
     solver.set_option(P.OPT_STEP_POLICY, P.STEP_PC_EXACT)
     solver.set_option(P.OPT_CHECK_EVERY, 7)
-    u, s, t, info = solver.solve(v, eps, alpha, beta, spec.k, max_iter=400, tol=2e-4)
-    assert info["converged"] == 1 and info["rel_change"] < 2e-4
-    assert abs(info["iters"] - it_ref) <= 1
+    u, s, t, info = solver.solve(v, eps, alpha, beta, spec.k, max_iter=400, tol=tol)
+    n = info["iters"]
+    assert info["converged"] == 1 and info["rel_change"] < tol
+    # the stop happened where the oracle's relative change crosses tol, up to the
+    # FP32 error of the relative change itself (1%)
+    assert trace[n - 1] < tol * 1.01
+    assert all(r > tol * 0.99 for r in trace[: n - 1])
+    assert info["rel_change"] == pytest.approx(trace[n - 1], rel=1e-2)
     assert solver.get_state("u").shape == v.shape
 
 
@@ -242,8 +250,9 @@ def test_host_and_device_buffers_agree(solver):
     eps, alpha, beta = O.radii(v.size, 0.1, 0.05, 0.05)
     uh, sh, th, _ = solver.solve(v, eps, alpha, beta, 3, max_iter=25, tol=0.0)
     ud, sd, td, _ = solver.solve(torch.from_numpy(v).cuda(), eps, alpha, beta, 3, max_iter=25, tol=0.0)
-    np.testing.assert_array_equal(uh, ud.cpu().numpy())
-    np.testing.assert_array_equal(th, td.cpu().numpy())
+    # Z is accumulated with float atomics, so the last bits may differ run to run
+    for h, d in ((uh, ud), (sh, sd), (th, td)):
+        assert rel(h, d.cpu().numpy()) <= 1e-6
 
 
 def test_nan_input_reports_numeric_error(P, solver):
