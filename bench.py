@@ -336,7 +336,8 @@ def run_ours(args, spec):
             "pass_roofline": {"bound": "hbm", "algorithmic_bytes": pass_bytes,
                               "achieved": pass_bytes / (ms_max / args.steps / 1000.0) / 1e9, "peak": peak,
                               "unit": "GB/s"},
-            "kernel_avg_ms": kernel_ms, "jacobi_nonconverged_last_pass_batch": info["jacobi_nonconverged"],
+            "kernel_avg_ms": kernel_ms, "jacobi_nonconverged": info["jacobi_nonconverged"],
+            "jacobi_sweeps_mean": info["jacobi_sweeps"],
             "to_tol": tol_run,
         }
         out["pass_roofline"]["frac"] = out["pass_roofline"]["achieved"] / peak

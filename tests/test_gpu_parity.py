@@ -75,8 +75,9 @@ def test_l1_ball_host_and_device_buffers_agree(solver):
     r = 0.4 * float(np.abs(x).sum())
     out_h, tau_h = solver.l1_ball(x, r)
     out_d, tau_d = solver.l1_ball(torch.from_numpy(x).cuda(), r)
-    assert tau_h == tau_d
-    np.testing.assert_array_equal(out_h, out_d.cpu().numpy())
+    # histogram sums are accumulated with float atomics: tau may differ in its last bits
+    assert tau_h == pytest.approx(tau_d, rel=1e-6)
+    assert rel(out_h, out_d.cpu().numpy()) <= 1e-6
 
 
 def test_l1_ball_empty_and_zero(solver):
@@ -114,8 +115,10 @@ def test_block_dual_matches_oracle(solver, shape, k):
     assert rel(got, Yref) <= OP_TOL, rel(got, Yref)
     assert rel(Zv.cpu().numpy(), Zvr) <= OP_TOL
     assert rel(Zh.cpu().numpy(), Zhr) <= OP_TOL
-    # every block now lies in the spectral-norm unit ball
-    assert np.linalg.norm(got.astype(np.float64), 2, axis=(1, 2)).max() <= 1 + 1e-5
+    # every block now lies in the spectral-norm unit ball, up to the FP32 Gram
+    # error: eigenvalues of G = Y'Y'^T near 1 carry an absolute error of order
+    # eps * lambda_max, and these random blocks reach lambda_max ~ 100
+    assert np.linalg.norm(got.astype(np.float64), 2, axis=(1, 2)).max() <= 1 + 1e-4
 
 
 def test_block_dual_identity_when_inside_ball(solver):
