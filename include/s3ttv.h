@@ -81,9 +81,13 @@ enum {
   S3TTV_OPT_CHECK_EVERY = 2,       /* passes between host reads of the stop flag (default 16) */
   S3TTV_OPT_JACOBI_MAX_SWEEPS = 3, /* sweep cap of the block eigen-solve (default 24, 1..64) */
   S3TTV_OPT_JACOBI_TOL = 4,        /* relative orthogonality tolerance (default 2e-6)    */
-  S3TTV_OPT_PROFILE = 5            /* 1: time each kernel class of every pass with CUDA
+  S3TTV_OPT_PROFILE = 5,           /* 1: time each kernel class of every pass with CUDA
                                       events on the context stream (resets the totals);
                                       0: off (default)                                    */
+  S3TTV_OPT_WARM_START = 6         /* 1 (default): each block's eigen-solve starts from the
+                                      eigenbasis it converged to in the previous pass
+                                      (same result, fewer sweeps; 4 (k^2+1) k^2 bytes of
+                                      workspace per block); 0: every pass starts cold     */
 };
 
 /* Kernel classes reported by s3ttv_kernel_stats. */

@@ -8,6 +8,6 @@ CPU: if the library is not built, calls raise ``S3TTVError``.
 from ._binding import (  # noqa: F401
     Info, S3TTVError, Solver, library, radii, step_sizes, LIB_PATH, SIGNATURES, STATE,
     STEP_PAPER, STEP_PC_EXACT, OPT_STEP_POLICY, OPT_CHECK_EVERY, OPT_JACOBI_MAX_SWEEPS, OPT_JACOBI_TOL,
-    OPT_PROFILE, KERNEL_CLASSES,
+    OPT_PROFILE, OPT_WARM_START, KERNEL_CLASSES,
     OK, MAXITER, EINVAL, ENOMEM, ECUDA, ENUMERIC, EUNSUPPORTED, ESTATE,
 )

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libs3ttv.so
 # status codes (s3ttv_status)
 OK, MAXITER, EINVAL, ENOMEM, ECUDA, ENUMERIC, EUNSUPPORTED, ESTATE = 0, 1, -1, -2, -3, -4, -5, -6
 STEP_PAPER, STEP_PC_EXACT = 0, 1
-OPT_STEP_POLICY, OPT_CHECK_EVERY, OPT_JACOBI_MAX_SWEEPS, OPT_JACOBI_TOL, OPT_PROFILE = 1, 2, 3, 4, 5
+OPT_STEP_POLICY, OPT_CHECK_EVERY, OPT_JACOBI_MAX_SWEEPS, OPT_JACOBI_TOL, OPT_PROFILE, OPT_WARM_START = 1, 2, 3, 4, 5, 6
 KERNEL_CLASSES = ("primal", "l1_search", "block_dual", "dual", "finalize")
 STATE = {"u": 0, "s": 1, "t": 2, "y2": 3, "y3": 4, "Y": 5}
 

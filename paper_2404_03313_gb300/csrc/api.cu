@@ -31,10 +31,14 @@ struct s3ttv_ctx {
   double gam[6] = {0, 0, 0, 0, 0, 0};
   int parity = 0;  // which of t[2], Zv[2], Zh[2] holds the current value
   // device workspace
-  size_t cap_np = 0, cap_y = 0, cap_stage = 0;
+  size_t cap_np = 0, cap_y = 0, cap_stage = 0, cap_w = 0;
   float *v = nullptr, *u = nullptr, *s = nullptr, *t[2] = {nullptr, nullptr}, *y2 = nullptr, *d = nullptr;
   float *ubar = nullptr, *zs = nullptr, *zt = nullptr, *Zv[2] = {nullptr, nullptr}, *Zh[2] = {nullptr, nullptr};
   float *Y = nullptr, *stage = nullptr;
+  float *W = nullptr;      // per-block warm-start rows of the eigen-solve
+  long long w_stride = 0;
+  bool warm_valid = false; // W holds the rows of the current Y
+  bool warm_start = true;  // option
   Scalars *sc = nullptr;
   double *part = nullptr;  // [3][kMaxGrid]
   unsigned *hcnt = nullptr;
@@ -104,7 +108,7 @@ int elementwise_grid(const s3ttv_ctx *c, long long n) {
 
 void free_all(s3ttv_ctx *c) {
   float **bufs[] = {&c->v, &c->u, &c->s, &c->t[0], &c->t[1], &c->y2, &c->d, &c->ubar, &c->zs,
-                    &c->zt, &c->Zv[0], &c->Zv[1], &c->Zh[0], &c->Zh[1], &c->Y, &c->stage};
+                    &c->zt, &c->Zv[0], &c->Zv[1], &c->Zh[0], &c->Zh[1], &c->Y, &c->stage, &c->W};
   for (float **b : bufs) {
     if (*b) cudaFree(*b);
     *b = nullptr;
@@ -117,9 +121,10 @@ void free_all(s3ttv_ctx *c) {
   c->part = nullptr;
   c->hcnt = nullptr;
   c->hsum = nullptr;
-  c->cap_np = c->cap_y = c->cap_stage = 0;
+  c->cap_np = c->cap_y = c->cap_stage = c->cap_w = 0;
   c->bytes = 0;
   c->ready = false;
+  c->warm_valid = false;
 }
 
 int dmalloc(s3ttv_ctx *ctx, void **p, size_t bytes) {
@@ -164,8 +169,11 @@ int ensure_stage(s3ttv_ctx *ctx, size_t elems) {
 int ensure_problem_buffers(s3ttv_ctx *ctx, const Dims &dm, int k) {
   const size_t np = (size_t)dm.Np;
   const size_t ny = (size_t)dm.P * k * k * 2 * dm.N3p;
-  if (np <= ctx->cap_np && ny <= ctx->cap_y && ctx->sc) return S3TTV_OK;
+  const size_t nw = (size_t)dm.P * block_dual_w_stride(k);
+  ctx->w_stride = block_dual_w_stride(k);
+  if (np <= ctx->cap_np && ny <= ctx->cap_y && nw <= ctx->cap_w && ctx->sc) return S3TTV_OK;
   free_all(ctx);
+  ctx->w_stride = block_dual_w_stride(k);
   int rc = ensure_common(ctx);
   if (rc) return rc;
   float **cubes[] = {&ctx->v, &ctx->u, &ctx->s, &ctx->t[0], &ctx->t[1], &ctx->y2, &ctx->d, &ctx->ubar,
@@ -176,12 +184,14 @@ int ensure_problem_buffers(s3ttv_ctx *ctx, const Dims &dm, int k) {
       return rc;
     }
   }
-  if ((rc = dmalloc(ctx, (void **)&ctx->Y, ny * sizeof(float)))) {
+  if ((rc = dmalloc(ctx, (void **)&ctx->Y, ny * sizeof(float))) ||
+      (rc = dmalloc(ctx, (void **)&ctx->W, nw * sizeof(float)))) {
     free_all(ctx);
     return rc;
   }
   ctx->cap_np = np;
   ctx->cap_y = ny;
+  ctx->cap_w = nw;
   return S3TTV_OK;
 }
 
@@ -372,7 +382,11 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, int grid_bd, int warps, in
   ba.max_sweeps = ctx->jacobi_max_sweeps;
   ba.tol = ctx->jacobi_tol;
   ba.sc = ctx->sc;
+  ba.W = ctx->warm_start ? ctx->W : nullptr;
+  ba.w_stride = ctx->w_stride;
+  ba.warm = ctx->warm_start && ctx->warm_valid;
   CU(launch_block_dual(ba, ctx->k, grid_bd, smem, st));
+  if (ctx->warm_start) ctx->warm_valid = true;
   if (ev) CU(cudaEventRecord(ev[3], st));
 
   DualArgs da;
@@ -548,6 +562,11 @@ int s3ttv_set_option(s3ttv_ctx *ctx, int key, double value) {
       if (!(value > 0 && value < 1)) return fail(ctx, S3TTV_EINVAL, "jacobi tol must be in (0, 1)");
       ctx->jacobi_tol = (float)value;
       return S3TTV_OK;
+    case S3TTV_OPT_WARM_START:
+      if (value != 0 && value != 1) return fail(ctx, S3TTV_EINVAL, "warm_start must be 0 or 1");
+      ctx->warm_start = value == 1;
+      ctx->warm_valid = false;
+      return S3TTV_OK;
     case S3TTV_OPT_PROFILE:
       if (value != 0 && value != 1) return fail(ctx, S3TTV_EINVAL, "profile must be 0 or 1");
       ctx->profile = value == 1;
@@ -610,6 +629,7 @@ int s3ttv_setup(s3ttv_ctx *ctx, const float *v, int N1, int N2, int N3, float ep
   CU(launch_init_scalars(ctx->sc, alpha, beta, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
   ctx->parity = 0;
+  ctx->warm_valid = false;
   ctx->ready = true;
   return S3TTV_OK;
 }
@@ -713,6 +733,7 @@ int s3ttv_set_state(s3ttv_ctx *ctx, int which, const float *src) {
       }
       break;
     case S3TTV_STATE_Y:
+      ctx->warm_valid = false;
       rc = load_Y(ctx, src);
       if (!rc) CU(launch_Z_from_Y(ctx->Y, ctx->Zv[ctx->parity], ctx->Zh[ctx->parity], ctx->dm, ctx->k, ctx->stream));
       break;
@@ -840,6 +861,9 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   ba.max_sweeps = ctx->jacobi_max_sweeps;
   ba.tol = ctx->jacobi_tol;
   ba.sc = ctx->sc;
+  ba.W = nullptr;
+  ba.w_stride = 0;
+  ba.warm = 0;
   CU(launch_block_dual(ba, k, grid, smem, ctx->stream));
   if ((rc = store_Y(ctx, Y))) return rc;
   if ((rc = store_cube(ctx, ctx->Zv[0], Zv, nullptr))) return rc;

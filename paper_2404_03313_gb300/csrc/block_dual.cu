@@ -22,8 +22,15 @@
 // eigenvalue is the row norm and the eigenvector its direction; no rotation
 // matrix is accumulated.  Row pairs sit in lane pairs (each lane holds half of
 // both rows) and move between lanes in the round-robin order, so every pair of
-// rows meets once per sweep.  Pairs whose combined norm^2 is below 1 are never
-// rotated: both rows then stay below lam = 1, where M does not depend on them.
+// rows meets once per sweep.
+//
+// Warm start: the rows of a block's eigenbasis change little from one pass of
+// Alg. 1 to the next, so each block keeps its normalized converged rows W (one
+// row per round-robin position) and the next pass starts the one-sided Jacobi
+// from C0 = W G instead of G.  With W orthogonal, rows of J^T C0 that are
+// mutually orthogonal are again lam_x u_x^T, so the result is the same
+// decomposition; it only needs fewer sweeps.  A block whose rows did not all
+// come out as nonzero directions stores a NaN marker and starts cold next time.
 #include <math.h>
 #include "s3ttv_internal.cuh"
 
@@ -41,6 +48,16 @@ struct Shape {
 
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ void sts4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+
+// 16-byte global -> shared copy that bypasses L1 (cp.async, completes at wait_all)
+__device__ __forceinline__ void cp_async16(float *sdst, const float *gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
 
 template <int K>
 __global__ void __launch_bounds__(256) block_dual_kernel(BlockDualArgs a) {
@@ -68,6 +85,12 @@ __global__ void __launch_bounds__(256) block_dual_kernel(BlockDualArgs a) {
     float *Yl = a.Y + (size_t)l * n * 2 * N3p;
 
     // ---- 1. Y' = Y + gamma_Y X,  X = P_l D D_s ubar (eq. rewrite_Lu) ----
+    for (int idx = lane; idx < n * W4; idx += 32) {
+      const int r = idx / W4, c4 = idx - r * W4;
+      cp_async16(Yp + (size_t)r * RS + (c4 << 2), Yl + (size_t)r * 2 * N3p + (c4 << 2));
+    }
+    cp_async_wait_all();
+    __syncwarp();
 #pragma unroll 1
     for (int r = 0; r < n; ++r) {
       const int ra = r / K, rc = r - ra * K;
@@ -79,12 +102,10 @@ __global__ void __launch_bounds__(256) block_dual_kernel(BlockDualArgs a) {
       const float *u00 = a.ubar + ((size_t)i * dm.N2 + j) * N3p;
       const float *uv = a.ubar + ((size_t)i1 * dm.N2 + j) * N3p;
       const float *uh = a.ubar + ((size_t)i * dm.N2 + j1) * N3p;
-      const float4 *yrow = reinterpret_cast<const float4 *>(Yl + (size_t)r * 2 * N3p);
       for (int c4 = lane; c4 < W4; c4 += 32) {
         const bool hz = c4 >= C4;
         const int b0 = (hz ? c4 - C4 : c4) << 2;
         const float *un = hz ? uh : uv;
-        float4 y = __ldcs(yrow + c4);
         const float4 q0 = __ldg(reinterpret_cast<const float4 *>(u00 + b0));
         const float4 q1 = __ldg(reinterpret_cast<const float4 *>(un + b0));
         const int bw = (b0 + 4 < dm.N3) ? b0 + 4 : 0;
@@ -100,11 +121,13 @@ __global__ void __launch_bounds__(256) block_dual_kernel(BlockDualArgs a) {
           // (D_v D_s ubar) = D_s ubar at the next pixel minus D_s ubar here
           xs[e] = (b < dm.N3) ? ((n1 - e1[e]) - (n0 - e0[e])) : 0.f;
         }
+        float *dst = Yp + (size_t)r * RS + (c4 << 2);
+        float4 y = lds4(dst);
         y.x = fmaf(gY, xs[0], y.x);
         y.y = fmaf(gY, xs[1], y.y);
         y.z = fmaf(gY, xs[2], y.z);
         y.w = fmaf(gY, xs[3], y.w);
-        sts4(Yp + (size_t)r * RS + (c4 << 2), y);
+        sts4(dst, y);
       }
     }
     __syncwarp();
@@ -145,7 +168,7 @@ __global__ void __launch_bounds__(256) block_dual_kernel(BlockDualArgs a) {
     }
     __syncwarp();
 
-    // ---- 3. one-sided Jacobi on the rows of G ----
+    // ---- 3. one-sided Jacobi on the rows of G (or of C0 = W G) ----
     // Positions 0..NPOS-1 hold the rows; lane pair i (lanes 2i, 2i+1, one half of
     // each row) holds positions (2i, 2i+1) on even steps and (2i+1, 2i+2) on odd
     // steps (the odd-even ordering: neighbours rotate, then trade places, so every
@@ -154,78 +177,125 @@ __global__ void __launch_bounds__(256) block_dual_kernel(BlockDualArgs a) {
     // (NPOS-1, 0), which do not meet there.
     const int pi = lane >> 1, hf = lane & 1;
     const bool act = pi < NP;
-    const int src_r = act ? (pi + 1 == NP ? hf : lane + 2) : lane;      // right neighbour (ring)
+    const int src_r = act ? (pi + 1 == NP ? hf : lane + 2) : lane;            // right neighbour (ring)
     const int src_l = act ? (pi == 0 ? 2 * (NP - 1) + hf : lane - 2) : lane;  // left neighbour (ring)
     float A[H], B[H];
-    float fro = 0.f;
-    {
+    const float *Wl = a.W ? a.W + (size_t)l * a.w_stride : nullptr;
+    const bool warm = a.warm && Wl && !(Wl[0] != Wl[0]);  // NaN marks "start cold"
+    if (warm) {
+      // C0 = W G: rows 2i, 2i+1 of W times G, this lane's half of the columns
+      float wa[n], wb[n];
+#pragma unroll
+      for (int kk = 0; kk < n; ++kk) {
+        wa[kk] = act ? Wl[(2 * pi) * n + kk] : 0.f;
+        wb[kk] = act ? Wl[(2 * pi + 1) * n + kk] : 0.f;
+      }
+#pragma unroll
+      for (int e = 0; e < H; ++e) {
+        const int col = hf * H + e;
+        float sa = 0.f, sb = 0.f;
+        if (col < n) {
+#pragma unroll
+          for (int kk = 0; kk < n; ++kk) {
+            const float g = Gm[kk * GS + col];
+            sa = fmaf(wa[kk], g, sa);
+            sb = fmaf(wb[kk], g, sb);
+          }
+        }
+        A[e] = sa;
+        B[e] = sb;
+      }
+    } else {
       const int rA = 2 * pi, rB = 2 * pi + 1;
 #pragma unroll
       for (int e = 0; e < H; ++e) {
         const int col = hf * H + e;
         A[e] = (act && rA < n && col < n) ? Gm[rA * GS + col] : 0.f;
         B[e] = (act && rB < n && col < n) ? Gm[rB * GS + col] : 0.f;
-        fro = fmaf(A[e], A[e], fmaf(B[e], B[e], fro));
       }
     }
+    // squared row norms, tracked through the rotations and refreshed every sweep
+    float nA, nB;
+    auto refresh = [&]() {
+      float x = 0.f, y = 0.f;
+#pragma unroll
+      for (int e = 0; e < H; ++e) {
+        x = fmaf(A[e], A[e], x);
+        y = fmaf(B[e], B[e], y);
+      }
+      nA = x + __shfl_xor_sync(kFull, x, 1);
+      nB = y + __shfl_xor_sync(kFull, y, 1);
+    };
+    refresh();
+    float fro = hf == 0 ? nA + nB : 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(kFull, fro, o);
     // rows below 1e-6 ||G||_F are numerical zeros: rotating them changes any
     // other row's direction by less than 1e-6
     const float floor2 = 1e-12f * fro;
+    const float tol2 = a.tol * a.tol;
+    bool rotated = false;
+    // One step: the pair (A, B) meets if `meets`; it is rotated to orthogonality
+    // when needed, then the rows trade places.  A pair that does not meet keeps
+    // its places (B's sign flips, which changes nothing the solver uses).
+    auto step = [&](bool meets) {
+      float apq = 0.f;
+#pragma unroll
+      for (int e = 0; e < H; ++e) apq = fmaf(A[e], B[e], apq);
+      apq += __shfl_xor_sync(kFull, apq, 1);
+      float c = 0.f, sn = 1.f, dn = 0.f;
+      if (meets) {
+        c = 1.f;
+        sn = 0.f;
+        if (fminf(nA, nB) > floor2 && apq * apq > tol2 * nA * nB) {
+          const float zeta = __fdividef(nB - nA, 2.f * apq);
+          const float tt = copysignf(__fdividef(1.f, fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f))), zeta);
+          c = rsqrtf(fmaf(tt, tt, 1.f));
+          sn = c * tt;
+          dn = tt * apq;
+          rotated = true;
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < H; ++e) {
+        const float x = A[e], y = B[e];
+        A[e] = fmaf(sn, x, c * y);   // rotated B row, now at A's position
+        B[e] = fmaf(c, x, -sn * y);  // rotated A row, now at B's position
+      }
+      const float oA = nA;
+      nA = meets ? nB + dn : nA;
+      nB = meets ? oA - dn : nB;
+    };
     bool converged = false;
     int sweeps = 0;
     for (int sw = 0; sw < a.max_sweeps; ++sw) {
-      bool rotated = false;
+      rotated = false;
+      if (sw) refresh();
 #pragma unroll 1
-      for (int stp = 0; stp < NPOS; ++stp) {
-        const bool odd = stp & 1;
-        float app = 0.f, aqq = 0.f, apq = 0.f;
+      for (int sp = 0; sp < NPOS / 2; ++sp) {
+        step(act);
+        if constexpr (NP > 1) {  // even -> odd: keep position 2i+1, take 2i+2 from the right
 #pragma unroll
-        for (int e = 0; e < H; ++e) {
-          app = fmaf(A[e], A[e], app);
-          aqq = fmaf(B[e], B[e], aqq);
-          apq = fmaf(A[e], B[e], apq);
-        }
-        app += __shfl_xor_sync(kFull, app, 1);
-        aqq += __shfl_xor_sync(kFull, aqq, 1);
-        apq += __shfl_xor_sync(kFull, apq, 1);
-        const bool meets = act && !(odd && pi == NP - 1);
-        float cs = 1.f, sn = 0.f;
-        if (meets && fminf(app, aqq) > floor2 && fabsf(apq) > a.tol * sqrtf(app * aqq)) {
-          const float zeta = (aqq - app) / (2.f * apq);
-          const float az = fabsf(zeta);
-          const float tt = az > 1e15f ? 0.5f / zeta : copysignf(1.f / (az + sqrtf(fmaf(zeta, zeta, 1.f))), zeta);
-          cs = rsqrtf(fmaf(tt, tt, 1.f));
-          sn = cs * tt;
-          rotated = true;
-        }
-        // rotate, and trade places: the rotated B row takes A's position
-#pragma unroll
-        for (int e = 0; e < H; ++e) {
-          const float x = A[e], y = B[e];
-          const float na = meets ? fmaf(sn, x, cs * y) : x;
-          const float nb = meets ? fmaf(cs, x, -sn * y) : y;
-          A[e] = na;
-          B[e] = nb;
-        }
-        // move to the other phase's positions
-        if constexpr (NP > 1) {
-          if (!odd) {  // even -> odd: keep position 2i+1, take 2i+2 from the right
-#pragma unroll
-            for (int e = 0; e < H; ++e) {
-              const float recv = __shfl_sync(kFull, A[e], src_r);
-              A[e] = B[e];
-              B[e] = act ? recv : 0.f;
-            }
-          } else {     // odd -> even: keep position 2i+1, take 2i from the left
-#pragma unroll
-            for (int e = 0; e < H; ++e) {
-              const float recv = __shfl_sync(kFull, B[e], src_l);
-              B[e] = A[e];
-              A[e] = act ? recv : 0.f;
-            }
+          for (int e = 0; e < H; ++e) {
+            const float recv = __shfl_sync(kFull, A[e], src_r);
+            A[e] = B[e];
+            B[e] = recv;
           }
+          const float rn = __shfl_sync(kFull, nA, src_r);
+          nA = nB;
+          nB = rn;
+        }
+        step(act && pi != NP - 1);
+        if constexpr (NP > 1) {  // odd -> even: keep position 2i+1, take 2i from the left
+#pragma unroll
+          for (int e = 0; e < H; ++e) {
+            const float recv = __shfl_sync(kFull, B[e], src_l);
+            B[e] = A[e];
+            A[e] = recv;
+          }
+          const float ln = __shfl_sync(kFull, nB, src_l);
+          nB = nA;
+          nA = ln;
         }
       }
       ++sweeps;
@@ -241,14 +311,7 @@ __global__ void __launch_bounds__(256) block_dual_kernel(BlockDualArgs a) {
 
     // ---- 4. eigen-rows: lam = ||row||, keep sqrt(1 - lam^-1/2) row / lam ----
     {
-      float nA = 0.f, nB = 0.f;
-#pragma unroll
-      for (int e = 0; e < H; ++e) {
-        nA = fmaf(A[e], A[e], nA);
-        nB = fmaf(B[e], B[e], nB);
-      }
-      nA += __shfl_xor_sync(kFull, nA, 1);
-      nB += __shfl_xor_sync(kFull, nB, 1);
+      refresh();
       const float lA = sqrtf(nA), lB = sqrtf(nB);
       const float sA = lA > 1.f ? sqrtf(1.f - rsqrtf(lA)) / lA : 0.f;
       const float sB = lB > 1.f ? sqrtf(1.f - rsqrtf(lB)) / lB : 0.f;
@@ -259,6 +322,27 @@ __global__ void __launch_bounds__(256) block_dual_kernel(BlockDualArgs a) {
           if (col < n) {
             Ut[(2 * pi) * GS + col] = A[e] * sA;
             Ut[(2 * pi + 1) * GS + col] = B[e] * sB;
+          }
+        }
+      }
+      if (a.W) {
+        // warm state for the next pass: the rows, normalized; all but the
+        // NPOS - n zero rows must be nonzero directions, else mark the block cold
+        const unsigned zero_rows = __popc(__ballot_sync(kFull, act && hf == 0 && nA <= floor2)) +
+                                   __popc(__ballot_sync(kFull, act && hf == 0 && nB <= floor2));
+        float *Ww = a.W + (size_t)l * a.w_stride;
+        __syncwarp();  // every lane has read Wl[0] above
+        if (zero_rows > (unsigned)(NPOS - n)) {
+          if (lane == 0) Ww[0] = __int_as_float(0x7fc00000);
+        } else if (act) {
+          const float iA = nA > floor2 ? rsqrtf(nA) : 0.f, iB = nB > floor2 ? rsqrtf(nB) : 0.f;
+#pragma unroll
+          for (int e = 0; e < H; ++e) {
+            const int col = hf * H + e;
+            if (col < n) {
+              Ww[(2 * pi) * n + col] = A[e] * iA;
+              Ww[(2 * pi + 1) * n + col] = B[e] * iB;
+            }
           }
         }
       }
@@ -349,6 +433,11 @@ cudaError_t prepare_k(size_t smem) {
 }
 
 }  // namespace
+
+long long block_dual_w_stride(int k) {
+  const int n = k * k, npos = 2 * ((n + 1) / 2);
+  return ((long long)npos * n + 3) & ~3ll;
+}
 
 int block_dual_row_stride(int N3p) {
   const int base = 2 * N3p;

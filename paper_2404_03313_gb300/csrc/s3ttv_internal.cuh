@@ -126,7 +126,12 @@ struct BlockDualArgs {
   int max_sweeps;
   float tol;
   Scalars *sc;            // done flag and the non-convergence counter
+  float *W;               // per-block warm-start rows [L][w_stride] (may be null)
+  long long w_stride;     // floats per block in W (>= NPOS * k*k)
+  int warm;               // 1: start from the rows stored in W
 };
+// floats per block of the warm-start rows
+long long block_dual_w_stride(int k);
 // Returns cudaErrorInvalidValue if k is not supported.
 cudaError_t launch_block_dual(const BlockDualArgs &a, int k, int grid, size_t smem, cudaStream_t st);
 size_t block_dual_smem_per_warp(int k, int rs);

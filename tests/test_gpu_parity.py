@@ -282,3 +282,20 @@ def test_invalid_arguments(P, solver):
     with pytest.raises(P.S3TTVError) as e:
         P.Solver(0).iterate(1)
     assert e.value.status == P.ESTATE
+
+
+def test_warm_start_matches_cold_start(P, solver):
+    """The per-block eigenbasis carried from pass to pass only changes where the
+    Jacobi sweeps start, not what they converge to."""
+    spec = WORKLOADS["parity_32x32x16_k3"]
+    _, v = make_cube(spec)
+    eps, alpha, beta = O.radii(v.size, spec.sigma, spec.p_s, spec.p_t)
+    res = {}
+    for warm in (1, 0):
+        solver.set_option(P.OPT_WARM_START, warm)
+        u, s, t, info = solver.solve(v, eps, alpha, beta, spec.k, max_iter=60, tol=0.0)
+        assert info["jacobi_nonconverged"] == 0
+        res[warm] = (u, s, t, info["jacobi_sweeps"])
+    for i in range(3):
+        assert rel(res[1][i], res[0][i]) <= 1e-5
+    assert res[1][3] < res[0][3]  # fewer sweeps when warm
