@@ -132,7 +132,7 @@ int s3ttv_set_option(s3ttv_ctx *ctx, int key, double value);
 long long s3ttv_workspace_bytes(const s3ttv_ctx *ctx);
 
 /* Number of kernels the passes of Alg. 1 (s3ttv_iterate, s3ttv_solve) have
- * launched on this context since it was created (9 per pass, plus one per call). */
+ * launched on this context since it was created (10 per pass, plus one per call). */
 long long s3ttv_launch_count(const s3ttv_ctx *ctx);
 
 /* With S3TTV_OPT_PROFILE on: total device milliseconds (ms[c]) and launches

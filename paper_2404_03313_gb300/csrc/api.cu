@@ -34,6 +34,7 @@ struct s3ttv_ctx {
   size_t cap_np = 0, cap_y = 0, cap_stage = 0, cap_w = 0;
   float *v = nullptr, *u = nullptr, *s = nullptr, *t[2] = {nullptr, nullptr}, *y2 = nullptr, *d = nullptr;
   float *ubar = nullptr, *zs = nullptr, *zt = nullptr, *Zv[2] = {nullptr, nullptr}, *Zh[2] = {nullptr, nullptr};
+  float *Fv = nullptr, *Fh = nullptr;  // D_v D_s ubar, D_h D_s ubar
   float *Y = nullptr, *stage = nullptr;
   float *W = nullptr;      // per-block warm-start rows of the eigen-solve
   long long w_stride = 0;
@@ -108,7 +109,8 @@ int elementwise_grid(const s3ttv_ctx *c, long long n) {
 
 void free_all(s3ttv_ctx *c) {
   float **bufs[] = {&c->v, &c->u, &c->s, &c->t[0], &c->t[1], &c->y2, &c->d, &c->ubar, &c->zs,
-                    &c->zt, &c->Zv[0], &c->Zv[1], &c->Zh[0], &c->Zh[1], &c->Y, &c->stage, &c->W};
+                    &c->zt, &c->Zv[0], &c->Zv[1], &c->Zh[0], &c->Zh[1], &c->Y, &c->stage, &c->W,
+                    &c->Fv, &c->Fh};
   for (float **b : bufs) {
     if (*b) cudaFree(*b);
     *b = nullptr;
@@ -177,7 +179,8 @@ int ensure_problem_buffers(s3ttv_ctx *ctx, const Dims &dm, int k) {
   int rc = ensure_common(ctx);
   if (rc) return rc;
   float **cubes[] = {&ctx->v, &ctx->u, &ctx->s, &ctx->t[0], &ctx->t[1], &ctx->y2, &ctx->d, &ctx->ubar,
-                     &ctx->zs, &ctx->zt, &ctx->Zv[0], &ctx->Zv[1], &ctx->Zh[0], &ctx->Zh[1]};
+                     &ctx->zs, &ctx->zt, &ctx->Zv[0], &ctx->Zv[1], &ctx->Zh[0], &ctx->Zh[1],
+                     &ctx->Fv, &ctx->Fh};
   for (float **b : cubes) {
     if ((rc = dmalloc(ctx, (void **)b, np * sizeof(float)))) {
       free_all(ctx);
@@ -206,26 +209,26 @@ Dims make_dims(int N1, int N2, int N3) {
   return dm;
 }
 
-// Block-dual launch shape: warps per CTA limited by shared memory.
-int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, int *warps, int *rs, size_t *smem, int *grid) {
+// Block-dual launch shape: one CTA per block, a persistent grid of as many CTAs
+// as fit on the device at once.
+int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, int *rs, size_t *smem, int *grid) {
   *rs = block_dual_row_stride(dm.N3p);
-  const size_t per = block_dual_smem_per_warp(k, *rs);
+  *smem = block_dual_smem_bytes(k, *rs);
   int dev_max = 0;
   cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
   if (dev_max <= 0) dev_max = 227 * 1024;
-  int w = (int)((size_t)dev_max / per);
-  if (w > 8) w = 8;
-  if (w < 1)
-    return fail(ctx, S3TTV_EUNSUPPORTED,
-                "a %dx%dx%d block needs %zu bytes of shared memory per warp (device limit %d)", k, k, dm.N3,
-                per, dev_max);
-  *warps = w;
-  *smem = per * w;
-  long long g = (dm.P + w - 1) / w;
-  if (g > 1 << 30) g = 1 << 30;
-  *grid = (int)g;
+  if (*smem == 0 || *smem > (size_t)dev_max)
+    return fail(ctx, S3TTV_EUNSUPPORTED, "a %dx%dx%d block needs %zu bytes of shared memory (device limit %d)", k, k,
+                dm.N3, *smem, dev_max);
   cudaError_t e = block_dual_prepare(k, *smem);
   if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+  int per_sm = 0;
+  e = block_dual_occupancy(k, *smem, &per_sm);
+  if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+  if (per_sm < 1) per_sm = 1;
+  long long g = (long long)ctx->num_sms * per_sm;
+  if (g > dm.P) g = dm.P;
+  *grid = (int)g;
   return S3TTV_OK;
 }
 
@@ -324,7 +327,7 @@ __global__ void set_c3_kernel(Scalars *sc, double c3) { sc->c3 = c3; }
 
 // One pass of Alg. 1, enqueued on the context stream.  `par` selects the current
 // t / Z buffers; the pass writes the other ones.
-int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, int grid_bd, int warps, int rs, size_t smem,
+int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, int grid_bd, int rs, size_t smem,
                  cudaEvent_t *ev) {
   const Dims &dm = ctx->dm;
   cudaStream_t st = ctx->stream;
@@ -370,15 +373,16 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, int grid_bd, int warps, in
   CU(launch_l1_scan(la, 3, st));
   if (ev) CU(cudaEventRecord(ev[2], st));
 
+  CU(launch_xfield(ctx->ubar, ctx->Fv, ctx->Fh, dm, grid_e, st));
   BlockDualArgs ba;
   ba.Y = ctx->Y;
-  ba.ubar = ctx->ubar;
+  ba.Fv = ctx->Fv;
+  ba.Fh = ctx->Fh;
   ba.Zv = ctx->Zv[par ^ 1];
   ba.Zh = ctx->Zh[par ^ 1];
   ba.dm = dm;
   ba.gY = (float)ctx->gam[3];
   ba.rs = rs;
-  ba.warps = warps;
   ba.max_sweeps = ctx->jacobi_max_sweeps;
   ba.tol = ctx->jacobi_tol;
   ba.sc = ctx->sc;
@@ -418,7 +422,7 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, int grid_bd, int warps, in
   fa.g3 = ctx->gam[5];
   CU(launch_finalize(fa, st));
   if (ev) CU(cudaEventRecord(ev[5], st));
-  ctx->launches += 9;
+  ctx->launches += 10;
   return S3TTV_OK;
 }
 
@@ -605,9 +609,9 @@ int s3ttv_setup(s3ttv_ctx *ctx, const float *v, int N1, int N2, int N3, float ep
   DeviceGuard g(ctx->device);
   ctx->ready = false;
   const Dims dm = make_dims(N1, N2, N3);
-  int warps, rs, grid;
+  int rs, grid;
   size_t smem;
-  if ((rc = block_dual_shape(ctx, dm, k, &warps, &rs, &smem, &grid))) return rc;
+  if ((rc = block_dual_shape(ctx, dm, k, &rs, &smem, &grid))) return rc;
   if ((rc = ensure_problem_buffers(ctx, dm, k))) return rc;
   ctx->dm = dm;
   ctx->k = k;
@@ -642,9 +646,9 @@ int s3ttv_iterate(s3ttv_ctx *ctx, int n, float tol, s3ttv_info *info) {
   if (n < 1) return fail(ctx, S3TTV_EINVAL, "n = %d must be >= 1", n);
   if (!(tol >= 0.f) || !std::isfinite(tol)) return fail(ctx, S3TTV_EINVAL, "tol must be finite and >= 0");
   DeviceGuard g(ctx->device);
-  int warps, rs, grid_bd;
+  int rs, grid_bd;
   size_t smem;
-  int rc = block_dual_shape(ctx, ctx->dm, ctx->k, &warps, &rs, &smem, &grid_bd);
+  int rc = block_dual_shape(ctx, ctx->dm, ctx->k, &rs, &smem, &grid_bd);
   if (rc) return rc;
   const int grid_e = elementwise_grid(ctx, ctx->dm.Np);
   Scalars hs;
@@ -661,7 +665,7 @@ int s3ttv_iterate(s3ttv_ctx *ctx, int n, float tol, s3ttv_info *info) {
     if (ctx->profile && (rc = ensure_events(ctx, chunk))) return rc;
     for (int c = 0; c < chunk; ++c) {
       cudaEvent_t *ev = ctx->profile ? ctx->ev + (size_t)kEvPerPass * c : nullptr;
-      if ((rc = enqueue_pass(ctx, par, grid_e, grid_bd, warps, rs, smem, ev))) return rc;
+      if ((rc = enqueue_pass(ctx, par, grid_e, grid_bd, rs, smem, ev))) return rc;
       par ^= 1;
     }
     enq += chunk;
@@ -837,9 +841,9 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   if (k > kMaxK) return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: this build supports k <= %d", k, kMaxK);
   DeviceGuard g(ctx->device);
   const Dims dm = make_dims(N1, N2, N3);
-  int warps, rs, grid, rc;
+  int rs, grid, rc;
   size_t smem;
-  if ((rc = block_dual_shape(ctx, dm, k, &warps, &rs, &smem, &grid))) return rc;
+  if ((rc = block_dual_shape(ctx, dm, k, &rs, &smem, &grid))) return rc;
   ctx->ready = false;
   if ((rc = ensure_problem_buffers(ctx, dm, k))) return rc;
   ctx->dm = dm;
@@ -849,15 +853,16 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   CU(cudaMemsetAsync(ctx->Zv[0], 0, sizeof(float) * dm.Np, ctx->stream));
   CU(cudaMemsetAsync(ctx->Zh[0], 0, sizeof(float) * dm.Np, ctx->stream));
   CU(launch_init_scalars(ctx->sc, 0.0, 0.0, ctx->stream));
+  CU(launch_xfield(ctx->ubar, ctx->Fv, ctx->Fh, dm, elementwise_grid(ctx, dm.Np), ctx->stream));
   BlockDualArgs ba;
   ba.Y = ctx->Y;
-  ba.ubar = ctx->ubar;
+  ba.Fv = ctx->Fv;
+  ba.Fh = ctx->Fh;
   ba.Zv = ctx->Zv[0];
   ba.Zh = ctx->Zh[0];
   ba.dm = dm;
   ba.gY = gamma_Y;
   ba.rs = rs;
-  ba.warps = warps;
   ba.max_sweeps = ctx->jacobi_max_sweeps;
   ba.tol = ctx->jacobi_tol;
   ba.sc = ctx->sc;

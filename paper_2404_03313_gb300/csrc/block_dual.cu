@@ -13,16 +13,23 @@
 // k^2 x 2N3 block.  The kernel then scatters Z += P_l^T Y_l, the term step 2 of
 // the next pass needs.
 //
-// Work decomposition: one warp owns one block at a time.  Its Y' lives in shared
-// memory (rows of 2*N3p floats, padded so the row stride is 4 mod 32 words and
-// the float4 reads of the Gram tiles do not conflict).  The Gram is computed in
-// k x k register tiles (lane (R, S) owns G[Rk.., Sk..]).  The eigenproblem is
-// solved by one-sided (Hestenes) Jacobi on the rows of G: rotating pairs of rows
-// until all rows are mutually orthogonal leaves row x = lam_x u_x^T, so the
-// eigenvalue is the row norm and the eigenvector its direction; no rotation
-// matrix is accumulated.  Row pairs sit in lane pairs (each lane holds half of
-// both rows) and move between lanes in the round-robin order, so every pair of
-// rows meets once per sweep.
+// Work decomposition: one CTA of kNW warps owns one block at a time.
+//  1. The block's Y rows arrive in shared memory by cp.async; D D_s ubar
+//     (precomputed per pass as the cubes Fv, Fh) is added with weight gamma_Y.
+//     Rows are padded so the row stride is 4 mod 32 words and the float4 reads
+//     of the Gram tiles do not conflict.
+//  2. G = Y'Y'^T: only tiles reaching the upper triangle are formed (TR x K
+//     register tiles), the 2*N3 columns split across the warps, partial tiles
+//     summed in shared memory.
+//  3. Warp 0 solves the eigenproblem by one-sided (Hestenes) Jacobi on the rows
+//     of G: rotating pairs of rows until all rows are mutually orthogonal leaves
+//     row x = lam_x u_x^T, so the eigenvalue is the row norm and the eigenvector
+//     its direction; no rotation matrix is accumulated.  Row pairs sit in lane
+//     pairs (each lane holds half of both rows) and move between lanes in the
+//     odd-even order, so every pair of rows meets once per sweep.
+//  4. Warp 0 forms M = I - sum_x w_x u_x u_x^T (stored by columns, in halves).
+//  5. Every thread applies M to one float4 column chunk for half of the rows,
+//     stores Y_l and adds P_l^T Y_l into Z with float4 atomics.
 //
 // Warm start: the rows of a block's eigenbasis change little from one pass of
 // Alg. 1 to the next, so each block keeps its normalized converged rows W (one
@@ -37,14 +44,44 @@
 namespace s3ttv {
 namespace {
 
+constexpr int kNW = 4;  // warps per CTA
+
 template <int K>
 struct Shape {
-  static constexpr int n = K * K;        // rows of a block (and of G)
-  static constexpr int NP = (n + 1) / 2; // row pairs (a zero row when n is odd)
-  static constexpr int NPOS = 2 * NP;    // round-robin positions
-  static constexpr int H = (n + 1) / 2;  // half-row length held by one lane
-  static constexpr int GS = n + 1;       // stride of G, M and the eigen-rows
+  static constexpr int n = K * K;          // rows of a block (and of G)
+  static constexpr int NP = (n + 1) / 2;   // row pairs (a zero row when n is odd)
+  static constexpr int NPOS = 2 * NP;      // round-robin positions
+  static constexpr int H = (n + 1) / 2;    // half-row length held by one lane
+  static constexpr int GS = n + 1;         // stride of G and of the eigen-rows
+  static constexpr int TR = K < 3 ? K : 3; // Gram tile rows (tile columns: K)
+  static constexpr int RH = (n + 1) / 2;   // rows per thread in the apply
+  static constexpr int MH = (RH + 3) & ~3; // padded half of a column of M
+  static constexpr int MS = 2 * MH;        // stride of the columns of M
+  // Gram tiles: row groups of TR, column groups of K, those reaching the upper triangle
+  static constexpr int NRG = (n + TR - 1) / TR;
+  static constexpr int count_tiles() {
+    int c = 0;
+    for (int t = 0; t < NRG; ++t)
+      for (int g = 0; g < K; ++g)
+        if ((g + 1) * K - 1 >= t * TR) ++c;
+    return c;
+  }
+  static constexpr int NT = count_tiles();
+  static_assert(NT <= 32, "Gram tiles must fit one warp");
+  static constexpr int TS = TR * K;        // entries per tile
 };
+
+template <int K>
+__host__ __device__ constexpr int gm_floats() {
+  using S = Shape<K>;
+  return S::n * S::MS > S::n * S::GS ? S::n * S::MS : S::n * S::GS;
+}
+
+template <int K>
+__host__ __device__ constexpr int scr_floats() {
+  using S = Shape<K>;
+  return kNW * S::NT * S::TS > S::NPOS * S::GS ? kNW * S::NT * S::TS : S::NPOS * S::GS;
+}
 
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ void sts4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
@@ -59,195 +96,92 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
+// Warp 0: one-sided Jacobi on the rows of G (or of W G), then the scaled
+// eigen-rows into Ut and the warm rows into W.  Returns the sweeps used.
 template <int K>
-__global__ void __launch_bounds__(256) block_dual_kernel(BlockDualArgs a) {
+__device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Gm, float *Ut, bool *ok) {
   using S = Shape<K>;
   constexpr int n = S::n, NP = S::NP, NPOS = S::NPOS, H = S::H, GS = S::GS;
-  extern __shared__ __align__(16) float smem[];
-  __shared__ unsigned s_sweeps;
-  if (a.sc->done) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) s_sweeps = 0u;
-  __syncthreads();
-  const int RS = a.rs;
-  // per-warp slice rounded to 32 floats so every warp's Y' rows stay 16-byte aligned
-  const size_t per_warp = ((size_t)n * RS + (size_t)n * GS + (size_t)NPOS * GS + 31) & ~(size_t)31;
-  float *Yp = smem + warp * per_warp;
-  float *Gm = Yp + (size_t)n * RS;  // G, then M
-  float *Ut = Gm + n * GS;          // rows sqrt(1 - lam^-1/2) u_x^T
-  const Dims dm = a.dm;
-  const int N3p = dm.N3p, C4 = N3p >> 2, W4 = 2 * C4;
-  const long long L = dm.P;
-  const float gY = a.gY;
-
-  for (long long l = (long long)blockIdx.x * a.warps + warp; l < L; l += (long long)gridDim.x * a.warps) {
-    const int p = (int)(l / dm.N2), q = (int)(l - (long long)p * dm.N2);
-    float *Yl = a.Y + (size_t)l * n * 2 * N3p;
-
-    // ---- 1. Y' = Y + gamma_Y X,  X = P_l D D_s ubar (eq. rewrite_Lu) ----
-    for (int idx = lane; idx < n * W4; idx += 32) {
-      const int r = idx / W4, c4 = idx - r * W4;
-      cp_async16(Yp + (size_t)r * RS + (c4 << 2), Yl + (size_t)r * 2 * N3p + (c4 << 2));
+  const int lane = threadIdx.x & 31;
+  // Positions 0..NPOS-1 hold the rows; lane pair i (lanes 2i, 2i+1, one half of
+  // each row) holds positions (2i, 2i+1) on even steps and (2i+1, 2i+2) on odd
+  // steps (the odd-even ordering: neighbours rotate, then trade places, so every
+  // pair of rows meets once in NPOS steps).  Between steps one row per lane
+  // moves one lane pair along a ring; on odd steps the last lane pair holds
+  // (NPOS-1, 0), which do not meet there.
+  const int pi = lane >> 1, hf = lane & 1;
+  const bool act = pi < NP;
+  const int src_r = act ? (pi + 1 == NP ? hf : lane + 2) : lane;            // right neighbour (ring)
+  const int src_l = act ? (pi == 0 ? 2 * (NP - 1) + hf : lane - 2) : lane;  // left neighbour (ring)
+  float A[H], B[H];
+  const float *Wl = a.W ? a.W + (size_t)l * a.w_stride : nullptr;
+  const bool warm = a.warm && Wl && !(Wl[0] != Wl[0]);  // NaN marks "start cold"
+  if (warm) {
+    // C0 = W G: rows 2i, 2i+1 of W times G, this lane's half of the columns
+#pragma unroll
+    for (int e = 0; e < H; ++e) {
+      A[e] = 0.f;
+      B[e] = 0.f;
     }
-    cp_async_wait_all();
-    __syncwarp();
-#pragma unroll 1
-    for (int r = 0; r < n; ++r) {
-      const int ra = r / K, rc = r - ra * K;
-      int i = p + ra;
-      if (i >= dm.N1) i -= dm.N1;
-      int j = q + rc;
-      if (j >= dm.N2) j -= dm.N2;
-      const int i1 = (i + 1 == dm.N1) ? 0 : i + 1, j1 = (j + 1 == dm.N2) ? 0 : j + 1;
-      const float *u00 = a.ubar + ((size_t)i * dm.N2 + j) * N3p;
-      const float *uv = a.ubar + ((size_t)i1 * dm.N2 + j) * N3p;
-      const float *uh = a.ubar + ((size_t)i * dm.N2 + j1) * N3p;
-      for (int c4 = lane; c4 < W4; c4 += 32) {
-        const bool hz = c4 >= C4;
-        const int b0 = (hz ? c4 - C4 : c4) << 2;
-        const float *un = hz ? uh : uv;
-        const float4 q0 = __ldg(reinterpret_cast<const float4 *>(u00 + b0));
-        const float4 q1 = __ldg(reinterpret_cast<const float4 *>(un + b0));
-        const int bw = (b0 + 4 < dm.N3) ? b0 + 4 : 0;
-        const float e0[5] = {q0.x, q0.y, q0.z, q0.w, __ldg(u00 + bw)};
-        const float e1[5] = {q1.x, q1.y, q1.z, q1.w, __ldg(un + bw)};
-        const float w0 = __ldg(u00), w1 = __ldg(un);  // band 0, the periodic successor of N3-1
-        float xs[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int b = b0 + e;
-          const float n0 = (b + 1 == dm.N3) ? w0 : e0[e + 1];
-          const float n1 = (b + 1 == dm.N3) ? w1 : e1[e + 1];
-          // (D_v D_s ubar) = D_s ubar at the next pixel minus D_s ubar here
-          xs[e] = (b < dm.N3) ? ((n1 - e1[e]) - (n0 - e0[e])) : 0.f;
-        }
-        float *dst = Yp + (size_t)r * RS + (c4 << 2);
-        float4 y = lds4(dst);
-        y.x = fmaf(gY, xs[0], y.x);
-        y.y = fmaf(gY, xs[1], y.y);
-        y.z = fmaf(gY, xs[2], y.z);
-        y.w = fmaf(gY, xs[3], y.w);
-        sts4(dst, y);
-      }
-    }
-    __syncwarp();
-
-    // ---- 2. G = Y' Y'^T in k x k register tiles ----
-    if (lane < n) {
-      const int R = lane / K, Sx = lane - R * K;
-      float acc[K][K];
-#pragma unroll
-      for (int x = 0; x < K; ++x)
-#pragma unroll
-        for (int y = 0; y < K; ++y) acc[x][y] = 0.f;
-      const float *pa = Yp + (size_t)(R * K) * RS;
-      const float *pb = Yp + (size_t)(Sx * K) * RS;
-#pragma unroll 2
-      for (int c = 0; c < 2 * N3p; c += 4) {
-        float4 va[K], vb[K];
-#pragma unroll
-        for (int x = 0; x < K; ++x) va[x] = lds4(pa + (size_t)x * RS + c);
-#pragma unroll
-        for (int y = 0; y < K; ++y) vb[y] = lds4(pb + (size_t)y * RS + c);
-#pragma unroll
-        for (int x = 0; x < K; ++x)
-#pragma unroll
-          for (int y = 0; y < K; ++y) {
-            float t = acc[x][y];
-            t = fmaf(va[x].x, vb[y].x, t);
-            t = fmaf(va[x].y, vb[y].y, t);
-            t = fmaf(va[x].z, vb[y].z, t);
-            t = fmaf(va[x].w, vb[y].w, t);
-            acc[x][y] = t;
-          }
-      }
-#pragma unroll
-      for (int x = 0; x < K; ++x)
-#pragma unroll
-        for (int y = 0; y < K; ++y) Gm[(R * K + x) * GS + Sx * K + y] = acc[x][y];
-    }
-    __syncwarp();
-
-    // ---- 3. one-sided Jacobi on the rows of G (or of C0 = W G) ----
-    // Positions 0..NPOS-1 hold the rows; lane pair i (lanes 2i, 2i+1, one half of
-    // each row) holds positions (2i, 2i+1) on even steps and (2i+1, 2i+2) on odd
-    // steps (the odd-even ordering: neighbours rotate, then trade places, so every
-    // pair of rows meets once in NPOS steps).  Between steps one row per lane
-    // moves one lane pair along a ring; on odd steps the last lane pair holds
-    // (NPOS-1, 0), which do not meet there.
-    const int pi = lane >> 1, hf = lane & 1;
-    const bool act = pi < NP;
-    const int src_r = act ? (pi + 1 == NP ? hf : lane + 2) : lane;            // right neighbour (ring)
-    const int src_l = act ? (pi == 0 ? 2 * (NP - 1) + hf : lane - 2) : lane;  // left neighbour (ring)
-    float A[H], B[H];
-    const float *Wl = a.W ? a.W + (size_t)l * a.w_stride : nullptr;
-    const bool warm = a.warm && Wl && !(Wl[0] != Wl[0]);  // NaN marks "start cold"
-    if (warm) {
-      // C0 = W G: rows 2i, 2i+1 of W times G, this lane's half of the columns
-      float wa[n], wb[n];
-#pragma unroll
-      for (int kk = 0; kk < n; ++kk) {
-        wa[kk] = act ? Wl[(2 * pi) * n + kk] : 0.f;
-        wb[kk] = act ? Wl[(2 * pi + 1) * n + kk] : 0.f;
-      }
+    const float *wra = Wl + (2 * pi) * n, *wrb = Wl + (2 * pi + 1) * n;
+#pragma unroll 5
+    for (int kk = 0; kk < n; ++kk) {
+      const float wa = act ? __ldg(wra + kk) : 0.f;
+      const float wb = act ? __ldg(wrb + kk) : 0.f;
 #pragma unroll
       for (int e = 0; e < H; ++e) {
         const int col = hf * H + e;
-        float sa = 0.f, sb = 0.f;
-        if (col < n) {
-#pragma unroll
-          for (int kk = 0; kk < n; ++kk) {
-            const float g = Gm[kk * GS + col];
-            sa = fmaf(wa[kk], g, sa);
-            sb = fmaf(wb[kk], g, sb);
-          }
-        }
-        A[e] = sa;
-        B[e] = sb;
-      }
-    } else {
-      const int rA = 2 * pi, rB = 2 * pi + 1;
-#pragma unroll
-      for (int e = 0; e < H; ++e) {
-        const int col = hf * H + e;
-        A[e] = (act && rA < n && col < n) ? Gm[rA * GS + col] : 0.f;
-        B[e] = (act && rB < n && col < n) ? Gm[rB * GS + col] : 0.f;
+        const float g = col < n ? Gm[kk * GS + col] : 0.f;
+        A[e] = fmaf(wa, g, A[e]);
+        B[e] = fmaf(wb, g, B[e]);
       }
     }
-    // squared row norms, tracked through the rotations and refreshed every sweep
-    float nA, nB;
-    auto refresh = [&]() {
-      float x = 0.f, y = 0.f;
+  } else {
+    const int rA = 2 * pi, rB = 2 * pi + 1;
 #pragma unroll
-      for (int e = 0; e < H; ++e) {
-        x = fmaf(A[e], A[e], x);
-        y = fmaf(B[e], B[e], y);
-      }
-      nA = x + __shfl_xor_sync(kFull, x, 1);
-      nB = y + __shfl_xor_sync(kFull, y, 1);
-    };
-    refresh();
-    float fro = hf == 0 ? nA + nB : 0.f;
+    for (int e = 0; e < H; ++e) {
+      const int col = hf * H + e;
+      A[e] = (act && rA < n && col < n) ? Gm[rA * GS + col] : 0.f;
+      B[e] = (act && rB < n && col < n) ? Gm[rB * GS + col] : 0.f;
+    }
+  }
+  // squared row norms, tracked through the rotations and refreshed every sweep
+  float nA, nB;
+  auto refresh = [&]() {
+    float x = 0.f, y = 0.f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(kFull, fro, o);
-    // rows below 1e-6 ||G||_F are numerical zeros: rotating them changes any
-    // other row's direction by less than 1e-6
-    const float floor2 = 1e-12f * fro;
-    const float tol2 = a.tol * a.tol;
-    bool rotated = false;
-    // One step: the pair (A, B) meets if `meets`; it is rotated to orthogonality
-    // when needed, then the rows trade places.  A pair that does not meet keeps
-    // its places (B's sign flips, which changes nothing the solver uses).
-    auto step = [&](bool meets) {
-      float apq = 0.f;
+    for (int e = 0; e < H; ++e) {
+      x = fmaf(A[e], A[e], x);
+      y = fmaf(B[e], B[e], y);
+    }
+    nA = x + __shfl_xor_sync(kFull, x, 1);
+    nB = y + __shfl_xor_sync(kFull, y, 1);
+  };
+  refresh();
+  float fro = hf == 0 ? nA + nB : 0.f;
 #pragma unroll
-      for (int e = 0; e < H; ++e) apq = fmaf(A[e], B[e], apq);
-      apq += __shfl_xor_sync(kFull, apq, 1);
-      float c = 0.f, sn = 1.f, dn = 0.f;
+  for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(kFull, fro, o);
+  // rows below 1e-6 ||G||_F are numerical zeros: rotating them changes any
+  // other row's direction by less than 1e-6
+  const float floor2 = 1e-12f * fro;
+  const float tol2 = a.tol * a.tol;
+  bool rotated = false;
+  // One step: the pair (A, B) meets if `meets`; it is rotated to orthogonality
+  // when needed, then the rows trade places.  A pair that does not meet keeps
+  // its places.  When no pair of the warp needs a rotation the trade is a plain
+  // register exchange.
+  auto step = [&](bool meets) {
+    float apq = 0.f;
+#pragma unroll
+    for (int e = 0; e < H; ++e) apq = fmaf(A[e], B[e], apq);
+    apq += __shfl_xor_sync(kFull, apq, 1);
+    const bool need = meets && fminf(nA, nB) > floor2 && apq * apq > tol2 * nA * nB;
+    if (__any_sync(kFull, need)) {
+      float c = 0.f, sn = 1.f, dn = 0.f;  // not meeting: keep places (B's sign flips)
       if (meets) {
         c = 1.f;
         sn = 0.f;
-        if (fminf(nA, nB) > floor2 && apq * apq > tol2 * nA * nB) {
+        if (need) {
           const float zeta = __fdividef(nB - nA, 2.f * apq);
           const float tt = copysignf(__fdividef(1.f, fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f))), zeta);
           c = rsqrtf(fmaf(tt, tt, 1.f));
@@ -265,171 +199,319 @@ __global__ void __launch_bounds__(256) block_dual_kernel(BlockDualArgs a) {
       const float oA = nA;
       nA = meets ? nB + dn : nA;
       nB = meets ? oA - dn : nB;
-    };
-    bool converged = false;
-    int sweeps = 0;
-    for (int sw = 0; sw < a.max_sweeps; ++sw) {
-      rotated = false;
-      if (sw) refresh();
+    } else {
+#pragma unroll
+      for (int e = 0; e < H; ++e) {
+        const float x = A[e], y = B[e];
+        A[e] = meets ? y : x;
+        B[e] = meets ? x : y;
+      }
+      const float oA = nA;
+      nA = meets ? nB : nA;
+      nB = meets ? oA : nB;
+    }
+  };
+  bool converged = false;
+  int sweeps = 0;
+  for (int sw = 0; sw < a.max_sweeps; ++sw) {
+    rotated = false;
+    if (sw) refresh();
 #pragma unroll 1
-      for (int sp = 0; sp < NPOS / 2; ++sp) {
-        step(act);
-        if constexpr (NP > 1) {  // even -> odd: keep position 2i+1, take 2i+2 from the right
-#pragma unroll
-          for (int e = 0; e < H; ++e) {
-            const float recv = __shfl_sync(kFull, A[e], src_r);
-            A[e] = B[e];
-            B[e] = recv;
-          }
-          const float rn = __shfl_sync(kFull, nA, src_r);
-          nA = nB;
-          nB = rn;
-        }
-        step(act && pi != NP - 1);
-        if constexpr (NP > 1) {  // odd -> even: keep position 2i+1, take 2i from the left
-#pragma unroll
-          for (int e = 0; e < H; ++e) {
-            const float recv = __shfl_sync(kFull, B[e], src_l);
-            B[e] = A[e];
-            A[e] = recv;
-          }
-          const float ln = __shfl_sync(kFull, nB, src_l);
-          nB = nA;
-          nA = ln;
-        }
-      }
-      ++sweeps;
-      if (!__any_sync(kFull, rotated)) {
-        converged = true;
-        break;
-      }
-    }
-    if (lane == 0) {
-      if (!converged) atomicAdd(&a.sc->jacobi_fail, 1u);
-      atomicAdd(&s_sweeps, (unsigned)sweeps);
-    }
-
-    // ---- 4. eigen-rows: lam = ||row||, keep sqrt(1 - lam^-1/2) row / lam ----
-    {
-      refresh();
-      const float lA = sqrtf(nA), lB = sqrtf(nB);
-      const float sA = lA > 1.f ? sqrtf(1.f - rsqrtf(lA)) / lA : 0.f;
-      const float sB = lB > 1.f ? sqrtf(1.f - rsqrtf(lB)) / lB : 0.f;
-      if (act) {
+    for (int sp = 0; sp < NPOS / 2; ++sp) {
+      step(act);
+      if constexpr (NP > 1) {  // even -> odd: keep position 2i+1, take 2i+2 from the right
 #pragma unroll
         for (int e = 0; e < H; ++e) {
-          const int col = hf * H + e;
-          if (col < n) {
-            Ut[(2 * pi) * GS + col] = A[e] * sA;
-            Ut[(2 * pi + 1) * GS + col] = B[e] * sB;
-          }
+          const float recv = __shfl_sync(kFull, A[e], src_r);
+          A[e] = B[e];
+          B[e] = recv;
+        }
+        const float rn = __shfl_sync(kFull, nA, src_r);
+        nA = nB;
+        nB = rn;
+      }
+      step(act && pi != NP - 1);
+      if constexpr (NP > 1) {  // odd -> even: keep position 2i+1, take 2i from the left
+#pragma unroll
+        for (int e = 0; e < H; ++e) {
+          const float recv = __shfl_sync(kFull, B[e], src_l);
+          B[e] = A[e];
+          A[e] = recv;
+        }
+        const float ln = __shfl_sync(kFull, nB, src_l);
+        nB = nA;
+        nA = ln;
+      }
+    }
+    ++sweeps;
+    if (!__any_sync(kFull, rotated)) {
+      converged = true;
+      break;
+    }
+  }
+  *ok = converged;
+
+  // eigen-rows: lam = ||row||, keep sqrt(1 - lam^-1/2) row / lam
+  refresh();
+  const float lA = sqrtf(nA), lB = sqrtf(nB);
+  const float sA = lA > 1.f ? sqrtf(1.f - rsqrtf(lA)) / lA : 0.f;
+  const float sB = lB > 1.f ? sqrtf(1.f - rsqrtf(lB)) / lB : 0.f;
+  if (act) {
+#pragma unroll
+    for (int e = 0; e < H; ++e) {
+      const int col = hf * H + e;
+      if (col < n) {
+        Ut[(2 * pi) * GS + col] = A[e] * sA;
+        Ut[(2 * pi + 1) * GS + col] = B[e] * sB;
+      }
+    }
+  }
+  if (a.W) {
+    // warm state for the next pass: the rows, normalized; all but the
+    // NPOS - n zero rows must be nonzero directions, else mark the block cold
+    const unsigned zero_rows = __popc(__ballot_sync(kFull, act && hf == 0 && nA <= floor2)) +
+                               __popc(__ballot_sync(kFull, act && hf == 0 && nB <= floor2));
+    float *Ww = a.W + (size_t)l * a.w_stride;
+    __syncwarp();  // every lane has read Wl[0] above
+    if (zero_rows > (unsigned)(NPOS - n)) {
+      if (lane == 0) Ww[0] = __int_as_float(0x7fc00000);
+    } else if (act) {
+      const float iA = nA > floor2 ? rsqrtf(nA) : 0.f, iB = nB > floor2 ? rsqrtf(nB) : 0.f;
+#pragma unroll
+      for (int e = 0; e < H; ++e) {
+        const int col = hf * H + e;
+        if (col < n) {
+          Ww[(2 * pi) * n + col] = A[e] * iA;
+          Ww[(2 * pi + 1) * n + col] = B[e] * iB;
         }
       }
-      if (a.W) {
-        // warm state for the next pass: the rows, normalized; all but the
-        // NPOS - n zero rows must be nonzero directions, else mark the block cold
-        const unsigned zero_rows = __popc(__ballot_sync(kFull, act && hf == 0 && nA <= floor2)) +
-                                   __popc(__ballot_sync(kFull, act && hf == 0 && nB <= floor2));
-        float *Ww = a.W + (size_t)l * a.w_stride;
-        __syncwarp();  // every lane has read Wl[0] above
-        if (zero_rows > (unsigned)(NPOS - n)) {
-          if (lane == 0) Ww[0] = __int_as_float(0x7fc00000);
-        } else if (act) {
-          const float iA = nA > floor2 ? rsqrtf(nA) : 0.f, iB = nB > floor2 ? rsqrtf(nB) : 0.f;
+    }
+  }
+  return sweeps;
+}
+
+template <int K>
+__global__ void __launch_bounds__(kNW * 32, 5) block_dual_kernel(BlockDualArgs a) {
+  using S = Shape<K>;
+  constexpr int n = S::n, GS = S::GS, TR = S::TR, NT = S::NT, TS = S::TS, RH = S::RH, MH = S::MH,
+                MS = S::MS;
+  constexpr int NTH = kNW * 32;
+  extern __shared__ __align__(16) float smem[];
+  __shared__ unsigned s_sweeps;
+  __shared__ int s_tile_r0[32], s_tile_c0[32];
+  if (a.sc->done) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int RS = a.rs;
+  float *Yp = smem;                     // Y' [n][RS]
+  float *Gm = Yp + (size_t)n * RS;      // G [n][GS], then M by columns [n][MS]
+  float *Scr = Gm + gm_floats<K>();     // partial Gram tiles, then the eigen-rows
+  const Dims dm = a.dm;
+  const int N3p = dm.N3p, C4 = N3p >> 2, W4 = 2 * C4;
+  const long long L = dm.P;
+  const float gY = a.gY;
+  if (tid == 0) {
+    s_sweeps = 0u;
+    int c = 0;
+    for (int t = 0; t < S::NRG; ++t)
+      for (int g = 0; g < K; ++g)
+        if ((g + 1) * K - 1 >= t * TR) {
+          s_tile_r0[c] = t * TR;
+          s_tile_c0[c] = g * K;
+          ++c;
+        }
+  }
+  __syncthreads();
+
+  for (long long l = blockIdx.x; l < L; l += gridDim.x) {
+    const int p = (int)(l / dm.N2), q = (int)(l - (long long)p * dm.N2);
+    float *Yl = a.Y + (size_t)l * n * 2 * N3p;
+
+    // ---- 1. Y' = Y + gamma_Y X,  X = P_l D D_s ubar (eq. rewrite_Lu) ----
+    for (int idx = tid; idx < n * W4; idx += NTH) {
+      const int r = idx / W4, c4 = idx - r * W4;
+      cp_async16(Yp + (size_t)r * RS + (c4 << 2), Yl + (size_t)r * 2 * N3p + (c4 << 2));
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int idx = tid; idx < n * W4; idx += NTH) {
+      const int r = idx / W4, c4 = idx - r * W4;
+      const int ra = r / K, rc = r - ra * K;
+      int i = p + ra;
+      if (i >= dm.N1) i -= dm.N1;
+      int j = q + rc;
+      if (j >= dm.N2) j -= dm.N2;
+      const bool hz = c4 >= C4;
+      const float *F = (hz ? a.Fh : a.Fv) + ((size_t)i * dm.N2 + j) * N3p + ((hz ? c4 - C4 : c4) << 2);
+      const float4 x = __ldg(reinterpret_cast<const float4 *>(F));
+      float *dst = Yp + (size_t)r * RS + (c4 << 2);
+      float4 y = lds4(dst);
+      y.x = fmaf(gY, x.x, y.x);
+      y.y = fmaf(gY, x.y, y.y);
+      y.z = fmaf(gY, x.z, y.z);
+      y.w = fmaf(gY, x.w, y.w);
+      sts4(dst, y);
+    }
+    __syncthreads();
+
+    // ---- 2. G = Y' Y'^T: tiles reaching the upper triangle, columns split over warps ----
+    if (lane < NT) {
+      const int r0 = s_tile_r0[lane], c0 = s_tile_c0[lane];
+      float acc[TR][K];
 #pragma unroll
-          for (int e = 0; e < H; ++e) {
-            const int col = hf * H + e;
-            if (col < n) {
-              Ww[(2 * pi) * n + col] = A[e] * iA;
-              Ww[(2 * pi + 1) * n + col] = B[e] * iB;
+      for (int x = 0; x < TR; ++x)
+#pragma unroll
+        for (int y = 0; y < K; ++y) acc[x][y] = 0.f;
+      const float *pa = Yp + (size_t)r0 * RS;
+      const float *pb = Yp + (size_t)c0 * RS;
+      const int q0 = (W4 * warp) / kNW, q1 = (W4 * (warp + 1)) / kNW;
+#pragma unroll 2
+      for (int qq = q0; qq < q1; ++qq) {
+        const int c = qq << 2;
+        float4 va[TR], vb[K];
+#pragma unroll
+        for (int x = 0; x < TR; ++x)
+          va[x] = (r0 + x < n) ? lds4(pa + (size_t)x * RS + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int y = 0; y < K; ++y) vb[y] = lds4(pb + (size_t)y * RS + c);
+#pragma unroll
+        for (int x = 0; x < TR; ++x)
+#pragma unroll
+          for (int y = 0; y < K; ++y) {
+            float t = acc[x][y];
+            t = fmaf(va[x].x, vb[y].x, t);
+            t = fmaf(va[x].y, vb[y].y, t);
+            t = fmaf(va[x].z, vb[y].z, t);
+            t = fmaf(va[x].w, vb[y].w, t);
+            acc[x][y] = t;
+          }
+      }
+      float *pt = Scr + ((size_t)warp * NT + lane) * TS;
+#pragma unroll
+      for (int x = 0; x < TR; ++x)
+#pragma unroll
+        for (int y = 0; y < K; ++y) pt[x * K + y] = acc[x][y];
+    }
+    __syncthreads();
+    for (int e = tid; e < NT * TS; e += NTH) {
+      const int tl = e / TS, w = e - tl * TS, x = w / K, y = w - x * K;
+      const int r = s_tile_r0[tl] + x, s = s_tile_c0[tl] + y;
+      if (r < n) {
+        float g = 0.f;
+#pragma unroll
+        for (int ww = 0; ww < kNW; ++ww) g += Scr[((size_t)ww * NT + tl) * TS + w];
+        Gm[r * GS + s] = g;
+        Gm[s * GS + r] = g;
+      }
+    }
+    __syncthreads();
+
+    // ---- 3-4. eigen-solve and M (warp 0) ----
+    if (warp == 0) {
+      bool ok;
+      const int sweeps = eigen_rows<K>(a, l, Gm, Scr, &ok);
+      if (lane == 0) {
+        if (!ok) atomicAdd(&a.sc->jacobi_fail, 1u);
+        s_sweeps += (unsigned)sweeps;
+      }
+      __syncwarp();
+      // M = I - Ut^T Ut; column s at Gm + s*MS, rows [0, RH) then [RH, n) from MH
+      float macc[K][K];
+      const int R = lane / K, Sx = lane - R * K;
+#pragma unroll
+      for (int x = 0; x < K; ++x)
+#pragma unroll
+        for (int y = 0; y < K; ++y) macc[x][y] = 0.f;
+      if (lane < n) {
+#pragma unroll 2
+        for (int xr = 0; xr < S::NPOS; ++xr) {
+          float ua[K], ub[K];
+#pragma unroll
+          for (int x = 0; x < K; ++x) ua[x] = Scr[xr * GS + R * K + x];
+#pragma unroll
+          for (int y = 0; y < K; ++y) ub[y] = Scr[xr * GS + Sx * K + y];
+#pragma unroll
+          for (int x = 0; x < K; ++x)
+#pragma unroll
+            for (int y = 0; y < K; ++y) macc[x][y] = fmaf(ua[x], ub[y], macc[x][y]);
+        }
+      }
+      __syncwarp();  // G (in Gm) no longer read by anyone
+      for (int e = lane; e < n * MS; e += 32) Gm[e] = 0.f;
+      __syncwarp();
+      if (lane < n) {
+#pragma unroll
+        for (int x = 0; x < K; ++x)
+#pragma unroll
+          for (int y = 0; y < K; ++y) {
+            const int r = R * K + x, s = Sx * K + y;
+            const int slot = r < RH ? r : MH + (r - RH);
+            Gm[s * MS + slot] = (r == s ? 1.f : 0.f) - macc[x][y];
+          }
+      }
+    }
+    __syncthreads();
+
+    // ---- 5. Y = M Y', written back, and Z += P_l^T Y ----
+    for (int task = tid; task < 2 * W4; task += NTH) {
+      const int half = task / W4, c4 = task - half * W4;
+      const bool hz = c4 >= C4;
+      const int b0 = (hz ? c4 - C4 : c4) << 2;
+      float4 acc[RH];
+#pragma unroll
+      for (int x = 0; x < RH; ++x) acc[x] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+      for (int s = 0; s < n; ++s) {
+        const float4 y = lds4(Yp + (size_t)s * RS + (c4 << 2));
+        const float *mcol = Gm + s * MS + half * MH;  // M[r][s] for this half's rows
+#pragma unroll
+        for (int x4 = 0; x4 < MH; x4 += 4) {
+          const float4 m = lds4(mcol + x4);
+          const float mm[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if (x4 + e < RH) {
+              acc[x4 + e].x = fmaf(mm[e], y.x, acc[x4 + e].x);
+              acc[x4 + e].y = fmaf(mm[e], y.y, acc[x4 + e].y);
+              acc[x4 + e].z = fmaf(mm[e], y.z, acc[x4 + e].z);
+              acc[x4 + e].w = fmaf(mm[e], y.w, acc[x4 + e].w);
             }
           }
         }
       }
-    }
-    __syncwarp();
-
-    // ---- 5. M = I - Ut^T Ut (symmetric, written into G's space) ----
-    if (lane < n) {
-      const int R = lane / K, Sx = lane - R * K;
-      float acc[K][K];
-#pragma unroll
-      for (int x = 0; x < K; ++x)
-#pragma unroll
-        for (int y = 0; y < K; ++y) acc[x][y] = 0.f;
-#pragma unroll 2
-      for (int xr = 0; xr < NPOS; ++xr) {
-        float ua[K], ub[K];
-#pragma unroll
-        for (int x = 0; x < K; ++x) ua[x] = Ut[xr * GS + R * K + x];
-#pragma unroll
-        for (int y = 0; y < K; ++y) ub[y] = Ut[xr * GS + Sx * K + y];
-#pragma unroll
-        for (int x = 0; x < K; ++x)
-#pragma unroll
-          for (int y = 0; y < K; ++y) acc[x][y] = fmaf(ua[x], ub[y], acc[x][y]);
-      }
-#pragma unroll
-      for (int x = 0; x < K; ++x)
-#pragma unroll
-        for (int y = 0; y < K; ++y) {
-          const int r = R * K + x, s = Sx * K + y;
-          Gm[r * GS + s] = (r == s ? 1.f : 0.f) - acc[x][y];
-        }
-    }
-    __syncwarp();
-
-    // ---- 6. Y = M Y', written back, and Z += P_l^T Y ----
-#pragma unroll 1
-    for (int c4 = lane; c4 < W4; c4 += 32) {
-      const bool hz = c4 >= C4;
-      const int b0 = (hz ? c4 - C4 : c4) << 2;
       float *Zo = hz ? a.Zh : a.Zv;
-#pragma unroll 1
-      for (int R = 0; R < K; ++R) {
-        float4 acc[K];
 #pragma unroll
-        for (int x = 0; x < K; ++x) acc[x] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 5
-        for (int s = 0; s < n; ++s) {
-          const float4 y = lds4(Yp + (size_t)s * RS + (c4 << 2));
-          const float *mrow = Gm + s * GS + R * K;  // M[s][R*K + x] = M[R*K + x][s]
-#pragma unroll
-          for (int x = 0; x < K; ++x) {
-            const float m = mrow[x];
-            acc[x].x = fmaf(m, y.x, acc[x].x);
-            acc[x].y = fmaf(m, y.y, acc[x].y);
-            acc[x].z = fmaf(m, y.z, acc[x].z);
-            acc[x].w = fmaf(m, y.w, acc[x].w);
-          }
-        }
-        int i = p + R;
-        if (i >= dm.N1) i -= dm.N1;
-#pragma unroll
-        for (int x = 0; x < K; ++x) {
-          const int r = R * K + x;
+      for (int x = 0; x < RH; ++x) {
+        const int r = half * RH + x;
+        if (r < n) {
           __stcs(reinterpret_cast<float4 *>(Yl + (size_t)r * 2 * N3p) + c4, acc[x]);
-          int j = q + x;
+          const int ra = r / K, rc = r - ra * K;
+          int i = p + ra;
+          if (i >= dm.N1) i -= dm.N1;
+          int j = q + rc;
           if (j >= dm.N2) j -= dm.N2;
           atomicAdd(reinterpret_cast<float4 *>(Zo + ((size_t)i * dm.N2 + j) * N3p + b0), acc[x]);
         }
       }
     }
-    __syncwarp();
+    __syncthreads();
   }
-  __syncthreads();
-  if (threadIdx.x == 0 && s_sweeps) atomicAdd(&a.sc->jacobi_sweeps, (unsigned long long)s_sweeps);
+  if (tid == 0 && s_sweeps) atomicAdd(&a.sc->jacobi_sweeps, (unsigned long long)s_sweeps);
 }
 
 template <int K>
 cudaError_t launch_k(const BlockDualArgs &a, int grid, size_t smem, cudaStream_t st) {
-  block_dual_kernel<K><<<grid, a.warps * 32, smem, st>>>(a);
+  block_dual_kernel<K><<<grid, kNW * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 template <int K>
 cudaError_t prepare_k(size_t smem) {
   return cudaFuncSetAttribute(block_dual_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int K>
+size_t smem_k(int rs) {
+  return sizeof(float) * ((size_t)Shape<K>::n * rs + gm_floats<K>() + scr_floats<K>());
 }
 
 }  // namespace
@@ -445,10 +527,17 @@ int block_dual_row_stride(int N3p) {
   return base + pad;
 }
 
-size_t block_dual_smem_per_warp(int k, int rs) {
-  const int n = k * k, np = (n + 1) / 2, gs = n + 1;
-  const size_t floats = ((size_t)n * rs + (size_t)n * gs + (size_t)(2 * np) * gs + 31) & ~(size_t)31;
-  return sizeof(float) * floats;
+int block_dual_threads() { return kNW * 32; }
+
+size_t block_dual_smem_bytes(int k, int rs) {
+  switch (k) {
+    case 1: return smem_k<1>(rs);
+    case 2: return smem_k<2>(rs);
+    case 3: return smem_k<3>(rs);
+    case 4: return smem_k<4>(rs);
+    case 5: return smem_k<5>(rs);
+    default: return 0;
+  }
 }
 
 cudaError_t block_dual_prepare(int k, size_t smem) {
@@ -458,6 +547,17 @@ cudaError_t block_dual_prepare(int k, size_t smem) {
     case 3: return prepare_k<3>(smem);
     case 4: return prepare_k<4>(smem);
     case 5: return prepare_k<5>(smem);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t block_dual_occupancy(int k, size_t smem, int *ctas) {
+  switch (k) {
+    case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, block_dual_kernel<1>, kNW * 32, smem);
+    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, block_dual_kernel<2>, kNW * 32, smem);
+    case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, block_dual_kernel<3>, kNW * 32, smem);
+    case 4: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, block_dual_kernel<4>, kNW * 32, smem);
+    case 5: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, block_dual_kernel<5>, kNW * 32, smem);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -259,6 +259,30 @@ __global__ void Z_from_Y_kernel(const float *__restrict__ Y, float *__restrict__
   }
 }
 
+// Fv = D_v D_s ubar and Fh = D_h D_s ubar: the second-order differences the
+// structure tensors of eq. (SSST) are cut from, formed once per pass.
+__global__ void xfield_kernel(const float *__restrict__ ubar, float *__restrict__ Fv, float *__restrict__ Fh,
+                              Dims dm) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < dm.Np; idx += stride) {
+    const long long pix = idx / dm.N3p;
+    const int b = (int)(idx - pix * dm.N3p);
+    if (b >= dm.N3) {
+      Fv[idx] = 0.f;
+      Fh[idx] = 0.f;
+      continue;
+    }
+    const int i = (int)(pix / dm.N2), j = (int)(pix - (long long)i * dm.N2);
+    const int bn = b + 1 == dm.N3 ? 0 : b + 1;
+    const long long p0 = pix * dm.N3p;
+    const long long pv = ((long long)(i + 1 == dm.N1 ? 0 : i + 1) * dm.N2 + j) * dm.N3p;
+    const long long ph = ((long long)i * dm.N2 + (j + 1 == dm.N2 ? 0 : j + 1)) * dm.N3p;
+    const float ds0 = ubar[p0 + bn] - ubar[p0 + b];
+    Fv[idx] = (ubar[pv + bn] - ubar[pv + b]) - ds0;
+    Fh[idx] = (ubar[ph + bn] - ubar[ph + b]) - ds0;
+  }
+}
+
 __global__ void init_scalars_kernel(Scalars *sc, double alpha, double beta) {
   Scalars s = {};
   s.l1[0].radius = alpha;
@@ -307,6 +331,11 @@ cudaError_t launch_Y_to_internal(const float *ext, float *in, Dims dm, int k, cu
 
 cudaError_t launch_Y_to_external(const float *in, float *ext, Dims dm, int k, cudaStream_t st) {
   Y_to_external_kernel<<<grid_for(dm.P * k * k * 2 * dm.N3), 256, 0, st>>>(in, ext, dm, k * k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xfield(const float *ubar, float *Fv, float *Fh, Dims dm, int grid, cudaStream_t st) {
+  xfield_kernel<<<grid, 256, 0, st>>>(ubar, Fv, Fh, dm);
   return cudaGetLastError();
 }
 

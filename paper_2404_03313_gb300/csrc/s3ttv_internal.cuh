@@ -117,12 +117,11 @@ cudaError_t launch_soft_threshold(const float *x, float *out, long long n, const
 // Block dual (Alg. 1 steps 8-11) for all blocks.
 struct BlockDualArgs {
   float *Y;               // [L][k*k][2][N3p], in place
-  const float *ubar;
+  const float *Fv, *Fh;   // D_v D_s ubar and D_h D_s ubar (internal cubes)
   float *Zv, *Zh;         // accumulated with +=
   Dims dm;
   float gY;
   int rs;                 // shared-memory row stride (floats)
-  int warps;              // warps per CTA (one block per warp at a time)
   int max_sweeps;
   float tol;
   Scalars *sc;            // done flag and the non-convergence counter
@@ -134,15 +133,19 @@ struct BlockDualArgs {
 long long block_dual_w_stride(int k);
 // Returns cudaErrorInvalidValue if k is not supported.
 cudaError_t launch_block_dual(const BlockDualArgs &a, int k, int grid, size_t smem, cudaStream_t st);
-size_t block_dual_smem_per_warp(int k, int rs);
+size_t block_dual_smem_bytes(int k, int rs);
+int block_dual_threads();
 int block_dual_row_stride(int N3p);
 cudaError_t block_dual_prepare(int k, size_t smem_bytes);
+cudaError_t block_dual_occupancy(int k, size_t smem_bytes, int *ctas_per_sm);
 
 // Layout conversion and small helpers.
 cudaError_t launch_pad_cube(const float *src, float *dst, Dims dm, float scale, cudaStream_t st);
 cudaError_t launch_unpad_cube(const float *src, float *dst, Dims dm, const double *scale_dev, cudaStream_t st);
 cudaError_t launch_Y_to_internal(const float *ext, float *in, Dims dm, int k, cudaStream_t st);
 cudaError_t launch_Y_to_external(const float *in, float *ext, Dims dm, int k, cudaStream_t st);
+// Fv = D_v D_s ubar, Fh = D_h D_s ubar (Sec. II-A differences, periodic)
+cudaError_t launch_xfield(const float *ubar, float *Fv, float *Fh, Dims dm, int grid, cudaStream_t st);
 cudaError_t launch_Z_from_Y(const float *Y, float *Zv, float *Zh, Dims dm, int k, cudaStream_t st);
 cudaError_t launch_init_scalars(Scalars *sc, double alpha, double beta, cudaStream_t st);
 
