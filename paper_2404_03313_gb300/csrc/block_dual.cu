@@ -13,27 +13,23 @@
 // k^2 x 2N3 block.  The kernel then scatters Z += P_l^T Y_l, the term step 2 of
 // the next pass needs.
 //
-// Work decomposition: one CTA of kNW warps owns one block at a time and
-// pipelines two: while warp 0 solves the eigenproblem of block l, warps 1..kNW-1
-// form the Gram matrix of the CTA's next block.
-//  1. (warps 1..) The block's Y rows arrive in shared memory by cp.async; D D_s
-//     ubar (precomputed per pass as the cubes Fv, Fh) is added with weight
-//     gamma_Y.  Rows are padded so the row stride is 4 mod 32 words and the
-//     float4 reads of the Gram tiles do not conflict.
-//  2. (warps 1..) G = Y'Y'^T: only tiles reaching the upper triangle are formed
-//     (TR x K register tiles), the 2*N3 columns split across the warps, partial
-//     tiles summed in shared memory.
-//  3. (warp 0) One-sided (Hestenes) Jacobi on the rows of G: rotating pairs of
-//     rows until all rows are mutually orthogonal leaves row x = lam_x u_x^T, so
-//     the eigenvalue is the row norm and the eigenvector its direction; no
-//     rotation matrix is accumulated.  Row pairs sit in lane pairs (each lane
-//     holds half of both rows) and move between lanes in the odd-even order, so
-//     every pair of rows meets once per sweep.
-//  4. (warp 0) M = I - sum_x w_x u_x u_x^T, stored by columns in two halves.
-//  5. (all) Each thread applies M to one float4 column chunk for half of the
-//     rows, re-reading Y_l and Fv/Fh from global memory (read microseconds
-//     earlier, so served from L2; this frees the shared Y' buffer for the next
-//     block), stores Y_l and adds P_l^T Y_l into Z with float4 atomics.
+// Work decomposition: one CTA of kNW warps owns one block at a time.
+//  1. The block's Y rows arrive in shared memory by cp.async; D D_s ubar
+//     (precomputed per pass as the cubes Fv, Fh) is added with weight gamma_Y.
+//     Rows are padded so the row stride is 4 mod 32 words and the float4 reads
+//     of the Gram tiles do not conflict.
+//  2. G = Y'Y'^T: only tiles reaching the upper triangle are formed (TR x K
+//     register tiles), the 2*N3 columns split across the warps, partial tiles
+//     summed in shared memory.
+//  3. Warp 0 solves the eigenproblem by one-sided (Hestenes) Jacobi on the rows
+//     of G: rotating pairs of rows until all rows are mutually orthogonal leaves
+//     row x = lam_x u_x^T, so the eigenvalue is the row norm and the eigenvector
+//     its direction; no rotation matrix is accumulated.  Row pairs sit in lane
+//     pairs (each lane holds half of both rows) and move between lanes in the
+//     odd-even order, so every pair of rows meets once per sweep.
+//  4. Warp 0 forms M = I - sum_x w_x u_x u_x^T (stored by columns, in halves).
+//  5. Every thread applies M to one float4 column chunk for half of the rows,
+//     stores Y_l and adds P_l^T Y_l into Z with float4 atomics.
 //
 // Warm start: the rows of a block's eigenbasis change little from one pass of
 // Alg. 1 to the next, so each block keeps its normalized converged rows W (one
@@ -78,19 +74,13 @@ struct Shape {
 template <int K>
 __host__ __device__ constexpr int gm_floats() {
   using S = Shape<K>;
-  return ((S::n * S::MS > S::n * S::GS ? S::n * S::MS : S::n * S::GS) + 3) & ~3;
+  return S::n * S::MS > S::n * S::GS ? S::n * S::MS : S::n * S::GS;
 }
 
 template <int K>
-__host__ __device__ constexpr int tiles_floats() {
+__host__ __device__ constexpr int scr_floats() {
   using S = Shape<K>;
-  return (((kNW - 1) * S::NT * S::TS) + 3) & ~3;
-}
-
-template <int K>
-__host__ __device__ constexpr int ut_floats() {
-  using S = Shape<K>;
-  return S::NPOS * S::GS;
+  return kNW * S::NT * S::TS > S::NPOS * S::GS ? kNW * S::NT * S::TS : S::NPOS * S::GS;
 }
 
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
@@ -300,34 +290,51 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Gm, 
   return sweeps;
 }
 
-// Warps 1..kNW-1 (named barrier 1): Y'_l in shared memory, then the partial
-// Gram tiles of its columns, then G_l (both triangles) into Gout.
 template <int K>
-__device__ void stage_gram(const BlockDualArgs &a, long long l, float *Yp, float *Tiles, float *Gout,
-                           const int *tile_r0, const int *tile_c0) {
+__global__ void __launch_bounds__(kNW * 32, 5) block_dual_kernel(BlockDualArgs a) {
   using S = Shape<K>;
-  constexpr int n = S::n, GS = S::GS, TR = S::TR, NT = S::NT, TS = S::TS;
-  constexpr int NSW = kNW - 1, NST = NSW * 32;  // stream warps and their threads
-  const int st = threadIdx.x - 32, sw = st >> 5, lane = threadIdx.x & 31;
-  const Dims &dm = a.dm;
-  const int N3p = dm.N3p, C4 = N3p >> 2, W4 = 2 * C4, RS = a.rs;
-  const int p = (int)(l / dm.N2), q = (int)(l - (long long)p * dm.N2);
-  const float *Yl = a.Y + (size_t)l * n * 2 * N3p;
-  {  // rows of Y_l into Yp (cp.async)
-    int r = 0, c4 = st;
-    while (c4 >= W4) { c4 -= W4; ++r; }
-    for (; r < n;) {
-      cp_async16(Yp + (size_t)r * RS + (c4 << 2), Yl + (size_t)r * 2 * N3p + (c4 << 2));
-      c4 += NST;
-      while (c4 >= W4) { c4 -= W4; ++r; }
-    }
+  constexpr int n = S::n, GS = S::GS, TR = S::TR, NT = S::NT, TS = S::TS, RH = S::RH, MH = S::MH,
+                MS = S::MS;
+  constexpr int NTH = kNW * 32;
+  extern __shared__ __align__(16) float smem[];
+  __shared__ unsigned s_sweeps;
+  __shared__ int s_tile_r0[32], s_tile_c0[32];
+  if (a.sc->done) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int RS = a.rs;
+  float *Yp = smem;                     // Y' [n][RS]
+  float *Gm = Yp + (size_t)n * RS;      // G [n][GS], then M by columns [n][MS]
+  float *Scr = Gm + gm_floats<K>();     // partial Gram tiles, then the eigen-rows
+  const Dims dm = a.dm;
+  const int N3p = dm.N3p, C4 = N3p >> 2, W4 = 2 * C4;
+  const long long L = dm.P;
+  const float gY = a.gY;
+  if (tid == 0) {
+    s_sweeps = 0u;
+    int c = 0;
+    for (int t = 0; t < S::NRG; ++t)
+      for (int g = 0; g < K; ++g)
+        if ((g + 1) * K - 1 >= t * TR) {
+          s_tile_r0[c] = t * TR;
+          s_tile_c0[c] = g * K;
+          ++c;
+        }
   }
-  cp_async_wait_all();
-  asm volatile("bar.sync 1, %0;" ::"r"(NST) : "memory");
-  {  // Y' = Y + gamma_Y (D D_s ubar) of the row's pixel
-    int r = 0, c4 = st;
-    while (c4 >= W4) { c4 -= W4; ++r; }
-    for (; r < n;) {
+  __syncthreads();
+
+  for (long long l = blockIdx.x; l < L; l += gridDim.x) {
+    const int p = (int)(l / dm.N2), q = (int)(l - (long long)p * dm.N2);
+    float *Yl = a.Y + (size_t)l * n * 2 * N3p;
+
+    // ---- 1. Y' = Y + gamma_Y X,  X = P_l D D_s ubar (eq. rewrite_Lu) ----
+    for (int idx = tid; idx < n * W4; idx += NTH) {
+      const int r = idx / W4, c4 = idx - r * W4;
+      cp_async16(Yp + (size_t)r * RS + (c4 << 2), Yl + (size_t)r * 2 * N3p + (c4 << 2));
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int idx = tid; idx < n * W4; idx += NTH) {
+      const int r = idx / W4, c4 = idx - r * W4;
       const int ra = r / K, rc = r - ra * K;
       int i = p + ra;
       if (i >= dm.N1) i -= dm.N1;
@@ -338,222 +345,151 @@ __device__ void stage_gram(const BlockDualArgs &a, long long l, float *Yp, float
       const float4 x = __ldg(reinterpret_cast<const float4 *>(F));
       float *dst = Yp + (size_t)r * RS + (c4 << 2);
       float4 y = lds4(dst);
-      y.x = fmaf(a.gY, x.x, y.x);
-      y.y = fmaf(a.gY, x.y, y.y);
-      y.z = fmaf(a.gY, x.z, y.z);
-      y.w = fmaf(a.gY, x.w, y.w);
+      y.x = fmaf(gY, x.x, y.x);
+      y.y = fmaf(gY, x.y, y.y);
+      y.z = fmaf(gY, x.z, y.z);
+      y.w = fmaf(gY, x.w, y.w);
       sts4(dst, y);
-      c4 += NST;
-      while (c4 >= W4) { c4 -= W4; ++r; }
-    }
-  }
-  asm volatile("bar.sync 1, %0;" ::"r"(NST) : "memory");
-  if (lane < NT) {  // tiles reaching the upper triangle, this warp's share of the columns
-    const int r0 = tile_r0[lane], c0 = tile_c0[lane];
-    float acc[TR][K];
-#pragma unroll
-    for (int x = 0; x < TR; ++x)
-#pragma unroll
-      for (int y = 0; y < K; ++y) acc[x][y] = 0.f;
-    const float *pa = Yp + (size_t)r0 * RS;
-    const float *pb = Yp + (size_t)c0 * RS;
-    const int q0 = (W4 * sw) / NSW, q1 = (W4 * (sw + 1)) / NSW;
-#pragma unroll 2
-    for (int qq = q0; qq < q1; ++qq) {
-      const int c = qq << 2;
-      float4 va[TR], vb[K];
-#pragma unroll
-      for (int x = 0; x < TR; ++x)
-        va[x] = (r0 + x < n) ? lds4(pa + (size_t)x * RS + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int y = 0; y < K; ++y) vb[y] = lds4(pb + (size_t)y * RS + c);
-#pragma unroll
-      for (int x = 0; x < TR; ++x)
-#pragma unroll
-        for (int y = 0; y < K; ++y) {
-          float t = acc[x][y];
-          t = fmaf(va[x].x, vb[y].x, t);
-          t = fmaf(va[x].y, vb[y].y, t);
-          t = fmaf(va[x].z, vb[y].z, t);
-          t = fmaf(va[x].w, vb[y].w, t);
-          acc[x][y] = t;
-        }
-    }
-    float *pt = Tiles + ((size_t)sw * NT + lane) * TS;
-#pragma unroll
-    for (int x = 0; x < TR; ++x)
-#pragma unroll
-      for (int y = 0; y < K; ++y) pt[x * K + y] = acc[x][y];
-  }
-  asm volatile("bar.sync 1, %0;" ::"r"(NST) : "memory");
-  for (int e = st; e < NT * TS; e += NST) {
-    const int tl = e / TS, w = e - tl * TS, x = w / K, y = w - x * K;
-    const int r = tile_r0[tl] + x, c = tile_c0[tl] + y;
-    if (r < n) {
-      float g = 0.f;
-#pragma unroll
-      for (int ww = 0; ww < NSW; ++ww) g += Tiles[((size_t)ww * NT + tl) * TS + w];
-      Gout[r * GS + c] = g;
-      Gout[c * GS + r] = g;
-    }
-  }
-}
-
-// Warp 0: eigen-solve of G (in Gm) and M = I - Ut^T Ut written over Gm by
-// columns, rows [0, RH) then [RH, n) from MH.
-template <int K>
-__device__ void stage_eigen(const BlockDualArgs &a, long long l, float *Gm, float *Ut, unsigned *sweeps_acc) {
-  using S = Shape<K>;
-  constexpr int n = S::n, GS = S::GS, RH = S::RH, MH = S::MH, MS = S::MS;
-  const int lane = threadIdx.x & 31;
-  bool ok;
-  const int sweeps = eigen_rows<K>(a, l, Gm, Ut, &ok);
-  if (lane == 0) {
-    if (!ok) atomicAdd(&a.sc->jacobi_fail, 1u);
-    *sweeps_acc += (unsigned)sweeps;
-  }
-  __syncwarp();
-  float macc[K][K];
-  const int R = lane / K, Sx = lane - R * K;
-#pragma unroll
-  for (int x = 0; x < K; ++x)
-#pragma unroll
-    for (int y = 0; y < K; ++y) macc[x][y] = 0.f;
-  if (lane < n) {
-#pragma unroll 2
-    for (int xr = 0; xr < S::NPOS; ++xr) {
-      float ua[K], ub[K];
-#pragma unroll
-      for (int x = 0; x < K; ++x) ua[x] = Ut[xr * GS + R * K + x];
-#pragma unroll
-      for (int y = 0; y < K; ++y) ub[y] = Ut[xr * GS + Sx * K + y];
-#pragma unroll
-      for (int x = 0; x < K; ++x)
-#pragma unroll
-        for (int y = 0; y < K; ++y) macc[x][y] = fmaf(ua[x], ub[y], macc[x][y]);
-    }
-  }
-  __syncwarp();  // G no longer read
-  for (int e = lane; e < n * MS; e += 32) Gm[e] = 0.f;
-  __syncwarp();
-  if (lane < n) {
-#pragma unroll
-    for (int x = 0; x < K; ++x)
-#pragma unroll
-      for (int y = 0; y < K; ++y) {
-        const int r = R * K + x, c = Sx * K + y;
-        const int slot = r < RH ? r : MH + (r - RH);
-        Gm[c * MS + slot] = (r == c ? 1.f : 0.f) - macc[x][y];
-      }
-  }
-}
-
-template <int K>
-__global__ void __launch_bounds__(kNW * 32, 5) block_dual_kernel(BlockDualArgs a) {
-  using S = Shape<K>;
-  constexpr int n = S::n, RH = S::RH, MH = S::MH, MS = S::MS;
-  constexpr int NTH = kNW * 32;
-  extern __shared__ __align__(16) float smem[];
-  __shared__ unsigned s_sweeps;
-  __shared__ int s_tile_r0[32], s_tile_c0[32];
-  if (a.sc->done) return;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  float *Yp = smem;                                    // Y' [n][RS]
-  float *G0 = Yp + (size_t)n * a.rs;                   // two G (then M) buffers
-  float *Tiles = G0 + 2 * gm_floats<K>();              // partial Gram tiles
-  float *Ut = Tiles + tiles_floats<K>();               // scaled eigen-rows
-  const Dims dm = a.dm;
-  const int N3p = dm.N3p, C4 = N3p >> 2, W4 = 2 * C4;
-  const long long L = dm.P;
-  if (tid == 0) {
-    s_sweeps = 0u;
-    int c = 0;
-    for (int t = 0; t < S::NRG; ++t)
-      for (int g = 0; g < K; ++g)
-        if ((g + 1) * K - 1 >= t * S::TR) {
-          s_tile_r0[c] = t * S::TR;
-          s_tile_c0[c] = g * K;
-          ++c;
-        }
-  }
-  __syncthreads();
-  long long l = blockIdx.x;
-  if (l < L && warp > 0) stage_gram<K>(a, l, Yp, Tiles, G0, s_tile_r0, s_tile_c0);
-  __syncthreads();
-  for (int it = 0; l < L; ++it, l += gridDim.x) {
-    const int cur = it & 1;
-    const long long ln = l + gridDim.x;
-    // eigen-solve of block l (warp 0) while the other warps form G of block ln
-    float *Gc = G0 + cur * gm_floats<K>(), *Gn = G0 + (cur ^ 1) * gm_floats<K>();
-    if (warp == 0) {
-      stage_eigen<K>(a, l, Gc, Ut, &s_sweeps);
-    } else if (ln < L) {
-      stage_gram<K>(a, ln, Yp, Tiles, Gn, s_tile_r0, s_tile_c0);
     }
     __syncthreads();
 
-    // ---- Y_l = M Y'_l, with Y'_l re-read from global (still in L2), Z += P_l^T Y_l ----
-    const int p = (int)(l / dm.N2), q = (int)(l - (long long)p * dm.N2);
-    float *Yl = a.Y + (size_t)l * n * 2 * N3p;
-    const float *Mg = Gc;
-    // tasks (column chunk, half of the rows); both halves of a chunk fall in the
-    // same round, so one barrier orders every read of a column before its writes
-    for (int base = 0; base < 2 * W4; base += NTH) {
-      const int task = base + tid;
-      const bool has = task < 2 * W4;
-      const int c4 = task >> 1, half = task & 1;
+    // ---- 2. G = Y' Y'^T: tiles reaching the upper triangle, columns split over warps ----
+    if (lane < NT) {
+      const int r0 = s_tile_r0[lane], c0 = s_tile_c0[lane];
+      float acc[TR][K];
+#pragma unroll
+      for (int x = 0; x < TR; ++x)
+#pragma unroll
+        for (int y = 0; y < K; ++y) acc[x][y] = 0.f;
+      const float *pa = Yp + (size_t)r0 * RS;
+      const float *pb = Yp + (size_t)c0 * RS;
+      const int q0 = (W4 * warp) / kNW, q1 = (W4 * (warp + 1)) / kNW;
+#pragma unroll 2
+      for (int qq = q0; qq < q1; ++qq) {
+        const int c = qq << 2;
+        float4 va[TR], vb[K];
+#pragma unroll
+        for (int x = 0; x < TR; ++x)
+          va[x] = (r0 + x < n) ? lds4(pa + (size_t)x * RS + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int y = 0; y < K; ++y) vb[y] = lds4(pb + (size_t)y * RS + c);
+#pragma unroll
+        for (int x = 0; x < TR; ++x)
+#pragma unroll
+          for (int y = 0; y < K; ++y) {
+            float t = acc[x][y];
+            t = fmaf(va[x].x, vb[y].x, t);
+            t = fmaf(va[x].y, vb[y].y, t);
+            t = fmaf(va[x].z, vb[y].z, t);
+            t = fmaf(va[x].w, vb[y].w, t);
+            acc[x][y] = t;
+          }
+      }
+      float *pt = Scr + ((size_t)warp * NT + lane) * TS;
+#pragma unroll
+      for (int x = 0; x < TR; ++x)
+#pragma unroll
+        for (int y = 0; y < K; ++y) pt[x * K + y] = acc[x][y];
+    }
+    __syncthreads();
+    for (int e = tid; e < NT * TS; e += NTH) {
+      const int tl = e / TS, w = e - tl * TS, x = w / K, y = w - x * K;
+      const int r = s_tile_r0[tl] + x, s = s_tile_c0[tl] + y;
+      if (r < n) {
+        float g = 0.f;
+#pragma unroll
+        for (int ww = 0; ww < kNW; ++ww) g += Scr[((size_t)ww * NT + tl) * TS + w];
+        Gm[r * GS + s] = g;
+        Gm[s * GS + r] = g;
+      }
+    }
+    __syncthreads();
+
+    // ---- 3-4. eigen-solve and M (warp 0) ----
+    if (warp == 0) {
+      bool ok;
+      const int sweeps = eigen_rows<K>(a, l, Gm, Scr, &ok);
+      if (lane == 0) {
+        if (!ok) atomicAdd(&a.sc->jacobi_fail, 1u);
+        s_sweeps += (unsigned)sweeps;
+      }
+      __syncwarp();
+      // M = I - Ut^T Ut; column s at Gm + s*MS, rows [0, RH) then [RH, n) from MH
+      float macc[K][K];
+      const int R = lane / K, Sx = lane - R * K;
+#pragma unroll
+      for (int x = 0; x < K; ++x)
+#pragma unroll
+        for (int y = 0; y < K; ++y) macc[x][y] = 0.f;
+      if (lane < n) {
+#pragma unroll 2
+        for (int xr = 0; xr < S::NPOS; ++xr) {
+          float ua[K], ub[K];
+#pragma unroll
+          for (int x = 0; x < K; ++x) ua[x] = Scr[xr * GS + R * K + x];
+#pragma unroll
+          for (int y = 0; y < K; ++y) ub[y] = Scr[xr * GS + Sx * K + y];
+#pragma unroll
+          for (int x = 0; x < K; ++x)
+#pragma unroll
+            for (int y = 0; y < K; ++y) macc[x][y] = fmaf(ua[x], ub[y], macc[x][y]);
+        }
+      }
+      __syncwarp();  // G (in Gm) no longer read by anyone
+      for (int e = lane; e < n * MS; e += 32) Gm[e] = 0.f;
+      __syncwarp();
+      if (lane < n) {
+#pragma unroll
+        for (int x = 0; x < K; ++x)
+#pragma unroll
+          for (int y = 0; y < K; ++y) {
+            const int r = R * K + x, s = Sx * K + y;
+            const int slot = r < RH ? r : MH + (r - RH);
+            Gm[s * MS + slot] = (r == s ? 1.f : 0.f) - macc[x][y];
+          }
+      }
+    }
+    __syncthreads();
+
+    // ---- 5. Y = M Y', written back, and Z += P_l^T Y ----
+    for (int task = tid; task < 2 * W4; task += NTH) {
+      const int half = task / W4, c4 = task - half * W4;
       const bool hz = c4 >= C4;
       const int b0 = (hz ? c4 - C4 : c4) << 2;
       float4 acc[RH];
 #pragma unroll
       for (int x = 0; x < RH; ++x) acc[x] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (has) {
-        const float *Fb = hz ? a.Fh : a.Fv;
 #pragma unroll 1
-        for (int s = 0; s < n; ++s) {
-          const int ra = s / K, rc = s - ra * K;
-          int i = p + ra;
-          if (i >= dm.N1) i -= dm.N1;
-          int j = q + rc;
-          if (j >= dm.N2) j -= dm.N2;
-          float4 y = __ldcg(reinterpret_cast<const float4 *>(Yl + (size_t)s * 2 * N3p) + c4);
-          const float4 x = __ldg(reinterpret_cast<const float4 *>(Fb + ((size_t)i * dm.N2 + j) * N3p + b0));
-          y.x = fmaf(a.gY, x.x, y.x);
-          y.y = fmaf(a.gY, x.y, y.y);
-          y.z = fmaf(a.gY, x.z, y.z);
-          y.w = fmaf(a.gY, x.w, y.w);
-          const float *mcol = Mg + s * MS + half * MH;  // M[r][s] for this half's rows
+      for (int s = 0; s < n; ++s) {
+        const float4 y = lds4(Yp + (size_t)s * RS + (c4 << 2));
+        const float *mcol = Gm + s * MS + half * MH;  // M[r][s] for this half's rows
 #pragma unroll
-          for (int x4 = 0; x4 < MH; x4 += 4) {
-            const float4 m = lds4(mcol + x4);
-            const float mm[4] = {m.x, m.y, m.z, m.w};
+        for (int x4 = 0; x4 < MH; x4 += 4) {
+          const float4 m = lds4(mcol + x4);
+          const float mm[4] = {m.x, m.y, m.z, m.w};
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              if (x4 + e < RH) {
-                acc[x4 + e].x = fmaf(mm[e], y.x, acc[x4 + e].x);
-                acc[x4 + e].y = fmaf(mm[e], y.y, acc[x4 + e].y);
-                acc[x4 + e].z = fmaf(mm[e], y.z, acc[x4 + e].z);
-                acc[x4 + e].w = fmaf(mm[e], y.w, acc[x4 + e].w);
-              }
+          for (int e = 0; e < 4; ++e) {
+            if (x4 + e < RH) {
+              acc[x4 + e].x = fmaf(mm[e], y.x, acc[x4 + e].x);
+              acc[x4 + e].y = fmaf(mm[e], y.y, acc[x4 + e].y);
+              acc[x4 + e].z = fmaf(mm[e], y.z, acc[x4 + e].z);
+              acc[x4 + e].w = fmaf(mm[e], y.w, acc[x4 + e].w);
             }
           }
         }
       }
-      __syncthreads();  // every row of these columns of Y_l is read before any is overwritten
-      if (has) {
-        float *Zo = hz ? a.Zh : a.Zv;
+      float *Zo = hz ? a.Zh : a.Zv;
 #pragma unroll
-        for (int x = 0; x < RH; ++x) {
-          const int r = half * RH + x;
-          if (r < n) {
-            __stcs(reinterpret_cast<float4 *>(Yl + (size_t)r * 2 * N3p) + c4, acc[x]);
-            const int ra = r / K, rc = r - ra * K;
-            int i = p + ra;
-            if (i >= dm.N1) i -= dm.N1;
-            int j = q + rc;
-            if (j >= dm.N2) j -= dm.N2;
-            atomicAdd(reinterpret_cast<float4 *>(Zo + ((size_t)i * dm.N2 + j) * N3p + b0), acc[x]);
-          }
+      for (int x = 0; x < RH; ++x) {
+        const int r = half * RH + x;
+        if (r < n) {
+          __stcs(reinterpret_cast<float4 *>(Yl + (size_t)r * 2 * N3p) + c4, acc[x]);
+          const int ra = r / K, rc = r - ra * K;
+          int i = p + ra;
+          if (i >= dm.N1) i -= dm.N1;
+          int j = q + rc;
+          if (j >= dm.N2) j -= dm.N2;
+          atomicAdd(reinterpret_cast<float4 *>(Zo + ((size_t)i * dm.N2 + j) * N3p + b0), acc[x]);
         }
       }
     }
@@ -575,7 +511,7 @@ cudaError_t prepare_k(size_t smem) {
 
 template <int K>
 size_t smem_k(int rs) {
-  return sizeof(float) * ((size_t)Shape<K>::n * rs + 2 * gm_floats<K>() + tiles_floats<K>() + ut_floats<K>());
+  return sizeof(float) * ((size_t)Shape<K>::n * rs + gm_floats<K>() + scr_floats<K>());
 }
 
 }  // namespace
