@@ -42,6 +42,10 @@ METRIC = "S3TTV seconds-to-tol at 256×256×128; P-PDS iters/s; % of roofline"
 UNIT = "iter/s"
 DEFAULT_WORKLOAD = "s3ttv_256x256x128_k5"
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes (read + write) per voxel of one block-dual launch, from an ncu
+# capture of the kernel whose source hashes to `sha` (profiles/block_dual_k5_*.md);
+# traffic is reported only while the kernel source is unchanged.
+BLOCK_DUAL_TRAFFIC = {"sha": "eaa6a4d747bf92c3", "k": 5, "bytes_per_voxel": 915.98e6 / 2097152}
 
 
 # ---------------------------------------------------------------------------
@@ -147,6 +151,17 @@ def nvsmi_id(device_index):
     if ids and all(x.strip().isdigit() for x in ids) and device_index < len(ids):
         return ids[device_index].strip()
     return str(device_index)
+
+
+def block_dual_traffic(k, N):
+    import hashlib
+    try:
+        src = open(os.path.join(ROOT, "paper_2404_03313_gb300", "csrc", "block_dual.cu"), "rb").read()
+    except OSError:
+        return None
+    if hashlib.sha256(src).hexdigest()[:16] != BLOCK_DUAL_TRAFFIC["sha"] or k != BLOCK_DUAL_TRAFFIC["k"]:
+        return None
+    return BLOCK_DUAL_TRAFFIC["bytes_per_voxel"] * N
 
 
 def measured_peaks():
@@ -288,7 +303,8 @@ def run_ours(args, spec):
     peak, peak_src = measured_peaks()
     achieved = alg_bytes / bd_avg_s / 1e9 if bd_avg_s > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "block_dual_kernel<5>", "peak_source": peak_src,
+                "traffic": block_dual_traffic(spec.k, N), "kernel": f"block_dual_kernel<{spec.k}>",
+                "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": bd_avg_s * 1000.0}
     pass_bytes = (16 * k2 + 120) * N
     kernel_ms = {name: (t / max(c, 1)) for name, (t, c) in stats.items()}

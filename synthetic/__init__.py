@@ -60,6 +60,9 @@ WORKLOADS = {
                                      p_s=0.05, p_t=0.10, k=5, seed=0),
     "s3ttv_304x304x191_k5": CubeSpec(304, 304, 191, regions=32, endmembers=5, sigma=0.1,
                                      p_s=0.05, p_t=0.05, k=5, seed=0),
+    # a quarter of the headline cube's pixels, for profiler captures that must stay small
+    "profile_128x128x128_k5": CubeSpec(128, 128, 128, regions=16, endmembers=5, sigma=0.05,
+                                       p_s=0.05, p_t=0.10, k=5, seed=0),
 }
 
 
