@@ -54,7 +54,8 @@ typedef enum s3ttv_status {
   S3TTV_ECUDA = -3,        /* CUDA runtime error                                     */
   S3TTV_ENUMERIC = -4,     /* NaN or Inf appeared in the iterates                    */
   S3TTV_EUNSUPPORTED = -5, /* valid but outside what this build supports (see each call) */
-  S3TTV_ESTATE = -6        /* call made before s3ttv_setup                           */
+  S3TTV_ESTATE = -6,       /* call made before s3ttv_setup                           */
+  S3TTV_ETOOBIG = -7       /* input larger than an allocation-free entry point takes */
 } s3ttv_status;
 
 /* Per-call report.  Filled by the calls that take it (may be NULL). */
@@ -195,6 +196,33 @@ int s3ttv_l1_ball(s3ttv_ctx *ctx, const float *x, float *out, long long n,
  * Uses the context's workspace (replaces any problem set up before). */
 int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, float *Zh,
                      int N1, int N2, int N3, int k, float gamma_Y, s3ttv_info *info);
+
+/* Allocation-free l1-ball projection.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc, such as code whose
+ * device memory is owned by an arena or pool it may not bypass, a plug-in whose
+ * host forbids allocation after start-up, or a real-time loop that must not
+ * touch the allocator.  It computes what s3ttv_l1_ball computes, with the same
+ * kernels, needs no context and allocates nothing: its scratch (the threshold
+ * search state and 2048 histogram bins, about 24 KB) is a fixed array in the
+ * library's device memory, which every GPU that loads the library holds until
+ * the process exits.
+ *
+ * x, out   DEVICE pointers to n floats on the current CUDA device (may alias);
+ *          host pointers are rejected with S3TTV_EINVAL (staging them would
+ *          need an allocation).
+ * n        0 <= n <= S3TTV_L1_STATIC_MAX_N (the bins count in 32 bits); larger
+ *          n returns S3TTV_ETOOBIG before any work.
+ * radius   >= 0, finite.  tau_out (host, may be NULL) receives the threshold.
+ * stream   cudaStream_t to run on, NULL for the default stream; the call returns
+ *          after that stream has finished its work.
+ * The first call on a device looks up the device address of the scratch array
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call reuses the same array and clears it
+ * first, so calls that overlap on the GPU (other streams or host threads using
+ * the same device at the same time) race and must not be issued. */
+#define S3TTV_L1_STATIC_MAX_N 4294967295LL
+int s3ttv_l1_ball_static(const float *x, float *out, long long n, double radius, double *tau_out,
+                         void *stream);
 
 /* Radii of eq. (RadiusSet) (Sec. IV-A): alpha = rho N p_s / 2,
  * beta = rho 0.5 N p_t (1 - p_s) / 2, eps = rho sqrt(sigma^2 N (1 - p_s)), and

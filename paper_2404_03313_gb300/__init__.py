@@ -6,7 +6,8 @@ thin ctypes binding over it plus the build script.  Nothing here computes on the
 CPU: if the library is not built, calls raise ``S3TTVError``.
 """
 from ._binding import (  # noqa: F401
-    Info, S3TTVError, Solver, library, radii, step_sizes, LIB_PATH, SIGNATURES, STATE,
+    Info, S3TTVError, Solver, library, radii, step_sizes, l1_ball_static, LIB_PATH, SIGNATURES, STATE,
+    L1_STATIC_MAX_N, ETOOBIG,
     STEP_PAPER, STEP_PC_EXACT, OPT_STEP_POLICY, OPT_CHECK_EVERY, OPT_JACOBI_MAX_SWEEPS, OPT_JACOBI_TOL,
     OPT_PROFILE, OPT_WARM_START, KERNEL_CLASSES,
     OK, MAXITER, EINVAL, ENOMEM, ECUDA, ENUMERIC, EUNSUPPORTED, ESTATE,

@@ -15,7 +15,8 @@ import numpy as np
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libs3ttv.so")
 
 # status codes (s3ttv_status)
-OK, MAXITER, EINVAL, ENOMEM, ECUDA, ENUMERIC, EUNSUPPORTED, ESTATE = 0, 1, -1, -2, -3, -4, -5, -6
+OK, MAXITER, EINVAL, ENOMEM, ECUDA, ENUMERIC, EUNSUPPORTED, ESTATE, ETOOBIG = 0, 1, -1, -2, -3, -4, -5, -6, -7
+L1_STATIC_MAX_N = 4294967295
 STEP_PAPER, STEP_PC_EXACT = 0, 1
 OPT_STEP_POLICY, OPT_CHECK_EVERY, OPT_JACOBI_MAX_SWEEPS, OPT_JACOBI_TOL, OPT_PROFILE, OPT_WARM_START = 1, 2, 3, 4, 5, 6
 KERNEL_CLASSES = ("primal", "l1_search", "block_dual", "dual", "finalize")
@@ -52,6 +53,7 @@ SIGNATURES = {
     "s3ttv_set_state": (_c_int, [_vp, _c_int, _vp]),
     "s3ttv_l1_ball": (_c_int, [_vp, _vp, _vp, _c_ll, _c_d, _P(_c_d)]),
     "s3ttv_block_dual": (_c_int, [_vp, _vp, _vp, _vp, _vp, _c_int, _c_int, _c_int, _c_int, _c_f, _P(Info)]),
+    "s3ttv_l1_ball_static": (_c_int, [_vp, _vp, _c_ll, _c_d, _P(_c_d), _vp]),
     "s3ttv_radii": (_c_int, [_c_ll, _c_d, _c_d, _c_d, _c_d, _P(_c_d), _P(_c_d), _P(_c_d)]),
     "s3ttv_step_sizes": (_c_int, [_c_int, _c_int, _c_int, _c_int, _P(_c_d)]),
 }
@@ -129,6 +131,25 @@ def radii(N, sigma, p_s, p_t, rho=0.95):
     if rc:
         raise S3TTVError(rc, "s3ttv_radii")
     return e.value, a.value, b.value
+
+
+def l1_ball_static(x, radius, out=None, stream=None):
+    """Allocation-free l1-ball projection (s3ttv_l1_ball_static) for callers that
+    cannot allocate device memory: x and out must be CUDA tensors on the current
+    device; returns (out, tau).  Its fixed scratch is shared by every call, so
+    calls must not overlap on the GPU."""
+    n = int(np.prod(x.shape))
+    out = _empty_like(x, x.shape) if out is None else out
+    tau = ctypes.c_double()
+    st = None
+    if stream is not None:
+        st = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _sync_torch(x)
+    rc = library().s3ttv_l1_ball_static(_ptr(x, n, "x"), _ptr(out, n, "out"), n, float(radius),
+                                        ctypes.byref(tau), st)
+    if rc < 0:
+        raise S3TTVError(rc, "s3ttv_l1_ball_static: " + library().s3ttv_strerror(rc).decode())
+    return out, tau.value
 
 
 def step_sizes(N1, N2, k, policy=STEP_PAPER):

@@ -485,6 +485,7 @@ const char *s3ttv_strerror(int status) {
     case S3TTV_ENUMERIC: return "NaN or Inf in the iterates";
     case S3TTV_EUNSUPPORTED: return "not supported by this build";
     case S3TTV_ESTATE: return "no problem set up";
+    case S3TTV_ETOOBIG: return "input larger than the allocation-free entry point takes";
     default: return "unknown status";
   }
 }
