@@ -27,7 +27,9 @@
 //     its direction; no rotation matrix is accumulated.  Row pairs sit in lane
 //     pairs (each lane holds half of both rows) and move between lanes in the
 //     odd-even order, so every pair of rows meets once per sweep.
-//  4. Warp 0 forms M = I - sum_x w_x u_x u_x^T (stored by columns, in halves).
+//  4. All warps form M = I - sum_x w_x u_x u_x^T (each warp a share of the
+//     eigen-rows, partial sums reduced in shared memory; stored by columns, in
+//     two halves).
 //  5. Every thread applies M to one float4 column chunk for half of the rows,
 //     stores Y_l and adds P_l^T Y_l into Z with float4 atomics.
 //
@@ -78,9 +80,17 @@ __host__ __device__ constexpr int gm_floats() {
 }
 
 template <int K>
+__host__ __device__ constexpr int ut_floats() {
+  using S = Shape<K>;
+  return (S::NPOS * S::GS + 3) & ~3;
+}
+
+// partial Gram tiles, or the eigen-rows followed by the per-warp partial sums of M
+template <int K>
 __host__ __device__ constexpr int scr_floats() {
   using S = Shape<K>;
-  return kNW * S::NT * S::TS > S::NPOS * S::GS ? kNW * S::NT * S::TS : S::NPOS * S::GS;
+  return kNW * S::NT * S::TS > ut_floats<K>() + kNW * S::n * S::n ? kNW * S::NT * S::TS
+                                                                   : ut_floats<K>() + kNW * S::n * S::n;
 }
 
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
@@ -166,49 +176,55 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Gm, 
   const float floor2 = 1e-12f * fro;
   const float tol2 = a.tol * a.tol;
   bool rotated = false;
-  // One step: the pair (A, B) meets if `meets`; it is rotated to orthogonality
-  // when needed, then the rows trade places.  A pair that does not meet keeps
-  // its places.  When no pair of the warp needs a rotation the trade is a plain
-  // register exchange.
-  auto step = [&](bool meets) {
-    float apq = 0.f;
+  // One step.  The rows are rotated in place, A' = cA - sB, B' = sA + cB; read
+  // with the positions of the odd-even ordering, A' now sits at B's position and
+  // B' at A's (the pair traded places), so the movement below needs no copies.
+  // The pair that does not meet on odd steps keeps its places, which in these
+  // terms is the quarter turn (c, s) = (0, 1): its registers swap (one sign flips,
+  // which changes nothing the solver uses).  When no pair of the warp needs a
+  // rotation, meeting pairs are left as they are and only that swap remains.
+  auto step = [&](bool meets, bool odd) {
+    float p0 = 0.f, p1 = 0.f;
 #pragma unroll
-    for (int e = 0; e < H; ++e) apq = fmaf(A[e], B[e], apq);
+    for (int e = 0; e < H; e += 2) {
+      p0 = fmaf(A[e], B[e], p0);
+      if (e + 1 < H) p1 = fmaf(A[e + 1], B[e + 1], p1);
+    }
+    float apq = p0 + p1;
     apq += __shfl_xor_sync(kFull, apq, 1);
     const bool need = meets && fminf(nA, nB) > floor2 && apq * apq > tol2 * nA * nB;
+    const bool quarter = act && !meets;  // the odd step's idle pair
     if (__any_sync(kFull, need)) {
-      float c = 0.f, sn = 1.f, dn = 0.f;  // not meeting: keep places (B's sign flips)
-      if (meets) {
-        c = 1.f;
-        sn = 0.f;
-        if (need) {
-          const float zeta = __fdividef(nB - nA, 2.f * apq);
-          const float tt = copysignf(__fdividef(1.f, fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f))), zeta);
-          c = rsqrtf(fmaf(tt, tt, 1.f));
-          sn = c * tt;
-          dn = tt * apq;
-          rotated = true;
-        }
+      float c = quarter ? 0.f : 1.f, sn = quarter ? 1.f : 0.f, dn = 0.f;
+      if (need) {
+        const float zeta = __fdividef(nB - nA, 2.f * apq);
+        const float az = fabsf(zeta);
+        const float z2 = fmaf(zeta, zeta, 1.f);
+        const float tt = az > 1e15f ? __fdividef(0.5f, zeta) : copysignf(__fdividef(1.f, az + z2 * rsqrtf(z2)), zeta);
+        c = rsqrtf(fmaf(tt, tt, 1.f));
+        sn = c * tt;
+        dn = tt * apq;
+        rotated = true;
       }
 #pragma unroll
       for (int e = 0; e < H; ++e) {
         const float x = A[e], y = B[e];
-        A[e] = fmaf(sn, x, c * y);   // rotated B row, now at A's position
-        B[e] = fmaf(c, x, -sn * y);  // rotated A row, now at B's position
+        A[e] = fmaf(c, x, -sn * y);
+        B[e] = fmaf(sn, x, c * y);
       }
       const float oA = nA;
-      nA = meets ? nB + dn : nA;
-      nB = meets ? oA - dn : nB;
-    } else {
+      nA = quarter ? nB : nA - dn;
+      nB = quarter ? oA : nB + dn;
+    } else if (odd) {
 #pragma unroll
       for (int e = 0; e < H; ++e) {
         const float x = A[e], y = B[e];
-        A[e] = meets ? y : x;
-        B[e] = meets ? x : y;
+        A[e] = quarter ? y : x;
+        B[e] = quarter ? x : y;
       }
       const float oA = nA;
-      nA = meets ? nB : nA;
-      nB = meets ? oA : nB;
+      nA = quarter ? nB : nA;
+      nB = quarter ? oA : nB;
     }
   };
   bool converged = false;
@@ -218,29 +234,17 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Gm, 
     if (sw) refresh();
 #pragma unroll 1
     for (int sp = 0; sp < NPOS / 2; ++sp) {
-      step(act);
-      if constexpr (NP > 1) {  // even -> odd: keep position 2i+1, take 2i+2 from the right
+      step(act, false);
+      if constexpr (NP > 1) {  // to the odd positions: B takes the right neighbour's B
 #pragma unroll
-        for (int e = 0; e < H; ++e) {
-          const float recv = __shfl_sync(kFull, A[e], src_r);
-          A[e] = B[e];
-          B[e] = recv;
-        }
-        const float rn = __shfl_sync(kFull, nA, src_r);
-        nA = nB;
-        nB = rn;
+        for (int e = 0; e < H; ++e) B[e] = __shfl_sync(kFull, B[e], src_r);
+        nB = __shfl_sync(kFull, nB, src_r);
       }
-      step(act && pi != NP - 1);
-      if constexpr (NP > 1) {  // odd -> even: keep position 2i+1, take 2i from the left
+      step(act && pi != NP - 1, true);
+      if constexpr (NP > 1) {  // back to the even positions: A takes the left neighbour's A
 #pragma unroll
-        for (int e = 0; e < H; ++e) {
-          const float recv = __shfl_sync(kFull, B[e], src_l);
-          B[e] = A[e];
-          A[e] = recv;
-        }
-        const float ln = __shfl_sync(kFull, nB, src_l);
-        nB = nA;
-        nA = ln;
+        for (int e = 0; e < H; ++e) A[e] = __shfl_sync(kFull, A[e], src_l);
+        nA = __shfl_sync(kFull, nA, src_l);
       }
     }
     ++sweeps;
@@ -333,23 +337,43 @@ __global__ void __launch_bounds__(kNW * 32, 5) block_dual_kernel(BlockDualArgs a
     }
     cp_async_wait_all();
     __syncthreads();
-    for (int idx = tid; idx < n * W4; idx += NTH) {
-      const int r = idx / W4, c4 = idx - r * W4;
-      const int ra = r / K, rc = r - ra * K;
-      int i = p + ra;
-      if (i >= dm.N1) i -= dm.N1;
-      int j = q + rc;
-      if (j >= dm.N2) j -= dm.N2;
-      const bool hz = c4 >= C4;
-      const float *F = (hz ? a.Fh : a.Fv) + ((size_t)i * dm.N2 + j) * N3p + ((hz ? c4 - C4 : c4) << 2);
-      const float4 x = __ldg(reinterpret_cast<const float4 *>(F));
-      float *dst = Yp + (size_t)r * RS + (c4 << 2);
-      float4 y = lds4(dst);
-      y.x = fmaf(gY, x.x, y.x);
-      y.y = fmaf(gY, x.y, y.y);
-      y.z = fmaf(gY, x.z, y.z);
-      y.w = fmaf(gY, x.w, y.w);
-      sts4(dst, y);
+    {
+      // four chunks per thread in flight: (r, c4) of this thread's items, advanced by NTH
+      int r0 = 0, c0 = tid;
+      while (c0 >= W4) { c0 -= W4; ++r0; }
+      while (r0 < n) {
+        int rr[4], cc[4];
+        float4 xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          rr[u] = r0;
+          cc[u] = c0;
+          if (r0 < n) {
+            const int ra = r0 / K, rc = r0 - ra * K;
+            int i = p + ra;
+            if (i >= dm.N1) i -= dm.N1;
+            int j = q + rc;
+            if (j >= dm.N2) j -= dm.N2;
+            const bool hz = c0 >= C4;
+            const float *F = (hz ? a.Fh : a.Fv) + ((size_t)i * dm.N2 + j) * N3p + ((hz ? c0 - C4 : c0) << 2);
+            xv[u] = __ldg(reinterpret_cast<const float4 *>(F));
+          }
+          c0 += NTH;
+          while (c0 >= W4) { c0 -= W4; ++r0; }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (rr[u] < n) {
+            float *dst = Yp + (size_t)rr[u] * RS + (cc[u] << 2);
+            float4 y = lds4(dst);
+            y.x = fmaf(gY, xv[u].x, y.x);
+            y.y = fmaf(gY, xv[u].y, y.y);
+            y.z = fmaf(gY, xv[u].z, y.z);
+            y.w = fmaf(gY, xv[u].w, y.w);
+            sts4(dst, y);
+          }
+        }
+      }
     }
     __syncthreads();
 
@@ -405,7 +429,7 @@ __global__ void __launch_bounds__(kNW * 32, 5) block_dual_kernel(BlockDualArgs a
     }
     __syncthreads();
 
-    // ---- 3-4. eigen-solve and M (warp 0) ----
+    // ---- 3. eigen-solve (warp 0) ----
     if (warp == 0) {
       bool ok;
       const int sweeps = eigen_rows<K>(a, l, Gm, Scr, &ok);
@@ -413,17 +437,21 @@ __global__ void __launch_bounds__(kNW * 32, 5) block_dual_kernel(BlockDualArgs a
         if (!ok) atomicAdd(&a.sc->jacobi_fail, 1u);
         s_sweeps += (unsigned)sweeps;
       }
-      __syncwarp();
-      // M = I - Ut^T Ut; column s at Gm + s*MS, rows [0, RH) then [RH, n) from MH
-      float macc[K][K];
-      const int R = lane / K, Sx = lane - R * K;
-#pragma unroll
-      for (int x = 0; x < K; ++x)
-#pragma unroll
-        for (int y = 0; y < K; ++y) macc[x][y] = 0.f;
+    }
+    __syncthreads();
+
+    // ---- 4. M = I - Ut^T Ut: each warp sums a share of the eigen-rows ----
+    {
+      float *Part = Scr + ut_floats<K>();  // [kNW][n][n] partial sums
       if (lane < n) {
-#pragma unroll 2
-        for (int xr = 0; xr < S::NPOS; ++xr) {
+        const int R = lane / K, Sx = lane - R * K;
+        const int x0 = (S::NPOS * warp) / kNW, x1 = (S::NPOS * (warp + 1)) / kNW;
+        float macc[K][K];
+#pragma unroll
+        for (int x = 0; x < K; ++x)
+#pragma unroll
+          for (int y = 0; y < K; ++y) macc[x][y] = 0.f;
+        for (int xr = x0; xr < x1; ++xr) {
           float ua[K], ub[K];
 #pragma unroll
           for (int x = 0; x < K; ++x) ua[x] = Scr[xr * GS + R * K + x];
@@ -434,19 +462,25 @@ __global__ void __launch_bounds__(kNW * 32, 5) block_dual_kernel(BlockDualArgs a
 #pragma unroll
             for (int y = 0; y < K; ++y) macc[x][y] = fmaf(ua[x], ub[y], macc[x][y]);
         }
-      }
-      __syncwarp();  // G (in Gm) no longer read by anyone
-      for (int e = lane; e < n * MS; e += 32) Gm[e] = 0.f;
-      __syncwarp();
-      if (lane < n) {
+        float *pw = Part + (size_t)warp * n * n;
 #pragma unroll
         for (int x = 0; x < K; ++x)
 #pragma unroll
-          for (int y = 0; y < K; ++y) {
-            const int r = R * K + x, s = Sx * K + y;
-            const int slot = r < RH ? r : MH + (r - RH);
-            Gm[s * MS + slot] = (r == s ? 1.f : 0.f) - macc[x][y];
-          }
+          for (int y = 0; y < K; ++y) pw[(R * K + x) * n + Sx * K + y] = macc[x][y];
+      }
+      __syncthreads();
+      // column s of M at Gm + s*MS: rows [0, RH) from slot 0, rows [RH, n) from slot MH
+      for (int e = tid; e < n * MS; e += NTH) {
+        const int sc = e / MS, w = e - sc * MS;
+        const int r = w < RH ? w : (w >= MH && w - MH < n - RH ? RH + (w - MH) : -1);
+        float m = 0.f;
+        if (r >= 0) {
+          float acc = 0.f;
+#pragma unroll
+          for (int ww = 0; ww < kNW; ++ww) acc += Part[((size_t)ww * n + r) * n + sc];
+          m = (r == sc ? 1.f : 0.f) - acc;
+        }
+        Gm[e] = m;
       }
     }
     __syncthreads();
