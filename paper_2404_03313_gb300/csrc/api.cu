@@ -209,8 +209,8 @@ Dims make_dims(int N1, int N2, int N3) {
   return dm;
 }
 
-// Block-dual launch shape: one CTA per block, a persistent grid of as many CTAs
-// as fit on the device at once.
+// Block-dual launch shape: one CTA per group of block_dual_group() blocks, a
+// persistent grid of as many CTAs as fit on the device at once.
 int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, int *rs, size_t *smem, int *grid) {
   *rs = block_dual_row_stride(dm.N3p);
   *smem = block_dual_smem_bytes(k, *rs);
@@ -227,7 +227,8 @@ int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, int *rs, size_t *sme
   if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
   if (per_sm < 1) per_sm = 1;
   long long g = (long long)ctx->num_sms * per_sm;
-  if (g > dm.P) g = dm.P;
+  const long long groups = (dm.P + block_dual_group() - 1) / block_dual_group();
+  if (g > groups) g = groups;
   *grid = (int)g;
   return S3TTV_OK;
 }

@@ -13,25 +13,32 @@
 // k^2 x 2N3 block.  The kernel then scatters Z += P_l^T Y_l, the term step 2 of
 // the next pass needs.
 //
-// Work decomposition: one CTA of kNW warps owns one block at a time.
-//  1. The block's Y rows arrive in shared memory by cp.async; D D_s ubar
-//     (precomputed per pass as the cubes Fv, Fh) is added with weight gamma_Y.
-//     Rows are padded so the row stride is 4 mod 32 words and the float4 reads
-//     of the Gram tiles do not conflict.
-//  2. G = Y'Y'^T: only tiles reaching the upper triangle are formed (TR x K
-//     register tiles), the 2*N3 columns split across the warps, partial tiles
-//     summed in shared memory.
-//  3. Warp 0 solves the eigenproblem by one-sided (Hestenes) Jacobi on the rows
-//     of G: rotating pairs of rows until all rows are mutually orthogonal leaves
-//     row x = lam_x u_x^T, so the eigenvalue is the row norm and the eigenvector
-//     its direction; no rotation matrix is accumulated.  Row pairs sit in lane
-//     pairs (each lane holds half of both rows) and move between lanes in the
-//     odd-even order, so every pair of rows meets once per sweep.
-//  4. All warps form M = I - sum_x w_x u_x u_x^T (each warp a share of the
-//     eigen-rows, partial sums reduced in shared memory; stored by columns, in
-//     two halves).
-//  5. Every thread applies M to one float4 column chunk for half of the rows,
-//     stores Y_l and adds P_l^T Y_l into Z with float4 atomics.
+// Work decomposition: one CTA of kNW warps owns a group of kNW consecutive
+// blocks at a time (a persistent grid strides over the groups).
+//  1. For each block of the group in turn, its Y rows arrive in shared memory by
+//     cp.async (the next block's rows are prefetched into L2 meanwhile) and
+//     D D_s ubar (precomputed per pass as the cubes Fv, Fh) is added with weight
+//     gamma_Y.  Rows are padded so the row stride is 4 mod 32 words and the
+//     float4 reads of the Gram tiles do not conflict.
+//  2. G = Y'Y'^T of that block: only tiles reaching the upper triangle are
+//     formed (TR x K register tiles), the 2*N3 columns split across the warps,
+//     partial tiles summed into the block's own G slot.
+//  3. Warp w solves the eigenproblem of block w of the group by one-sided
+//     (Hestenes) Jacobi on the rows of G: rotating pairs of rows until all rows
+//     are mutually orthogonal leaves row x = lam_x u_x^T, so the eigenvalue is
+//     the row norm and the eigenvector its direction; no rotation matrix is
+//     accumulated.  Row pairs sit in lane pairs (each lane holds half of both
+//     rows) and move between lanes in the odd-even order, so every pair of rows
+//     meets once per sweep.  The kNW solves run side by side: one solve is a
+//     chain of dependent shuffles and rotations, so an SM needs many of them in
+//     flight to keep busy.
+//  4. Warp w forms M = I - sum_x w_x u_x u_x^T of its block over that block's G
+//     (stored by columns, in two halves).
+//  5. For each block, Y' returns to shared memory (step 1 wrote it over Y_l in
+//     global memory, where it stays in L2), every thread applies M to one float4
+//     column chunk for half of the rows, in place; then the block's rows are
+//     stored and added into Z (P_l^T Y_l) with float4 atomics.  Only one Y'
+//     buffer is kept in shared memory, so four CTAs fit on an SM.
 //
 // Warm start: the rows of a block's eigenbasis change little from one pass of
 // Alg. 1 to the next, so each block keeps its normalized converged rows W (one
@@ -76,7 +83,7 @@ struct Shape {
 template <int K>
 __host__ __device__ constexpr int gm_floats() {
   using S = Shape<K>;
-  return S::n * S::MS > S::n * S::GS ? S::n * S::MS : S::n * S::GS;
+  return ((S::n * S::MS > S::n * S::GS ? S::n * S::MS : S::n * S::GS) + 3) & ~3;
 }
 
 template <int K>
@@ -85,12 +92,11 @@ __host__ __device__ constexpr int ut_floats() {
   return (S::NPOS * S::GS + 3) & ~3;
 }
 
-// partial Gram tiles, or the eigen-rows followed by the per-warp partial sums of M
+// partial Gram tiles of the kNW warps
 template <int K>
-__host__ __device__ constexpr int scr_floats() {
+__host__ __device__ constexpr int tiles_floats() {
   using S = Shape<K>;
-  return kNW * S::NT * S::TS > ut_floats<K>() + kNW * S::n * S::n ? kNW * S::NT * S::TS
-                                                                   : ut_floats<K>() + kNW * S::n * S::n;
+  return (kNW * S::NT * S::TS + 3) & ~3;
 }
 
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
@@ -106,7 +112,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-// Warp 0: one-sided Jacobi on the rows of G (or of W G), then the scaled
+// One warp: one-sided Jacobi on the rows of G (or of W G), then the scaled
 // eigen-rows into Ut and the warm rows into W.  Returns the sweeps used.
 template <int K>
 __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Gm, float *Ut, bool *ok) {
@@ -294,24 +300,95 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Gm, 
   return sweeps;
 }
 
+// Warp w: M = I - Ut^T Ut of its own block, written over that block's G by
+// columns, rows [0, RH) from slot 0 and rows [RH, n) from slot MH.
 template <int K>
-__global__ void __launch_bounds__(kNW * 32, 5) block_dual_kernel(BlockDualArgs a) {
+__device__ void form_M(float *Gm, const float *Ut) {
+  using S = Shape<K>;
+  constexpr int n = S::n, GS = S::GS, RH = S::RH, MH = S::MH, MS = S::MS;
+  const int lane = threadIdx.x & 31;
+  const int R = lane / K, Sx = lane - R * K;
+  float macc[K][K];
+#pragma unroll
+  for (int x = 0; x < K; ++x)
+#pragma unroll
+    for (int y = 0; y < K; ++y) macc[x][y] = 0.f;
+  if (lane < n) {
+#pragma unroll 2
+    for (int xr = 0; xr < S::NPOS; ++xr) {
+      float ua[K], ub[K];
+#pragma unroll
+      for (int x = 0; x < K; ++x) ua[x] = Ut[xr * GS + R * K + x];
+#pragma unroll
+      for (int y = 0; y < K; ++y) ub[y] = Ut[xr * GS + Sx * K + y];
+#pragma unroll
+      for (int x = 0; x < K; ++x)
+#pragma unroll
+        for (int y = 0; y < K; ++y) macc[x][y] = fmaf(ua[x], ub[y], macc[x][y]);
+    }
+  }
+  __syncwarp();  // G no longer read
+  for (int e = lane; e < n * MS; e += 32) Gm[e] = 0.f;
+  __syncwarp();
+  if (lane < n) {
+#pragma unroll
+    for (int x = 0; x < K; ++x)
+#pragma unroll
+      for (int y = 0; y < K; ++y) {
+        const int r = R * K + x, c = Sx * K + y;
+        const int slot = r < RH ? r : MH + (r - RH);
+        Gm[c * MS + slot] = (r == c ? 1.f : 0.f) - macc[x][y];
+      }
+  }
+}
+
+// Shared-memory copy of the n rows of Y_l (row stride RS), one 16-byte chunk per
+// thread at a time; completes at cp_async_wait_all.
+template <int K>
+__device__ __forceinline__ void load_rows(float *Yp, const float *Yl, int RS, int N3p, int W4) {
+  constexpr int n = K * K;
+  int r = 0, c4 = threadIdx.x;
+  while (c4 >= W4) { c4 -= W4; ++r; }
+  while (r < n) {
+    cp_async16(Yp + (size_t)r * RS + (c4 << 2), Yl + (size_t)r * 2 * N3p + (c4 << 2));
+    c4 += kNW * 32;
+    while (c4 >= W4) { c4 -= W4; ++r; }
+  }
+}
+
+// Start moving the n rows of Y_l (contiguous) into L2 ahead of their load.
+template <int K>
+__device__ __forceinline__ void prefetch_rows(const float *Yl, int N3p) {
+  constexpr int n = K * K;
+  const int lane = threadIdx.x & 31;
+  for (int r = lane; r < n; r += 32)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(Yl + (size_t)r * 2 * N3p),
+                 "r"((unsigned)(2 * N3p * sizeof(float)))
+                 : "memory");
+}
+
+template <int K>
+__global__ void __launch_bounds__(kNW * 32, 4) block_dual_kernel(BlockDualArgs a) {
   using S = Shape<K>;
   constexpr int n = S::n, GS = S::GS, TR = S::TR, NT = S::NT, TS = S::TS, RH = S::RH, MH = S::MH,
                 MS = S::MS;
   constexpr int NTH = kNW * 32;
+  constexpr int NF = 6;  // F loads in flight per thread
   extern __shared__ __align__(16) float smem[];
   __shared__ unsigned s_sweeps;
   __shared__ int s_tile_r0[32], s_tile_c0[32];
+  __shared__ long long s_off[kNW][n];  // element offset of pixel P_l row r in a cube
   if (a.sc->done) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int RS = a.rs;
-  float *Yp = smem;                     // Y' [n][RS]
-  float *Gm = Yp + (size_t)n * RS;      // G [n][GS], then M by columns [n][MS]
-  float *Scr = Gm + gm_floats<K>();     // partial Gram tiles, then the eigen-rows
+  float *Yp = smem;                           // Y' (then Y) of one block [n][RS]
+  float *Gall = Yp + (size_t)n * RS;          // kNW x (G, then M)
+  float *Uall = Gall + kNW * gm_floats<K>();  // kNW x eigen-rows
+  float *Tiles = Uall + kNW * ut_floats<K>(); // partial Gram tiles
   const Dims dm = a.dm;
   const int N3p = dm.N3p, C4 = N3p >> 2, W4 = 2 * C4;
   const long long L = dm.P;
+  const long long groups = (L + kNW - 1) / kNW;
   const float gY = a.gY;
   if (tid == 0) {
     s_sweeps = 0u;
@@ -326,208 +403,198 @@ __global__ void __launch_bounds__(kNW * 32, 5) block_dual_kernel(BlockDualArgs a
   }
   __syncthreads();
 
-  for (long long l = blockIdx.x; l < L; l += gridDim.x) {
-    const int p = (int)(l / dm.N2), q = (int)(l - (long long)p * dm.N2);
-    float *Yl = a.Y + (size_t)l * n * 2 * N3p;
+  for (long long grp = blockIdx.x; grp < groups; grp += gridDim.x) {
+    const long long l0 = grp * kNW;
+    const int nb = (int)(L - l0 < kNW ? L - l0 : kNW);  // blocks in this group
 
-    // ---- 1. Y' = Y + gamma_Y X,  X = P_l D D_s ubar (eq. rewrite_Lu) ----
-    for (int idx = tid; idx < n * W4; idx += NTH) {
-      const int r = idx / W4, c4 = idx - r * W4;
-      cp_async16(Yp + (size_t)r * RS + (c4 << 2), Yl + (size_t)r * 2 * N3p + (c4 << 2));
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    {
-      // four chunks per thread in flight: (r, c4) of this thread's items, advanced by NTH
-      int r0 = 0, c0 = tid;
-      while (c0 >= W4) { c0 -= W4; ++r0; }
-      while (r0 < n) {
-        int rr[4], cc[4];
-        float4 xv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          rr[u] = r0;
-          cc[u] = c0;
-          if (r0 < n) {
-            const int ra = r0 / K, rc = r0 - ra * K;
-            int i = p + ra;
-            if (i >= dm.N1) i -= dm.N1;
-            int j = q + rc;
-            if (j >= dm.N2) j -= dm.N2;
-            const bool hz = c0 >= C4;
-            const float *F = (hz ? a.Fh : a.Fv) + ((size_t)i * dm.N2 + j) * N3p + ((hz ? c0 - C4 : c0) << 2);
-            xv[u] = __ldg(reinterpret_cast<const float4 *>(F));
-          }
-          c0 += NTH;
-          while (c0 >= W4) { c0 -= W4; ++r0; }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (rr[u] < n) {
-            float *dst = Yp + (size_t)rr[u] * RS + (cc[u] << 2);
-            float4 y = lds4(dst);
-            y.x = fmaf(gY, xv[u].x, y.x);
-            y.y = fmaf(gY, xv[u].y, y.y);
-            y.z = fmaf(gY, xv[u].z, y.z);
-            y.w = fmaf(gY, xv[u].w, y.w);
-            sts4(dst, y);
-          }
-        }
+    // ---- 1-2. for each block of the group: Y' in shared memory, then its Gram ----
+    for (int b = 0; b < nb; ++b) {
+      const long long l = l0 + b;
+      float *Yl = a.Y + (size_t)l * n * 2 * N3p;
+      load_rows<K>(Yp, Yl, RS, N3p, W4);
+      if (warp == 1 && b + 1 < nb) prefetch_rows<K>(Yl + (size_t)n * 2 * N3p, N3p);
+      if (tid < n) {
+        const int p = (int)(l / dm.N2), q = (int)(l - (long long)p * dm.N2);
+        const int ra = tid / K, rc = tid - ra * K;
+        int i = p + ra;
+        if (i >= dm.N1) i -= dm.N1;
+        int j = q + rc;
+        if (j >= dm.N2) j -= dm.N2;
+        s_off[b][tid] = ((long long)i * dm.N2 + j) * N3p;
       }
-    }
-    __syncthreads();
-
-    // ---- 2. G = Y' Y'^T: tiles reaching the upper triangle, columns split over warps ----
-    if (lane < NT) {
-      const int r0 = s_tile_r0[lane], c0 = s_tile_c0[lane];
-      float acc[TR][K];
-#pragma unroll
-      for (int x = 0; x < TR; ++x)
-#pragma unroll
-        for (int y = 0; y < K; ++y) acc[x][y] = 0.f;
-      const float *pa = Yp + (size_t)r0 * RS;
-      const float *pb = Yp + (size_t)c0 * RS;
-      const int q0 = (W4 * warp) / kNW, q1 = (W4 * (warp + 1)) / kNW;
-#pragma unroll 2
-      for (int qq = q0; qq < q1; ++qq) {
-        const int c = qq << 2;
-        float4 va[TR], vb[K];
-#pragma unroll
-        for (int x = 0; x < TR; ++x)
-          va[x] = (r0 + x < n) ? lds4(pa + (size_t)x * RS + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int y = 0; y < K; ++y) vb[y] = lds4(pb + (size_t)y * RS + c);
-#pragma unroll
-        for (int x = 0; x < TR; ++x)
-#pragma unroll
-          for (int y = 0; y < K; ++y) {
-            float t = acc[x][y];
-            t = fmaf(va[x].x, vb[y].x, t);
-            t = fmaf(va[x].y, vb[y].y, t);
-            t = fmaf(va[x].z, vb[y].z, t);
-            t = fmaf(va[x].w, vb[y].w, t);
-            acc[x][y] = t;
-          }
-      }
-      float *pt = Scr + ((size_t)warp * NT + lane) * TS;
-#pragma unroll
-      for (int x = 0; x < TR; ++x)
-#pragma unroll
-        for (int y = 0; y < K; ++y) pt[x * K + y] = acc[x][y];
-    }
-    __syncthreads();
-    for (int e = tid; e < NT * TS; e += NTH) {
-      const int tl = e / TS, w = e - tl * TS, x = w / K, y = w - x * K;
-      const int r = s_tile_r0[tl] + x, s = s_tile_c0[tl] + y;
-      if (r < n) {
-        float g = 0.f;
-#pragma unroll
-        for (int ww = 0; ww < kNW; ++ww) g += Scr[((size_t)ww * NT + tl) * TS + w];
-        Gm[r * GS + s] = g;
-        Gm[s * GS + r] = g;
-      }
-    }
-    __syncthreads();
-
-    // ---- 3. eigen-solve (warp 0) ----
-    if (warp == 0) {
-      bool ok;
-      const int sweeps = eigen_rows<K>(a, l, Gm, Scr, &ok);
-      if (lane == 0) {
-        if (!ok) atomicAdd(&a.sc->jacobi_fail, 1u);
-        s_sweeps += (unsigned)sweeps;
-      }
-    }
-    __syncthreads();
-
-    // ---- 4. M = I - Ut^T Ut: each warp sums a share of the eigen-rows ----
-    {
-      float *Part = Scr + ut_floats<K>();  // [kNW][n][n] partial sums
-      if (lane < n) {
-        const int R = lane / K, Sx = lane - R * K;
-        const int x0 = (S::NPOS * warp) / kNW, x1 = (S::NPOS * (warp + 1)) / kNW;
-        float macc[K][K];
-#pragma unroll
-        for (int x = 0; x < K; ++x)
-#pragma unroll
-          for (int y = 0; y < K; ++y) macc[x][y] = 0.f;
-        for (int xr = x0; xr < x1; ++xr) {
-          float ua[K], ub[K];
-#pragma unroll
-          for (int x = 0; x < K; ++x) ua[x] = Scr[xr * GS + R * K + x];
-#pragma unroll
-          for (int y = 0; y < K; ++y) ub[y] = Scr[xr * GS + Sx * K + y];
-#pragma unroll
-          for (int x = 0; x < K; ++x)
-#pragma unroll
-            for (int y = 0; y < K; ++y) macc[x][y] = fmaf(ua[x], ub[y], macc[x][y]);
-        }
-        float *pw = Part + (size_t)warp * n * n;
-#pragma unroll
-        for (int x = 0; x < K; ++x)
-#pragma unroll
-          for (int y = 0; y < K; ++y) pw[(R * K + x) * n + Sx * K + y] = macc[x][y];
-      }
+      cp_async_wait_all();
       __syncthreads();
-      // column s of M at Gm + s*MS: rows [0, RH) from slot 0, rows [RH, n) from slot MH
-      for (int e = tid; e < n * MS; e += NTH) {
-        const int sc = e / MS, w = e - sc * MS;
-        const int r = w < RH ? w : (w >= MH && w - MH < n - RH ? RH + (w - MH) : -1);
-        float m = 0.f;
-        if (r >= 0) {
-          float acc = 0.f;
+      {
+        // NF chunks per thread in flight: (r, c4) of this thread's items, advanced by NTH
+        int r0 = 0, c0 = tid;
+        while (c0 >= W4) { c0 -= W4; ++r0; }
+        while (r0 < n) {
+          int rr[NF], cc[NF];
+          float4 xv[NF];
 #pragma unroll
-          for (int ww = 0; ww < kNW; ++ww) acc += Part[((size_t)ww * n + r) * n + sc];
-          m = (r == sc ? 1.f : 0.f) - acc;
-        }
-        Gm[e] = m;
-      }
-    }
-    __syncthreads();
-
-    // ---- 5. Y = M Y', written back, and Z += P_l^T Y ----
-    for (int task = tid; task < 2 * W4; task += NTH) {
-      const int half = task / W4, c4 = task - half * W4;
-      const bool hz = c4 >= C4;
-      const int b0 = (hz ? c4 - C4 : c4) << 2;
-      float4 acc[RH];
+          for (int u = 0; u < NF; ++u) {
+            rr[u] = r0;
+            cc[u] = c0;
+            if (r0 < n) {
+              const bool hz = c0 >= C4;
+              const float *F = (hz ? a.Fh : a.Fv) + s_off[b][r0] + ((hz ? c0 - C4 : c0) << 2);
+              xv[u] = __ldg(reinterpret_cast<const float4 *>(F));
+            }
+            c0 += NTH;
+            while (c0 >= W4) { c0 -= W4; ++r0; }
+          }
 #pragma unroll
-      for (int x = 0; x < RH; ++x) acc[x] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 1
-      for (int s = 0; s < n; ++s) {
-        const float4 y = lds4(Yp + (size_t)s * RS + (c4 << 2));
-        const float *mcol = Gm + s * MS + half * MH;  // M[r][s] for this half's rows
-#pragma unroll
-        for (int x4 = 0; x4 < MH; x4 += 4) {
-          const float4 m = lds4(mcol + x4);
-          const float mm[4] = {m.x, m.y, m.z, m.w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            if (x4 + e < RH) {
-              acc[x4 + e].x = fmaf(mm[e], y.x, acc[x4 + e].x);
-              acc[x4 + e].y = fmaf(mm[e], y.y, acc[x4 + e].y);
-              acc[x4 + e].z = fmaf(mm[e], y.z, acc[x4 + e].z);
-              acc[x4 + e].w = fmaf(mm[e], y.w, acc[x4 + e].w);
+          for (int u = 0; u < NF; ++u) {
+            if (rr[u] < n) {
+              float *dst = Yp + (size_t)rr[u] * RS + (cc[u] << 2);
+              float4 y = lds4(dst);
+              y.x = fmaf(gY, xv[u].x, y.x);
+              y.y = fmaf(gY, xv[u].y, y.y);
+              y.z = fmaf(gY, xv[u].z, y.z);
+              y.w = fmaf(gY, xv[u].w, y.w);
+              sts4(dst, y);
+              // Y' replaces Y_l in global memory (kept in L2) for step 5
+              reinterpret_cast<float4 *>(Yl + (size_t)rr[u] * 2 * N3p)[cc[u]] = y;
             }
           }
         }
       }
-      float *Zo = hz ? a.Zh : a.Zv;
+      __syncthreads();
+      if (lane < NT) {  // tiles reaching the upper triangle, this warp's share of the columns
+        const int r0 = s_tile_r0[lane], c0 = s_tile_c0[lane];
+        float acc[TR][K];
 #pragma unroll
-      for (int x = 0; x < RH; ++x) {
-        const int r = half * RH + x;
+        for (int x = 0; x < TR; ++x)
+#pragma unroll
+          for (int y = 0; y < K; ++y) acc[x][y] = 0.f;
+        const float *pa = Yp + (size_t)r0 * RS;
+        const float *pb = Yp + (size_t)c0 * RS;
+        const int q0 = (W4 * warp) / kNW, q1 = (W4 * (warp + 1)) / kNW;
+#pragma unroll 2
+        for (int qq = q0; qq < q1; ++qq) {
+          const int c = qq << 2;
+          float4 va[TR], vb[K];
+#pragma unroll
+          for (int x = 0; x < TR; ++x)
+            va[x] = (r0 + x < n) ? lds4(pa + (size_t)x * RS + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int y = 0; y < K; ++y) vb[y] = lds4(pb + (size_t)y * RS + c);
+#pragma unroll
+          for (int x = 0; x < TR; ++x)
+#pragma unroll
+            for (int y = 0; y < K; ++y) {
+              float t = acc[x][y];
+              t = fmaf(va[x].x, vb[y].x, t);
+              t = fmaf(va[x].y, vb[y].y, t);
+              t = fmaf(va[x].z, vb[y].z, t);
+              t = fmaf(va[x].w, vb[y].w, t);
+              acc[x][y] = t;
+            }
+        }
+        float *pt = Tiles + ((size_t)warp * NT + lane) * TS;
+#pragma unroll
+        for (int x = 0; x < TR; ++x)
+#pragma unroll
+          for (int y = 0; y < K; ++y) pt[x * K + y] = acc[x][y];
+      }
+      __syncthreads();
+      float *Gb = Gall + b * gm_floats<K>();
+      for (int e = tid; e < NT * TS; e += NTH) {
+        const int tl = e / TS, w = e - tl * TS, x = w / K, y = w - x * K;
+        const int r = s_tile_r0[tl] + x, c = s_tile_c0[tl] + y;
         if (r < n) {
-          __stcs(reinterpret_cast<float4 *>(Yl + (size_t)r * 2 * N3p) + c4, acc[x]);
-          const int ra = r / K, rc = r - ra * K;
-          int i = p + ra;
-          if (i >= dm.N1) i -= dm.N1;
-          int j = q + rc;
-          if (j >= dm.N2) j -= dm.N2;
-          atomicAdd(reinterpret_cast<float4 *>(Zo + ((size_t)i * dm.N2 + j) * N3p + b0), acc[x]);
+          float g = 0.f;
+#pragma unroll
+          for (int ww = 0; ww < kNW; ++ww) g += Tiles[((size_t)ww * NT + tl) * TS + w];
+          Gb[r * GS + c] = g;
+          Gb[c * GS + r] = g;
         }
       }
+      __syncthreads();
+    }
+
+    // ---- 3-4. every warp: eigen-solve of one block of the group, then its M ----
+    if (warp == 0 && grp + gridDim.x < groups)  // the next group's first block
+      prefetch_rows<K>(a.Y + (size_t)(grp + gridDim.x) * kNW * n * 2 * N3p, N3p);
+    if (warp < nb) {
+      float *Gb = Gall + warp * gm_floats<K>();
+      float *Ub = Uall + warp * ut_floats<K>();
+      bool ok;
+      const int sweeps = eigen_rows<K>(a, l0 + warp, Gb, Ub, &ok);
+      if (lane == 0) {
+        if (!ok) atomicAdd(&a.sc->jacobi_fail, 1u);
+        atomicAdd(&s_sweeps, (unsigned)sweeps);
+      }
+      __syncwarp();
+      form_M<K>(Gb, Ub);
     }
     __syncthreads();
+
+    // ---- 5. for each block: Y' back into shared memory, Y_l = M Y' in place, then
+    //         Y_l stored and P_l^T Y_l added into Z, row by row ----
+    for (int b = 0; b < nb; ++b) {
+      const long long l = l0 + b;
+      float *Yl = a.Y + (size_t)l * n * 2 * N3p;
+      const float *Mg = Gall + b * gm_floats<K>();
+      load_rows<K>(Yp, Yl, RS, N3p, W4);
+      cp_async_wait_all();
+      __syncthreads();
+      // task: one float4 column chunk, half of the rows.  The two tasks of a chunk
+      // are neighbouring lanes of one warp in the same round, so a warp barrier
+      // orders every read of the chunk before it is overwritten with Y_l.
+      for (int base = 0; base < 2 * W4; base += NTH) {
+        const int task = base + tid;
+        const bool has = task < 2 * W4;
+        const int c4 = task >> 1, half = task & 1;
+        float4 acc[RH];
+#pragma unroll
+        for (int x = 0; x < RH; ++x) acc[x] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (has) {
+          const float *col = Yp + (c4 << 2);
+#pragma unroll 5
+          for (int s = 0; s < n; ++s) {
+            const float4 y = lds4(col + (size_t)s * RS);
+            const float *mcol = Mg + s * MS + half * MH;  // M[r][s] for this half's rows
+#pragma unroll
+            for (int x4 = 0; x4 < MH; x4 += 4) {
+              const float4 m = lds4(mcol + x4);
+              const float mm[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                if (x4 + e < RH) {
+                  acc[x4 + e].x = fmaf(mm[e], y.x, acc[x4 + e].x);
+                  acc[x4 + e].y = fmaf(mm[e], y.y, acc[x4 + e].y);
+                  acc[x4 + e].z = fmaf(mm[e], y.z, acc[x4 + e].z);
+                  acc[x4 + e].w = fmaf(mm[e], y.w, acc[x4 + e].w);
+                }
+              }
+            }
+          }
+        }
+        __syncwarp();
+        if (has) {
+          float *dst = Yp + (size_t)(half * RH) * RS + (c4 << 2);
+#pragma unroll
+          for (int x = 0; x < RH; ++x)
+            if (half * RH + x < n) sts4(dst + (size_t)x * RS, acc[x]);
+        }
+      }
+      __syncthreads();  // Y_l complete in shared memory
+      {
+        int r = 0, c4 = tid;
+        while (c4 >= W4) { c4 -= W4; ++r; }
+        while (r < n) {
+          const float4 y = lds4(Yp + (size_t)r * RS + (c4 << 2));
+          __stcs(reinterpret_cast<float4 *>(Yl + (size_t)r * 2 * N3p) + c4, y);
+          const bool hz = c4 >= C4;
+          float *Zo = (hz ? a.Zh : a.Zv) + s_off[b][r] + ((hz ? c4 - C4 : c4) << 2);
+          atomicAdd(reinterpret_cast<float4 *>(Zo), y);
+          c4 += NTH;
+          while (c4 >= W4) { c4 -= W4; ++r; }
+        }
+      }
+      __syncthreads();  // the shared buffer is free for the next block
+    }
   }
   if (tid == 0 && s_sweeps) atomicAdd(&a.sc->jacobi_sweeps, (unsigned long long)s_sweeps);
 }
@@ -545,7 +612,7 @@ cudaError_t prepare_k(size_t smem) {
 
 template <int K>
 size_t smem_k(int rs) {
-  return sizeof(float) * ((size_t)Shape<K>::n * rs + gm_floats<K>() + scr_floats<K>());
+  return sizeof(float) * ((size_t)Shape<K>::n * rs + kNW * gm_floats<K>() + kNW * ut_floats<K>() + tiles_floats<K>());
 }
 
 }  // namespace
@@ -562,6 +629,8 @@ int block_dual_row_stride(int N3p) {
 }
 
 int block_dual_threads() { return kNW * 32; }
+
+int block_dual_group() { return kNW; }
 
 size_t block_dual_smem_bytes(int k, int rs) {
   switch (k) {

@@ -135,6 +135,8 @@ long long block_dual_w_stride(int k);
 cudaError_t launch_block_dual(const BlockDualArgs &a, int k, int grid, size_t smem, cudaStream_t st);
 size_t block_dual_smem_bytes(int k, int rs);
 int block_dual_threads();
+// blocks one CTA of the block-dual kernel takes at a time
+int block_dual_group();
 int block_dual_row_stride(int N3p);
 cudaError_t block_dual_prepare(int k, size_t smem_bytes);
 cudaError_t block_dual_occupancy(int k, size_t smem_bytes, int *ctas_per_sm);
