@@ -210,26 +210,40 @@ Dims make_dims(int N1, int N2, int N3) {
 }
 
 // Block-dual launch shape: one CTA per group of block_dual_group() blocks, a
-// persistent grid of as many CTAs as fit on the device at once.
-int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, int *rs, size_t *smem, int *grid) {
-  *rs = block_dual_row_stride(dm.N3p);
-  *smem = block_dual_smem_bytes(k, *rs);
+// persistent grid of as many CTAs as fit on the device at once.  The kernel
+// variant sized for five CTAs per SM is taken when five fit by shared memory.
+struct BdShape {
+  int rs = 0;       // shared-memory row stride (floats)
+  size_t smem = 0;  // dynamic shared memory per CTA
+  int grid = 0;
+  int minb = 4;     // kernel variant
+};
+
+int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, BdShape *sh) {
+  if (dm.P > 2147483647LL)  // the kernel indexes pixels with 32-bit integers
+    return fail(ctx, S3TTV_EUNSUPPORTED, "N1 * N2 = %lld pixels: this build supports fewer than 2^31", dm.P);
+  sh->rs = block_dual_row_stride(dm.N3p);
+  sh->smem = block_dual_smem_bytes(k, sh->rs);
   int dev_max = 0;
   cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
   if (dev_max <= 0) dev_max = 227 * 1024;
-  if (*smem == 0 || *smem > (size_t)dev_max)
+  if (sh->smem == 0 || sh->smem > (size_t)dev_max)
     return fail(ctx, S3TTV_EUNSUPPORTED, "a %dx%dx%d block needs %zu bytes of shared memory (device limit %d)", k, k,
-                dm.N3, *smem, dev_max);
-  cudaError_t e = block_dual_prepare(k, *smem);
-  if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+                dm.N3, sh->smem, dev_max);
   int per_sm = 0;
-  e = block_dual_occupancy(k, *smem, &per_sm);
-  if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+  for (int minb = 5; minb >= 4; --minb) {
+    cudaError_t e = block_dual_prepare(k, minb, sh->smem);
+    if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    e = block_dual_occupancy(k, minb, sh->smem, &per_sm);
+    if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+    sh->minb = minb;
+    if (per_sm >= minb) break;
+  }
   if (per_sm < 1) per_sm = 1;
   long long g = (long long)ctx->num_sms * per_sm;
   const long long groups = (dm.P + block_dual_group() - 1) / block_dual_group();
   if (g > groups) g = groups;
-  *grid = (int)g;
+  sh->grid = (int)g;
   return S3TTV_OK;
 }
 
@@ -328,7 +342,7 @@ __global__ void set_c3_kernel(Scalars *sc, double c3) { sc->c3 = c3; }
 
 // One pass of Alg. 1, enqueued on the context stream.  `par` selects the current
 // t / Z buffers; the pass writes the other ones.
-int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, int grid_bd, int rs, size_t smem,
+int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
                  cudaEvent_t *ev) {
   const Dims &dm = ctx->dm;
   cudaStream_t st = ctx->stream;
@@ -383,14 +397,14 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, int grid_bd, int rs, size_
   ba.Zh = ctx->Zh[par ^ 1];
   ba.dm = dm;
   ba.gY = (float)ctx->gam[3];
-  ba.rs = rs;
+  ba.rs = bd.rs;
   ba.max_sweeps = ctx->jacobi_max_sweeps;
   ba.tol = ctx->jacobi_tol;
   ba.sc = ctx->sc;
   ba.W = ctx->warm_start ? ctx->W : nullptr;
   ba.w_stride = ctx->w_stride;
   ba.warm = ctx->warm_start && ctx->warm_valid;
-  CU(launch_block_dual(ba, ctx->k, grid_bd, smem, st));
+  CU(launch_block_dual(ba, ctx->k, bd.minb, bd.grid, bd.smem, st));
   if (ctx->warm_start) ctx->warm_valid = true;
   if (ev) CU(cudaEventRecord(ev[3], st));
 
@@ -611,9 +625,8 @@ int s3ttv_setup(s3ttv_ctx *ctx, const float *v, int N1, int N2, int N3, float ep
   DeviceGuard g(ctx->device);
   ctx->ready = false;
   const Dims dm = make_dims(N1, N2, N3);
-  int rs, grid;
-  size_t smem;
-  if ((rc = block_dual_shape(ctx, dm, k, &rs, &smem, &grid))) return rc;
+  BdShape bd;
+  if ((rc = block_dual_shape(ctx, dm, k, &bd))) return rc;
   if ((rc = ensure_problem_buffers(ctx, dm, k))) return rc;
   ctx->dm = dm;
   ctx->k = k;
@@ -648,9 +661,8 @@ int s3ttv_iterate(s3ttv_ctx *ctx, int n, float tol, s3ttv_info *info) {
   if (n < 1) return fail(ctx, S3TTV_EINVAL, "n = %d must be >= 1", n);
   if (!(tol >= 0.f) || !std::isfinite(tol)) return fail(ctx, S3TTV_EINVAL, "tol must be finite and >= 0");
   DeviceGuard g(ctx->device);
-  int rs, grid_bd;
-  size_t smem;
-  int rc = block_dual_shape(ctx, ctx->dm, ctx->k, &rs, &smem, &grid_bd);
+  BdShape bd;
+  int rc = block_dual_shape(ctx, ctx->dm, ctx->k, &bd);
   if (rc) return rc;
   const int grid_e = elementwise_grid(ctx, ctx->dm.Np);
   Scalars hs;
@@ -667,7 +679,7 @@ int s3ttv_iterate(s3ttv_ctx *ctx, int n, float tol, s3ttv_info *info) {
     if (ctx->profile && (rc = ensure_events(ctx, chunk))) return rc;
     for (int c = 0; c < chunk; ++c) {
       cudaEvent_t *ev = ctx->profile ? ctx->ev + (size_t)kEvPerPass * c : nullptr;
-      if ((rc = enqueue_pass(ctx, par, grid_e, grid_bd, rs, smem, ev))) return rc;
+      if ((rc = enqueue_pass(ctx, par, grid_e, bd, ev))) return rc;
       par ^= 1;
     }
     enq += chunk;
@@ -843,9 +855,9 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   if (k > kMaxK) return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: this build supports k <= %d", k, kMaxK);
   DeviceGuard g(ctx->device);
   const Dims dm = make_dims(N1, N2, N3);
-  int rs, grid, rc;
-  size_t smem;
-  if ((rc = block_dual_shape(ctx, dm, k, &rs, &smem, &grid))) return rc;
+  int rc;
+  BdShape bd;
+  if ((rc = block_dual_shape(ctx, dm, k, &bd))) return rc;
   ctx->ready = false;
   if ((rc = ensure_problem_buffers(ctx, dm, k))) return rc;
   ctx->dm = dm;
@@ -864,14 +876,14 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   ba.Zh = ctx->Zh[0];
   ba.dm = dm;
   ba.gY = gamma_Y;
-  ba.rs = rs;
+  ba.rs = bd.rs;
   ba.max_sweeps = ctx->jacobi_max_sweeps;
   ba.tol = ctx->jacobi_tol;
   ba.sc = ctx->sc;
   ba.W = nullptr;
   ba.w_stride = 0;
   ba.warm = 0;
-  CU(launch_block_dual(ba, k, grid, smem, ctx->stream));
+  CU(launch_block_dual(ba, k, bd.minb, bd.grid, bd.smem, ctx->stream));
   if ((rc = store_Y(ctx, Y))) return rc;
   if ((rc = store_cube(ctx, ctx->Zv[0], Zv, nullptr))) return rc;
   if ((rc = store_cube(ctx, ctx->Zh[0], Zh, nullptr))) return rc;

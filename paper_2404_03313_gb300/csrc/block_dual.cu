@@ -65,7 +65,7 @@ struct Shape {
   static constexpr int TR = K < 3 ? K : 3; // Gram tile rows (tile columns: K)
   static constexpr int RH = (n + 1) / 2;   // rows per thread in the apply
   static constexpr int MH = (RH + 3) & ~3; // padded half of a column of M
-  static constexpr int MS = 2 * MH;        // stride of the columns of M
+  static constexpr int MS = (MH + n - RH + 3) & ~3;  // stride of the columns of M
   // Gram tiles: row groups of TR, column groups of K, those reaching the upper triangle
   static constexpr int NRG = (n + TR - 1) / TR;
   static constexpr int count_tiles() {
@@ -80,16 +80,14 @@ struct Shape {
   static constexpr int TS = TR * K;        // entries per tile
 };
 
+// One slot per block of the group: G, then the scaled eigen-rows (NPOS rows of
+// stride GS), then M by columns.  The float4 reads of the last column's second
+// half run MH floats past n * MS (values that multiply only unused rows).
 template <int K>
 __host__ __device__ constexpr int gm_floats() {
   using S = Shape<K>;
-  return ((S::n * S::MS > S::n * S::GS ? S::n * S::MS : S::n * S::GS) + 3) & ~3;
-}
-
-template <int K>
-__host__ __device__ constexpr int ut_floats() {
-  using S = Shape<K>;
-  return (S::NPOS * S::GS + 3) & ~3;
+  constexpr int m = S::n * S::MS + S::MH, u = S::NPOS * S::GS;
+  return ((m > u ? m : u) + 3) & ~3;
 }
 
 // partial Gram tiles of the kNW warps
@@ -266,6 +264,7 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Gm, 
   const float lA = sqrtf(nA), lB = sqrtf(nB);
   const float sA = lA > 1.f ? sqrtf(1.f - rsqrtf(lA)) / lA : 0.f;
   const float sB = lB > 1.f ? sqrtf(1.f - rsqrtf(lB)) / lB : 0.f;
+  __syncwarp();  // Ut takes the place of G, which every lane has read
   if (act) {
 #pragma unroll
     for (int e = 0; e < H; ++e) {
@@ -300,10 +299,11 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Gm, 
   return sweeps;
 }
 
-// Warp w: M = I - Ut^T Ut of its own block, written over that block's G by
-// columns, rows [0, RH) from slot 0 and rows [RH, n) from slot MH.
+// Warp w: M = I - Ut^T Ut of its own block, written over Ut (in the block's
+// slot) by columns, rows [0, RH) from slot 0 and rows [RH, n) from slot MH.
 template <int K>
-__device__ void form_M(float *Gm, const float *Ut) {
+__device__ void form_M(float *Gm) {
+  const float *Ut = Gm;
   using S = Shape<K>;
   constexpr int n = S::n, GS = S::GS, RH = S::RH, MH = S::MH, MS = S::MS;
   const int lane = threadIdx.x & 31;
@@ -327,7 +327,7 @@ __device__ void form_M(float *Gm, const float *Ut) {
         for (int y = 0; y < K; ++y) macc[x][y] = fmaf(ua[x], ub[y], macc[x][y]);
     }
   }
-  __syncwarp();  // G no longer read
+  __syncwarp();  // Ut no longer read
   for (int e = lane; e < n * MS; e += 32) Gm[e] = 0.f;
   __syncwarp();
   if (lane < n) {
@@ -367,8 +367,10 @@ __device__ __forceinline__ void prefetch_rows(const float *Yl, int N3p) {
                  : "memory");
 }
 
-template <int K>
-__global__ void __launch_bounds__(kNW * 32, 4) block_dual_kernel(BlockDualArgs a) {
+// MINB: CTAs per SM the register budget is sized for (5: 96 registers a thread,
+// when five CTAs' shared memory fits on an SM; 4: 128 registers otherwise).
+template <int K, int MINB>
+__global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArgs a) {
   using S = Shape<K>;
   constexpr int n = S::n, GS = S::GS, TR = S::TR, NT = S::NT, TS = S::TS, RH = S::RH, MH = S::MH,
                 MS = S::MS;
@@ -377,14 +379,13 @@ __global__ void __launch_bounds__(kNW * 32, 4) block_dual_kernel(BlockDualArgs a
   extern __shared__ __align__(16) float smem[];
   __shared__ unsigned s_sweeps;
   __shared__ int s_tile_r0[32], s_tile_c0[32];
-  __shared__ long long s_off[kNW][n];  // element offset of pixel P_l row r in a cube
+  __shared__ int s_off[kNW][n];  // pixel (i * N2 + j) of row r of P_l
   if (a.sc->done) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int RS = a.rs;
   float *Yp = smem;                           // Y' (then Y) of one block [n][RS]
-  float *Gall = Yp + (size_t)n * RS;          // kNW x (G, then M)
-  float *Uall = Gall + kNW * gm_floats<K>();  // kNW x eigen-rows
-  float *Tiles = Uall + kNW * ut_floats<K>(); // partial Gram tiles
+  float *Gall = Yp + (size_t)n * RS;          // kNW x (G, eigen-rows, M)
+  float *Tiles = Gall + kNW * gm_floats<K>(); // partial Gram tiles
   const Dims dm = a.dm;
   const int N3p = dm.N3p, C4 = N3p >> 2, W4 = 2 * C4;
   const long long L = dm.P;
@@ -420,7 +421,7 @@ __global__ void __launch_bounds__(kNW * 32, 4) block_dual_kernel(BlockDualArgs a
         if (i >= dm.N1) i -= dm.N1;
         int j = q + rc;
         if (j >= dm.N2) j -= dm.N2;
-        s_off[b][tid] = ((long long)i * dm.N2 + j) * N3p;
+        s_off[b][tid] = i * dm.N2 + j;
       }
       cp_async_wait_all();
       __syncthreads();
@@ -437,7 +438,7 @@ __global__ void __launch_bounds__(kNW * 32, 4) block_dual_kernel(BlockDualArgs a
             cc[u] = c0;
             if (r0 < n) {
               const bool hz = c0 >= C4;
-              const float *F = (hz ? a.Fh : a.Fv) + s_off[b][r0] + ((hz ? c0 - C4 : c0) << 2);
+              const float *F = (hz ? a.Fh : a.Fv) + (size_t)s_off[b][r0] * N3p + ((hz ? c0 - C4 : c0) << 2);
               xv[u] = __ldg(reinterpret_cast<const float4 *>(F));
             }
             c0 += NTH;
@@ -518,15 +519,14 @@ __global__ void __launch_bounds__(kNW * 32, 4) block_dual_kernel(BlockDualArgs a
       prefetch_rows<K>(a.Y + (size_t)(grp + gridDim.x) * kNW * n * 2 * N3p, N3p);
     if (warp < nb) {
       float *Gb = Gall + warp * gm_floats<K>();
-      float *Ub = Uall + warp * ut_floats<K>();
       bool ok;
-      const int sweeps = eigen_rows<K>(a, l0 + warp, Gb, Ub, &ok);
+      const int sweeps = eigen_rows<K>(a, l0 + warp, Gb, Gb, &ok);
       if (lane == 0) {
         if (!ok) atomicAdd(&a.sc->jacobi_fail, 1u);
         atomicAdd(&s_sweeps, (unsigned)sweeps);
       }
       __syncwarp();
-      form_M<K>(Gb, Ub);
+      form_M<K>(Gb);
     }
     __syncthreads();
 
@@ -551,7 +551,7 @@ __global__ void __launch_bounds__(kNW * 32, 4) block_dual_kernel(BlockDualArgs a
         for (int x = 0; x < RH; ++x) acc[x] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (has) {
           const float *col = Yp + (c4 << 2);
-#pragma unroll 5
+#pragma unroll(MINB >= 5 ? 1 : 5)
           for (int s = 0; s < n; ++s) {
             const float4 y = lds4(col + (size_t)s * RS);
             const float *mcol = Mg + s * MS + half * MH;  // M[r][s] for this half's rows
@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(kNW * 32, 4) block_dual_kernel(BlockDualArgs a
           const float4 y = lds4(Yp + (size_t)r * RS + (c4 << 2));
           __stcs(reinterpret_cast<float4 *>(Yl + (size_t)r * 2 * N3p) + c4, y);
           const bool hz = c4 >= C4;
-          float *Zo = (hz ? a.Zh : a.Zv) + s_off[b][r] + ((hz ? c4 - C4 : c4) << 2);
+          float *Zo = (hz ? a.Zh : a.Zv) + (size_t)s_off[b][r] * N3p + ((hz ? c4 - C4 : c4) << 2);
           atomicAdd(reinterpret_cast<float4 *>(Zo), y);
           c4 += NTH;
           while (c4 >= W4) { c4 -= W4; ++r; }
@@ -599,20 +599,27 @@ __global__ void __launch_bounds__(kNW * 32, 4) block_dual_kernel(BlockDualArgs a
   if (tid == 0 && s_sweeps) atomicAdd(&a.sc->jacobi_sweeps, (unsigned long long)s_sweeps);
 }
 
-template <int K>
-cudaError_t launch_k(const BlockDualArgs &a, int grid, size_t smem, cudaStream_t st) {
-  block_dual_kernel<K><<<grid, kNW * 32, smem, st>>>(a);
-  return cudaGetLastError();
-}
+using KernelFn = void (*)(BlockDualArgs);
 
 template <int K>
-cudaError_t prepare_k(size_t smem) {
-  return cudaFuncSetAttribute(block_dual_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+KernelFn kernel_k(int minb) {
+  return minb >= 5 ? block_dual_kernel<K, 5> : block_dual_kernel<K, 4>;
+}
+
+KernelFn kernel_for(int k, int minb) {
+  switch (k) {
+    case 1: return kernel_k<1>(minb);
+    case 2: return kernel_k<2>(minb);
+    case 3: return kernel_k<3>(minb);
+    case 4: return kernel_k<4>(minb);
+    case 5: return kernel_k<5>(minb);
+    default: return nullptr;
+  }
 }
 
 template <int K>
 size_t smem_k(int rs) {
-  return sizeof(float) * ((size_t)Shape<K>::n * rs + kNW * gm_floats<K>() + kNW * ut_floats<K>() + tiles_floats<K>());
+  return sizeof(float) * ((size_t)Shape<K>::n * rs + kNW * gm_floats<K>() + tiles_floats<K>());
 }
 
 }  // namespace
@@ -643,37 +650,23 @@ size_t block_dual_smem_bytes(int k, int rs) {
   }
 }
 
-cudaError_t block_dual_prepare(int k, size_t smem) {
-  switch (k) {
-    case 1: return prepare_k<1>(smem);
-    case 2: return prepare_k<2>(smem);
-    case 3: return prepare_k<3>(smem);
-    case 4: return prepare_k<4>(smem);
-    case 5: return prepare_k<5>(smem);
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t block_dual_prepare(int k, int minb, size_t smem) {
+  KernelFn f = kernel_for(k, minb);
+  if (!f) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(reinterpret_cast<const void *>(f), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-cudaError_t block_dual_occupancy(int k, size_t smem, int *ctas) {
-  switch (k) {
-    case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, block_dual_kernel<1>, kNW * 32, smem);
-    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, block_dual_kernel<2>, kNW * 32, smem);
-    case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, block_dual_kernel<3>, kNW * 32, smem);
-    case 4: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, block_dual_kernel<4>, kNW * 32, smem);
-    case 5: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, block_dual_kernel<5>, kNW * 32, smem);
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t block_dual_occupancy(int k, int minb, size_t smem, int *ctas) {
+  KernelFn f = kernel_for(k, minb);
+  if (!f) return cudaErrorInvalidValue;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, reinterpret_cast<const void *>(f), kNW * 32, smem);
 }
 
-cudaError_t launch_block_dual(const BlockDualArgs &a, int k, int grid, size_t smem, cudaStream_t st) {
-  switch (k) {
-    case 1: return launch_k<1>(a, grid, smem, st);
-    case 2: return launch_k<2>(a, grid, smem, st);
-    case 3: return launch_k<3>(a, grid, smem, st);
-    case 4: return launch_k<4>(a, grid, smem, st);
-    case 5: return launch_k<5>(a, grid, smem, st);
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t launch_block_dual(const BlockDualArgs &a, int k, int minb, int grid, size_t smem, cudaStream_t st) {
+  KernelFn f = kernel_for(k, minb);
+  if (!f) return cudaErrorInvalidValue;
+  f<<<grid, kNW * 32, smem, st>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace s3ttv

@@ -132,14 +132,15 @@ struct BlockDualArgs {
 // floats per block of the warm-start rows
 long long block_dual_w_stride(int k);
 // Returns cudaErrorInvalidValue if k is not supported.
-cudaError_t launch_block_dual(const BlockDualArgs &a, int k, int grid, size_t smem, cudaStream_t st);
+// minb: 5 or 4, the kernel variant sized for that many CTAs per SM
+cudaError_t launch_block_dual(const BlockDualArgs &a, int k, int minb, int grid, size_t smem, cudaStream_t st);
 size_t block_dual_smem_bytes(int k, int rs);
 int block_dual_threads();
 // blocks one CTA of the block-dual kernel takes at a time
 int block_dual_group();
 int block_dual_row_stride(int N3p);
-cudaError_t block_dual_prepare(int k, size_t smem_bytes);
-cudaError_t block_dual_occupancy(int k, size_t smem_bytes, int *ctas_per_sm);
+cudaError_t block_dual_prepare(int k, int minb, size_t smem_bytes);
+cudaError_t block_dual_occupancy(int k, int minb, size_t smem_bytes, int *ctas_per_sm);
 
 // Layout conversion and small helpers.
 cudaError_t launch_pad_cube(const float *src, float *dst, Dims dm, float scale, cudaStream_t st);
