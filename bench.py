@@ -45,7 +45,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per voxel of one block-dual launch, from an ncu
 # capture of the kernel whose source hashes to `sha` (profiles/block_dual_k5_*.md);
 # traffic is reported only while the kernel source is unchanged.
-BLOCK_DUAL_TRAFFIC = {"sha": "eaa6a4d747bf92c3", "k": 5, "bytes_per_voxel": 915.98e6 / 2097152}
+BLOCK_DUAL_TRAFFIC = {"sha": "0c45ec1216dcfa0c", "k": 5, "bytes_per_voxel": (708.317696e6 + 715.485440e6) / 2097152}
 
 
 # ---------------------------------------------------------------------------
@@ -303,7 +303,7 @@ def run_ours(args, spec):
     peak, peak_src = measured_peaks()
     achieved = alg_bytes / bd_avg_s / 1e9 if bd_avg_s > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": block_dual_traffic(spec.k, N), "kernel": f"block_dual_kernel<{spec.k}>",
+                "traffic": block_dual_traffic(spec.k, N), "kernel": f"block_dual_kernel<{spec.k}, *>",
                 "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": bd_avg_s * 1000.0}
     pass_bytes = (16 * k2 + 120) * N
