@@ -85,10 +85,15 @@ enum {
   S3TTV_OPT_PROFILE = 5,           /* 1: time each kernel class of every pass with CUDA
                                       events on the context stream (resets the totals);
                                       0: off (default)                                    */
-  S3TTV_OPT_WARM_START = 6         /* 1 (default): each block's eigen-solve starts from the
+  S3TTV_OPT_WARM_START = 6,        /* 1 (default): each block's eigen-solve starts from the
                                       eigenbasis it converged to in the previous pass
                                       (same result, fewer sweeps; 4 (k^2+1) k^2 bytes of
                                       workspace per block); 0: every pass starts cold     */
+  S3TTV_OPT_TENSOR_CORES = 7       /* block duals (Alg. 1 steps 8-11): 1 (default) forms
+                                      the Gram Y'Y'^T and the product M Y' on tensor cores,
+                                      each FP32 operand split into two TF32 parts and three
+                                      of the four part products kept (FP32-level accuracy);
+                                      0: the same products with FP32 FMAs on CUDA cores   */
 };
 
 /* Kernel classes reported by s3ttv_kernel_stats. */

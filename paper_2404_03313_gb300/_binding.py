@@ -19,6 +19,7 @@ OK, MAXITER, EINVAL, ENOMEM, ECUDA, ENUMERIC, EUNSUPPORTED, ESTATE, ETOOBIG = 0,
 L1_STATIC_MAX_N = 4294967295
 STEP_PAPER, STEP_PC_EXACT = 0, 1
 OPT_STEP_POLICY, OPT_CHECK_EVERY, OPT_JACOBI_MAX_SWEEPS, OPT_JACOBI_TOL, OPT_PROFILE, OPT_WARM_START = 1, 2, 3, 4, 5, 6
+OPT_TENSOR_CORES = 7
 KERNEL_CLASSES = ("primal", "l1_search", "block_dual", "dual", "finalize")
 STATE = {"u": 0, "s": 1, "t": 2, "y2": 3, "y3": 4, "Y": 5}
 

@@ -23,6 +23,7 @@ struct s3ttv_ctx {
   int check_every = 16;
   int jacobi_max_sweeps = 24;
   float jacobi_tol = 2e-6f;
+  int tensor_cores = 1;
   // problem
   bool ready = false;
   Dims dm{};
@@ -210,20 +211,25 @@ Dims make_dims(int N1, int N2, int N3) {
 }
 
 // Block-dual launch shape: one CTA per group of block_dual_group() blocks, a
-// persistent grid of as many CTAs as fit on the device at once.  The kernel
-// variant sized for five CTAs per SM is taken when five fit by shared memory.
+// persistent grid of as many CTAs as fit on the device at once.  The CUDA-core
+// form takes its variant sized for five CTAs per SM when five fit by shared
+// memory; the tensor-core form has the four-CTA variant only.
 struct BdShape {
-  int rs = 0;       // shared-memory row stride (floats)
+  int rs = 0;       // shared-memory row stride (floats) while forming Y' and G
+  int rs2 = 0;      // shared-memory row stride (floats) while applying M
   size_t smem = 0;  // dynamic shared memory per CTA
   int grid = 0;
-  int minb = 4;     // kernel variant
+  BdVariant v;
 };
 
 int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, BdShape *sh) {
   if (dm.P > 2147483647LL)  // the kernel indexes pixels with 32-bit integers
     return fail(ctx, S3TTV_EUNSUPPORTED, "N1 * N2 = %lld pixels: this build supports fewer than 2^31", dm.P);
+  sh->v.k = k;
+  sh->v.tc = ctx->tensor_cores;
   sh->rs = block_dual_row_stride(dm.N3p);
-  sh->smem = block_dual_smem_bytes(k, sh->rs);
+  sh->rs2 = block_dual_apply_stride(dm.N3p, sh->v.tc);
+  sh->smem = block_dual_smem_bytes(sh->v, dm.N3p);
   int dev_max = 0;
   cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
   if (dev_max <= 0) dev_max = 227 * 1024;
@@ -231,12 +237,12 @@ int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, BdShape *sh) {
     return fail(ctx, S3TTV_EUNSUPPORTED, "a %dx%dx%d block needs %zu bytes of shared memory (device limit %d)", k, k,
                 dm.N3, sh->smem, dev_max);
   int per_sm = 0;
-  for (int minb = 5; minb >= 4; --minb) {
-    cudaError_t e = block_dual_prepare(k, minb, sh->smem);
+  for (int minb = sh->v.tc ? 4 : 5; minb >= 4; --minb) {
+    sh->v.minb = minb;
+    cudaError_t e = block_dual_prepare(sh->v, sh->smem);
     if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-    e = block_dual_occupancy(k, minb, sh->smem, &per_sm);
+    e = block_dual_occupancy(sh->v, sh->smem, &per_sm);
     if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
-    sh->minb = minb;
     if (per_sm >= minb) break;
   }
   if (per_sm < 1) per_sm = 1;
@@ -398,13 +404,14 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   ba.dm = dm;
   ba.gY = (float)ctx->gam[3];
   ba.rs = bd.rs;
+  ba.rs2 = bd.rs2;
   ba.max_sweeps = ctx->jacobi_max_sweeps;
   ba.tol = ctx->jacobi_tol;
   ba.sc = ctx->sc;
   ba.W = ctx->warm_start ? ctx->W : nullptr;
   ba.w_stride = ctx->w_stride;
   ba.warm = ctx->warm_start && ctx->warm_valid;
-  CU(launch_block_dual(ba, ctx->k, bd.minb, bd.grid, bd.smem, st));
+  CU(launch_block_dual(ba, bd.v, bd.grid, bd.smem, st));
   if (ctx->warm_start) ctx->warm_valid = true;
   if (ev) CU(cudaEventRecord(ev[3], st));
 
@@ -581,6 +588,10 @@ int s3ttv_set_option(s3ttv_ctx *ctx, int key, double value) {
     case S3TTV_OPT_JACOBI_TOL:
       if (!(value > 0 && value < 1)) return fail(ctx, S3TTV_EINVAL, "jacobi tol must be in (0, 1)");
       ctx->jacobi_tol = (float)value;
+      return S3TTV_OK;
+    case S3TTV_OPT_TENSOR_CORES:
+      if (value != 0 && value != 1) return fail(ctx, S3TTV_EINVAL, "tensor_cores must be 0 or 1");
+      ctx->tensor_cores = (int)value;
       return S3TTV_OK;
     case S3TTV_OPT_WARM_START:
       if (value != 0 && value != 1) return fail(ctx, S3TTV_EINVAL, "warm_start must be 0 or 1");
@@ -877,13 +888,14 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   ba.dm = dm;
   ba.gY = gamma_Y;
   ba.rs = bd.rs;
+  ba.rs2 = bd.rs2;
   ba.max_sweeps = ctx->jacobi_max_sweeps;
   ba.tol = ctx->jacobi_tol;
   ba.sc = ctx->sc;
   ba.W = nullptr;
   ba.w_stride = 0;
   ba.warm = 0;
-  CU(launch_block_dual(ba, k, bd.minb, bd.grid, bd.smem, ctx->stream));
+  CU(launch_block_dual(ba, bd.v, bd.grid, bd.smem, ctx->stream));
   if ((rc = store_Y(ctx, Y))) return rc;
   if ((rc = store_cube(ctx, ctx->Zv[0], Zv, nullptr))) return rc;
   if ((rc = store_cube(ctx, ctx->Zh[0], Zh, nullptr))) return rc;

@@ -80,21 +80,47 @@ struct Shape {
   static constexpr int TS = TR * K;        // entries per tile
 };
 
-// One slot per block of the group: G, then the scaled eigen-rows (NPOS rows of
-// stride GS), then M by columns.  The float4 reads of the last column's second
-// half run MH floats past n * MS (values that multiply only unused rows).
+// Tensor-core form: G and M padded to 32 x 32 and cut into 16 x 8 tiles
+// (m-tile m: rows 16m..16m+15; n-tile q: columns 8q..8q+7).  The Gram needs
+// the tiles that hold data and reach the upper triangle.
 template <int K>
+struct MmaShape {
+  static constexpr int n = K * K;
+  __host__ __device__ static constexpr bool need(int m, int q) { return 16 * m < n && 8 * q < n && 8 * q + 7 >= 16 * m; }
+  static constexpr int count() {
+    int c = 0;
+    for (int m = 0; m < 2; ++m)
+      for (int q = 0; q < 4; ++q)
+        if (need(m, q)) ++c;
+    return c;
+  }
+  static constexpr int NTILE = count();
+  static constexpr int NM = (n + 15) / 16;  // m-tiles holding rows of M
+  // The apply sums over the n rows of Y': full 8-row k-steps on tensor cores; a
+  // remainder of one or two rows (n = 1, 9, 25) as FP32 FMAs, a longer one as
+  // one more zero-padded k-step.
+  static constexpr int NR0 = n % 8;
+  static constexpr int NKS = n / 8 + (NR0 > 2 ? 1 : 0);  // tensor-core k-steps
+  static constexpr int NR = NR0 > 2 ? 0 : NR0;           // rows left to FMAs
+};
+
+// One slot per block of the group: G, then the scaled eigen-rows (NPOS rows of
+// stride GS), then M.  CUDA-core form: M by columns in two halves; the float4
+// reads of the last column's second half run MH floats past n * MS (values that
+// multiply only unused rows).  Tensor-core form: M by rows, stride GS.
+template <int K, bool TC>
 __host__ __device__ constexpr int gm_floats() {
   using S = Shape<K>;
-  constexpr int m = S::n * S::MS + S::MH, u = S::NPOS * S::GS;
+  constexpr int m = TC ? S::n * S::GS : S::n * S::MS + S::MH, u = S::NPOS * S::GS;
   return ((m > u ? m : u) + 3) & ~3;
 }
 
-// partial Gram tiles of the kNW warps
-template <int K>
+// Partial Gram tiles: CUDA-core form, every warp's register tiles; tensor-core
+// form, the fragments of two warps (reduced in two rounds).
+template <int K, bool TC>
 __host__ __device__ constexpr int tiles_floats() {
   using S = Shape<K>;
-  return (kNW * S::NT * S::TS + 3) & ~3;
+  return TC ? 2 * MmaShape<K>::NTILE * 128 : (kNW * S::NT * S::TS + 3) & ~3;
 }
 
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
@@ -108,6 +134,37 @@ __device__ __forceinline__ void cp_async16(float *sdst, const float *gsrc) {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// TF32 value nearest to x (low 13 mantissa bits cleared), as the bits an mma reads.
+__device__ __forceinline__ unsigned tf32_rna(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+  return r;
+}
+// x = hi + lo with hi a TF32 value; lo (exact in FP32) goes to the tensor core
+// as is, which reads its leading 11 significant bits.
+__device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo) {
+  hi = tf32_rna(x);
+  lo = __float_as_uint(x - __uint_as_float(hi));
+}
+// d += A B for one 16 x 8 x 8 tile, TF32 operands, FP32 accumulation (warp-wide).
+__device__ __forceinline__ void mma_tf32(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+// d += A B with both operands split hi + lo: lo*hi + hi*lo + hi*hi (the lo*lo
+// term, below 2^-21 of the product, is dropped), so the tile product keeps
+// FP32-level accuracy.
+__device__ __forceinline__ void mma_3xtf32(float (&d)[4], const unsigned (&ah)[4], const unsigned (&al)[4],
+                                           unsigned bh0, unsigned bh1, unsigned bl0, unsigned bl1) {
+  mma_tf32(d, al[0], al[1], al[2], al[3], bh0, bh1);
+  mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+  mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bh0, bh1);
 }
 
 // One warp: one-sided Jacobi on the rows of G (or of W G), then the scaled
@@ -300,8 +357,9 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Gm, 
 }
 
 // Warp w: M = I - Ut^T Ut of its own block, written over Ut (in the block's
-// slot) by columns, rows [0, RH) from slot 0 and rows [RH, n) from slot MH.
-template <int K>
+// slot).  CUDA-core form: by columns, rows [0, RH) from slot 0 and rows [RH, n)
+// from slot MH.  Tensor-core form: by rows, stride GS.
+template <int K, bool TC>
 __device__ void form_M(float *Gm) {
   const float *Ut = Gm;
   using S = Shape<K>;
@@ -328,17 +386,202 @@ __device__ void form_M(float *Gm) {
     }
   }
   __syncwarp();  // Ut no longer read
-  for (int e = lane; e < n * MS; e += 32) Gm[e] = 0.f;
-  __syncwarp();
-  if (lane < n) {
+  if constexpr (TC) {
+    if (lane < n) {
 #pragma unroll
-    for (int x = 0; x < K; ++x)
+      for (int x = 0; x < K; ++x)
 #pragma unroll
-      for (int y = 0; y < K; ++y) {
-        const int r = R * K + x, c = Sx * K + y;
-        const int slot = r < RH ? r : MH + (r - RH);
-        Gm[c * MS + slot] = (r == c ? 1.f : 0.f) - macc[x][y];
+        for (int y = 0; y < K; ++y) {
+          const int r = R * K + x, c = Sx * K + y;
+          Gm[r * GS + c] = (r == c ? 1.f : 0.f) - macc[x][y];
+        }
+    }
+  } else {
+    for (int e = lane; e < n * MS; e += 32) Gm[e] = 0.f;
+    __syncwarp();
+    if (lane < n) {
+#pragma unroll
+      for (int x = 0; x < K; ++x)
+#pragma unroll
+        for (int y = 0; y < K; ++y) {
+          const int r = R * K + x, c = Sx * K + y;
+          const int slot = r < RH ? r : MH + (r - RH);
+          Gm[c * MS + slot] = (r == c ? 1.f : 0.f) - macc[x][y];
+        }
+    }
+  }
+}
+
+// Tensor-core Gram of the block in Yp (n rows of stride RS, 2 N3p = 8 C4
+// columns): warp w takes k-steps [w C4 / 4, (w+1) C4 / 4) of 8 columns, each
+// operand split hi + lo; the four warps' partial tiles are summed in a fixed
+// order (w0 + w2) + (w1 + w3) and warp 0 writes G (both triangles, each pair
+// once, from the entry with i <= j).  Called by all threads; holds barriers.
+template <int K>
+__device__ void gram_mma(const float *Yp, int RS, int C4, float *Part, float *Gb) {
+  using T = MmaShape<K>;
+  constexpr int n = T::n, GS = K * K + 1, NTILE = T::NTILE;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float acc[NTILE][4];
+#pragma unroll
+  for (int i = 0; i < NTILE; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+  const int k0 = (C4 * warp) / kNW, k1 = (C4 * (warp + 1)) / kNW;
+#pragma unroll 2
+  for (int ks = k0; ks < k1; ++ks) {
+    // x[q][h] = Y'[8q + g][8 ks + t + 4h], rows >= n read as 0
+    unsigned xh[4][2], xl[4][2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        xh[q][h] = xl[q][h] = 0u;
+        if (8 * q < n) {
+          const int row = 8 * q + g;
+          const float x = row < n ? Yp[(size_t)row * RS + 8 * ks + t + 4 * h] : 0.f;
+          split_tf32(x, xh[q][h], xl[q][h]);
+        }
       }
+    int idx = 0;
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const unsigned ah[4] = {xh[2 * m][0], xh[2 * m + 1][0], xh[2 * m][1], xh[2 * m + 1][1]};
+      const unsigned al[4] = {xl[2 * m][0], xl[2 * m + 1][0], xl[2 * m][1], xl[2 * m + 1][1]};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (T::need(m, q)) {
+          mma_3xtf32(acc[idx], ah, al, xh[q][0], xh[q][1], xl[q][0], xl[q][1]);
+          ++idx;
+        }
+    }
+  }
+  float *P2 = Part, *P3 = Part + NTILE * 128;
+  if (warp >= 2) {
+    float *P = warp == 2 ? P2 : P3;
+#pragma unroll
+    for (int i = 0; i < NTILE; ++i) sts4(P + i * 128 + lane * 4, make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]));
+  }
+  __syncthreads();
+  if (warp < 2) {
+    const float *P = warp == 0 ? P2 : P3;
+#pragma unroll
+    for (int i = 0; i < NTILE; ++i) {
+      const float4 v = lds4(P + i * 128 + lane * 4);
+      acc[i][0] += v.x;
+      acc[i][1] += v.y;
+      acc[i][2] += v.z;
+      acc[i][3] += v.w;
+    }
+    if (warp == 1) {  // warp 1 alone read P3
+#pragma unroll
+      for (int i = 0; i < NTILE; ++i)
+        sts4(P3 + i * 128 + lane * 4, make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]));
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    int idx = 0;
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (T::need(m, q)) {
+          const float4 v = lds4(P3 + idx * 128 + lane * 4);
+          const float d[4] = {acc[idx][0] + v.x, acc[idx][1] + v.y, acc[idx][2] + v.z, acc[idx][3] + v.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int i = 16 * m + g + 8 * (e >> 1), j = 8 * q + 2 * t + (e & 1);
+            if (i < n && j < n && i <= j) {
+              Gb[i * GS + j] = d[e];
+              Gb[j * GS + i] = d[e];
+            }
+          }
+          ++idx;
+        }
+  }
+}
+
+// Tensor-core apply: Y[r][c] = sum_s M[r][s] Y'[s][c] with Y' in shared memory
+// (n rows of stride RS2), written straight to Y_l in global memory and added
+// into Z (P_l^T Y_l), so Y' is never overwritten.  Warp w takes the 8-column
+// n-tiles [w C4 / 4, (w+1) C4 / 4).  The A fragments of M (rows of stride GS)
+// are split hi + lo into registers once; the B fragments of Y' one k-step at a
+// time; the last NR rows of Y' are added with FP32 FMAs.  pix[r]: pixel of row r.
+template <int K>
+__device__ void apply_mma(const float *Yp, int RS2, int C4, const float *Mg, float *Yl, float *Zv, float *Zh,
+                          const int *pix, int N3p) {
+  using T = MmaShape<K>;
+  constexpr int n = T::n, GS = K * K + 1, MT = T::NM, NKS = T::NKS, NR = T::NR, S0 = n - NR;
+  constexpr int m0 = 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int q0 = (C4 * warp) / kNW, q1 = (C4 * (warp + 1)) / kNW;
+  {
+    // A fragments of M: rows 16 m + g (+8), columns 8 kk + t (+4); columns
+    // >= S0 are the FMA rows, held as M[row][S0 + j]
+    unsigned mh[MT][NKS > 0 ? NKS : 1][4], ml[MT][NKS > 0 ? NKS : 1][4];
+    float mr[MT][2][NR > 0 ? NR : 1];
+#pragma unroll
+    for (int mi = 0; mi < MT; ++mi) {
+#pragma unroll
+      for (int kk = 0; kk < NKS; ++kk)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int r = 16 * (m0 + mi) + g + 8 * (e & 1), c = 8 * kk + t + 4 * (e >> 1);
+          const float x = (r < n && c < S0) ? Mg[r * GS + c] : 0.f;
+          split_tf32(x, mh[mi][kk][e], ml[mi][kk][e]);
+        }
+#pragma unroll
+      for (int e2 = 0; e2 < 2; ++e2)
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+          const int r = 16 * (m0 + mi) + g + 8 * e2;
+          mr[mi][e2][j] = r < n ? Mg[r * GS + S0 + j] : 0.f;
+        }
+    }
+#pragma unroll 1
+    for (int q = q0; q < q1; ++q) {
+      const float *col = Yp + 8 * q + g;
+      float d[MT][4];
+#pragma unroll
+      for (int mi = 0; mi < MT; ++mi) d[mi][0] = d[mi][1] = d[mi][2] = d[mi][3] = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < NKS; ++kk) {
+        // B fragment: Y'[8 kk + t (+4)][col], rows >= S0 read as 0
+        const int s0 = 8 * kk + t, s1 = s0 + 4;
+        unsigned bh0, bl0, bh1, bl1;
+        split_tf32(s0 < S0 ? col[(size_t)s0 * RS2] : 0.f, bh0, bl0);
+        split_tf32(s1 < S0 ? col[(size_t)s1 * RS2] : 0.f, bh1, bl1);
+#pragma unroll
+        for (int mi = 0; mi < MT; ++mi) mma_3xtf32(d[mi], mh[mi][kk], ml[mi][kk], bh0, bh1, bl0, bl1);
+      }
+      // columns c, c + 1 of rows 16 m + g (+8); a pair never straddles the
+      // vertical / horizontal halves (N3p is a multiple of 4)
+      const int c = 8 * q + 2 * t;
+#pragma unroll
+      for (int j = 0; j < NR; ++j) {
+        const float2 y = *reinterpret_cast<const float2 *>(Yp + (size_t)(S0 + j) * RS2 + c);
+#pragma unroll
+        for (int mi = 0; mi < MT; ++mi)
+#pragma unroll
+          for (int e2 = 0; e2 < 2; ++e2) {
+            d[mi][2 * e2] = fmaf(mr[mi][e2][j], y.x, d[mi][2 * e2]);
+            d[mi][2 * e2 + 1] = fmaf(mr[mi][e2][j], y.y, d[mi][2 * e2 + 1]);
+          }
+      }
+      const bool hz = c >= N3p;
+      float *Zo = hz ? Zh : Zv;
+      const int band = hz ? c - N3p : c;
+#pragma unroll
+      for (int mi = 0; mi < MT; ++mi)
+#pragma unroll
+        for (int e2 = 0; e2 < 2; ++e2) {
+          const int r = 16 * (m0 + mi) + g + 8 * e2;
+          if (r < n) {
+            const float2 y = make_float2(d[mi][2 * e2], d[mi][2 * e2 + 1]);
+            __stcs(reinterpret_cast<float2 *>(Yl + (size_t)r * 2 * N3p + c), y);
+            atomicAdd(reinterpret_cast<float2 *>(Zo + (size_t)pix[r] * N3p + band), y);
+          }
+        }
+    }
   }
 }
 
@@ -368,8 +611,11 @@ __device__ __forceinline__ void prefetch_rows(const float *Yl, int N3p) {
 }
 
 // MINB: CTAs per SM the register budget is sized for (5: 96 registers a thread,
-// when five CTAs' shared memory fits on an SM; 4: 128 registers otherwise).
-template <int K, int MINB>
+// when five CTAs' shared memory fits on an SM; 4: 128 registers otherwise; the
+// tensor-core form always takes 4).
+// TC: Gram and apply on tensor cores (three TF32 products per FP32 product)
+// instead of FP32 CUDA cores.
+template <int K, int MINB, bool TC>
 __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArgs a) {
   using S = Shape<K>;
   constexpr int n = S::n, GS = S::GS, TR = S::TR, NT = S::NT, TS = S::TS, RH = S::RH, MH = S::MH,
@@ -382,17 +628,16 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
   __shared__ int s_off[kNW][n];  // pixel (i * N2 + j) of row r of P_l
   if (a.sc->done) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int RS = a.rs;
-  float *Yp = smem;                           // Y' (then Y) of one block [n][RS]
-  float *Gall = Yp + (size_t)n * RS;          // kNW x (G, eigen-rows, M)
-  float *Tiles = Gall + kNW * gm_floats<K>(); // partial Gram tiles
+  const int RS = a.rs, RSA = TC ? a.rs2 : a.rs;  // row strides: forming Y' and G / applying M
+  float *Yp = smem;                                      // Y' (then Y) of one block
+  float *Gall = Yp + (size_t)n * (RS > RSA ? RS : RSA);  // kNW x (G, eigen-rows, M)
+  float *Tiles = Gall + kNW * gm_floats<K, TC>();        // partial Gram tiles
   const Dims dm = a.dm;
   const int N3p = dm.N3p, C4 = N3p >> 2, W4 = 2 * C4;
   const long long L = dm.P;
   const long long groups = (L + kNW - 1) / kNW;
   const float gY = a.gY;
-  if (tid == 0) {
-    s_sweeps = 0u;
+  if (tid == 0 && !TC) {
     int c = 0;
     for (int t = 0; t < S::NRG; ++t)
       for (int g = 0; g < K; ++g)
@@ -402,6 +647,7 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
           ++c;
         }
   }
+  if (tid == 0) s_sweeps = 0u;
   __syncthreads();
 
   for (long long grp = blockIdx.x; grp < groups; grp += gridDim.x) {
@@ -461,54 +707,58 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
         }
       }
       __syncthreads();
-      if (lane < NT) {  // tiles reaching the upper triangle, this warp's share of the columns
-        const int r0 = s_tile_r0[lane], c0 = s_tile_c0[lane];
-        float acc[TR][K];
+      if constexpr (TC) {
+        gram_mma<K>(Yp, RS, C4, Tiles, Gall + b * gm_floats<K, TC>());
+      } else {
+        if (lane < NT) {  // tiles reaching the upper triangle, this warp's share of the columns
+          const int r0 = s_tile_r0[lane], c0 = s_tile_c0[lane];
+          float acc[TR][K];
 #pragma unroll
-        for (int x = 0; x < TR; ++x)
+          for (int x = 0; x < TR; ++x)
 #pragma unroll
-          for (int y = 0; y < K; ++y) acc[x][y] = 0.f;
-        const float *pa = Yp + (size_t)r0 * RS;
-        const float *pb = Yp + (size_t)c0 * RS;
-        const int q0 = (W4 * warp) / kNW, q1 = (W4 * (warp + 1)) / kNW;
+            for (int y = 0; y < K; ++y) acc[x][y] = 0.f;
+          const float *pa = Yp + (size_t)r0 * RS;
+          const float *pb = Yp + (size_t)c0 * RS;
+          const int q0 = (W4 * warp) / kNW, q1 = (W4 * (warp + 1)) / kNW;
 #pragma unroll 2
-        for (int qq = q0; qq < q1; ++qq) {
-          const int c = qq << 2;
-          float4 va[TR], vb[K];
+          for (int qq = q0; qq < q1; ++qq) {
+            const int c = qq << 2;
+            float4 va[TR], vb[K];
+#pragma unroll
+            for (int x = 0; x < TR; ++x)
+              va[x] = (r0 + x < n) ? lds4(pa + (size_t)x * RS + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int y = 0; y < K; ++y) vb[y] = lds4(pb + (size_t)y * RS + c);
+#pragma unroll
+            for (int x = 0; x < TR; ++x)
+#pragma unroll
+              for (int y = 0; y < K; ++y) {
+                float t = acc[x][y];
+                t = fmaf(va[x].x, vb[y].x, t);
+                t = fmaf(va[x].y, vb[y].y, t);
+                t = fmaf(va[x].z, vb[y].z, t);
+                t = fmaf(va[x].w, vb[y].w, t);
+                acc[x][y] = t;
+              }
+          }
+          float *pt = Tiles + ((size_t)warp * NT + lane) * TS;
 #pragma unroll
           for (int x = 0; x < TR; ++x)
-            va[x] = (r0 + x < n) ? lds4(pa + (size_t)x * RS + c) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-          for (int y = 0; y < K; ++y) vb[y] = lds4(pb + (size_t)y * RS + c);
-#pragma unroll
-          for (int x = 0; x < TR; ++x)
-#pragma unroll
-            for (int y = 0; y < K; ++y) {
-              float t = acc[x][y];
-              t = fmaf(va[x].x, vb[y].x, t);
-              t = fmaf(va[x].y, vb[y].y, t);
-              t = fmaf(va[x].z, vb[y].z, t);
-              t = fmaf(va[x].w, vb[y].w, t);
-              acc[x][y] = t;
-            }
+            for (int y = 0; y < K; ++y) pt[x * K + y] = acc[x][y];
         }
-        float *pt = Tiles + ((size_t)warp * NT + lane) * TS;
+        __syncthreads();
+        float *Gb = Gall + b * gm_floats<K, TC>();
+        for (int e = tid; e < NT * TS; e += NTH) {
+          const int tl = e / TS, w = e - tl * TS, x = w / K, y = w - x * K;
+          const int r = s_tile_r0[tl] + x, c = s_tile_c0[tl] + y;
+          if (r < n) {
+            float g = 0.f;
 #pragma unroll
-        for (int x = 0; x < TR; ++x)
-#pragma unroll
-          for (int y = 0; y < K; ++y) pt[x * K + y] = acc[x][y];
-      }
-      __syncthreads();
-      float *Gb = Gall + b * gm_floats<K>();
-      for (int e = tid; e < NT * TS; e += NTH) {
-        const int tl = e / TS, w = e - tl * TS, x = w / K, y = w - x * K;
-        const int r = s_tile_r0[tl] + x, c = s_tile_c0[tl] + y;
-        if (r < n) {
-          float g = 0.f;
-#pragma unroll
-          for (int ww = 0; ww < kNW; ++ww) g += Tiles[((size_t)ww * NT + tl) * TS + w];
-          Gb[r * GS + c] = g;
-          Gb[c * GS + r] = g;
+            for (int ww = 0; ww < kNW; ++ww) g += Tiles[((size_t)ww * NT + tl) * TS + w];
+            Gb[r * GS + c] = g;
+            Gb[c * GS + r] = g;
+          }
         }
       }
       __syncthreads();
@@ -518,7 +768,7 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
     if (warp == 0 && grp + gridDim.x < groups)  // the next group's first block
       prefetch_rows<K>(a.Y + (size_t)(grp + gridDim.x) * kNW * n * 2 * N3p, N3p);
     if (warp < nb) {
-      float *Gb = Gall + warp * gm_floats<K>();
+      float *Gb = Gall + warp * gm_floats<K, TC>();
       bool ok;
       const int sweeps = eigen_rows<K>(a, l0 + warp, Gb, Gb, &ok);
       if (lane == 0) {
@@ -526,71 +776,75 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
         atomicAdd(&s_sweeps, (unsigned)sweeps);
       }
       __syncwarp();
-      form_M<K>(Gb);
+      form_M<K, TC>(Gb);
     }
     __syncthreads();
 
-    // ---- 5. for each block: Y' back into shared memory, Y_l = M Y' in place, then
-    //         Y_l stored and P_l^T Y_l added into Z, row by row ----
+    // ---- 5. for each block: Y' back into shared memory, Y_l = M Y' stored and
+    //         P_l^T Y_l added into Z (CUDA-core form: M Y' in place, then row by row) ----
     for (int b = 0; b < nb; ++b) {
       const long long l = l0 + b;
       float *Yl = a.Y + (size_t)l * n * 2 * N3p;
-      const float *Mg = Gall + b * gm_floats<K>();
-      load_rows<K>(Yp, Yl, RS, N3p, W4);
+      const float *Mg = Gall + b * gm_floats<K, TC>();
+      load_rows<K>(Yp, Yl, RSA, N3p, W4);
       cp_async_wait_all();
       __syncthreads();
-      // task: one float4 column chunk, half of the rows.  The two tasks of a chunk
-      // are neighbouring lanes of one warp in the same round, so a warp barrier
-      // orders every read of the chunk before it is overwritten with Y_l.
-      for (int base = 0; base < 2 * W4; base += NTH) {
-        const int task = base + tid;
-        const bool has = task < 2 * W4;
-        const int c4 = task >> 1, half = task & 1;
-        float4 acc[RH];
+      if constexpr (TC) {
+        apply_mma<K>(Yp, RSA, C4, Mg, Yl, a.Zv, a.Zh, s_off[b], N3p);
+      } else {
+        // task: one float4 column chunk, half of the rows.  The two tasks of a chunk
+        // are neighbouring lanes of one warp in the same round, so a warp barrier
+        // orders every read of the chunk before it is overwritten with Y_l.
+        for (int base = 0; base < 2 * W4; base += NTH) {
+          const int task = base + tid;
+          const bool has = task < 2 * W4;
+          const int c4 = task >> 1, half = task & 1;
+          float4 acc[RH];
 #pragma unroll
-        for (int x = 0; x < RH; ++x) acc[x] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (has) {
-          const float *col = Yp + (c4 << 2);
+          for (int x = 0; x < RH; ++x) acc[x] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (has) {
+            const float *col = Yp + (c4 << 2);
 #pragma unroll(MINB >= 5 ? 1 : 5)
-          for (int s = 0; s < n; ++s) {
-            const float4 y = lds4(col + (size_t)s * RS);
-            const float *mcol = Mg + s * MS + half * MH;  // M[r][s] for this half's rows
+            for (int s = 0; s < n; ++s) {
+              const float4 y = lds4(col + (size_t)s * RS);
+              const float *mcol = Mg + s * MS + half * MH;  // M[r][s] for this half's rows
 #pragma unroll
-            for (int x4 = 0; x4 < MH; x4 += 4) {
-              const float4 m = lds4(mcol + x4);
-              const float mm[4] = {m.x, m.y, m.z, m.w};
+              for (int x4 = 0; x4 < MH; x4 += 4) {
+                const float4 m = lds4(mcol + x4);
+                const float mm[4] = {m.x, m.y, m.z, m.w};
 #pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                if (x4 + e < RH) {
-                  acc[x4 + e].x = fmaf(mm[e], y.x, acc[x4 + e].x);
-                  acc[x4 + e].y = fmaf(mm[e], y.y, acc[x4 + e].y);
-                  acc[x4 + e].z = fmaf(mm[e], y.z, acc[x4 + e].z);
-                  acc[x4 + e].w = fmaf(mm[e], y.w, acc[x4 + e].w);
+                for (int e = 0; e < 4; ++e) {
+                  if (x4 + e < RH) {
+                    acc[x4 + e].x = fmaf(mm[e], y.x, acc[x4 + e].x);
+                    acc[x4 + e].y = fmaf(mm[e], y.y, acc[x4 + e].y);
+                    acc[x4 + e].z = fmaf(mm[e], y.z, acc[x4 + e].z);
+                    acc[x4 + e].w = fmaf(mm[e], y.w, acc[x4 + e].w);
+                  }
                 }
               }
             }
           }
-        }
-        __syncwarp();
-        if (has) {
-          float *dst = Yp + (size_t)(half * RH) * RS + (c4 << 2);
+          __syncwarp();
+          if (has) {
+            float *dst = Yp + (size_t)(half * RH) * RS + (c4 << 2);
 #pragma unroll
-          for (int x = 0; x < RH; ++x)
-            if (half * RH + x < n) sts4(dst + (size_t)x * RS, acc[x]);
+            for (int x = 0; x < RH; ++x)
+              if (half * RH + x < n) sts4(dst + (size_t)x * RS, acc[x]);
+          }
         }
-      }
-      __syncthreads();  // Y_l complete in shared memory
-      {
-        int r = 0, c4 = tid;
-        while (c4 >= W4) { c4 -= W4; ++r; }
-        while (r < n) {
-          const float4 y = lds4(Yp + (size_t)r * RS + (c4 << 2));
-          __stcs(reinterpret_cast<float4 *>(Yl + (size_t)r * 2 * N3p) + c4, y);
-          const bool hz = c4 >= C4;
-          float *Zo = (hz ? a.Zh : a.Zv) + (size_t)s_off[b][r] * N3p + ((hz ? c4 - C4 : c4) << 2);
-          atomicAdd(reinterpret_cast<float4 *>(Zo), y);
-          c4 += NTH;
+        __syncthreads();  // Y_l complete in shared memory
+        {
+          int r = 0, c4 = tid;
           while (c4 >= W4) { c4 -= W4; ++r; }
+          while (r < n) {
+            const float4 y = lds4(Yp + (size_t)r * RSA + (c4 << 2));
+            __stcs(reinterpret_cast<float4 *>(Yl + (size_t)r * 2 * N3p) + c4, y);
+            const bool hz = c4 >= C4;
+            float *Zo = (hz ? a.Zh : a.Zv) + (size_t)s_off[b][r] * N3p + ((hz ? c4 - C4 : c4) << 2);
+            atomicAdd(reinterpret_cast<float4 *>(Zo), y);
+            c4 += NTH;
+            while (c4 >= W4) { c4 -= W4; ++r; }
+          }
         }
       }
       __syncthreads();  // the shared buffer is free for the next block
@@ -601,25 +855,34 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
 
 using KernelFn = void (*)(BlockDualArgs);
 
+// The tensor-core form keeps M's split fragments in registers for the whole
+// apply, which needs the 128-register budget: it has the four-CTA variant only.
 template <int K>
-KernelFn kernel_k(int minb) {
-  return minb >= 5 ? block_dual_kernel<K, 5> : block_dual_kernel<K, 4>;
+KernelFn kernel_k(int minb, int tc) {
+  if (tc) return minb == 4 ? block_dual_kernel<K, 4, true> : nullptr;
+  return minb >= 5 ? block_dual_kernel<K, 5, false> : block_dual_kernel<K, 4, false>;
 }
 
-KernelFn kernel_for(int k, int minb) {
-  switch (k) {
-    case 1: return kernel_k<1>(minb);
-    case 2: return kernel_k<2>(minb);
-    case 3: return kernel_k<3>(minb);
-    case 4: return kernel_k<4>(minb);
-    case 5: return kernel_k<5>(minb);
+KernelFn kernel_for(const BdVariant &v) {
+  switch (v.k) {
+    case 1: return kernel_k<1>(v.minb, v.tc);
+    case 2: return kernel_k<2>(v.minb, v.tc);
+    case 3: return kernel_k<3>(v.minb, v.tc);
+    case 4: return kernel_k<4>(v.minb, v.tc);
+    case 5: return kernel_k<5>(v.minb, v.tc);
     default: return nullptr;
   }
 }
 
+template <int K, bool TC>
+size_t smem_k(int rs, int rs2) {
+  const int rsy = rs > rs2 ? rs : rs2;
+  return sizeof(float) * ((size_t)Shape<K>::n * rsy + kNW * gm_floats<K, TC>() + tiles_floats<K, TC>());
+}
+
 template <int K>
-size_t smem_k(int rs) {
-  return sizeof(float) * ((size_t)Shape<K>::n * rs + kNW * gm_floats<K>() + tiles_floats<K>());
+size_t smem_kt(int tc, int rs, int rs2) {
+  return tc ? smem_k<K, true>(rs, rs2) : smem_k<K, false>(rs, rs2);
 }
 
 }  // namespace
@@ -629,9 +892,20 @@ long long block_dual_w_stride(int k) {
   return ((long long)npos * n + 3) & ~3ll;
 }
 
+// 2 N3p plus padding to 4 mod 32 words: the Gram's reads (8 rows x 4
+// consecutive columns per warp access) hit 32 distinct banks.
 int block_dual_row_stride(int N3p) {
   const int base = 2 * N3p;
   const int pad = ((4 - base % 32) + 32) % 32;
+  return base + pad;
+}
+
+// Tensor-core apply: 2 N3p plus padding to 8 mod 32 words, so its reads (4 rows
+// x 8 consecutive columns per warp access) hit 32 distinct banks.
+int block_dual_apply_stride(int N3p, int tc) {
+  if (!tc) return block_dual_row_stride(N3p);
+  const int base = 2 * N3p;
+  const int pad = ((8 - base % 32) + 32) % 32;
   return base + pad;
 }
 
@@ -639,31 +913,32 @@ int block_dual_threads() { return kNW * 32; }
 
 int block_dual_group() { return kNW; }
 
-size_t block_dual_smem_bytes(int k, int rs) {
-  switch (k) {
-    case 1: return smem_k<1>(rs);
-    case 2: return smem_k<2>(rs);
-    case 3: return smem_k<3>(rs);
-    case 4: return smem_k<4>(rs);
-    case 5: return smem_k<5>(rs);
+size_t block_dual_smem_bytes(const BdVariant &v, int N3p) {
+  const int rs = block_dual_row_stride(N3p), rs2 = block_dual_apply_stride(N3p, v.tc);
+  switch (v.k) {
+    case 1: return smem_kt<1>(v.tc, rs, rs2);
+    case 2: return smem_kt<2>(v.tc, rs, rs2);
+    case 3: return smem_kt<3>(v.tc, rs, rs2);
+    case 4: return smem_kt<4>(v.tc, rs, rs2);
+    case 5: return smem_kt<5>(v.tc, rs, rs2);
     default: return 0;
   }
 }
 
-cudaError_t block_dual_prepare(int k, int minb, size_t smem) {
-  KernelFn f = kernel_for(k, minb);
+cudaError_t block_dual_prepare(const BdVariant &v, size_t smem) {
+  KernelFn f = kernel_for(v);
   if (!f) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(reinterpret_cast<const void *>(f), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-cudaError_t block_dual_occupancy(int k, int minb, size_t smem, int *ctas) {
-  KernelFn f = kernel_for(k, minb);
+cudaError_t block_dual_occupancy(const BdVariant &v, size_t smem, int *ctas) {
+  KernelFn f = kernel_for(v);
   if (!f) return cudaErrorInvalidValue;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, reinterpret_cast<const void *>(f), kNW * 32, smem);
 }
 
-cudaError_t launch_block_dual(const BlockDualArgs &a, int k, int minb, int grid, size_t smem, cudaStream_t st) {
-  KernelFn f = kernel_for(k, minb);
+cudaError_t launch_block_dual(const BlockDualArgs &a, const BdVariant &v, int grid, size_t smem, cudaStream_t st) {
+  KernelFn f = kernel_for(v);
   if (!f) return cudaErrorInvalidValue;
   f<<<grid, kNW * 32, smem, st>>>(a);
   return cudaGetLastError();

@@ -121,7 +121,8 @@ struct BlockDualArgs {
   float *Zv, *Zh;         // accumulated with +=
   Dims dm;
   float gY;
-  int rs;                 // shared-memory row stride (floats)
+  int rs;                 // shared-memory row stride (floats) while forming Y' and G
+  int rs2;                // shared-memory row stride (floats) while applying M
   int max_sweeps;
   float tol;
   Scalars *sc;            // done flag and the non-convergence counter
@@ -131,16 +132,26 @@ struct BlockDualArgs {
 };
 // floats per block of the warm-start rows
 long long block_dual_w_stride(int k);
-// Returns cudaErrorInvalidValue if k is not supported.
-// minb: 5 or 4, the kernel variant sized for that many CTAs per SM
-cudaError_t launch_block_dual(const BlockDualArgs &a, int k, int minb, int grid, size_t smem, cudaStream_t st);
-size_t block_dual_smem_bytes(int k, int rs);
+// Kernel variant: block side k (1..5), minb = 5 or 4 (CTAs per SM its register
+// budget is sized for; the tensor-core form has 4 only), tc = 1 for the Gram
+// and the apply on tensor cores (three TF32 products per FP32 product), 0 for
+// FP32 CUDA cores.
+struct BdVariant {
+  int k = 0;
+  int minb = 4;
+  int tc = 0;
+};
+// Row strides (floats) of the shared block copies for N3p bands.
+int block_dual_row_stride(int N3p);
+int block_dual_apply_stride(int N3p, int tc);
+size_t block_dual_smem_bytes(const BdVariant &v, int N3p);
 int block_dual_threads();
 // blocks one CTA of the block-dual kernel takes at a time
 int block_dual_group();
-int block_dual_row_stride(int N3p);
-cudaError_t block_dual_prepare(int k, int minb, size_t smem_bytes);
-cudaError_t block_dual_occupancy(int k, int minb, size_t smem_bytes, int *ctas_per_sm);
+// All return cudaErrorInvalidValue for an unsupported variant.
+cudaError_t launch_block_dual(const BlockDualArgs &a, const BdVariant &v, int grid, size_t smem, cudaStream_t st);
+cudaError_t block_dual_prepare(const BdVariant &v, size_t smem_bytes);
+cudaError_t block_dual_occupancy(const BdVariant &v, size_t smem_bytes, int *ctas_per_sm);
 
 // Layout conversion and small helpers.
 cudaError_t launch_pad_cube(const float *src, float *dst, Dims dm, float scale, cudaStream_t st);

@@ -1,7 +1,8 @@
 """Parity at full size, in the launch configuration bench.py times.
 
 After a few warm passes of Alg. 1 on the 256x256x128 (k = 5) and 304x304x191
-(k = 5, odd band count) cubes, one more pass on the GPU is compared with the FP64
+(k = 5, odd band count) cubes, with the block-dual products on tensor cores and
+on CUDA cores, one more pass on the GPU is compared with the FP64
 oracle applied to the same state: whole arrays where the oracle can afford them
 (both l1-ball projections, y2, y3 over every voxel), sampled blocks for the block
 duals, sampled voxels for u; plus the constraints each projection guarantees.
@@ -53,8 +54,9 @@ def P():
     return P
 
 
+@pytest.mark.parametrize("form", [pytest.param(1, id="tc"), pytest.param(0, id="fp32")])
 @pytest.mark.parametrize("name,warm_passes", [("s3ttv_256x256x128_k5", 3), ("s3ttv_304x304x191_k5", 2)])
-def test_one_full_size_pass(P, name, warm_passes):
+def test_one_full_size_pass(P, name, warm_passes, form):
     spec = WORKLOADS[name]
     k = spec.k
     clean, v = make_cube(spec)
@@ -63,6 +65,7 @@ def test_one_full_size_pass(P, name, warm_passes):
     eps, alpha, beta = O.radii(v.size, spec.sigma, spec.p_s, spec.p_t)
     g = O.step_sizes(N1, N2, k, "paper")
     s = P.Solver(0)
+    s.set_option(P.OPT_TENSOR_CORES, form)
     try:
         vd = torch.from_numpy(v).cuda()
         s.setup(vd, eps, alpha, beta, k)

@@ -34,9 +34,15 @@ def P():
     return P
 
 
-@pytest.fixture()
-def solver(P):
+# Both forms of the block-dual products: tensor cores (three TF32 products per
+# FP32 product) and FP32 FMAs on CUDA cores.
+FORMS = [pytest.param(1, id="tc"), pytest.param(0, id="fp32")]
+
+
+@pytest.fixture(params=FORMS)
+def solver(P, request):
     s = P.Solver(0)
+    s.set_option(P.OPT_TENSOR_CORES, request.param)
     yield s
     s.close()
 
@@ -178,12 +184,19 @@ def test_one_pass_matches_oracle(P, solver, shape, k, policy):
 # 300 passes on the parity cube
 # ---------------------------------------------------------------------------
 @pytest.fixture(scope="module")
-def parity_run(P):
+def parity_oracle():
     spec = WORKLOADS["parity_32x32x16_k3"]
     clean, v = make_cube(spec)
     eps, alpha, beta = O.radii(v.size, spec.sigma, spec.p_s, spec.p_t)
     ref, it, _ = O.solve(v, spec.k, eps, alpha, beta, max_iter=300, tol=0.0)
+    return spec, clean, v, (eps, alpha, beta), ref
+
+
+@pytest.fixture(scope="module", params=FORMS)
+def parity_run(P, parity_oracle, request):
+    spec, clean, v, (eps, alpha, beta), ref = parity_oracle
     with P.Solver(0) as s:
+        s.set_option(P.OPT_TENSOR_CORES, request.param)
         u, sp, t, info = s.solve(torch.from_numpy(v).cuda(), eps, alpha, beta, spec.k, max_iter=300, tol=0.0)
     return clean, v, ref, (u.cpu().numpy(), sp.cpu().numpy(), t.cpu().numpy()), info
 
