@@ -266,6 +266,7 @@ def run_ours(args, spec):
     stream = torch.cuda.Stream(device=dev)
     solver = P.Solver(dev, stream=stream)
     solver.set_option(P.OPT_STEP_POLICY, policy)
+    solver.set_option(P.OPT_TENSOR_CORES, args.tensor_cores)
     vd = torch.from_numpy(v).to(f"cuda:{dev}")
     torch.cuda.synchronize()
 
@@ -345,6 +346,8 @@ def run_ours(args, spec):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "N1": spec.N1, "N2": spec.N2, "N3": spec.N3, "k": spec.k,
                        "policy": args.policy, "parallelism": f"replicas{world}",
+                       "block_dual_products": ("tensor cores, each FP32 operand split into two TF32 parts"
+                                               if args.tensor_cores else "CUDA cores, FP32 FMA"),
                        "l2": "inputs larger than L2 (block duals Y: %.2f GB, read and written every pass)"
                              % (8 * k2 * N / 1e9)},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
@@ -373,6 +376,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--policy", choices=("paper", "pc_exact"), default="paper")
+    ap.add_argument("--tensor-cores", type=int, choices=(0, 1), default=1,
+                    help="block-dual Gram and apply on tensor cores (1) or CUDA cores (0)")
     ap.add_argument("--no-tol-run", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -211,9 +211,8 @@ Dims make_dims(int N1, int N2, int N3) {
 }
 
 // Block-dual launch shape: one CTA per group of block_dual_group() blocks, a
-// persistent grid of as many CTAs as fit on the device at once.  The CUDA-core
-// form takes its variant sized for five CTAs per SM when five fit by shared
-// memory; the tensor-core form has the four-CTA variant only.
+// persistent grid of as many CTAs as fit on the device at once.  The kernel
+// variant sized for five CTAs per SM is taken when five fit by shared memory.
 struct BdShape {
   int rs = 0;       // shared-memory row stride (floats) while forming Y' and G
   int rs2 = 0;      // shared-memory row stride (floats) while applying M
@@ -237,7 +236,7 @@ int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, BdShape *sh) {
     return fail(ctx, S3TTV_EUNSUPPORTED, "a %dx%dx%d block needs %zu bytes of shared memory (device limit %d)", k, k,
                 dm.N3, sh->smem, dev_max);
   int per_sm = 0;
-  for (int minb = sh->v.tc ? 4 : 5; minb >= 4; --minb) {
+  for (int minb = 5; minb >= 4; --minb) {
     sh->v.minb = minb;
     cudaError_t e = block_dual_prepare(sh->v, sh->smem);
     if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));

@@ -115,6 +115,21 @@ __host__ __device__ constexpr int gm_floats() {
   return ((m > u ? m : u) + 3) & ~3;
 }
 
+// Warm-start rows of one block: NPOS rows of n, padded to 16 bytes (the host's
+// block_dual_w_stride).
+template <int K>
+__host__ __device__ constexpr int w_floats() {
+  using S = Shape<K>;
+  return (S::NPOS * S::n + 3) & ~3;
+}
+
+// The Y' buffer: n rows of stride rs, also the staging area of the group's
+// warm-start rows during the eigen-solves.
+template <int K>
+__host__ __device__ constexpr size_t yp_floats(int rs) {
+  return (size_t)K * K * rs > (size_t)kNW * w_floats<K>() ? (size_t)K * K * rs : (size_t)kNW * w_floats<K>();
+}
+
 // Partial Gram tiles: CUDA-core form, every warp's register tiles; tensor-core
 // form, the fragments of two warps (reduced in two rounds).
 template <int K, bool TC>
@@ -167,10 +182,12 @@ __device__ __forceinline__ void mma_3xtf32(float (&d)[4], const unsigned (&ah)[4
   mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bh0, bh1);
 }
 
-// One warp: one-sided Jacobi on the rows of G (or of W G), then the scaled
-// eigen-rows into Ut and the warm rows into W.  Returns the sweeps used.
+// One warp: one-sided Jacobi on the rows of G (or of W G, Ws being a shared
+// copy of the block's warm-start rows W, null for a cold start), then the
+// scaled eigen-rows into Ut and the warm rows into W.  Returns the sweeps used.
 template <int K>
-__device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Gm, float *Ut, bool *ok) {
+__device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Ws, const float *Gm, float *Ut,
+                          bool *ok) {
   using S = Shape<K>;
   constexpr int n = S::n, NP = S::NP, NPOS = S::NPOS, H = S::H, GS = S::GS;
   const int lane = threadIdx.x & 31;
@@ -185,8 +202,7 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Gm, 
   const int src_r = act ? (pi + 1 == NP ? hf : lane + 2) : lane;            // right neighbour (ring)
   const int src_l = act ? (pi == 0 ? 2 * (NP - 1) + hf : lane - 2) : lane;  // left neighbour (ring)
   float A[H], B[H];
-  const float *Wl = a.W ? a.W + (size_t)l * a.w_stride : nullptr;
-  const bool warm = a.warm && Wl && !(Wl[0] != Wl[0]);  // NaN marks "start cold"
+  const bool warm = Ws && !(Ws[0] != Ws[0]);  // NaN marks "start cold"
   if (warm) {
     // C0 = W G: rows 2i, 2i+1 of W times G, this lane's half of the columns
 #pragma unroll
@@ -194,11 +210,11 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Gm, 
       A[e] = 0.f;
       B[e] = 0.f;
     }
-    const float *wra = Wl + (2 * pi) * n, *wrb = Wl + (2 * pi + 1) * n;
+    const float *wra = Ws + (2 * pi) * n, *wrb = Ws + (2 * pi + 1) * n;
 #pragma unroll 5
     for (int kk = 0; kk < n; ++kk) {
-      const float wa = act ? __ldg(wra + kk) : 0.f;
-      const float wb = act ? __ldg(wrb + kk) : 0.f;
+      const float wa = act ? wra[kk] : 0.f;
+      const float wb = act ? wrb[kk] : 0.f;
 #pragma unroll
       for (int e = 0; e < H; ++e) {
         const int col = hf * H + e;
@@ -232,6 +248,24 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Gm, 
   float fro = hf == 0 ? nA + nB : 0.f;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(kFull, fro, o);
+  // Exact power-of-two scaling of the rows to a Frobenius norm near 1 keeps the
+  // squares of the rotation parameters in range; eigenvalues are unscaled at
+  // the end by inv_s.
+  float inv_s = 1.f;
+  if (fro > 0.f && fro < 1e30f) {
+    const int ex = ((__float_as_int(fro) >> 23) & 255) - 127;  // fro = m 2^ex, m in [1, 2)
+    const int h = ex >> 1;                                      // rows scale by 2^-h
+    const float sc = __int_as_float((127 - h) << 23), sc2 = sc * sc;
+    inv_s = __int_as_float((127 + h) << 23);
+#pragma unroll
+    for (int e = 0; e < H; ++e) {
+      A[e] *= sc;
+      B[e] *= sc;
+    }
+    nA *= sc2;
+    nB *= sc2;
+    fro *= sc2;
+  }
   // rows below 1e-6 ||G||_F are numerical zeros: rotating them changes any
   // other row's direction by less than 1e-6
   const float floor2 = 1e-12f * fro;
@@ -245,26 +279,26 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Gm, 
   // which changes nothing the solver uses).  When no pair of the warp needs a
   // rotation, meeting pairs are left as they are and only that swap remains.
   auto step = [&](bool meets, bool odd) {
-    float p0 = 0.f, p1 = 0.f;
+    float p[4] = {0.f, 0.f, 0.f, 0.f};  // four short chains
 #pragma unroll
-    for (int e = 0; e < H; e += 2) {
-      p0 = fmaf(A[e], B[e], p0);
-      if (e + 1 < H) p1 = fmaf(A[e + 1], B[e + 1], p1);
-    }
-    float apq = p0 + p1;
+    for (int e = 0; e < H; ++e) p[e & 3] = fmaf(A[e], B[e], p[e & 3]);
+    float apq = (p[0] + p[1]) + (p[2] + p[3]);
     apq += __shfl_xor_sync(kFull, apq, 1);
     const bool need = meets && fminf(nA, nB) > floor2 && apq * apq > tol2 * nA * nB;
     const bool quarter = act && !meets;  // the odd step's idle pair
     if (__any_sync(kFull, need)) {
       float c = quarter ? 0.f : 1.f, sn = quarter ? 1.f : 0.f, dn = 0.f;
       if (need) {
-        const float zeta = __fdividef(nB - nA, 2.f * apq);
-        const float az = fabsf(zeta);
-        const float z2 = fmaf(zeta, zeta, 1.f);
-        const float tt = az > 1e15f ? __fdividef(0.5f, zeta) : copysignf(__fdividef(1.f, az + z2 * rsqrtf(z2)), zeta);
-        c = rsqrtf(fmaf(tt, tt, 1.f));
-        sn = c * tt;
-        dn = tt * apq;
+        // tan 2 theta = y / x with x = nB - nA, y = 2 apq and |theta| <= pi / 4:
+        // cos 2 theta = |x| / r (r = |(x, y)|), c = sqrt((1 + cos 2 theta) / 2),
+        // s = sign(x) y / (2 r c), t = s / c; two reciprocal square roots in all
+        const float x = nB - nA, y = 2.f * apq;
+        const float rr = rsqrtf(fmaf(x, x, y * y));
+        const float hc = fmaf(0.5f * fabsf(x), rr, 0.5f);
+        const float rc = rsqrtf(hc);
+        c = hc * rc;
+        sn = copysignf(0.5f, x) * y * rr * rc;
+        dn = sn * rc * apq;  // t apq
         rotated = true;
       }
 #pragma unroll
@@ -316,11 +350,11 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Gm, 
   }
   *ok = converged;
 
-  // eigen-rows: lam = ||row||, keep sqrt(1 - lam^-1/2) row / lam
+  // eigen-rows: lam = ||row|| (unscaled), keep sqrt(1 - lam^-1/2) row / ||row||
   refresh();
-  const float lA = sqrtf(nA), lB = sqrtf(nB);
-  const float sA = lA > 1.f ? sqrtf(1.f - rsqrtf(lA)) / lA : 0.f;
-  const float sB = lB > 1.f ? sqrtf(1.f - rsqrtf(lB)) / lB : 0.f;
+  const float lA = sqrtf(nA) * inv_s, lB = sqrtf(nB) * inv_s;
+  const float sA = lA > 1.f ? sqrtf(1.f - rsqrtf(lA)) * rsqrtf(nA) : 0.f;
+  const float sB = lB > 1.f ? sqrtf(1.f - rsqrtf(lB)) * rsqrtf(nB) : 0.f;
   __syncwarp();  // Ut takes the place of G, which every lane has read
   if (act) {
 #pragma unroll
@@ -338,7 +372,6 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Gm, 
     const unsigned zero_rows = __popc(__ballot_sync(kFull, act && hf == 0 && nA <= floor2)) +
                                __popc(__ballot_sync(kFull, act && hf == 0 && nB <= floor2));
     float *Ww = a.W + (size_t)l * a.w_stride;
-    __syncwarp();  // every lane has read Wl[0] above
     if (zero_rows > (unsigned)(NPOS - n)) {
       if (lane == 0) Ww[0] = __int_as_float(0x7fc00000);
     } else if (act) {
@@ -500,102 +533,115 @@ __device__ void gram_mma(const float *Yp, int RS, int C4, float *Part, float *Gb
   }
 }
 
-// Tensor-core apply: Y[r][c] = sum_s M[r][s] Y'[s][c] with Y' in shared memory
-// (n rows of stride RS2), written straight to Y_l in global memory and added
-// into Z (P_l^T Y_l), so Y' is never overwritten.  Warp w takes the 8-column
-// n-tiles [w C4 / 4, (w+1) C4 / 4).  The A fragments of M (rows of stride GS)
-// are split hi + lo into registers once; the B fragments of Y' one k-step at a
-// time; the last NR rows of Y' are added with FP32 FMAs.  pix[r]: pixel of row r.
+// Tensor-core apply, in place: Y'[s][c] (n rows of stride RS2, shared memory)
+// becomes Y[r][c] = sum_s M[r][s] Y'[s][c].  Warp w takes the 8-column n-tiles
+// [w C4 / 4, (w+1) C4 / 4) and reads, then writes, only those columns.  The A
+// fragments of M (rows of stride GS) are split hi + lo into registers once; the
+// B fragments of Y' one k-step at a time; the last NR rows of Y' are added with
+// FP32 FMAs.
 template <int K>
-__device__ void apply_mma(const float *Yp, int RS2, int C4, const float *Mg, float *Yl, float *Zv, float *Zh,
-                          const int *pix, int N3p) {
+__device__ void apply_mma(float *Yp, int RS2, int C4, const float *Mg) {
   using T = MmaShape<K>;
-  constexpr int n = T::n, GS = K * K + 1, MT = T::NM, NKS = T::NKS, NR = T::NR, S0 = n - NR;
-  constexpr int m0 = 0;
+  constexpr int n = T::n, GS = K * K + 1, NM = T::NM, NKS = T::NKS, NR = T::NR, S0 = n - NR;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const int q0 = (C4 * warp) / kNW, q1 = (C4 * (warp + 1)) / kNW;
-  {
-    // A fragments of M: rows 16 m + g (+8), columns 8 kk + t (+4); columns
-    // >= S0 are the FMA rows, held as M[row][S0 + j]
-    unsigned mh[MT][NKS > 0 ? NKS : 1][4], ml[MT][NKS > 0 ? NKS : 1][4];
-    float mr[MT][2][NR > 0 ? NR : 1];
+  // A fragments of M: rows 16 m + g (+8), columns 8 kk + t (+4); columns >= S0
+  // are the FMA rows, held as M[row][S0 + j]
+  unsigned mh[NM][NKS > 0 ? NKS : 1][4], ml[NM][NKS > 0 ? NKS : 1][4];
+  float mr[NM][2][NR > 0 ? NR : 1];
 #pragma unroll
-    for (int mi = 0; mi < MT; ++mi) {
+  for (int m = 0; m < NM; ++m) {
 #pragma unroll
-      for (int kk = 0; kk < NKS; ++kk)
+    for (int kk = 0; kk < NKS; ++kk)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int r = 16 * (m0 + mi) + g + 8 * (e & 1), c = 8 * kk + t + 4 * (e >> 1);
-          const float x = (r < n && c < S0) ? Mg[r * GS + c] : 0.f;
-          split_tf32(x, mh[mi][kk][e], ml[mi][kk][e]);
-        }
-#pragma unroll
-      for (int e2 = 0; e2 < 2; ++e2)
-#pragma unroll
-        for (int j = 0; j < NR; ++j) {
-          const int r = 16 * (m0 + mi) + g + 8 * e2;
-          mr[mi][e2][j] = r < n ? Mg[r * GS + S0 + j] : 0.f;
-        }
-    }
-#pragma unroll 1
-    for (int q = q0; q < q1; ++q) {
-      const float *col = Yp + 8 * q + g;
-      float d[MT][4];
-#pragma unroll
-      for (int mi = 0; mi < MT; ++mi) d[mi][0] = d[mi][1] = d[mi][2] = d[mi][3] = 0.f;
-#pragma unroll
-      for (int kk = 0; kk < NKS; ++kk) {
-        // B fragment: Y'[8 kk + t (+4)][col], rows >= S0 read as 0
-        const int s0 = 8 * kk + t, s1 = s0 + 4;
-        unsigned bh0, bl0, bh1, bl1;
-        split_tf32(s0 < S0 ? col[(size_t)s0 * RS2] : 0.f, bh0, bl0);
-        split_tf32(s1 < S0 ? col[(size_t)s1 * RS2] : 0.f, bh1, bl1);
-#pragma unroll
-        for (int mi = 0; mi < MT; ++mi) mma_3xtf32(d[mi], mh[mi][kk], ml[mi][kk], bh0, bh1, bl0, bl1);
+      for (int e = 0; e < 4; ++e) {
+        const int r = 16 * m + g + 8 * (e & 1), c = 8 * kk + t + 4 * (e >> 1);
+        const float x = (r < n && c < S0) ? Mg[r * GS + c] : 0.f;
+        split_tf32(x, mh[m][kk][e], ml[m][kk][e]);
       }
-      // columns c, c + 1 of rows 16 m + g (+8); a pair never straddles the
-      // vertical / horizontal halves (N3p is a multiple of 4)
-      const int c = 8 * q + 2 * t;
+#pragma unroll
+    for (int e2 = 0; e2 < 2; ++e2)
 #pragma unroll
       for (int j = 0; j < NR; ++j) {
-        const float2 y = *reinterpret_cast<const float2 *>(Yp + (size_t)(S0 + j) * RS2 + c);
-#pragma unroll
-        for (int mi = 0; mi < MT; ++mi)
-#pragma unroll
-          for (int e2 = 0; e2 < 2; ++e2) {
-            d[mi][2 * e2] = fmaf(mr[mi][e2][j], y.x, d[mi][2 * e2]);
-            d[mi][2 * e2 + 1] = fmaf(mr[mi][e2][j], y.y, d[mi][2 * e2 + 1]);
-          }
+        const int r = 16 * m + g + 8 * e2;
+        mr[m][e2][j] = r < n ? Mg[r * GS + S0 + j] : 0.f;
       }
-      const bool hz = c >= N3p;
-      float *Zo = hz ? Zh : Zv;
-      const int band = hz ? c - N3p : c;
+  }
+#pragma unroll 1
+  for (int q = q0; q < q1; ++q) {
+    float *col = Yp + 8 * q + g;
+    float d[NM][4];
 #pragma unroll
-      for (int mi = 0; mi < MT; ++mi)
+    for (int m = 0; m < NM; ++m) d[m][0] = d[m][1] = d[m][2] = d[m][3] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < NKS; ++kk) {
+      // B fragment: Y'[8 kk + t (+4)][col], rows >= S0 read as 0
+      const int s0 = 8 * kk + t, s1 = s0 + 4;
+      unsigned bh0, bl0, bh1, bl1;
+      split_tf32(s0 < S0 ? col[(size_t)s0 * RS2] : 0.f, bh0, bl0);
+      split_tf32(s1 < S0 ? col[(size_t)s1 * RS2] : 0.f, bh1, bl1);
+#pragma unroll
+      for (int m = 0; m < NM; ++m) mma_3xtf32(d[m], mh[m][kk], ml[m][kk], bh0, bh1, bl0, bl1);
+    }
+    // columns c, c + 1 of rows 16 m + g (+8)
+    const int c = 8 * q + 2 * t;
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      const float2 y = *reinterpret_cast<const float2 *>(Yp + (size_t)(S0 + j) * RS2 + c);
+#pragma unroll
+      for (int m = 0; m < NM; ++m)
 #pragma unroll
         for (int e2 = 0; e2 < 2; ++e2) {
-          const int r = 16 * (m0 + mi) + g + 8 * e2;
-          if (r < n) {
-            const float2 y = make_float2(d[mi][2 * e2], d[mi][2 * e2 + 1]);
-            __stcs(reinterpret_cast<float2 *>(Yl + (size_t)r * 2 * N3p + c), y);
-            atomicAdd(reinterpret_cast<float2 *>(Zo + (size_t)pix[r] * N3p + band), y);
-          }
+          d[m][2 * e2] = fmaf(mr[m][e2][j], y.x, d[m][2 * e2]);
+          d[m][2 * e2 + 1] = fmaf(mr[m][e2][j], y.y, d[m][2 * e2 + 1]);
         }
     }
+    __syncwarp();  // every lane has read these columns
+#pragma unroll
+    for (int m = 0; m < NM; ++m)
+#pragma unroll
+      for (int e2 = 0; e2 < 2; ++e2) {
+        const int r = 16 * m + g + 8 * e2;
+        if (r < n) *reinterpret_cast<float2 *>(Yp + (size_t)r * RS2 + c) = make_float2(d[m][2 * e2], d[m][2 * e2 + 1]);
+      }
   }
 }
 
-// Shared-memory copy of the n rows of Y_l (row stride RS), one 16-byte chunk per
-// thread at a time; completes at cp_async_wait_all.
+// This thread's share of a block's n x W4 grid of 16-byte chunks (rows r,
+// chunks c4 of 4 floats): chunks c4 = c0, c0 + cs, ... < W4 and, for each,
+// rows r = r0, r0 + rs, ... < n.  With W4 < threads, a thread keeps one chunk
+// column (threads beyond the last whole set of columns stay idle), so the loops
+// below carry no division.
+// The steps cs, rs are the same for every thread.
+struct Walk {
+  int c0, r0;  // this thread's first chunk and row
+  int cs, rs;  // steps
+};
+__device__ __forceinline__ Walk make_walk(int W4) {
+  constexpr int NTH = kNW * 32;
+  const int tid = threadIdx.x;
+  Walk w;
+  w.cs = W4 >= NTH ? NTH : W4;
+  w.rs = W4 >= NTH ? 1 : NTH / W4;  // rows taken at once
+  w.c0 = W4 >= NTH ? tid : tid % W4;
+  w.r0 = W4 >= NTH ? 0 : tid / W4;
+  if (w.r0 >= w.rs) w.c0 = W4;  // idle
+  return w;
+}
+
+// Shared-memory copy of the n rows of Y_l (row stride RS); completes at
+// cp_async_wait_all.
 template <int K>
-__device__ __forceinline__ void load_rows(float *Yp, const float *Yl, int RS, int N3p, int W4) {
+__device__ __forceinline__ void load_rows(float *Yp, const float *Yl, int RS, int N3p, int W4, const Walk &wk) {
   constexpr int n = K * K;
-  int r = 0, c4 = threadIdx.x;
-  while (c4 >= W4) { c4 -= W4; ++r; }
-  while (r < n) {
-    cp_async16(Yp + (size_t)r * RS + (c4 << 2), Yl + (size_t)r * 2 * N3p + (c4 << 2));
-    c4 += kNW * 32;
-    while (c4 >= W4) { c4 -= W4; ++r; }
+  for (int c4 = wk.c0; c4 < W4; c4 += wk.cs) {
+    float *sp = Yp + (size_t)wk.r0 * RS + (c4 << 2);
+    const float *gp = Yl + (size_t)wk.r0 * 2 * N3p + (c4 << 2);
+    for (int r = wk.r0; r < n; r += wk.rs) {
+      cp_async16(sp, gp);
+      sp += (size_t)wk.rs * RS;
+      gp += (size_t)wk.rs * 2 * N3p;
+    }
   }
 }
 
@@ -611,8 +657,7 @@ __device__ __forceinline__ void prefetch_rows(const float *Yl, int N3p) {
 }
 
 // MINB: CTAs per SM the register budget is sized for (5: 96 registers a thread,
-// when five CTAs' shared memory fits on an SM; 4: 128 registers otherwise; the
-// tensor-core form always takes 4).
+// when five CTAs' shared memory fits on an SM; 4: 128 registers otherwise).
 // TC: Gram and apply on tensor cores (three TF32 products per FP32 product)
 // instead of FP32 CUDA cores.
 template <int K, int MINB, bool TC>
@@ -630,13 +675,15 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int RS = a.rs, RSA = TC ? a.rs2 : a.rs;  // row strides: forming Y' and G / applying M
   float *Yp = smem;                                      // Y' (then Y) of one block
-  float *Gall = Yp + (size_t)n * (RS > RSA ? RS : RSA);  // kNW x (G, eigen-rows, M)
+  float *Gall = Yp + yp_floats<K>(RS > RSA ? RS : RSA);  // kNW x (G, eigen-rows, M)
   float *Tiles = Gall + kNW * gm_floats<K, TC>();        // partial Gram tiles
   const Dims dm = a.dm;
   const int N3p = dm.N3p, C4 = N3p >> 2, W4 = 2 * C4;
   const long long L = dm.P;
   const long long groups = (L + kNW - 1) / kNW;
   const float gY = a.gY;
+  const bool warm = a.warm && a.W;  // a.w_stride == w_floats<K>()
+  const Walk wk = make_walk(W4);
   if (tid == 0 && !TC) {
     int c = 0;
     for (int t = 0; t < S::NRG; ++t)
@@ -653,12 +700,16 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
   for (long long grp = blockIdx.x; grp < groups; grp += gridDim.x) {
     const long long l0 = grp * kNW;
     const int nb = (int)(L - l0 < kNW ? L - l0 : kNW);  // blocks in this group
+    if (warm && warp == 2 && lane < nb)  // warm-start rows into L2 for step 3
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(a.W + (size_t)(l0 + lane) * w_floats<K>()),
+                   "r"((unsigned)(w_floats<K>() * sizeof(float)))
+                   : "memory");
 
     // ---- 1-2. for each block of the group: Y' in shared memory, then its Gram ----
     for (int b = 0; b < nb; ++b) {
       const long long l = l0 + b;
       float *Yl = a.Y + (size_t)l * n * 2 * N3p;
-      load_rows<K>(Yp, Yl, RS, N3p, W4);
+      load_rows<K>(Yp, Yl, RS, N3p, W4, wk);
       if (warp == 1 && b + 1 < nb) prefetch_rows<K>(Yl + (size_t)n * 2 * N3p, N3p);
       if (tid < n) {
         const int p = (int)(l / dm.N2), q = (int)(l - (long long)p * dm.N2);
@@ -671,29 +722,22 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
       }
       cp_async_wait_all();
       __syncthreads();
-      {
-        // NF chunks per thread in flight: (r, c4) of this thread's items, advanced by NTH
-        int r0 = 0, c0 = tid;
-        while (c0 >= W4) { c0 -= W4; ++r0; }
-        while (r0 < n) {
-          int rr[NF], cc[NF];
+      // Y' = Y + gamma_Y (Fv | Fh), NF loads of D D_s ubar in flight per thread
+      for (int c4 = wk.c0; c4 < W4; c4 += wk.cs) {
+        const bool hz = c4 >= C4;
+        const float *Fb = (hz ? a.Fh : a.Fv) + ((hz ? c4 - C4 : c4) << 2);
+        for (int rb = wk.r0; rb < n; rb += NF * wk.rs) {
           float4 xv[NF];
 #pragma unroll
           for (int u = 0; u < NF; ++u) {
-            rr[u] = r0;
-            cc[u] = c0;
-            if (r0 < n) {
-              const bool hz = c0 >= C4;
-              const float *F = (hz ? a.Fh : a.Fv) + (size_t)s_off[b][r0] * N3p + ((hz ? c0 - C4 : c0) << 2);
-              xv[u] = __ldg(reinterpret_cast<const float4 *>(F));
-            }
-            c0 += NTH;
-            while (c0 >= W4) { c0 -= W4; ++r0; }
+            const int r = rb + u * wk.rs;
+            if (r < n) xv[u] = __ldg(reinterpret_cast<const float4 *>(Fb + (size_t)s_off[b][r] * N3p));
           }
 #pragma unroll
           for (int u = 0; u < NF; ++u) {
-            if (rr[u] < n) {
-              float *dst = Yp + (size_t)rr[u] * RS + (cc[u] << 2);
+            const int r = rb + u * wk.rs;
+            if (r < n) {
+              float *dst = Yp + (size_t)r * RS + (c4 << 2);
               float4 y = lds4(dst);
               y.x = fmaf(gY, xv[u].x, y.x);
               y.y = fmaf(gY, xv[u].y, y.y);
@@ -701,7 +745,7 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
               y.w = fmaf(gY, xv[u].w, y.w);
               sts4(dst, y);
               // Y' replaces Y_l in global memory (kept in L2) for step 5
-              reinterpret_cast<float4 *>(Yl + (size_t)rr[u] * 2 * N3p)[cc[u]] = y;
+              reinterpret_cast<float4 *>(Yl + (size_t)r * 2 * N3p)[c4] = y;
             }
           }
         }
@@ -767,10 +811,19 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
     // ---- 3-4. every warp: eigen-solve of one block of the group, then its M ----
     if (warp == 0 && grp + gridDim.x < groups)  // the next group's first block
       prefetch_rows<K>(a.Y + (size_t)(grp + gridDim.x) * kNW * n * 2 * N3p, N3p);
+    if (warm) {  // the group's warm-start rows into the free Y' buffer
+      constexpr int WS4 = w_floats<K>() / 4;
+      for (int idx = tid; idx < nb * WS4; idx += NTH) {
+        const int b = idx / WS4, c = idx - b * WS4;
+        cp_async16(Yp + b * w_floats<K>() + 4 * c, a.W + (size_t)(l0 + b) * w_floats<K>() + 4 * c);
+      }
+      cp_async_wait_all();
+      __syncthreads();
+    }
     if (warp < nb) {
       float *Gb = Gall + warp * gm_floats<K, TC>();
       bool ok;
-      const int sweeps = eigen_rows<K>(a, l0 + warp, Gb, Gb, &ok);
+      const int sweeps = eigen_rows<K>(a, l0 + warp, warm ? Yp + warp * w_floats<K>() : nullptr, Gb, Gb, &ok);
       if (lane == 0) {
         if (!ok) atomicAdd(&a.sc->jacobi_fail, 1u);
         atomicAdd(&s_sweeps, (unsigned)sweeps);
@@ -780,17 +833,17 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
     }
     __syncthreads();
 
-    // ---- 5. for each block: Y' back into shared memory, Y_l = M Y' stored and
-    //         P_l^T Y_l added into Z (CUDA-core form: M Y' in place, then row by row) ----
+    // ---- 5. for each block: Y' back into shared memory, Y_l = M Y' in place, then
+    //         Y_l stored and P_l^T Y_l added into Z, row by row ----
     for (int b = 0; b < nb; ++b) {
       const long long l = l0 + b;
       float *Yl = a.Y + (size_t)l * n * 2 * N3p;
       const float *Mg = Gall + b * gm_floats<K, TC>();
-      load_rows<K>(Yp, Yl, RSA, N3p, W4);
+      load_rows<K>(Yp, Yl, RSA, N3p, W4, wk);
       cp_async_wait_all();
       __syncthreads();
       if constexpr (TC) {
-        apply_mma<K>(Yp, RSA, C4, Mg, Yl, a.Zv, a.Zh, s_off[b], N3p);
+        apply_mma<K>(Yp, RSA, C4, Mg);
       } else {
         // task: one float4 column chunk, half of the rows.  The two tasks of a chunk
         // are neighbouring lanes of one warp in the same round, so a warp barrier
@@ -832,19 +885,15 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
               if (half * RH + x < n) sts4(dst + (size_t)x * RS, acc[x]);
           }
         }
-        __syncthreads();  // Y_l complete in shared memory
-        {
-          int r = 0, c4 = tid;
-          while (c4 >= W4) { c4 -= W4; ++r; }
-          while (r < n) {
-            const float4 y = lds4(Yp + (size_t)r * RSA + (c4 << 2));
-            __stcs(reinterpret_cast<float4 *>(Yl + (size_t)r * 2 * N3p) + c4, y);
-            const bool hz = c4 >= C4;
-            float *Zo = (hz ? a.Zh : a.Zv) + (size_t)s_off[b][r] * N3p + ((hz ? c4 - C4 : c4) << 2);
-            atomicAdd(reinterpret_cast<float4 *>(Zo), y);
-            c4 += NTH;
-            while (c4 >= W4) { c4 -= W4; ++r; }
-          }
+      }
+      __syncthreads();  // Y_l complete in shared memory
+      for (int c4 = wk.c0; c4 < W4; c4 += wk.cs) {
+        const bool hz = c4 >= C4;
+        float *Zb = (hz ? a.Zh : a.Zv) + ((hz ? c4 - C4 : c4) << 2);
+        for (int r = wk.r0; r < n; r += wk.rs) {
+          const float4 y = lds4(Yp + (size_t)r * RSA + (c4 << 2));
+          __stcs(reinterpret_cast<float4 *>(Yl + (size_t)r * 2 * N3p) + c4, y);
+          atomicAdd(reinterpret_cast<float4 *>(Zb + (size_t)s_off[b][r] * N3p), y);
         }
       }
       __syncthreads();  // the shared buffer is free for the next block
@@ -855,11 +904,9 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
 
 using KernelFn = void (*)(BlockDualArgs);
 
-// The tensor-core form keeps M's split fragments in registers for the whole
-// apply, which needs the 128-register budget: it has the four-CTA variant only.
 template <int K>
 KernelFn kernel_k(int minb, int tc) {
-  if (tc) return minb == 4 ? block_dual_kernel<K, 4, true> : nullptr;
+  if (tc) return minb >= 5 ? block_dual_kernel<K, 5, true> : block_dual_kernel<K, 4, true>;
   return minb >= 5 ? block_dual_kernel<K, 5, false> : block_dual_kernel<K, 4, false>;
 }
 
@@ -877,7 +924,7 @@ KernelFn kernel_for(const BdVariant &v) {
 template <int K, bool TC>
 size_t smem_k(int rs, int rs2) {
   const int rsy = rs > rs2 ? rs : rs2;
-  return sizeof(float) * ((size_t)Shape<K>::n * rsy + kNW * gm_floats<K, TC>() + tiles_floats<K, TC>());
+  return sizeof(float) * (yp_floats<K>(rsy) + kNW * gm_floats<K, TC>() + tiles_floats<K, TC>());
 }
 
 template <int K>
@@ -888,8 +935,14 @@ size_t smem_kt(int tc, int rs, int rs2) {
 }  // namespace
 
 long long block_dual_w_stride(int k) {
-  const int n = k * k, npos = 2 * ((n + 1) / 2);
-  return ((long long)npos * n + 3) & ~3ll;
+  switch (k) {
+    case 1: return w_floats<1>();
+    case 2: return w_floats<2>();
+    case 3: return w_floats<3>();
+    case 4: return w_floats<4>();
+    case 5: return w_floats<5>();
+    default: return 0;
+  }
 }
 
 // 2 N3p plus padding to 4 mod 32 words: the Gram's reads (8 rows x 4

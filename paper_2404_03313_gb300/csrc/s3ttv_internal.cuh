@@ -133,9 +133,8 @@ struct BlockDualArgs {
 // floats per block of the warm-start rows
 long long block_dual_w_stride(int k);
 // Kernel variant: block side k (1..5), minb = 5 or 4 (CTAs per SM its register
-// budget is sized for; the tensor-core form has 4 only), tc = 1 for the Gram
-// and the apply on tensor cores (three TF32 products per FP32 product), 0 for
-// FP32 CUDA cores.
+// budget is sized for), tc = 1 for the Gram and the apply on tensor cores (three
+// TF32 products per FP32 product), 0 for FP32 CUDA cores.
 struct BdVariant {
   int k = 0;
   int minb = 4;
