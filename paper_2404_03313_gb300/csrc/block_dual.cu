@@ -60,8 +60,9 @@ struct Shape {
   static constexpr int n = K * K;          // rows of a block (and of G)
   static constexpr int NP = (n + 1) / 2;   // row pairs (a zero row when n is odd)
   static constexpr int NPOS = 2 * NP;      // round-robin positions
-  static constexpr int H = (n + 1) / 2;    // half-row length held by one lane
-  static constexpr int GS = n + 1;         // stride of G and of the eigen-rows
+  static constexpr int HP = (n + 3) / 4;   // column pairs of a row held by one lane
+  static constexpr int HW = 2 * HP;        // columns held by one lane
+  static constexpr int GS = (n + 2) & ~1;  // stride of G and of the eigen-rows (even)
   static constexpr int TR = K < 3 ? K : 3; // Gram tile rows (tile columns: K)
   static constexpr int RH = (n + 1) / 2;   // rows per thread in the apply
   static constexpr int MH = (RH + 3) & ~3; // padded half of a column of M
@@ -151,6 +152,30 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
+// Two FP32 values in one 64-bit register pair, and the packed FP32x2
+// arithmetic of sm_100 and later (each lane rounds as its scalar counterpart).
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 up2(f32x2 v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
 // TF32 value nearest to x (low 13 mantissa bits cleared), as the bits an mma reads.
 __device__ __forceinline__ unsigned tf32_rna(float x) {
   unsigned r;
@@ -189,60 +214,66 @@ template <int K>
 __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Ws, const float *Gm, float *Ut,
                           bool *ok) {
   using S = Shape<K>;
-  constexpr int n = S::n, NP = S::NP, NPOS = S::NPOS, H = S::H, GS = S::GS;
+  constexpr int n = S::n, NP = S::NP, NPOS = S::NPOS, HP = S::HP, HW = S::HW, GS = S::GS;
   const int lane = threadIdx.x & 31;
-  // Positions 0..NPOS-1 hold the rows; lane pair i (lanes 2i, 2i+1, one half of
-  // each row) holds positions (2i, 2i+1) on even steps and (2i+1, 2i+2) on odd
-  // steps (the odd-even ordering: neighbours rotate, then trade places, so every
-  // pair of rows meets once in NPOS steps).  Between steps one row per lane
-  // moves one lane pair along a ring; on odd steps the last lane pair holds
-  // (NPOS-1, 0), which do not meet there.
+  // Positions 0..NPOS-1 hold the rows; lane pair i (lanes 2i, 2i+1, columns
+  // [0, HW) and [HW, 2 HW) of both rows, as HP packed column pairs) holds
+  // positions (2i, 2i+1) on even steps and (2i+1, 2i+2) on odd steps (the
+  // odd-even ordering: neighbours rotate, then trade places, so every pair of
+  // rows meets once in NPOS steps).  Between steps one row per lane moves one
+  // lane pair along a ring; on odd steps the last lane pair holds (NPOS-1, 0),
+  // which do not meet there.  Columns >= n stay 0.
   const int pi = lane >> 1, hf = lane & 1;
   const bool act = pi < NP;
   const int src_r = act ? (pi + 1 == NP ? hf : lane + 2) : lane;            // right neighbour (ring)
   const int src_l = act ? (pi == 0 ? 2 * (NP - 1) + hf : lane - 2) : lane;  // left neighbour (ring)
-  float A[H], B[H];
+  const int col0 = hf * HW;
+  // element (row r, column c) of a row-major matrix of stride ld, 0 outside
+  auto ld2 = [&](const float *M, int ld, int r, bool ok_row, int c) -> f32x2 {
+    const float x = (ok_row && c < n) ? M[r * ld + c] : 0.f;
+    const float y = (ok_row && c + 1 < n) ? M[r * ld + c + 1] : 0.f;
+    return pk2(x, y);
+  };
+  f32x2 A[HP], B[HP];
   const bool warm = Ws && !(Ws[0] != Ws[0]);  // NaN marks "start cold"
   if (warm) {
-    // C0 = W G: rows 2i, 2i+1 of W times G, this lane's half of the columns
+    // C0 = W G: rows 2i, 2i+1 of W times G, this lane's columns
 #pragma unroll
-    for (int e = 0; e < H; ++e) {
-      A[e] = 0.f;
-      B[e] = 0.f;
-    }
+    for (int j = 0; j < HP; ++j) A[j] = B[j] = 0ull;
     const float *wra = Ws + (2 * pi) * n, *wrb = Ws + (2 * pi + 1) * n;
 #pragma unroll 5
     for (int kk = 0; kk < n; ++kk) {
       const float wa = act ? wra[kk] : 0.f;
       const float wb = act ? wrb[kk] : 0.f;
+      const f32x2 wa2 = pk2(wa, wa), wb2 = pk2(wb, wb);
 #pragma unroll
-      for (int e = 0; e < H; ++e) {
-        const int col = hf * H + e;
-        const float g = col < n ? Gm[kk * GS + col] : 0.f;
-        A[e] = fmaf(wa, g, A[e]);
-        B[e] = fmaf(wb, g, B[e]);
+      for (int j = 0; j < HP; ++j) {
+        const f32x2 g = ld2(Gm, GS, kk, true, col0 + 2 * j);
+        A[j] = fma2(wa2, g, A[j]);
+        B[j] = fma2(wb2, g, B[j]);
       }
     }
   } else {
     const int rA = 2 * pi, rB = 2 * pi + 1;
 #pragma unroll
-    for (int e = 0; e < H; ++e) {
-      const int col = hf * H + e;
-      A[e] = (act && rA < n && col < n) ? Gm[rA * GS + col] : 0.f;
-      B[e] = (act && rB < n && col < n) ? Gm[rB * GS + col] : 0.f;
+    for (int j = 0; j < HP; ++j) {
+      A[j] = ld2(Gm, GS, rA, act && rA < n, col0 + 2 * j);
+      B[j] = ld2(Gm, GS, rB, act && rB < n, col0 + 2 * j);
     }
   }
   // squared row norms, tracked through the rotations and refreshed every sweep
   float nA, nB;
   auto refresh = [&]() {
-    float x = 0.f, y = 0.f;
+    f32x2 x = 0ull, y = 0ull;
 #pragma unroll
-    for (int e = 0; e < H; ++e) {
-      x = fmaf(A[e], A[e], x);
-      y = fmaf(B[e], B[e], y);
+    for (int j = 0; j < HP; ++j) {
+      x = fma2(A[j], A[j], x);
+      y = fma2(B[j], B[j], y);
     }
-    nA = x + __shfl_xor_sync(kFull, x, 1);
-    nB = y + __shfl_xor_sync(kFull, y, 1);
+    const float2 xs = up2(x), ys = up2(y);
+    const float sa = xs.x + xs.y, sb = ys.x + ys.y;
+    nA = sa + __shfl_xor_sync(kFull, sa, 1);
+    nB = sb + __shfl_xor_sync(kFull, sb, 1);
   };
   refresh();
   float fro = hf == 0 ? nA + nB : 0.f;
@@ -257,10 +288,11 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Ws, 
     const int h = ex >> 1;                                      // rows scale by 2^-h
     const float sc = __int_as_float((127 - h) << 23), sc2 = sc * sc;
     inv_s = __int_as_float((127 + h) << 23);
+    const f32x2 scp = pk2(sc, sc);
 #pragma unroll
-    for (int e = 0; e < H; ++e) {
-      A[e] *= sc;
-      B[e] *= sc;
+    for (int j = 0; j < HP; ++j) {
+      A[j] = mul2(A[j], scp);
+      B[j] = mul2(B[j], scp);
     }
     nA *= sc2;
     nB *= sc2;
@@ -279,10 +311,14 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Ws, 
   // which changes nothing the solver uses).  When no pair of the warp needs a
   // rotation, meeting pairs are left as they are and only that swap remains.
   auto step = [&](bool meets, bool odd) {
-    float p[4] = {0.f, 0.f, 0.f, 0.f};  // four short chains
+    f32x2 p0 = 0ull, p1 = 0ull;  // two short chains
 #pragma unroll
-    for (int e = 0; e < H; ++e) p[e & 3] = fmaf(A[e], B[e], p[e & 3]);
-    float apq = (p[0] + p[1]) + (p[2] + p[3]);
+    for (int j = 0; j < HP; ++j) {
+      if (j & 1) p1 = fma2(A[j], B[j], p1);
+      else p0 = fma2(A[j], B[j], p0);
+    }
+    const float2 q0 = up2(p0), q1 = up2(p1);
+    float apq = (q0.x + q0.y) + (q1.x + q1.y);
     apq += __shfl_xor_sync(kFull, apq, 1);
     const bool need = meets && fminf(nA, nB) > floor2 && apq * apq > tol2 * nA * nB;
     const bool quarter = act && !meets;  // the odd step's idle pair
@@ -301,21 +337,22 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Ws, 
         dn = sn * rc * apq;  // t apq
         rotated = true;
       }
+      const f32x2 c2 = pk2(c, c), s2 = pk2(sn, sn), ns2 = pk2(-sn, -sn);
 #pragma unroll
-      for (int e = 0; e < H; ++e) {
-        const float x = A[e], y = B[e];
-        A[e] = fmaf(c, x, -sn * y);
-        B[e] = fmaf(sn, x, c * y);
+      for (int j = 0; j < HP; ++j) {
+        const f32x2 x = A[j], y = B[j];
+        A[j] = fma2(c2, x, mul2(ns2, y));
+        B[j] = fma2(s2, x, mul2(c2, y));
       }
       const float oA = nA;
       nA = quarter ? nB : nA - dn;
       nB = quarter ? oA : nB + dn;
     } else if (odd) {
 #pragma unroll
-      for (int e = 0; e < H; ++e) {
-        const float x = A[e], y = B[e];
-        A[e] = quarter ? y : x;
-        B[e] = quarter ? x : y;
+      for (int j = 0; j < HP; ++j) {
+        const f32x2 x = A[j], y = B[j];
+        A[j] = quarter ? y : x;
+        B[j] = quarter ? x : y;
       }
       const float oA = nA;
       nA = quarter ? nB : nA;
@@ -332,13 +369,13 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Ws, 
       step(act, false);
       if constexpr (NP > 1) {  // to the odd positions: B takes the right neighbour's B
 #pragma unroll
-        for (int e = 0; e < H; ++e) B[e] = __shfl_sync(kFull, B[e], src_r);
+        for (int j = 0; j < HP; ++j) B[j] = __shfl_sync(kFull, B[j], src_r);
         nB = __shfl_sync(kFull, nB, src_r);
       }
       step(act && pi != NP - 1, true);
       if constexpr (NP > 1) {  // back to the even positions: A takes the left neighbour's A
 #pragma unroll
-        for (int e = 0; e < H; ++e) A[e] = __shfl_sync(kFull, A[e], src_l);
+        for (int j = 0; j < HP; ++j) A[j] = __shfl_sync(kFull, A[j], src_l);
         nA = __shfl_sync(kFull, nA, src_l);
       }
     }
@@ -358,11 +395,16 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Ws, 
   __syncwarp();  // Ut takes the place of G, which every lane has read
   if (act) {
 #pragma unroll
-    for (int e = 0; e < H; ++e) {
-      const int col = hf * H + e;
+    for (int j = 0; j < HP; ++j) {
+      const float2 x = up2(A[j]), y = up2(B[j]);
+      const int col = col0 + 2 * j;
       if (col < n) {
-        Ut[(2 * pi) * GS + col] = A[e] * sA;
-        Ut[(2 * pi + 1) * GS + col] = B[e] * sB;
+        Ut[(2 * pi) * GS + col] = x.x * sA;
+        Ut[(2 * pi + 1) * GS + col] = y.x * sB;
+      }
+      if (col + 1 < n) {
+        Ut[(2 * pi) * GS + col + 1] = x.y * sA;
+        Ut[(2 * pi + 1) * GS + col + 1] = y.y * sB;
       }
     }
   }
@@ -377,11 +419,16 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Ws, 
     } else if (act) {
       const float iA = nA > floor2 ? rsqrtf(nA) : 0.f, iB = nB > floor2 ? rsqrtf(nB) : 0.f;
 #pragma unroll
-      for (int e = 0; e < H; ++e) {
-        const int col = hf * H + e;
+      for (int j = 0; j < HP; ++j) {
+        const float2 x = up2(A[j]), y = up2(B[j]);
+        const int col = col0 + 2 * j;
         if (col < n) {
-          Ww[(2 * pi) * n + col] = A[e] * iA;
-          Ww[(2 * pi + 1) * n + col] = B[e] * iB;
+          Ww[(2 * pi) * n + col] = x.x * iA;
+          Ww[(2 * pi + 1) * n + col] = y.x * iB;
+        }
+        if (col + 1 < n) {
+          Ww[(2 * pi) * n + col + 1] = x.y * iA;
+          Ww[(2 * pi + 1) * n + col + 1] = y.y * iB;
         }
       }
     }
@@ -453,7 +500,7 @@ __device__ void form_M(float *Gm) {
 template <int K>
 __device__ void gram_mma(const float *Yp, int RS, int C4, float *Part, float *Gb) {
   using T = MmaShape<K>;
-  constexpr int n = T::n, GS = K * K + 1, NTILE = T::NTILE;
+  constexpr int n = T::n, GS = Shape<K>::GS, NTILE = T::NTILE;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   float acc[NTILE][4];
 #pragma unroll
@@ -542,7 +589,7 @@ __device__ void gram_mma(const float *Yp, int RS, int C4, float *Part, float *Gb
 template <int K>
 __device__ void apply_mma(float *Yp, int RS2, int C4, const float *Mg) {
   using T = MmaShape<K>;
-  constexpr int n = T::n, GS = K * K + 1, NM = T::NM, NKS = T::NKS, NR = T::NR, S0 = n - NR;
+  constexpr int n = T::n, GS = Shape<K>::GS, NM = T::NM, NKS = T::NKS, NR = T::NR, S0 = n - NR;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const int q0 = (C4 * warp) / kNW, q1 = (C4 * (warp + 1)) / kNW;
   // A fragments of M: rows 16 m + g (+8), columns 8 kk + t (+4); columns >= S0
