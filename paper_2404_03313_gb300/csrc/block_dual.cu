@@ -176,17 +176,13 @@ __device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
   return r;
 }
 
-// TF32 value nearest to x (low 13 mantissa bits cleared), as the bits an mma reads.
-__device__ __forceinline__ unsigned tf32_rna(float x) {
-  unsigned r;
-  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
-  return r;
-}
-// x = hi + lo with hi a TF32 value; lo (exact in FP32) goes to the tensor core
-// as is, which reads its leading 11 significant bits.
+// x ~ hi + lo with hi = x truncated to TF32 (low 13 mantissa bits cleared,
+// |x - hi| < 2^-10 |x|) and lo = x - hi (exact in FP32) truncated to TF32 as
+// well: |x - hi - lo| < 2^-20 |x|.  Three integer / FP32 instructions, and the
+// tensor core reads both parts exactly.
 __device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo) {
-  hi = tf32_rna(x);
-  lo = __float_as_uint(x - __uint_as_float(hi));
+  hi = __float_as_uint(x) & 0xffffe000u;
+  lo = __float_as_uint(x - __uint_as_float(hi)) & 0xffffe000u;
 }
 // d += A B for one 16 x 8 x 8 tile, TF32 operands, FP32 accumulation (warp-wide).
 __device__ __forceinline__ void mma_tf32(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
@@ -198,8 +194,8 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], unsigned a0, unsigned a1
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 // d += A B with both operands split hi + lo: lo*hi + hi*lo + hi*hi (the lo*lo
-// term, below 2^-21 of the product, is dropped), so the tile product keeps
-// FP32-level accuracy.
+// term, below 2^-20 of the product, is dropped), so the tile product keeps
+// FP32-level accuracy (a few 2^-20 relative).
 __device__ __forceinline__ void mma_3xtf32(float (&d)[4], const unsigned (&ah)[4], const unsigned (&al)[4],
                                            unsigned bh0, unsigned bh1, unsigned bl0, unsigned bl1) {
   mma_tf32(d, al[0], al[1], al[2], al[3], bh0, bh1);
