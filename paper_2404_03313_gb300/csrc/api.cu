@@ -212,10 +212,9 @@ Dims make_dims(int N1, int N2, int N3) {
 
 // Block-dual launch shape: one CTA per group of block_dual_group() blocks, a
 // persistent grid of as many CTAs as fit on the device at once.  The kernel
-// variant sized for five CTAs per SM is taken when five fit by shared memory.
+// variant sized for the most CTAs per SM whose shared memory fits is taken.
 struct BdShape {
-  int rs = 0;       // shared-memory row stride (floats) while forming Y' and G
-  int rs2 = 0;      // shared-memory row stride (floats) while applying M
+  int rs = 0;       // shared-memory row stride (floats) of the block copies
   size_t smem = 0;  // dynamic shared memory per CTA
   int grid = 0;
   BdVariant v;
@@ -227,7 +226,6 @@ int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, BdShape *sh) {
   sh->v.k = k;
   sh->v.tc = ctx->tensor_cores;
   sh->rs = block_dual_row_stride(dm.N3p);
-  sh->rs2 = block_dual_apply_stride(dm.N3p, sh->v.tc);
   sh->smem = block_dual_smem_bytes(sh->v, dm.N3p);
   int dev_max = 0;
   cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
@@ -238,6 +236,7 @@ int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, BdShape *sh) {
   int per_sm = 0;
   for (int minb = 5; minb >= 4; --minb) {
     sh->v.minb = minb;
+    if (!block_dual_has(sh->v)) continue;  // variant not compiled
     cudaError_t e = block_dual_prepare(sh->v, sh->smem);
     if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
     e = block_dual_occupancy(sh->v, sh->smem, &per_sm);
@@ -403,7 +402,6 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   ba.dm = dm;
   ba.gY = (float)ctx->gam[3];
   ba.rs = bd.rs;
-  ba.rs2 = bd.rs2;
   ba.max_sweeps = ctx->jacobi_max_sweeps;
   ba.tol = ctx->jacobi_tol;
   ba.sc = ctx->sc;
@@ -887,7 +885,6 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   ba.dm = dm;
   ba.gY = gamma_Y;
   ba.rs = bd.rs;
-  ba.rs2 = bd.rs2;
   ba.max_sweeps = ctx->jacobi_max_sweeps;
   ba.tol = ctx->jacobi_tol;
   ba.sc = ctx->sc;

@@ -62,7 +62,8 @@ struct Shape {
   static constexpr int NPOS = 2 * NP;      // round-robin positions
   static constexpr int HP = (n + 3) / 4;   // column pairs of a row held by one lane
   static constexpr int HW = 2 * HP;        // columns held by one lane
-  static constexpr int GS = (n + 2) & ~1;  // stride of G and of the eigen-rows (even)
+  static constexpr int GS = (n + 2) & ~1;  // stride of G and of M (even)
+  static constexpr int UTS = n;            // stride of the scaled eigen-rows
   static constexpr int TR = K < 3 ? K : 3; // Gram tile rows (tile columns: K)
   static constexpr int RH = (n + 1) / 2;   // rows per thread in the apply
   static constexpr int MH = (RH + 3) & ~3; // padded half of a column of M
@@ -106,14 +107,15 @@ struct MmaShape {
 };
 
 // One slot per block of the group: G, then the scaled eigen-rows (NPOS rows of
-// stride GS), then M.  CUDA-core form: M by columns in two halves; the float4
+// stride UTS), then M.  CUDA-core form: M by columns in two halves; the float4
 // reads of the last column's second half run MH floats past n * MS (values that
 // multiply only unused rows).  Tensor-core form: M by rows, stride GS.
 template <int K, bool TC>
 __host__ __device__ constexpr int gm_floats() {
   using S = Shape<K>;
-  constexpr int m = TC ? S::n * S::GS : S::n * S::MS + S::MH, u = S::NPOS * S::GS;
-  return ((m > u ? m : u) + 3) & ~3;
+  constexpr int m = TC ? S::n * S::GS : S::n * S::MS + S::MH, u = S::NPOS * S::UTS, g = S::n * S::GS;
+  constexpr int mu = m > u ? m : u;
+  return ((mu > g ? mu : g) + 3) & ~3;
 }
 
 // Warm-start rows of one block: NPOS rows of n, padded to 16 bytes (the host's
@@ -124,19 +126,22 @@ __host__ __device__ constexpr int w_floats() {
   return (S::NPOS * S::n + 3) & ~3;
 }
 
-// The Y' buffer: n rows of stride rs, also the staging area of the group's
-// warm-start rows during the eigen-solves.
-template <int K>
-__host__ __device__ constexpr size_t yp_floats(int rs) {
-  return (size_t)K * K * rs > (size_t)kNW * w_floats<K>() ? (size_t)K * K * rs : (size_t)kNW * w_floats<K>();
-}
-
 // Partial Gram tiles: CUDA-core form, every warp's register tiles; tensor-core
 // form, the fragments of two warps (reduced in two rounds).
 template <int K, bool TC>
 __host__ __device__ constexpr int tiles_floats() {
   using S = Shape<K>;
   return TC ? 2 * MmaShape<K>::NTILE * 128 : (kNW * S::NT * S::TS + 3) & ~3;
+}
+
+// The Y' buffer: n rows of stride rs, also the staging area of the group's
+// warm-start rows during the eigen-solves and, in the tensor-core form, of the
+// partial Gram tiles once the Gram has read Y'.
+template <int K, bool TC>
+__host__ __device__ constexpr size_t yp_floats(int rs) {
+  const size_t y = (size_t)K * K * rs, w = (size_t)kNW * w_floats<K>(), t = TC ? (size_t)tiles_floats<K, TC>() : 0;
+  const size_t yw = y > w ? y : w;
+  return yw > t ? yw : t;
 }
 
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
@@ -210,7 +215,7 @@ template <int K>
 __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Ws, const float *Gm, float *Ut,
                           bool *ok) {
   using S = Shape<K>;
-  constexpr int n = S::n, NP = S::NP, NPOS = S::NPOS, HP = S::HP, HW = S::HW, GS = S::GS;
+  constexpr int n = S::n, NP = S::NP, NPOS = S::NPOS, HP = S::HP, HW = S::HW, GS = S::GS, UTS = S::UTS;
   const int lane = threadIdx.x & 31;
   // Positions 0..NPOS-1 hold the rows; lane pair i (lanes 2i, 2i+1, columns
   // [0, HW) and [HW, 2 HW) of both rows, as HP packed column pairs) holds
@@ -395,12 +400,12 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Ws, 
       const float2 x = up2(A[j]), y = up2(B[j]);
       const int col = col0 + 2 * j;
       if (col < n) {
-        Ut[(2 * pi) * GS + col] = x.x * sA;
-        Ut[(2 * pi + 1) * GS + col] = y.x * sB;
+        Ut[(2 * pi) * UTS + col] = x.x * sA;
+        Ut[(2 * pi + 1) * UTS + col] = y.x * sB;
       }
       if (col + 1 < n) {
-        Ut[(2 * pi) * GS + col + 1] = x.y * sA;
-        Ut[(2 * pi + 1) * GS + col + 1] = y.y * sB;
+        Ut[(2 * pi) * UTS + col + 1] = x.y * sA;
+        Ut[(2 * pi + 1) * UTS + col + 1] = y.y * sB;
       }
     }
   }
@@ -452,9 +457,9 @@ __device__ void form_M(float *Gm) {
     for (int xr = 0; xr < S::NPOS; ++xr) {
       float ua[K], ub[K];
 #pragma unroll
-      for (int x = 0; x < K; ++x) ua[x] = Ut[xr * GS + R * K + x];
+      for (int x = 0; x < K; ++x) ua[x] = Ut[xr * S::UTS + R * K + x];
 #pragma unroll
-      for (int y = 0; y < K; ++y) ub[y] = Ut[xr * GS + Sx * K + y];
+      for (int y = 0; y < K; ++y) ub[y] = Ut[xr * S::UTS + Sx * K + y];
 #pragma unroll
       for (int x = 0; x < K; ++x)
 #pragma unroll
@@ -491,8 +496,9 @@ __device__ void form_M(float *Gm) {
 // Tensor-core Gram of the block in Yp (n rows of stride RS, 2 N3p = 8 C4
 // columns): warp w takes k-steps [w C4 / 4, (w+1) C4 / 4) of 8 columns, each
 // operand split hi + lo; the four warps' partial tiles are summed in a fixed
-// order (w0 + w2) + (w1 + w3) and warp 0 writes G (both triangles, each pair
-// once, from the entry with i <= j).  Called by all threads; holds barriers.
+// order (w0 + w2) + (w1 + w3) through Part (which may overlay Yp) and warp 0
+// writes G (both triangles, each pair once, from the entry with i <= j).
+// Called by all threads; holds barriers.
 template <int K>
 __device__ void gram_mma(const float *Yp, int RS, int C4, float *Part, float *Gb) {
   using T = MmaShape<K>;
@@ -531,6 +537,7 @@ __device__ void gram_mma(const float *Yp, int RS, int C4, float *Part, float *Gb
     }
   }
   float *P2 = Part, *P3 = Part + NTILE * 128;
+  __syncthreads();  // the partials take the place of Y', which every warp has read
   if (warp >= 2) {
     float *P = warp == 2 ? P2 : P3;
 #pragma unroll
@@ -700,7 +707,7 @@ __device__ __forceinline__ void prefetch_rows(const float *Yl, int N3p) {
 }
 
 // MINB: CTAs per SM the register budget is sized for (5: 96 registers a thread,
-// when five CTAs' shared memory fits on an SM; 4: 128 registers otherwise).
+// 4: 128), the largest whose shared memory fits on an SM.
 // TC: Gram and apply on tensor cores (three TF32 products per FP32 product)
 // instead of FP32 CUDA cores.
 template <int K, int MINB, bool TC>
@@ -712,14 +719,14 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
   constexpr int NF = 6;  // F loads in flight per thread
   extern __shared__ __align__(16) float smem[];
   __shared__ unsigned s_sweeps;
-  __shared__ int s_tile_r0[32], s_tile_c0[32];
+  __shared__ int s_tile_r0[TC ? 1 : 32], s_tile_c0[TC ? 1 : 32];
   __shared__ int s_off[kNW][n];  // pixel (i * N2 + j) of row r of P_l
   if (a.sc->done) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int RS = a.rs, RSA = TC ? a.rs2 : a.rs;  // row strides: forming Y' and G / applying M
-  float *Yp = smem;                                      // Y' (then Y) of one block
-  float *Gall = Yp + yp_floats<K>(RS > RSA ? RS : RSA);  // kNW x (G, eigen-rows, M)
-  float *Tiles = Gall + kNW * gm_floats<K, TC>();        // partial Gram tiles
+  const int RS = a.rs;                              // row stride of the block copies
+  float *Yp = smem;                                 // Y' (then Y) of one block
+  float *Gall = Yp + yp_floats<K, TC>(RS);          // kNW x (G, eigen-rows, M)
+  float *Tiles = TC ? Yp : Gall + kNW * gm_floats<K, TC>();  // partial Gram tiles
   const Dims dm = a.dm;
   const int N3p = dm.N3p, C4 = N3p >> 2, W4 = 2 * C4;
   const long long L = dm.P;
@@ -882,11 +889,11 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
       const long long l = l0 + b;
       float *Yl = a.Y + (size_t)l * n * 2 * N3p;
       const float *Mg = Gall + b * gm_floats<K, TC>();
-      load_rows<K>(Yp, Yl, RSA, N3p, W4, wk);
+      load_rows<K>(Yp, Yl, RS, N3p, W4, wk);
       cp_async_wait_all();
       __syncthreads();
       if constexpr (TC) {
-        apply_mma<K>(Yp, RSA, C4, Mg);
+        apply_mma<K>(Yp, RS, C4, Mg);
       } else {
         // task: one float4 column chunk, half of the rows.  The two tasks of a chunk
         // are neighbouring lanes of one warp in the same round, so a warp barrier
@@ -934,7 +941,7 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
         const bool hz = c4 >= C4;
         float *Zb = (hz ? a.Zh : a.Zv) + ((hz ? c4 - C4 : c4) << 2);
         for (int r = wk.r0; r < n; r += wk.rs) {
-          const float4 y = lds4(Yp + (size_t)r * RSA + (c4 << 2));
+          const float4 y = lds4(Yp + (size_t)r * RS + (c4 << 2));
           __stcs(reinterpret_cast<float4 *>(Yl + (size_t)r * 2 * N3p) + c4, y);
           atomicAdd(reinterpret_cast<float4 *>(Zb + (size_t)s_off[b][r] * N3p), y);
         }
@@ -947,10 +954,14 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
 
 using KernelFn = void (*)(BlockDualArgs);
 
+// Variants compiled: both forms for 5 and 4 CTAs per SM (null for others; a
+// six-CTA tensor-core variant fits in shared memory but its 80 registers spill
+// and it ran slower).
 template <int K>
 KernelFn kernel_k(int minb, int tc) {
-  if (tc) return minb >= 5 ? block_dual_kernel<K, 5, true> : block_dual_kernel<K, 4, true>;
-  return minb >= 5 ? block_dual_kernel<K, 5, false> : block_dual_kernel<K, 4, false>;
+  if (minb != 5 && minb != 4) return nullptr;
+  if (tc) return minb == 5 ? block_dual_kernel<K, 5, true> : block_dual_kernel<K, 4, true>;
+  return minb == 5 ? block_dual_kernel<K, 5, false> : block_dual_kernel<K, 4, false>;
 }
 
 KernelFn kernel_for(const BdVariant &v) {
@@ -965,14 +976,13 @@ KernelFn kernel_for(const BdVariant &v) {
 }
 
 template <int K, bool TC>
-size_t smem_k(int rs, int rs2) {
-  const int rsy = rs > rs2 ? rs : rs2;
-  return sizeof(float) * (yp_floats<K>(rsy) + kNW * gm_floats<K, TC>() + tiles_floats<K, TC>());
+size_t smem_k(int rs) {
+  return sizeof(float) * (yp_floats<K, TC>(rs) + kNW * gm_floats<K, TC>() + (TC ? 0 : tiles_floats<K, TC>()));
 }
 
 template <int K>
-size_t smem_kt(int tc, int rs, int rs2) {
-  return tc ? smem_k<K, true>(rs, rs2) : smem_k<K, false>(rs, rs2);
+size_t smem_kt(int tc, int rs) {
+  return tc ? smem_k<K, true>(rs) : smem_k<K, false>(rs);
 }
 
 }  // namespace
@@ -988,20 +998,13 @@ long long block_dual_w_stride(int k) {
   }
 }
 
-// 2 N3p plus padding to 4 mod 32 words: the Gram's reads (8 rows x 4
-// consecutive columns per warp access) hit 32 distinct banks.
+// 2 N3p plus padding to 12 mod 32 words: the Gram's reads (8 rows x 4
+// consecutive columns, or 8 rows x one float4, per warp access) and the
+// tensor-core apply's reads (4 rows x 8 consecutive columns) spread over the
+// banks (the apply's with 2-way conflicts on 4 of them).
 int block_dual_row_stride(int N3p) {
   const int base = 2 * N3p;
-  const int pad = ((4 - base % 32) + 32) % 32;
-  return base + pad;
-}
-
-// Tensor-core apply: 2 N3p plus padding to 8 mod 32 words, so its reads (4 rows
-// x 8 consecutive columns per warp access) hit 32 distinct banks.
-int block_dual_apply_stride(int N3p, int tc) {
-  if (!tc) return block_dual_row_stride(N3p);
-  const int base = 2 * N3p;
-  const int pad = ((8 - base % 32) + 32) % 32;
+  const int pad = ((12 - base % 32) + 32) % 32;
   return base + pad;
 }
 
@@ -1010,16 +1013,18 @@ int block_dual_threads() { return kNW * 32; }
 int block_dual_group() { return kNW; }
 
 size_t block_dual_smem_bytes(const BdVariant &v, int N3p) {
-  const int rs = block_dual_row_stride(N3p), rs2 = block_dual_apply_stride(N3p, v.tc);
+  const int rs = block_dual_row_stride(N3p);
   switch (v.k) {
-    case 1: return smem_kt<1>(v.tc, rs, rs2);
-    case 2: return smem_kt<2>(v.tc, rs, rs2);
-    case 3: return smem_kt<3>(v.tc, rs, rs2);
-    case 4: return smem_kt<4>(v.tc, rs, rs2);
-    case 5: return smem_kt<5>(v.tc, rs, rs2);
+    case 1: return smem_kt<1>(v.tc, rs);
+    case 2: return smem_kt<2>(v.tc, rs);
+    case 3: return smem_kt<3>(v.tc, rs);
+    case 4: return smem_kt<4>(v.tc, rs);
+    case 5: return smem_kt<5>(v.tc, rs);
     default: return 0;
   }
 }
+
+bool block_dual_has(const BdVariant &v) { return kernel_for(v) != nullptr; }
 
 cudaError_t block_dual_prepare(const BdVariant &v, size_t smem) {
   KernelFn f = kernel_for(v);

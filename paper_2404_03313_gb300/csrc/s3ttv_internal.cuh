@@ -121,8 +121,7 @@ struct BlockDualArgs {
   float *Zv, *Zh;         // accumulated with +=
   Dims dm;
   float gY;
-  int rs;                 // shared-memory row stride (floats) while forming Y' and G
-  int rs2;                // shared-memory row stride (floats) while applying M
+  int rs;                 // shared-memory row stride (floats) of the block copies
   int max_sweeps;
   float tol;
   Scalars *sc;            // done flag and the non-convergence counter
@@ -142,13 +141,13 @@ struct BdVariant {
 };
 // Row strides (floats) of the shared block copies for N3p bands.
 int block_dual_row_stride(int N3p);
-int block_dual_apply_stride(int N3p, int tc);
 size_t block_dual_smem_bytes(const BdVariant &v, int N3p);
 int block_dual_threads();
 // blocks one CTA of the block-dual kernel takes at a time
 int block_dual_group();
 // All return cudaErrorInvalidValue for an unsupported variant.
 cudaError_t launch_block_dual(const BlockDualArgs &a, const BdVariant &v, int grid, size_t smem, cudaStream_t st);
+bool block_dual_has(const BdVariant &v);  // compiled in this build
 cudaError_t block_dual_prepare(const BdVariant &v, size_t smem_bytes);
 cudaError_t block_dual_occupancy(const BdVariant &v, size_t smem_bytes, int *ctas_per_sm);
 
