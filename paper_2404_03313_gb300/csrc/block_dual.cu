@@ -954,13 +954,13 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
 
 using KernelFn = void (*)(BlockDualArgs);
 
-// Variants compiled: both forms for 5 and 4 CTAs per SM (null for others; a
-// six-CTA tensor-core variant fits in shared memory but its 80 registers spill
-// and it ran slower).
+// Variants compiled (null for the others): the CUDA-core form for 5 and 4 CTAs
+// per SM; the tensor-core form for 4 only (its five- and six-CTA variants fit
+// in shared memory, but at 96 and 80 registers they spill and ran slower).
 template <int K>
 KernelFn kernel_k(int minb, int tc) {
+  if (tc) return minb == 4 ? block_dual_kernel<K, 4, true> : nullptr;
   if (minb != 5 && minb != 4) return nullptr;
-  if (tc) return minb == 5 ? block_dual_kernel<K, 5, true> : block_dual_kernel<K, 4, true>;
   return minb == 5 ? block_dual_kernel<K, 5, false> : block_dual_kernel<K, 4, false>;
 }
 
