@@ -168,6 +168,36 @@ int s3ttv_solve(s3ttv_ctx *ctx, const float *v, int N1, int N2, int N3,
                 int k, int max_iter, float tol,
                 float *u, float *s, float *t, s3ttv_info *info);
 
+/* One problem of a batch for s3ttv_solve_batched: the arguments s3ttv_solve
+ * takes for one cube (same meaning, layout and checks). */
+typedef struct s3ttv_problem {
+  const float *v;          /* observed cube [N1][N2][N3], host or device           */
+  int N1, N2, N3;
+  float eps, alpha, beta;  /* radii of the three constraint sets                   */
+  float mu_min, mu_max;    /* box of u                                             */
+  int k;                   /* block side                                           */
+  float *u, *s, *t;        /* outputs (u required; s, t may be NULL), host or device */
+} s3ttv_problem;
+
+/* Solve n independent problems (cubes of different sizes and block sides) with
+ * Alg. 1, each exactly as s3ttv_solve would solve it alone (the same passes, the
+ * stop rule eq. StopCri_simulated applied to each problem on its own), but
+ * concurrently: every problem has its own workspace and stream inside ctx
+ * (created on first use, kept for later calls, released by s3ttv_destroy), and
+ * one chunk of S3TTV_OPT_CHECK_EVERY passes (rounded up to even) of every
+ * problem is recorded once as a CUDA graph and replayed, one graph launch per
+ * chunk.  Options set on ctx apply to every problem (profiling excepted).  The
+ * paper has no counterpart: it denoises one scene at a time.
+ *
+ * problems: n >= 1 descriptions; max_iter >= 1 and tol >= 0 as in s3ttv_solve.
+ * infos: NULL or n reports; infos[i].status is problem i's result.
+ * Returns S3TTV_OK when every problem's stop rule fired, S3TTV_MAXITER when
+ * some problem reached max_iter first (all results valid), or the first
+ * negative status (s3ttv_last_error names the problem); a problem whose setup
+ * fails leaves its outputs unwritten. */
+int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, int max_iter, float tol,
+                        s3ttv_info *infos);
+
 /* Stepping interface (the same solver, split so a caller can time passes,
  * inspect or replace the state).  s3ttv_setup loads a problem (same arguments and
  * checks as s3ttv_solve) and sets the initial values; s3ttv_iterate runs up to n

@@ -36,6 +36,14 @@ class Info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Problem(ctypes.Structure):
+    """s3ttv_problem: one cube of a batched solve."""
+    _fields_ = [("v", _vp), ("N1", ctypes.c_int), ("N2", ctypes.c_int), ("N3", ctypes.c_int),
+                ("eps", ctypes.c_float), ("alpha", ctypes.c_float), ("beta", ctypes.c_float),
+                ("mu_min", ctypes.c_float), ("mu_max", ctypes.c_float), ("k", ctypes.c_int),
+                ("u", _vp), ("s", _vp), ("t", _vp)]
+
+
 _P = ctypes.POINTER
 SIGNATURES = {
     "s3ttv_create": (_c_int, [_P(_vp), _c_int, _vp]),
@@ -48,6 +56,7 @@ SIGNATURES = {
     "s3ttv_kernel_stats": (_c_int, [_vp, _P(_c_d), _P(_c_ll)]),
     "s3ttv_solve": (_c_int, [_vp, _vp, _c_int, _c_int, _c_int, _c_f, _c_f, _c_f, _c_f, _c_f, _c_int, _c_int,
                              _c_f, _vp, _vp, _vp, _P(Info)]),
+    "s3ttv_solve_batched": (_c_int, [_vp, _c_int, _P(Problem), _c_int, _c_f, _P(Info)]),
     "s3ttv_setup": (_c_int, [_vp, _vp, _c_int, _c_int, _c_int, _c_f, _c_f, _c_f, _c_f, _c_f, _c_int]),
     "s3ttv_iterate": (_c_int, [_vp, _c_int, _c_f, _P(Info)]),
     "s3ttv_get_state": (_c_int, [_vp, _c_int, _vp]),
@@ -231,6 +240,29 @@ class Solver:
         self._check(rc, "s3ttv_solve")
         self.shape, self.k = (N1, N2, N3), k
         return u, s, t, info.as_dict()
+
+    def solve_batched(self, problems, max_iter=5000, tol=1e-5):
+        """Solve several cubes at once (s3ttv_solve_batched).  problems: a list of
+        dicts with keys v (N1, N2, N3), eps, alpha, beta, k and optionally mu_min,
+        mu_max.  Returns a list of (u, s, t, info dict), outputs shaped and placed
+        like each v."""
+        n = len(problems)
+        arr = (Problem * n)()
+        outs = []
+        for i, p in enumerate(problems):
+            v = p["v"]
+            N1, N2, N3 = v.shape
+            m = N1 * N2 * N3
+            u, s, t = (_empty_like(v, v.shape) for _ in range(3))
+            outs.append((u, s, t))
+            arr[i] = Problem(_ptr(v, m, "v"), N1, N2, N3, p["eps"], p["alpha"], p["beta"],
+                             p.get("mu_min", 0.0), p.get("mu_max", 1.0), p["k"],
+                             _ptr(u, m, "u"), _ptr(s, m, "s"), _ptr(t, m, "t"))
+        infos = (Info * n)()
+        _sync_torch(*[p["v"] for p in problems])
+        rc = self._lib.s3ttv_solve_batched(self._h, n, arr, int(max_iter), float(tol), infos)
+        self._check(rc, "s3ttv_solve_batched")
+        return [(u, s, t, infos[i].as_dict()) for i, (u, s, t) in enumerate(outs)]
 
     def setup(self, v, eps, alpha, beta, k, mu_min=0.0, mu_max=1.0):
         N1, N2, N3 = v.shape

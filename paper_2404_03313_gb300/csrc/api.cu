@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "s3ttv.h"
 #include "s3ttv_internal.cuh"
@@ -53,12 +54,15 @@ struct s3ttv_ctx {
   int ev_passes = 0;
   double prof_ms[S3TTV_KERNEL_CLASSES] = {0, 0, 0, 0, 0};
   long long prof_n[S3TTV_KERNEL_CLASSES] = {0, 0, 0, 0, 0};
+  // batched solves: one member context (workspace and stream) per problem
+  std::vector<s3ttv_ctx *> members;
 };
 
 namespace {
 
 constexpr int kMaxGrid = 4096;
 constexpr int kMaxK = 5;
+constexpr int kLaunchesPerPass = 10;  // kernels enqueue_pass launches
 
 int fail(s3ttv_ctx *c, int status, const char *fmt, ...) {
   if (c) {
@@ -441,7 +445,7 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   fa.g3 = ctx->gam[5];
   CU(launch_finalize(fa, st));
   if (ev) CU(cudaEventRecord(ev[5], st));
-  ctx->launches += 10;
+  ctx->launches += kLaunchesPerPass;
   return S3TTV_OK;
 }
 
@@ -555,6 +559,8 @@ int s3ttv_create(s3ttv_ctx **out, int device, void *stream) {
 
 void s3ttv_destroy(s3ttv_ctx *ctx) {
   if (!ctx) return;
+  for (s3ttv_ctx *m : ctx->members) s3ttv_destroy(m);
+  ctx->members.clear();
   {
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
@@ -804,6 +810,191 @@ int s3ttv_solve(s3ttv_ctx *ctx, const float *v, int N1, int N2, int N3, float ep
     info->seconds = now_s() - t0;
   }
   return st;
+}
+
+namespace {
+
+// Fork from ctx->stream into every member stream and join back (events owned by
+// the caller), so work enqueued on the members orders after, and before, the
+// work on ctx->stream.
+struct ForkJoin {
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  ~ForkJoin() {
+    if (fork) cudaEventDestroy(fork);
+    for (cudaEvent_t e : join)
+      if (e) cudaEventDestroy(e);
+  }
+  cudaError_t create(size_t n) {
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    join.assign(n, nullptr);
+    for (size_t i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
+    return e;
+  }
+};
+
+// Enqueue `passes` passes of every member (member i starting at parity par[i])
+// between a fork from and a join into ctx->stream.
+int enqueue_batch(s3ttv_ctx *ctx, int n, const std::vector<BdShape> &bd, const std::vector<int> &grid_e,
+                  const std::vector<int> &par, int passes, ForkJoin &fj) {
+  CU(cudaEventRecord(fj.fork, ctx->stream));
+  for (int i = 0; i < n; ++i) {
+    s3ttv_ctx *m = ctx->members[i];
+    CU(cudaStreamWaitEvent(m->stream, fj.fork, 0));
+    for (int c = 0; c < passes; ++c) {
+      const int rc = enqueue_pass(m, par[i] ^ (c & 1), grid_e[i], bd[i], nullptr);
+      if (rc) return fail(ctx, rc, "problem %d: %s", i, m->err);
+    }
+    CU(cudaEventRecord(fj.join[i], m->stream));
+    CU(cudaStreamWaitEvent(ctx->stream, fj.join[i], 0));
+  }
+  return S3TTV_OK;
+}
+
+}  // namespace
+
+int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, int max_iter, float tol,
+                        s3ttv_info *infos) {
+  const double t0 = now_s();
+  if (!ctx) return S3TTV_EINVAL;
+  if (n < 1) return fail(ctx, S3TTV_EINVAL, "n = %d must be >= 1", n);
+  if (infos) memset(infos, 0, sizeof(*infos) * (size_t)n);
+  if (!problems) return fail(ctx, S3TTV_EINVAL, "problems is NULL");
+  if (max_iter < 1) return fail(ctx, S3TTV_EINVAL, "max_iter = %d must be >= 1", max_iter);
+  if (!(tol >= 0.f) || !std::isfinite(tol)) return fail(ctx, S3TTV_EINVAL, "tol must be finite and >= 0");
+  for (int i = 0; i < n; ++i)
+    if (!problems[i].u) {
+      if (infos) infos[i].status = S3TTV_EINVAL;
+      return fail(ctx, S3TTV_EINVAL, "problem %d: u is NULL", i);
+    }
+  DeviceGuard g(ctx->device);
+  while ((int)ctx->members.size() < n) {
+    s3ttv_ctx *m = nullptr;
+    const int rc = s3ttv_create(&m, ctx->device, nullptr);
+    if (rc) return fail(ctx, rc, "creating the workspace of problem %zu failed", ctx->members.size());
+    ctx->members.push_back(m);
+  }
+  std::vector<BdShape> bd(n);
+  std::vector<int> grid_e(n), par(n, 0), iter0(n, 0);
+  for (int i = 0; i < n; ++i) {
+    s3ttv_ctx *m = ctx->members[i];
+    m->step_policy = ctx->step_policy;
+    m->jacobi_max_sweeps = ctx->jacobi_max_sweeps;
+    m->jacobi_tol = ctx->jacobi_tol;
+    m->tensor_cores = ctx->tensor_cores;
+    m->warm_start = ctx->warm_start;
+    m->profile = false;
+    const s3ttv_problem &p = problems[i];
+    int rc = s3ttv_setup(m, p.v, p.N1, p.N2, p.N3, p.eps, p.alpha, p.beta, p.mu_min, p.mu_max, p.k);
+    if (!rc) rc = block_dual_shape(m, m->dm, m->k, &bd[i]);
+    if (rc) {
+      if (infos) infos[i].status = rc;
+      return fail(ctx, rc, "problem %d: %s", i, m->err);
+    }
+    grid_e[i] = elementwise_grid(m, m->dm.Np);
+    begin_iterate_kernel<<<1, 1, 0, m->stream>>>(m->sc, max_iter, tol);
+    CU(cudaGetLastError());
+    m->launches += 1;
+  }
+  // one chunk of passes of every problem, recorded as a graph (an even number
+  // of passes returns every problem to its starting parity)
+  const int chunk = (ctx->check_every + 1) & ~1;
+  ForkJoin fj;
+  CU(fj.create(n));
+  cudaGraphExec_t exec = nullptr;
+  std::vector<long long> launches0(n);
+  // the legacy default streams cannot be captured: then every chunk is enqueued
+  const bool capturable = ctx->stream != nullptr && ctx->stream != cudaStreamLegacy && ctx->stream != cudaStreamPerThread;
+  if (max_iter >= chunk && capturable) {
+    for (int i = 0; i < n; ++i) launches0[i] = ctx->members[i]->launches;
+    CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_batch(ctx, n, bd, grid_e, par, chunk, fj);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(ctx->stream, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return rc;
+    }
+    CU(ec);
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CU(ei);
+    for (int i = 0; i < n; ++i) ctx->members[i]->launches = launches0[i];  // recorded, not run
+  }
+  std::vector<Scalars> hs(n);
+  int enq = 0, rc = S3TTV_OK;
+  while (enq < max_iter) {
+    const int step = max_iter - enq >= chunk ? chunk : max_iter - enq;
+    if (step == chunk && exec) {
+      const cudaError_t e = cudaGraphLaunch(exec, ctx->stream);
+      if (e != cudaSuccess) {
+        rc = fail(ctx, S3TTV_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+        break;
+      }
+      for (int i = 0; i < n; ++i) ctx->members[i]->launches += (long long)kLaunchesPerPass * chunk;
+    } else {
+      if ((rc = enqueue_batch(ctx, n, bd, grid_e, par, step, fj))) break;
+      for (int i = 0; i < n; ++i) par[i] ^= step & 1;
+    }
+    enq += step;
+    for (int i = 0; i < n; ++i) {
+      const cudaError_t e = cudaMemcpyAsync(&hs[i], ctx->members[i]->sc, sizeof(Scalars), cudaMemcpyDeviceToHost,
+                                            ctx->stream);
+      if (e != cudaSuccess) rc = fail(ctx, S3TTV_ECUDA, "reading problem %d's scalars: %s", i, cudaGetErrorString(e));
+    }
+    if (rc) break;
+    const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+      rc = fail(ctx, S3TTV_ECUDA, "batched passes: %s", cudaGetErrorString(e));
+      break;
+    }
+    bool all_done = true;
+    for (int i = 0; i < n; ++i) all_done = all_done && hs[i].done;
+    if (all_done) break;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (rc) return rc;
+  // results: each problem's outputs on its own stream, then one wait
+  int result = S3TTV_OK;
+  for (int i = 0; i < n; ++i) {
+    s3ttv_ctx *m = ctx->members[i];
+    const int done_iters = hs[i].iter - iter0[i];
+    m->parity = done_iters & 1;
+    int status;
+    if (hs[i].status == -4) {
+      status = S3TTV_ENUMERIC;
+      fail(m, S3TTV_ENUMERIC, "NaN or Inf after %d passes", done_iters);
+    } else {
+      status = hs[i].status == 1 ? S3TTV_OK : S3TTV_MAXITER;
+    }
+    if (status >= 0) {
+      const s3ttv_problem &p = problems[i];
+      int r = store_cube(m, m->u, p.u, nullptr);
+      if (!r && p.s) r = store_cube(m, m->s, p.s, nullptr);
+      if (!r && p.t) r = store_cube(m, m->t[m->parity], p.t, nullptr);
+      if (r) status = r;
+    }
+    if (infos) {
+      infos[i].status = status;
+      infos[i].iters = done_iters;
+      infos[i].converged = hs[i].status == 1;
+      infos[i].jacobi_nonconverged = (int)hs[i].jacobi_fail;
+      infos[i].rel_change = hs[i].rel;
+      infos[i].jacobi_sweeps =
+          done_iters > 0 ? (double)hs[i].jacobi_sweeps / ((double)done_iters * m->dm.P) : 0.0;
+    }
+    if (status < 0 && result >= 0) result = fail(ctx, status, "problem %d: %s", i, m->err);
+    else if (status == S3TTV_MAXITER && result == S3TTV_OK) result = S3TTV_MAXITER;
+  }
+  for (int i = 0; i < n; ++i) {
+    const cudaError_t e = cudaStreamSynchronize(ctx->members[i]->stream);
+    if (e != cudaSuccess && result >= 0) result = fail(ctx, S3TTV_ECUDA, "problem %d: %s", i, cudaGetErrorString(e));
+  }
+  const double secs = now_s() - t0;
+  if (infos)
+    for (int i = 0; i < n; ++i) infos[i].seconds = secs;
+  return result;
 }
 
 int s3ttv_l1_ball(s3ttv_ctx *ctx, const float *x, float *out, long long n, double radius, double *tau_out) {

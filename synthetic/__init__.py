@@ -32,7 +32,7 @@ from __future__ import annotations
 import dataclasses
 import numpy as np
 
-__all__ = ["CubeSpec", "make_cube", "WORKLOADS", "random_state"]
+__all__ = ["CubeSpec", "make_cube", "WORKLOADS", "random_state", "batch_specs"]
 
 
 @dataclasses.dataclass(frozen=True)
@@ -64,6 +64,28 @@ WORKLOADS = {
     "profile_128x128x128_k5": CubeSpec(128, 128, 128, regions=16, endmembers=5, sigma=0.05,
                                        p_s=0.05, p_t=0.10, k=5, seed=0),
 }
+
+
+def batch_specs(count: int = 64, seed: int = 0, size_range=(64, 256)):
+    """An uneven batch of cubes: the shape and noise of cube i come from one
+    batch generator seeded with `seed`, its contents from seed 1000 + i.
+
+    N1, N2 ~ U{lo..hi} (size_range), N3 from {31, 64, 128, 191}, sigma from
+    {0.05, 0.1}, p_s = 0.05, p_t from {0, 0.05, 0.10}, k from {3, 5},
+    R = max(4, N1 N2 // 2048) regions, M = 5 endmembers.
+    """
+    rng = np.random.default_rng(seed)
+    lo, hi = size_range
+    specs = []
+    for i in range(count):
+        N1, N2 = (int(x) for x in rng.integers(lo, hi + 1, size=2))
+        N3 = int(rng.choice([31, 64, 128, 191]))
+        sigma = float(rng.choice([0.05, 0.1]))
+        p_t = float(rng.choice([0.0, 0.05, 0.10]))
+        k = int(rng.choice([3, 5]))
+        specs.append(CubeSpec(N1, N2, N3, regions=max(4, N1 * N2 // 2048), endmembers=5, sigma=sigma,
+                              p_s=0.05, p_t=p_t, k=k, seed=1000 + i))
+    return specs
 
 
 def _endmembers(rng: np.random.Generator, M: int, N3: int) -> np.ndarray:

@@ -59,6 +59,7 @@ def test_invalid_arguments_rejected_on_host(lib):
     g = (ctypes.c_double * 6)()
     assert lib.s3ttv_step_sizes(4, 4, 2, 7, g) == -1
     assert lib.s3ttv_create(None, 0, None) == -1
+    assert lib.s3ttv_solve_batched(None, 1, None, 10, 0.0, None) == -1
     assert lib.s3ttv_strerror(-4).decode() == "NaN or Inf in the iterates"
 
 
