@@ -137,8 +137,9 @@ int s3ttv_set_option(s3ttv_ctx *ctx, int key, double value);
 /* Bytes of device workspace the context holds now. */
 long long s3ttv_workspace_bytes(const s3ttv_ctx *ctx);
 
-/* Number of kernels the passes of Alg. 1 (s3ttv_iterate, s3ttv_solve) have
- * launched on this context since it was created (10 per pass, plus one per call). */
+/* Number of kernels the passes of Alg. 1 (s3ttv_iterate, s3ttv_solve,
+ * s3ttv_solve_batched) have launched on this context since it was created (10
+ * per pass of each problem, plus one per problem and call). */
 long long s3ttv_launch_count(const s3ttv_ctx *ctx);
 
 /* With S3TTV_OPT_PROFILE on: total device milliseconds (ms[c]) and launches

@@ -517,7 +517,12 @@ const char *s3ttv_last_error(const s3ttv_ctx *ctx) { return ctx ? ctx->err : "nu
 
 long long s3ttv_workspace_bytes(const s3ttv_ctx *ctx) { return ctx ? (long long)ctx->bytes : 0; }
 
-long long s3ttv_launch_count(const s3ttv_ctx *ctx) { return ctx ? ctx->launches : 0; }
+long long s3ttv_launch_count(const s3ttv_ctx *ctx) {
+  if (!ctx) return 0;
+  long long n = ctx->launches;
+  for (const s3ttv_ctx *m : ctx->members) n += m->launches;  // batched solves
+  return n;
+}
 
 int s3ttv_kernel_stats(const s3ttv_ctx *ctx, double *ms, long long *launches) {
   if (!ctx) return S3TTV_EINVAL;

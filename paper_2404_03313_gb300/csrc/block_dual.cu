@@ -1026,10 +1026,23 @@ size_t block_dual_smem_bytes(const BdVariant &v, int N3p) {
 
 bool block_dual_has(const BdVariant &v) { return kernel_for(v) != nullptr; }
 
+// The launch limit is a property of the kernel, shared by every context and
+// problem that launches it, so it is raised to the device's opt-in maximum
+// (the launch's own request decides what a CTA gets) rather than to one
+// problem's size, which a later, smaller problem would lower again.
 cudaError_t block_dual_prepare(const BdVariant &v, size_t smem) {
   KernelFn f = kernel_for(v);
   if (!f) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(reinterpret_cast<const void *>(f), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, cap = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void *>(f));
+  if (e != cudaSuccess) return e;
+  const size_t dyn = (size_t)cap > fa.sharedSizeBytes ? (size_t)cap - fa.sharedSizeBytes : 0;  // minus static
+  if (dyn < smem) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(reinterpret_cast<const void *>(f), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)dyn);
 }
 
 cudaError_t block_dual_occupancy(const BdVariant &v, size_t smem, int *ctas) {

@@ -94,3 +94,15 @@ def test_invalid_problem_is_named(P):
         with pytest.raises(P.S3TTVError) as e:
             s.solve_batched(probs, max_iter=5)
     assert e.value.status == P.EINVAL and "problem 1" in str(e.value)
+
+
+def test_problems_that_need_different_shared_memory(P):
+    """Cubes whose block-dual CTAs need different amounts of shared memory (band
+    counts 191 and 8, the smaller set up last) launch side by side."""
+    specs = [CubeSpec(10, 9, 191, regions=2, k=5, seed=5), CubeSpec(11, 10, 8, regions=2, k=5, seed=6)]
+    probs = _problems(specs)
+    with P.Solver(0) as s:
+        out = s.solve_batched(probs, max_iter=4, tol=0.0)
+        alone = [s.solve(p["v"], p["eps"], p["alpha"], p["beta"], p["k"], max_iter=4, tol=0.0) for p in probs]
+    for o, a in zip(out, alone):
+        assert rel(o[0].cpu().numpy(), a[0].cpu().numpy()) <= 1e-6
