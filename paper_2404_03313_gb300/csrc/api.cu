@@ -225,8 +225,10 @@ struct BdShape {
 };
 
 int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, BdShape *sh) {
-  if (dm.P > 2147483647LL)  // the kernel indexes pixels with 32-bit integers
+  if (dm.P > 2147483647LL)  // the kernels index pixels with 32-bit integers
     return fail(ctx, S3TTV_EUNSUPPORTED, "N1 * N2 = %lld pixels: this build supports fewer than 2^31", dm.P);
+  if (dm.Np / 4 > 2147483647LL)  // and float4 chunks of bands with 32-bit integers
+    return fail(ctx, S3TTV_EUNSUPPORTED, "%lld voxels: this build supports fewer than 2^33", dm.Np);
   sh->v.k = k;
   sh->v.tc = ctx->tensor_cores;
   sh->rs = block_dual_row_stride(dm.N3p);

@@ -39,6 +39,14 @@ __device__ __forceinline__ void hist_add(unsigned *cnt, float *sum, float z) {
   atomicAdd(&sum[key], __uint_as_float(bits));
 }
 
+// Work unit of primal_kernel and dual_kernel: one float4 chunk (4 consecutive
+// bands) of one pixel; chunk c is pixel c / C4, bands 4 (c mod C4) .. + 3.
+// The host admits cubes of fewer than 2^31 chunks, so the index arithmetic is
+// 32-bit.
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ float comp(const float4 &v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+
 // Alg. 1 steps 2-7 for u, and the arguments of the projections of steps 3-4.
 //   u+   = P_[lo,hi](u - gu (D_s^T (D_v^T Zv + D_h^T Zh) + y3))     (step 2)
 //   ubar = 2 u+ - u                                                  (step 5)
@@ -57,44 +65,56 @@ __global__ void __launch_bounds__(256) primal_kernel(PrimalArgs a) {
   }
   __syncthreads();
   const Dims dm = a.dm;
-  const long long N3p = dm.N3p;
+  const int N3p = dm.N3p, C4 = N3p >> 2, N2 = dm.N2;
+  const int nch = (int)(dm.P * C4);
   const float c3 = (float)a.sc->c3;
   float du2 = 0.f, u2 = 0.f;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < dm.Np; idx += stride) {
-    const long long pix = idx / N3p;
-    const int b = (int)(idx - pix * N3p);
-    a.Znv[idx] = 0.f;
-    a.Znh[idx] = 0.f;
-    if (b >= dm.N3) {
-      a.ubar[idx] = 0.f;
-      a.zs[idx] = 0.f;
-      a.zt[idx] = 0.f;
-      continue;
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += gridDim.x * blockDim.x) {
+    const int pix = (unsigned)c / (unsigned)C4, q = c - pix * C4, b0 = q << 2;
+    const int i = (unsigned)pix / (unsigned)N2, j = pix - i * N2;
+    const size_t p0 = (size_t)pix * N3p + b0;
+    const size_t pim = ((size_t)(i == 0 ? dm.N1 - 1 : i - 1) * N2 + j) * N3p + b0;
+    const size_t pjm = ((size_t)i * N2 + (j == 0 ? N2 - 1 : j - 1)) * N3p + b0;
+    st4(a.Znv + p0, zero4);
+    st4(a.Znh + p0, zero4);
+    // w = D_v^T Zv + D_h^T Zh at bands b0..b0+3 and at the band before b0
+    // (periodic over the N3 true bands)
+    const float4 zv = ld4(a.Zv + p0), zvm = ld4(a.Zv + pim), zh = ld4(a.Zh + p0), zhm = ld4(a.Zh + pjm);
+    const float w[4] = {(zvm.x - zv.x) + (zhm.x - zh.x), (zvm.y - zv.y) + (zhm.y - zh.y),
+                        (zvm.z - zv.z) + (zhm.z - zh.z), (zvm.w - zv.w) + (zhm.w - zh.w)};
+    const long long o = (b0 == 0 ? dm.N3 - 1 : b0 - 1) - b0;  // to the band before (periodic)
+    const float wbm = (a.Zv[(long long)pim + o] - a.Zv[(long long)p0 + o]) +
+                      (a.Zh[(long long)pjm + o] - a.Zh[(long long)p0 + o]);
+    const float4 d4 = ld4(a.d + p0), u4 = ld4(a.u + p0), s4 = ld4(a.s + p0), t4 = ld4(a.t + p0);
+    const float4 y2c = ld4(a.y2 + p0), y2m = ld4(a.y2 + pim);
+    float un[4], ub[4], zs[4], zt[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (b0 + e < dm.N3) {
+        const float grad = (e == 0 ? wbm : w[e - 1]) - w[e];  // (D_s^T w)[b] = w[b-1] - w[b]
+        const float y3 = c3 * comp(d4, e);
+        const float u = comp(u4, e);
+        const float x = u - a.gu * (grad + y3);
+        const float v = (x != x) ? x : fminf(fmaxf(x, a.lo), a.hi);  // NaN stays visible
+        un[e] = v;
+        ub[e] = 2.f * v - u;
+        zs[e] = comp(s4, e) - a.gs * y3;
+        zt[e] = comp(t4, e) - a.gt * ((comp(y2m, e) - comp(y2c, e)) + y3);
+        const float dl = v - u;
+        du2 = fmaf(dl, dl, du2);
+        u2 = fmaf(u, u, u2);
+        hist_add(s_cnt, s_sum, zs[e]);
+        hist_add(s_cnt + kHistBins, s_sum + kHistBins, zt[e]);
+      } else {  // padding bands stay 0
+        un[e] = comp(u4, e);
+        ub[e] = zs[e] = zt[e] = 0.f;
+      }
     }
-    const int i = (int)(pix / dm.N2), j = (int)(pix - (long long)i * dm.N2);
-    const long long pim = ((long long)(i == 0 ? dm.N1 - 1 : i - 1) * dm.N2 + j) * N3p;
-    const long long pjm = ((long long)i * dm.N2 + (j == 0 ? dm.N2 - 1 : j - 1)) * N3p;
-    const long long p0 = pix * N3p;
-    const int bm = b == 0 ? dm.N3 - 1 : b - 1;
-    const float w_b = (a.Zv[pim + b] - a.Zv[p0 + b]) + (a.Zh[pjm + b] - a.Zh[p0 + b]);
-    const float w_bm = (a.Zv[pim + bm] - a.Zv[p0 + bm]) + (a.Zh[pjm + bm] - a.Zh[p0 + bm]);
-    const float grad = w_bm - w_b;  // (D_s^T w)[b] = w[b-1] - w[b]
-    const float y3 = c3 * a.d[idx];
-    const float u = a.u[idx];
-    const float x = u - a.gu * (grad + y3);
-    const float un = (x != x) ? x : fminf(fmaxf(x, a.lo), a.hi);  // NaN stays visible
-    a.u[idx] = un;
-    a.ubar[idx] = 2.f * un - u;
-    const float zs = a.s[idx] - a.gs * y3;
-    const float zt = a.t[idx] - a.gt * ((a.y2[pim + b] - a.y2[idx]) + y3);
-    a.zs[idx] = zs;
-    a.zt[idx] = zt;
-    const float dl = un - u;
-    du2 = fmaf(dl, dl, du2);
-    u2 = fmaf(u, u, u2);
-    hist_add(s_cnt, s_sum, zs);
-    hist_add(s_cnt + kHistBins, s_sum + kHistBins, zt);
+    st4(a.u + p0, make_float4(un[0], un[1], un[2], un[3]));
+    st4(a.ubar + p0, make_float4(ub[0], ub[1], ub[2], ub[3]));
+    st4(a.zs + p0, make_float4(zs[0], zs[1], zs[2], zs[3]));
+    st4(a.zt + p0, make_float4(zt[0], zt[1], zt[2], zt[3]));
   }
   double v[2] = {(double)du2, (double)u2};
   block_sum<2>(v, s_red);
@@ -112,52 +132,59 @@ __global__ void __launch_bounds__(256) primal_kernel(PrimalArgs a) {
   }
 }
 
-// Steps 3-4 finish (soft thresholds found by the radix selection), steps 6-7,
-// step 12 and step 13:
-//   s+ = soft(zs, tau_s), t+ = soft(zt, tau_t), sbar = 2s+ - s, tbar = 2t+ - t,
-//   y2 += g2 D_v tbar,   y3' = y3 + g3 (ubar + sbar + tbar),   d = y3'/g3 - v.
-// Step 14 then sets y3 = g3 max(0, 1 - eps/||d||) d, i.e. only the scalar c3
-// changes (finalize_kernel).  D_v tbar needs tbar of the pixel below, which is
-// recomputed from zt and the old t there, so t is double-buffered.
+// Alg. 1 steps 3-4 finish (soft thresholds), 6-7, 12 and 13:
+//   s+ = S_tau_s(zs), t+ = S_tau_t(zt), sbar = 2 s+ - s, tbar = 2 t+ - t
+//   y2 += g2 D_v tbar                                                (step 12)
+//   y3' = y3 + g3 (ubar + sbar + tbar),  d = y3' / g3 - v            (step 13)
+// (step 14 scales d by the scalar c3 of finalize_kernel), and sum d^2.
 __global__ void __launch_bounds__(256) dual_kernel(DualArgs a) {
   __shared__ double s_red[1][32];
   if (a.sc->done) return;
   const Dims dm = a.dm;
-  const long long N3p = dm.N3p;
+  const int N3p = dm.N3p, C4 = N3p >> 2, N2 = dm.N2;
+  const int nch = (int)(dm.P * C4);
   const float c3 = (float)a.sc->c3;
   const float tau_s = a.sc->l1[0].tau, tau_t = a.sc->l1[1].tau;
   const float tls = a.sc->l1[0].tau_lo, tlt = a.sc->l1[1].tau_lo;
   const float inv_g3 = 1.f / a.g3;
   float d2 = 0.f;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < dm.Np; idx += stride) {
-    const long long pix = idx / N3p;
-    const int b = (int)(idx - pix * N3p);
-    if (b >= dm.N3) {
-      a.t_new[idx] = 0.f;
-      continue;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += gridDim.x * blockDim.x) {
+    const int pix = (unsigned)c / (unsigned)C4, q = c - pix * C4, b0 = q << 2;
+    const int i = (unsigned)pix / (unsigned)N2, j = pix - i * N2;
+    const size_t p0 = (size_t)pix * N3p + b0;
+    const size_t pip = ((size_t)(i + 1 == dm.N1 ? 0 : i + 1) * N2 + j) * N3p + b0;
+    const float4 zs4 = ld4(a.zs + p0), zt4 = ld4(a.zt + p0), ztn = ld4(a.zt + pip);
+    const float4 so4 = ld4(a.s_old + p0), to4 = ld4(a.t_old + p0), ton = ld4(a.t_old + pip);
+    const float4 y24 = ld4(a.y2 + p0), ub4 = ld4(a.ubar + p0), d4 = ld4(a.d + p0), v4 = ld4(a.v + p0);
+    float sp[4], tp[4], y2n[4], dn[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (b0 + e < dm.N3) {
+        sp[e] = soft_threshold(comp(zs4, e), tau_s, tls);
+        const float sbar = 2.f * sp[e] - comp(so4, e);
+        tp[e] = soft_threshold(comp(zt4, e), tau_t, tlt);
+        const float tbar = 2.f * tp[e] - comp(to4, e);
+        const float tbar_n = 2.f * soft_threshold(comp(ztn, e), tau_t, tlt) - comp(ton, e);
+        y2n[e] = fmaf(a.g2, tbar_n - tbar, comp(y24, e));
+        const float y3p = fmaf(a.g3, comp(ub4, e) + sbar + tbar, c3 * comp(d4, e));
+        dn[e] = y3p * inv_g3 - comp(v4, e);
+        d2 = fmaf(dn[e], dn[e], d2);
+      } else {  // padding bands stay 0
+        sp[e] = tp[e] = 0.f;
+        y2n[e] = comp(y24, e);
+        dn[e] = comp(d4, e);
+      }
     }
-    const int i = (int)(pix / dm.N2), j = (int)(pix - (long long)i * dm.N2);
-    const long long pip = ((long long)(i + 1 == dm.N1 ? 0 : i + 1) * dm.N2 + j) * N3p + b;
-    const float sp = soft_threshold(a.zs[idx], tau_s, tls);
-    const float sbar = 2.f * sp - a.s_old[idx];
-    const float tp = soft_threshold(a.zt[idx], tau_t, tlt);
-    const float tbar = 2.f * tp - a.t_old[idx];
-    const float tbar_n = 2.f * soft_threshold(a.zt[pip], tau_t, tlt) - a.t_old[pip];
-    a.y2[idx] = fmaf(a.g2, tbar_n - tbar, a.y2[idx]);
-    const float y3p = fmaf(a.g3, a.ubar[idx] + sbar + tbar, c3 * a.d[idx]);
-    const float dn = y3p * inv_g3 - a.v[idx];
-    a.s_new[idx] = sp;
-    a.t_new[idx] = tp;
-    a.d[idx] = dn;
-    d2 = fmaf(dn, dn, d2);
+    st4(a.s_new + p0, make_float4(sp[0], sp[1], sp[2], sp[3]));
+    st4(a.t_new + p0, make_float4(tp[0], tp[1], tp[2], tp[3]));
+    st4(a.y2 + p0, make_float4(y2n[0], y2n[1], y2n[2], y2n[3]));
+    st4(a.d + p0, make_float4(dn[0], dn[1], dn[2], dn[3]));
   }
   double v[1] = {(double)d2};
   block_sum<1>(v, s_red);
   if (threadIdx.x == 0) a.part[blockIdx.x] = v[0];
 }
 
-// Step 14's scalar (eq. prox_l2ball_constraint through Moreau) and the stop rule.
 __global__ void __launch_bounds__(256) finalize_kernel(FinalizeArgs a) {
   __shared__ double s_red[3][32];
   Scalars *sc = a.sc;
