@@ -290,23 +290,32 @@ __global__ void Z_from_Y_kernel(const float *__restrict__ Y, float *__restrict__
 // structure tensors of eq. (SSST) are cut from, formed once per pass.
 __global__ void xfield_kernel(const float *__restrict__ ubar, float *__restrict__ Fv, float *__restrict__ Fh,
                               Dims dm) {
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < dm.Np; idx += stride) {
-    const long long pix = idx / dm.N3p;
-    const int b = (int)(idx - pix * dm.N3p);
-    if (b >= dm.N3) {
-      Fv[idx] = 0.f;
-      Fh[idx] = 0.f;
-      continue;
+  const int N3p = dm.N3p, C4 = N3p >> 2, N2 = dm.N2;
+  const int nch = (int)(dm.P * C4);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += gridDim.x * blockDim.x) {
+    const int pix = (unsigned)c / (unsigned)C4, q = c - pix * C4, b0 = q << 2;
+    const int i = (unsigned)pix / (unsigned)N2, j = pix - i * N2;
+    const size_t p0 = (size_t)pix * N3p;
+    const size_t pv = ((size_t)(i + 1 == dm.N1 ? 0 : i + 1) * N2 + j) * N3p;
+    const size_t ph = ((size_t)i * N2 + (j + 1 == N2 ? 0 : j + 1)) * N3p;
+    // bands b0..b0+3 and the band after the chunk (periodic over the N3 true bands)
+    const float4 x0 = ld4(ubar + p0 + b0), xv = ld4(ubar + pv + b0), xh = ld4(ubar + ph + b0);
+    const int nb = b0 + 4 < dm.N3 ? b0 + 4 : 0;
+    const float n0 = ubar[p0 + nb], nv = ubar[pv + nb], nh = ubar[ph + nb];
+    float fv[4], fh[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (b0 + e < dm.N3) {
+        const bool in = e < 3 && b0 + e + 1 < dm.N3;
+        const float ds0 = (in ? comp(x0, e + 1) : n0) - comp(x0, e);
+        fv[e] = ((in ? comp(xv, e + 1) : nv) - comp(xv, e)) - ds0;
+        fh[e] = ((in ? comp(xh, e + 1) : nh) - comp(xh, e)) - ds0;
+      } else {
+        fv[e] = fh[e] = 0.f;
+      }
     }
-    const int i = (int)(pix / dm.N2), j = (int)(pix - (long long)i * dm.N2);
-    const int bn = b + 1 == dm.N3 ? 0 : b + 1;
-    const long long p0 = pix * dm.N3p;
-    const long long pv = ((long long)(i + 1 == dm.N1 ? 0 : i + 1) * dm.N2 + j) * dm.N3p;
-    const long long ph = ((long long)i * dm.N2 + (j + 1 == dm.N2 ? 0 : j + 1)) * dm.N3p;
-    const float ds0 = ubar[p0 + bn] - ubar[p0 + b];
-    Fv[idx] = (ubar[pv + bn] - ubar[pv + b]) - ds0;
-    Fh[idx] = (ubar[ph + bn] - ubar[ph + b]) - ds0;
+    st4(Fv + p0 + b0, make_float4(fv[0], fv[1], fv[2], fv[3]));
+    st4(Fh + p0 + b0, make_float4(fh[0], fh[1], fh[2], fh[3]));
   }
 }
 
