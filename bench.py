@@ -45,7 +45,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per voxel of one block-dual launch, from an ncu
 # capture of the kernel whose source hashes to `sha` (profiles/block_dual_k5_*.md);
 # traffic is reported only while the kernel source is unchanged.
-BLOCK_DUAL_TRAFFIC = {"sha": "57351256dbd6b8a5", "k": 5, "bytes_per_voxel": (760.603648e6 + 741.757440e6) / 2097152}
+BLOCK_DUAL_TRAFFIC = {"sha": "8d61c0e5204900a5", "k": 5, "bytes_per_voxel": (593.626880e6 + 611.794176e6) / 2097152}
 
 
 # ---------------------------------------------------------------------------
