@@ -155,8 +155,10 @@ int s3ttv_kernel_stats(const s3ttv_ctx *ctx, double *ms, long long *launches);
  * alpha    radius of the l1 ball of the sparse noise s (eq. constraint_sparse), >= 0.
  * beta     radius of the l1 ball of the stripe noise t (eq. constraint_stripe), >= 0.
  * mu_min, mu_max  box of u (eq. constraint_box), mu_min < mu_max.
- * k        block side (k x k x N3 blocks), 1 <= k <= min(N1, N2); this build supports k <= 5
- *          and N1 * N2 < 2^31, N1 * N2 * N3 < 2^33 (S3TTV_EUNSUPPORTED otherwise).
+ * k        block side (k x k x N3 blocks), 1 <= k <= min(N1, N2); this build supports k <= 12
+ *          (k <= 5 on the tensor-core or CUDA-core per-warp path, 6..12, the paper's
+ *          own 10 x 10 blocks included, on a per-CTA path in FP32) and N1 * N2 < 2^31,
+ *          N1 * N2 * N3 < 2^33 (S3TTV_EUNSUPPORTED otherwise).
  * max_iter iteration cap, >= 1.
  * tol      stop when ||u+ - u||_2 / ||u||_2 < tol (eq. StopCri_simulated), >= 0;
  *          0 runs exactly max_iter passes.

@@ -61,7 +61,7 @@ struct s3ttv_ctx {
 namespace {
 
 constexpr int kMaxGrid = 4096;
-constexpr int kMaxK = 5;
+constexpr int kMaxK = kMaxLargeK;  // k <= 5: block_dual.cu; 6..12: block_dual_large.cu
 constexpr int kLaunchesPerPass = 10;  // kernels enqueue_pass launches
 
 int fail(s3ttv_ctx *c, int status, const char *fmt, ...) {
@@ -222,6 +222,7 @@ struct BdShape {
   size_t smem = 0;  // dynamic shared memory per CTA
   int grid = 0;
   BdVariant v;
+  bool large = false;  // block_dual_large.cu (k > 5)
 };
 
 int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, BdShape *sh) {
@@ -231,6 +232,25 @@ int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, BdShape *sh) {
     return fail(ctx, S3TTV_EUNSUPPORTED, "%lld voxels: this build supports fewer than 2^33", dm.Np);
   sh->v.k = k;
   sh->v.tc = ctx->tensor_cores;
+  if (k >= kMinLargeK) {  // one CTA per block at a time; FP32 CUDA cores whatever the option
+    sh->large = true;
+    sh->smem = block_dual_large_smem_bytes(k);
+    int dev_max = 0;
+    cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    if (sh->smem > (size_t)dev_max)
+      return fail(ctx, S3TTV_EUNSUPPORTED, "a %dx%d block needs %zu bytes of shared memory (device limit %d)", k, k,
+                  sh->smem, dev_max);
+    cudaError_t e = block_dual_large_prepare(sh->smem);
+    if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    int per_sm = 0;
+    e = block_dual_large_occupancy(sh->smem, &per_sm);
+    if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+    if (per_sm < 1) per_sm = 1;
+    long long g = (long long)ctx->num_sms * per_sm;
+    if (g > dm.P) g = dm.P;
+    sh->grid = (int)g;
+    return S3TTV_OK;
+  }
   sh->rs = block_dual_row_stride(dm.N3p);
   sh->smem = block_dual_smem_bytes(sh->v, dm.N3p);
   int dev_max = 0;
@@ -414,7 +434,8 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   ba.W = ctx->warm_start ? ctx->W : nullptr;
   ba.w_stride = ctx->w_stride;
   ba.warm = ctx->warm_start && ctx->warm_valid;
-  CU(launch_block_dual(ba, bd.v, bd.grid, bd.smem, st));
+  if (bd.large) CU(launch_block_dual_large(ba, ctx->k, bd.grid, bd.smem, st));
+  else CU(launch_block_dual(ba, bd.v, bd.grid, bd.smem, st));
   if (ctx->warm_start) ctx->warm_valid = true;
   if (ev) CU(cudaEventRecord(ev[3], st));
 
@@ -1089,7 +1110,8 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   ba.W = nullptr;
   ba.w_stride = 0;
   ba.warm = 0;
-  CU(launch_block_dual(ba, bd.v, bd.grid, bd.smem, ctx->stream));
+  if (bd.large) CU(launch_block_dual_large(ba, k, bd.grid, bd.smem, ctx->stream));
+  else CU(launch_block_dual(ba, bd.v, bd.grid, bd.smem, ctx->stream));
   if ((rc = store_Y(ctx, Y))) return rc;
   if ((rc = store_cube(ctx, ctx->Zv[0], Zv, nullptr))) return rc;
   if ((rc = store_cube(ctx, ctx->Zh[0], Zh, nullptr))) return rc;

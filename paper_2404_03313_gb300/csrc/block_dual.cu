@@ -988,6 +988,7 @@ size_t smem_kt(int tc, int rs) {
 }  // namespace
 
 long long block_dual_w_stride(int k) {
+  if (k >= kMinLargeK) return block_dual_large_w_stride(k);
   switch (k) {
     case 1: return w_floats<1>();
     case 2: return w_floats<2>();

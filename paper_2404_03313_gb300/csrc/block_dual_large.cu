@@ -1,0 +1,451 @@
+// Alg. 1 steps 8-11 for the larger blocks the paper itself uses (Sec. IV sets
+// the block to 10 x 10 pixels; this file takes k = 6..12, n = k^2 = 36..144
+// block rows).  The mathematics is that of block_dual.cu: with
+// Y'_l = Y_l + gamma_Y P_l D D_s ubar and G = Y' Y'^T = sum_x lam_x u_x u_x^T,
+//
+//   Y_l = M Y'_l,   M = I - sum_{lam_x > 1} (1 - lam_x^-1/2) u_x u_x^T,
+//
+// (eq. prox_nuclear_norm through eq. ProxConjugate: the singular values of Y'_l
+// clipped at 1), and Z += P_l^T Y_l.  Only the organisation differs: an n x n
+// eigenproblem no longer fits one warp, and a block's Y' (n x 2 N3p floats) no
+// longer fits shared memory, so one CTA of kLW warps owns one block at a time
+// (a persistent grid strides over the blocks):
+//  1. Y' streams through a shared chunk of kCW columns: Y rows plus gamma_Y F
+//     (F = D D_s ubar, the cubes Fv, Fh), written back over Y_l for step 5, and
+//     accumulated into the Gram by 4 x 4 register tiles of the upper triangle.
+//  2. Warm start: C0 = W G from the block's stored normalized eigen-rows W (a
+//     NaN marker in W starts cold from C0 = G).
+//  3. One-sided (Hestenes) Jacobi on the rows of C, resident in shared memory,
+//     in the round-robin ordering: each of the NPOS - 1 steps of a sweep meets
+//     NPOS / 2 disjoint row pairs, which the warps take in turn (one warp per
+//     pair: a warp-wide dot product, then the rotation of both rows in place);
+//     rows never move, only the pairing changes.  Rows are scaled by an exact
+//     power of two first; the tolerance, the numerical-zero floor and the
+//     rotation formula are those of block_dual.cu.
+//  4. Converged rows are lam_x u_x^T: scaled eigen-rows into shared memory, the
+//     normalized rows into W for the next pass.
+//  5. M = I - Ut^T Ut by 4 x 4 tiles; then Y' streams through the chunk again
+//     and every thread forms a 4 x 4 tile of M Y', stored to Y_l and added into
+//     Z with float4 atomics.
+// FP32 throughout (FP32 FMAs on CUDA cores).
+#include <math.h>
+#include "s3ttv_internal.cuh"
+
+namespace s3ttv {
+namespace {
+
+constexpr int kLW = 16;        // warps per CTA
+constexpr int kLT = kLW * 32;  // threads per CTA
+constexpr int kCW = 64;        // columns of Y' per streamed chunk
+constexpr int kGramTiles = 2;  // upper-triangle Gram tiles a thread may own
+constexpr int kSlots = (kMaxLargeK * kMaxLargeK + 31) / 32;  // row elements a lane holds
+
+struct Layout {
+  int n, npos, gs, cs;  // block rows, rows padded to even, row strides of the n x n buffers and the chunk
+  int nt4;              // 4-row tiles across npos
+  size_t x1, x2, chunk, nrm, pix, total;  // float offsets; total floats
+};
+
+__host__ __device__ inline Layout layout(int k) {
+  Layout L;
+  L.n = k * k;
+  L.npos = (L.n + 1) & ~1;
+  L.nt4 = (L.npos + 3) / 4;
+  const int w = 4 * L.nt4;  // rows and columns rounded to whole tiles
+  L.gs = w + 4;             // a multiple of 4 (float4 rows)
+  L.cs = kCW + 4;
+  L.x1 = 0;
+  L.x2 = L.x1 + (size_t)w * L.gs;
+  L.chunk = L.x2 + (size_t)w * L.gs;
+  L.nrm = L.chunk + (size_t)w * L.cs;
+  L.pix = L.nrm + w;
+  L.total = L.pix + w;
+  return L;
+}
+
+__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void sts4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ float c4(const float4 &v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+
+// (row, column) of upper-triangle 4 x 4 tile t of an nt4 x nt4 tile grid
+__device__ __forceinline__ void upper_tile(int t, int nt4, int &ti, int &tj) {
+  ti = 0;
+  int left = t, row_len = nt4;
+  while (left >= row_len) {
+    left -= row_len;
+    --row_len;
+    ++ti;
+  }
+  tj = ti + left;
+}
+
+// The chunk [c0, c0 + kCW) of Y'_l into shared memory, all 4 nt4 rows (rows
+// >= n and columns >= 2 N3p read as 0).  form: add gamma_Y F and write Y'
+// back over Y_l.
+__device__ void stream_chunk(const Layout &L, float *chunk, float *Yl, const BlockDualArgs &a, const int *pix,
+                             int c0, bool form) {
+  const Dims &dm = a.dm;
+  const int N3p = dm.N3p, W = 2 * N3p;
+  constexpr int Q = kCW / 4;
+  for (int it = threadIdx.x; it < 4 * L.nt4 * Q; it += kLT) {
+    const int r = it / Q, q = it - r * Q, c = c0 + 4 * q;
+    float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r < L.n && c < W) {
+      float *g = Yl + (size_t)r * W + c;
+      y = *reinterpret_cast<const float4 *>(g);
+      if (form) {
+        const bool hz = c >= N3p;
+        const float4 f = __ldg(reinterpret_cast<const float4 *>((hz ? a.Fh : a.Fv) + (size_t)pix[r] * N3p +
+                                                                (hz ? c - N3p : c)));
+        y.x = fmaf(a.gY, f.x, y.x);
+        y.y = fmaf(a.gY, f.y, y.y);
+        y.z = fmaf(a.gY, f.z, y.z);
+        y.w = fmaf(a.gY, f.w, y.w);
+        *reinterpret_cast<float4 *>(g) = y;
+      }
+    }
+    sts4(chunk + (size_t)r * L.cs + 4 * q, y);
+  }
+}
+
+__global__ void __launch_bounds__(kLT, 1) block_dual_large_kernel(BlockDualArgs a, int k) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ float s_red[kLW];
+  __shared__ unsigned s_sweeps;
+  if (a.sc->done) return;
+  const Layout L = layout(k);
+  const int n = L.n, NP = L.npos, GS = L.gs, nt4 = L.nt4;
+  float *X1 = sm + L.x1, *X2 = sm + L.x2, *chunk = sm + L.chunk, *nrm = sm + L.nrm;
+  int *pix = reinterpret_cast<int *>(sm + L.pix);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const Dims dm = a.dm;
+  const int N3p = dm.N3p, W = 2 * N3p;
+  const long long Lb = dm.P;
+  if (tid == 0) s_sweeps = 0u;
+  const int n_upper = nt4 * (nt4 + 1) / 2;
+
+  for (long long l = blockIdx.x; l < Lb; l += gridDim.x) {
+    float *Yl = a.Y + (size_t)l * n * W;
+    if (tid < n) {
+      const int p = (int)(l / dm.N2), q = (int)(l - (long long)p * dm.N2);
+      const int ra = tid / k, rc = tid - ra * k;
+      int i = p + ra;
+      if (i >= dm.N1) i -= dm.N1;
+      int j = q + rc;
+      if (j >= dm.N2) j -= dm.N2;
+      pix[tid] = i * dm.N2 + j;
+    }
+    __syncthreads();
+
+    // ---- 1. Gram of Y', streamed by column chunks ----
+    float acc[kGramTiles][16];
+#pragma unroll
+    for (int u = 0; u < kGramTiles; ++u)
+#pragma unroll
+      for (int e = 0; e < 16; ++e) acc[u][e] = 0.f;
+    for (int c0 = 0; c0 < W; c0 += kCW) {
+      stream_chunk(L, chunk, Yl, a, pix, c0, true);
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < kGramTiles; ++u) {
+        const int t = tid + u * kLT;
+        if (t < n_upper) {
+          int ti, tj;
+          upper_tile(t, nt4, ti, tj);
+          const float *pa = chunk + (size_t)(4 * ti) * L.cs, *pb = chunk + (size_t)(4 * tj) * L.cs;
+#pragma unroll 2
+          for (int c = 0; c < kCW; c += 4) {
+            float4 va[4], vb[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+              va[x] = lds4(pa + (size_t)x * L.cs + c);
+              vb[x] = lds4(pb + (size_t)x * L.cs + c);
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+              for (int y = 0; y < 4; ++y) {
+                float s = acc[u][4 * x + y];
+                s = fmaf(va[x].x, vb[y].x, s);
+                s = fmaf(va[x].y, vb[y].y, s);
+                s = fmaf(va[x].z, vb[y].z, s);
+                s = fmaf(va[x].w, vb[y].w, s);
+                acc[u][4 * x + y] = s;
+              }
+          }
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < kGramTiles; ++u) {
+      const int t = tid + u * kLT;
+      if (t < n_upper) {
+        int ti, tj;
+        upper_tile(t, nt4, ti, tj);
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            const int r = 4 * ti + x, c = 4 * tj + y;
+            X1[(size_t)r * GS + c] = acc[u][4 * x + y];
+            X1[(size_t)c * GS + r] = acc[u][4 * x + y];
+          }
+      }
+    }
+    __syncthreads();
+
+    // ---- 2. C0 = W G (warm) or G (cold), rows of C into X2 ----
+    const float *Wl = a.W ? a.W + (size_t)l * a.w_stride : nullptr;
+    const bool warm = a.warm && Wl && !(Wl[0] != Wl[0]);  // NaN marks "start cold"
+    for (int r = warp; r < NP; r += kLW) {
+      float acc2[kSlots];
+      if (warm) {
+        float wr[kSlots];  // lane j holds W[r][j + 32 i]
+#pragma unroll
+        for (int i = 0; i < kSlots; ++i) {
+          const int c = lane + 32 * i;
+          wr[i] = c < n ? __ldg(Wl + (size_t)r * n + c) : 0.f;
+          acc2[i] = 0.f;
+        }
+#pragma unroll
+        for (int kb = 0; kb < kSlots; ++kb) {
+          for (int j = 0; j < 32 && kb * 32 + j < n; ++j) {
+            const float w = __shfl_sync(kFull, wr[kb], j);
+            const float *g = X1 + (size_t)(kb * 32 + j) * GS;
+#pragma unroll
+            for (int i = 0; i < kSlots; ++i) {
+              const int c = lane + 32 * i;
+              if (c < n) acc2[i] = fmaf(w, g[c], acc2[i]);
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < kSlots; ++i) {
+          const int c = lane + 32 * i;
+          acc2[i] = r < n && c < n ? X1[(size_t)r * GS + c] : 0.f;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < kSlots; ++i) {
+        const int c = lane + 32 * i;
+        if (c < GS) X2[(size_t)r * GS + c] = c < n ? acc2[i] : 0.f;
+      }
+    }
+    __syncthreads();
+
+    // ---- 3. one-sided Jacobi on the rows of C ----
+    // squared row norms (one warp per row)
+    auto norms = [&]() {
+      for (int r = warp; r < NP; r += kLW) {
+        float s = 0.f;
+        for (int c = lane; c < n; c += 32) s = fmaf(X2[(size_t)r * GS + c], X2[(size_t)r * GS + c], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+        if (lane == 0) nrm[r] = s;
+      }
+      __syncthreads();
+    };
+    norms();
+    // every warp sums the same norms in the same order: a block-uniform value
+    float fro = 0.f;
+    for (int r = lane; r < NP; r += 32) fro += nrm[r];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(kFull, fro, o);
+    // exact power-of-two scaling to a Frobenius norm near 1; eigenvalues are
+    // unscaled at the end by inv_s
+    float inv_s = 1.f;
+    if (fro > 0.f && fro < 1e30f) {
+      const int ex = ((__float_as_int(fro) >> 23) & 255) - 127;
+      const int h = ex >> 1;
+      const float sc = __int_as_float((127 - h) << 23), sc2 = sc * sc;
+      inv_s = __int_as_float((127 + h) << 23);
+      __syncthreads();  // every warp has read nrm for fro
+      for (int e = tid; e < NP * GS; e += kLT) X2[e] *= sc;
+      for (int r = tid; r < NP; r += kLT) nrm[r] *= sc2;
+      fro *= sc2;
+      __syncthreads();
+    }
+    const float floor2 = 1e-12f * fro;
+    const float tol2 = a.tol * a.tol;
+    bool converged = false;
+    int sweeps = 0;
+    for (int sw = 0; sw < a.max_sweeps; ++sw) {
+      if (sw) norms();
+      int rotated = 0;
+      for (int step = 0; step < NP - 1; ++step) {
+        for (int i = warp; i < NP / 2; i += kLW) {
+          // round robin: position 0 fixed, positions 1..NP-1 turn by one each step
+          const int pa = i, pb = NP - 1 - i;
+          const int ra = pa == 0 ? 0 : 1 + (pa - 1 + step) % (NP - 1);
+          const int rb = 1 + (pb - 1 + step) % (NP - 1);
+          float *A = X2 + (size_t)ra * GS, *B = X2 + (size_t)rb * GS;
+          float d = 0.f;
+          for (int c = lane; c < n; c += 32) d = fmaf(A[c], B[c], d);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
+          const float nA = nrm[ra], nB = nrm[rb];
+          if (fminf(nA, nB) > floor2 && d * d > tol2 * nA * nB) {
+            const float x = nB - nA, y = 2.f * d;
+            const float rr = rsqrtf(fmaf(x, x, y * y));
+            const float hc = fmaf(0.5f * fabsf(x), rr, 0.5f);
+            const float rc = rsqrtf(hc);
+            const float cs = hc * rc, sn = copysignf(0.5f, x) * y * rr * rc;
+            const float dn = sn * rc * d;  // t apq
+            for (int c = lane; c < n; c += 32) {
+              const float p = A[c], q = B[c];
+              A[c] = fmaf(cs, p, -sn * q);
+              B[c] = fmaf(sn, p, cs * q);
+            }
+            __syncwarp();
+            if (lane == 0) {
+              nrm[ra] = nA - dn;
+              nrm[rb] = nB + dn;
+            }
+            rotated = 1;
+          }
+        }
+        __syncthreads();
+      }
+      ++sweeps;
+      if (!__syncthreads_or(rotated)) {
+        converged = true;
+        break;
+      }
+    }
+    if (tid == 0) {
+      if (!converged) atomicAdd(&a.sc->jacobi_fail, 1u);
+      s_sweeps += (unsigned)sweeps;
+    }
+    norms();
+
+    // ---- 4. eigen-rows: Ut (X1) and the warm rows W ----
+    {
+      int zero = 0;
+      for (int r = tid; r < NP; r += kLT) zero += nrm[r] <= floor2 ? 1 : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) zero += __shfl_xor_sync(kFull, zero, o);
+      if (lane == 0) s_red[warp] = (float)zero;
+    }
+    __syncthreads();
+    float zero_rows = 0.f;
+    for (int w = 0; w < kLW; ++w) zero_rows += s_red[w];
+    // all but the NPOS - n zero rows must be nonzero directions, else mark cold
+    const bool mark_cold = zero_rows > (float)(NP - n);
+    for (int r = warp; r < NP; r += kLW) {
+      const float nr = nrm[r];
+      const float lam = sqrtf(nr) * inv_s;
+      const float wt = lam > 1.f ? sqrtf(1.f - rsqrtf(lam)) * rsqrtf(nr) : 0.f;
+      const float inr = nr > floor2 ? rsqrtf(nr) : 0.f;
+      float *ww = a.W ? a.W + (size_t)l * a.w_stride + (size_t)r * n : nullptr;
+      for (int c = lane; c < GS; c += 32) {
+        const float v = c < n ? X2[(size_t)r * GS + c] : 0.f;
+        X1[(size_t)r * GS + c] = v * wt;
+        if (ww && !mark_cold && c < n) ww[c] = v * inr;
+      }
+    }
+    __syncthreads();  // every W row written before the marker may overwrite W[0]
+    if (a.W && mark_cold && tid == 0) a.W[(size_t)l * a.w_stride] = __int_as_float(0x7fc00000);
+
+    // ---- 5a. M = I - Ut^T Ut into X2, 4 x 4 tiles ----
+    for (int t = tid; t < nt4 * nt4; t += kLT) {
+      const int ti = t / nt4, tj = t - ti * nt4;
+      float m[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) m[e] = 0.f;
+      for (int x = 0; x < NP; ++x) {
+        const float4 ua = lds4(X1 + (size_t)x * GS + 4 * ti), ub = lds4(X1 + (size_t)x * GS + 4 * tj);
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) m[4 * p + q] = fmaf(c4(ua, p), c4(ub, q), m[4 * p + q]);
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const int r = 4 * ti + p;
+        sts4(X2 + (size_t)r * GS + 4 * tj,
+             make_float4((r == 4 * tj ? 1.f : 0.f) - m[4 * p], (r == 4 * tj + 1 ? 1.f : 0.f) - m[4 * p + 1],
+                         (r == 4 * tj + 2 ? 1.f : 0.f) - m[4 * p + 2], (r == 4 * tj + 3 ? 1.f : 0.f) - m[4 * p + 3]));
+      }
+    }
+    __syncthreads();
+
+    // ---- 5b. Y_l = M Y' by chunks; Z += P_l^T Y_l ----
+    for (int c0 = 0; c0 < W; c0 += kCW) {
+      stream_chunk(L, chunk, Yl, a, pix, c0, false);
+      __syncthreads();
+      constexpr int Q = kCW / 4;
+      for (int t = tid; t < nt4 * Q; t += kLT) {
+        const int ti = t / Q, q = t - ti * Q;
+        float4 y[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) y[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int s = 0; s < n; ++s) {
+          const float4 m = lds4(X2 + (size_t)s * GS + 4 * ti);  // M[s][r] = M[r][s]
+          const float4 v = lds4(chunk + (size_t)s * L.cs + 4 * q);
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const float mp = c4(m, p);
+            y[p].x = fmaf(mp, v.x, y[p].x);
+            y[p].y = fmaf(mp, v.y, y[p].y);
+            y[p].z = fmaf(mp, v.z, y[p].z);
+            y[p].w = fmaf(mp, v.w, y[p].w);
+          }
+        }
+        const int c = c0 + 4 * q;
+        if (c < W) {
+          const bool hz = c >= N3p;
+          float *Zb = (hz ? a.Zh : a.Zv) + (hz ? c - N3p : c);
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const int r = 4 * ti + p;
+            if (r < n) {
+              __stcs(reinterpret_cast<float4 *>(Yl + (size_t)r * W + c), y[p]);
+              atomicAdd(reinterpret_cast<float4 *>(Zb + (size_t)pix[r] * N3p), y[p]);
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0 && s_sweeps) atomicAdd(&a.sc->jacobi_sweeps, (unsigned long long)s_sweeps);
+}
+
+}  // namespace
+
+size_t block_dual_large_smem_bytes(int k) { return sizeof(float) * layout(k).total; }
+
+long long block_dual_large_w_stride(int k) {
+  const Layout L = layout(k);
+  return ((long long)L.npos * L.n + 3) & ~3ll;
+}
+
+int block_dual_large_threads() { return kLT; }
+
+// The launch limit is raised to the device's opt-in maximum (less the static
+// shared memory): every context launching the kernel shares the attribute.
+cudaError_t block_dual_large_prepare(size_t smem) {
+  int dev = 0, cap = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, block_dual_large_kernel);
+  if (e != cudaSuccess) return e;
+  const size_t dyn = (size_t)cap > fa.sharedSizeBytes ? (size_t)cap - fa.sharedSizeBytes : 0;
+  if (dyn < smem) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(block_dual_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+}
+
+cudaError_t block_dual_large_occupancy(size_t smem, int *ctas) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, block_dual_large_kernel, kLT, smem);
+}
+
+cudaError_t launch_block_dual_large(const BlockDualArgs &a, int k, int grid, size_t smem, cudaStream_t st) {
+  if (k < kMinLargeK || k > kMaxLargeK) return cudaErrorInvalidValue;
+  block_dual_large_kernel<<<grid, kLT, smem, st>>>(a, k);
+  return cudaGetLastError();
+}
+
+}  // namespace s3ttv

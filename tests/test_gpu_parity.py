@@ -18,6 +18,14 @@ pytestmark = pytest.mark.gpu
 OP_TOL = 1e-5
 
 
+def op_tol(k):
+    """Per-operator bound: 1e-5 for blocks of up to 25 rows (k <= 5); beyond,
+    scaled by n / 25 for n = k^2 rows, the growth of the worst-case rounding of
+    the n-term sums of the FP32 Gram route (G = Y'Y'^T, M = I - sum of n
+    rank-one terms, M Y')."""
+    return OP_TOL * max(1.0, k * k / 25.0)
+
+
 def rel(a, b):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
@@ -99,6 +107,8 @@ def test_l1_ball_empty_and_zero(solver):
 BLOCK_CASES = [
     ((8, 7, 6), 1), ((6, 6, 5), 2), ((9, 8, 16), 3), ((3, 3, 4), 3), ((5, 5, 3), 5),
     ((12, 10, 13), 4), ((10, 11, 7), 5), ((32, 32, 16), 3), ((20, 24, 33), 5), ((16, 16, 128), 5),
+    # the larger blocks of the paper's own setting (one CTA per block): k = 6..12
+    ((9, 8, 7), 6), ((8, 9, 33), 7), ((10, 10, 16), 8), ((11, 10, 20), 10), ((10, 12, 70), 10), ((12, 12, 9), 12),
 ]
 
 
@@ -118,9 +128,9 @@ def test_block_dual_matches_oracle(solver, shape, k):
     Yref = O.block_dual_update(Y.astype(np.float64), X, 0.25)
     Zvr, Zhr = O.structure_tensors_adjoint(Yref, k, shape)
     got = Yd.cpu().numpy()
-    assert rel(got, Yref) <= OP_TOL, rel(got, Yref)
-    assert rel(Zv.cpu().numpy(), Zvr) <= OP_TOL
-    assert rel(Zh.cpu().numpy(), Zhr) <= OP_TOL
+    assert rel(got, Yref) <= op_tol(k), rel(got, Yref)
+    assert rel(Zv.cpu().numpy(), Zvr) <= op_tol(k)
+    assert rel(Zh.cpu().numpy(), Zhr) <= op_tol(k)
     # every block now lies in the spectral-norm unit ball, up to the FP32 Gram
     # error: eigenvalues of G = Y'Y'^T near 1 carry an absolute error of order
     # eps * lambda_max, and these random blocks reach lambda_max ~ 100
@@ -157,7 +167,8 @@ def _radii_for_state(st, v, k, g):
 
 
 @pytest.mark.parametrize("shape,k,policy", [((32, 32, 16), 3, "paper"), ((13, 11, 7), 2, "pc_exact"),
-                                            ((10, 9, 5), 5, "pc_exact"), ((6, 6, 2), 1, "pc_exact")])
+                                            ((10, 9, 5), 5, "pc_exact"), ((6, 6, 2), 1, "pc_exact"),
+                                            ((12, 11, 9), 10, "pc_exact"), ((9, 9, 6), 7, "paper")])
 def test_one_pass_matches_oracle(P, solver, shape, k, policy):
     N1, N2, N3 = shape
     _, v = make_cube(CubeSpec(N1, N2, N3, regions=4, endmembers=3, seed=7))
@@ -177,7 +188,7 @@ def test_one_pass_matches_oracle(P, solver, shape, k, policy):
     for key in ("u", "s", "t", "y2", "y3", "Y"):
         got = solver.get_state(key)
         e = rel(got, ref[key])
-        assert e <= OP_TOL, (key, e)
+        assert e <= op_tol(k), (key, e)
 
 
 # ---------------------------------------------------------------------------
@@ -290,14 +301,15 @@ def test_invalid_arguments(P, solver):
                          max_iter=3)
         assert e.value.status == P.EINVAL
     with pytest.raises(P.S3TTVError) as e:
-        solver.solve(np.zeros((8, 8, 6), np.float32), 1.0, 1.0, 1.0, 6, max_iter=3)
+        solver.solve(np.zeros((14, 14, 6), np.float32), 1.0, 1.0, 1.0, 13, max_iter=3)
     assert e.value.status == P.EUNSUPPORTED
     with pytest.raises(P.S3TTVError) as e:
         P.Solver(0).iterate(1)
     assert e.value.status == P.ESTATE
 
 
-def test_warm_start_matches_cold_start(P, solver):
+@pytest.mark.parametrize("k", [3, 10])
+def test_warm_start_matches_cold_start(P, solver, k):
     """The per-block eigenbasis carried from pass to pass only changes where the
     Jacobi sweeps start, not what they converge to."""
     spec = WORKLOADS["parity_32x32x16_k3"]
@@ -306,7 +318,7 @@ def test_warm_start_matches_cold_start(P, solver):
     res = {}
     for warm in (1, 0):
         solver.set_option(P.OPT_WARM_START, warm)
-        u, s, t, info = solver.solve(v, eps, alpha, beta, spec.k, max_iter=60, tol=0.0)
+        u, s, t, info = solver.solve(v, eps, alpha, beta, k, max_iter=60, tol=0.0)
         assert info["jacobi_nonconverged"] == 0
         res[warm] = (u, s, t, info["jacobi_sweeps"])
     for i in range(3):
