@@ -17,9 +17,10 @@
 //     NaN marker in W starts cold from C0 = G).
 //  3. One-sided (Hestenes) Jacobi on the rows of C, resident in shared memory,
 //     in the round-robin ordering: each of the NPOS - 1 steps of a sweep meets
-//     NPOS / 2 disjoint row pairs, which the warps take in turn (one warp per
-//     pair: a warp-wide dot product, then the rotation of both rows in place);
-//     rows never move, only the pairing changes.  Rows are scaled by an exact
+//     NPOS / 2 disjoint row pairs, kPG lanes per pair and four pairs per warp
+//     side by side (a dot product over the group, then the rotation of both
+//     rows, held in registers, written back in place); rows never move, only
+//     the pairing changes.  Rows are scaled by an exact
 //     power of two first; the tolerance, the numerical-zero floor and the
 //     rotation formula are those of block_dual.cu.
 //  4. Converged rows are lam_x u_x^T: scaled eigen-rows into shared memory, the
@@ -39,6 +40,8 @@ constexpr int kLT = kLW * 32;  // threads per CTA
 constexpr int kCW = 64;        // columns of Y' per streamed chunk
 constexpr int kGramTiles = 2;  // upper-triangle Gram tiles a thread may own
 constexpr int kSlots = (kMaxLargeK * kMaxLargeK + 31) / 32;  // row elements a lane holds
+constexpr int kPG = 8;                                        // lanes per row pair in the Jacobi
+constexpr int kPE = (kMaxLargeK * kMaxLargeK + kPG - 1) / kPG; // row elements such a lane holds
 
 struct Layout {
   int n, npos, gs, cs;  // block rows, rows padded to even, row strides of the n x n buffers and the chunk
@@ -275,31 +278,46 @@ __global__ void __launch_bounds__(kLT, 1) block_dual_large_kernel(BlockDualArgs 
       if (sw) norms();
       int rotated = 0;
       for (int step = 0; step < NP - 1; ++step) {
-        for (int i = warp; i < NP / 2; i += kLW) {
+        // kPG lanes per pair, 32 / kPG pairs per warp side by side
+        for (int base = 0; base < NP / 2; base += kLW * (32 / kPG)) {
+          const int i = base + warp * (32 / kPG) + (lane / kPG), gl = lane % kPG;
+          const bool act = i < NP / 2;
           // round robin: position 0 fixed, positions 1..NP-1 turn by one each step
-          const int pa = i, pb = NP - 1 - i;
+          const int pa = act ? i : 0, pb = NP - 1 - pa;
           const int ra = pa == 0 ? 0 : 1 + (pa - 1 + step) % (NP - 1);
           const int rb = 1 + (pb - 1 + step) % (NP - 1);
           float *A = X2 + (size_t)ra * GS, *B = X2 + (size_t)rb * GS;
-          float d = 0.f;
-          for (int c = lane; c < n; c += 32) d = fmaf(A[c], B[c], d);
+          float va[kPE], vb[kPE];
+          float d0 = 0.f, d1 = 0.f;
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
-          const float nA = nrm[ra], nB = nrm[rb];
-          if (fminf(nA, nB) > floor2 && d * d > tol2 * nA * nB) {
+          for (int e = 0; e < kPE; ++e) {
+            const int c = gl + kPG * e;
+            const bool in = act && c < n;
+            va[e] = in ? A[c] : 0.f;
+            vb[e] = in ? B[c] : 0.f;
+            if (e & 1) d1 = fmaf(va[e], vb[e], d1);
+            else d0 = fmaf(va[e], vb[e], d0);
+          }
+          float d = d0 + d1;
+#pragma unroll
+          for (int o = kPG / 2; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
+          const float nA = act ? nrm[ra] : 0.f, nB = act ? nrm[rb] : 0.f;
+          if (act && fminf(nA, nB) > floor2 && d * d > tol2 * nA * nB) {
             const float x = nB - nA, y = 2.f * d;
             const float rr = rsqrtf(fmaf(x, x, y * y));
             const float hc = fmaf(0.5f * fabsf(x), rr, 0.5f);
             const float rc = rsqrtf(hc);
             const float cs = hc * rc, sn = copysignf(0.5f, x) * y * rr * rc;
             const float dn = sn * rc * d;  // t apq
-            for (int c = lane; c < n; c += 32) {
-              const float p = A[c], q = B[c];
-              A[c] = fmaf(cs, p, -sn * q);
-              B[c] = fmaf(sn, p, cs * q);
+#pragma unroll
+            for (int e = 0; e < kPE; ++e) {
+              const int c = gl + kPG * e;
+              if (c < n) {
+                A[c] = fmaf(cs, va[e], -sn * vb[e]);
+                B[c] = fmaf(sn, va[e], cs * vb[e]);
+              }
             }
-            __syncwarp();
-            if (lane == 0) {
+            if (gl == 0) {
               nrm[ra] = nA - dn;
               nrm[rb] = nB + dn;
             }

@@ -52,7 +52,8 @@ class CubeSpec:
 
 
 # The workloads: a parity case small enough for the FP64 oracle to finish in
-# seconds, the 256x256x128 headline cube, and the larger 304x304x191 cube.
+# seconds, the 256x256x128 headline cube, the larger 304x304x191 cube, and
+# cubes of the paper's scene sizes with its 10 x 10 blocks.
 WORKLOADS = {
     "parity_32x32x16_k3": CubeSpec(32, 32, 16, regions=6, endmembers=3, sigma=0.1,
                                    p_s=0.05, p_t=0.05, k=3, seed=0),
@@ -63,6 +64,11 @@ WORKLOADS = {
     # a quarter of the headline cube's pixels, for profiler captures that must stay small
     "profile_128x128x128_k5": CubeSpec(128, 128, 128, regions=16, endmembers=5, sigma=0.05,
                                        p_s=0.05, p_t=0.10, k=5, seed=0),
+    # the paper's own scene sizes (Sec. IV) with its 10 x 10 blocks
+    "paper_100x100x198_k10": CubeSpec(100, 100, 198, regions=8, endmembers=5, sigma=0.1,
+                                      p_s=0.05, p_t=0.05, k=10, seed=0),
+    "paper_120x120x98_k10": CubeSpec(120, 120, 98, regions=8, endmembers=5, sigma=0.1,
+                                     p_s=0.05, p_t=0.05, k=10, seed=0),
 }
 
 

@@ -1,8 +1,9 @@
 """Parity at full size, in the launch configuration bench.py times.
 
 After a few warm passes of Alg. 1 on the 256x256x128 (k = 5) and 304x304x191
-(k = 5, odd band count) cubes, with the block-dual products on tensor cores and
-on CUDA cores, one more pass on the GPU is compared with the FP64
+(k = 5, odd band count) cubes and a 100x100x198 cube with the paper's 10 x 10
+blocks, with the block-dual products on tensor cores and on CUDA cores (the
+same FP32 path for k = 10), one more pass on the GPU is compared with the FP64
 oracle applied to the same state: whole arrays where the oracle can afford them
 (both l1-ball projections, y2, y3 over every voxel), sampled blocks for the block
 duals, sampled voxels for u; plus the constraints each projection guarantees.
@@ -19,6 +20,12 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 OP_TOL = 1e-5
+
+
+def op_tol(k):
+    """1e-5 for blocks of up to 25 rows; scaled by n / 25 for n = k^2 rows (the
+    worst-case growth of the rounding in the n-term sums of the Gram route)."""
+    return OP_TOL * max(1.0, k * k / 25.0)
 
 
 def rel(a, b):
@@ -55,7 +62,8 @@ def P():
 
 
 @pytest.mark.parametrize("form", [pytest.param(1, id="tc"), pytest.param(0, id="fp32")])
-@pytest.mark.parametrize("name,warm_passes", [("s3ttv_256x256x128_k5", 3), ("s3ttv_304x304x191_k5", 2)])
+@pytest.mark.parametrize("name,warm_passes", [("s3ttv_256x256x128_k5", 3), ("s3ttv_304x304x191_k5", 2),
+                                              ("paper_100x100x198_k10", 2)])
 def test_one_full_size_pass(P, name, warm_passes, form):
     spec = WORKLOADS[name]
     k = spec.k
@@ -109,7 +117,7 @@ def test_one_full_size_pass(P, name, warm_passes, form):
         X = O.structure_tensor_block(ubar, k, p, q)
         ref = O.block_dual_update(Yb[l].double().cpu().numpy(), X, g["Y"])
         got = Ya[l].double().cpu().numpy()
-        assert rel(got, ref) <= OP_TOL, l
+        assert rel(got, ref) <= op_tol(k), l
         assert np.linalg.norm(got, 2) <= 1 + 1e-4
 
     # steps 5-7, 12-14 over every voxel, from the oracle's own s+, t+
