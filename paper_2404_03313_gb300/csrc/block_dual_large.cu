@@ -35,10 +35,10 @@
 namespace s3ttv {
 namespace {
 
-constexpr int kLW = 16;        // warps per CTA
+constexpr int kLW = 8;         // warps per CTA (two CTAs per SM where shared memory allows)
 constexpr int kLT = kLW * 32;  // threads per CTA
 constexpr int kCW = 64;        // columns of Y' per streamed chunk
-constexpr int kGramTiles = 2;  // upper-triangle Gram tiles a thread may own
+constexpr int kGramTiles = 3;  // upper-triangle Gram tiles a thread may own
 constexpr int kSlots = (kMaxLargeK * kMaxLargeK + 31) / 32;  // row elements a lane holds
 constexpr int kPG = 8;                                        // lanes per row pair in the Jacobi
 constexpr int kPE = (kMaxLargeK * kMaxLargeK + kPG - 1) / kPG; // row elements such a lane holds
@@ -111,7 +111,7 @@ __device__ void stream_chunk(const Layout &L, float *chunk, float *Yl, const Blo
   }
 }
 
-__global__ void __launch_bounds__(kLT, 1) block_dual_large_kernel(BlockDualArgs a, int k) {
+__global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs a, int k) {
   extern __shared__ __align__(16) float sm[];
   __shared__ float s_red[kLW];
   __shared__ unsigned s_sweeps;
