@@ -8,7 +8,9 @@ method's arithmetic).
 
 Every function here is pinned by a ``-m "not gpu"`` test against something other
 than itself (brute force on tiny inputs, closed forms, optimality conditions,
-invariances, values the paper prints).  See ``oracle/s3ttv.py``.
+invariances, values the paper prints).  See ``oracle/s3ttv.py`` (Alg. 1) and
+``oracle/unet.py`` (the network of the learned warm start, which the paper does
+not have; import it as ``oracle.unet``).
 """
 from .s3ttv import *  # noqa: F401,F403
 from .s3ttv import __all__  # noqa: F401

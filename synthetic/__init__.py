@@ -32,7 +32,8 @@ from __future__ import annotations
 import dataclasses
 import numpy as np
 
-__all__ = ["CubeSpec", "make_cube", "WORKLOADS", "random_state", "batch_specs"]
+__all__ = ["CubeSpec", "make_cube", "WORKLOADS", "random_state", "batch_specs", "network_params",
+           "warm_start_specs"]
 
 
 @dataclasses.dataclass(frozen=True)
@@ -172,3 +173,36 @@ def random_state(N1: int, N2: int, N3: int, k: int, seed: int, scale: float = 0.
         "Y": scale * rng.standard_normal((N1 * N2, k * k, 2 * N3)),
     }
     return {key: val.astype(np.float32) for key, val in st.items()}
+
+
+def network_params(shapes, seed: int, head_scale: float = 0.1) -> np.ndarray:
+    """Seeded initial parameters of a convolutional network, flat float32.
+
+    ``shapes`` lists the parameter arrays in order: a 3-D weight (out, taps, in)
+    draws He-normal values, N(0, 2 / (taps * in)); a 2-D weight (out, in) draws
+    N(0, head_scale^2 / in); a 1-D bias is zero.  Only random draws happen here.
+    """
+    rng = np.random.default_rng(seed)
+    parts = []
+    for shp in shapes:
+        if len(shp) == 3:
+            parts.append(rng.standard_normal(shp) * np.sqrt(2.0 / (shp[1] * shp[2])))
+        elif len(shp) == 2:
+            parts.append(rng.standard_normal(shp) * (head_scale / np.sqrt(shp[1])))
+        else:
+            parts.append(np.zeros(shp))
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+
+
+def warm_start_specs(count: int, seed: int, shape=(128, 128, 64)):
+    """Training or evaluation cubes for the learned warm start: ``count`` cubes
+    of one shape with cube i seeded ``seed + i``; noise levels cycle through
+    sigma in {0.05, 0.1} and stripe rates in {0.05, 0.10}, sparse rate 0.05,
+    k = 5, 32 regions of 5 endmembers (fewer regions on small cubes)."""
+    N1, N2, N3 = shape
+    R = max(4, min(32, (N1 * N2) // 2048))
+    out = []
+    for i in range(count):
+        out.append(CubeSpec(N1, N2, N3, regions=R, endmembers=5, sigma=(0.05, 0.1)[i % 2], p_s=0.05,
+                            p_t=(0.05, 0.10)[(i // 2) % 2], k=5, seed=seed + i))
+    return out
