@@ -274,6 +274,65 @@ int s3ttv_radii(long long N, double sigma, double p_s, double p_t, double rho,
  * written to gammas[6] (host). */
 int s3ttv_step_sizes(int N1, int N2, int k, int policy, double gammas[6]);
 
+/* ---------------------------------------------------------------------------
+ * Learned warm start.  The paper has no network: Alg. 1 starts from u = v,
+ * s = t = 0.  These entry points train and run a small 3-D convolutional U-Net
+ * that maps a noisy cube v to an estimate of (u, s, t); s3ttv_set_state then
+ * starts the solver there, and the solver alone decides the result.
+ *
+ * Network: 3 levels of 32 / 64 / 128 channels, two 3 x 3 x 3 convolutions per
+ * level (zero padding, bias, ReLU), 2 x 2 x 2 mean pooling, nearest upsampling,
+ * skip connections by channel concatenation [upsampled, skip], and a
+ * 1 x 1 x 1 head to three channels h; the prediction is (v + h0, h1, h2).
+ * Weights are used in BF16 (FP32 master copies for Adam), activations are
+ * stored in BF16, products accumulate in FP32.  Training minimises the mean
+ * squared error over all voxels and the three outputs.
+ *
+ * Parameters: one flat FP32 vector of s3ttv_net_param_count() values: for each
+ * convolution in network order (e1a 1->32, e1b 32->32, e2a 32->64, e2b 64->64,
+ * ba 64->128, bb 128->128, d2a 192->64, d2b 64->64, d1a 96->32, d1b 32->32) the
+ * weight w[out][tap][in], tap = 9 (dz+1) + 3 (dy+1) + (dx+1), then the bias
+ * b[out]; last the head Wh[3][32] and bh[3].
+ *
+ * Volumes: B volumes of D x H x W voxels, C-contiguous [B][D][H][W]; a cube
+ * [N1][N2][N3] is B = 1, D = N1, H = N2, W = N3.  D, H and W must be positive
+ * multiples of 4 and B*D*H*W <= 2^26 (S3TTV_EUNSUPPORTED beyond).  Data
+ * pointers may be host or device memory, as for the solver.  Every call returns
+ * after the network's stream has finished; the network owns its workspace
+ * (about 700 bytes per voxel, grown on demand).  Status codes as above;
+ * S3TTV_ESTATE until parameters are set.
+ * ------------------------------------------------------------------------- */
+typedef struct s3ttv_net s3ttv_net;
+
+/* Number of parameters (1,411,651). */
+long long s3ttv_net_param_count(void);
+
+/* Create a network on `device`, running on `cuda_stream` (NULL: its own). */
+int s3ttv_net_create(s3ttv_net **out, int device, void *cuda_stream);
+void s3ttv_net_destroy(s3ttv_net *net); /* NULL-safe */
+const char *s3ttv_net_last_error(const s3ttv_net *net);
+
+/* Load parameters (param_count floats) and reset the Adam state. */
+int s3ttv_net_set_params(s3ttv_net *net, const float *theta);
+/* Copy the current FP32 parameters out (param_count floats). */
+int s3ttv_net_get_params(s3ttv_net *net, float *theta);
+
+/* Prediction: u, s, t (B*D*H*W floats each) from v. */
+int s3ttv_net_forward(s3ttv_net *net, const float *v, int B, int D, int H, int W,
+                      float *u, float *s, float *t);
+
+/* Loss (mean squared error of the prediction against u_ref, s_ref, t_ref; host
+ * double, may be NULL) and its gradient with respect to every parameter
+ * (param_count floats in the parameter order, may be NULL). */
+int s3ttv_net_gradient(s3ttv_net *net, const float *v, const float *u_ref, const float *s_ref,
+                       const float *t_ref, int B, int D, int H, int W, double *loss, float *grad);
+
+/* One training step: the gradient as above, then one Adam update (beta1 0.9,
+ * beta2 0.999, eps 1e-8, bias-corrected) with learning rate lr in [0, 1].
+ * `loss` (may be NULL) receives the loss before the update. */
+int s3ttv_net_train_step(s3ttv_net *net, const float *v, const float *u_ref, const float *s_ref,
+                         const float *t_ref, int B, int D, int H, int W, float lr, double *loss);
+
 #ifdef __cplusplus
 }
 #endif

@@ -2,11 +2,12 @@
 
 The solver (Alg. 1 of the paper, P-PDS) runs in hand-written sm_103a CUDA kernels
 behind the C ABI of ``include/s3ttv.h`` (``libs3ttv.so``); this package is the
-thin ctypes binding over it plus the build script.  Nothing here computes on the
+thin ctypes binding over it plus the build script.  ``warmstart`` trains and
+applies the learned warm start (a 3-D U-Net, also on the library's kernels).  Nothing here computes on the
 CPU: if the library is not built, calls raise ``S3TTVError``.
 """
 from ._binding import (  # noqa: F401
-    Info, S3TTVError, Solver, library, radii, step_sizes, l1_ball_static, LIB_PATH, SIGNATURES, STATE,
+    Info, S3TTVError, Solver, WarmStartNet, library, radii, step_sizes, l1_ball_static, LIB_PATH, SIGNATURES, STATE,
     L1_STATIC_MAX_N, ETOOBIG,
     STEP_PAPER, STEP_PC_EXACT, OPT_STEP_POLICY, OPT_CHECK_EVERY, OPT_JACOBI_MAX_SWEEPS, OPT_JACOBI_TOL,
     OPT_PROFILE, OPT_WARM_START, OPT_TENSOR_CORES, KERNEL_CLASSES,

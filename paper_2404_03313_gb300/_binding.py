@@ -66,6 +66,15 @@ SIGNATURES = {
     "s3ttv_l1_ball_static": (_c_int, [_vp, _vp, _c_ll, _c_d, _P(_c_d), _vp]),
     "s3ttv_radii": (_c_int, [_c_ll, _c_d, _c_d, _c_d, _c_d, _P(_c_d), _P(_c_d), _P(_c_d)]),
     "s3ttv_step_sizes": (_c_int, [_c_int, _c_int, _c_int, _c_int, _P(_c_d)]),
+    "s3ttv_net_param_count": (_c_ll, []),
+    "s3ttv_net_create": (_c_int, [_P(_vp), _c_int, _vp]),
+    "s3ttv_net_destroy": (None, [_vp]),
+    "s3ttv_net_last_error": (ctypes.c_char_p, [_vp]),
+    "s3ttv_net_set_params": (_c_int, [_vp, _vp]),
+    "s3ttv_net_get_params": (_c_int, [_vp, _vp]),
+    "s3ttv_net_forward": (_c_int, [_vp, _vp, _c_int, _c_int, _c_int, _c_int, _vp, _vp, _vp]),
+    "s3ttv_net_gradient": (_c_int, [_vp, _vp, _vp, _vp, _vp, _c_int, _c_int, _c_int, _c_int, _P(_c_d), _vp]),
+    "s3ttv_net_train_step": (_c_int, [_vp, _vp, _vp, _vp, _vp, _c_int, _c_int, _c_int, _c_int, _c_f, _P(_c_d)]),
 }
 
 
@@ -320,3 +329,98 @@ class Solver:
                                         ctypes.byref(info))
         self._check(rc, "s3ttv_block_dual")
         return Zv, Zh, info.as_dict()
+
+
+def _vol_shape(x):
+    """(B, D, H, W) of a cube (N1, N2, N3) or a batch (B, N1, N2, N3)."""
+    shp = tuple(x.shape)
+    if len(shp) == 3:
+        return (1,) + shp
+    if len(shp) == 4:
+        return shp
+    raise S3TTVError(EINVAL, f"expected a cube (N1, N2, N3) or a batch (B, N1, N2, N3), got {shp}")
+
+
+class WarmStartNet:
+    """The learned warm start's 3-D U-Net (s3ttv_net_*): forward, gradient and
+    Adam training steps on the library's kernels.  Arrays are float32 cubes
+    (N1, N2, N3) or batches (B, N1, N2, N3), torch (CUDA or CPU) or numpy."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._lib = library()
+        h = ctypes.c_void_p()
+        st = None
+        if stream is not None:
+            st = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        rc = self._lib.s3ttv_net_create(ctypes.byref(h), int(device), st)
+        if rc:
+            raise S3TTVError(rc, f"s3ttv_net_create(device={device}) failed")
+        self._h = h
+        self.device = device
+        self.param_count = int(self._lib.s3ttv_net_param_count())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.s3ttv_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc, what):
+        if rc < 0:
+            msg = self._lib.s3ttv_net_last_error(self._h).decode(errors="replace")
+            raise S3TTVError(rc, f"{what}: {msg}")
+        return rc
+
+    def set_params(self, theta):
+        _sync_torch(theta)
+        self._check(self._lib.s3ttv_net_set_params(self._h, _ptr(theta, self.param_count, "theta")), "set_params")
+
+    def get_params(self, like=None):
+        out = _empty_like(like, (self.param_count,)) if like is not None else np.empty(self.param_count, np.float32)
+        self._check(self._lib.s3ttv_net_get_params(self._h, _ptr(out, self.param_count, "theta")), "get_params")
+        return out
+
+    def forward(self, v):
+        """Predicted (u, s, t), shaped and placed like v."""
+        B, D, H, W = _vol_shape(v)
+        n = B * D * H * W
+        u, s, t = (_empty_like(v, v.shape) for _ in range(3))
+        _sync_torch(v)
+        self._check(self._lib.s3ttv_net_forward(self._h, _ptr(v, n, "v"), B, D, H, W, _ptr(u, n, "u"),
+                                                _ptr(s, n, "s"), _ptr(t, n, "t")), "s3ttv_net_forward")
+        return u, s, t
+
+    def gradient(self, v, u_ref, s_ref, t_ref, grad=None):
+        """(loss, flat gradient) of the mean squared error against (u_ref, s_ref, t_ref)."""
+        B, D, H, W = _vol_shape(v)
+        n = B * D * H * W
+        g = grad if grad is not None else np.empty(self.param_count, np.float32)
+        loss = ctypes.c_double()
+        _sync_torch(v, u_ref, s_ref, t_ref)
+        self._check(self._lib.s3ttv_net_gradient(self._h, _ptr(v, n, "v"), _ptr(u_ref, n, "u_ref"),
+                                                 _ptr(s_ref, n, "s_ref"), _ptr(t_ref, n, "t_ref"), B, D, H, W,
+                                                 ctypes.byref(loss), _ptr(g, self.param_count, "grad")),
+                    "s3ttv_net_gradient")
+        return loss.value, g
+
+    def train_step(self, v, u_ref, s_ref, t_ref, lr):
+        """One Adam step; returns the loss before it."""
+        B, D, H, W = _vol_shape(v)
+        n = B * D * H * W
+        loss = ctypes.c_double()
+        _sync_torch(v, u_ref, s_ref, t_ref)
+        self._check(self._lib.s3ttv_net_train_step(self._h, _ptr(v, n, "v"), _ptr(u_ref, n, "u_ref"),
+                                                   _ptr(s_ref, n, "s_ref"), _ptr(t_ref, n, "t_ref"), B, D, H, W,
+                                                   float(lr), ctypes.byref(loss)), "s3ttv_net_train_step")
+        return loss.value
