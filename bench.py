@@ -584,6 +584,68 @@ def run_warm_start(args):
     return 0
 
 
+NET_FORWARD_PREFIX = "net_forward_"
+
+
+def run_net_forward(args):
+    """The warm-start network's forward alone on a random cube of the size the
+    workload names (net_forward_<N1>x<N2>x<N3>), seeded He-normal parameters:
+    value = voxels/s over `steps` forwards after `warmup`, CUDA events on the
+    network's stream; roofline = convolution FLOPs / time on the tensor pipe."""
+    import torch
+    import paper_2404_03313_gb300 as P
+    from synthetic import network_params
+
+    N1, N2, N3 = (int(x) for x in args.workload[len(NET_FORWARD_PREFIX):].split("x"))
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream(device=0)
+    net = P.WarmStartNet(0, stream=stream)
+    shapes = []
+    for ci, co in ((1, 32), (32, 32), (32, 64), (64, 64), (64, 128), (128, 128), (192, 64), (64, 64), (96, 32),
+                   (32, 32)):
+        shapes += [(co, 27, ci), (co,)]
+    shapes += [(3, 32), (3,)]
+    net.set_params(network_params(shapes, seed=0, head_scale=0.1))
+    x = torch.rand(N1, N2, N3, device="cuda:0")
+    for _ in range(args.warmup):
+        net.forward(x)
+    sampler = ClockSampler(nvsmi_id(0)).start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        net.forward(x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    net.close()
+    V = N1 * N2 * N3
+    flops = unet_forward_flops(V)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("bf16_tflops") or 1900.0
+    achieved = flops / (ms / 1000.0) / 1e12
+    print(json.dumps({
+        "metric": "warm-start network forward, voxels/s", "value": V / (ms / 1000.0), "unit": "voxel/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": args.workload, "N1": N1, "N2": N2, "N3": N3,
+                   "l2": "activations larger than L2 (%.2f GB per 32-channel full-size tensor)" % (64 * V / 1e9)},
+        "clocks": clocks,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "network forward (all launches)",
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops" if "bf16_tflops" in peaks
+                     else "fallback 1900 TFLOP/s", "flops_per_forward": flops},
+    }), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -606,6 +668,12 @@ def main(argv=None):
                               "run it on their workloads"}), flush=True)
             return 0
         return run_batch(args)
+    if args.workload.startswith(NET_FORWARD_PREFIX):
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the network forward has no solver "
+                              "counterpart in the oracle arm"}), flush=True)
+            return 0
+        return run_net_forward(args)
     if args.workload == WARM_WORKLOAD:
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the learned warm start has no oracle "
