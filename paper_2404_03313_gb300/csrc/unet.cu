@@ -35,7 +35,9 @@
 //    M = output channels, N = 32 input channels of one tap, K = voxels of one
 //    chunk; fragments come from the voxel-major tiles through ldmatrix.trans;
 //    partial sums are added into FP32 dW with atomics.
-//  * the first layer (one input channel) and the head run on CUDA cores.
+//  * the first layer (one input channel) and the head run on CUDA cores; the
+//    first layer's weight gradient goes through an im2col of its 27 taps and
+//    the tensor-core weight-gradient kernel.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -126,23 +128,29 @@ __device__ __forceinline__ void decode(int p, const Vol &g, int &b, int &z, int 
   b = t / g.D;
 }
 
-// Source of the 16-byte piece (8 channels starting at channel cb + 8 q) of the
-// conv input at voxel (b, z, y, x) + delta, or nullptr outside the volume.  The
-// input is cat[up(x1) (c1 channels, half size), x0 (c0 channels)].
-__device__ __forceinline__ const bf16 *gather_src(const bf16 *x0, int c0, const bf16 *x1, int c1, const Vol &g,
-                                                  int b, int z, int y, int x, int cb) {
-  if (z < 0 || z >= g.D || y < 0 || y >= g.H || x < 0 || x >= g.W) return nullptr;
-  if (cb < c1) {
-    const int D2 = g.D >> 1, H2 = g.H >> 1, W2 = g.W >> 1;
-    return x1 + ((((size_t)b * D2 + (z >> 1)) * H2 + (y >> 1)) * W2 + (x >> 1)) * c1 + cb;
+// 8 BF16 values <-> 8 floats through one 16-byte access
+__device__ __forceinline__ void load8(const bf16 *p, float f[8]) {
+  const uint4 u = *reinterpret_cast<const uint4 *>(p);
+  const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 t = __bfloat1622float2(h[i]);
+    f[2 * i] = t.x;
+    f[2 * i + 1] = t.y;
   }
-  return x0 + ((((size_t)b * g.D + z) * g.H + y) * g.W + x) * c0 + (cb - c1);
+}
+__device__ __forceinline__ void store8(bf16 *p, const float f[8]) {
+  uint4 u;
+  __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&u);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+  *reinterpret_cast<uint4 *>(p) = u;
 }
 
 // ---------------------------------------------------------------- conv forward
-constexpr int kBM = 128;  // voxels per CTA
-constexpr int kBK = 32;   // input channels per K step
-constexpr int kAS = 40;   // shared row stride in bf16 (80 B: ldmatrix rows hit distinct banks)
+constexpr int kBK = 32;     // input channels per K step
+constexpr int kAS = 40;     // shared row stride in bf16 (80 B: ldmatrix rows hit distinct banks)
+constexpr int kStages = 3;  // cp.async pipeline depth
 
 struct ConvArgs {
   const bf16 *x0;
@@ -155,77 +163,124 @@ struct ConvArgs {
   Vol g;
 };
 
-template <int NT>
-__global__ void __launch_bounds__(256) conv_fwd_kernel(ConvArgs a) {
-  __shared__ __align__(16) bf16 As[2][kBM * kAS];
-  __shared__ __align__(16) bf16 Bs[2][NT * kAS];
+template <int BM, int BN>
+constexpr int conv_smem_bytes() {
+  return kStages * (BM + BN) * kAS * (int)sizeof(bf16);
+}
+
+// CTA tile BM voxels x BN output channels; (BM / 32) x (BN / 32) warps, each
+// owning a 32 x 32 tile (2 m16 x 4 n8 fragments).  The K loop runs tap by tap
+// and, within a tap, over 32-channel slices of the input; the voxel rows a
+// thread gathers get their neighbour pointers once per tap.
+template <int BM, int BN>
+__global__ void __launch_bounds__((BM / 32) * (BN / 32) * 32) conv_fwd_kernel(ConvArgs a) {
+  constexpr int WN = BN / 32;
+  constexpr int NTH = (BM / 32) * WN * 32;
+  constexpr int RPT = BM * 4 / NTH;  // 16-byte A pieces a thread copies per stage
+  constexpr int AE = BM * kAS, BE = BN * kAS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  bf16 *As = reinterpret_cast<bf16 *>(smem_raw);
+  bf16 *Bs = As + kStages * AE;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp & 3, wn = warp >> 2;
+  const int wm = warp / WN, wn = warp % WN;
   const int V = nvox(a.g);
-  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * NT;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int cin = a.c0 + a.c1, nch = cin / kBK, ksteps = 27 * nch;
   const int q = tid & 3;
-  int rb[2], rz[2], ry[2], rx[2];
-  bool rv[2];
+  // per gathered row: its voxel index, its index in the half-size grid, and a
+  // mask of the volume faces it touches (bit 0/1: z = 0 / D-1, 2/3: y, 4/5: x,
+  // 6: past the last voxel) plus its coordinate parities (bits 8-10: z, y, x)
+  int vi[RPT], li[RPT], rm[RPT];
+  const int D2 = a.g.D >> 1, H2 = a.g.H >> 1, W2 = a.g.W >> 1;
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const int p = m0 + (tid >> 2) + 64 * i;
-    rv[i] = p < V;
-    decode(rv[i] ? p : 0, a.g, rb[i], rz[i], ry[i], rx[i]);
+  for (int i = 0; i < RPT; ++i) {
+    const int p = m0 + (tid >> 2) + i * (NTH / 4);
+    int b, z, y, x;
+    decode(p < V ? p : 0, a.g, b, z, y, x);
+    vi[i] = p;
+    li[i] = ((b * D2 + (z >> 1)) * H2 + (y >> 1)) * W2 + (x >> 1);
+    rm[i] = (z == 0) | (z == a.g.D - 1) << 1 | (y == 0) << 2 | (y == a.g.H - 1) << 3 | (x == 0) << 4 |
+            (x == a.g.W - 1) << 5 | (p >= V) << 6 | (z & 1) << 8 | (y & 1) << 9 | (x & 1) << 10;
   }
-  auto load_stage = [&](int ks, int buf) {
-    const int tap = ks / nch, cb = (ks - tap * nch) * kBK;
-    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+  // loader state: the tap and slice of the next stage to load; per tap the
+  // faces it may not cross and the neighbour offset in the full-size grid
+  int ltap = -1, lch = nch, forbid = 0, off0 = 0, dz = 0, dy = 0, dx = 0;
+  auto load = [&](int buf) {
+    if (lch == nch) {
+      lch = 0;
+      ++ltap;
+      dz = ltap / 9 - 1;
+      dy = (ltap / 3) % 3 - 1;
+      dx = ltap % 3 - 1;
+      forbid = 64 | (dz < 0) | (dz > 0) << 1 | (dy < 0) << 2 | (dy > 0) << 3 | (dx < 0) << 4 | (dx > 0) << 5;
+      off0 = (dz * a.g.H + dy) * a.g.W + dx;
+    }
+    const int cb = lch * kBK;
+    bf16 *as = As + buf * AE;
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int row = (tid >> 2) + 64 * i;
-      const bf16 *src = rv[i] ? gather_src(a.x0, a.c0, a.x1, a.c1, a.g, rb[i], rz[i] + dz, ry[i] + dy,
-                                           rx[i] + dx, cb)
-                              : nullptr;
-      cp_async16(&As[buf][row * kAS + q * 8], src ? src + q * 8 : a.w, src ? 16 : 0);
+    for (int i = 0; i < RPT; ++i) {
+      const int row = (tid >> 2) + i * (NTH / 4);
+      const bool ok = (rm[i] & forbid) == 0;
+      const bf16 *src;
+      if (cb < a.c1) {
+        // nearest upsampling: the neighbour's half-size cell moves by
+        // floor((parity + d) / 2) along each axis
+        const int oz = (((rm[i] >> 8) & 1) + dz) >> 1, oy = (((rm[i] >> 9) & 1) + dy) >> 1,
+                  ox = (((rm[i] >> 10) & 1) + dx) >> 1;
+        const int n = ok ? li[i] + (oz * H2 + oy) * W2 + ox : 0;
+        src = a.x1 + (size_t)(unsigned)n * a.c1 + cb;
+      } else {
+        const int n = ok ? vi[i] + off0 : 0;
+        src = a.x0 + (size_t)(unsigned)n * a.c0 + (cb - a.c1);
+      }
+      cp_async16(as + row * kAS + q * 8, ok ? src + q * 8 : a.w, ok ? 16 : 0);
     }
-    for (int e = tid; e < NT * 4; e += 256) {
+    bf16 *bs = Bs + buf * BE;
+    const bf16 *wt = a.w + (size_t)ltap * cin + cb;
+    for (int e = tid; e < BN * 4; e += NTH) {
       const int r = e >> 2, qq = e & 3;
-      cp_async16(&Bs[buf][r * kAS + qq * 8], a.w + ((size_t)(n0 + r) * 27 + tap) * cin + cb + qq * 8, 16);
+      cp_async16(bs + r * kAS + qq * 8, wt + (size_t)(n0 + r) * 27 * cin + qq * 8, 16);
     }
+    ++lch;
   };
 
-  constexpr int NJ = NT / 16;  // n8 tiles per warp (the warp owns NT / 2 columns)
-  float acc[2][NJ][4];
+  float acc[2][4][4];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < NJ; ++j)
+    for (int j = 0; j < 4; ++j)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
 
-  load_stage(0, 0);
-  cp_async_commit();
-  for (int ks = 0; ks < ksteps; ++ks) {
-    if (ks + 1 < ksteps) load_stage(ks + 1, (ks + 1) & 1);
+#pragma unroll
+  for (int st = 0; st < kStages - 1; ++st) {
+    if (st < ksteps) load(st);
     cp_async_commit();
-    cp_async_wait1();
+  }
+  for (int ks = 0; ks < ksteps; ++ks) {
+    cp_async_wait1();  // kStages - 2 groups may stay in flight
     __syncthreads();
-    const bf16 *as = As[ks & 1], *bs = Bs[ks & 1];
+    if (ks + kStages - 1 < ksteps) load((ks + kStages - 1) % kStages);
+    cp_async_commit();
+    const bf16 *as = As + (ks % kStages) * AE, *bs = Bs + (ks % kStages) * BE;
 #pragma unroll
     for (int kk = 0; kk < kBK; kk += 16) {
-      uint32_t af[2][4];
+      uint32_t af[2][4], bfr[2][4];
 #pragma unroll
       for (int mi = 0; mi < 2; ++mi)
         ldsm_x4(af[mi], as + (wm * 32 + mi * 16 + (lane & 15)) * kAS + kk + (lane >> 4) * 8);
 #pragma unroll
-      for (int nj2 = 0; nj2 < NJ / 2; ++nj2) {
-        uint32_t bfr[4];
-        const int nrow = wn * (NT / 2) + nj2 * 16 + ((lane >> 4) << 3) + (lane & 7);
-        ldsm_x4(bfr, bs + nrow * kAS + kk + ((lane >> 3) & 1) * 8);
+      for (int nj2 = 0; nj2 < 2; ++nj2)
+        ldsm_x4(bfr[nj2], bs + (wn * 32 + nj2 * 16 + ((lane >> 4) << 3) + (lane & 7)) * kAS + kk +
+                              ((lane >> 3) & 1) * 8);
 #pragma unroll
-        for (int mi = 0; mi < 2; ++mi) {
-          mma_bf16(acc[mi][2 * nj2], af[mi], bfr[0], bfr[1]);
-          mma_bf16(acc[mi][2 * nj2 + 1], af[mi], bfr[2], bfr[3]);
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int nj2 = 0; nj2 < 2; ++nj2) {
+          mma_bf16(acc[mi][2 * nj2], af[mi], bfr[nj2][0], bfr[nj2][1]);
+          mma_bf16(acc[mi][2 * nj2 + 1], af[mi], bfr[nj2][2], bfr[nj2][3]);
         }
-      }
     }
-    __syncthreads();
   }
 
   const int gq = lane >> 2, t4 = lane & 3;
@@ -236,8 +291,8 @@ __global__ void __launch_bounds__(256) conv_fwd_kernel(ConvArgs a) {
       const int row = m0 + wm * 32 + mi * 16 + gq + 8 * h;
       if (row >= V) continue;
 #pragma unroll
-      for (int nj = 0; nj < NJ; ++nj) {
-        const int col = n0 + wn * (NT / 2) + nj * 8 + 2 * t4;
+      for (int nj = 0; nj < 4; ++nj) {
+        const int col = n0 + wn * 32 + nj * 8 + 2 * t4;
         float v0 = acc[mi][nj][2 * h], v1 = acc[mi][nj][2 * h + 1];
         if (a.bias) {
           v0 += a.bias[col];
@@ -265,45 +320,83 @@ struct WgradArgs {
   const bf16 *x1;
   float *dw;        // [cout][27][c1 + c0], accumulated
   int c0, c1, cout, chunk;
+  int first;        // 1: x0 holds the first layer's 27 neighbour values per voxel (+5 zeros); one
+                    // unshifted "tap", output dw[o][j] for j < 27
   Vol vol;
 };
 
+constexpr int kWS = 64;  // voxels per weight-gradient stage
+
+template <int MT>
+constexpr int wgrad_smem_bytes() {
+  return kStages * kWS * ((MT + 8) + kAS) * (int)sizeof(bf16);
+}
+
+// CTA: MT output channels x 32 input channels of one tap, over one chunk of
+// voxels in stages of kWS; four warps, each (MT / 2) x 16.
 template <int MT>
 __global__ void __launch_bounds__(128) conv_wgrad_kernel(WgradArgs a) {
   constexpr int GS = MT + 8;  // shared row stride of the gradient tile (bf16)
-  __shared__ __align__(16) bf16 Gs[2][32 * GS];
-  __shared__ __align__(16) bf16 Xs[2][32 * kAS];
+  constexpr int GE = kWS * GS, XE = kWS * kAS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  bf16 *Gs = reinterpret_cast<bf16 *>(smem_raw);
+  bf16 *Xs = Gs + kStages * GE;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp & 1, wn = warp >> 1;
   const int cin = a.c0 + a.c1, nch = cin / kBK;
-  const int tap = blockIdx.x / nch, cb = (blockIdx.x - tap * nch) * kBK;
+  const int tap = a.first ? 13 : blockIdx.x / nch, cb = (blockIdx.x - (a.first ? 0 : tap) * nch) * kBK;
   const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
   const int co0 = blockIdx.y * MT;
-  const int V = nvox(a.vol);
+  const Vol &g = a.vol;
+  const int V = nvox(g);
   const int pbeg = blockIdx.z * a.chunk, pend = min(V, pbeg + a.chunk);
   if (pbeg >= pend) return;
-  const int nst = (pend - pbeg + 31) / 32;
+  const int nst = (pend - pbeg + kWS - 1) / kWS;
+  const int off0 = (dz * g.H + dy) * g.W + dx;
+  const int D2 = g.D >> 1, H2 = g.H >> 1, W2 = g.W >> 1;
 
-  auto load_stage = [&](int st, int buf) {
-    const int pb = pbeg + st * 32;
+  // the two X rows this thread gathers (r0, r0 + 32), advanced by kWS per stage
+  const int r0 = tid >> 2, xq = tid & 3;
+  int vb[2], vz[2], vy[2], vx[2];
 #pragma unroll
-    for (int i = 0; i < MT / 32; ++i) {
+  for (int i = 0; i < 2; ++i) decode(min(pbeg + r0 + 32 * i, V - 1), g, vb[i], vz[i], vy[i], vx[i]);
+  auto load = [&](int st, int buf) {
+    const int pb = pbeg + st * kWS;
+    bf16 *gs = Gs + buf * GE;
+#pragma unroll
+    for (int i = 0; i < MT / 16; ++i) {
       const int e = tid + 128 * i;
       const int r = e / (MT / 8), qq = e % (MT / 8);
       const int p = pb + r;
       const bool ok = p < pend;
-      cp_async16(&Gs[buf][r * GS + qq * 8], ok ? a.g + (size_t)p * a.cout + co0 + qq * 8 : a.g, ok ? 16 : 0);
+      cp_async16(gs + r * GS + qq * 8, ok ? a.g + (size_t)p * a.cout + co0 + qq * 8 : a.g, ok ? 16 : 0);
     }
-    {
-      const int r = tid >> 2, q = tid & 3;
-      const int p = pb + r;
-      const bf16 *src = nullptr;
-      if (p < pend) {
-        int b, z, y, x;
-        decode(p, a.vol, b, z, y, x);
-        src = gather_src(a.x0, a.c0, a.x1, a.c1, a.vol, b, z + dz, y + dy, x + dx, cb);
+    bf16 *xs = Xs + buf * XE;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int r = r0 + 32 * i, p = pb + r;
+      const int z = vz[i] + dz, y = vy[i] + dy, x = vx[i] + dx;
+      const bool ok = p < pend && z >= 0 && z < g.D && y >= 0 && y < g.H && x >= 0 && x < g.W;
+      const bf16 *src = a.g;
+      if (ok) {
+        if (cb < a.c1)
+          src = a.x1 + (size_t)(unsigned)(((vb[i] * D2 + (z >> 1)) * H2 + (y >> 1)) * W2 + (x >> 1)) * a.c1 + cb +
+                xq * 8;
+        else
+          src = a.x0 + (size_t)(unsigned)(p + off0) * a.c0 + (cb - a.c1) + xq * 8;
       }
-      cp_async16(&Xs[buf][r * kAS + q * 8], src ? src + q * 8 : a.g, src ? 16 : 0);
+      cp_async16(xs + r * kAS + xq * 8, src, ok ? 16 : 0);
+      vx[i] += kWS;
+      while (vx[i] >= g.W) {
+        vx[i] -= g.W;
+        if (++vy[i] == g.H) {
+          vy[i] = 0;
+          if (++vz[i] == g.D) {
+            vz[i] = 0;
+            ++vb[i];
+          }
+        }
+      }
     }
   };
 
@@ -316,17 +409,20 @@ __global__ void __launch_bounds__(128) conv_wgrad_kernel(WgradArgs a) {
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
 
-  load_stage(0, 0);
-  cp_async_commit();
+#pragma unroll
+  for (int st = 0; st < kStages - 1; ++st) {
+    if (st < nst) load(st, st);
+    cp_async_commit();
+  }
   const int mat = lane >> 3, r8 = lane & 7;
   for (int st = 0; st < nst; ++st) {
-    if (st + 1 < nst) load_stage(st + 1, (st + 1) & 1);
-    cp_async_commit();
     cp_async_wait1();
     __syncthreads();
-    const bf16 *gs = Gs[st & 1], *xs = Xs[st & 1];
+    if (st + kStages - 1 < nst) load(st + kStages - 1, (st + kStages - 1) % kStages);
+    cp_async_commit();
+    const bf16 *gs = Gs + (st % kStages) * GE, *xs = Xs + (st % kStages) * XE;
 #pragma unroll
-    for (int kk = 0; kk < 32; kk += 16) {
+    for (int kk = 0; kk < kWS; kk += 16) {
       uint32_t bfr[4];  // B[k = voxel][n = channel] from Xs[k][n], transposed on load
       ldsm_x4_t(bfr, xs + (kk + (mat & 1) * 8 + r8) * kAS + wn * 16 + (mat >> 1) * 8);
 #pragma unroll
@@ -337,7 +433,6 @@ __global__ void __launch_bounds__(128) conv_wgrad_kernel(WgradArgs a) {
         mma_bf16(acc[mi][1], af, bfr[2], bfr[3]);
       }
     }
-    __syncthreads();
   }
 
   const int gq = lane >> 2, t4 = lane & 3;
@@ -349,7 +444,11 @@ __global__ void __launch_bounds__(128) conv_wgrad_kernel(WgradArgs a) {
       for (int e = 0; e < 4; ++e) {
         const int o = co0 + wm * (MT / 2) + mi * 16 + gq + 8 * (e >> 1);
         const int c = cb + wn * 16 + nj * 8 + 2 * t4 + (e & 1);
-        atomicAdd(a.dw + ((size_t)o * 27 + tap) * cin + c, acc[mi][nj][e]);
+        if (a.first) {
+          if (c < 27) atomicAdd(a.dw + o * 27 + c, acc[mi][nj][e]);
+        } else {
+          atomicAdd(a.dw + ((size_t)o * 27 + tap) * cin + c, acc[mi][nj][e]);
+        }
       }
 }
 
@@ -391,31 +490,26 @@ __global__ void __launch_bounds__(256) conv_first_kernel(const float *v, const b
   }
 }
 
-// dW[o][tap] += sum_p G[p][o] v[p + delta_tap] over one chunk of voxels; thread
-// (o = tid % 32, taps tid / 32 + 8 j).
-__global__ void __launch_bounds__(256) wgrad_first_kernel(const bf16 *G, const float *v, float *dw, Vol g, int chunk) {
-  const int o = threadIdx.x & 31, tg = threadIdx.x >> 5;
+// col[p][j] = v[p + delta_j] for the 27 taps j (zero outside the volume), then
+// five zeros: the first layer's input as 32 BF16 channels, so its weight
+// gradient runs on the tensor-core weight-gradient kernel.
+__global__ void __launch_bounds__(256) im2col_first_kernel(const float *v, bf16 *col, Vol g) {
   const int V = nvox(g);
-  const int pbeg = blockIdx.x * chunk, pend = min(V, pbeg + chunk);
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int p = pbeg; p < pend; ++p) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < V; p += gridDim.x * blockDim.x) {
     int b, z, y, x;
     decode(p, g, b, z, y, x);
-    const float gv = __bfloat162float(G[(size_t)p * 32 + o]);
+    float nb[32];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int t = tg + 8 * j;
+    for (int t = 0; t < 32; ++t) {
+      nb[t] = 0.f;
       if (t < 27) {
         const int zz = z + t / 9 - 1, y2 = y + (t / 3) % 3 - 1, x2 = x + t % 3 - 1;
         if (zz >= 0 && zz < g.D && y2 >= 0 && y2 < g.H && x2 >= 0 && x2 < g.W)
-          acc[j] = fmaf(gv, v[(((size_t)b * g.D + zz) * g.H + y2) * g.W + x2], acc[j]);
+          nb[t] = v[(((size_t)b * g.D + zz) * g.H + y2) * g.W + x2];
       }
     }
-  }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int t = tg + 8 * j;
-    if (t < 27) atomicAdd(dw + o * 27 + t, acc[j]);
+    for (int c8 = 0; c8 < 4; ++c8) store8(col + (size_t)p * 32 + c8 * 8, nb + 8 * c8);
   }
 }
 
@@ -436,24 +530,6 @@ __global__ void __launch_bounds__(256) colsum_kernel(const bf16 *G, int V, int C
 }
 
 // ---------------------------------------------------------------- pooling and its transposes
-__device__ __forceinline__ void load8(const bf16 *p, float f[8]) {
-  const uint4 u = *reinterpret_cast<const uint4 *>(p);
-  const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float2 t = __bfloat1622float2(h[i]);
-    f[2 * i] = t.x;
-    f[2 * i + 1] = t.y;
-  }
-}
-__device__ __forceinline__ void store8(bf16 *p, const float f[8]) {
-  uint4 u;
-  __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&u);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
-  *reinterpret_cast<uint4 *>(p) = u;
-}
-
 // mode 0: y[q] = mean of the 8 children of q in x (x: C channels).
 // mode 1: y[q] = (sum of the 8 children of q in x[., coff : coff + C] (stride cx))
 //         zeroed where mask[q] <= 0 (transpose of nearest upsampling, then ReLU mask).
@@ -733,11 +809,11 @@ cudaError_t launch_conv(const s3ttv_net *net, const bf16 *x0, int c0, const bf16
   ConvArgs a{x0, x1, w, bias, mask, y, c0, c1, cout, relu ? 1 : 0, g};
   const int V = nvox(g);
   if (cout % 64 == 0) {
-    dim3 grid((V + kBM - 1) / kBM, cout / 64);
-    conv_fwd_kernel<64><<<grid, 256, 0, net->stream>>>(a);
+    dim3 grid((V + 127) / 128, cout / 64);
+    conv_fwd_kernel<128, 64><<<grid, 256, conv_smem_bytes<128, 64>(), net->stream>>>(a);
   } else {
-    dim3 grid((V + kBM - 1) / kBM, cout / 32);
-    conv_fwd_kernel<32><<<grid, 256, 0, net->stream>>>(a);
+    dim3 grid((V + 255) / 256, cout / 32);
+    conv_fwd_kernel<256, 32><<<grid, 256, conv_smem_bytes<256, 32>(), net->stream>>>(a);
   }
   return cudaGetLastError();
 }
@@ -745,21 +821,23 @@ cudaError_t launch_conv(const s3ttv_net *net, const bf16 *x0, int c0, const bf16
 cudaError_t launch_wgrad(const s3ttv_net *net, const bf16 *G, int cout, const bf16 *x0, int c0, const bf16 *x1,
                          int c1, float *dw, Vol g) {
   const int V = nvox(g);
-  const int MT = cout % 64 == 0 ? 64 : 32;
+  const int MT = cout % 128 == 0 ? 128 : (cout % 64 == 0 ? 64 : 32);
   const int gx = 27 * ((c0 + c1) / kBK), gy = cout / MT;
   const long long target = (long long)net->num_sms * 8;
   long long z = (target + (long long)gx * gy - 1) / ((long long)gx * gy);
-  const long long zmax = (V + 255) / 256;
+  const long long zmax = (V + 511) / 512;
   if (z > zmax) z = zmax;
   if (z < 1) z = 1;
-  int chunk = (int)(((V + z - 1) / z + 31) / 32 * 32);
+  int chunk = (int)(((V + z - 1) / z + kWS - 1) / kWS * kWS);
   z = (V + chunk - 1) / chunk;
-  WgradArgs a{G, x0, x1, dw, c0, c1, cout, chunk, g};
+  WgradArgs a{G, x0, x1, dw, c0, c1, cout, chunk, 0, g};
   dim3 grid(gx, gy, (unsigned)z);
-  if (MT == 64)
-    conv_wgrad_kernel<64><<<grid, 128, 0, net->stream>>>(a);
+  if (MT == 128)
+    conv_wgrad_kernel<128><<<grid, 128, wgrad_smem_bytes<128>(), net->stream>>>(a);
+  else if (MT == 64)
+    conv_wgrad_kernel<64><<<grid, 128, wgrad_smem_bytes<64>(), net->stream>>>(a);
   else
-    conv_wgrad_kernel<32><<<grid, 128, 0, net->stream>>>(a);
+    conv_wgrad_kernel<32><<<grid, 128, wgrad_smem_bytes<32>(), net->stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -929,11 +1007,19 @@ int run_backward(s3ttv_net *net, const float *v, const float *tu, const float *t
   NCU(cudaGetLastError());
   NCU(wgrad(1, net->gB0, net->e1a, 32, nullptr, 0, g0));
   NCU(launch_conv(net, net->gB0, 32, nullptr, 0, wbk(net, 1), nullptr, net->e1a, net->gC0, 32, false, g0));
-  // e1a (one input channel)
+  // e1a (one input channel): its 27 neighbour values as 32 channels (into gA0,
+  // free by now), then the weight gradient of one unshifted tap
+  im2col_first_kernel<<<grid_for(net, V0, 256), 256, 0, net->stream>>>(v, net->gA0, g0);
+  NCU(cudaGetLastError());
   {
-    const int blocks = grid_for(net, V0, 256);
-    const int chunk = (V0 + blocks - 1) / blocks;
-    wgrad_first_kernel<<<(V0 + chunk - 1) / chunk, 256, 0, net->stream>>>(net->gC0, v, G + T.woff[0], g0, chunk);
+    const long long target = (long long)net->num_sms * 8;
+    long long z = target;
+    const long long zmax = (V0 + 511) / 512;
+    if (z > zmax) z = zmax;
+    int chunk = (int)(((V0 + z - 1) / z + kWS - 1) / kWS * kWS);
+    z = (V0 + chunk - 1) / chunk;
+    WgradArgs wa{net->gC0, net->gA0, nullptr, G + T.woff[0], 32, 0, 32, chunk, 1, g0};
+    conv_wgrad_kernel<32><<<dim3(1, 1, (unsigned)z), 128, wgrad_smem_bytes<32>(), net->stream>>>(wa);
     NCU(cudaGetLastError());
     NCU(launch_colsum(net, net->gC0, V0, 32, G + T.boff[0]));
   }
@@ -1010,6 +1096,20 @@ int s3ttv_net_create(s3ttv_net **out, int device, void *stream) {
     cudaGetLastError();
     s3ttv_net_destroy(net);
     return S3TTV_ENOMEM;
+  }
+  if (cudaFuncSetAttribute(conv_fwd_kernel<128, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           conv_smem_bytes<128, 64>()) != cudaSuccess ||
+      cudaFuncSetAttribute(conv_fwd_kernel<256, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           conv_smem_bytes<256, 32>()) != cudaSuccess ||
+      cudaFuncSetAttribute(conv_wgrad_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           wgrad_smem_bytes<128>()) != cudaSuccess ||
+      cudaFuncSetAttribute(conv_wgrad_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           wgrad_smem_bytes<64>()) != cudaSuccess ||
+      cudaFuncSetAttribute(conv_wgrad_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           wgrad_smem_bytes<32>()) != cudaSuccess) {
+    cudaGetLastError();
+    s3ttv_net_destroy(net);
+    return S3TTV_ECUDA;
   }
   *out = net;
   return S3TTV_OK;
