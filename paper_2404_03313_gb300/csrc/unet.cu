@@ -452,6 +452,146 @@ __global__ void __launch_bounds__(128) conv_wgrad_kernel(WgradArgs a) {
       }
 }
 
+template <int MT>
+constexpr int wgrad4_smem_bytes() {
+  return kStages * kWS * ((MT + 8) + 4 * kAS) * (int)sizeof(bf16);
+}
+
+// Four taps per CTA: warp w owns tap 4 t + w (t = blockIdx.x / nch) for all MT
+// output channels x 32 input channels, so the gradient tile of a stage is
+// shared by four warps and each warp runs (MT / 16) x 4 fragments per 16 voxels.
+template <int MT>
+__global__ void __launch_bounds__(128) conv_wgrad4_kernel(WgradArgs a) {
+  constexpr int GS = MT + 8;
+  constexpr int GE = kWS * GS, XE = kWS * kAS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  bf16 *Gs = reinterpret_cast<bf16 *>(smem_raw);
+  bf16 *Xs = Gs + kStages * GE;  // [stage][tap][voxel][channel]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int cin = a.c0 + a.c1, nch = cin / kBK;
+  const int tg = blockIdx.x / nch, cb = (blockIdx.x - tg * nch) * kBK;
+  const int co0 = blockIdx.y * MT;
+  const Vol &g = a.vol;
+  const int V = nvox(g);
+  const int pbeg = blockIdx.z * a.chunk, pend = min(V, pbeg + a.chunk);
+  if (pbeg >= pend) return;
+  const int nst = (pend - pbeg + kWS - 1) / kWS;
+  const int D2 = g.D >> 1, H2 = g.H >> 1, W2 = g.W >> 1;
+  int tdz[4], tdy[4], tdx[4], toff[4];
+  bool tv[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int t = 4 * tg + j;
+    tv[j] = t < 27;
+    tdz[j] = t / 9 - 1;
+    tdy[j] = (t / 3) % 3 - 1;
+    tdx[j] = t % 3 - 1;
+    toff[j] = (tdz[j] * g.H + tdy[j]) * g.W + tdx[j];
+  }
+
+  const int r0 = tid >> 2, xq = tid & 3;
+  int vb[2], vz[2], vy[2], vx[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) decode(min(pbeg + r0 + 32 * i, V - 1), g, vb[i], vz[i], vy[i], vx[i]);
+  auto load = [&](int st, int buf) {
+    const int pb = pbeg + st * kWS;
+    bf16 *gs = Gs + buf * GE;
+#pragma unroll
+    for (int i = 0; i < MT / 16; ++i) {
+      const int e = tid + 128 * i;
+      const int r = e / (MT / 8), qq = e % (MT / 8);
+      const int p = pb + r;
+      const bool ok = p < pend;
+      cp_async16(gs + r * GS + qq * 8, ok ? a.g + (size_t)p * a.cout + co0 + qq * 8 : a.g, ok ? 16 : 0);
+    }
+    bf16 *xs = Xs + buf * 4 * XE;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int r = r0 + 32 * i, p = pb + r;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int z = vz[i] + tdz[j], y = vy[i] + tdy[j], x = vx[i] + tdx[j];
+        const bool ok = tv[j] && p < pend && z >= 0 && z < g.D && y >= 0 && y < g.H && x >= 0 && x < g.W;
+        const bf16 *src = a.g;
+        if (ok) {
+          if (cb < a.c1)
+            src = a.x1 + (size_t)(unsigned)(((vb[i] * D2 + (z >> 1)) * H2 + (y >> 1)) * W2 + (x >> 1)) * a.c1 + cb +
+                  xq * 8;
+          else
+            src = a.x0 + (size_t)(unsigned)(p + toff[j]) * a.c0 + (cb - a.c1) + xq * 8;
+        }
+        cp_async16(xs + j * XE + r * kAS + xq * 8, src, ok ? 16 : 0);
+      }
+      vx[i] += kWS;
+      while (vx[i] >= g.W) {
+        vx[i] -= g.W;
+        if (++vy[i] == g.H) {
+          vy[i] = 0;
+          if (++vz[i] == g.D) {
+            vz[i] = 0;
+            ++vb[i];
+          }
+        }
+      }
+    }
+  };
+
+  constexpr int MI = MT / 16;
+  float acc[MI][4][4];
+#pragma unroll
+  for (int i = 0; i < MI; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+
+#pragma unroll
+  for (int st = 0; st < kStages - 1; ++st) {
+    if (st < nst) load(st, st);
+    cp_async_commit();
+  }
+  const int mat = lane >> 3, r8 = lane & 7;
+  const bool active = 4 * tg + warp < 27;
+  for (int st = 0; st < nst; ++st) {
+    cp_async_wait1();
+    __syncthreads();
+    if (st + kStages - 1 < nst) load(st + kStages - 1, (st + kStages - 1) % kStages);
+    cp_async_commit();
+    if (!active) continue;
+    const bf16 *gs = Gs + (st % kStages) * GE, *xs = Xs + ((st % kStages) * 4 + warp) * XE;
+#pragma unroll
+    for (int kk = 0; kk < kWS; kk += 16) {
+      uint32_t bfr[2][4];
+#pragma unroll
+      for (int nj2 = 0; nj2 < 2; ++nj2)
+        ldsm_x4_t(bfr[nj2], xs + (kk + (mat & 1) * 8 + r8) * kAS + nj2 * 16 + (mat >> 1) * 8);
+#pragma unroll
+      for (int mi = 0; mi < MI; ++mi) {
+        uint32_t af[4];
+        ldsm_x4_t(af, gs + (kk + (mat >> 1) * 8 + r8) * GS + mi * 16 + (mat & 1) * 8);
+#pragma unroll
+        for (int nj2 = 0; nj2 < 2; ++nj2) {
+          mma_bf16(acc[mi][2 * nj2], af, bfr[nj2][0], bfr[nj2][1]);
+          mma_bf16(acc[mi][2 * nj2 + 1], af, bfr[nj2][2], bfr[nj2][3]);
+        }
+      }
+    }
+  }
+  if (!active) return;
+  const int tap = 4 * tg + warp;
+  const int gq = lane >> 2, t4 = lane & 3;
+#pragma unroll
+  for (int mi = 0; mi < MI; ++mi)
+#pragma unroll
+    for (int nj = 0; nj < 4; ++nj)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int o = co0 + mi * 16 + gq + 8 * (e >> 1);
+        const int c = cb + nj * 8 + 2 * t4 + (e & 1);
+        atomicAdd(a.dw + ((size_t)o * 27 + tap) * cin + c, acc[mi][nj][e]);
+      }
+}
+
 // ---------------------------------------------------------------- first layer (one input channel)
 __global__ void __launch_bounds__(256) conv_first_kernel(const float *v, const bf16 *w, const float *bias, bf16 *y,
                                                          Vol g) {
@@ -821,8 +961,10 @@ cudaError_t launch_conv(const s3ttv_net *net, const bf16 *x0, int c0, const bf16
 cudaError_t launch_wgrad(const s3ttv_net *net, const bf16 *G, int cout, const bf16 *x0, int c0, const bf16 *x1,
                          int c1, float *dw, Vol g) {
   const int V = nvox(g);
-  const int MT = cout % 128 == 0 ? 128 : (cout % 64 == 0 ? 64 : 32);
-  const int gx = 27 * ((c0 + c1) / kBK), gy = cout / MT;
+  // up to 64 output channels: four taps per CTA; 128: one tap per CTA
+  const bool four = cout <= 64;
+  const int MT = four ? cout : 128;
+  const int gx = (four ? 7 : 27) * ((c0 + c1) / kBK), gy = cout / MT;
   const long long target = (long long)net->num_sms * 8;
   long long z = (target + (long long)gx * gy - 1) / ((long long)gx * gy);
   const long long zmax = (V + 511) / 512;
@@ -835,9 +977,9 @@ cudaError_t launch_wgrad(const s3ttv_net *net, const bf16 *G, int cout, const bf
   if (MT == 128)
     conv_wgrad_kernel<128><<<grid, 128, wgrad_smem_bytes<128>(), net->stream>>>(a);
   else if (MT == 64)
-    conv_wgrad_kernel<64><<<grid, 128, wgrad_smem_bytes<64>(), net->stream>>>(a);
+    conv_wgrad4_kernel<64><<<grid, 128, wgrad4_smem_bytes<64>(), net->stream>>>(a);
   else
-    conv_wgrad_kernel<32><<<grid, 128, wgrad_smem_bytes<32>(), net->stream>>>(a);
+    conv_wgrad4_kernel<32><<<grid, 128, wgrad4_smem_bytes<32>(), net->stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -1106,7 +1248,11 @@ int s3ttv_net_create(s3ttv_net **out, int device, void *stream) {
       cudaFuncSetAttribute(conv_wgrad_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            wgrad_smem_bytes<64>()) != cudaSuccess ||
       cudaFuncSetAttribute(conv_wgrad_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           wgrad_smem_bytes<32>()) != cudaSuccess) {
+                           wgrad_smem_bytes<32>()) != cudaSuccess ||
+      cudaFuncSetAttribute(conv_wgrad4_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           wgrad4_smem_bytes<64>()) != cudaSuccess ||
+      cudaFuncSetAttribute(conv_wgrad4_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           wgrad4_smem_bytes<32>()) != cudaSuccess) {
     cudaGetLastError();
     s3ttv_net_destroy(net);
     return S3TTV_ECUDA;
