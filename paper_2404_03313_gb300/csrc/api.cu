@@ -240,10 +240,10 @@ int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, BdShape *sh) {
     if (sh->smem > (size_t)dev_max)
       return fail(ctx, S3TTV_EUNSUPPORTED, "a %dx%d block needs %zu bytes of shared memory (device limit %d)", k, k,
                   sh->smem, dev_max);
-    cudaError_t e = block_dual_large_prepare(sh->smem);
+    cudaError_t e = block_dual_large_prepare(k, sh->smem);
     if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
     int per_sm = 0;
-    e = block_dual_large_occupancy(sh->smem, &per_sm);
+    e = block_dual_large_occupancy(k, sh->smem, &per_sm);
     if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
     if (per_sm < 1) per_sm = 1;
     long long g = (long long)ctx->num_sms * per_sm;

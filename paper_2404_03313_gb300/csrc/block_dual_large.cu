@@ -41,7 +41,30 @@ constexpr int kCW = 64;        // columns of Y' per streamed chunk
 constexpr int kGramTiles = 3;  // upper-triangle Gram tiles a thread may own
 constexpr int kSlots = (kMaxLargeK * kMaxLargeK + 31) / 32;  // row elements a lane holds
 constexpr int kPG = 8;                                        // lanes per row pair in the Jacobi
-constexpr int kPE = (kMaxLargeK * kMaxLargeK + kPG - 1) / kPG; // row elements such a lane holds
+
+// Two FP32 values in one 64-bit register pair, and the packed FP32x2
+// arithmetic of sm_100 and later (each lane rounds as its scalar counterpart).
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 up2(f32x2 v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
 
 struct Layout {
   int n, npos, gs, cs;  // block rows, rows padded to even, row strides of the n x n buffers and the chunk
@@ -111,7 +134,10 @@ __device__ void stream_chunk(const Layout &L, float *chunk, float *Yl, const Blo
   }
 }
 
-__global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs a, int k) {
+template <int K>
+__global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs a) {
+  constexpr int k = K;
+  constexpr int PE2 = (K * K + 2 * kPG - 1) / (2 * kPG);  // float2 pieces of a row a Jacobi lane holds
   extern __shared__ __align__(16) float sm[];
   __shared__ float s_red[kLW];
   __shared__ unsigned s_sweeps;
@@ -280,25 +306,30 @@ __global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs 
       for (int step = 0; step < NP - 1; ++step) {
         // kPG lanes per pair, 32 / kPG pairs per warp side by side
         for (int base = 0; base < NP / 2; base += kLW * (32 / kPG)) {
+          if (base + warp * (32 / kPG) >= NP / 2) continue;  // the whole warp has no pair this round
           const int i = base + warp * (32 / kPG) + (lane / kPG), gl = lane % kPG;
           const bool act = i < NP / 2;
           // round robin: position 0 fixed, positions 1..NP-1 turn by one each step
           const int pa = act ? i : 0, pb = NP - 1 - pa;
-          const int ra = pa == 0 ? 0 : 1 + (pa - 1 + step) % (NP - 1);
-          const int rb = 1 + (pb - 1 + step) % (NP - 1);
+          int xa = pa - 1 + step, xb = pb - 1 + step;  // both < 2 (NP - 1)
+          xa -= xa >= NP - 1 ? NP - 1 : 0;
+          xb -= xb >= NP - 1 ? NP - 1 : 0;
+          const int ra = pa == 0 ? 0 : 1 + xa, rb = 1 + xb;
           float *A = X2 + (size_t)ra * GS, *B = X2 + (size_t)rb * GS;
-          float va[kPE], vb[kPE];
-          float d0 = 0.f, d1 = 0.f;
+          // lane gl holds the float2 pieces at columns 2 gl + 16 e; columns
+          // n..GS-1 of every row are zero, so a piece starting below n is whole
+          f32x2 va[PE2], vb[PE2];
+          f32x2 dd = 0ull;
 #pragma unroll
-          for (int e = 0; e < kPE; ++e) {
-            const int c = gl + kPG * e;
+          for (int e = 0; e < PE2; ++e) {
+            const int c = 2 * gl + 2 * kPG * e;
             const bool in = act && c < n;
-            va[e] = in ? A[c] : 0.f;
-            vb[e] = in ? B[c] : 0.f;
-            if (e & 1) d1 = fmaf(va[e], vb[e], d1);
-            else d0 = fmaf(va[e], vb[e], d0);
+            va[e] = in ? *reinterpret_cast<const f32x2 *>(A + c) : 0ull;
+            vb[e] = in ? *reinterpret_cast<const f32x2 *>(B + c) : 0ull;
+            dd = fma2(va[e], vb[e], dd);
           }
-          float d = d0 + d1;
+          const float2 d2 = up2(dd);
+          float d = d2.x + d2.y;
 #pragma unroll
           for (int o = kPG / 2; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
           const float nA = act ? nrm[ra] : 0.f, nB = act ? nrm[rb] : 0.f;
@@ -309,12 +340,13 @@ __global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs 
             const float rc = rsqrtf(hc);
             const float cs = hc * rc, sn = copysignf(0.5f, x) * y * rr * rc;
             const float dn = sn * rc * d;  // t apq
+            const f32x2 cs2 = pk2(cs, cs), sn2 = pk2(sn, sn), ns2 = pk2(-sn, -sn);
 #pragma unroll
-            for (int e = 0; e < kPE; ++e) {
-              const int c = gl + kPG * e;
+            for (int e = 0; e < PE2; ++e) {
+              const int c = 2 * gl + 2 * kPG * e;
               if (c < n) {
-                A[c] = fmaf(cs, va[e], -sn * vb[e]);
-                B[c] = fmaf(sn, va[e], cs * vb[e]);
+                *reinterpret_cast<f32x2 *>(A + c) = fma2(cs2, va[e], mul2(ns2, vb[e]));
+                *reinterpret_cast<f32x2 *>(B + c) = fma2(sn2, va[e], mul2(cs2, vb[e]));
               }
             }
             if (gl == 0) {
@@ -444,25 +476,41 @@ int block_dual_large_threads() { return kLT; }
 
 // The launch limit is raised to the device's opt-in maximum (less the static
 // shared memory): every context launching the kernel shares the attribute.
-cudaError_t block_dual_large_prepare(size_t smem) {
+namespace {
+typedef void (*LargeKernel)(BlockDualArgs);
+LargeKernel large_kernel(int k) {
+  static const LargeKernel table[] = {block_dual_large_kernel<6>,  block_dual_large_kernel<7>,
+                                      block_dual_large_kernel<8>,  block_dual_large_kernel<9>,
+                                      block_dual_large_kernel<10>, block_dual_large_kernel<11>,
+                                      block_dual_large_kernel<12>};
+  return k >= kMinLargeK && k <= kMaxLargeK ? table[k - kMinLargeK] : nullptr;
+}
+}  // namespace
+
+cudaError_t block_dual_large_prepare(int k, size_t smem) {
+  const LargeKernel f = large_kernel(k);
+  if (!f) return cudaErrorInvalidValue;
   int dev = 0, cap = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaFuncAttributes fa;
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, block_dual_large_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, f);
   if (e != cudaSuccess) return e;
   const size_t dyn = (size_t)cap > fa.sharedSizeBytes ? (size_t)cap - fa.sharedSizeBytes : 0;
   if (dyn < smem) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(block_dual_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
 }
 
-cudaError_t block_dual_large_occupancy(size_t smem, int *ctas) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, block_dual_large_kernel, kLT, smem);
+cudaError_t block_dual_large_occupancy(int k, size_t smem, int *ctas) {
+  const LargeKernel f = large_kernel(k);
+  if (!f) return cudaErrorInvalidValue;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, f, kLT, smem);
 }
 
 cudaError_t launch_block_dual_large(const BlockDualArgs &a, int k, int grid, size_t smem, cudaStream_t st) {
-  if (k < kMinLargeK || k > kMaxLargeK) return cudaErrorInvalidValue;
-  block_dual_large_kernel<<<grid, kLT, smem, st>>>(a, k);
+  const LargeKernel f = large_kernel(k);
+  if (!f) return cudaErrorInvalidValue;
+  f<<<grid, kLT, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -154,8 +154,8 @@ constexpr int kMinLargeK = 6, kMaxLargeK = 12;
 size_t block_dual_large_smem_bytes(int k);
 long long block_dual_large_w_stride(int k);
 int block_dual_large_threads();
-cudaError_t block_dual_large_prepare(size_t smem_bytes);
-cudaError_t block_dual_large_occupancy(size_t smem_bytes, int *ctas_per_sm);
+cudaError_t block_dual_large_prepare(int k, size_t smem_bytes);
+cudaError_t block_dual_large_occupancy(int k, size_t smem_bytes, int *ctas_per_sm);
 cudaError_t launch_block_dual_large(const BlockDualArgs &a, int k, int grid, size_t smem, cudaStream_t st);
 cudaError_t block_dual_prepare(const BdVariant &v, size_t smem_bytes);
 cudaError_t block_dual_occupancy(const BdVariant &v, size_t smem_bytes, int *ctas_per_sm);
