@@ -236,6 +236,30 @@ int s3ttv_l1_ball(s3ttv_ctx *ctx, const float *x, float *out, long long n,
 int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, float *Zh,
                      int N1, int N2, int N3, int k, float gamma_Y, s3ttv_info *info);
 
+/* Objective value S3TTV(u) = sum_l || P_l D D_s u ||_* of Prob.
+ * (S3TTV_denoising) (eq. rewrite_Lu): the sum of the nuclear norms of the
+ * k^2 x 2N3 structure tensors of all N1*N2 blocks.  u: cube (host or device);
+ * value: host double.  Computed in FP64 (the block entries from the FP32 cube,
+ * the Gram of each block and a one-sided Jacobi on its rows, sigma =
+ * sqrt(eigenvalue)); an evaluation aid, far slower than a solver pass.
+ * S3TTV_ENUMERIC if u is not finite or a block does not converge; k <= 12. */
+int s3ttv_objective(s3ttv_ctx *ctx, const float *u, int N1, int N2, int N3, int k, double *value);
+
+/* Quality of a restored cube u against a reference cube ref (both host or
+ * device, same shape), the measures of Sec. IV-A:
+ *   mpsnr     eq. (MPSNR), peak 1, averaged over the bands left after dropping
+ *             the first and last `trim` (all bands if N3 <= 2 trim);
+ *   mssim     eq. (MSSIM): SSIM [Wang et al. 2004] of each of those bands with
+ *             the 11 x 11 Gaussian window of standard deviation 1.5 over every
+ *             pixel whose window lies inside the image, C1 = 0.01^2,
+ *             C2 = 0.03^2 (dynamic range 1); needs N1, N2 >= 11;
+ *   sam_mean  eq. (2D_SAM) averaged over all pixels, radians (a pixel where one
+ *             spectrum is zero counts pi/2, where both are zero 0);
+ *   sam_map   the 2-D SAM itself, N1*N2 floats [N1][N2] (host or device).
+ * Any output may be NULL (its work is skipped).  Sums in FP64. */
+int s3ttv_quality(s3ttv_ctx *ctx, const float *u, const float *ref, int N1, int N2, int N3, int trim,
+                  double *mpsnr, double *mssim, double *sam_mean, float *sam_map);
+
 /* Allocation-free l1-ball projection.  The paper has no counterpart: this entry
  * point exists for callers that cannot call cudaMalloc, such as code whose
  * device memory is owned by an arena or pool it may not bypass, a plug-in whose

@@ -36,7 +36,8 @@ __all__ = [
     "linear_op_adjoint_u_at",
     "prox_nuclear", "block_dual_update", "proj_box", "proj_l2_ball",
     "proj_l1_ball", "step_sizes", "assemble_operator", "lemma1_step_sizes",
-    "radii", "init_state", "iterate", "solve", "mpsnr", "objective",
+    "radii", "init_state", "iterate", "solve", "mpsnr", "objective", "ssim_window", "ssim_band", "mssim",
+    "sam_map",
 ]
 
 AXIS_V, AXIS_H, AXIS_S = 0, 1, 2
@@ -380,3 +381,66 @@ def objective(u: np.ndarray, k: int) -> float:
     """S3TTV(u) = sum_l ||T_u^(l)||_*, eq. (S3TTV_Lu)."""
     X = structure_tensors(np.asarray(u, np.float64), k)
     return float(np.linalg.svd(X, compute_uv=False).sum())
+
+
+def ssim_window(radius: int = 5, sigma: float = 1.5) -> np.ndarray:
+    """The (2 radius + 1)^2 Gaussian window of [Wang et al. 2004] (standard
+    deviation 1.5, 11 x 11), normalized to sum 1."""
+    x = np.arange(-radius, radius + 1, dtype=np.float64)
+    g = np.exp(-(x[:, None] ** 2 + x[None, :] ** 2) / (2.0 * sigma * sigma))
+    return g / g.sum()
+
+
+def ssim_band(x: np.ndarray, y: np.ndarray, L: float = 1.0) -> float:
+    """SSIM of two images [Wang et al. 2004] as eq. (MSSIM) cites it: local
+    Gaussian-weighted means mu, variances sigma^2 and covariance sigma_xy at
+    every pixel whose whole 11 x 11 window lies inside the image ("valid"
+    windows), the map ((2 mu_x mu_y + C1)(2 sigma_xy + C2)) /
+    ((mu_x^2 + mu_y^2 + C1)(sigma_x^2 + sigma_y^2 + C2)) with C1 = (0.01 L)^2 and
+    C2 = (0.03 L)^2, averaged over those pixels."""
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    w = ssim_window()
+    r = w.shape[0] // 2
+    H, W = x.shape
+    C1, C2 = (0.01 * L) ** 2, (0.03 * L) ** 2
+
+    def filt(img):
+        out = np.zeros((H - 2 * r, W - 2 * r))
+        for a in range(2 * r + 1):
+            for b in range(2 * r + 1):
+                out += w[a, b] * img[a:a + H - 2 * r, b:b + W - 2 * r]
+        return out
+
+    mx, my = filt(x), filt(y)
+    sxx = filt(x * x) - mx * mx
+    syy = filt(y * y) - my * my
+    sxy = filt(x * y) - mx * my
+    m = ((2 * mx * my + C1) * (2 * sxy + C2)) / ((mx * mx + my * my + C1) * (sxx + syy + C2))
+    return float(m.mean())
+
+
+def mssim(u: np.ndarray, ref: np.ndarray, trim: int = 3) -> float:
+    """eq. (MSSIM): the SSIM of every band, averaged over the bands left after
+    dropping the first and last ``trim`` (as for MPSNR)."""
+    u = np.asarray(u, np.float64)
+    ref = np.asarray(ref, np.float64)
+    N3 = u.shape[2]
+    bands = range(trim, N3 - trim) if N3 > 2 * trim else range(N3)
+    return float(np.mean([ssim_band(ref[:, :, b], u[:, :, b]) for b in bands]))
+
+
+def sam_map(u: np.ndarray, ref: np.ndarray) -> np.ndarray:
+    """eq. (2D_SAM): the angle (radians) between the spectra of u and ref at
+    every pixel, arccos of the normalized inner product clipped to [-1, 1]; a
+    pixel where either spectrum is zero gets pi / 2 (0 if both are zero)."""
+    u = np.asarray(u, np.float64)
+    ref = np.asarray(ref, np.float64)
+    dot = (u * ref).sum(axis=2)
+    nu = np.sqrt((u * u).sum(axis=2))
+    nr = np.sqrt((ref * ref).sum(axis=2))
+    out = np.empty(dot.shape)
+    both = (nu > 0) & (nr > 0)
+    out[both] = np.arccos(np.clip(dot[both] / (nu[both] * nr[both]), -1.0, 1.0))
+    out[~both] = np.where((nu[~both] == 0) & (nr[~both] == 0), 0.0, np.pi / 2)
+    return out

@@ -66,6 +66,8 @@ SIGNATURES = {
     "s3ttv_l1_ball_static": (_c_int, [_vp, _vp, _c_ll, _c_d, _P(_c_d), _vp]),
     "s3ttv_radii": (_c_int, [_c_ll, _c_d, _c_d, _c_d, _c_d, _P(_c_d), _P(_c_d), _P(_c_d)]),
     "s3ttv_step_sizes": (_c_int, [_c_int, _c_int, _c_int, _c_int, _P(_c_d)]),
+    "s3ttv_objective": (_c_int, [_vp, _vp, _c_int, _c_int, _c_int, _c_int, _P(_c_d)]),
+    "s3ttv_quality": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _c_int, _P(_c_d), _P(_c_d), _P(_c_d), _vp]),
     "s3ttv_net_param_count": (_c_ll, []),
     "s3ttv_net_create": (_c_int, [_P(_vp), _c_int, _vp]),
     "s3ttv_net_destroy": (None, [_vp]),
@@ -315,6 +317,33 @@ class Solver:
         self._check(self._lib.s3ttv_l1_ball(self._h, _ptr(x, n, "x"), _ptr(out, n, "out"), n, float(radius),
                                             ctypes.byref(tau)), "s3ttv_l1_ball")
         return out, tau.value
+
+    def objective(self, u, k):
+        """S3TTV(u), the sum of the nuclear norms of the structure tensors of all blocks."""
+        N1, N2, N3 = u.shape
+        val = ctypes.c_double()
+        _sync_torch(u)
+        self._check(self._lib.s3ttv_objective(self._h, _ptr(u, N1 * N2 * N3, "u"), N1, N2, N3, int(k),
+                                              ctypes.byref(val)), "s3ttv_objective")
+        return val.value
+
+    def quality(self, u, ref, trim=3, sam_map=False):
+        """{mpsnr, mssim, sam} of u against ref (MSSIM needs N1, N2 >= 11), plus
+        the 2-D SAM map (N1, N2) when sam_map is true."""
+        N1, N2, N3 = u.shape
+        n = N1 * N2 * N3
+        ps, ss, sm = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        want_ssim = N1 >= 11 and N2 >= 11
+        m = _empty_like(u, (N1, N2)) if sam_map else None
+        _sync_torch(u, ref)
+        self._check(self._lib.s3ttv_quality(self._h, _ptr(u, n, "u"), _ptr(ref, n, "ref"), N1, N2, N3, int(trim),
+                                            ctypes.byref(ps), ctypes.byref(ss) if want_ssim else None,
+                                            ctypes.byref(sm), _ptr(m, N1 * N2, "sam_map") if sam_map else None),
+                    "s3ttv_quality")
+        out = {"mpsnr": ps.value, "mssim": ss.value if want_ssim else None, "sam": sm.value}
+        if sam_map:
+            out["sam_map"] = m
+        return out
 
     def block_dual(self, Y, ubar, k, gamma_Y=0.25):
         """Alg. 1 steps 8-11 on every block; Y (L, k*k, 2*N3) is updated in place.

@@ -46,6 +46,8 @@ struct s3ttv_ctx {
   double *part = nullptr;  // [3][kMaxGrid]
   unsigned *hcnt = nullptr;
   double *hsum = nullptr;
+  double *macc = nullptr;  // accumulators of s3ttv_quality / s3ttv_objective
+  size_t cap_macc = 0;
   size_t bytes = 0;
   // launch accounting and optional per-class event timing
   long long launches = 0;
@@ -124,6 +126,9 @@ void free_all(s3ttv_ctx *c) {
   if (c->part) cudaFree(c->part);
   if (c->hcnt) cudaFree(c->hcnt);
   if (c->hsum) cudaFree(c->hsum);
+  if (c->macc) cudaFree(c->macc);
+  c->macc = nullptr;
+  c->cap_macc = 0;
   c->sc = nullptr;
   c->part = nullptr;
   c->hcnt = nullptr;
@@ -173,6 +178,20 @@ int ensure_stage(s3ttv_ctx *ctx, size_t elems) {
 }
 
 // Problem-sized buffers; reuses them when they are large enough.
+int ensure_macc(s3ttv_ctx *ctx, size_t n) {
+  if (n <= ctx->cap_macc) return S3TTV_OK;
+  if (ctx->macc) {
+    cudaFree(ctx->macc);
+    ctx->bytes -= ctx->cap_macc * sizeof(double);
+    ctx->macc = nullptr;
+    ctx->cap_macc = 0;
+  }
+  int rc = dmalloc(ctx, (void **)&ctx->macc, n * sizeof(double));
+  if (rc) return rc;
+  ctx->cap_macc = n;
+  return S3TTV_OK;
+}
+
 int ensure_problem_buffers(s3ttv_ctx *ctx, const Dims &dm, int k) {
   const size_t np = (size_t)dm.Np;
   const size_t ny = (size_t)dm.P * k * k * 2 * dm.N3p;
@@ -1122,6 +1141,93 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
     info->jacobi_nonconverged = (int)hs.jacobi_fail;
     info->jacobi_sweeps = (double)hs.jacobi_sweeps / (double)dm.P;
   }
+  return S3TTV_OK;
+}
+
+int s3ttv_objective(s3ttv_ctx *ctx, const float *u, int N1, int N2, int N3, int k, double *value) {
+  if (!ctx) return S3TTV_EINVAL;
+  if (!u || !value) return fail(ctx, S3TTV_EINVAL, "u and value are required");
+  if (k < 1 || N1 < k || N2 < k || N3 < 1) return fail(ctx, S3TTV_EINVAL, "need N1, N2 >= k >= 1 and N3 >= 1");
+  if (k > kMaxK) return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: this build supports k <= %d", k, kMaxK);
+  DeviceGuard g(ctx->device);
+  int rc;
+  const long long N = (long long)N1 * N2 * N3;
+  const float *du = u;
+  if (!is_device_ptr(u)) {
+    if ((rc = ensure_stage(ctx, (size_t)N))) return rc;
+    CU(cudaMemcpyAsync(ctx->stage, u, sizeof(float) * N, cudaMemcpyHostToDevice, ctx->stream));
+    du = ctx->stage;
+  }
+  if ((rc = ensure_macc(ctx, 2))) return rc;
+  CU(cudaMemsetAsync(ctx->macc, 0, 2 * sizeof(double), ctx->stream));
+  unsigned *nonconv = reinterpret_cast<unsigned *>(ctx->macc + 1);
+  int dev_max = 0;
+  CU(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+  if (objective_smem_bytes(k) + 2048 > (size_t)dev_max)
+    return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d needs %zu bytes of shared memory", k, objective_smem_bytes(k));
+  CU(launch_objective(du, N1, N2, N3, k, ctx->macc, nonconv, ctx->num_sms * 4, ctx->stream));
+  double h[2] = {0.0, 0.0};
+  CU(cudaMemcpyAsync(h, ctx->macc, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  unsigned nc;
+  memcpy(&nc, &h[1], sizeof(nc));
+  if (nc) return fail(ctx, S3TTV_ENUMERIC, "%u blocks did not converge in the FP64 Jacobi", nc);
+  if (!std::isfinite(h[0])) return fail(ctx, S3TTV_ENUMERIC, "u is not finite");
+  *value = h[0];
+  return S3TTV_OK;
+}
+
+int s3ttv_quality(s3ttv_ctx *ctx, const float *u, const float *ref, int N1, int N2, int N3, int trim,
+                  double *mpsnr, double *mssim, double *sam_mean, float *sam_map) {
+  if (!ctx) return S3TTV_EINVAL;
+  if (!u || !ref) return fail(ctx, S3TTV_EINVAL, "u and ref are required");
+  if (N1 < 1 || N2 < 1 || N3 < 1 || trim < 0) return fail(ctx, S3TTV_EINVAL, "need N1, N2, N3 >= 1 and trim >= 0");
+  const int r = kSsimTaps / 2;
+  if (mssim && (N1 <= 2 * r || N2 <= 2 * r))
+    return fail(ctx, S3TTV_EINVAL, "MSSIM needs N1, N2 >= %d (one whole %dx%d window)", 2 * r + 1, 2 * r + 1,
+                2 * r + 1);
+  DeviceGuard g(ctx->device);
+  int rc;
+  if ((rc = ensure_common(ctx))) return rc;
+  const long long P = (long long)N1 * N2, N = P * N3;
+  const int b0 = N3 > 2 * trim ? trim : 0, nb = N3 > 2 * trim ? N3 - 2 * trim : N3;
+  const bool ud = is_device_ptr(u), rd = is_device_ptr(ref), md = !sam_map || is_device_ptr(sam_map);
+  if (!ud || !rd || !md) {
+    if ((rc = ensure_stage(ctx, (size_t)(2 * N + P)))) return rc;
+  }
+  const float *du = u, *dr = ref;
+  if (!ud) {
+    CU(cudaMemcpyAsync(ctx->stage, u, sizeof(float) * N, cudaMemcpyHostToDevice, ctx->stream));
+    du = ctx->stage;
+  }
+  if (!rd) {
+    CU(cudaMemcpyAsync(ctx->stage + N, ref, sizeof(float) * N, cudaMemcpyHostToDevice, ctx->stream));
+    dr = ctx->stage + N;
+  }
+  float *dmap = sam_map ? (md ? sam_map : ctx->stage + 2 * N) : nullptr;
+  if ((rc = ensure_macc(ctx, (size_t)2 * N3 + 1))) return rc;
+  CU(cudaMemsetAsync(ctx->macc, 0, sizeof(double) * (2 * N3 + 1), ctx->stream));
+  const int grid = ctx->num_sms * 8;
+  if (mpsnr) CU(launch_band_sqerr(du, dr, P, N3, ctx->macc, grid, ctx->stream));
+  if (mssim) CU(launch_ssim(du, dr, N1, N2, N3, b0, nb, ctx->macc + N3, grid, ctx->stream));
+  if (sam_mean || sam_map) CU(launch_sam(du, dr, P, N3, dmap, ctx->macc + 2 * N3, grid, ctx->stream));
+  if (sam_map && !md)
+    CU(cudaMemcpyAsync(sam_map, dmap, sizeof(float) * P, cudaMemcpyDeviceToHost, ctx->stream));
+  std::vector<double> h((size_t)2 * N3 + 1);
+  CU(cudaMemcpyAsync(h.data(), ctx->macc, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  if (mpsnr) {
+    double s = 0.0;
+    for (int b = b0; b < b0 + nb; ++b) s += h[b] > 0.0 ? 10.0 * log10((double)P / h[b]) : INFINITY;
+    *mpsnr = s / nb;
+  }
+  if (mssim) {
+    const double npix = (double)(N1 - 2 * r) * (N2 - 2 * r);
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += h[N3 + b] / npix;
+    *mssim = s / nb;
+  }
+  if (sam_mean) *sam_mean = h[2 * N3] / (double)P;
   return S3TTV_OK;
 }
 

@@ -170,4 +170,16 @@ cudaError_t launch_xfield(const float *ubar, float *Fv, float *Fh, Dims dm, int 
 cudaError_t launch_Z_from_Y(const float *Y, float *Zv, float *Zh, Dims dm, int k, cudaStream_t st);
 cudaError_t launch_init_scalars(Scalars *sc, double alpha, double beta, cudaStream_t st);
 
+// evaluation (metrics.cu); plain [N1][N2][N3] cubes, FP64 sums
+constexpr int kSsimTaps = 11;
+cudaError_t launch_band_sqerr(const float *u, const float *ref, long long P, int N3, double *out, int grid,
+                              cudaStream_t st);
+cudaError_t launch_sam(const float *u, const float *ref, long long P, int N3, float *map, double *sum, int grid,
+                       cudaStream_t st);
+cudaError_t launch_ssim(const float *u, const float *ref, int N1, int N2, int N3, int b0, int nb, double *out,
+                        int grid, cudaStream_t st);
+size_t objective_smem_bytes(int k);
+cudaError_t launch_objective(const float *u, int N1, int N2, int N3, int k, double *out, unsigned *nonconv,
+                             int grid, cudaStream_t st);
+
 }  // namespace s3ttv

@@ -66,6 +66,8 @@ WORKLOADS = {
     "profile_128x128x128_k5": CubeSpec(128, 128, 128, regions=16, endmembers=5, sigma=0.05,
                                        p_s=0.05, p_t=0.10, k=5, seed=0),
     # the paper's own scene sizes (Sec. IV) with its 10 x 10 blocks
+    "profile_64x64x64_k10": CubeSpec(64, 64, 64, regions=8, endmembers=5, sigma=0.1, p_s=0.05, p_t=0.05,
+                                     k=10, seed=0),
     "paper_100x100x198_k10": CubeSpec(100, 100, 198, regions=8, endmembers=5, sigma=0.1,
                                       p_s=0.05, p_t=0.05, k=10, seed=0),
     "paper_120x120x98_k10": CubeSpec(120, 120, 98, regions=8, endmembers=5, sigma=0.1,

@@ -454,3 +454,84 @@ def test_parity_cube_improves_mpsnr():
     assert it == 300
     assert O.mpsnr(st["u"], clean) > O.mpsnr(v, clean) + 1.0
     assert np.median(trace[-20:]) < np.median(trace[1:21])
+
+
+# ---------------------------------------------------------------------------
+# Evaluation metrics: objective S3TTV(u), MSSIM (eq. MSSIM), SAM (eq. 2D_SAM)
+# ---------------------------------------------------------------------------
+def test_objective_k1_is_a_sum_of_row_norms():
+    """With 1 x 1 blocks each structure tensor is one row (the 2 N3 second
+    differences of one pixel), whose only singular value is its l2 norm."""
+    r = np.random.default_rng(21)
+    u = r.standard_normal((5, 6, 4))
+    dvs = np.roll(np.roll(u, -1, 0) - u, -1, 2) - (np.roll(u, -1, 0) - u)
+    dhs = np.roll(np.roll(u, -1, 1) - u, -1, 2) - (np.roll(u, -1, 1) - u)
+    expect = np.sqrt((dvs ** 2).sum(axis=2) + (dhs ** 2).sum(axis=2)).sum()
+    assert O.objective(u, 1) == pytest.approx(expect, rel=1e-12)
+
+
+def test_objective_invariances():
+    r = np.random.default_rng(22)
+    u = r.uniform(0, 1, (6, 7, 5))
+    f = O.objective(u, 3)
+    assert f > 0
+    assert O.objective(u + 0.37, 3) == pytest.approx(f, rel=1e-12)  # differences remove constants
+    assert O.objective(-2.5 * u, 3) == pytest.approx(2.5 * f, rel=1e-12)  # absolute homogeneity
+    flat = np.repeat(r.uniform(0, 1, (6, 7, 1)), 5, axis=2)  # spectrally flat: D_s u = 0
+    assert O.objective(flat, 3) == 0.0
+
+
+def _ssim_loops(x, y):
+    """SSIM written pixel by pixel with explicit window loops."""
+    w = O.ssim_window()
+    H, W = x.shape
+    C1, C2 = 1e-4, 9e-4
+    vals = []
+    for i in range(5, H - 5):
+        for j in range(5, W - 5):
+            mx = my = sxx = syy = sxy = 0.0
+            for a in range(11):
+                for b in range(11):
+                    xv, yv, wt = x[i + a - 5, j + b - 5], y[i + a - 5, j + b - 5], w[a, b]
+                    mx += wt * xv
+                    my += wt * yv
+                    sxx += wt * xv * xv
+                    syy += wt * yv * yv
+                    sxy += wt * xv * yv
+            sxx -= mx * mx
+            syy -= my * my
+            sxy -= mx * my
+            vals.append(((2 * mx * my + C1) * (2 * sxy + C2)) / ((mx * mx + my * my + C1) * (sxx + syy + C2)))
+    return float(np.mean(vals))
+
+
+def test_ssim_window_is_the_standard_gaussian():
+    w = O.ssim_window()
+    assert w.shape == (11, 11) and abs(w.sum() - 1.0) < 1e-15
+    assert w[5, 6] / w[5, 5] == pytest.approx(np.exp(-1 / 4.5), rel=1e-13)
+
+
+def test_ssim_against_loops_and_closed_forms():
+    r = np.random.default_rng(23)
+    x = r.uniform(0, 1, (13, 14))
+    y = np.clip(x + 0.1 * r.standard_normal((13, 14)), 0, 1)
+    assert O.ssim_band(x, y) == pytest.approx(_ssim_loops(x, y), rel=1e-12)
+    assert O.ssim_band(x, x) == pytest.approx(1.0, abs=1e-15)
+    assert O.ssim_band(x, y) == pytest.approx(O.ssim_band(y, x), rel=1e-14)
+    # constant images a, b: variances vanish, SSIM = (2ab + C1) / (a^2 + b^2 + C1)
+    a, b = 0.3, 0.7
+    cx, cy = np.full((12, 12), a), np.full((12, 12), b)
+    assert O.ssim_band(cx, cy) == pytest.approx((2 * a * b + 1e-4) / (a * a + b * b + 1e-4), rel=1e-12)
+    u = np.stack([x, y, x], axis=2)
+    assert O.mssim(u, u, trim=0) == pytest.approx(1.0, abs=1e-15)
+
+
+def test_sam_hand_cases():
+    ref = np.zeros((1, 5, 2))
+    u = np.zeros((1, 5, 2))
+    ref[0, 0], u[0, 0] = (1, 0), (0, 1)        # orthogonal: pi / 2
+    ref[0, 1], u[0, 1] = (1, 1), (1, 0)        # 45 degrees
+    ref[0, 2], u[0, 2] = (0.2, 0.4), (1, 2)    # parallel, scaled: 0
+    ref[0, 3], u[0, 3] = (1, 0), (-1, 0)       # opposite: pi
+    ref[0, 4] = (0, 0)                         # both zero: 0
+    np.testing.assert_allclose(O.sam_map(u, ref)[0], [np.pi / 2, np.pi / 4, 0.0, np.pi, 0.0], atol=1e-7)
