@@ -37,7 +37,7 @@ namespace {
 
 constexpr int kLW = 8;         // warps per CTA (two CTAs per SM where shared memory allows)
 constexpr int kLT = kLW * 32;  // threads per CTA
-constexpr int kCW = 64;        // columns of Y' per streamed chunk
+constexpr int kCW = 48;        // columns of Y' per streamed chunk
 constexpr int kGramTiles = 3;  // upper-triangle Gram tiles a thread may own
 constexpr int kSlots = (kMaxLargeK * kMaxLargeK + 31) / 32;  // row elements a lane holds
 constexpr int kPG = 8;                                        // lanes per row pair in the Jacobi
@@ -78,7 +78,10 @@ __host__ __device__ inline Layout layout(int k) {
   L.npos = (L.n + 1) & ~1;
   L.nt4 = (L.npos + 3) / 4;
   const int w = 4 * L.nt4;  // rows and columns rounded to whole tiles
-  L.gs = w + 4;             // a multiple of 4 (float4 rows)
+  // a multiple of 4 (float4 rows) and 16 mod 32: consecutive rows start 16
+  // banks apart, so the two 8-lane Jacobi groups of a half-warp, which read
+  // neighbouring rows, touch disjoint banks
+  L.gs = w + (16 - w % 32 + 32) % 32;
   L.cs = kCW + 4;
   L.x1 = 0;
   L.x2 = L.x1 + (size_t)w * L.gs;
