@@ -282,6 +282,32 @@ class Solver:
                                    mu_min, mu_max, k)
         self._check(rc, "s3ttv_setup")
         self.shape, self.k = (N1, N2, N3), k
+        self._problem = {"v": v, "eps": float(eps), "alpha": float(alpha), "beta": float(beta), "k": int(k),
+                         "mu_min": float(mu_min), "mu_max": float(mu_max)}
+
+    def save(self, path):
+        """Write the problem and the whole P-PDS state (u, s, t, y2, y3 and the
+        block duals Y) to a .npz file, so that a later ``load`` continues the
+        iteration where it stopped (the eigen-solves then start cold once)."""
+        p = getattr(self, "_problem", None)
+        if p is None:
+            raise S3TTVError(ESTATE, "save before setup")
+        v = p["v"].cpu().numpy() if _is_torch(p["v"]) else np.asarray(p["v"])
+        arrays = {name: self.get_state(name) for name in STATE}
+        np.savez(path, v=v, **arrays, **{key: np.asarray(p[key]) for key in
+                                        ("eps", "alpha", "beta", "k", "mu_min", "mu_max")})
+
+    def load(self, path, device_arrays=True):
+        """Set up the problem stored by ``save`` and restore its state."""
+        z = np.load(path)
+        v = np.ascontiguousarray(z["v"], dtype=np.float32)
+        if device_arrays:
+            import torch
+            v = torch.from_numpy(v).to(f"cuda:{self.device}")
+        self.setup(v, float(z["eps"]), float(z["alpha"]), float(z["beta"]), int(z["k"]), float(z["mu_min"]),
+                   float(z["mu_max"]))
+        for name in STATE:
+            self.set_state(name, np.ascontiguousarray(z[name], dtype=np.float32))
 
     def iterate(self, n, tol=0.0):
         info = Info()
