@@ -31,7 +31,7 @@ import math
 import numpy as np
 
 __all__ = [
-    "AXIS_V", "AXIS_H", "AXIS_S", "diff", "diff_adj", "structure_tensors",
+    "AXIS_V", "AXIS_H", "AXIS_S", "diff", "diff_adj", "spectral_diffs", "spectral_diff_adjoint", "structure_tensors",
     "structure_tensors_adjoint", "structure_tensor_block", "linear_op_adjoint_u",
     "linear_op_adjoint_u_at",
     "prox_nuclear", "block_dual_update", "proj_box", "proj_l2_ball",
@@ -59,25 +59,46 @@ def diff_adj(y: np.ndarray, axis: int) -> np.ndarray:
 # ----------------------------------------------------------------------------
 # Sec. III-A: spatio-spectral structure tensors T_u^(l) = P_l D D_s u.
 # ----------------------------------------------------------------------------
-def structure_tensors(u: np.ndarray, k: int) -> np.ndarray:
-    """All structure tensors of eq. (SSST) / eq. (rewrite_Lu), shape (L, k*k, 2*N3).
+def spectral_diffs(u: np.ndarray, periodic_s: bool = True):
+    """(D_v D_s u, D_h D_s u).  With periodic_s (Sec. II-A) D_s wraps from the
+    last band to the first and both have N3 bands; otherwise D_s stops at the
+    last band (x[b+1] - x[b], b < N3 - 1) and both have N3 - 1 bands."""
+    Ds = diff(u, AXIS_S) if periodic_s else u[..., 1:] - u[..., :-1]
+    return diff(Ds, AXIS_V), diff(Ds, AXIS_H)
+
+
+def structure_tensors(u: np.ndarray, k: int, layout: str = "paper", periodic_s: bool = True) -> np.ndarray:
+    """All structure tensors of eq. (SSST) / eq. (rewrite_Lu).
 
     Block l = p*N2 + q holds the second-order differences D_v D_s u and D_h D_s u
     of the k x k window whose pixels are ((p+a) mod N1, (q+c) mod N2) (the
     footnote of Sec. III-A pads a window at the border with pixels from the
-    opposite side).  Row r = a*k + c; columns [v_1 h_1 ... v_N3 h_N3].
+    opposite side); window pixel r = a*k + c.
+    layout "paper" (eq. SSST): shape (L, k*k, 2*M), row r, columns
+    [v_1 h_1 ... v_M h_M].  layout "stacked": shape (L, 2*k*k, M), row 2r the
+    vertical and row 2r + 1 the horizontal differences of pixel r, one column per
+    band.  M = N3 with the periodic D_s, N3 - 1 without.
     """
     N1, N2, N3 = u.shape
-    Ds = diff(u, AXIS_S)
-    Fv = diff(Ds, AXIS_V)
-    Fh = diff(Ds, AXIS_H)
-    X = np.empty((N1, N2, k * k, 2 * N3))
-    for a in range(k):
-        for c in range(k):
-            r = a * k + c
-            X[:, :, r, 0::2] = np.roll(Fv, shift=(-a, -c), axis=(0, 1))
-            X[:, :, r, 1::2] = np.roll(Fh, shift=(-a, -c), axis=(0, 1))
-    return X.reshape(N1 * N2, k * k, 2 * N3)
+    Fv, Fh = spectral_diffs(u, periodic_s)
+    M = Fv.shape[2]
+    if layout == "paper":
+        X = np.empty((N1, N2, k * k, 2 * M))
+        for a in range(k):
+            for c in range(k):
+                r = a * k + c
+                X[:, :, r, 0::2] = np.roll(Fv, shift=(-a, -c), axis=(0, 1))
+                X[:, :, r, 1::2] = np.roll(Fh, shift=(-a, -c), axis=(0, 1))
+        return X.reshape(N1 * N2, k * k, 2 * M)
+    if layout == "stacked":
+        X = np.empty((N1, N2, 2 * k * k, M))
+        for a in range(k):
+            for c in range(k):
+                r = a * k + c
+                X[:, :, 2 * r] = np.roll(Fv, shift=(-a, -c), axis=(0, 1))
+                X[:, :, 2 * r + 1] = np.roll(Fh, shift=(-a, -c), axis=(0, 1))
+        return X.reshape(N1 * N2, 2 * k * k, M)
+    raise ValueError(f"unknown layout {layout!r}")
 
 
 def structure_tensor_block(u: np.ndarray, k: int, p: int, q: int) -> np.ndarray:
@@ -94,24 +115,43 @@ def structure_tensor_block(u: np.ndarray, k: int, p: int, q: int) -> np.ndarray:
     return X
 
 
-def structure_tensors_adjoint(Y: np.ndarray, k: int, shape) -> tuple[np.ndarray, np.ndarray]:
-    """sum_l P_l^T Y_l split into its vertical and horizontal parts (Zv, Zh)."""
+def structure_tensors_adjoint(Y: np.ndarray, k: int, shape, layout: str = "paper",
+                              periodic_s: bool = True) -> tuple[np.ndarray, np.ndarray]:
+    """sum_l P_l^T Y_l split into its vertical and horizontal parts (Zv, Zh),
+    each (N1, N2, M) with M as in :func:`structure_tensors`."""
     N1, N2, N3 = shape
-    Y = Y.reshape(N1, N2, k * k, 2 * N3)
-    Zv = np.zeros((N1, N2, N3))
-    Zh = np.zeros((N1, N2, N3))
+    M = N3 if periodic_s else N3 - 1
+    Zv = np.zeros((N1, N2, M))
+    Zh = np.zeros((N1, N2, M))
+    if layout == "paper":
+        Y = Y.reshape(N1, N2, k * k, 2 * M)
+        parts = lambda r: (Y[:, :, r, 0::2], Y[:, :, r, 1::2])
+    else:
+        Y = Y.reshape(N1, N2, 2 * k * k, M)
+        parts = lambda r: (Y[:, :, 2 * r], Y[:, :, 2 * r + 1])
     for a in range(k):
         for c in range(k):
-            r = a * k + c
-            Zv += np.roll(Y[:, :, r, 0::2], shift=(a, c), axis=(0, 1))
-            Zh += np.roll(Y[:, :, r, 1::2], shift=(a, c), axis=(0, 1))
+            yv, yh = parts(a * k + c)
+            Zv += np.roll(yv, shift=(a, c), axis=(0, 1))
+            Zh += np.roll(yh, shift=(a, c), axis=(0, 1))
     return Zv, Zh
 
 
-def linear_op_adjoint_u(Y: np.ndarray, k: int, shape) -> np.ndarray:
+def spectral_diff_adjoint(w: np.ndarray, periodic_s: bool = True) -> np.ndarray:
+    """Adjoint of the D_s of :func:`spectral_diffs`: (D_s^T w)[b] = w[b-1] - w[b],
+    with w[-1] = w[N3-1] (periodic) or w[-1] = w[N3-1] = 0 (open; w has N3 - 1
+    bands and the result N3)."""
+    if periodic_s:
+        return diff_adj(w, AXIS_S)
+    pad = np.zeros(w.shape[:-1] + (w.shape[-1] + 2,))
+    pad[..., 1:-1] = w
+    return pad[..., :-1] - pad[..., 1:]
+
+
+def linear_op_adjoint_u(Y: np.ndarray, k: int, shape, layout: str = "paper", periodic_s: bool = True) -> np.ndarray:
     """sum_l D_s^T D^T P_l^T Y_l, the dual-to-primal term of Alg. 1 step 2."""
-    Zv, Zh = structure_tensors_adjoint(Y, k, shape)
-    return diff_adj(diff_adj(Zv, AXIS_V) + diff_adj(Zh, AXIS_H), AXIS_S)
+    Zv, Zh = structure_tensors_adjoint(Y, k, shape, layout, periodic_s)
+    return spectral_diff_adjoint(diff_adj(Zv, AXIS_V) + diff_adj(Zh, AXIS_H), periodic_s)
 
 
 def linear_op_adjoint_u_at(Y: np.ndarray, k: int, shape, i: int, j: int, b: int) -> float:
@@ -298,26 +338,28 @@ def radii(N: int, sigma: float, p_s: float, p_t: float, rho: float = 0.95):
 # ----------------------------------------------------------------------------
 # Alg. 1: the P-PDS solver.
 # ----------------------------------------------------------------------------
-def init_state(v: np.ndarray, k: int) -> dict:
+def init_state(v: np.ndarray, k: int, layout: str = "paper", periodic_s: bool = True) -> dict:
     """Initial values (Alg. 1 leaves them open): u = v, s = t = 0, duals 0."""
     v = np.asarray(v, dtype=np.float64)
-    N1, N2, N3 = v.shape
     z = np.zeros_like(v)
-    return {"u": v.copy(), "s": z.copy(), "t": z.copy(), "y2": z.copy(), "y3": z.copy(),
-            "Y": np.zeros((N1 * N2, k * k, 2 * N3))}
+    Y = np.zeros_like(structure_tensors(v, k, layout, periodic_s))
+    return {"u": v.copy(), "s": z.copy(), "t": z.copy(), "y2": z.copy(), "y3": z.copy(), "Y": Y}
 
 
 def iterate(state: dict, v: np.ndarray, k: int, eps: float, alpha: float, beta: float,
-            mu_min: float, mu_max: float, gammas: dict) -> tuple[dict, float]:
+            mu_min: float, mu_max: float, gammas: dict, layout: str = "paper",
+            periodic_s: bool = True) -> tuple[dict, float]:
     """One pass of Alg. 1 (steps 2-14); returns (new state, relative change).
 
     The relative change is eq. (StopCri_simulated): ||u+ - u||_2 / ||u||_2.
+    ``layout`` and ``periodic_s`` choose the block matrices (see
+    :func:`structure_tensors`); the paper's are the defaults.
     """
     v = np.asarray(v, dtype=np.float64)
     u, s, t, y2, y3, Y = (state[n] for n in ("u", "s", "t", "y2", "y3", "Y"))
     g = gammas
     # Step 2: u update, box projection.
-    u_new = proj_box(u - g["u"] * (linear_op_adjoint_u(Y, k, u.shape) + y3), mu_min, mu_max)
+    u_new = proj_box(u - g["u"] * (linear_op_adjoint_u(Y, k, u.shape, layout, periodic_s) + y3), mu_min, mu_max)
     # Step 3: sparse noise, l1 ball of radius alpha.
     s_new = proj_l1_ball(s - g["s"] * y3, alpha)
     # Step 4: stripe noise, l1 ball of radius beta.
@@ -325,7 +367,7 @@ def iterate(state: dict, v: np.ndarray, k: int, eps: float, alpha: float, beta: 
     # Steps 5-7: extrapolation.
     ub, sb, tb = 2.0 * u_new - u, 2.0 * s_new - s, 2.0 * t_new - t
     # Steps 8-11: every block dual, through the nuclear-norm conjugate prox.
-    Y_new = block_dual_update(Y, structure_tensors(ub, k), g["Y"])
+    Y_new = block_dual_update(Y, structure_tensors(ub, k, layout, periodic_s), g["Y"])
     # Step 12: prox of the conjugate of iota_{0} is the identity (eq. prox_zeroset).
     y2_new = y2 + g["y2"] * diff(tb, AXIS_V)
     # Steps 13-14: fidelity dual through the l2-ball projection.
@@ -339,7 +381,7 @@ def iterate(state: dict, v: np.ndarray, k: int, eps: float, alpha: float, beta: 
 
 def solve(v: np.ndarray, k: int, eps: float, alpha: float, beta: float, mu_min: float = 0.0,
           mu_max: float = 1.0, max_iter: int = 5000, tol: float = 1e-5, policy: str = "paper",
-          state: dict | None = None, trace: list | None = None):
+          state: dict | None = None, trace: list | None = None, layout: str = "paper", periodic_s: bool = True):
     """Run Alg. 1 until the relative change is below ``tol`` or ``max_iter`` passes.
 
     Returns (state, iterations completed, last relative change).
@@ -347,11 +389,11 @@ def solve(v: np.ndarray, k: int, eps: float, alpha: float, beta: float, mu_min: 
     v = np.asarray(v, dtype=np.float64)
     N1, N2, _ = v.shape
     gam = step_sizes(N1, N2, k, policy)
-    st = init_state(v, k) if state is None else state
+    st = init_state(v, k, layout, periodic_s) if state is None else state
     rel = float("inf")
     it = 0
     while it < max_iter:
-        st, rel = iterate(st, v, k, eps, alpha, beta, mu_min, mu_max, gam)
+        st, rel = iterate(st, v, k, eps, alpha, beta, mu_min, mu_max, gam, layout, periodic_s)
         it += 1
         if trace is not None:
             trace.append(rel)
@@ -377,9 +419,9 @@ def mpsnr(u: np.ndarray, ref: np.ndarray, trim: int = 3) -> float:
     return float(np.mean(vals))
 
 
-def objective(u: np.ndarray, k: int) -> float:
-    """S3TTV(u) = sum_l ||T_u^(l)||_*, eq. (S3TTV_Lu)."""
-    X = structure_tensors(np.asarray(u, np.float64), k)
+def objective(u: np.ndarray, k: int, layout: str = "paper", periodic_s: bool = True) -> float:
+    """S3TTV(u) = sum_l ||T_u^(l)||_*, eq. (S3TTV_Lu) (for the chosen block matrices)."""
+    X = structure_tensors(np.asarray(u, np.float64), k, layout, periodic_s)
     return float(np.linalg.svd(X, compute_uv=False).sum())
 
 

@@ -535,3 +535,52 @@ def test_sam_hand_cases():
     ref[0, 3], u[0, 3] = (1, 0), (-1, 0)       # opposite: pi
     ref[0, 4] = (0, 0)                         # both zero: 0
     np.testing.assert_allclose(O.sam_map(u, ref)[0], [np.pi / 2, np.pi / 4, 0.0, np.pi, 0.0], atol=1e-7)
+
+
+# ---------------------------------------------------------------------------
+# The stacked (2k^2) x (N3 or N3 - 1) block matrices and the open D_s
+# ---------------------------------------------------------------------------
+def _stacked_loops(u, k, periodic_s):
+    N1, N2, N3 = u.shape
+    M = N3 if periodic_s else N3 - 1
+    X = np.zeros((N1 * N2, 2 * k * k, M))
+    for p in range(N1):
+        for q in range(N2):
+            for a in range(k):
+                for c in range(k):
+                    i, j = (p + a) % N1, (q + c) % N2
+                    for b in range(M):
+                        b1 = (b + 1) % N3
+                        ds = lambda ii, jj: u[ii, jj, b1] - u[ii, jj, b]
+                        X[p * N2 + q, 2 * (a * k + c), b] = ds((i + 1) % N1, j) - ds(i, j)
+                        X[p * N2 + q, 2 * (a * k + c) + 1, b] = ds(i, (j + 1) % N2) - ds(i, j)
+    return X
+
+
+@pytest.mark.parametrize("periodic_s", [True, False])
+def test_stacked_tensors_match_loops(periodic_s):
+    u = np.random.default_rng(31).standard_normal((4, 5, 6))
+    np.testing.assert_allclose(O.structure_tensors(u, 2, "stacked", periodic_s), _stacked_loops(u, 2, periodic_s),
+                               rtol=0, atol=1e-13)
+
+
+def test_stacked_and_paper_forms_share_entries_not_singular_values():
+    u = np.random.default_rng(32).standard_normal((5, 6, 7))
+    Xp = O.structure_tensors(u, 3)
+    Xs = O.structure_tensors(u, 3, "stacked")
+    # the same second differences, arranged differently
+    np.testing.assert_allclose(np.sort(Xp.ravel()), np.sort(Xs.ravel()), atol=1e-14)
+    assert O.objective(u, 3, "stacked") != pytest.approx(O.objective(u, 3), rel=1e-3)
+    # the open D_s drops exactly the wrap-around band
+    np.testing.assert_allclose(O.structure_tensors(u, 3, "stacked", False), Xs[:, :, :-1], atol=1e-14)
+
+
+@pytest.mark.parametrize("layout,periodic_s", [("stacked", True), ("stacked", False), ("paper", False)])
+def test_stacked_and_open_adjoint_identities(layout, periodic_s):
+    r = np.random.default_rng(33)
+    u = r.standard_normal((4, 5, 6))
+    X = O.structure_tensors(u, 2, layout, periodic_s)
+    Y = r.standard_normal(X.shape)
+    lhs = float((X * Y).sum())
+    rhs = float((u * O.linear_op_adjoint_u(Y, 2, u.shape, layout, periodic_s)).sum())
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
