@@ -267,6 +267,8 @@ def run_ours(args, spec):
     solver = P.Solver(dev, stream=stream)
     solver.set_option(P.OPT_STEP_POLICY, policy)
     solver.set_option(P.OPT_TENSOR_CORES, args.tensor_cores)
+    solver.set_option(P.OPT_LAYOUT, P.LAYOUT_STACKED if args.layout == "stacked" else P.LAYOUT_PAPER)
+    solver.set_option(P.OPT_SPECTRAL_BOUNDARY, P.SPECTRAL_OPEN if args.spectral == "open" else P.SPECTRAL_PERIODIC)
     vd = torch.from_numpy(v).to(f"cuda:{dev}")
     torch.cuda.synchronize()
 
@@ -302,23 +304,27 @@ def run_ours(args, spec):
     bytes_per_voxel = 16 * k2 + 4 + 8  # Y read + write, ubar read, Z written once
     alg_bytes = bytes_per_voxel * N
     peak, peak_src = measured_peaks()
-    if spec.k <= 5:
+    stacked = args.layout == "stacked"
+    if spec.k <= 5 and not stacked:
         achieved = alg_bytes / bd_avg_s / 1e9 if bd_avg_s > 0 else 0.0
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": block_dual_traffic(spec.k, N), "kernel": f"block_dual_kernel<{spec.k}, *>",
                     "peak_source": peak_src,
                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": bd_avg_s * 1000.0}
     else:
-        # k = 6..12: the eigen-solve binds, not HBM.  Algorithmic FP32 work per
-        # block: Gram and apply 2 n^2 (2 N3) each, a symmetric eigen-solve with
-        # vectors ~9 n^3; peak = 152 SMs x 128 FP32 lanes x 2 flops x max SM clock.
-        n = k2
-        flops = (4.0 * n * n * 2 * spec.N3 + 9.0 * n ** 3) * spec.N1 * spec.N2
+        # k = 6..12 and the stacked layout: the eigen-solve binds, not HBM.
+        # Algorithmic FP32 work per block: Gram and apply 2 n^2 (2 k^2 N3 / n
+        # columns) each, a symmetric eigen-solve with vectors ~9 n^3; peak = 152
+        # SMs x 128 FP32 lanes x 2 flops x max SM clock.
+        n = 2 * k2 if stacked else k2
+        cols = spec.N3 if stacked else 2 * spec.N3
+        flops = (4.0 * n * n * cols + 9.0 * n ** 3) * spec.N1 * spec.N2
         sm_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
         alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
         achieved = flops / bd_avg_s / 1e12 if bd_avg_s > 0 else 0.0
         roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                    "frac": achieved / alu_peak, "traffic": None, "kernel": f"block_dual_large_kernel<{spec.k}>",
+                    "frac": achieved / alu_peak, "traffic": None,
+                    "kernel": f"block_dual_large_kernel<{spec.k}, {'true' if stacked else 'false'}>",
                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x max SM clock",
                     "algorithmic_flops_per_launch": flops, "avg_launch_ms": bd_avg_s * 1000.0,
                     "hbm_frac": alg_bytes / bd_avg_s / 1e9 / peak if bd_avg_s > 0 else 0.0}
@@ -360,7 +366,8 @@ def run_ours(args, spec):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "N1": spec.N1, "N2": spec.N2, "N3": spec.N3, "k": spec.k,
-                       "policy": args.policy, "parallelism": f"replicas{world}",
+                       "policy": args.policy, "layout": args.layout, "spectral": args.spectral,
+                       "parallelism": f"replicas{world}",
                        "block_dual_products": ("tensor cores, each FP32 operand split into two TF32 parts"
                                                if args.tensor_cores else "CUDA cores, FP32 FMA"),
                        "l2": "inputs larger than L2 (block duals Y: %.2f GB, read and written every pass)"
@@ -671,6 +678,10 @@ def main(argv=None):
     ap.add_argument("--policy", choices=("paper", "pc_exact"), default="paper")
     ap.add_argument("--tensor-cores", type=int, choices=(0, 1), default=1,
                     help="block-dual Gram and apply on tensor cores (1) or CUDA cores (0)")
+    ap.add_argument("--layout", choices=("paper", "stacked"), default="paper",
+                    help="block matrices: the paper's k^2 x 2N3 or the stacked 2k^2 x N3")
+    ap.add_argument("--spectral", choices=("periodic", "open"), default="periodic",
+                    help="spectral difference: periodic (the paper) or open (no wrap-around)")
     ap.add_argument("--no-tol-run", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

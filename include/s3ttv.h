@@ -89,12 +89,35 @@ enum {
                                       eigenbasis it converged to in the previous pass
                                       (same result, fewer sweeps; 4 (k^2+1) k^2 bytes of
                                       workspace per block); 0: every pass starts cold     */
-  S3TTV_OPT_TENSOR_CORES = 7       /* block duals (Alg. 1 steps 8-11): 1 (default) forms
+  S3TTV_OPT_TENSOR_CORES = 7,      /* block duals (Alg. 1 steps 8-11): 1 (default) forms
                                       the Gram Y'Y'^T and the product M Y' on tensor cores,
                                       each FP32 operand split into two TF32 parts and three
                                       of the four part products kept (FP32-level accuracy);
                                       0: the same products with FP32 FMAs on CUDA cores   */
+  S3TTV_OPT_LAYOUT = 8,            /* block matrices X_l: S3TTV_LAYOUT_PAPER (default) or
+                                      S3TTV_LAYOUT_STACKED (below)                        */
+  S3TTV_OPT_SPECTRAL_BOUNDARY = 9  /* D_s: S3TTV_SPECTRAL_PERIODIC (default, Sec. II-A)
+                                      or S3TTV_SPECTRAL_OPEN (below)                      */
 };
+/* Block-matrix layouts (option S3TTV_OPT_LAYOUT).  PAPER is eq. (SSST): X_l is
+ * k^2 x 2N3, row r the window pixel r = a k + c, columns [v_1 h_1 ... v_N3 h_N3].
+ * STACKED is the (2k^2) x N3 matrix of the vertical and horizontal differences
+ * stacked as rows (row 2r: D_v D_s u at pixel r, row 2r + 1: D_h D_s u; one
+ * column per band).  The two hold the same entries but are different matrices
+ * (different nuclear norms); the paper's Prob. (S3TTV_denoising) uses PAPER.
+ * STACKED supports k <= 8 and runs every block on the per-CTA path (FP32).
+ * The external block-dual layout ("Y" in s3ttv_get_state / s3ttv_set_state /
+ * s3ttv_block_dual) follows: [N1*N2][k*k][2*N3] (PAPER) or [N1*N2][2*k*k][N3]
+ * (STACKED).  Spectral boundary (option S3TTV_OPT_SPECTRAL_BOUNDARY): PERIODIC
+ * wraps D_s from the last band to the first (the paper, Sec. II-A); OPEN stops
+ * at the last band, so X_l has N3 - 1 band columns (the library keeps the
+ * band-N3 column and its dual at zero).  With STACKED and OPEN, X_l is the
+ * (2k^2) x (N3 - 1) matrix.  Changing either option drops the problem set up
+ * (S3TTV_ESTATE until the next s3ttv_setup or s3ttv_solve); the step sizes are
+ * those of the PAPER / PERIODIC operator (its column and row sums bound the
+ * others'), so Theorem 1's condition still holds. */
+enum { S3TTV_LAYOUT_PAPER = 0, S3TTV_LAYOUT_STACKED = 1 };
+enum { S3TTV_SPECTRAL_PERIODIC = 0, S3TTV_SPECTRAL_OPEN = 1 };
 
 /* Kernel classes reported by s3ttv_kernel_stats. */
 enum {

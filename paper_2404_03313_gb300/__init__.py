@@ -10,6 +10,7 @@ from ._binding import (  # noqa: F401
     Info, S3TTVError, Solver, WarmStartNet, library, radii, step_sizes, l1_ball_static, LIB_PATH, SIGNATURES, STATE,
     L1_STATIC_MAX_N, ETOOBIG,
     STEP_PAPER, STEP_PC_EXACT, OPT_STEP_POLICY, OPT_CHECK_EVERY, OPT_JACOBI_MAX_SWEEPS, OPT_JACOBI_TOL,
-    OPT_PROFILE, OPT_WARM_START, OPT_TENSOR_CORES, KERNEL_CLASSES,
+    OPT_PROFILE, OPT_WARM_START, OPT_TENSOR_CORES, OPT_LAYOUT, OPT_SPECTRAL_BOUNDARY, LAYOUT_PAPER,
+    LAYOUT_STACKED, SPECTRAL_PERIODIC, SPECTRAL_OPEN, KERNEL_CLASSES,
     OK, MAXITER, EINVAL, ENOMEM, ECUDA, ENUMERIC, EUNSUPPORTED, ESTATE,
 )

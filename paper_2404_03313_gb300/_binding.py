@@ -20,6 +20,9 @@ L1_STATIC_MAX_N = 4294967295
 STEP_PAPER, STEP_PC_EXACT = 0, 1
 OPT_STEP_POLICY, OPT_CHECK_EVERY, OPT_JACOBI_MAX_SWEEPS, OPT_JACOBI_TOL, OPT_PROFILE, OPT_WARM_START = 1, 2, 3, 4, 5, 6
 OPT_TENSOR_CORES = 7
+OPT_LAYOUT, OPT_SPECTRAL_BOUNDARY = 8, 9
+LAYOUT_PAPER, LAYOUT_STACKED = 0, 1
+SPECTRAL_PERIODIC, SPECTRAL_OPEN = 0, 1
 KERNEL_CLASSES = ("primal", "l1_search", "block_dual", "dual", "finalize")
 STATE = {"u": 0, "s": 1, "t": 2, "y2": 3, "y3": 4, "Y": 5}
 
@@ -223,6 +226,8 @@ class Solver:
 
     def set_option(self, key, value):
         self._check(self._lib.s3ttv_set_option(self._h, key, float(value)), "set_option")
+        if key == OPT_LAYOUT:
+            self.layout = int(value)
 
     def workspace_bytes(self):
         return int(self._lib.s3ttv_workspace_bytes(self._h))
@@ -318,6 +323,8 @@ class Solver:
     def _state_size(self, which):
         N1, N2, N3 = self.shape
         if which == "Y":
+            if getattr(self, "layout", LAYOUT_PAPER) == LAYOUT_STACKED:
+                return (N1 * N2, 2 * self.k * self.k, N3)
             return (N1 * N2, self.k * self.k, 2 * N3)
         return (N1, N2, N3)
 

@@ -25,6 +25,8 @@ struct s3ttv_ctx {
   int jacobi_max_sweeps = 24;
   float jacobi_tol = 2e-6f;
   int tensor_cores = 1;
+  int layout = S3TTV_LAYOUT_PAPER;  // block matrices: paper k^2 x 2N3 or stacked 2k^2 x N3
+  int open_s = 0;                   // 1: D_s stops at the last band (no wrap-around)
   // problem
   bool ready = false;
   Dims dm{};
@@ -195,11 +197,12 @@ int ensure_macc(s3ttv_ctx *ctx, size_t n) {
 int ensure_problem_buffers(s3ttv_ctx *ctx, const Dims &dm, int k) {
   const size_t np = (size_t)dm.Np;
   const size_t ny = (size_t)dm.P * k * k * 2 * dm.N3p;
-  const size_t nw = (size_t)dm.P * block_dual_w_stride(k);
-  ctx->w_stride = block_dual_w_stride(k);
+  const long long ws = ctx->layout == S3TTV_LAYOUT_STACKED ? block_dual_large_w_stride(k, true) : block_dual_w_stride(k);
+  const size_t nw = (size_t)dm.P * ws;
+  ctx->w_stride = ws;
   if (np <= ctx->cap_np && ny <= ctx->cap_y && nw <= ctx->cap_w && ctx->sc) return S3TTV_OK;
   free_all(ctx);
-  ctx->w_stride = block_dual_w_stride(k);
+  ctx->w_stride = ws;
   int rc = ensure_common(ctx);
   if (rc) return rc;
   float **cubes[] = {&ctx->v, &ctx->u, &ctx->s, &ctx->t[0], &ctx->t[1], &ctx->y2, &ctx->d, &ctx->ubar,
@@ -251,18 +254,21 @@ int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, BdShape *sh) {
     return fail(ctx, S3TTV_EUNSUPPORTED, "%lld voxels: this build supports fewer than 2^33", dm.Np);
   sh->v.k = k;
   sh->v.tc = ctx->tensor_cores;
-  if (k >= kMinLargeK) {  // one CTA per block at a time; FP32 CUDA cores whatever the option
+  const bool stacked = ctx->layout == S3TTV_LAYOUT_STACKED;
+  if (stacked && k > kMaxStackedK)
+    return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: the stacked layout supports k <= %d", k, kMaxStackedK);
+  if (stacked || k >= kMinLargeK) {  // one CTA per block at a time; FP32 CUDA cores whatever the option
     sh->large = true;
-    sh->smem = block_dual_large_smem_bytes(k);
+    sh->smem = block_dual_large_smem_bytes(k, stacked);
     int dev_max = 0;
     cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
     if (sh->smem > (size_t)dev_max)
       return fail(ctx, S3TTV_EUNSUPPORTED, "a %dx%d block needs %zu bytes of shared memory (device limit %d)", k, k,
                   sh->smem, dev_max);
-    cudaError_t e = block_dual_large_prepare(k, sh->smem);
+    cudaError_t e = block_dual_large_prepare(k, stacked, sh->smem);
     if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
     int per_sm = 0;
-    e = block_dual_large_occupancy(k, sh->smem, &per_sm);
+    e = block_dual_large_occupancy(k, stacked, sh->smem, &per_sm);
     if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
     if (per_sm < 1) per_sm = 1;
     long long g = (long long)ctx->num_sms * per_sm;
@@ -360,7 +366,7 @@ int load_Y(s3ttv_ctx *ctx, const float *src) {
     CU(cudaMemcpyAsync(ctx->stage, src, sizeof(float) * ne, cudaMemcpyHostToDevice, ctx->stream));
     from = ctx->stage;
   }
-  CU(launch_Y_to_internal(from, ctx->Y, dm, ctx->k, ctx->stream));
+  CU(launch_Y_to_internal(from, ctx->Y, dm, ctx->k, ctx->stream, ctx->layout == S3TTV_LAYOUT_STACKED));
   return S3TTV_OK;
 }
 
@@ -368,12 +374,12 @@ int store_Y(s3ttv_ctx *ctx, float *dst) {
   const Dims &dm = ctx->dm;
   const size_t ne = (size_t)dm.P * ctx->k * ctx->k * 2 * dm.N3;
   if (is_device_ptr(dst)) {
-    CU(launch_Y_to_external(ctx->Y, dst, dm, ctx->k, ctx->stream));
+    CU(launch_Y_to_external(ctx->Y, dst, dm, ctx->k, ctx->stream, ctx->layout == S3TTV_LAYOUT_STACKED));
     return S3TTV_OK;
   }
   int rc = ensure_stage(ctx, ne);
   if (rc) return rc;
-  CU(launch_Y_to_external(ctx->Y, ctx->stage, dm, ctx->k, ctx->stream));
+  CU(launch_Y_to_external(ctx->Y, ctx->stage, dm, ctx->k, ctx->stream, ctx->layout == S3TTV_LAYOUT_STACKED));
   CU(cudaMemcpyAsync(dst, ctx->stage, sizeof(float) * ne, cudaMemcpyDeviceToHost, ctx->stream));
   return S3TTV_OK;
 }
@@ -437,7 +443,7 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   CU(launch_l1_scan(la, 3, st));
   if (ev) CU(cudaEventRecord(ev[2], st));
 
-  CU(launch_xfield(ctx->ubar, ctx->Fv, ctx->Fh, dm, grid_e, st));
+  CU(launch_xfield(ctx->ubar, ctx->Fv, ctx->Fh, dm, grid_e, st, ctx->open_s));
   BlockDualArgs ba;
   ba.Y = ctx->Y;
   ba.Fv = ctx->Fv;
@@ -453,7 +459,7 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   ba.W = ctx->warm_start ? ctx->W : nullptr;
   ba.w_stride = ctx->w_stride;
   ba.warm = ctx->warm_start && ctx->warm_valid;
-  if (bd.large) CU(launch_block_dual_large(ba, ctx->k, bd.grid, bd.smem, st));
+  if (bd.large) CU(launch_block_dual_large(ba, ctx->k, ctx->layout == S3TTV_LAYOUT_STACKED, bd.grid, bd.smem, st));
   else CU(launch_block_dual(ba, bd.v, bd.grid, bd.smem, st));
   if (ctx->warm_start) ctx->warm_valid = true;
   if (ev) CU(cudaEventRecord(ev[3], st));
@@ -647,6 +653,24 @@ int s3ttv_set_option(s3ttv_ctx *ctx, int key, double value) {
       if (value != 0 && value != 1) return fail(ctx, S3TTV_EINVAL, "warm_start must be 0 or 1");
       ctx->warm_start = value == 1;
       ctx->warm_valid = false;
+      return S3TTV_OK;
+    case S3TTV_OPT_LAYOUT:
+      if (value != S3TTV_LAYOUT_PAPER && value != S3TTV_LAYOUT_STACKED)
+        return fail(ctx, S3TTV_EINVAL, "layout must be S3TTV_LAYOUT_PAPER or S3TTV_LAYOUT_STACKED");
+      if ((int)value != ctx->layout) {
+        ctx->layout = (int)value;
+        ctx->ready = false;  // the block duals change meaning: set the problem up again
+        ctx->warm_valid = false;
+      }
+      return S3TTV_OK;
+    case S3TTV_OPT_SPECTRAL_BOUNDARY:
+      if (value != S3TTV_SPECTRAL_PERIODIC && value != S3TTV_SPECTRAL_OPEN)
+        return fail(ctx, S3TTV_EINVAL, "spectral boundary must be S3TTV_SPECTRAL_PERIODIC or S3TTV_SPECTRAL_OPEN");
+      if ((int)value != ctx->open_s) {
+        ctx->open_s = (int)value;
+        ctx->ready = false;
+        ctx->warm_valid = false;
+      }
       return S3TTV_OK;
     case S3TTV_OPT_PROFILE:
       if (value != 0 && value != 1) return fail(ctx, S3TTV_EINVAL, "profile must be 0 or 1");
@@ -930,6 +954,8 @@ int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, in
     m->jacobi_tol = ctx->jacobi_tol;
     m->tensor_cores = ctx->tensor_cores;
     m->warm_start = ctx->warm_start;
+    m->layout = ctx->layout;
+    m->open_s = ctx->open_s;
     m->profile = false;
     const s3ttv_problem &p = problems[i];
     int rc = s3ttv_setup(m, p.v, p.N1, p.N2, p.N3, p.eps, p.alpha, p.beta, p.mu_min, p.mu_max, p.k);
@@ -1113,7 +1139,7 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   CU(cudaMemsetAsync(ctx->Zv[0], 0, sizeof(float) * dm.Np, ctx->stream));
   CU(cudaMemsetAsync(ctx->Zh[0], 0, sizeof(float) * dm.Np, ctx->stream));
   CU(launch_init_scalars(ctx->sc, 0.0, 0.0, ctx->stream));
-  CU(launch_xfield(ctx->ubar, ctx->Fv, ctx->Fh, dm, elementwise_grid(ctx, dm.Np), ctx->stream));
+  CU(launch_xfield(ctx->ubar, ctx->Fv, ctx->Fh, dm, elementwise_grid(ctx, dm.Np), ctx->stream, ctx->open_s));
   BlockDualArgs ba;
   ba.Y = ctx->Y;
   ba.Fv = ctx->Fv;
@@ -1129,7 +1155,7 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   ba.W = nullptr;
   ba.w_stride = 0;
   ba.warm = 0;
-  if (bd.large) CU(launch_block_dual_large(ba, k, bd.grid, bd.smem, ctx->stream));
+  if (bd.large) CU(launch_block_dual_large(ba, k, ctx->layout == S3TTV_LAYOUT_STACKED, bd.grid, bd.smem, ctx->stream));
   else CU(launch_block_dual(ba, bd.v, bd.grid, bd.smem, ctx->stream));
   if ((rc = store_Y(ctx, Y))) return rc;
   if ((rc = store_cube(ctx, ctx->Zv[0], Zv, nullptr))) return rc;
@@ -1148,7 +1174,9 @@ int s3ttv_objective(s3ttv_ctx *ctx, const float *u, int N1, int N2, int N3, int 
   if (!ctx) return S3TTV_EINVAL;
   if (!u || !value) return fail(ctx, S3TTV_EINVAL, "u and value are required");
   if (k < 1 || N1 < k || N2 < k || N3 < 1) return fail(ctx, S3TTV_EINVAL, "need N1, N2 >= k >= 1 and N3 >= 1");
-  if (k > kMaxK) return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: this build supports k <= %d", k, kMaxK);
+  const int stacked = ctx->layout == S3TTV_LAYOUT_STACKED;
+  if (k > (stacked ? kMaxStackedK : kMaxK))
+    return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: this build supports k <= %d", k, stacked ? kMaxStackedK : kMaxK);
   DeviceGuard g(ctx->device);
   int rc;
   const long long N = (long long)N1 * N2 * N3;
@@ -1163,9 +1191,9 @@ int s3ttv_objective(s3ttv_ctx *ctx, const float *u, int N1, int N2, int N3, int 
   unsigned *nonconv = reinterpret_cast<unsigned *>(ctx->macc + 1);
   int dev_max = 0;
   CU(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
-  if (objective_smem_bytes(k) + 2048 > (size_t)dev_max)
-    return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d needs %zu bytes of shared memory", k, objective_smem_bytes(k));
-  CU(launch_objective(du, N1, N2, N3, k, ctx->macc, nonconv, ctx->num_sms * 4, ctx->stream));
+  if (objective_smem_bytes(k, stacked) + 2048 > (size_t)dev_max)
+    return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d needs %zu bytes of shared memory", k, objective_smem_bytes(k, stacked));
+  CU(launch_objective(du, N1, N2, N3, k, stacked, ctx->open_s, ctx->macc, nonconv, ctx->num_sms * 4, ctx->stream));
   double h[2] = {0.0, 0.0};
   CU(cudaMemcpyAsync(h, ctx->macc, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));

@@ -72,9 +72,10 @@ struct Layout {
   size_t x1, x2, chunk, nrm, pix, total;  // float offsets; total floats
 };
 
-__host__ __device__ inline Layout layout(int k) {
+// n: rows of a block matrix (k^2 in the paper's layout, 2 k^2 stacked)
+__host__ __device__ inline Layout layout(int n) {
   Layout L;
-  L.n = k * k;
+  L.n = n;
   L.npos = (L.n + 1) & ~1;
   L.nt4 = (L.npos + 3) / 4;
   const int w = 4 * L.nt4;  // rows and columns rounded to whole tiles
@@ -111,10 +112,11 @@ __device__ __forceinline__ void upper_tile(int t, int nt4, int &ti, int &tj) {
 // The chunk [c0, c0 + kCW) of Y'_l into shared memory, all 4 nt4 rows (rows
 // >= n and columns >= 2 N3p read as 0).  form: add gamma_Y F and write Y'
 // back over Y_l.
+template <bool ST>
 __device__ void stream_chunk(const Layout &L, float *chunk, float *Yl, const BlockDualArgs &a, const int *pix,
                              int c0, bool form) {
   const Dims &dm = a.dm;
-  const int N3p = dm.N3p, W = 2 * N3p;
+  const int N3p = dm.N3p, W = ST ? N3p : 2 * N3p;
   constexpr int Q = kCW / 4;
   for (int it = threadIdx.x; it < 4 * L.nt4 * Q; it += kLT) {
     const int r = it / Q, q = it - r * Q, c = c0 + 4 * q;
@@ -123,9 +125,11 @@ __device__ void stream_chunk(const Layout &L, float *chunk, float *Yl, const Blo
       float *g = Yl + (size_t)r * W + c;
       y = *reinterpret_cast<const float4 *>(g);
       if (form) {
-        const bool hz = c >= N3p;
+        // paper layout: a row is one pixel, columns [v bands | h bands];
+        // stacked: rows 2r and 2r + 1 are the v and h bands of pixel r
+        const bool hz = ST ? (r & 1) != 0 : c >= N3p;
         const float4 f = __ldg(reinterpret_cast<const float4 *>((hz ? a.Fh : a.Fv) + (size_t)pix[r] * N3p +
-                                                                (hz ? c - N3p : c)));
+                                                                (hz && !ST ? c - N3p : c)));
         y.x = fmaf(a.gY, f.x, y.x);
         y.y = fmaf(a.gY, f.y, y.y);
         y.z = fmaf(a.gY, f.z, y.z);
@@ -137,21 +141,22 @@ __device__ void stream_chunk(const Layout &L, float *chunk, float *Yl, const Blo
   }
 }
 
-template <int K>
+template <int K, bool ST>
 __global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs a) {
   constexpr int k = K;
-  constexpr int PE2 = (K * K + 2 * kPG - 1) / (2 * kPG);  // float2 pieces of a row a Jacobi lane holds
+  constexpr int NR = ST ? 2 * K * K : K * K;            // rows of a block matrix
+  constexpr int PE2 = (NR + 2 * kPG - 1) / (2 * kPG);  // float2 pieces of a row a Jacobi lane holds
   extern __shared__ __align__(16) float sm[];
   __shared__ float s_red[kLW];
   __shared__ unsigned s_sweeps;
   if (a.sc->done) return;
-  const Layout L = layout(k);
+  const Layout L = layout(NR);
   const int n = L.n, NP = L.npos, GS = L.gs, nt4 = L.nt4;
   float *X1 = sm + L.x1, *X2 = sm + L.x2, *chunk = sm + L.chunk, *nrm = sm + L.nrm;
   int *pix = reinterpret_cast<int *>(sm + L.pix);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const Dims dm = a.dm;
-  const int N3p = dm.N3p, W = 2 * N3p;
+  const int N3p = dm.N3p, W = ST ? N3p : 2 * N3p;
   const long long Lb = dm.P;
   if (tid == 0) s_sweeps = 0u;
   const int n_upper = nt4 * (nt4 + 1) / 2;
@@ -160,7 +165,8 @@ __global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs 
     float *Yl = a.Y + (size_t)l * n * W;
     if (tid < n) {
       const int p = (int)(l / dm.N2), q = (int)(l - (long long)p * dm.N2);
-      const int ra = tid / k, rc = tid - ra * k;
+      const int pr = ST ? tid >> 1 : tid;  // window pixel of row tid
+      const int ra = pr / k, rc = pr - ra * k;
       int i = p + ra;
       if (i >= dm.N1) i -= dm.N1;
       int j = q + rc;
@@ -176,7 +182,7 @@ __global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs 
 #pragma unroll
       for (int e = 0; e < 16; ++e) acc[u][e] = 0.f;
     for (int c0 = 0; c0 < W; c0 += kCW) {
-      stream_chunk(L, chunk, Yl, a, pix, c0, true);
+      stream_chunk<ST>(L, chunk, Yl, a, pix, c0, true);
       __syncthreads();
 #pragma unroll
       for (int u = 0; u < kGramTiles; ++u) {
@@ -426,7 +432,7 @@ __global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs 
 
     // ---- 5b. Y_l = M Y' by chunks; Z += P_l^T Y_l ----
     for (int c0 = 0; c0 < W; c0 += kCW) {
-      stream_chunk(L, chunk, Yl, a, pix, c0, false);
+      stream_chunk<ST>(L, chunk, Yl, a, pix, c0, false);
       __syncthreads();
       constexpr int Q = kCW / 4;
       for (int t = tid; t < nt4 * Q; t += kLT) {
@@ -448,12 +454,12 @@ __global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs 
         }
         const int c = c0 + 4 * q;
         if (c < W) {
-          const bool hz = c >= N3p;
-          float *Zb = (hz ? a.Zh : a.Zv) + (hz ? c - N3p : c);
 #pragma unroll
           for (int p = 0; p < 4; ++p) {
             const int r = 4 * ti + p;
             if (r < n) {
+              const bool hz = ST ? (r & 1) != 0 : c >= N3p;
+              float *Zb = (hz ? a.Zh : a.Zv) + (hz && !ST ? c - N3p : c);
               __stcs(reinterpret_cast<float4 *>(Yl + (size_t)r * W + c), y[p]);
               atomicAdd(reinterpret_cast<float4 *>(Zb + (size_t)pix[r] * N3p), y[p]);
             }
@@ -468,30 +474,37 @@ __global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs 
 
 }  // namespace
 
-size_t block_dual_large_smem_bytes(int k) { return sizeof(float) * layout(k).total; }
-
-long long block_dual_large_w_stride(int k) {
-  const Layout L = layout(k);
-  return ((long long)L.npos * L.n + 3) & ~3ll;
+size_t block_dual_large_smem_bytes(int k, bool stacked) {
+  return sizeof(float) * layout(stacked ? 2 * k * k : k * k).total;
 }
+
+long long block_dual_large_w_stride(int k, bool stacked) {
+  const Layout L = layout(stacked ? 2 * k * k : k * k);
+  return ((long long)L.npos * L.n + 3) / 4 * 4;
+}
+
+long long block_dual_large_w_stride(int k) { return block_dual_large_w_stride(k, false); }
 
 int block_dual_large_threads() { return kLT; }
 
-// The launch limit is raised to the device's opt-in maximum (less the static
-// shared memory): every context launching the kernel shares the attribute.
 namespace {
 typedef void (*LargeKernel)(BlockDualArgs);
-LargeKernel large_kernel(int k) {
-  static const LargeKernel table[] = {block_dual_large_kernel<6>,  block_dual_large_kernel<7>,
-                                      block_dual_large_kernel<8>,  block_dual_large_kernel<9>,
-                                      block_dual_large_kernel<10>, block_dual_large_kernel<11>,
-                                      block_dual_large_kernel<12>};
-  return k >= kMinLargeK && k <= kMaxLargeK ? table[k - kMinLargeK] : nullptr;
+LargeKernel large_kernel(int k, bool stacked) {
+  static const LargeKernel paper[] = {block_dual_large_kernel<6, false>,  block_dual_large_kernel<7, false>,
+                                      block_dual_large_kernel<8, false>,  block_dual_large_kernel<9, false>,
+                                      block_dual_large_kernel<10, false>, block_dual_large_kernel<11, false>,
+                                      block_dual_large_kernel<12, false>};
+  static const LargeKernel stack[] = {block_dual_large_kernel<1, true>, block_dual_large_kernel<2, true>,
+                                      block_dual_large_kernel<3, true>, block_dual_large_kernel<4, true>,
+                                      block_dual_large_kernel<5, true>, block_dual_large_kernel<6, true>,
+                                      block_dual_large_kernel<7, true>, block_dual_large_kernel<8, true>};
+  if (stacked) return k >= 1 && k <= kMaxStackedK ? stack[k - 1] : nullptr;
+  return k >= kMinLargeK && k <= kMaxLargeK ? paper[k - kMinLargeK] : nullptr;
 }
 }  // namespace
 
-cudaError_t block_dual_large_prepare(int k, size_t smem) {
-  const LargeKernel f = large_kernel(k);
+cudaError_t block_dual_large_prepare(int k, bool stacked, size_t smem) {
+  const LargeKernel f = large_kernel(k, stacked);
   if (!f) return cudaErrorInvalidValue;
   int dev = 0, cap = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -504,14 +517,15 @@ cudaError_t block_dual_large_prepare(int k, size_t smem) {
   return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
 }
 
-cudaError_t block_dual_large_occupancy(int k, size_t smem, int *ctas) {
-  const LargeKernel f = large_kernel(k);
+cudaError_t block_dual_large_occupancy(int k, bool stacked, size_t smem, int *ctas) {
+  const LargeKernel f = large_kernel(k, stacked);
   if (!f) return cudaErrorInvalidValue;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, f, kLT, smem);
 }
 
-cudaError_t launch_block_dual_large(const BlockDualArgs &a, int k, int grid, size_t smem, cudaStream_t st) {
-  const LargeKernel f = large_kernel(k);
+cudaError_t launch_block_dual_large(const BlockDualArgs &a, int k, bool stacked, int grid, size_t smem,
+                                    cudaStream_t st) {
+  const LargeKernel f = large_kernel(k, stacked);
   if (!f) return cudaErrorInvalidValue;
   f<<<grid, kLT, smem, st>>>(a);
   return cudaGetLastError();

@@ -238,7 +238,11 @@ __global__ void unpad_cube_kernel(const float *__restrict__ src, float *__restri
 }
 
 // External Y [L][n][2*N3] (column 2b + o) <-> internal [L][n][2][N3p].
-__global__ void Y_to_internal_kernel(const float *__restrict__ ext, float *__restrict__ in, Dims dm, int n) {
+// External block duals: paper layout [L][k^2][2 N3] with interleaved columns
+// (v_b, h_b); stacked layout [L][2 k^2][N3] (row 2r + o, band b).  Internal:
+// [L][k^2][2][N3p] for both.
+__global__ void Y_to_internal_kernel(const float *__restrict__ ext, float *__restrict__ in, Dims dm, int n,
+                                     int stacked) {
   const long long total = dm.P * n * 2 * dm.N3p;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
@@ -246,17 +250,18 @@ __global__ void Y_to_internal_kernel(const float *__restrict__ ext, float *__res
     const int rem = (int)(idx - row * 2 * dm.N3p);
     const int o = rem >= dm.N3p;
     const int b = rem - o * dm.N3p;
-    in[idx] = b < dm.N3 ? ext[row * 2 * dm.N3 + 2 * b + o] : 0.f;
+    in[idx] = b < dm.N3 ? ext[stacked ? (2 * row + o) * dm.N3 + b : row * 2 * dm.N3 + 2 * b + o] : 0.f;
   }
 }
 
-__global__ void Y_to_external_kernel(const float *__restrict__ in, float *__restrict__ ext, Dims dm, int n) {
+__global__ void Y_to_external_kernel(const float *__restrict__ in, float *__restrict__ ext, Dims dm, int n,
+                                     int stacked) {
   const long long total = dm.P * n * 2 * dm.N3;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
     const long long row = idx / (2 * dm.N3);
     const int col = (int)(idx - row * 2 * dm.N3);
-    const int b = col >> 1, o = col & 1;
+    const int b = stacked ? col % dm.N3 : col >> 1, o = stacked ? col / dm.N3 : col & 1;
     ext[idx] = in[row * 2 * dm.N3p + (long long)o * dm.N3p + b];
   }
 }
@@ -289,7 +294,7 @@ __global__ void Z_from_Y_kernel(const float *__restrict__ Y, float *__restrict__
 // Fv = D_v D_s ubar and Fh = D_h D_s ubar: the second-order differences the
 // structure tensors of eq. (SSST) are cut from, formed once per pass.
 __global__ void xfield_kernel(const float *__restrict__ ubar, float *__restrict__ Fv, float *__restrict__ Fh,
-                              Dims dm) {
+                              Dims dm, int open_s) {
   const int N3p = dm.N3p, C4 = N3p >> 2, N2 = dm.N2;
   const int nch = (int)(dm.P * C4);
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += gridDim.x * blockDim.x) {
@@ -305,7 +310,7 @@ __global__ void xfield_kernel(const float *__restrict__ ubar, float *__restrict_
     float fv[4], fh[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      if (b0 + e < dm.N3) {
+      if (b0 + e < dm.N3 - open_s) {  // open D_s: no difference past the last band
         const bool in = e < 3 && b0 + e + 1 < dm.N3;
         const float ds0 = (in ? comp(x0, e + 1) : n0) - comp(x0, e);
         fv[e] = ((in ? comp(xv, e + 1) : nv) - comp(xv, e)) - ds0;
@@ -360,18 +365,18 @@ cudaError_t launch_unpad_cube(const float *src, float *dst, Dims dm, const doubl
   return cudaGetLastError();
 }
 
-cudaError_t launch_Y_to_internal(const float *ext, float *in, Dims dm, int k, cudaStream_t st) {
-  Y_to_internal_kernel<<<grid_for(dm.P * k * k * 2 * dm.N3p), 256, 0, st>>>(ext, in, dm, k * k);
+cudaError_t launch_Y_to_internal(const float *ext, float *in, Dims dm, int k, cudaStream_t st, int stacked) {
+  Y_to_internal_kernel<<<grid_for(dm.P * k * k * 2 * dm.N3p), 256, 0, st>>>(ext, in, dm, k * k, stacked);
   return cudaGetLastError();
 }
 
-cudaError_t launch_Y_to_external(const float *in, float *ext, Dims dm, int k, cudaStream_t st) {
-  Y_to_external_kernel<<<grid_for(dm.P * k * k * 2 * dm.N3), 256, 0, st>>>(in, ext, dm, k * k);
+cudaError_t launch_Y_to_external(const float *in, float *ext, Dims dm, int k, cudaStream_t st, int stacked) {
+  Y_to_external_kernel<<<grid_for(dm.P * k * k * 2 * dm.N3), 256, 0, st>>>(in, ext, dm, k * k, stacked);
   return cudaGetLastError();
 }
 
-cudaError_t launch_xfield(const float *ubar, float *Fv, float *Fh, Dims dm, int grid, cudaStream_t st) {
-  xfield_kernel<<<grid, 256, 0, st>>>(ubar, Fv, Fh, dm);
+cudaError_t launch_xfield(const float *ubar, float *Fv, float *Fh, Dims dm, int grid, cudaStream_t st, int open_s) {
+  xfield_kernel<<<grid, 256, 0, st>>>(ubar, Fv, Fh, dm, open_s);
   return cudaGetLastError();
 }
 

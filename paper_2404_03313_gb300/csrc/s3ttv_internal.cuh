@@ -150,23 +150,30 @@ cudaError_t launch_block_dual(const BlockDualArgs &a, const BdVariant &v, int gr
 bool block_dual_has(const BdVariant &v);  // compiled in this build
 // Larger blocks, k = kMinLargeK..kMaxLargeK (block_dual_large.cu): one CTA of
 // block_dual_large_threads() threads per block at a time, FP32 CUDA cores.
-constexpr int kMinLargeK = 6, kMaxLargeK = 12;
-size_t block_dual_large_smem_bytes(int k);
-long long block_dual_large_w_stride(int k);
+// The same kernel also runs the stacked layout (2 k^2 rows of N3 bands, rows 2r
+// and 2r + 1 the vertical and horizontal differences of window pixel r) for
+// k = 1..kMaxStackedK; the block memory [L][k^2][2][N3p] is the same.
+constexpr int kMinLargeK = 6, kMaxLargeK = 12, kMaxStackedK = 8;
+size_t block_dual_large_smem_bytes(int k, bool stacked);
+long long block_dual_large_w_stride(int k, bool stacked);
+long long block_dual_large_w_stride(int k);  // paper layout
 int block_dual_large_threads();
-cudaError_t block_dual_large_prepare(int k, size_t smem_bytes);
-cudaError_t block_dual_large_occupancy(int k, size_t smem_bytes, int *ctas_per_sm);
-cudaError_t launch_block_dual_large(const BlockDualArgs &a, int k, int grid, size_t smem, cudaStream_t st);
+cudaError_t block_dual_large_prepare(int k, bool stacked, size_t smem_bytes);
+cudaError_t block_dual_large_occupancy(int k, bool stacked, size_t smem_bytes, int *ctas_per_sm);
+cudaError_t launch_block_dual_large(const BlockDualArgs &a, int k, bool stacked, int grid, size_t smem,
+                                    cudaStream_t st);
 cudaError_t block_dual_prepare(const BdVariant &v, size_t smem_bytes);
 cudaError_t block_dual_occupancy(const BdVariant &v, size_t smem_bytes, int *ctas_per_sm);
 
 // Layout conversion and small helpers.
 cudaError_t launch_pad_cube(const float *src, float *dst, Dims dm, float scale, cudaStream_t st);
 cudaError_t launch_unpad_cube(const float *src, float *dst, Dims dm, const double *scale_dev, cudaStream_t st);
-cudaError_t launch_Y_to_internal(const float *ext, float *in, Dims dm, int k, cudaStream_t st);
-cudaError_t launch_Y_to_external(const float *in, float *ext, Dims dm, int k, cudaStream_t st);
+cudaError_t launch_Y_to_internal(const float *ext, float *in, Dims dm, int k, cudaStream_t st, int stacked);
+cudaError_t launch_Y_to_external(const float *in, float *ext, Dims dm, int k, cudaStream_t st, int stacked);
 // Fv = D_v D_s ubar, Fh = D_h D_s ubar (Sec. II-A differences, periodic)
-cudaError_t launch_xfield(const float *ubar, float *Fv, float *Fh, Dims dm, int grid, cudaStream_t st);
+// open_s: the spectral difference stops at the last band (F's last band is 0)
+cudaError_t launch_xfield(const float *ubar, float *Fv, float *Fh, Dims dm, int grid, cudaStream_t st,
+                         int open_s);
 cudaError_t launch_Z_from_Y(const float *Y, float *Zv, float *Zh, Dims dm, int k, cudaStream_t st);
 cudaError_t launch_init_scalars(Scalars *sc, double alpha, double beta, cudaStream_t st);
 
@@ -178,8 +185,8 @@ cudaError_t launch_sam(const float *u, const float *ref, long long P, int N3, fl
                        cudaStream_t st);
 cudaError_t launch_ssim(const float *u, const float *ref, int N1, int N2, int N3, int b0, int nb, double *out,
                         int grid, cudaStream_t st);
-size_t objective_smem_bytes(int k);
-cudaError_t launch_objective(const float *u, int N1, int N2, int N3, int k, double *out, unsigned *nonconv,
-                             int grid, cudaStream_t st);
+size_t objective_smem_bytes(int k, int stacked);
+cudaError_t launch_objective(const float *u, int N1, int N2, int N3, int k, int stacked, int open_s, double *out,
+                             unsigned *nonconv, int grid, cudaStream_t st);
 
 }  // namespace s3ttv

@@ -1,0 +1,106 @@
+"""GPU parity of the stacked block matrices (2k^2 rows of N3 bands, the
+(2k^2) x (N3 - 1) matrix with the open spectral difference) against the FP64
+oracle, through the C ABI.
+
+Tolerances as in test_gpu_parity: per-operator relative L2 1e-5, scaled by
+n / 25 for n > 25 block rows (n = 2k^2 here: the growth of the worst-case
+rounding of the n-term sums of the FP32 Gram route); after 300 passes relative
+L2 1e-3 of the iterates and MPSNR within 0.01 dB; the FP64 objective 1e-5."""
+import numpy as np
+import pytest
+
+import oracle as O
+from synthetic import WORKLOADS, make_cube, random_state
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def op_tol(n_rows):
+    return 1e-5 * max(1.0, n_rows / 25.0)
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2404_03313_gb300 as P
+    P.library()
+    return P
+
+
+def stacked_solver(P, open_s):
+    s = P.Solver(0)
+    s.set_option(P.OPT_LAYOUT, P.LAYOUT_STACKED)
+    s.set_option(P.OPT_SPECTRAL_BOUNDARY, P.SPECTRAL_OPEN if open_s else P.SPECTRAL_PERIODIC)
+    return s
+
+
+@pytest.mark.parametrize("open_s", [False, True])
+@pytest.mark.parametrize("shape,k", [((9, 8, 7), 3), ((12, 11, 10), 5), ((10, 9, 6), 1), ((16, 16, 12), 8)])
+def test_block_dual_stacked_one_step(P, shape, k, open_s):
+    N1, N2, N3 = shape
+    st = random_state(N1, N2, N3, k, seed=N1 + k + 7 * open_s)
+    M = N3 - 1 if open_s else N3
+    r = np.random.default_rng(k)
+    Y0 = (0.3 * r.standard_normal((N1 * N2, 2 * k * k, M)))
+    ubar = st["u"].astype(np.float64)
+    X = O.structure_tensors(ubar, k, "stacked", not open_s)
+    Yref = O.block_dual_update(Y0, X, 0.25)
+    Zv_ref, Zh_ref = O.structure_tensors_adjoint(Yref, k, shape, "stacked", not open_s)
+    Yg = np.zeros((N1 * N2, 2 * k * k, N3), np.float32)  # the library keeps the last column (open) at 0
+    Yg[:, :, :M] = Y0
+    with stacked_solver(P, open_s) as s:
+        Zv, Zh, info = s.block_dual(Yg, st["u"], k, 0.25)  # Yg updated in place
+    tol = op_tol(2 * k * k)
+    assert rel(Yg[:, :, :M], Yref) <= tol, rel(Yg[:, :, :M], Yref)
+    if open_s:
+        assert not Yg[:, :, M:].any()
+    assert rel(Zv[:, :, :M], Zv_ref) <= tol and rel(Zh[:, :, :M], Zh_ref) <= tol
+    assert info["jacobi_nonconverged"] == 0
+
+
+@pytest.mark.parametrize("open_s", [False, True])
+def test_stacked_300_passes(P, open_s):
+    spec = WORKLOADS["parity_32x32x16_k3"]
+    clean, v = make_cube(spec)
+    eps, alpha, beta = O.radii(v.size, spec.sigma, spec.p_s, spec.p_t)
+    ref, _, _ = O.solve(v, spec.k, eps, alpha, beta, max_iter=300, tol=0.0, layout="stacked",
+                        periodic_s=not open_s)
+    with stacked_solver(P, open_s) as s:
+        u, sp, t, info = s.solve(torch.from_numpy(v).cuda(), eps, alpha, beta, spec.k, max_iter=300, tol=0.0)
+        u, sp, t = (x.cpu().numpy() for x in (u, sp, t))
+    assert info["iters"] == 300
+    for name, got in (("u", u), ("s", sp), ("t", t)):
+        assert rel(got, ref[name]) <= 1e-3, (name, rel(got, ref[name]))
+    assert abs(O.mpsnr(u, clean) - O.mpsnr(ref["u"], clean)) <= 0.01
+    # the stacked problem is a different one: its solution differs from the paper form's
+    with P.Solver(0) as s:
+        up, _, _, _ = s.solve(torch.from_numpy(v).cuda(), eps, alpha, beta, spec.k, max_iter=300, tol=0.0)
+    assert rel(up.cpu().numpy(), u) > 1e-4
+
+
+@pytest.mark.parametrize("open_s", [False, True])
+def test_stacked_objective_and_state_round_trip(P, open_s):
+    spec = WORKLOADS["parity_32x32x16_k3"]
+    clean, v = make_cube(spec)
+    with stacked_solver(P, open_s) as s:
+        got = s.objective(v, 3)
+        ref = O.objective(v.astype(np.float64), 3, "stacked", not open_s)
+        assert abs(got - ref) <= 1e-5 * ref
+        eps, alpha, beta = O.radii(v.size, spec.sigma, spec.p_s, spec.p_t)
+        s.setup(torch.from_numpy(v).cuda(), eps, alpha, beta, 3)
+        s.iterate(5)
+        Y = s.get_state("Y")
+        assert Y.shape == (32 * 32, 18, 16)
+        if open_s:
+            assert not Y[:, :, -1].any()
+        s.set_state("Y", Y)
+        np.testing.assert_array_equal(s.get_state("Y"), Y)
