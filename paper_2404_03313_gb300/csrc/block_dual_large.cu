@@ -38,7 +38,6 @@ namespace {
 constexpr int kLW = 8;         // warps per CTA (two CTAs per SM where shared memory allows)
 constexpr int kLT = kLW * 32;  // threads per CTA
 constexpr int kCW = 48;        // columns of Y' per streamed chunk
-constexpr int kGramTiles = 3;  // upper-triangle Gram tiles a thread may own
 constexpr int kSlots = (kMaxLargeK * kMaxLargeK + 31) / 32;  // row elements a lane holds
 constexpr int kPG = 8;                                        // lanes per row pair in the Jacobi
 
@@ -112,13 +111,13 @@ __device__ __forceinline__ void upper_tile(int t, int nt4, int &ti, int &tj) {
 // The chunk [c0, c0 + kCW) of Y'_l into shared memory, all 4 nt4 rows (rows
 // >= n and columns >= 2 N3p read as 0).  form: add gamma_Y F and write Y'
 // back over Y_l.
-template <bool ST>
+template <bool ST, int LT>
 __device__ void stream_chunk(const Layout &L, float *chunk, float *Yl, const BlockDualArgs &a, const int *pix,
                              int c0, bool form) {
   const Dims &dm = a.dm;
   const int N3p = dm.N3p, W = ST ? N3p : 2 * N3p;
   constexpr int Q = kCW / 4;
-  for (int it = threadIdx.x; it < 4 * L.nt4 * Q; it += kLT) {
+  for (int it = threadIdx.x; it < 4 * L.nt4 * Q; it += LT) {
     const int r = it / Q, q = it - r * Q, c = c0 + 4 * q;
     float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
     if (r < L.n && c < W) {
@@ -141,13 +140,24 @@ __device__ void stream_chunk(const Layout &L, float *chunk, float *Yl, const Blo
   }
 }
 
+// warps per CTA: stacked blocks of up to 64 rows (k <= 5) run four-warp CTAs,
+// four per SM; everything else eight-warp CTAs, two per SM
 template <int K, bool ST>
-__global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs a) {
+__host__ __device__ constexpr int large_warps() {
+  return ST && 2 * K * K <= 64 ? 4 : kLW;
+}
+
+template <int K, bool ST>
+__global__ void __launch_bounds__(large_warps<K, ST>() * 32, large_warps<K, ST>() == 4 ? 4 : 2)
+    block_dual_large_kernel(BlockDualArgs a) {
+  constexpr int LW = large_warps<K, ST>(), LT = LW * 32;
   constexpr int k = K;
   constexpr int NR = ST ? 2 * K * K : K * K;            // rows of a block matrix
+  constexpr int NT4 = (((NR + 1) & ~1) + 3) / 4;
+  constexpr int GT = (NT4 * (NT4 + 1) / 2 + LT - 1) / LT;  // upper-triangle Gram tiles per thread
   constexpr int PE2 = (NR + 2 * kPG - 1) / (2 * kPG);  // float2 pieces of a row a Jacobi lane holds
   extern __shared__ __align__(16) float sm[];
-  __shared__ float s_red[kLW];
+  __shared__ float s_red[LW];
   __shared__ unsigned s_sweeps;
   if (a.sc->done) return;
   const Layout L = layout(NR);
@@ -176,17 +186,17 @@ __global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs 
     __syncthreads();
 
     // ---- 1. Gram of Y', streamed by column chunks ----
-    float acc[kGramTiles][16];
+    float acc[GT][16];
 #pragma unroll
-    for (int u = 0; u < kGramTiles; ++u)
+    for (int u = 0; u < GT; ++u)
 #pragma unroll
       for (int e = 0; e < 16; ++e) acc[u][e] = 0.f;
     for (int c0 = 0; c0 < W; c0 += kCW) {
-      stream_chunk<ST>(L, chunk, Yl, a, pix, c0, true);
+      stream_chunk<ST, LT>(L, chunk, Yl, a, pix, c0, true);
       __syncthreads();
 #pragma unroll
-      for (int u = 0; u < kGramTiles; ++u) {
-        const int t = tid + u * kLT;
+      for (int u = 0; u < GT; ++u) {
+        const int t = tid + u * LT;
         if (t < n_upper) {
           int ti, tj;
           upper_tile(t, nt4, ti, tj);
@@ -216,8 +226,8 @@ __global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs 
       __syncthreads();
     }
 #pragma unroll
-    for (int u = 0; u < kGramTiles; ++u) {
-      const int t = tid + u * kLT;
+    for (int u = 0; u < GT; ++u) {
+      const int t = tid + u * LT;
       if (t < n_upper) {
         int ti, tj;
         upper_tile(t, nt4, ti, tj);
@@ -236,7 +246,7 @@ __global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs 
     // ---- 2. C0 = W G (warm) or G (cold), rows of C into X2 ----
     const float *Wl = a.W ? a.W + (size_t)l * a.w_stride : nullptr;
     const bool warm = a.warm && Wl && !(Wl[0] != Wl[0]);  // NaN marks "start cold"
-    for (int r = warp; r < NP; r += kLW) {
+    for (int r = warp; r < NP; r += LW) {
       float acc2[kSlots];
       if (warm) {
         float wr[kSlots];  // lane j holds W[r][j + 32 i]
@@ -276,7 +286,7 @@ __global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs 
     // ---- 3. one-sided Jacobi on the rows of C ----
     // squared row norms (one warp per row)
     auto norms = [&]() {
-      for (int r = warp; r < NP; r += kLW) {
+      for (int r = warp; r < NP; r += LW) {
         float s = 0.f;
         for (int c = lane; c < n; c += 32) s = fmaf(X2[(size_t)r * GS + c], X2[(size_t)r * GS + c], s);
 #pragma unroll
@@ -300,8 +310,8 @@ __global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs 
       const float sc = __int_as_float((127 - h) << 23), sc2 = sc * sc;
       inv_s = __int_as_float((127 + h) << 23);
       __syncthreads();  // every warp has read nrm for fro
-      for (int e = tid; e < NP * GS; e += kLT) X2[e] *= sc;
-      for (int r = tid; r < NP; r += kLT) nrm[r] *= sc2;
+      for (int e = tid; e < NP * GS; e += LT) X2[e] *= sc;
+      for (int r = tid; r < NP; r += LT) nrm[r] *= sc2;
       fro *= sc2;
       __syncthreads();
     }
@@ -314,7 +324,7 @@ __global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs 
       int rotated = 0;
       for (int step = 0; step < NP - 1; ++step) {
         // kPG lanes per pair, 32 / kPG pairs per warp side by side
-        for (int base = 0; base < NP / 2; base += kLW * (32 / kPG)) {
+        for (int base = 0; base < NP / 2; base += LW * (32 / kPG)) {
           if (base + warp * (32 / kPG) >= NP / 2) continue;  // the whole warp has no pair this round
           const int i = base + warp * (32 / kPG) + (lane / kPG), gl = lane % kPG;
           const bool act = i < NP / 2;
@@ -382,17 +392,17 @@ __global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs 
     // ---- 4. eigen-rows: Ut (X1) and the warm rows W ----
     {
       int zero = 0;
-      for (int r = tid; r < NP; r += kLT) zero += nrm[r] <= floor2 ? 1 : 0;
+      for (int r = tid; r < NP; r += LT) zero += nrm[r] <= floor2 ? 1 : 0;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) zero += __shfl_xor_sync(kFull, zero, o);
       if (lane == 0) s_red[warp] = (float)zero;
     }
     __syncthreads();
     float zero_rows = 0.f;
-    for (int w = 0; w < kLW; ++w) zero_rows += s_red[w];
+    for (int w = 0; w < LW; ++w) zero_rows += s_red[w];
     // all but the NPOS - n zero rows must be nonzero directions, else mark cold
     const bool mark_cold = zero_rows > (float)(NP - n);
-    for (int r = warp; r < NP; r += kLW) {
+    for (int r = warp; r < NP; r += LW) {
       const float nr = nrm[r];
       const float lam = sqrtf(nr) * inv_s;
       const float wt = lam > 1.f ? sqrtf(1.f - rsqrtf(lam)) * rsqrtf(nr) : 0.f;
@@ -408,7 +418,7 @@ __global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs 
     if (a.W && mark_cold && tid == 0) a.W[(size_t)l * a.w_stride] = __int_as_float(0x7fc00000);
 
     // ---- 5a. M = I - Ut^T Ut into X2, 4 x 4 tiles ----
-    for (int t = tid; t < nt4 * nt4; t += kLT) {
+    for (int t = tid; t < nt4 * nt4; t += LT) {
       const int ti = t / nt4, tj = t - ti * nt4;
       float m[16];
 #pragma unroll
@@ -432,10 +442,10 @@ __global__ void __launch_bounds__(kLT, 2) block_dual_large_kernel(BlockDualArgs 
 
     // ---- 5b. Y_l = M Y' by chunks; Z += P_l^T Y_l ----
     for (int c0 = 0; c0 < W; c0 += kCW) {
-      stream_chunk<ST>(L, chunk, Yl, a, pix, c0, false);
+      stream_chunk<ST, LT>(L, chunk, Yl, a, pix, c0, false);
       __syncthreads();
       constexpr int Q = kCW / 4;
-      for (int t = tid; t < nt4 * Q; t += kLT) {
+      for (int t = tid; t < nt4 * Q; t += LT) {
         const int ti = t / Q, q = t - ti * Q;
         float4 y[4];
 #pragma unroll
@@ -485,7 +495,7 @@ long long block_dual_large_w_stride(int k, bool stacked) {
 
 long long block_dual_large_w_stride(int k) { return block_dual_large_w_stride(k, false); }
 
-int block_dual_large_threads() { return kLT; }
+int block_dual_large_threads(int k, bool stacked) { return stacked && 2 * k * k <= 64 ? 128 : kLT; }
 
 namespace {
 typedef void (*LargeKernel)(BlockDualArgs);
@@ -520,14 +530,14 @@ cudaError_t block_dual_large_prepare(int k, bool stacked, size_t smem) {
 cudaError_t block_dual_large_occupancy(int k, bool stacked, size_t smem, int *ctas) {
   const LargeKernel f = large_kernel(k, stacked);
   if (!f) return cudaErrorInvalidValue;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, f, kLT, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, f, block_dual_large_threads(k, stacked), smem);
 }
 
 cudaError_t launch_block_dual_large(const BlockDualArgs &a, int k, bool stacked, int grid, size_t smem,
                                     cudaStream_t st) {
   const LargeKernel f = large_kernel(k, stacked);
   if (!f) return cudaErrorInvalidValue;
-  f<<<grid, kLT, smem, st>>>(a);
+  f<<<grid, block_dual_large_threads(k, stacked), smem, st>>>(a);
   return cudaGetLastError();
 }
 

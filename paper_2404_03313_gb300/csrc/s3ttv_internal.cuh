@@ -157,7 +157,7 @@ constexpr int kMinLargeK = 6, kMaxLargeK = 12, kMaxStackedK = 8;
 size_t block_dual_large_smem_bytes(int k, bool stacked);
 long long block_dual_large_w_stride(int k, bool stacked);
 long long block_dual_large_w_stride(int k);  // paper layout
-int block_dual_large_threads();
+int block_dual_large_threads(int k, bool stacked);
 cudaError_t block_dual_large_prepare(int k, bool stacked, size_t smem_bytes);
 cudaError_t block_dual_large_occupancy(int k, bool stacked, size_t smem_bytes, int *ctas_per_sm);
 cudaError_t launch_block_dual_large(const BlockDualArgs &a, int k, bool stacked, int grid, size_t smem,
