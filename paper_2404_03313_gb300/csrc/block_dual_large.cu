@@ -389,33 +389,82 @@ __global__ void __launch_bounds__(large_warps<K, ST>() * 32, large_warps<K, ST>(
     }
     norms();
 
-    // ---- 4. eigen-rows: Ut (X1) and the warm rows W ----
-    {
-      int zero = 0;
-      for (int r = tid; r < NP; r += LT) zero += nrm[r] <= floor2 ? 1 : 0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) zero += __shfl_xor_sync(kFull, zero, o);
-      if (lane == 0) s_red[warp] = (float)zero;
-    }
-    __syncthreads();
-    float zero_rows = 0.f;
-    for (int w = 0; w < LW; ++w) zero_rows += s_red[w];
-    // all but the NPOS - n zero rows must be nonzero directions, else mark cold
-    const bool mark_cold = zero_rows > (float)(NP - n);
+    // ---- 4. eigen-rows: Ut (X1), and the unit eigenvectors in place in X2 ----
     for (int r = warp; r < NP; r += LW) {
       const float nr = nrm[r];
       const float lam = sqrtf(nr) * inv_s;
       const float wt = lam > 1.f ? sqrtf(1.f - rsqrtf(lam)) * rsqrtf(nr) : 0.f;
       const float inr = nr > floor2 ? rsqrtf(nr) : 0.f;
-      float *ww = a.W ? a.W + (size_t)l * a.w_stride + (size_t)r * n : nullptr;
       for (int c = lane; c < GS; c += 32) {
         const float v = c < n ? X2[(size_t)r * GS + c] : 0.f;
         X1[(size_t)r * GS + c] = v * wt;
-        if (ww && !mark_cold && c < n) ww[c] = v * inr;
+        X2[(size_t)r * GS + c] = v * inr;
       }
     }
-    __syncthreads();  // every W row written before the marker may overwrite W[0]
-    if (a.W && mark_cold && tid == 0) a.W[(size_t)l * a.w_stride] = __int_as_float(0x7fc00000);
+    __syncthreads();
+
+    // ---- 4b. the warm rows W: the eigenvectors completed to an orthonormal basis ----
+    // Rows below the numerical-zero floor carry no reliable direction.  Each is
+    // replaced by a unit vector e_j orthogonalized (classical Gram-Schmidt,
+    // twice) against every unit row so far, taking the first j whose remainder
+    // keeps more than 1 / (2 n) of its squared norm (the largest remainder is
+    // at least 1 / n while the rows span less than R^n).  The next pass starts
+    // from this complete basis; a block is marked cold only if that fails.
+    if (a.W) {
+      float *xv = chunk, *coef = chunk + GS;  // the chunk is free until the apply
+      bool cold = false;
+      int next_e = 0;
+      for (int r = 0; r < n && !cold; ++r) {
+        if (nrm[r] > floor2) continue;  // block-uniform: shared memory read after a barrier
+        bool placed = false;
+        while (!placed && next_e < n) {
+          const int j = next_e++;
+          for (int c = tid; c < n; c += LT) xv[c] = c == j ? 1.f : 0.f;
+          __syncthreads();
+          for (int pass = 0; pass < 2; ++pass) {
+            for (int s2 = warp; s2 < n; s2 += LW) {
+              float d = 0.f;
+              if (nrm[s2] > floor2)
+                for (int c = lane; c < n; c += 32) d = fmaf(X2[(size_t)s2 * GS + c], xv[c], d);
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
+              if (lane == 0) coef[s2] = d;
+            }
+            __syncthreads();
+            for (int c = tid; c < n; c += LT) {
+              float x = xv[c];
+              for (int s2 = 0; s2 < n; ++s2) x = fmaf(-coef[s2], X2[(size_t)s2 * GS + c], x);
+              xv[c] = x;
+            }
+            __syncthreads();
+          }
+          float q = 0.f;
+          for (int c = tid; c < n; c += LT) q = fmaf(xv[c], xv[c], q);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(kFull, q, o);
+          if (lane == 0) s_red[warp] = q;
+          __syncthreads();
+          q = 0.f;
+          for (int w = 0; w < LW; ++w) q += s_red[w];
+          if (q * (float)(2 * n) > 1.f) {
+            const float iq = rsqrtf(q);
+            for (int c = tid; c < GS; c += LT) X2[(size_t)r * GS + c] = c < n ? xv[c] * iq : 0.f;
+            if (tid == 0) nrm[r] = 1.f;  // a unit row from now on
+            placed = true;
+          }
+          __syncthreads();
+        }
+        if (!placed) cold = true;
+      }
+      if (!cold) {
+        for (int r = warp; r < NP; r += LW) {
+          float *ww = a.W + (size_t)l * a.w_stride + (size_t)r * n;
+          for (int c = lane; c < n; c += 32) ww[c] = X2[(size_t)r * GS + c];
+        }
+      }
+      __syncthreads();  // every W row written before the marker may overwrite W[0]
+      if (cold && tid == 0) a.W[(size_t)l * a.w_stride] = __int_as_float(0x7fc00000);
+    }
 
     // ---- 5a. M = I - Ut^T Ut into X2, 4 x 4 tiles ----
     for (int t = tid; t < nt4 * nt4; t += LT) {
