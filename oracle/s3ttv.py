@@ -67,7 +67,8 @@ def spectral_diffs(u: np.ndarray, periodic_s: bool = True):
     return diff(Ds, AXIS_V), diff(Ds, AXIS_H)
 
 
-def structure_tensors(u: np.ndarray, k: int, layout: str = "paper", periodic_s: bool = True) -> np.ndarray:
+def structure_tensors(u: np.ndarray, k: int, layout: str = "paper", periodic_s: bool = True,
+                      second_order: bool = True) -> np.ndarray:
     """All structure tensors of eq. (SSST) / eq. (rewrite_Lu).
 
     Block l = p*N2 + q holds the second-order differences D_v D_s u and D_h D_s u
@@ -77,10 +78,12 @@ def structure_tensors(u: np.ndarray, k: int, layout: str = "paper", periodic_s: 
     layout "paper" (eq. SSST): shape (L, k*k, 2*M), row r, columns
     [v_1 h_1 ... v_M h_M].  layout "stacked": shape (L, 2*k*k, M), row 2r the
     vertical and row 2r + 1 the horizontal differences of pixel r, one column per
-    band.  M = N3 with the periodic D_s, N3 - 1 without.
+    band.  M = N3 with the periodic D_s, N3 - 1 without.  second_order=False
+    builds STV's tensors instead: first-order spatial differences D_v u, D_h u
+    (no D_s; M = N3).
     """
     N1, N2, N3 = u.shape
-    Fv, Fh = spectral_diffs(u, periodic_s)
+    Fv, Fh = spectral_diffs(u, periodic_s) if second_order else (diff(u, AXIS_V), diff(u, AXIS_H))
     M = Fv.shape[2]
     if layout == "paper":
         X = np.empty((N1, N2, k * k, 2 * M))
@@ -120,7 +123,7 @@ def structure_tensors_adjoint(Y: np.ndarray, k: int, shape, layout: str = "paper
     """sum_l P_l^T Y_l split into its vertical and horizontal parts (Zv, Zh),
     each (N1, N2, M) with M as in :func:`structure_tensors`."""
     N1, N2, N3 = shape
-    M = N3 if periodic_s else N3 - 1
+    M = Y.shape[-1] // 2 if layout == "paper" else Y.shape[-1]
     Zv = np.zeros((N1, N2, M))
     Zh = np.zeros((N1, N2, M))
     if layout == "paper":
@@ -148,10 +151,13 @@ def spectral_diff_adjoint(w: np.ndarray, periodic_s: bool = True) -> np.ndarray:
     return pad[..., :-1] - pad[..., 1:]
 
 
-def linear_op_adjoint_u(Y: np.ndarray, k: int, shape, layout: str = "paper", periodic_s: bool = True) -> np.ndarray:
-    """sum_l D_s^T D^T P_l^T Y_l, the dual-to-primal term of Alg. 1 step 2."""
+def linear_op_adjoint_u(Y: np.ndarray, k: int, shape, layout: str = "paper", periodic_s: bool = True,
+                        second_order: bool = True) -> np.ndarray:
+    """sum_l D_s^T D^T P_l^T Y_l, the dual-to-primal term of Alg. 1 step 2
+    (sum_l D^T P_l^T Y_l for STV's first-order tensors)."""
     Zv, Zh = structure_tensors_adjoint(Y, k, shape, layout, periodic_s)
-    return spectral_diff_adjoint(diff_adj(Zv, AXIS_V) + diff_adj(Zh, AXIS_H), periodic_s)
+    w = diff_adj(Zv, AXIS_V) + diff_adj(Zh, AXIS_H)
+    return spectral_diff_adjoint(w, periodic_s) if second_order else w
 
 
 def linear_op_adjoint_u_at(Y: np.ndarray, k: int, shape, i: int, j: int, b: int) -> float:
@@ -238,8 +244,14 @@ def proj_l1_ball(x: np.ndarray, radius: float) -> np.ndarray:
 # ----------------------------------------------------------------------------
 # Step sizes: eq. (stepsize_denoising) and Lemma 1 (eq. Preconditioners).
 # ----------------------------------------------------------------------------
-def step_sizes(N1: int, N2: int, k: int, policy: str = "paper") -> dict:
+def step_sizes(N1: int, N2: int, k: int, policy: str = "paper", reg: str = "s3ttv") -> dict:
     """Step sizes of Alg. 1.
+
+    For the comparison regularisers the paper runs through the same P-PDS (Sec.
+    IV: the regularisation function of Prob. (S3TTV_denoising) replaced), the
+    exact Lemma 1 values of their operators (``policy`` is ignored): STV
+    (nuclear norms of P_l D u): gamma_u = 1/(4k^2 + 1), gamma_Y = 1/2; SSTV
+    (l1 norm of D D_s u): gamma_u = 1/9, gamma_Y = 1/4.
 
     ``policy="paper"``: eq. (stepsize_denoising) as printed, gamma_u = 1/(8L + 1)
     with L = N1*N2 blocks.  ``policy="pc_exact"``: gamma_u = 1/(8k^2 + 1), the exact
@@ -247,6 +259,12 @@ def step_sizes(N1: int, N2: int, k: int, policy: str = "paper") -> dict:
     The other five are the same in both (Lemma 1 reproduces them exactly).
     """
     L = N1 * N2
+    if reg == "stv":
+        return {"u": 1.0 / (4.0 * k * k + 1.0), "s": 1.0, "t": 1.0 / 3.0, "Y": 0.5, "y2": 0.5, "y3": 1.0 / 3.0}
+    if reg == "sstv":
+        return {"u": 1.0 / 9.0, "s": 1.0, "t": 1.0 / 3.0, "Y": 0.25, "y2": 0.5, "y3": 1.0 / 3.0}
+    if reg != "s3ttv":
+        raise ValueError(reg)
     if policy == "paper":
         gu = 1.0 / (8.0 * L + 1.0)
     elif policy == "pc_exact":
@@ -256,7 +274,7 @@ def step_sizes(N1: int, N2: int, k: int, policy: str = "paper") -> dict:
     return {"u": gu, "s": 1.0, "t": 1.0 / 3.0, "Y": 0.25, "y2": 0.5, "y3": 1.0 / 3.0}
 
 
-def assemble_operator(N1: int, N2: int, N3: int, k: int):
+def assemble_operator(N1: int, N2: int, N3: int, k: int, reg: str = "s3ttv"):
     """The linear operator of Prob. (denoising2PPDS) as scipy.sparse blocks.
 
     Built entry by entry from the index definitions (not from :func:`diff`), so it
@@ -286,6 +304,8 @@ def assemble_operator(N1: int, N2: int, N3: int, k: int):
     Dv, Dh, Ds = dmat(0), dmat(1), dmat(2)
     DvDs = (Dv @ Ds).tocsr()
     DhDs = (Dh @ Ds).tocsr()
+    if reg == "stv":  # first-order spatial differences in the blocks
+        DvDs, DhDs = Dv, Dh
     L = N1 * N2
     rows, cols, vals = [], [], []
     for p in range(N1):
@@ -302,6 +322,8 @@ def assemble_operator(N1: int, N2: int, N3: int, k: int):
                             cols += list(src.indices)
                             vals += list(src.data)
     AY = sp.csr_matrix((vals, (rows, cols)), shape=(L * k * k * 2 * N3, N))
+    if reg == "sstv":  # no blocks: the dual is (D_v D_s u, D_h D_s u) itself
+        AY = sp.vstack([DvDs, DhDs]).tocsr()
     I = sp.identity(N, format="csr")
     Z = sp.csr_matrix((N, N))
     return {
@@ -338,28 +360,40 @@ def radii(N: int, sigma: float, p_s: float, p_t: float, rho: float = 0.95):
 # ----------------------------------------------------------------------------
 # Alg. 1: the P-PDS solver.
 # ----------------------------------------------------------------------------
-def init_state(v: np.ndarray, k: int, layout: str = "paper", periodic_s: bool = True) -> dict:
-    """Initial values (Alg. 1 leaves them open): u = v, s = t = 0, duals 0."""
+def init_state(v: np.ndarray, k: int, layout: str = "paper", periodic_s: bool = True, reg: str = "s3ttv") -> dict:
+    """Initial values (Alg. 1 leaves them open): u = v, s = t = 0, duals 0.  For
+    SSTV the dual Y is the pair (Y_v, Y_h) of cubes, shape (2, N1, N2, N3)."""
     v = np.asarray(v, dtype=np.float64)
     z = np.zeros_like(v)
-    Y = np.zeros_like(structure_tensors(v, k, layout, periodic_s))
+    if reg == "sstv":
+        Y = np.zeros((2,) + v.shape)
+    else:
+        Y = np.zeros_like(structure_tensors(v, k, layout, periodic_s, reg != "stv"))
     return {"u": v.copy(), "s": z.copy(), "t": z.copy(), "y2": z.copy(), "y3": z.copy(), "Y": Y}
 
 
 def iterate(state: dict, v: np.ndarray, k: int, eps: float, alpha: float, beta: float,
             mu_min: float, mu_max: float, gammas: dict, layout: str = "paper",
-            periodic_s: bool = True) -> tuple[dict, float]:
+            periodic_s: bool = True, reg: str = "s3ttv") -> tuple[dict, float]:
     """One pass of Alg. 1 (steps 2-14); returns (new state, relative change).
 
     The relative change is eq. (StopCri_simulated): ||u+ - u||_2 / ||u||_2.
     ``layout`` and ``periodic_s`` choose the block matrices (see
-    :func:`structure_tensors`); the paper's are the defaults.
+    :func:`structure_tensors`); the paper's are the defaults.  ``reg`` replaces
+    the regularisation function as Sec. IV does for the comparison methods:
+    "stv" (block nuclear norms of first-order spatial differences) or "sstv"
+    (l1 norm of D D_s u, whose conjugate prox is the projection onto the unit
+    l_inf ball, computed here through eq. ProxConjugate and soft thresholding).
     """
     v = np.asarray(v, dtype=np.float64)
     u, s, t, y2, y3, Y = (state[n] for n in ("u", "s", "t", "y2", "y3", "Y"))
     g = gammas
     # Step 2: u update, box projection.
-    u_new = proj_box(u - g["u"] * (linear_op_adjoint_u(Y, k, u.shape, layout, periodic_s) + y3), mu_min, mu_max)
+    if reg == "sstv":
+        lin = spectral_diff_adjoint(diff_adj(Y[0], AXIS_V) + diff_adj(Y[1], AXIS_H), True)
+    else:
+        lin = linear_op_adjoint_u(Y, k, u.shape, layout, periodic_s, reg != "stv")
+    u_new = proj_box(u - g["u"] * (lin + y3), mu_min, mu_max)
     # Step 3: sparse noise, l1 ball of radius alpha.
     s_new = proj_l1_ball(s - g["s"] * y3, alpha)
     # Step 4: stripe noise, l1 ball of radius beta.
@@ -367,7 +401,12 @@ def iterate(state: dict, v: np.ndarray, k: int, eps: float, alpha: float, beta: 
     # Steps 5-7: extrapolation.
     ub, sb, tb = 2.0 * u_new - u, 2.0 * s_new - s, 2.0 * t_new - t
     # Steps 8-11: every block dual, through the nuclear-norm conjugate prox.
-    Y_new = block_dual_update(Y, structure_tensors(ub, k, layout, periodic_s), g["Y"])
+    if reg == "sstv":
+        Yp = Y + g["Y"] * np.stack(spectral_diffs(ub, True))
+        w = Yp / g["Y"]  # Y+ = Y' - gamma prox_{||.||_1 / gamma}(Y' / gamma)
+        Y_new = Yp - g["Y"] * np.sign(w) * np.maximum(np.abs(w) - 1.0 / g["Y"], 0.0)
+    else:
+        Y_new = block_dual_update(Y, structure_tensors(ub, k, layout, periodic_s, reg != "stv"), g["Y"])
     # Step 12: prox of the conjugate of iota_{0} is the identity (eq. prox_zeroset).
     y2_new = y2 + g["y2"] * diff(tb, AXIS_V)
     # Steps 13-14: fidelity dual through the l2-ball projection.
@@ -381,19 +420,20 @@ def iterate(state: dict, v: np.ndarray, k: int, eps: float, alpha: float, beta: 
 
 def solve(v: np.ndarray, k: int, eps: float, alpha: float, beta: float, mu_min: float = 0.0,
           mu_max: float = 1.0, max_iter: int = 5000, tol: float = 1e-5, policy: str = "paper",
-          state: dict | None = None, trace: list | None = None, layout: str = "paper", periodic_s: bool = True):
+          state: dict | None = None, trace: list | None = None, layout: str = "paper", periodic_s: bool = True,
+          reg: str = "s3ttv"):
     """Run Alg. 1 until the relative change is below ``tol`` or ``max_iter`` passes.
 
     Returns (state, iterations completed, last relative change).
     """
     v = np.asarray(v, dtype=np.float64)
     N1, N2, _ = v.shape
-    gam = step_sizes(N1, N2, k, policy)
-    st = init_state(v, k, layout, periodic_s) if state is None else state
+    gam = step_sizes(N1, N2, k, policy, reg)
+    st = init_state(v, k, layout, periodic_s, reg) if state is None else state
     rel = float("inf")
     it = 0
     while it < max_iter:
-        st, rel = iterate(st, v, k, eps, alpha, beta, mu_min, mu_max, gam, layout, periodic_s)
+        st, rel = iterate(st, v, k, eps, alpha, beta, mu_min, mu_max, gam, layout, periodic_s, reg)
         it += 1
         if trace is not None:
             trace.append(rel)
@@ -419,9 +459,15 @@ def mpsnr(u: np.ndarray, ref: np.ndarray, trim: int = 3) -> float:
     return float(np.mean(vals))
 
 
-def objective(u: np.ndarray, k: int, layout: str = "paper", periodic_s: bool = True) -> float:
-    """S3TTV(u) = sum_l ||T_u^(l)||_*, eq. (S3TTV_Lu) (for the chosen block matrices)."""
-    X = structure_tensors(np.asarray(u, np.float64), k, layout, periodic_s)
+def objective(u: np.ndarray, k: int, layout: str = "paper", periodic_s: bool = True, reg: str = "s3ttv") -> float:
+    """S3TTV(u) = sum_l ||T_u^(l)||_*, eq. (S3TTV_Lu) (for the chosen block
+    matrices); STV's block nuclear norms of first-order differences; SSTV's
+    ||D D_s u||_1."""
+    u = np.asarray(u, np.float64)
+    if reg == "sstv":
+        Fv, Fh = spectral_diffs(u, True)
+        return float(np.abs(Fv).sum() + np.abs(Fh).sum())
+    X = structure_tensors(u, k, layout, periodic_s, reg != "stv")
     return float(np.linalg.svd(X, compute_uv=False).sum())
 
 

@@ -584,3 +584,47 @@ def test_stacked_and_open_adjoint_identities(layout, periodic_s):
     lhs = float((X * Y).sum())
     rhs = float((u * O.linear_op_adjoint_u(Y, 2, u.shape, layout, periodic_s)).sum())
     assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+
+
+# ---------------------------------------------------------------------------
+# Comparison regularisers through the same P-PDS (Sec. IV): STV and SSTV
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("reg,k", [("stv", 2), ("stv", 1), ("sstv", 2)])
+def test_comparison_step_sizes_are_lemma1_on_assembled_operators(reg, k):
+    got = O.lemma1_step_sizes(O.assemble_operator(4, 5, 3, k, reg))
+    want = O.step_sizes(4, 5, k, "paper", reg)
+    for key in ("u", "s", "t", "Y", "y2", "y3"):
+        assert got[key][0] == pytest.approx(want[key], rel=1e-12), key
+        assert got[key][1], key  # every column (row) has the same abs-sum
+
+
+def test_sstv_dual_prox_is_the_clip_to_the_unit_box():
+    """Moreau (eq. ProxConjugate) with prox of gamma^-1 ||.||_1 (soft threshold)
+    reduces to clipping every entry of Y' to [-1, 1]."""
+    r = np.random.default_rng(41)
+    v = r.uniform(0, 1, (5, 6, 4))
+    st = O.init_state(v, 1, reg="sstv")
+    st["Y"] = 2.0 * r.standard_normal(st["Y"].shape)
+    gam = O.step_sizes(5, 6, 1, "paper", "sstv")
+    new, _ = O.iterate(st, v, 1, 1.0, 5.0, 3.0, 0.0, 1.0, gam, reg="sstv")
+    ub = 2.0 * new["u"] - st["u"]
+    Yp = st["Y"] + gam["Y"] * np.stack(O.spectral_diffs(ub, True))
+    np.testing.assert_allclose(new["Y"], np.clip(Yp, -1.0, 1.0), atol=1e-14)
+
+
+def test_stv_tensors_adjoint_and_k1_closed_form():
+    r = np.random.default_rng(42)
+    u = r.standard_normal((4, 5, 6))
+    X = O.structure_tensors(u, 2, second_order=False)
+    Y = r.standard_normal(X.shape)
+    lhs = float((X * Y).sum())
+    rhs = float((u * O.linear_op_adjoint_u(Y, 2, u.shape, second_order=False)).sum())
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+    dv = np.roll(u, -1, 0) - u
+    dh = np.roll(u, -1, 1) - u
+    expect = np.sqrt((dv ** 2).sum(axis=2) + (dh ** 2).sum(axis=2)).sum()
+    assert O.objective(u, 1, reg="stv") == pytest.approx(expect, rel=1e-12)
+    flat = np.ones((4, 5, 6))
+    assert O.objective(flat, 2, reg="stv") == 0.0 and O.objective(flat, 2, reg="sstv") == 0.0
+    Fv, Fh = O.spectral_diffs(u, True)
+    assert O.objective(u, 2, reg="sstv") == pytest.approx(np.abs(Fv).sum() + np.abs(Fh).sum(), rel=1e-14)
