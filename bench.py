@@ -269,6 +269,7 @@ def run_ours(args, spec):
     solver.set_option(P.OPT_TENSOR_CORES, args.tensor_cores)
     solver.set_option(P.OPT_LAYOUT, P.LAYOUT_STACKED if args.layout == "stacked" else P.LAYOUT_PAPER)
     solver.set_option(P.OPT_SPECTRAL_BOUNDARY, P.SPECTRAL_OPEN if args.spectral == "open" else P.SPECTRAL_PERIODIC)
+    solver.set_option(P.OPT_REGULARIZER, {"s3ttv": P.REG_S3TTV, "stv": P.REG_STV, "sstv": P.REG_SSTV}[args.reg])
     vd = torch.from_numpy(v).to(f"cuda:{dev}")
     torch.cuda.synchronize()
 
@@ -305,7 +306,15 @@ def run_ours(args, spec):
     alg_bytes = bytes_per_voxel * N
     peak, peak_src = measured_peaks()
     stacked = args.layout == "stacked"
-    if spec.k <= 5 and not stacked:
+    if args.reg == "sstv":
+        # SSTV: the dual step is one elementwise kernel (the block_dual class):
+        # ubar read, Y read and written, Z written: 4 + 8 + 8 + 8 B per voxel
+        sb = 28 * N
+        achieved = sb / bd_avg_s / 1e9 if bd_avg_s > 0 else 0.0
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": None, "kernel": "sstv_dual_kernel", "peak_source": peak_src,
+                    "algorithmic_bytes_per_launch": sb, "avg_launch_ms": bd_avg_s * 1000.0}
+    elif spec.k <= 5 and not stacked:
         achieved = alg_bytes / bd_avg_s / 1e9 if bd_avg_s > 0 else 0.0
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": block_dual_traffic(spec.k, N), "kernel": f"block_dual_kernel<{spec.k}, *>",
@@ -366,7 +375,7 @@ def run_ours(args, spec):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "N1": spec.N1, "N2": spec.N2, "N3": spec.N3, "k": spec.k,
-                       "policy": args.policy, "layout": args.layout, "spectral": args.spectral,
+                       "policy": args.policy, "layout": args.layout, "spectral": args.spectral, "reg": args.reg,
                        "parallelism": f"replicas{world}",
                        "block_dual_products": ("tensor cores, each FP32 operand split into two TF32 parts"
                                                if args.tensor_cores else "CUDA cores, FP32 FMA"),
@@ -682,6 +691,8 @@ def main(argv=None):
                     help="block matrices: the paper's k^2 x 2N3 or the stacked 2k^2 x N3")
     ap.add_argument("--spectral", choices=("periodic", "open"), default="periodic",
                     help="spectral difference: periodic (the paper) or open (no wrap-around)")
+    ap.add_argument("--reg", choices=("s3ttv", "stv", "sstv"), default="s3ttv",
+                    help="regularisation function: S3TTV (the paper) or a comparison one run by the same P-PDS")
     ap.add_argument("--no-tol-run", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

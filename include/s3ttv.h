@@ -96,9 +96,25 @@ enum {
                                       0: the same products with FP32 FMAs on CUDA cores   */
   S3TTV_OPT_LAYOUT = 8,            /* block matrices X_l: S3TTV_LAYOUT_PAPER (default) or
                                       S3TTV_LAYOUT_STACKED (below)                        */
-  S3TTV_OPT_SPECTRAL_BOUNDARY = 9  /* D_s: S3TTV_SPECTRAL_PERIODIC (default, Sec. II-A)
+  S3TTV_OPT_SPECTRAL_BOUNDARY = 9, /* D_s: S3TTV_SPECTRAL_PERIODIC (default, Sec. II-A)
                                       or S3TTV_SPECTRAL_OPEN (below)                      */
+  S3TTV_OPT_REGULARIZER = 10       /* the regularisation function of the problem:
+                                      S3TTV_REG_S3TTV (default) or a comparison one (below) */
 };
+/* Regularisers (option S3TTV_OPT_REGULARIZER).  Sec. IV runs its P-PDS-solvable
+ * comparison methods by replacing S3TTV in Prob. (S3TTV_denoising) and solving
+ * with the same P-PDS; two of them are built:
+ *   S3TTV_REG_STV   sum_l || P_l D u ||_*: the nuclear norms of structure
+ *                   tensors of first-order spatial differences (k^2 x 2N3
+ *                   blocks, same block-dual path; the primal step has no D_s^T);
+ *   S3TTV_REG_SSTV  || D D_s u ||_1: the dual is the cube pair (Y_v, Y_h) and
+ *                   its conjugate prox is the clip to [-1, 1].
+ * Their step sizes are the exact Lemma 1 values of their operators
+ * (STV: gamma_u = 1/(4k^2 + 1), gamma_Y = 1/2; SSTV: gamma_u = 1/9,
+ * gamma_Y = 1/4; S3TTV_OPT_STEP_POLICY applies to S3TTV only).  With SSTV the
+ * external "Y" state is [2][N1][N2][N3] (Y_v then Y_h) and s3ttv_block_dual
+ * returns S3TTV_EUNSUPPORTED.  Changing the option drops the problem set up. */
+enum { S3TTV_REG_S3TTV = 0, S3TTV_REG_STV = 1, S3TTV_REG_SSTV = 2 };
 /* Block-matrix layouts (option S3TTV_OPT_LAYOUT).  PAPER is eq. (SSST): X_l is
  * k^2 x 2N3, row r the window pixel r = a k + c, columns [v_1 h_1 ... v_N3 h_N3].
  * STACKED is the (2k^2) x N3 matrix of the vertical and horizontal differences

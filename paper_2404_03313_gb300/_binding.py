@@ -23,6 +23,8 @@ OPT_TENSOR_CORES = 7
 OPT_LAYOUT, OPT_SPECTRAL_BOUNDARY = 8, 9
 LAYOUT_PAPER, LAYOUT_STACKED = 0, 1
 SPECTRAL_PERIODIC, SPECTRAL_OPEN = 0, 1
+OPT_REGULARIZER = 10
+REG_S3TTV, REG_STV, REG_SSTV = 0, 1, 2
 KERNEL_CLASSES = ("primal", "l1_search", "block_dual", "dual", "finalize")
 STATE = {"u": 0, "s": 1, "t": 2, "y2": 3, "y3": 4, "Y": 5}
 
@@ -228,6 +230,8 @@ class Solver:
         self._check(self._lib.s3ttv_set_option(self._h, key, float(value)), "set_option")
         if key == OPT_LAYOUT:
             self.layout = int(value)
+        if key == OPT_REGULARIZER:
+            self.reg = int(value)
 
     def workspace_bytes(self):
         return int(self._lib.s3ttv_workspace_bytes(self._h))
@@ -323,6 +327,8 @@ class Solver:
     def _state_size(self, which):
         N1, N2, N3 = self.shape
         if which == "Y":
+            if getattr(self, "reg", REG_S3TTV) == REG_SSTV:
+                return (2, N1, N2, N3)
             if getattr(self, "layout", LAYOUT_PAPER) == LAYOUT_STACKED:
                 return (N1 * N2, 2 * self.k * self.k, N3)
             return (N1 * N2, self.k * self.k, 2 * N3)

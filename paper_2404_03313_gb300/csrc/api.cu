@@ -27,6 +27,7 @@ struct s3ttv_ctx {
   int tensor_cores = 1;
   int layout = S3TTV_LAYOUT_PAPER;  // block matrices: paper k^2 x 2N3 or stacked 2k^2 x N3
   int open_s = 0;                   // 1: D_s stops at the last band (no wrap-around)
+  int reg = S3TTV_REG_S3TTV;        // regularisation function (S3TTV, STV or SSTV)
   // problem
   bool ready = false;
   Dims dm{};
@@ -319,7 +320,11 @@ int check_problem(s3ttv_ctx *ctx, const float *v, int N1, int N2, int N3, float 
   return S3TTV_OK;
 }
 
-void step_sizes(int N1, int N2, int k, int policy, double g[6]) {
+// Step sizes (u, s, t, Y, y2, y3).  S3TTV: eq. (stepsize_denoising) under the
+// policy; STV and SSTV: the exact Lemma 1 values of their operators (column
+// abs-sums 4k^2 and 8 of P_l D and D D_s, row abs-sums 2 and 4, plus the
+// identity of y3).
+void step_sizes(int N1, int N2, int k, int policy, double g[6], int reg = S3TTV_REG_S3TTV) {
   const double L = (double)N1 * (double)N2;
   g[0] = policy == S3TTV_STEP_PC_EXACT ? 1.0 / (8.0 * k * k + 1.0) : 1.0 / (8.0 * L + 1.0);
   g[1] = 1.0;
@@ -327,6 +332,12 @@ void step_sizes(int N1, int N2, int k, int policy, double g[6]) {
   g[3] = 0.25;
   g[4] = 0.5;
   g[5] = 1.0 / 3.0;
+  if (reg == S3TTV_REG_STV) {
+    g[0] = 1.0 / (4.0 * k * k + 1.0);
+    g[3] = 0.5;
+  } else if (reg == S3TTV_REG_SSTV) {
+    g[0] = 1.0 / 9.0;
+  }
 }
 
 // Copy a caller cube (host or device, [N1][N2][N3]) into an internal padded cube.
@@ -358,6 +369,11 @@ int store_cube(s3ttv_ctx *ctx, const float *src, float *dst, const double *scale
 
 int load_Y(s3ttv_ctx *ctx, const float *src) {
   const Dims &dm = ctx->dm;
+  if (ctx->reg == S3TTV_REG_SSTV) {  // (Yv, Yh): two cubes
+    int rc = load_cube(ctx, src, ctx->Y, 1.f);
+    if (!rc) rc = load_cube(ctx, src + dm.P * dm.N3, ctx->Y + dm.Np, 1.f);
+    return rc;
+  }
   const size_t ne = (size_t)dm.P * ctx->k * ctx->k * 2 * dm.N3;
   const float *from = src;
   if (!is_device_ptr(src)) {
@@ -372,6 +388,11 @@ int load_Y(s3ttv_ctx *ctx, const float *src) {
 
 int store_Y(s3ttv_ctx *ctx, float *dst) {
   const Dims &dm = ctx->dm;
+  if (ctx->reg == S3TTV_REG_SSTV) {
+    int rc = store_cube(ctx, ctx->Y, dst, nullptr);
+    if (!rc) rc = store_cube(ctx, ctx->Y + dm.Np, dst + dm.P * dm.N3, nullptr);
+    return rc;
+  }
   const size_t ne = (size_t)dm.P * ctx->k * ctx->k * 2 * dm.N3;
   if (is_device_ptr(dst)) {
     CU(launch_Y_to_external(ctx->Y, dst, dm, ctx->k, ctx->stream, ctx->layout == S3TTV_LAYOUT_STACKED));
@@ -425,6 +446,7 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   pa.part = ctx->part;
   pa.hcnt = ctx->hcnt;
   pa.hsum = ctx->hsum;
+  pa.no_ds = ctx->reg == S3TTV_REG_STV;
   CU(launch_primal(pa, grid_e, st));
   if (ev) CU(cudaEventRecord(ev[1], st));
 
@@ -443,7 +465,11 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   CU(launch_l1_scan(la, 3, st));
   if (ev) CU(cudaEventRecord(ev[2], st));
 
-  CU(launch_xfield(ctx->ubar, ctx->Fv, ctx->Fh, dm, grid_e, st, ctx->open_s));
+  if (ctx->reg == S3TTV_REG_SSTV) {
+    CU(launch_sstv_dual(ctx->ubar, ctx->Y, ctx->Y + dm.Np, ctx->Zv[par ^ 1], ctx->Zh[par ^ 1], dm,
+                        (float)ctx->gam[3], grid_e, st));
+  } else {
+  CU(launch_xfield(ctx->ubar, ctx->Fv, ctx->Fh, dm, grid_e, st, ctx->open_s, ctx->reg == S3TTV_REG_STV));
   BlockDualArgs ba;
   ba.Y = ctx->Y;
   ba.Fv = ctx->Fv;
@@ -462,6 +488,7 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   if (bd.large) CU(launch_block_dual_large(ba, ctx->k, ctx->layout == S3TTV_LAYOUT_STACKED, bd.grid, bd.smem, st));
   else CU(launch_block_dual(ba, bd.v, bd.grid, bd.smem, st));
   if (ctx->warm_start) ctx->warm_valid = true;
+  }
   if (ev) CU(cudaEventRecord(ev[3], st));
 
   DualArgs da;
@@ -631,7 +658,7 @@ int s3ttv_set_option(s3ttv_ctx *ctx, int key, double value) {
       if (value != S3TTV_STEP_PAPER && value != S3TTV_STEP_PC_EXACT)
         return fail(ctx, S3TTV_EINVAL, "unknown step policy %g", value);
       ctx->step_policy = (int)value;
-      if (ctx->ready) step_sizes(ctx->dm.N1, ctx->dm.N2, ctx->k, ctx->step_policy, ctx->gam);
+      if (ctx->ready) step_sizes(ctx->dm.N1, ctx->dm.N2, ctx->k, ctx->step_policy, ctx->gam, ctx->reg);
       return S3TTV_OK;
     case S3TTV_OPT_CHECK_EVERY:
       if (!(value >= 1 && value <= 1e6)) return fail(ctx, S3TTV_EINVAL, "check_every must be in [1, 1e6]");
@@ -669,6 +696,15 @@ int s3ttv_set_option(s3ttv_ctx *ctx, int key, double value) {
       if ((int)value != ctx->open_s) {
         ctx->open_s = (int)value;
         ctx->ready = false;
+        ctx->warm_valid = false;
+      }
+      return S3TTV_OK;
+    case S3TTV_OPT_REGULARIZER:
+      if (value != S3TTV_REG_S3TTV && value != S3TTV_REG_STV && value != S3TTV_REG_SSTV)
+        return fail(ctx, S3TTV_EINVAL, "regularizer must be S3TTV_REG_S3TTV, S3TTV_REG_STV or S3TTV_REG_SSTV");
+      if ((int)value != ctx->reg) {
+        ctx->reg = (int)value;
+        ctx->ready = false;  // the duals change meaning: set the problem up again
         ctx->warm_valid = false;
       }
       return S3TTV_OK;
@@ -720,7 +756,7 @@ int s3ttv_setup(s3ttv_ctx *ctx, const float *v, int N1, int N2, int N3, float ep
   ctx->beta = beta;
   ctx->mu_min = mu_min;
   ctx->mu_max = mu_max;
-  step_sizes(N1, N2, k, ctx->step_policy, ctx->gam);
+  step_sizes(N1, N2, k, ctx->step_policy, ctx->gam, ctx->reg);
   const size_t cb = sizeof(float) * dm.Np;
   if ((rc = load_cube(ctx, v, ctx->v, 1.f))) return rc;
   CU(cudaMemcpyAsync(ctx->u, ctx->v, cb, cudaMemcpyDeviceToDevice, ctx->stream));  // u0 = v
@@ -838,7 +874,14 @@ int s3ttv_set_state(s3ttv_ctx *ctx, int which, const float *src) {
     case S3TTV_STATE_Y:
       ctx->warm_valid = false;
       rc = load_Y(ctx, src);
-      if (!rc) CU(launch_Z_from_Y(ctx->Y, ctx->Zv[ctx->parity], ctx->Zh[ctx->parity], ctx->dm, ctx->k, ctx->stream));
+      if (!rc && ctx->reg == S3TTV_REG_SSTV) {  // SSTV: Z = Y
+        CU(cudaMemcpyAsync(ctx->Zv[ctx->parity], ctx->Y, sizeof(float) * ctx->dm.Np, cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        CU(cudaMemcpyAsync(ctx->Zh[ctx->parity], ctx->Y + ctx->dm.Np, sizeof(float) * ctx->dm.Np,
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+      } else if (!rc) {
+        CU(launch_Z_from_Y(ctx->Y, ctx->Zv[ctx->parity], ctx->Zh[ctx->parity], ctx->dm, ctx->k, ctx->stream));
+      }
       break;
     default: return fail(ctx, S3TTV_EINVAL, "unknown state %d", which);
   }
@@ -956,6 +999,7 @@ int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, in
     m->warm_start = ctx->warm_start;
     m->layout = ctx->layout;
     m->open_s = ctx->open_s;
+    m->reg = ctx->reg;
     m->profile = false;
     const s3ttv_problem &p = problems[i];
     int rc = s3ttv_setup(m, p.v, p.N1, p.N2, p.N3, p.eps, p.alpha, p.beta, p.mu_min, p.mu_max, p.k);
@@ -1124,6 +1168,7 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   if (!Y || !ubar || !Zv || !Zh) return fail(ctx, S3TTV_EINVAL, "Y, ubar, Zv and Zh are required");
   if (k < 1 || N1 < k || N2 < k || N3 < 1) return fail(ctx, S3TTV_EINVAL, "need N1, N2 >= k >= 1 and N3 >= 1");
   if (!(gamma_Y > 0.f) || !std::isfinite(gamma_Y)) return fail(ctx, S3TTV_EINVAL, "gamma_Y must be > 0");
+  if (ctx->reg == S3TTV_REG_SSTV) return fail(ctx, S3TTV_EUNSUPPORTED, "SSTV has no block duals");
   if (k > kMaxK) return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: this build supports k <= %d", k, kMaxK);
   DeviceGuard g(ctx->device);
   const Dims dm = make_dims(N1, N2, N3);
@@ -1139,7 +1184,8 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   CU(cudaMemsetAsync(ctx->Zv[0], 0, sizeof(float) * dm.Np, ctx->stream));
   CU(cudaMemsetAsync(ctx->Zh[0], 0, sizeof(float) * dm.Np, ctx->stream));
   CU(launch_init_scalars(ctx->sc, 0.0, 0.0, ctx->stream));
-  CU(launch_xfield(ctx->ubar, ctx->Fv, ctx->Fh, dm, elementwise_grid(ctx, dm.Np), ctx->stream, ctx->open_s));
+  CU(launch_xfield(ctx->ubar, ctx->Fv, ctx->Fh, dm, elementwise_grid(ctx, dm.Np), ctx->stream, ctx->open_s,
+                   ctx->reg == S3TTV_REG_STV));
   BlockDualArgs ba;
   ba.Y = ctx->Y;
   ba.Fv = ctx->Fv;
@@ -1193,7 +1239,11 @@ int s3ttv_objective(s3ttv_ctx *ctx, const float *u, int N1, int N2, int N3, int 
   CU(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
   if (objective_smem_bytes(k, stacked) + 2048 > (size_t)dev_max)
     return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d needs %zu bytes of shared memory", k, objective_smem_bytes(k, stacked));
-  CU(launch_objective(du, N1, N2, N3, k, stacked, ctx->open_s, ctx->macc, nonconv, ctx->num_sms * 4, ctx->stream));
+  if (ctx->reg == S3TTV_REG_SSTV)
+    CU(launch_sstv_l1(du, N1, N2, N3, ctx->macc, ctx->num_sms * 8, ctx->stream));
+  else
+    CU(launch_objective(du, N1, N2, N3, k, stacked, ctx->open_s, ctx->reg == S3TTV_REG_STV, ctx->macc, nonconv,
+                        ctx->num_sms * 4, ctx->stream));
   double h[2] = {0.0, 0.0};
   CU(cudaMemcpyAsync(h, ctx->macc, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));

@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(256) primal_kernel(PrimalArgs a) {
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       if (b0 + e < dm.N3) {
-        const float grad = (e == 0 ? wbm : w[e - 1]) - w[e];  // (D_s^T w)[b] = w[b-1] - w[b]
+        // (D_s^T w)[b] = w[b-1] - w[b]; STV's first-order term has no D_s
+        const float grad = a.no_ds ? w[e] : (e == 0 ? wbm : w[e - 1]) - w[e];
         const float y3 = c3 * comp(d4, e);
         const float u = comp(u4, e);
         const float x = u - a.gu * (grad + y3);
@@ -294,7 +295,7 @@ __global__ void Z_from_Y_kernel(const float *__restrict__ Y, float *__restrict__
 // Fv = D_v D_s ubar and Fh = D_h D_s ubar: the second-order differences the
 // structure tensors of eq. (SSST) are cut from, formed once per pass.
 __global__ void xfield_kernel(const float *__restrict__ ubar, float *__restrict__ Fv, float *__restrict__ Fh,
-                              Dims dm, int open_s) {
+                              Dims dm, int open_s, int first_order) {
   const int N3p = dm.N3p, C4 = N3p >> 2, N2 = dm.N2;
   const int nch = (int)(dm.P * C4);
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += gridDim.x * blockDim.x) {
@@ -312,9 +313,14 @@ __global__ void xfield_kernel(const float *__restrict__ ubar, float *__restrict_
     for (int e = 0; e < 4; ++e) {
       if (b0 + e < dm.N3 - open_s) {  // open D_s: no difference past the last band
         const bool in = e < 3 && b0 + e + 1 < dm.N3;
-        const float ds0 = (in ? comp(x0, e + 1) : n0) - comp(x0, e);
-        fv[e] = ((in ? comp(xv, e + 1) : nv) - comp(xv, e)) - ds0;
-        fh[e] = ((in ? comp(xh, e + 1) : nh) - comp(xh, e)) - ds0;
+        if (first_order) {  // STV: D_v u, D_h u
+          fv[e] = comp(xv, e) - comp(x0, e);
+          fh[e] = comp(xh, e) - comp(x0, e);
+        } else {
+          const float ds0 = (in ? comp(x0, e + 1) : n0) - comp(x0, e);
+          fv[e] = ((in ? comp(xv, e + 1) : nv) - comp(xv, e)) - ds0;
+          fh[e] = ((in ? comp(xh, e + 1) : nh) - comp(xh, e)) - ds0;
+        }
       } else {
         fv[e] = fh[e] = 0.f;
       }
@@ -355,6 +361,53 @@ cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// SSTV's dual step (the l1 norm of D D_s u in place of the block nuclear
+// norms): Y' = Y + gamma_Y (D_v D_s ubar, D_h D_s ubar), and the conjugate prox
+// of the l1 norm (eq. ProxConjugate) is the projection onto the unit l_inf
+// ball, Y = clip(Y', -1, 1).  Y = (Yv, Yh) are internal cubes, and
+// Z = sum_l P_l^T Y_l becomes Y itself: written to (Zv, Zh).
+__global__ void sstv_dual_kernel(const float *__restrict__ ubar, float *__restrict__ Yv, float *__restrict__ Yh,
+                                 float *__restrict__ Zv, float *__restrict__ Zh, Dims dm, float gY) {
+  const int N3p = dm.N3p, C4 = N3p >> 2, N2 = dm.N2;
+  const int nch = (int)(dm.P * C4);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += gridDim.x * blockDim.x) {
+    const int pix = (unsigned)c / (unsigned)C4, q = c - pix * C4, b0 = q << 2;
+    const int i = (unsigned)pix / (unsigned)N2, j = pix - i * N2;
+    const size_t p0 = (size_t)pix * N3p;
+    const size_t pv = ((size_t)(i + 1 == dm.N1 ? 0 : i + 1) * N2 + j) * N3p;
+    const size_t ph = ((size_t)i * N2 + (j + 1 == N2 ? 0 : j + 1)) * N3p;
+    const float4 x0 = ld4(ubar + p0 + b0), xv = ld4(ubar + pv + b0), xh = ld4(ubar + ph + b0);
+    const int nb = b0 + 4 < dm.N3 ? b0 + 4 : 0;
+    const float n0 = ubar[p0 + nb], nv = ubar[pv + nb], nh = ubar[ph + nb];
+    const float4 yv4 = ld4(Yv + p0 + b0), yh4 = ld4(Yh + p0 + b0);
+    float yv[4], yh[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (b0 + e < dm.N3) {
+        const bool in = e < 3 && b0 + e + 1 < dm.N3;
+        const float ds0 = (in ? comp(x0, e + 1) : n0) - comp(x0, e);
+        const float fv = ((in ? comp(xv, e + 1) : nv) - comp(xv, e)) - ds0;
+        const float fh = ((in ? comp(xh, e + 1) : nh) - comp(xh, e)) - ds0;
+        yv[e] = fminf(fmaxf(fmaf(gY, fv, comp(yv4, e)), -1.f), 1.f);
+        yh[e] = fminf(fmaxf(fmaf(gY, fh, comp(yh4, e)), -1.f), 1.f);
+      } else {
+        yv[e] = yh[e] = 0.f;
+      }
+    }
+    const float4 ov = make_float4(yv[0], yv[1], yv[2], yv[3]), oh = make_float4(yh[0], yh[1], yh[2], yh[3]);
+    st4(Yv + p0 + b0, ov);
+    st4(Yh + p0 + b0, oh);
+    st4(Zv + p0 + b0, ov);
+    st4(Zh + p0 + b0, oh);
+  }
+}
+
+cudaError_t launch_sstv_dual(const float *ubar, float *Yv, float *Yh, float *Zv, float *Zh, Dims dm, float gY,
+                             int grid, cudaStream_t st) {
+  sstv_dual_kernel<<<grid, 256, 0, st>>>(ubar, Yv, Yh, Zv, Zh, dm, gY);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pad_cube(const float *src, float *dst, Dims dm, float scale, cudaStream_t st) {
   pad_cube_kernel<<<grid_for(dm.Np), 256, 0, st>>>(src, dst, dm, scale);
   return cudaGetLastError();
@@ -375,8 +428,9 @@ cudaError_t launch_Y_to_external(const float *in, float *ext, Dims dm, int k, cu
   return cudaGetLastError();
 }
 
-cudaError_t launch_xfield(const float *ubar, float *Fv, float *Fh, Dims dm, int grid, cudaStream_t st, int open_s) {
-  xfield_kernel<<<grid, 256, 0, st>>>(ubar, Fv, Fh, dm, open_s);
+cudaError_t launch_xfield(const float *ubar, float *Fv, float *Fh, Dims dm, int grid, cudaStream_t st, int open_s,
+                          int first_order) {
+  xfield_kernel<<<grid, 256, 0, st>>>(ubar, Fv, Fh, dm, open_s, first_order);
   return cudaGetLastError();
 }
 

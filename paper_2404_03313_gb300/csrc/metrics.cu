@@ -127,8 +127,8 @@ __global__ void __launch_bounds__(256) ssim_kernel(const float *u, const float *
 constexpr int kObjCW = 32;
 
 __global__ void __launch_bounds__(256) objective_kernel(const float *u, int N1, int N2, int N3, int k, int stacked,
-                                                       int open_s, double tol, int max_sweeps, double *out,
-                                                       unsigned *nonconv) {
+                                                       int open_s, int first_order, double tol, int max_sweeps,
+                                                       double *out, unsigned *nonconv) {
   extern __shared__ double dsm[];
   const int n = stacked ? 2 * k * k : k * k, NP = n + (n & 1), W = stacked ? N3 : 2 * N3;
   double *G = dsm;                 // NP x n
@@ -155,9 +155,13 @@ __global__ void __launch_bounds__(256) objective_kernel(const float *u, int N1, 
           const int i1 = i + 1 == N1 ? 0 : i + 1, j1 = j + 1 == N2 ? 0 : j + 1, b1 = b + 1 == N3 ? 0 : b + 1;
           const size_t s00 = ((size_t)i * N2 + j) * N3;
           const size_t s10 = o ? ((size_t)i * N2 + j1) * N3 : ((size_t)i1 * N2 + j) * N3;
-          const double ds0 = (double)u[s00 + b1] - (double)u[s00 + b];
-          const double ds1 = (double)u[s10 + b1] - (double)u[s10 + b];
-          x = ds1 - ds0;
+          if (first_order) {  // STV: D_v u or D_h u
+            x = (double)u[s10 + b] - (double)u[s00 + b];
+          } else {
+            const double ds0 = (double)u[s00 + b1] - (double)u[s00 + b];
+            const double ds1 = (double)u[s10 + b1] - (double)u[s10 + b];
+            x = ds1 - ds0;
+          }
         }
         X[r * kObjCW + cc] = x;
       }
@@ -249,7 +253,37 @@ __global__ void __launch_bounds__(256) objective_kernel(const float *u, int N1, 
   if (tid == 0) atomicAdd(out, total);
 }
 
+// SSTV's objective ||D D_s u||_1 = sum |D_v D_s u| + |D_h D_s u| (periodic), FP64
+__global__ void __launch_bounds__(256) sstv_l1_kernel(const float *u, int N1, int N2, int N3, double *out) {
+  __shared__ double red[8];
+  const long long N = (long long)N1 * N2 * N3;
+  double acc = 0.0;
+  for (long long e = blockIdx.x * 256LL + threadIdx.x; e < N; e += gridDim.x * 256LL) {
+    const int b = (int)(e % N3);
+    const long long pix = e / N3;
+    const int i = (int)(pix / N2), j = (int)(pix % N2);
+    const int i1 = i + 1 == N1 ? 0 : i + 1, j1 = j + 1 == N2 ? 0 : j + 1, b1 = b + 1 == N3 ? 0 : b + 1;
+    const size_t p0 = (size_t)pix * N3, pv = ((size_t)i1 * N2 + j) * N3, ph = ((size_t)i * N2 + j1) * N3;
+    const double ds0 = (double)u[p0 + b1] - (double)u[p0 + b];
+    acc += fabs(((double)u[pv + b1] - (double)u[pv + b]) - ds0) + fabs(((double)u[ph + b1] - (double)u[ph + b]) - ds0);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    atomicAdd(out, t);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_sstv_l1(const float *u, int N1, int N2, int N3, double *out, int grid, cudaStream_t st) {
+  sstv_l1_kernel<<<grid, 256, 0, st>>>(u, N1, N2, N3, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_band_sqerr(const float *u, const float *ref, long long P, int N3, double *out, int grid,
                               cudaStream_t st) {
@@ -295,14 +329,14 @@ size_t objective_smem_bytes(int k, int stacked) {
   return sizeof(double) * ((size_t)NP * n + (size_t)n * kObjCW);
 }
 
-cudaError_t launch_objective(const float *u, int N1, int N2, int N3, int k, int stacked, int open_s, double *out,
-                             unsigned *nonconv, int grid, cudaStream_t st) {
+cudaError_t launch_objective(const float *u, int N1, int N2, int N3, int k, int stacked, int open_s,
+                             int first_order, double *out, unsigned *nonconv, int grid, cudaStream_t st) {
   const size_t smem = objective_smem_bytes(k, stacked);
   cudaError_t e = cudaFuncSetAttribute(objective_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long L = (long long)N1 * N2;
-  objective_kernel<<<(unsigned)(L < grid ? L : grid), 256, smem, st>>>(u, N1, N2, N3, k, stacked, open_s, 1e-13, 60,
-                                                                       out, nonconv);
+  objective_kernel<<<(unsigned)(L < grid ? L : grid), 256, smem, st>>>(u, N1, N2, N3, k, stacked, open_s, first_order,
+                                                                       1e-13, 60, out, nonconv);
   return cudaGetLastError();
 }
 

@@ -75,6 +75,7 @@ struct PrimalArgs {
   double *part;           // [2][grid]: sum (u+ - u)^2, sum u^2
   unsigned *hcnt;         // [2][kHistBins]
   double *hsum;           // [2][kHistBins]
+  int no_ds;              // 1: the dual term is D^T Z (STV's first-order tensors), no D_s^T
 };
 cudaError_t launch_primal(const PrimalArgs &a, int grid, cudaStream_t st);
 
@@ -172,8 +173,13 @@ cudaError_t launch_Y_to_internal(const float *ext, float *in, Dims dm, int k, cu
 cudaError_t launch_Y_to_external(const float *in, float *ext, Dims dm, int k, cudaStream_t st, int stacked);
 // Fv = D_v D_s ubar, Fh = D_h D_s ubar (Sec. II-A differences, periodic)
 // open_s: the spectral difference stops at the last band (F's last band is 0)
+// first_order: F = (D_v u, D_h u) (STV) instead of the second-order differences
 cudaError_t launch_xfield(const float *ubar, float *Fv, float *Fh, Dims dm, int grid, cudaStream_t st,
-                         int open_s);
+                         int open_s, int first_order);
+// SSTV's dual step: Y = clip(Y + gamma_Y D D_s ubar, -1, 1) on the cube pair
+// (Yv, Yh), and Z = Y
+cudaError_t launch_sstv_dual(const float *ubar, float *Yv, float *Yh, float *Zv, float *Zh, Dims dm, float gY,
+                             int grid, cudaStream_t st);
 cudaError_t launch_Z_from_Y(const float *Y, float *Zv, float *Zh, Dims dm, int k, cudaStream_t st);
 cudaError_t launch_init_scalars(Scalars *sc, double alpha, double beta, cudaStream_t st);
 
@@ -186,7 +192,8 @@ cudaError_t launch_sam(const float *u, const float *ref, long long P, int N3, fl
 cudaError_t launch_ssim(const float *u, const float *ref, int N1, int N2, int N3, int b0, int nb, double *out,
                         int grid, cudaStream_t st);
 size_t objective_smem_bytes(int k, int stacked);
-cudaError_t launch_objective(const float *u, int N1, int N2, int N3, int k, int stacked, int open_s, double *out,
-                             unsigned *nonconv, int grid, cudaStream_t st);
+cudaError_t launch_objective(const float *u, int N1, int N2, int N3, int k, int stacked, int open_s,
+                             int first_order, double *out, unsigned *nonconv, int grid, cudaStream_t st);
+cudaError_t launch_sstv_l1(const float *u, int N1, int N2, int N3, double *out, int grid, cudaStream_t st);
 
 }  // namespace s3ttv

@@ -1,0 +1,90 @@
+"""GPU parity of the comparison regularisers the paper runs through the same
+P-PDS (Sec. IV): STV (block nuclear norms of first-order spatial differences)
+and SSTV (l1 norm of D D_s u), against the FP64 oracle through the C ABI.
+
+Tolerances as in test_gpu_parity: one pass from a random state, relative L2
+1e-5 per state (SSTV's clip is exact; STV's blocks have k^2 = 9 rows); after
+300 passes relative L2 1e-3 of the iterates and MPSNR within 0.01 dB; the FP64
+objective 1e-5 relative."""
+import numpy as np
+import pytest
+
+import oracle as O
+from synthetic import WORKLOADS, make_cube, random_state
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REGS = ["stv", "sstv"]
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2404_03313_gb300 as P
+    P.library()
+    return P
+
+
+def solver_for(P, reg):
+    s = P.Solver(0)
+    s.set_option(P.OPT_REGULARIZER, {"stv": P.REG_STV, "sstv": P.REG_SSTV}[reg])
+    return s
+
+
+@pytest.mark.parametrize("reg", REGS)
+def test_one_pass_from_a_random_state(P, reg):
+    N1, N2, N3, k = 12, 11, 9, 3
+    st = random_state(N1, N2, N3, k, seed=5)
+    r = np.random.default_rng(6)
+    v = r.uniform(0, 1, (N1, N2, N3)).astype(np.float32)
+    if reg == "sstv":
+        st["Y"] = (0.3 * r.standard_normal((2, N1, N2, N3))).astype(np.float32)
+    eps, alpha, beta = 3.0, 20.0, 10.0
+    ref_state = {key: val.astype(np.float64) for key, val in st.items()}
+    gam = O.step_sizes(N1, N2, k, "paper", reg)
+    ref, _ = O.iterate(ref_state, v, k, eps, alpha, beta, 0.0, 1.0, gam, reg=reg)
+    with solver_for(P, reg) as s:
+        s.setup(v, eps, alpha, beta, k)
+        for name in ("u", "s", "t", "y2", "y3", "Y"):
+            s.set_state(name, st[name])
+        s.iterate(1)
+        for name in ("u", "s", "t", "y2", "y3", "Y"):
+            got = s.get_state(name)
+            assert rel(got, ref[name].reshape(got.shape)) <= 1e-5, (name, rel(got, ref[name].reshape(got.shape)))
+
+
+@pytest.mark.parametrize("reg", REGS)
+def test_300_passes(P, reg):
+    spec = WORKLOADS["parity_32x32x16_k3"]
+    clean, v = make_cube(spec)
+    eps, alpha, beta = O.radii(v.size, spec.sigma, spec.p_s, spec.p_t)
+    ref, _, _ = O.solve(v, spec.k, eps, alpha, beta, max_iter=300, tol=0.0, reg=reg)
+    with solver_for(P, reg) as s:
+        u, sp, t, info = s.solve(torch.from_numpy(v).cuda(), eps, alpha, beta, spec.k, max_iter=300, tol=0.0)
+        u, sp, t = (x.cpu().numpy() for x in (u, sp, t))
+    assert info["iters"] == 300
+    for name, got in (("u", u), ("s", sp), ("t", t)):
+        assert rel(got, ref[name]) <= 1e-3, (name, rel(got, ref[name]))
+    assert abs(O.mpsnr(u, clean) - O.mpsnr(ref["u"], clean)) <= 0.01
+    with P.Solver(0) as s:  # a different problem from S3TTV's
+        us, _, _, _ = s.solve(torch.from_numpy(v).cuda(), eps, alpha, beta, spec.k, max_iter=300, tol=0.0)
+    assert rel(us.cpu().numpy(), u) > 1e-4
+
+
+@pytest.mark.parametrize("reg", REGS)
+def test_objective(P, reg):
+    spec = WORKLOADS["parity_32x32x16_k3"]
+    _, v = make_cube(spec)
+    with solver_for(P, reg) as s:
+        got = s.objective(v, 3)
+    ref = O.objective(v.astype(np.float64), 3, reg=reg)
+    assert abs(got - ref) <= 1e-5 * ref, (got, ref)
