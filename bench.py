@@ -270,13 +270,16 @@ def run_ours(args, spec):
     solver.set_option(P.OPT_LAYOUT, P.LAYOUT_STACKED if args.layout == "stacked" else P.LAYOUT_PAPER)
     solver.set_option(P.OPT_SPECTRAL_BOUNDARY, P.SPECTRAL_OPEN if args.spectral == "open" else P.SPECTRAL_PERIODIC)
     solver.set_option(P.OPT_REGULARIZER, {"s3ttv": P.REG_S3TTV, "stv": P.REG_STV, "sstv": P.REG_SSTV}[args.reg])
+    if args.autotune:
+        solver.set_option(P.OPT_AUTOTUNE, 1)
     vd = torch.from_numpy(v).to(f"cuda:{dev}")
     torch.cuda.synchronize()
 
     # ---- device-resident timing ----
     solver.setup(vd, eps, alpha, beta, spec.k)
     solver.set_option(P.OPT_CHECK_EVERY, max(args.steps, args.warmup, 1))
-    solver.iterate(args.warmup)
+    solver.iterate(max(args.warmup, 12) if args.autotune else args.warmup)  # the tuner needs 2 + 2 x forms passes
+    tuned = solver.tuned_form() if args.autotune else None
     solver.set_option(P.OPT_PROFILE, 1)
     launches0 = solver.launch_count()
     sampler = ClockSampler(nvsmi_id(dev)).start()
@@ -376,6 +379,7 @@ def run_ours(args, spec):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "N1": spec.N1, "N2": spec.N2, "N3": spec.N3, "k": spec.k,
                        "policy": args.policy, "layout": args.layout, "spectral": args.spectral, "reg": args.reg,
+                       "autotuned_form": ({"tensor_cores": tuned[0], "ctas_per_sm": tuned[1]} if tuned else None),
                        "parallelism": f"replicas{world}",
                        "block_dual_products": ("tensor cores, each FP32 operand split into two TF32 parts"
                                                if args.tensor_cores else "CUDA cores, FP32 FMA"),
@@ -693,6 +697,8 @@ def main(argv=None):
                     help="spectral difference: periodic (the paper) or open (no wrap-around)")
     ap.add_argument("--reg", choices=("s3ttv", "stv", "sstv"), default="s3ttv",
                     help="regularisation function: S3TTV (the paper) or a comparison one run by the same P-PDS")
+    ap.add_argument("--autotune", action="store_true",
+                    help="let the library time the block-dual forms on the warm-up passes and keep the fastest")
     ap.add_argument("--no-tol-run", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

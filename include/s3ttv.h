@@ -98,8 +98,16 @@ enum {
                                       S3TTV_LAYOUT_STACKED (below)                        */
   S3TTV_OPT_SPECTRAL_BOUNDARY = 9, /* D_s: S3TTV_SPECTRAL_PERIODIC (default, Sec. II-A)
                                       or S3TTV_SPECTRAL_OPEN (below)                      */
-  S3TTV_OPT_REGULARIZER = 10       /* the regularisation function of the problem:
+  S3TTV_OPT_REGULARIZER = 10,      /* the regularisation function of the problem:
                                       S3TTV_REG_S3TTV (default) or a comparison one (below) */
+  S3TTV_OPT_AUTOTUNE = 11          /* 1: the first s3ttv_iterate (or s3ttv_solve) of a
+                                      problem shape with k <= 5 runs two passes, then one
+                                      pass of every compiled block-dual form that fits
+                                      (tensor or CUDA cores x CTAs per SM), twice each,
+                                      timed with CUDA events, and keeps the fastest for
+                                      the context (these are passes of the solve; the
+                                      forms agree to FP32 rounding).  0 (default): the
+                                      occupancy rule and S3TTV_OPT_TENSOR_CORES choose */
 };
 /* Regularisers (option S3TTV_OPT_REGULARIZER).  Sec. IV runs its P-PDS-solvable
  * comparison methods by replacing S3TTV in Prob. (S3TTV_denoising) and solving
@@ -274,6 +282,11 @@ int s3ttv_l1_ball(s3ttv_ctx *ctx, const float *x, float *out, long long n,
  * Uses the context's workspace (replaces any problem set up before). */
 int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, float *Zh,
                      int N1, int N2, int N3, int k, float gamma_Y, s3ttv_info *info);
+
+/* The block-dual form S3TTV_OPT_AUTOTUNE chose: *tensor_cores 1 or 0 and
+ * *ctas_per_sm (4 or 5), or *tensor_cores = -1 and *ctas_per_sm = 0 when none
+ * has been chosen.  Host pointers, required. */
+int s3ttv_tuned_form(const s3ttv_ctx *ctx, int *tensor_cores, int *ctas_per_sm);
 
 /* Objective value S3TTV(u) = sum_l || P_l D D_s u ||_* of Prob.
  * (S3TTV_denoising) (eq. rewrite_Lu): the sum of the nuclear norms of the

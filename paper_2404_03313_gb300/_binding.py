@@ -24,6 +24,7 @@ OPT_LAYOUT, OPT_SPECTRAL_BOUNDARY = 8, 9
 LAYOUT_PAPER, LAYOUT_STACKED = 0, 1
 SPECTRAL_PERIODIC, SPECTRAL_OPEN = 0, 1
 OPT_REGULARIZER = 10
+OPT_AUTOTUNE = 11
 REG_S3TTV, REG_STV, REG_SSTV = 0, 1, 2
 KERNEL_CLASSES = ("primal", "l1_search", "block_dual", "dual", "finalize")
 STATE = {"u": 0, "s": 1, "t": 2, "y2": 3, "y3": 4, "Y": 5}
@@ -72,6 +73,7 @@ SIGNATURES = {
     "s3ttv_radii": (_c_int, [_c_ll, _c_d, _c_d, _c_d, _c_d, _P(_c_d), _P(_c_d), _P(_c_d)]),
     "s3ttv_step_sizes": (_c_int, [_c_int, _c_int, _c_int, _c_int, _P(_c_d)]),
     "s3ttv_objective": (_c_int, [_vp, _vp, _c_int, _c_int, _c_int, _c_int, _P(_c_d)]),
+    "s3ttv_tuned_form": (_c_int, [_vp, _P(_c_int), _P(_c_int)]),
     "s3ttv_quality": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _c_int, _P(_c_d), _P(_c_d), _P(_c_d), _vp]),
     "s3ttv_net_param_count": (_c_ll, []),
     "s3ttv_net_create": (_c_int, [_P(_vp), _c_int, _vp]),
@@ -356,6 +358,12 @@ class Solver:
         self._check(self._lib.s3ttv_l1_ball(self._h, _ptr(x, n, "x"), _ptr(out, n, "out"), n, float(radius),
                                             ctypes.byref(tau)), "s3ttv_l1_ball")
         return out, tau.value
+
+    def tuned_form(self):
+        """(tensor_cores, ctas_per_sm) the autotuner chose, or (-1, 0)."""
+        tc, cp = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.s3ttv_tuned_form(self._h, ctypes.byref(tc), ctypes.byref(cp)), "s3ttv_tuned_form")
+        return tc.value, cp.value
 
     def objective(self, u, k):
         """S3TTV(u), the sum of the nuclear norms of the structure tensors of all blocks."""

@@ -28,6 +28,9 @@ struct s3ttv_ctx {
   int layout = S3TTV_LAYOUT_PAPER;  // block matrices: paper k^2 x 2N3 or stacked 2k^2 x N3
   int open_s = 0;                   // 1: D_s stops at the last band (no wrap-around)
   int reg = S3TTV_REG_S3TTV;        // regularisation function (S3TTV, STV or SSTV)
+  int autotune = 0;                 // 1: time the block-dual forms on the first passes, keep the fastest
+  int tuned_tc = -1, tuned_minb = 0;  // the chosen form (tc -1: none chosen yet)
+  int tuned_k = 0, tuned_n3p = 0;     // the problem shape it was chosen for
   // problem
   bool ready = false;
   Dims dm{};
@@ -248,6 +251,33 @@ struct BdShape {
   bool large = false;  // block_dual_large.cu (k > 5)
 };
 
+// The launch shape of one block-dual form of the k <= 5 kernel: tensor cores
+// (tc) or CUDA cores, compiled for minb CTAs per SM.  Fails (S3TTV_EUNSUPPORTED)
+// when that form is not compiled or does not fit.
+int block_dual_variant_shape(s3ttv_ctx *ctx, const Dims &dm, int k, int tc, int minb, BdShape *sh) {
+  sh->large = false;
+  sh->v.k = k;
+  sh->v.tc = tc;
+  sh->v.minb = minb;
+  if (!block_dual_has(sh->v)) return fail(ctx, S3TTV_EUNSUPPORTED, "form tc=%d minb=%d not compiled", tc, minb);
+  sh->rs = block_dual_row_stride(dm.N3p);
+  sh->smem = block_dual_smem_bytes(sh->v, dm.N3p);
+  int dev_max = 0;
+  cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+  if (sh->smem == 0 || sh->smem > (size_t)dev_max) return fail(ctx, S3TTV_EUNSUPPORTED, "form does not fit");
+  cudaError_t e = block_dual_prepare(sh->v, sh->smem);
+  if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+  int per_sm = 0;
+  e = block_dual_occupancy(sh->v, sh->smem, &per_sm);
+  if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+  if (per_sm < 1) return fail(ctx, S3TTV_EUNSUPPORTED, "form does not fit on an SM");
+  long long g = (long long)ctx->num_sms * per_sm;
+  const long long groups = (dm.P + block_dual_group() - 1) / block_dual_group();
+  if (g > groups) g = groups;
+  sh->grid = (int)g;
+  return S3TTV_OK;
+}
+
 int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, BdShape *sh) {
   if (dm.P > 2147483647LL)  // the kernels index pixels with 32-bit integers
     return fail(ctx, S3TTV_EUNSUPPORTED, "N1 * N2 = %lld pixels: this build supports fewer than 2^31", dm.P);
@@ -285,6 +315,10 @@ int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, BdShape *sh) {
   if (sh->smem == 0 || sh->smem > (size_t)dev_max)
     return fail(ctx, S3TTV_EUNSUPPORTED, "a %dx%dx%d block needs %zu bytes of shared memory (device limit %d)", k, k,
                 dm.N3, sh->smem, dev_max);
+  if (ctx->tuned_tc >= 0 && ctx->tuned_k == k && ctx->tuned_n3p == dm.N3p) {
+    // the autotuned form (block_dual_variant_shape checked it when it was chosen)
+    return block_dual_variant_shape(ctx, dm, k, ctx->tuned_tc, ctx->tuned_minb, sh);
+  }
   int per_sm = 0;
   for (int minb = 5; minb >= 4; --minb) {
     sh->v.minb = minb;
@@ -673,6 +707,7 @@ int s3ttv_set_option(s3ttv_ctx *ctx, int key, double value) {
       ctx->jacobi_tol = (float)value;
       return S3TTV_OK;
     case S3TTV_OPT_TENSOR_CORES:
+      ctx->tuned_tc = -1;
       if (value != 0 && value != 1) return fail(ctx, S3TTV_EINVAL, "tensor_cores must be 0 or 1");
       ctx->tensor_cores = (int)value;
       return S3TTV_OK;
@@ -698,6 +733,11 @@ int s3ttv_set_option(s3ttv_ctx *ctx, int key, double value) {
         ctx->ready = false;
         ctx->warm_valid = false;
       }
+      return S3TTV_OK;
+    case S3TTV_OPT_AUTOTUNE:
+      if (value != 0 && value != 1) return fail(ctx, S3TTV_EINVAL, "autotune must be 0 or 1");
+      ctx->autotune = (int)value;
+      ctx->tuned_tc = -1;  // choose again on the next passes
       return S3TTV_OK;
     case S3TTV_OPT_REGULARIZER:
       if (value != S3TTV_REG_S3TTV && value != S3TTV_REG_STV && value != S3TTV_REG_SSTV)
@@ -795,6 +835,49 @@ int s3ttv_iterate(s3ttv_ctx *ctx, int n, float tol, s3ttv_info *info) {
   CU(cudaGetLastError());
   ctx->launches += 1;
   int enq = 0, par = par0;
+  if (ctx->autotune && ctx->reg != S3TTV_REG_SSTV && !bd.large &&
+      !(ctx->tuned_tc >= 0 && ctx->tuned_k == ctx->k && ctx->tuned_n3p == ctx->dm.N3p)) {
+    // Autotuning of the block-dual form: after two passes (the cold eigen-
+    // solves), time one pass of every compiled form that fits, twice each, with
+    // CUDA events, and keep the fastest.  Every timed pass is a pass of the solve.
+    struct Cand { int tc, minb; BdShape sh; float ms = 1e30f; };
+    std::vector<Cand> cands;
+    for (int tc = 1; tc >= 0; --tc)
+      for (int minb = 5; minb >= 4; --minb) {
+        Cand c;
+        c.tc = tc;
+        c.minb = minb;
+        if (block_dual_variant_shape(ctx, ctx->dm, ctx->k, tc, minb, &c.sh) == S3TTV_OK) cands.push_back(c);
+      }
+    ctx->err[0] = 0;
+    const int need = 2 + 2 * (int)cands.size();
+    if (cands.size() > 1 && n >= need) {
+      for (int w = 0; w < 2; ++w, ++enq, par ^= 1)
+        if ((rc = enqueue_pass(ctx, par, grid_e, cands[0].sh, nullptr))) return rc;
+      if ((rc = ensure_events(ctx, 1))) return rc;
+      for (int rep = 0; rep < 2; ++rep)
+        for (Cand &c : cands) {
+          CU(cudaEventRecord(ctx->ev[0], ctx->stream));
+          if ((rc = enqueue_pass(ctx, par, grid_e, c.sh, nullptr))) return rc;
+          CU(cudaEventRecord(ctx->ev[1], ctx->stream));
+          CU(cudaEventSynchronize(ctx->ev[1]));
+          float ms = 0.f;
+          CU(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
+          if (ms < c.ms) c.ms = ms;
+          ++enq;
+          par ^= 1;
+        }
+      const Cand *best = &cands[0];
+      for (const Cand &c : cands)
+        if (c.ms < best->ms) best = &c;
+      ctx->tuned_tc = best->tc;
+      ctx->tuned_minb = best->minb;
+      ctx->tuned_k = ctx->k;
+      ctx->tuned_n3p = ctx->dm.N3p;
+      ctx->tensor_cores = best->tc;
+      bd = best->sh;
+    }
+  }
   while (enq < n) {
     const int chunk = n - enq < ctx->check_every ? n - enq : ctx->check_every;
     if (ctx->profile && (rc = ensure_events(ctx, chunk))) return rc;
@@ -1213,6 +1296,13 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
     info->jacobi_nonconverged = (int)hs.jacobi_fail;
     info->jacobi_sweeps = (double)hs.jacobi_sweeps / (double)dm.P;
   }
+  return S3TTV_OK;
+}
+
+int s3ttv_tuned_form(const s3ttv_ctx *ctx, int *tensor_cores, int *ctas_per_sm) {
+  if (!ctx || !tensor_cores || !ctas_per_sm) return S3TTV_EINVAL;
+  *tensor_cores = ctx->tuned_tc;
+  *ctas_per_sm = ctx->tuned_tc >= 0 ? ctx->tuned_minb : 0;
   return S3TTV_OK;
 }
 

@@ -72,3 +72,23 @@ def test_save_and_resume_continue_the_iteration(P, tmp_path):
         ref = straight[n].astype(np.float64)
         err = np.linalg.norm(resumed[n] - ref) / max(np.linalg.norm(ref), 1e-30)
         assert err <= 1e-5, (n, err)
+
+
+def test_autotuner_picks_a_form_and_keeps_the_results(P):
+    """S3TTV_OPT_AUTOTUNE: the first passes time every block-dual form and keep
+    the fastest; the solve is the same solve (the forms agree to rounding)."""
+    spec = WORKLOADS["parity_32x32x16_k3"]
+    clean, v = make_cube(spec)
+    eps, alpha, beta = O.radii(v.size, spec.sigma, spec.p_s, spec.p_t)
+    vd = torch.from_numpy(v).cuda()
+    with P.Solver(0) as a:
+        u_ref, _, _, _ = a.solve(vd, eps, alpha, beta, spec.k, max_iter=40, tol=0.0)
+        assert a.tuned_form() == (-1, 0)
+    with P.Solver(0) as b:
+        b.set_option(P.OPT_AUTOTUNE, 1)
+        u, _, _, info = b.solve(vd, eps, alpha, beta, spec.k, max_iter=40, tol=0.0)
+        tc, ctas = b.tuned_form()
+    assert info["iters"] == 40
+    assert tc in (0, 1) and ctas in (4, 5)
+    err = float((u - u_ref).norm() / u_ref.norm())
+    assert err <= 1e-5, err
