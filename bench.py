@@ -463,6 +463,22 @@ def run_batch(args):
         t_alone += a0.elapsed_time(a1)
         alone_u.append(u)
     agree = max(float((o[0] - a).norm() / a.norm()) for o, a in zip(out, alone_u))
+    # to the stop rule: every cube with its own stop rule (PC_EXACT step sizes,
+    # with which it fires; bounded so the run stays short), per-cube times
+    tol_run = None
+    if not args.no_tol_run:
+        solver.set_option(P.OPT_STEP_POLICY, P.STEP_PC_EXACT)
+        t0 = time.perf_counter()
+        res = solver.solve_batched(probs, max_iter=args.batch_max_iter, tol=args.batch_tol)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        secs = sorted(r[3]["seconds"] for r in res)
+        q = lambda f: secs[min(len(secs) - 1, int(round(f * (len(secs) - 1))))]
+        tol_run = {"policy": "pc_exact", "tol": args.batch_tol, "max_iter": args.batch_max_iter,
+                   "seconds": wall, "cubes_per_s": len(probs) / wall,
+                   "converged": sum(1 for r in res if r[3]["converged"]),
+                   "p50_s": q(0.5), "p99_s": q(0.99),
+                   "iters_p50": sorted(r[3]["iters"] for r in res)[len(res) // 2]}
     solver.close()
     value = world * args.steps / (ms / 1000.0)
     peak, peak_src = measured_peaks()
@@ -483,6 +499,7 @@ def run_batch(args):
                          "peak_source": peak_src, "algorithmic_bytes_per_step": pass_bytes},
             "cubes_alone_ms_per_step": t_alone / args.steps, "batching_gain": t_alone / ms,
             "max_rel_diff_batched_vs_alone": agree,
+            "to_tol": tol_run,
         }), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -699,6 +716,9 @@ def main(argv=None):
                     help="regularisation function: S3TTV (the paper) or a comparison one run by the same P-PDS")
     ap.add_argument("--autotune", action="store_true",
                     help="let the library time the block-dual forms on the warm-up passes and keep the fastest")
+    ap.add_argument("--batch-tol", type=float, default=1e-4,
+                    help="stop rule of the batched to-tolerance run (per cube)")
+    ap.add_argument("--batch-max-iter", type=int, default=600)
     ap.add_argument("--no-tol-run", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -240,7 +240,10 @@ typedef struct s3ttv_problem {
  * paper has no counterpart: it denoises one scene at a time.
  *
  * problems: n >= 1 descriptions; max_iter >= 1 and tol >= 0 as in s3ttv_solve.
- * infos: NULL or n reports; infos[i].status is problem i's result.
+ * infos: NULL or n reports; infos[i].status is problem i's result and
+ * infos[i].seconds the time from the call's start until problem i was seen
+ * stopped (the host reads the stop flags after each chunk, so to within one
+ * chunk of passes; the whole call for a problem that ran to max_iter).
  * Returns S3TTV_OK when every problem's stop rule fired, S3TTV_MAXITER when
  * some problem reached max_iter first (all results valid), or the first
  * negative status (s3ttv_last_error names the problem); a problem whose setup

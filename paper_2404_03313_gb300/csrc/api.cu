@@ -1123,6 +1123,7 @@ int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, in
     for (int i = 0; i < n; ++i) ctx->members[i]->launches = launches0[i];  // recorded, not run
   }
   std::vector<Scalars> hs(n);
+  std::vector<double> finish(n, -1.0);  // host time at which each problem was seen stopped
   int enq = 0, rc = S3TTV_OK;
   while (enq < max_iter) {
     const int step = max_iter - enq >= chunk ? chunk : max_iter - enq;
@@ -1150,7 +1151,11 @@ int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, in
       break;
     }
     bool all_done = true;
-    for (int i = 0; i < n; ++i) all_done = all_done && hs[i].done;
+    const double now = now_s() - t0;
+    for (int i = 0; i < n; ++i) {
+      all_done = all_done && hs[i].done;
+      if (hs[i].done && finish[i] < 0.0) finish[i] = now;
+    }
     if (all_done) break;
   }
   if (exec) cudaGraphExecDestroy(exec);
@@ -1192,8 +1197,8 @@ int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, in
     if (e != cudaSuccess && result >= 0) result = fail(ctx, S3TTV_ECUDA, "problem %d: %s", i, cudaGetErrorString(e));
   }
   const double secs = now_s() - t0;
-  if (infos)
-    for (int i = 0; i < n; ++i) infos[i].seconds = secs;
+  if (infos)  // per problem: until its stop rule was seen (to a chunk of passes), else the whole call
+    for (int i = 0; i < n; ++i) infos[i].seconds = finish[i] >= 0.0 ? finish[i] : secs;
   return result;
 }
 
