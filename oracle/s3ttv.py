@@ -31,7 +31,7 @@ import math
 import numpy as np
 
 __all__ = [
-    "AXIS_V", "AXIS_H", "AXIS_S", "diff", "diff_adj", "spectral_diffs", "spectral_diff_adjoint", "structure_tensors",
+    "AXIS_V", "AXIS_H", "AXIS_S", "HSSTV_OMEGA", "diff", "diff_adj", "spectral_diffs", "spectral_diff_adjoint", "structure_tensors",
     "structure_tensors_adjoint", "structure_tensor_block", "linear_op_adjoint_u",
     "linear_op_adjoint_u_at",
     "prox_nuclear", "block_dual_update", "proj_box", "proj_l2_ball",
@@ -41,6 +41,9 @@ __all__ = [
 ]
 
 AXIS_V, AXIS_H, AXIS_S = 0, 1, 2
+# HSSTV's weight of the first-order spatial differences (a reading: the paper
+# names HSSTV [Takeyama et al. 2020] without its parameters)
+HSSTV_OMEGA = 0.05
 
 
 # ----------------------------------------------------------------------------
@@ -263,6 +266,11 @@ def step_sizes(N1: int, N2: int, k: int, policy: str = "paper", reg: str = "s3tt
         return {"u": 1.0 / (4.0 * k * k + 1.0), "s": 1.0, "t": 1.0 / 3.0, "Y": 0.5, "y2": 0.5, "y3": 1.0 / 3.0}
     if reg == "sstv":
         return {"u": 1.0 / 9.0, "s": 1.0, "t": 1.0 / 3.0, "Y": 0.25, "y2": 0.5, "y3": 1.0 / 3.0}
+    if reg in ("hsstv1", "hsstv2"):
+        # column abs-sum 8 + 4 omega (+1 for y3); the dual rows' sums are 4 and
+        # 2 omega, and one gamma_Y = 1/4 serves all four parts (omega <= 2)
+        return {"u": 1.0 / (9.0 + 4.0 * HSSTV_OMEGA), "s": 1.0, "t": 1.0 / 3.0, "Y": 0.25, "y2": 0.5,
+                "y3": 1.0 / 3.0}
     if reg != "s3ttv":
         raise ValueError(reg)
     if policy == "paper":
@@ -324,6 +332,8 @@ def assemble_operator(N1: int, N2: int, N3: int, k: int, reg: str = "s3ttv"):
     AY = sp.csr_matrix((vals, (rows, cols)), shape=(L * k * k * 2 * N3, N))
     if reg == "sstv":  # no blocks: the dual is (D_v D_s u, D_h D_s u) itself
         AY = sp.vstack([DvDs, DhDs]).tocsr()
+    if reg in ("hsstv1", "hsstv2"):
+        AY = sp.vstack([DvDs, DhDs, HSSTV_OMEGA * Dv, HSSTV_OMEGA * Dh]).tocsr()
     I = sp.identity(N, format="csr")
     Z = sp.csr_matrix((N, N))
     return {
@@ -367,6 +377,8 @@ def init_state(v: np.ndarray, k: int, layout: str = "paper", periodic_s: bool = 
     z = np.zeros_like(v)
     if reg == "sstv":
         Y = np.zeros((2,) + v.shape)
+    elif reg in ("hsstv1", "hsstv2"):
+        Y = np.zeros((4,) + v.shape)
     else:
         Y = np.zeros_like(structure_tensors(v, k, layout, periodic_s, reg != "stv"))
     return {"u": v.copy(), "s": z.copy(), "t": z.copy(), "y2": z.copy(), "y3": z.copy(), "Y": Y}
@@ -391,6 +403,9 @@ def iterate(state: dict, v: np.ndarray, k: int, eps: float, alpha: float, beta: 
     # Step 2: u update, box projection.
     if reg == "sstv":
         lin = spectral_diff_adjoint(diff_adj(Y[0], AXIS_V) + diff_adj(Y[1], AXIS_H), True)
+    elif reg in ("hsstv1", "hsstv2"):
+        lin = (spectral_diff_adjoint(diff_adj(Y[0], AXIS_V) + diff_adj(Y[1], AXIS_H), True)
+               + HSSTV_OMEGA * (diff_adj(Y[2], AXIS_V) + diff_adj(Y[3], AXIS_H)))
     else:
         lin = linear_op_adjoint_u(Y, k, u.shape, layout, periodic_s, reg != "stv")
     u_new = proj_box(u - g["u"] * (lin + y3), mu_min, mu_max)
@@ -405,6 +420,16 @@ def iterate(state: dict, v: np.ndarray, k: int, eps: float, alpha: float, beta: 
         Yp = Y + g["Y"] * np.stack(spectral_diffs(ub, True))
         w = Yp / g["Y"]  # Y+ = Y' - gamma prox_{||.||_1 / gamma}(Y' / gamma)
         Y_new = Yp - g["Y"] * np.sign(w) * np.maximum(np.abs(w) - 1.0 / g["Y"], 0.0)
+    elif reg in ("hsstv1", "hsstv2"):
+        A = np.stack(spectral_diffs(ub, True) + (HSSTV_OMEGA * diff(ub, AXIS_V), HSSTV_OMEGA * diff(ub, AXIS_H)))
+        Yp = Y + g["Y"] * A
+        w = Yp / g["Y"]  # Y+ = Y' - gamma prox_{||.|| / gamma}(Y' / gamma)
+        if reg == "hsstv1":  # l1: soft thresholding entry by entry
+            prox = np.sign(w) * np.maximum(np.abs(w) - 1.0 / g["Y"], 0.0)
+        else:  # l1,2 over the four differences of each voxel: group soft thresholding
+            nrm = np.sqrt((w * w).sum(axis=0, keepdims=True))
+            prox = w * np.maximum(1.0 - (1.0 / g["Y"]) / np.maximum(nrm, 1e-300), 0.0)
+        Y_new = Yp - g["Y"] * prox
     else:
         Y_new = block_dual_update(Y, structure_tensors(ub, k, layout, periodic_s, reg != "stv"), g["Y"])
     # Step 12: prox of the conjugate of iota_{0} is the identity (eq. prox_zeroset).
@@ -467,6 +492,9 @@ def objective(u: np.ndarray, k: int, layout: str = "paper", periodic_s: bool = T
     if reg == "sstv":
         Fv, Fh = spectral_diffs(u, True)
         return float(np.abs(Fv).sum() + np.abs(Fh).sum())
+    if reg in ("hsstv1", "hsstv2"):
+        A = np.stack(spectral_diffs(u, True) + (HSSTV_OMEGA * diff(u, AXIS_V), HSSTV_OMEGA * diff(u, AXIS_H)))
+        return float(np.abs(A).sum() if reg == "hsstv1" else np.sqrt((A * A).sum(axis=0)).sum())
     X = structure_tensors(u, k, layout, periodic_s, reg != "stv")
     return float(np.linalg.svd(X, compute_uv=False).sum())
 

@@ -628,3 +628,54 @@ def test_stv_tensors_adjoint_and_k1_closed_form():
     assert O.objective(flat, 2, reg="stv") == 0.0 and O.objective(flat, 2, reg="sstv") == 0.0
     Fv, Fh = O.spectral_diffs(u, True)
     assert O.objective(u, 2, reg="sstv") == pytest.approx(np.abs(Fv).sum() + np.abs(Fh).sum(), rel=1e-14)
+
+
+@pytest.mark.parametrize("reg", ["hsstv1", "hsstv2"])
+def test_hsstv_step_sizes_and_dual_prox(reg):
+    """Lemma 1 on the assembled operator: gamma_u is the exact column bound; the
+    dual rows' bound is 4 for the second-order and 2 omega for the first-order
+    parts, and the common gamma_Y = 1/4 respects both.  The conjugate prox is
+    the projection onto the unit l_inf ball (HSSTV1) or onto each voxel's unit
+    l2 ball of its four differences (HSSTV2)."""
+    got = O.lemma1_step_sizes(O.assemble_operator(4, 5, 3, 1, reg))
+    want = O.step_sizes(4, 5, 1, "paper", reg)
+    assert got["u"][0] == pytest.approx(want["u"], rel=1e-12) and got["u"][1]
+    assert want["Y"] <= got["Y"][0] + 1e-15  # the smallest row bound is 1/4
+    r = np.random.default_rng(51)
+    v = r.uniform(0, 1, (5, 6, 4))
+    st = O.init_state(v, 1, reg=reg)
+    st["Y"] = 2.0 * r.standard_normal(st["Y"].shape)
+    new, _ = O.iterate(st, v, 1, 1.0, 5.0, 3.0, 0.0, 1.0, want, reg=reg)
+    ub = 2.0 * new["u"] - st["u"]
+    w = O.HSSTV_OMEGA
+    A = np.stack(O.spectral_diffs(ub, True) + (w * O.diff(ub, O.AXIS_V), w * O.diff(ub, O.AXIS_H)))
+    Yp = st["Y"] + want["Y"] * A
+    if reg == "hsstv1":
+        expect = np.clip(Yp, -1.0, 1.0)
+    else:
+        expect = Yp / np.maximum(1.0, np.sqrt((Yp * Yp).sum(axis=0, keepdims=True)))
+    np.testing.assert_allclose(new["Y"], expect, atol=1e-13)
+
+
+def test_hsstv_objectives_and_adjoint():
+    r = np.random.default_rng(52)
+    u = r.standard_normal((4, 5, 6))
+    w = O.HSSTV_OMEGA
+    F2v, F2h = O.spectral_diffs(u, True)
+    F1v, F1h = O.diff(u, O.AXIS_V), O.diff(u, O.AXIS_H)
+    l1 = np.abs(F2v).sum() + np.abs(F2h).sum() + w * (np.abs(F1v).sum() + np.abs(F1h).sum())
+    l12 = np.sqrt(F2v ** 2 + F2h ** 2 + (w * F1v) ** 2 + (w * F1h) ** 2).sum()
+    assert O.objective(u, 1, reg="hsstv1") == pytest.approx(l1, rel=1e-13)
+    assert O.objective(u, 1, reg="hsstv2") == pytest.approx(l12, rel=1e-13)
+    # the primal term is the adjoint of the stacked operator
+    Y = r.standard_normal((4,) + u.shape)
+    st = {"u": u, "s": np.zeros_like(u), "t": np.zeros_like(u), "y2": np.zeros_like(u), "y3": np.zeros_like(u),
+          "Y": Y}
+    g = dict(O.step_sizes(4, 5, 1, "paper", "hsstv1"))
+    # one pass with a tiny gamma_u and a wide box: u+ - u = -gamma_u (A^T Y)
+    g["u"] = 1e-6
+    new, _ = O.iterate(st, np.zeros_like(u), 1, 1e9, 1e9, 1e9, -1e9, 1e9, g, reg="hsstv1")
+    ATY = -(new["u"] - u) / g["u"]
+    A = np.stack((F2v, F2h, w * F1v, w * F1h))
+    lhs, rhs = float((A * Y).sum()), float((u * ATY).sum())
+    assert abs(lhs - rhs) <= 1e-6 * max(1.0, abs(lhs))
