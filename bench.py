@@ -269,7 +269,8 @@ def run_ours(args, spec):
     solver.set_option(P.OPT_TENSOR_CORES, args.tensor_cores)
     solver.set_option(P.OPT_LAYOUT, P.LAYOUT_STACKED if args.layout == "stacked" else P.LAYOUT_PAPER)
     solver.set_option(P.OPT_SPECTRAL_BOUNDARY, P.SPECTRAL_OPEN if args.spectral == "open" else P.SPECTRAL_PERIODIC)
-    solver.set_option(P.OPT_REGULARIZER, {"s3ttv": P.REG_S3TTV, "stv": P.REG_STV, "sstv": P.REG_SSTV}[args.reg])
+    solver.set_option(P.OPT_REGULARIZER, {"s3ttv": P.REG_S3TTV, "stv": P.REG_STV, "sstv": P.REG_SSTV,
+                                          "hsstv1": P.REG_HSSTV1, "hsstv2": P.REG_HSSTV2}[args.reg])
     if args.autotune:
         solver.set_option(P.OPT_AUTOTUNE, 1)
     vd = torch.from_numpy(v).to(f"cuda:{dev}")
@@ -309,13 +310,14 @@ def run_ours(args, spec):
     alg_bytes = bytes_per_voxel * N
     peak, peak_src = measured_peaks()
     stacked = args.layout == "stacked"
-    if args.reg == "sstv":
-        # SSTV: the dual step is one elementwise kernel (the block_dual class):
-        # ubar read, Y read and written, Z written: 4 + 8 + 8 + 8 B per voxel
-        sb = 28 * N
+    if args.reg in ("sstv", "hsstv1", "hsstv2"):
+        # SSTV / HSSTV: the dual step is one elementwise kernel (the block_dual
+        # class): ubar read, Y (2 or 4 cubes) read and written, Z written
+        sb = (28 if args.reg == "sstv" else 44) * N
         achieved = sb / bd_avg_s / 1e9 if bd_avg_s > 0 else 0.0
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": "sstv_dual_kernel", "peak_source": peak_src,
+                    "traffic": None, "kernel": "sstv_dual_kernel" if args.reg == "sstv" else "hsstv_dual_kernel",
+                    "peak_source": peak_src,
                     "algorithmic_bytes_per_launch": sb, "avg_launch_ms": bd_avg_s * 1000.0}
     elif spec.k <= 5 and not stacked:
         achieved = alg_bytes / bd_avg_s / 1e9 if bd_avg_s > 0 else 0.0
@@ -712,7 +714,7 @@ def main(argv=None):
                     help="block matrices: the paper's k^2 x 2N3 or the stacked 2k^2 x N3")
     ap.add_argument("--spectral", choices=("periodic", "open"), default="periodic",
                     help="spectral difference: periodic (the paper) or open (no wrap-around)")
-    ap.add_argument("--reg", choices=("s3ttv", "stv", "sstv"), default="s3ttv",
+    ap.add_argument("--reg", choices=("s3ttv", "stv", "sstv", "hsstv1", "hsstv2"), default="s3ttv",
                     help="regularisation function: S3TTV (the paper) or a comparison one run by the same P-PDS")
     ap.add_argument("--autotune", action="store_true",
                     help="let the library time the block-dual forms on the warm-up passes and keep the fastest")

@@ -28,6 +28,7 @@ struct s3ttv_ctx {
   int layout = S3TTV_LAYOUT_PAPER;  // block matrices: paper k^2 x 2N3 or stacked 2k^2 x N3
   int open_s = 0;                   // 1: D_s stops at the last band (no wrap-around)
   int reg = S3TTV_REG_S3TTV;        // regularisation function (S3TTV, STV or SSTV)
+  float hsstv_omega = 0.05f;        // HSSTV's weight of the first-order differences
   int autotune = 0;                 // 1: time the block-dual forms on the first passes, keep the fastest
   int tuned_tc = -1, tuned_minb = 0;  // the chosen form (tc -1: none chosen yet)
   int tuned_k = 0, tuned_n3p = 0;     // the problem shape it was chosen for
@@ -110,6 +111,8 @@ bool is_device_ptr(const void *p) {
 }
 
 int round4(int x) { return (x + 3) & ~3; }
+
+bool is_hsstv(const s3ttv_ctx *c) { return c->reg == S3TTV_REG_HSSTV1 || c->reg == S3TTV_REG_HSSTV2; }
 
 int elementwise_grid(const s3ttv_ctx *c, long long n) {
   long long g = (n + 255) / 256;
@@ -200,7 +203,8 @@ int ensure_macc(s3ttv_ctx *ctx, size_t n) {
 
 int ensure_problem_buffers(s3ttv_ctx *ctx, const Dims &dm, int k) {
   const size_t np = (size_t)dm.Np;
-  const size_t ny = (size_t)dm.P * k * k * 2 * dm.N3p;
+  size_t ny = (size_t)dm.P * k * k * 2 * dm.N3p;
+  if (ny < 4 * np) ny = 4 * np;  // HSSTV keeps four dual cubes
   const long long ws = ctx->layout == S3TTV_LAYOUT_STACKED ? block_dual_large_w_stride(k, true) : block_dual_w_stride(k);
   const size_t nw = (size_t)dm.P * ws;
   ctx->w_stride = ws;
@@ -358,7 +362,7 @@ int check_problem(s3ttv_ctx *ctx, const float *v, int N1, int N2, int N3, float 
 // policy; STV and SSTV: the exact Lemma 1 values of their operators (column
 // abs-sums 4k^2 and 8 of P_l D and D D_s, row abs-sums 2 and 4, plus the
 // identity of y3).
-void step_sizes(int N1, int N2, int k, int policy, double g[6], int reg = S3TTV_REG_S3TTV) {
+void step_sizes(int N1, int N2, int k, int policy, double g[6], int reg = S3TTV_REG_S3TTV, double omega = 0.05) {
   const double L = (double)N1 * (double)N2;
   g[0] = policy == S3TTV_STEP_PC_EXACT ? 1.0 / (8.0 * k * k + 1.0) : 1.0 / (8.0 * L + 1.0);
   g[1] = 1.0;
@@ -371,6 +375,8 @@ void step_sizes(int N1, int N2, int k, int policy, double g[6], int reg = S3TTV_
     g[3] = 0.5;
   } else if (reg == S3TTV_REG_SSTV) {
     g[0] = 1.0 / 9.0;
+  } else if (reg == S3TTV_REG_HSSTV1 || reg == S3TTV_REG_HSSTV2) {
+    g[0] = 1.0 / (9.0 + 4.0 * omega);  // gamma_Y = 1/4 serves all four dual parts (omega <= 2)
   }
 }
 
@@ -403,9 +409,10 @@ int store_cube(s3ttv_ctx *ctx, const float *src, float *dst, const double *scale
 
 int load_Y(s3ttv_ctx *ctx, const float *src) {
   const Dims &dm = ctx->dm;
-  if (ctx->reg == S3TTV_REG_SSTV) {  // (Yv, Yh): two cubes
-    int rc = load_cube(ctx, src, ctx->Y, 1.f);
-    if (!rc) rc = load_cube(ctx, src + dm.P * dm.N3, ctx->Y + dm.Np, 1.f);
+  const int ncubes = ctx->reg == S3TTV_REG_SSTV ? 2 : (is_hsstv(ctx) ? 4 : 0);
+  if (ncubes) {  // SSTV (Yv, Yh) / HSSTV (four parts): cubes
+    int rc = S3TTV_OK;
+    for (int m = 0; m < ncubes && !rc; ++m) rc = load_cube(ctx, src + m * dm.P * dm.N3, ctx->Y + m * dm.Np, 1.f);
     return rc;
   }
   const size_t ne = (size_t)dm.P * ctx->k * ctx->k * 2 * dm.N3;
@@ -422,9 +429,10 @@ int load_Y(s3ttv_ctx *ctx, const float *src) {
 
 int store_Y(s3ttv_ctx *ctx, float *dst) {
   const Dims &dm = ctx->dm;
-  if (ctx->reg == S3TTV_REG_SSTV) {
-    int rc = store_cube(ctx, ctx->Y, dst, nullptr);
-    if (!rc) rc = store_cube(ctx, ctx->Y + dm.Np, dst + dm.P * dm.N3, nullptr);
+  const int ncubes = ctx->reg == S3TTV_REG_SSTV ? 2 : (is_hsstv(ctx) ? 4 : 0);
+  if (ncubes) {
+    int rc = S3TTV_OK;
+    for (int m = 0; m < ncubes && !rc; ++m) rc = store_cube(ctx, ctx->Y + m * dm.Np, dst + m * dm.P * dm.N3, nullptr);
     return rc;
   }
   const size_t ne = (size_t)dm.P * ctx->k * ctx->k * 2 * dm.N3;
@@ -481,6 +489,11 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   pa.hcnt = ctx->hcnt;
   pa.hsum = ctx->hsum;
   pa.no_ds = ctx->reg == S3TTV_REG_STV;
+  if (is_hsstv(ctx)) {
+    pa.Z1v = ctx->Y + 2 * dm.Np;
+    pa.Z1h = ctx->Y + 3 * dm.Np;
+    pa.w1 = ctx->hsstv_omega;
+  }
   CU(launch_primal(pa, grid_e, st));
   if (ev) CU(cudaEventRecord(ev[1], st));
 
@@ -502,6 +515,9 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   if (ctx->reg == S3TTV_REG_SSTV) {
     CU(launch_sstv_dual(ctx->ubar, ctx->Y, ctx->Y + dm.Np, ctx->Zv[par ^ 1], ctx->Zh[par ^ 1], dm,
                         (float)ctx->gam[3], grid_e, st));
+  } else if (is_hsstv(ctx)) {
+    CU(launch_hsstv_dual(ctx->ubar, ctx->Y, ctx->Zv[par ^ 1], ctx->Zh[par ^ 1], dm, (float)ctx->gam[3],
+                         ctx->hsstv_omega, ctx->reg == S3TTV_REG_HSSTV2, grid_e, st));
   } else {
   CU(launch_xfield(ctx->ubar, ctx->Fv, ctx->Fh, dm, grid_e, st, ctx->open_s, ctx->reg == S3TTV_REG_STV));
   BlockDualArgs ba;
@@ -692,7 +708,7 @@ int s3ttv_set_option(s3ttv_ctx *ctx, int key, double value) {
       if (value != S3TTV_STEP_PAPER && value != S3TTV_STEP_PC_EXACT)
         return fail(ctx, S3TTV_EINVAL, "unknown step policy %g", value);
       ctx->step_policy = (int)value;
-      if (ctx->ready) step_sizes(ctx->dm.N1, ctx->dm.N2, ctx->k, ctx->step_policy, ctx->gam, ctx->reg);
+      if (ctx->ready) step_sizes(ctx->dm.N1, ctx->dm.N2, ctx->k, ctx->step_policy, ctx->gam, ctx->reg, ctx->hsstv_omega);
       return S3TTV_OK;
     case S3TTV_OPT_CHECK_EVERY:
       if (!(value >= 1 && value <= 1e6)) return fail(ctx, S3TTV_EINVAL, "check_every must be in [1, 1e6]");
@@ -734,14 +750,20 @@ int s3ttv_set_option(s3ttv_ctx *ctx, int key, double value) {
         ctx->warm_valid = false;
       }
       return S3TTV_OK;
+    case S3TTV_OPT_HSSTV_OMEGA:
+      if (!(value > 0.0 && value <= 2.0)) return fail(ctx, S3TTV_EINVAL, "HSSTV omega must be in (0, 2]");
+      ctx->hsstv_omega = (float)value;
+      if (ctx->ready) step_sizes(ctx->dm.N1, ctx->dm.N2, ctx->k, ctx->step_policy, ctx->gam, ctx->reg, ctx->hsstv_omega);
+      return S3TTV_OK;
     case S3TTV_OPT_AUTOTUNE:
       if (value != 0 && value != 1) return fail(ctx, S3TTV_EINVAL, "autotune must be 0 or 1");
       ctx->autotune = (int)value;
       ctx->tuned_tc = -1;  // choose again on the next passes
       return S3TTV_OK;
     case S3TTV_OPT_REGULARIZER:
-      if (value != S3TTV_REG_S3TTV && value != S3TTV_REG_STV && value != S3TTV_REG_SSTV)
-        return fail(ctx, S3TTV_EINVAL, "regularizer must be S3TTV_REG_S3TTV, S3TTV_REG_STV or S3TTV_REG_SSTV");
+      if (!(value == S3TTV_REG_S3TTV || value == S3TTV_REG_STV || value == S3TTV_REG_SSTV ||
+            value == S3TTV_REG_HSSTV1 || value == S3TTV_REG_HSSTV2))
+        return fail(ctx, S3TTV_EINVAL, "unknown regularizer %g", value);
       if ((int)value != ctx->reg) {
         ctx->reg = (int)value;
         ctx->ready = false;  // the duals change meaning: set the problem up again
@@ -796,7 +818,7 @@ int s3ttv_setup(s3ttv_ctx *ctx, const float *v, int N1, int N2, int N3, float ep
   ctx->beta = beta;
   ctx->mu_min = mu_min;
   ctx->mu_max = mu_max;
-  step_sizes(N1, N2, k, ctx->step_policy, ctx->gam, ctx->reg);
+  step_sizes(N1, N2, k, ctx->step_policy, ctx->gam, ctx->reg, ctx->hsstv_omega);
   const size_t cb = sizeof(float) * dm.Np;
   if ((rc = load_cube(ctx, v, ctx->v, 1.f))) return rc;
   CU(cudaMemcpyAsync(ctx->u, ctx->v, cb, cudaMemcpyDeviceToDevice, ctx->stream));  // u0 = v
@@ -835,7 +857,7 @@ int s3ttv_iterate(s3ttv_ctx *ctx, int n, float tol, s3ttv_info *info) {
   CU(cudaGetLastError());
   ctx->launches += 1;
   int enq = 0, par = par0;
-  if (ctx->autotune && ctx->reg != S3TTV_REG_SSTV && !bd.large &&
+  if (ctx->autotune && ctx->reg != S3TTV_REG_SSTV && !is_hsstv(ctx) && !bd.large &&
       !(ctx->tuned_tc >= 0 && ctx->tuned_k == ctx->k && ctx->tuned_n3p == ctx->dm.N3p)) {
     // Autotuning of the block-dual form: after two passes (the cold eigen-
     // solves), time one pass of every compiled form that fits, twice each, with
@@ -957,7 +979,7 @@ int s3ttv_set_state(s3ttv_ctx *ctx, int which, const float *src) {
     case S3TTV_STATE_Y:
       ctx->warm_valid = false;
       rc = load_Y(ctx, src);
-      if (!rc && ctx->reg == S3TTV_REG_SSTV) {  // SSTV: Z = Y
+      if (!rc && (ctx->reg == S3TTV_REG_SSTV || is_hsstv(ctx))) {  // SSTV, HSSTV: Z = the second-order pair
         CU(cudaMemcpyAsync(ctx->Zv[ctx->parity], ctx->Y, sizeof(float) * ctx->dm.Np, cudaMemcpyDeviceToDevice,
                            ctx->stream));
         CU(cudaMemcpyAsync(ctx->Zh[ctx->parity], ctx->Y + ctx->dm.Np, sizeof(float) * ctx->dm.Np,
@@ -1083,6 +1105,7 @@ int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, in
     m->layout = ctx->layout;
     m->open_s = ctx->open_s;
     m->reg = ctx->reg;
+    m->hsstv_omega = ctx->hsstv_omega;
     m->profile = false;
     const s3ttv_problem &p = problems[i];
     int rc = s3ttv_setup(m, p.v, p.N1, p.N2, p.N3, p.eps, p.alpha, p.beta, p.mu_min, p.mu_max, p.k);
@@ -1256,7 +1279,8 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   if (!Y || !ubar || !Zv || !Zh) return fail(ctx, S3TTV_EINVAL, "Y, ubar, Zv and Zh are required");
   if (k < 1 || N1 < k || N2 < k || N3 < 1) return fail(ctx, S3TTV_EINVAL, "need N1, N2 >= k >= 1 and N3 >= 1");
   if (!(gamma_Y > 0.f) || !std::isfinite(gamma_Y)) return fail(ctx, S3TTV_EINVAL, "gamma_Y must be > 0");
-  if (ctx->reg == S3TTV_REG_SSTV) return fail(ctx, S3TTV_EUNSUPPORTED, "SSTV has no block duals");
+  if (ctx->reg == S3TTV_REG_SSTV || is_hsstv(ctx))
+    return fail(ctx, S3TTV_EUNSUPPORTED, "SSTV and HSSTV have no block duals");
   if (k > kMaxK) return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: this build supports k <= %d", k, kMaxK);
   DeviceGuard g(ctx->device);
   const Dims dm = make_dims(N1, N2, N3);
@@ -1336,6 +1360,9 @@ int s3ttv_objective(s3ttv_ctx *ctx, const float *u, int N1, int N2, int N3, int 
     return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d needs %zu bytes of shared memory", k, objective_smem_bytes(k, stacked));
   if (ctx->reg == S3TTV_REG_SSTV)
     CU(launch_sstv_l1(du, N1, N2, N3, ctx->macc, ctx->num_sms * 8, ctx->stream));
+  else if (is_hsstv(ctx))
+    CU(launch_hsstv_norm(du, N1, N2, N3, ctx->hsstv_omega, ctx->reg == S3TTV_REG_HSSTV2, ctx->macc, ctx->num_sms * 8,
+                         ctx->stream));
   else
     CU(launch_objective(du, N1, N2, N3, k, stacked, ctx->open_s, ctx->reg == S3TTV_REG_STV, ctx->macc, nonconv,
                         ctx->num_sms * 4, ctx->stream));

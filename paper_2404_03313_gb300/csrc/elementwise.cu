@@ -93,7 +93,9 @@ __global__ void __launch_bounds__(256) primal_kernel(PrimalArgs a) {
     for (int e = 0; e < 4; ++e) {
       if (b0 + e < dm.N3) {
         // (D_s^T w)[b] = w[b-1] - w[b]; STV's first-order term has no D_s
-        const float grad = a.no_ds ? w[e] : (e == 0 ? wbm : w[e - 1]) - w[e];
+        float grad = a.no_ds ? w[e] : (e == 0 ? wbm : w[e - 1]) - w[e];
+        if (a.Z1v)  // HSSTV: + omega D^T (Y1v, Y1h), first-order, no D_s
+          grad = fmaf(a.w1, (a.Z1v[pim + e] - a.Z1v[p0 + e]) + (a.Z1h[pjm + e] - a.Z1h[p0 + e]), grad);
         const float y3 = c3 * comp(d4, e);
         const float u = comp(u4, e);
         const float x = u - a.gu * (grad + y3);
@@ -400,6 +402,64 @@ __global__ void sstv_dual_kernel(const float *__restrict__ ubar, float *__restri
     st4(Zv + p0 + b0, ov);
     st4(Zh + p0 + b0, oh);
   }
+}
+
+// HSSTV's dual step: the four parts (D_v D_s ubar, D_h D_s ubar, omega D_v ubar,
+// omega D_h ubar) added to Y with gamma_Y, then the conjugate prox of the l1
+// norm (l12 = 0: clip every entry to [-1, 1]) or of the l1,2 norm over each
+// voxel's four entries (l12 = 1: scale the 4-vector into the unit l2 ball).
+// Y holds four internal cubes; the second-order pair is also written to Z.
+__global__ void hsstv_dual_kernel(const float *__restrict__ ubar, float *__restrict__ Y, float *__restrict__ Zv,
+                                  float *__restrict__ Zh, Dims dm, float gY, float omega, int l12) {
+  const int N3p = dm.N3p, C4 = N3p >> 2, N2 = dm.N2;
+  const int nch = (int)(dm.P * C4);
+  const size_t Np = (size_t)dm.Np;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += gridDim.x * blockDim.x) {
+    const int pix = (unsigned)c / (unsigned)C4, q = c - pix * C4, b0 = q << 2;
+    const int i = (unsigned)pix / (unsigned)N2, j = pix - i * N2;
+    const size_t p0 = (size_t)pix * N3p;
+    const size_t pv = ((size_t)(i + 1 == dm.N1 ? 0 : i + 1) * N2 + j) * N3p;
+    const size_t ph = ((size_t)i * N2 + (j + 1 == N2 ? 0 : j + 1)) * N3p;
+    const float4 x0 = ld4(ubar + p0 + b0), xv = ld4(ubar + pv + b0), xh = ld4(ubar + ph + b0);
+    const int nb = b0 + 4 < dm.N3 ? b0 + 4 : 0;
+    const float n0 = ubar[p0 + nb], nv = ubar[pv + nb], nh = ubar[ph + nb];
+    float4 y4[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) y4[m] = ld4(Y + m * Np + p0 + b0);
+    float o[4][4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (b0 + e < dm.N3) {
+        const bool in = e < 3 && b0 + e + 1 < dm.N3;
+        const float ds0 = (in ? comp(x0, e + 1) : n0) - comp(x0, e);
+        const float f[4] = {((in ? comp(xv, e + 1) : nv) - comp(xv, e)) - ds0,
+                            ((in ? comp(xh, e + 1) : nh) - comp(xh, e)) - ds0,
+                            omega * (comp(xv, e) - comp(x0, e)), omega * (comp(xh, e) - comp(x0, e))};
+        float yp[4], s2 = 0.f;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          yp[m] = fmaf(gY, f[m], comp(y4[m], e));
+          s2 = fmaf(yp[m], yp[m], s2);
+        }
+        const float sc = l12 && s2 > 1.f ? rsqrtf(s2) : 1.f;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) o[m][e] = l12 ? yp[m] * sc : fminf(fmaxf(yp[m], -1.f), 1.f);
+      } else {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) o[m][e] = 0.f;
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) st4(Y + m * Np + p0 + b0, make_float4(o[m][0], o[m][1], o[m][2], o[m][3]));
+    st4(Zv + p0 + b0, make_float4(o[0][0], o[0][1], o[0][2], o[0][3]));
+    st4(Zh + p0 + b0, make_float4(o[1][0], o[1][1], o[1][2], o[1][3]));
+  }
+}
+
+cudaError_t launch_hsstv_dual(const float *ubar, float *Y, float *Zv, float *Zh, Dims dm, float gY, float omega,
+                              int l12, int grid, cudaStream_t st) {
+  hsstv_dual_kernel<<<grid, 256, 0, st>>>(ubar, Y, Zv, Zh, dm, gY, omega, l12);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sstv_dual(const float *ubar, float *Yv, float *Yh, float *Zv, float *Zh, Dims dm, float gY,

@@ -278,7 +278,44 @@ __global__ void __launch_bounds__(256) sstv_l1_kernel(const float *u, int N1, in
   }
 }
 
+// HSSTV's objective: || (D_v D_s u, D_h D_s u, omega D_v u, omega D_h u) || summed
+// over voxels, l1 (l12 = 0) or the l2 norm of each voxel's four entries (l12 = 1)
+__global__ void __launch_bounds__(256) hsstv_norm_kernel(const float *u, int N1, int N2, int N3, double omega, int l12,
+                                                        double *out) {
+  __shared__ double red[8];
+  const long long N = (long long)N1 * N2 * N3;
+  double acc = 0.0;
+  for (long long e = blockIdx.x * 256LL + threadIdx.x; e < N; e += gridDim.x * 256LL) {
+    const int b = (int)(e % N3);
+    const long long pix = e / N3;
+    const int i = (int)(pix / N2), j = (int)(pix % N2);
+    const int i1 = i + 1 == N1 ? 0 : i + 1, j1 = j + 1 == N2 ? 0 : j + 1, b1 = b + 1 == N3 ? 0 : b + 1;
+    const size_t p0 = (size_t)pix * N3, pv = ((size_t)i1 * N2 + j) * N3, ph = ((size_t)i * N2 + j1) * N3;
+    const double ds0 = (double)u[p0 + b1] - (double)u[p0 + b];
+    const double a0 = ((double)u[pv + b1] - (double)u[pv + b]) - ds0;
+    const double a1 = ((double)u[ph + b1] - (double)u[ph + b]) - ds0;
+    const double a2 = omega * ((double)u[pv + b] - (double)u[p0 + b]);
+    const double a3 = omega * ((double)u[ph + b] - (double)u[p0 + b]);
+    acc += l12 ? sqrt(a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3) : fabs(a0) + fabs(a1) + fabs(a2) + fabs(a3);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    atomicAdd(out, t);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_hsstv_norm(const float *u, int N1, int N2, int N3, double omega, int l12, double *out, int grid,
+                              cudaStream_t st) {
+  hsstv_norm_kernel<<<grid, 256, 0, st>>>(u, N1, N2, N3, omega, l12, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sstv_l1(const float *u, int N1, int N2, int N3, double *out, int grid, cudaStream_t st) {
   sstv_l1_kernel<<<grid, 256, 0, st>>>(u, N1, N2, N3, out);

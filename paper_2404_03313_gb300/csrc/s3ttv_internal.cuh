@@ -76,6 +76,8 @@ struct PrimalArgs {
   unsigned *hcnt;         // [2][kHistBins]
   double *hsum;           // [2][kHistBins]
   int no_ds;              // 1: the dual term is D^T Z (STV's first-order tensors), no D_s^T
+  const float *Z1v = nullptr, *Z1h = nullptr;  // HSSTV: first-order dual pair, adds w1 D^T Z1
+  float w1 = 0.f;
 };
 cudaError_t launch_primal(const PrimalArgs &a, int grid, cudaStream_t st);
 
@@ -180,6 +182,10 @@ cudaError_t launch_xfield(const float *ubar, float *Fv, float *Fh, Dims dm, int 
 // (Yv, Yh), and Z = Y
 cudaError_t launch_sstv_dual(const float *ubar, float *Yv, float *Yh, float *Zv, float *Zh, Dims dm, float gY,
                              int grid, cudaStream_t st);
+// HSSTV's dual step on four cubes Y (second-order pair then omega-weighted
+// first-order pair): l1 (l12 = 0) or per-voxel l1,2 (l12 = 1) conjugate prox
+cudaError_t launch_hsstv_dual(const float *ubar, float *Y, float *Zv, float *Zh, Dims dm, float gY, float omega,
+                              int l12, int grid, cudaStream_t st);
 cudaError_t launch_Z_from_Y(const float *Y, float *Zv, float *Zh, Dims dm, int k, cudaStream_t st);
 cudaError_t launch_init_scalars(Scalars *sc, double alpha, double beta, cudaStream_t st);
 
@@ -195,5 +201,7 @@ size_t objective_smem_bytes(int k, int stacked);
 cudaError_t launch_objective(const float *u, int N1, int N2, int N3, int k, int stacked, int open_s,
                              int first_order, double *out, unsigned *nonconv, int grid, cudaStream_t st);
 cudaError_t launch_sstv_l1(const float *u, int N1, int N2, int N3, double *out, int grid, cudaStream_t st);
+cudaError_t launch_hsstv_norm(const float *u, int N1, int N2, int N3, double omega, int l12, double *out, int grid,
+                              cudaStream_t st);
 
 }  // namespace s3ttv

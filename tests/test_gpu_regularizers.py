@@ -1,6 +1,8 @@
 """GPU parity of the comparison regularisers the paper runs through the same
-P-PDS (Sec. IV): STV (block nuclear norms of first-order spatial differences)
-and SSTV (l1 norm of D D_s u), against the FP64 oracle through the C ABI.
+P-PDS (Sec. IV): STV (block nuclear norms of first-order spatial differences),
+SSTV (l1 norm of D D_s u) and HSSTV1 / HSSTV2 (SSTV plus omega-weighted
+first-order differences, l1 or per-voxel l1,2), against the FP64 oracle through
+the C ABI.
 
 Tolerances as in test_gpu_parity: one pass from a random state, relative L2
 1e-5 per state (SSTV's clip is exact; STV's blocks have k^2 = 9 rows); after
@@ -15,7 +17,7 @@ from synthetic import WORKLOADS, make_cube, random_state
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-REGS = ["stv", "sstv"]
+REGS = ["stv", "sstv", "hsstv1", "hsstv2"]
 
 
 def rel(a, b):
@@ -36,7 +38,8 @@ def P():
 
 def solver_for(P, reg):
     s = P.Solver(0)
-    s.set_option(P.OPT_REGULARIZER, {"stv": P.REG_STV, "sstv": P.REG_SSTV}[reg])
+    s.set_option(P.OPT_REGULARIZER, {"stv": P.REG_STV, "sstv": P.REG_SSTV, "hsstv1": P.REG_HSSTV1,
+                                      "hsstv2": P.REG_HSSTV2}[reg])
     return s
 
 
@@ -46,8 +49,8 @@ def test_one_pass_from_a_random_state(P, reg):
     st = random_state(N1, N2, N3, k, seed=5)
     r = np.random.default_rng(6)
     v = r.uniform(0, 1, (N1, N2, N3)).astype(np.float32)
-    if reg == "sstv":
-        st["Y"] = (0.3 * r.standard_normal((2, N1, N2, N3))).astype(np.float32)
+    if reg in ("sstv", "hsstv1", "hsstv2"):
+        st["Y"] = (0.3 * r.standard_normal((2 if reg == "sstv" else 4, N1, N2, N3))).astype(np.float32)
     eps, alpha, beta = 3.0, 20.0, 10.0
     ref_state = {key: val.astype(np.float64) for key, val in st.items()}
     gam = O.step_sizes(N1, N2, k, "paper", reg)
