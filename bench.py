@@ -593,13 +593,21 @@ def run_warm_start(args):
         e, a, b = P.radii(v.size, sp.sigma, sp.p_s, sp.p_t)
         cold = WS.solve(vd, e, a, b, 5, None, 5000, 1e-5, policy, device=dev)
         warm = WS.solve(vd, e, a, b, 5, net, 5000, 1e-5, policy, device=dev)
+        # the paper's printed step sizes: the stop rule does not fire, so compare
+        # the restored cube after a fixed budget of passes
+        cold_p = WS.solve(vd, e, a, b, 5, None, args.ws_paper_passes, 0.0, P.STEP_PAPER, device=dev)
+        warm_p = WS.solve(vd, e, a, b, 5, net, args.ws_paper_passes, 0.0, P.STEP_PAPER, device=dev)
         pred = net.forward(vd)[0]
         evals.append({"cold_s": cold["seconds"], "cold_iters": cold["info"]["iters"],
                       "warm_s": warm["seconds"], "warm_iters": warm["info"]["iters"],
                       "net_s": warm["net_seconds"],
                       "mpsnr_observed": mpsnr(v, clean), "mpsnr_network": mpsnr(pred.cpu().numpy(), clean),
                       "mpsnr_cold": mpsnr(cold["u"].cpu().numpy(), clean),
-                      "mpsnr_warm": mpsnr(warm["u"].cpu().numpy(), clean)})
+                      "mpsnr_warm": mpsnr(warm["u"].cpu().numpy(), clean),
+                      "paper_steps": {"passes": args.ws_paper_passes,
+                                      "cold_s": cold_p["seconds"], "warm_s": warm_p["seconds"],
+                                      "mpsnr_cold": mpsnr(cold_p["u"].cpu().numpy(), clean),
+                                      "mpsnr_warm": mpsnr(warm_p["u"].cpu().numpy(), clean)}})
     clocks = sampler.stop()
     net.close()
     warm_s = statistics.mean(ev["warm_s"] for ev in evals)
@@ -721,6 +729,8 @@ def main(argv=None):
     ap.add_argument("--batch-tol", type=float, default=1e-4,
                     help="stop rule of the batched to-tolerance run (per cube)")
     ap.add_argument("--batch-max-iter", type=int, default=600)
+    ap.add_argument("--ws-paper-passes", type=int, default=1000,
+                    help="warm-start workload: fixed pass budget of the runs with the paper's step sizes")
     ap.add_argument("--no-tol-run", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

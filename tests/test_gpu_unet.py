@@ -183,6 +183,7 @@ def test_trained_network_as_warm_start(P):
         losses = WS.train(net, cubes, [x[:3] for x in targets], 300, crop=(32, 32, 32), batch=4, lr=1e-3,
                           lr_final=1e-4)
         assert np.mean(losses[-20:]) < 0.5 * np.mean(losses[:5])
+        net_params = net.get_params()
         sp = warm_start_specs(1, 20000, shape)[0]
         clean, v = make_cube(sp)
         vd = torch.from_numpy(v).cuda()
@@ -198,3 +199,12 @@ def test_trained_network_as_warm_start(P):
     # both runs end at the stop rule or at the same cap, at the same minimiser
     assert cold["info"]["iters"] <= 20000 and warm["info"]["iters"] <= 20000
     assert abs(m_warm - m_cold) <= 0.01
+    # with the paper's printed step sizes the stop rule does not fire and u moves
+    # slowly: after a fixed budget of passes the warm start is far ahead
+    with P.WarmStartNet(0) as net2:
+        net2.set_params(net_params)
+        cold_p = WS.solve(vd, e, a, b, 5, None, 200, 0.0, P.STEP_PAPER)
+        warm_p = WS.solve(vd, e, a, b, 5, net2, 200, 0.0, P.STEP_PAPER)
+    mc, mw = O.mpsnr(cold_p["u"].cpu().numpy(), clean), O.mpsnr(warm_p["u"].cpu().numpy(), clean)
+    print(f"paper steps, 200 passes: MPSNR cold {mc:.3f} warm {mw:.3f}")
+    assert mw > mc + 3.0
