@@ -34,7 +34,7 @@ __all__ = [
     "AXIS_V", "AXIS_H", "AXIS_S", "HSSTV_OMEGA", "diff", "diff_adj", "spectral_diffs", "spectral_diff_adjoint", "structure_tensors",
     "structure_tensors_adjoint", "structure_tensor_block", "linear_op_adjoint_u",
     "linear_op_adjoint_u_at",
-    "prox_nuclear", "block_dual_update", "proj_box", "proj_l2_ball",
+    "prox_nuclear", "ssst_adjoint_u", "block_dual_update", "proj_box", "proj_l2_ball",
     "proj_l1_ball", "step_sizes", "assemble_operator", "lemma1_step_sizes",
     "radii", "init_state", "iterate", "solve", "mpsnr", "objective", "ssim_window", "ssim_band", "mssim",
     "sam_map",
@@ -71,7 +71,7 @@ def spectral_diffs(u: np.ndarray, periodic_s: bool = True):
 
 
 def structure_tensors(u: np.ndarray, k: int, layout: str = "paper", periodic_s: bool = True,
-                      second_order: bool = True) -> np.ndarray:
+                      second_order: bool = True, spectral_part: bool = False) -> np.ndarray:
     """All structure tensors of eq. (SSST) / eq. (rewrite_Lu).
 
     Block l = p*N2 + q holds the second-order differences D_v D_s u and D_h D_s u
@@ -83,9 +83,18 @@ def structure_tensors(u: np.ndarray, k: int, layout: str = "paper", periodic_s: 
     vertical and row 2r + 1 the horizontal differences of pixel r, one column per
     band.  M = N3 with the periodic D_s, N3 - 1 without.  second_order=False
     builds STV's tensors instead: first-order spatial differences D_v u, D_h u
-    (no D_s; M = N3).
+    (no D_s; M = N3); with spectral_part as well, SSST's: a third part D_s u,
+    columns [v_1 h_1 s_1 ... v_N3 h_N3 s_N3] (paper layout only).
     """
     N1, N2, N3 = u.shape
+    if spectral_part:
+        parts = (diff(u, AXIS_V), diff(u, AXIS_H), diff(u, AXIS_S))
+        X = np.empty((N1, N2, k * k, 3 * N3))
+        for a in range(k):
+            for c in range(k):
+                for o in range(3):
+                    X[:, :, a * k + c, o::3] = np.roll(parts[o], shift=(-a, -c), axis=(0, 1))
+        return X.reshape(N1 * N2, k * k, 3 * N3)
     Fv, Fh = spectral_diffs(u, periodic_s) if second_order else (diff(u, AXIS_V), diff(u, AXIS_H))
     M = Fv.shape[2]
     if layout == "paper":
@@ -152,6 +161,18 @@ def spectral_diff_adjoint(w: np.ndarray, periodic_s: bool = True) -> np.ndarray:
     pad = np.zeros(w.shape[:-1] + (w.shape[-1] + 2,))
     pad[..., 1:-1] = w
     return pad[..., :-1] - pad[..., 1:]
+
+
+def ssst_adjoint_u(Y: np.ndarray, k: int, shape) -> np.ndarray:
+    """SSST's dual-to-primal term: sum_l [D_v; D_h; D_s]^T P_l^T Y_l."""
+    N1, N2, N3 = shape
+    Y = Y.reshape(N1, N2, k * k, 3 * N3)
+    Z = [np.zeros((N1, N2, N3)) for _ in range(3)]
+    for a in range(k):
+        for c in range(k):
+            for o in range(3):
+                Z[o] += np.roll(Y[:, :, a * k + c, o::3], shift=(a, c), axis=(0, 1))
+    return diff_adj(Z[0], AXIS_V) + diff_adj(Z[1], AXIS_H) + diff_adj(Z[2], AXIS_S)
 
 
 def linear_op_adjoint_u(Y: np.ndarray, k: int, shape, layout: str = "paper", periodic_s: bool = True,
@@ -266,6 +287,9 @@ def step_sizes(N1: int, N2: int, k: int, policy: str = "paper", reg: str = "s3tt
         return {"u": 1.0 / (4.0 * k * k + 1.0), "s": 1.0, "t": 1.0 / 3.0, "Y": 0.5, "y2": 0.5, "y3": 1.0 / 3.0}
     if reg == "sstv":
         return {"u": 1.0 / 9.0, "s": 1.0, "t": 1.0 / 3.0, "Y": 0.25, "y2": 0.5, "y3": 1.0 / 3.0}
+    if reg == "ssst":
+        # first-order D_v, D_h, D_s: column abs-sum 6 per block, in k^2 blocks; rows 2
+        return {"u": 1.0 / (6.0 * k * k + 1.0), "s": 1.0, "t": 1.0 / 3.0, "Y": 0.5, "y2": 0.5, "y3": 1.0 / 3.0}
     if reg in ("hsstv1", "hsstv2"):
         # column abs-sum 8 + 4 omega (+1 for y3); the dual rows' sums are 4 and
         # 2 omega, and one gamma_Y = 1/4 serves all four parts (omega <= 2)
@@ -315,6 +339,27 @@ def assemble_operator(N1: int, N2: int, N3: int, k: int, reg: str = "s3ttv"):
     if reg == "stv":  # first-order spatial differences in the blocks
         DvDs, DhDs = Dv, Dh
     L = N1 * N2
+    if reg == "ssst":  # blocks of [D_v u, D_h u, D_s u], columns 3b + o
+        rows, cols, vals = [], [], []
+        for p in range(N1):
+            for q in range(N2):
+                l = p * N2 + q
+                for a in range(k):
+                    for c in range(k):
+                        r = a * k + c
+                        for b in range(N3):
+                            for o, M in ((0, Dv), (1, Dh), (2, Ds)):
+                                row = (l * k * k + r) * 3 * N3 + 3 * b + o
+                                src = M.getrow(idx(p + a, q + c, b))
+                                rows += [row] * src.nnz
+                                cols += list(src.indices)
+                                vals += list(src.data)
+        AY = sp.csr_matrix((vals, (rows, cols)), shape=(L * k * k * 3 * N3, N))
+        I = sp.identity(N, format="csr")
+        Z = sp.csr_matrix((N, N))
+        return {("Y", "u"): AY, ("Y", "s"): sp.csr_matrix((AY.shape[0], N)),
+                ("Y", "t"): sp.csr_matrix((AY.shape[0], N)), ("y2", "u"): Z, ("y2", "s"): Z, ("y2", "t"): Dv,
+                ("y3", "u"): I, ("y3", "s"): I, ("y3", "t"): I}
     rows, cols, vals = [], [], []
     for p in range(N1):
         for q in range(N2):
@@ -379,6 +424,8 @@ def init_state(v: np.ndarray, k: int, layout: str = "paper", periodic_s: bool = 
         Y = np.zeros((2,) + v.shape)
     elif reg in ("hsstv1", "hsstv2"):
         Y = np.zeros((4,) + v.shape)
+    elif reg == "ssst":
+        Y = np.zeros_like(structure_tensors(v, k, spectral_part=True))
     else:
         Y = np.zeros_like(structure_tensors(v, k, layout, periodic_s, reg != "stv"))
     return {"u": v.copy(), "s": z.copy(), "t": z.copy(), "y2": z.copy(), "y3": z.copy(), "Y": Y}
@@ -403,6 +450,8 @@ def iterate(state: dict, v: np.ndarray, k: int, eps: float, alpha: float, beta: 
     # Step 2: u update, box projection.
     if reg == "sstv":
         lin = spectral_diff_adjoint(diff_adj(Y[0], AXIS_V) + diff_adj(Y[1], AXIS_H), True)
+    elif reg == "ssst":
+        lin = ssst_adjoint_u(Y, k, u.shape)
     elif reg in ("hsstv1", "hsstv2"):
         lin = (spectral_diff_adjoint(diff_adj(Y[0], AXIS_V) + diff_adj(Y[1], AXIS_H), True)
                + HSSTV_OMEGA * (diff_adj(Y[2], AXIS_V) + diff_adj(Y[3], AXIS_H)))
@@ -430,6 +479,8 @@ def iterate(state: dict, v: np.ndarray, k: int, eps: float, alpha: float, beta: 
             nrm = np.sqrt((w * w).sum(axis=0, keepdims=True))
             prox = w * np.maximum(1.0 - (1.0 / g["Y"]) / np.maximum(nrm, 1e-300), 0.0)
         Y_new = Yp - g["Y"] * prox
+    elif reg == "ssst":
+        Y_new = block_dual_update(Y, structure_tensors(ub, k, spectral_part=True), g["Y"])
     else:
         Y_new = block_dual_update(Y, structure_tensors(ub, k, layout, periodic_s, reg != "stv"), g["Y"])
     # Step 12: prox of the conjugate of iota_{0} is the identity (eq. prox_zeroset).
@@ -495,7 +546,10 @@ def objective(u: np.ndarray, k: int, layout: str = "paper", periodic_s: bool = T
     if reg in ("hsstv1", "hsstv2"):
         A = np.stack(spectral_diffs(u, True) + (HSSTV_OMEGA * diff(u, AXIS_V), HSSTV_OMEGA * diff(u, AXIS_H)))
         return float(np.abs(A).sum() if reg == "hsstv1" else np.sqrt((A * A).sum(axis=0)).sum())
-    X = structure_tensors(u, k, layout, periodic_s, reg != "stv")
+    if reg == "ssst":
+        X = structure_tensors(u, k, spectral_part=True)
+    else:
+        X = structure_tensors(u, k, layout, periodic_s, reg != "stv")
     return float(np.linalg.svd(X, compute_uv=False).sum())
 
 

@@ -679,3 +679,23 @@ def test_hsstv_objectives_and_adjoint():
     A = np.stack((F2v, F2h, w * F1v, w * F1h))
     lhs, rhs = float((A * Y).sum()), float((u * ATY).sum())
     assert abs(lhs - rhs) <= 1e-6 * max(1.0, abs(lhs))
+
+
+def test_ssst_step_sizes_adjoint_and_k1_closed_form():
+    """SSST (structure tensors of first-order spatial and spectral differences):
+    Lemma 1 on the assembled operator gives gamma_u = 1/(6k^2 + 1), gamma_Y = 1/2;
+    the adjoint identity; with k = 1 each tensor is one row, its norm the
+    nuclear norm."""
+    got = O.lemma1_step_sizes(O.assemble_operator(4, 5, 3, 2, "ssst"))
+    want = O.step_sizes(4, 5, 2, "paper", "ssst")
+    for key in ("u", "s", "t", "Y", "y2", "y3"):
+        assert got[key][0] == pytest.approx(want[key], rel=1e-12) and got[key][1], key
+    r = np.random.default_rng(61)
+    u = r.standard_normal((4, 5, 6))
+    X = O.structure_tensors(u, 2, spectral_part=True)
+    Y = r.standard_normal(X.shape)
+    lhs, rhs = float((X * Y).sum()), float((u * O.ssst_adjoint_u(Y, 2, u.shape)).sum())
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+    dv, dh, ds = (np.roll(u, -1, ax) - u for ax in (0, 1, 2))
+    expect = np.sqrt((dv ** 2 + dh ** 2 + ds ** 2).sum(axis=2)).sum()
+    assert O.objective(u, 1, reg="ssst") == pytest.approx(expect, rel=1e-12)
