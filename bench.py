@@ -270,7 +270,8 @@ def run_ours(args, spec):
     solver.set_option(P.OPT_LAYOUT, P.LAYOUT_STACKED if args.layout == "stacked" else P.LAYOUT_PAPER)
     solver.set_option(P.OPT_SPECTRAL_BOUNDARY, P.SPECTRAL_OPEN if args.spectral == "open" else P.SPECTRAL_PERIODIC)
     solver.set_option(P.OPT_REGULARIZER, {"s3ttv": P.REG_S3TTV, "stv": P.REG_STV, "sstv": P.REG_SSTV,
-                                          "hsstv1": P.REG_HSSTV1, "hsstv2": P.REG_HSSTV2}[args.reg])
+                                          "hsstv1": P.REG_HSSTV1, "hsstv2": P.REG_HSSTV2,
+                                          "ssst": P.REG_SSST}[args.reg])
     if args.autotune:
         solver.set_option(P.OPT_AUTOTUNE, 1)
     vd = torch.from_numpy(v).to(f"cuda:{dev}")
@@ -306,7 +307,8 @@ def run_ours(args, spec):
     k2 = spec.k * spec.k
     bd_ms, bd_n = stats["block_dual"]
     bd_avg_s = bd_ms / max(bd_n, 1) / 1000.0
-    bytes_per_voxel = 16 * k2 + 4 + 8  # Y read + write, ubar read, Z written once
+    # Y read + write, ubar read, Z written once (SSST: three parts of Y and Z)
+    bytes_per_voxel = 24 * k2 + 4 + 12 if args.reg == "ssst" else 16 * k2 + 4 + 8
     alg_bytes = bytes_per_voxel * N
     peak, peak_src = measured_peaks()
     stacked = args.layout == "stacked"
@@ -319,26 +321,27 @@ def run_ours(args, spec):
                     "traffic": None, "kernel": "sstv_dual_kernel" if args.reg == "sstv" else "hsstv_dual_kernel",
                     "peak_source": peak_src,
                     "algorithmic_bytes_per_launch": sb, "avg_launch_ms": bd_avg_s * 1000.0}
-    elif spec.k <= 5 and not stacked:
+    elif spec.k <= 5 and not stacked and args.reg != "ssst":
         achieved = alg_bytes / bd_avg_s / 1e9 if bd_avg_s > 0 else 0.0
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": block_dual_traffic(spec.k, N), "kernel": f"block_dual_kernel<{spec.k}, *>",
                     "peak_source": peak_src,
                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": bd_avg_s * 1000.0}
     else:
-        # k = 6..12 and the stacked layout: the eigen-solve binds, not HBM.
-        # Algorithmic FP32 work per block: Gram and apply 2 n^2 (2 k^2 N3 / n
-        # columns) each, a symmetric eigen-solve with vectors ~9 n^3; peak = 152
-        # SMs x 128 FP32 lanes x 2 flops x max SM clock.
+        # k = 6..12, the stacked layout and SSST: the eigen-solve binds, not
+        # HBM.  Algorithmic FP32 work per block: Gram and apply 2 n^2 cols each
+        # (n rows, cols = N3, 2 N3 or SSST's 3 N3), a symmetric eigen-solve with
+        # vectors ~9 n^3; peak = 152 SMs x 128 FP32 lanes x 2 flops x max SM clock.
         n = 2 * k2 if stacked else k2
-        cols = spec.N3 if stacked else 2 * spec.N3
+        cols = spec.N3 if stacked else (3 if args.reg == "ssst" else 2) * spec.N3
         flops = (4.0 * n * n * cols + 9.0 * n ** 3) * spec.N1 * spec.N2
         sm_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
         alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
         achieved = flops / bd_avg_s / 1e12 if bd_avg_s > 0 else 0.0
         roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                     "frac": achieved / alu_peak, "traffic": None,
-                    "kernel": f"block_dual_large_kernel<{spec.k}, {'true' if stacked else 'false'}>",
+                    "kernel": f"block_dual_large_kernel<{spec.k}, {'true' if stacked else 'false'}, "
+                              f"{3 if args.reg == 'ssst' else 2}>",
                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x max SM clock",
                     "algorithmic_flops_per_launch": flops, "avg_launch_ms": bd_avg_s * 1000.0,
                     "hbm_frac": alg_bytes / bd_avg_s / 1e9 / peak if bd_avg_s > 0 else 0.0}
@@ -722,7 +725,7 @@ def main(argv=None):
                     help="block matrices: the paper's k^2 x 2N3 or the stacked 2k^2 x N3")
     ap.add_argument("--spectral", choices=("periodic", "open"), default="periodic",
                     help="spectral difference: periodic (the paper) or open (no wrap-around)")
-    ap.add_argument("--reg", choices=("s3ttv", "stv", "sstv", "hsstv1", "hsstv2"), default="s3ttv",
+    ap.add_argument("--reg", choices=("s3ttv", "stv", "sstv", "hsstv1", "hsstv2", "ssst"), default="s3ttv",
                     help="regularisation function: S3TTV (the paper) or a comparison one run by the same P-PDS")
     ap.add_argument("--autotune", action="store_true",
                     help="let the library time the block-dual forms on the warm-up passes and keep the fastest")

@@ -113,25 +113,40 @@ enum {
 };
 /* Regularisers (option S3TTV_OPT_REGULARIZER).  Sec. IV runs its P-PDS-solvable
  * comparison methods by replacing S3TTV in Prob. (S3TTV_denoising) and solving
- * with the same P-PDS; four of them are built:
+ * with the same P-PDS; five of them are built:
  *   S3TTV_REG_STV   sum_l || P_l D u ||_*: the nuclear norms of structure
  *                   tensors of first-order spatial differences (k^2 x 2N3
  *                   blocks, same block-dual path; the primal step has no D_s^T);
  *   S3TTV_REG_SSTV  || D D_s u ||_1: the dual is the cube pair (Y_v, Y_h) and
  *                   its conjugate prox is the clip to [-1, 1];
- *   S3TTV_REG_HSSTV1, S3TTV_REG_HSSTV2: below.
+ *   S3TTV_REG_HSSTV1, S3TTV_REG_HSSTV2, S3TTV_REG_SSST: below.
  * Their step sizes are the exact Lemma 1 values of their operators
  * (STV: gamma_u = 1/(4k^2 + 1), gamma_Y = 1/2; SSTV: gamma_u = 1/9,
  * gamma_Y = 1/4; S3TTV_OPT_STEP_POLICY applies to S3TTV only).  With SSTV the
  * external "Y" state is [2][N1][N2][N3] (Y_v then Y_h) and s3ttv_block_dual
  * returns S3TTV_EUNSUPPORTED.  Changing the option drops the problem set up. */
-enum { S3TTV_REG_S3TTV = 0, S3TTV_REG_STV = 1, S3TTV_REG_SSTV = 2, S3TTV_REG_HSSTV1 = 3, S3TTV_REG_HSSTV2 = 4 };
+enum {
+  S3TTV_REG_S3TTV = 0,
+  S3TTV_REG_STV = 1,
+  S3TTV_REG_SSTV = 2,
+  S3TTV_REG_HSSTV1 = 3,
+  S3TTV_REG_HSSTV2 = 4,
+  S3TTV_REG_SSST = 5
+};
 /* HSSTV (Hybrid SSTV): || (D_v D_s u, D_h D_s u, omega D_v u, omega D_h u) ||, the
  * l1 norm (S3TTV_REG_HSSTV1) or the l1,2 norm grouping each voxel's four entries
  * (S3TTV_REG_HSSTV2); the dual is four cubes ("Y" state [4][N1][N2][N3]) whose
  * conjugate prox clips each entry to [-1, 1] (l1) or scales each voxel's
  * 4-vector into the unit l2 ball (l1,2); gamma_u = 1/(9 + 4 omega), gamma_Y = 1/4
  * for all four parts (Lemma 1: row bounds 1/4 and 1/(2 omega)). */
+/* SSST (spatio-spectral structure tensors): sum_l || P_l [D_v u, D_h u, D_s u] ||_*,
+ * structure tensors of the first-order spatial and spectral differences, each a
+ * k^2 x 3N3 block, row r the window pixel r, columns [v_1 h_1 s_1 ... v_N3 h_N3
+ * s_N3]; the external "Y" state is [N1*N2][k*k][3*N3].  The blocks run on the
+ * per-CTA path (FP32) for k <= 8, paper layout and periodic D_s only (other
+ * settings return S3TTV_EUNSUPPORTED); gamma_u = 1/(6k^2 + 1), gamma_Y = 1/2
+ * (Lemma 1: column abs-sums 6k^2, row abs-sums 2); s3ttv_block_dual returns
+ * S3TTV_EUNSUPPORTED; s3ttv_objective evaluates the sum of nuclear norms. */
 /* Block-matrix layouts (option S3TTV_OPT_LAYOUT).  PAPER is eq. (SSST): X_l is
  * k^2 x 2N3, row r the window pixel r = a k + c, columns [v_1 h_1 ... v_N3 h_N3].
  * STACKED is the (2k^2) x N3 matrix of the vertical and horizontal differences

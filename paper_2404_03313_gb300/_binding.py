@@ -26,7 +26,7 @@ SPECTRAL_PERIODIC, SPECTRAL_OPEN = 0, 1
 OPT_REGULARIZER = 10
 OPT_AUTOTUNE = 11
 OPT_HSSTV_OMEGA = 12
-REG_S3TTV, REG_STV, REG_SSTV, REG_HSSTV1, REG_HSSTV2 = 0, 1, 2, 3, 4
+REG_S3TTV, REG_STV, REG_SSTV, REG_HSSTV1, REG_HSSTV2, REG_SSST = 0, 1, 2, 3, 4, 5
 KERNEL_CLASSES = ("primal", "l1_search", "block_dual", "dual", "finalize")
 STATE = {"u": 0, "s": 1, "t": 2, "y2": 3, "y3": 4, "Y": 5}
 
@@ -334,6 +334,8 @@ class Solver:
                 return (2, N1, N2, N3)
             if getattr(self, "reg", REG_S3TTV) in (REG_HSSTV1, REG_HSSTV2):
                 return (4, N1, N2, N3)
+            if getattr(self, "reg", REG_S3TTV) == REG_SSST:
+                return (N1 * N2, self.k * self.k, 3 * N3)
             if getattr(self, "layout", LAYOUT_PAPER) == LAYOUT_STACKED:
                 return (N1 * N2, 2 * self.k * self.k, N3)
             return (N1 * N2, self.k * self.k, 2 * N3)

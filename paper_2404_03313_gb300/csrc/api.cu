@@ -27,7 +27,7 @@ struct s3ttv_ctx {
   int tensor_cores = 1;
   int layout = S3TTV_LAYOUT_PAPER;  // block matrices: paper k^2 x 2N3 or stacked 2k^2 x N3
   int open_s = 0;                   // 1: D_s stops at the last band (no wrap-around)
-  int reg = S3TTV_REG_S3TTV;        // regularisation function (S3TTV, STV or SSTV)
+  int reg = S3TTV_REG_S3TTV;        // regularisation function (S3TTV or a comparison method)
   float hsstv_omega = 0.05f;        // HSSTV's weight of the first-order differences
   int autotune = 0;                 // 1: time the block-dual forms on the first passes, keep the fastest
   int tuned_tc = -1, tuned_minb = 0;  // the chosen form (tc -1: none chosen yet)
@@ -44,6 +44,7 @@ struct s3ttv_ctx {
   float *v = nullptr, *u = nullptr, *s = nullptr, *t[2] = {nullptr, nullptr}, *y2 = nullptr, *d = nullptr;
   float *ubar = nullptr, *zs = nullptr, *zt = nullptr, *Zv[2] = {nullptr, nullptr}, *Zh[2] = {nullptr, nullptr};
   float *Fv = nullptr, *Fh = nullptr;  // D_v D_s ubar, D_h D_s ubar
+  float *Fs = nullptr, *Zs[2] = {nullptr, nullptr};  // SSST: D_s ubar and the third part of Z
   float *Y = nullptr, *stage = nullptr;
   float *W = nullptr;      // per-block warm-start rows of the eigen-solve
   long long w_stride = 0;
@@ -113,6 +114,9 @@ bool is_device_ptr(const void *p) {
 int round4(int x) { return (x + 3) & ~3; }
 
 bool is_hsstv(const s3ttv_ctx *c) { return c->reg == S3TTV_REG_HSSTV1 || c->reg == S3TTV_REG_HSSTV2; }
+bool is_ssst(const s3ttv_ctx *c) { return c->reg == S3TTV_REG_SSST; }
+// parts of a block row: [D_v | D_h] (S3TTV, STV) or SSST's [D_v | D_h | D_s]
+int row_parts(const s3ttv_ctx *c) { return is_ssst(c) ? 3 : 2; }
 
 int elementwise_grid(const s3ttv_ctx *c, long long n) {
   long long g = (n + 255) / 256;
@@ -126,7 +130,7 @@ int elementwise_grid(const s3ttv_ctx *c, long long n) {
 void free_all(s3ttv_ctx *c) {
   float **bufs[] = {&c->v, &c->u, &c->s, &c->t[0], &c->t[1], &c->y2, &c->d, &c->ubar, &c->zs,
                     &c->zt, &c->Zv[0], &c->Zv[1], &c->Zh[0], &c->Zh[1], &c->Y, &c->stage, &c->W,
-                    &c->Fv, &c->Fh};
+                    &c->Fv, &c->Fh, &c->Fs, &c->Zs[0], &c->Zs[1]};
   for (float **b : bufs) {
     if (*b) cudaFree(*b);
     *b = nullptr;
@@ -203,12 +207,15 @@ int ensure_macc(s3ttv_ctx *ctx, size_t n) {
 
 int ensure_problem_buffers(s3ttv_ctx *ctx, const Dims &dm, int k) {
   const size_t np = (size_t)dm.Np;
-  size_t ny = (size_t)dm.P * k * k * 2 * dm.N3p;
+  size_t ny = (size_t)dm.P * k * k * row_parts(ctx) * dm.N3p;
   if (ny < 4 * np) ny = 4 * np;  // HSSTV keeps four dual cubes
-  const long long ws = ctx->layout == S3TTV_LAYOUT_STACKED ? block_dual_large_w_stride(k, true) : block_dual_w_stride(k);
+  const long long ws = ctx->layout == S3TTV_LAYOUT_STACKED ? block_dual_large_w_stride(k, true)
+                       : is_ssst(ctx)                      ? block_dual_large_w_stride(k, false)
+                                                           : block_dual_w_stride(k);
   const size_t nw = (size_t)dm.P * ws;
   ctx->w_stride = ws;
-  if (np <= ctx->cap_np && ny <= ctx->cap_y && nw <= ctx->cap_w && ctx->sc) return S3TTV_OK;
+  if (np <= ctx->cap_np && ny <= ctx->cap_y && nw <= ctx->cap_w && ctx->sc && (!is_ssst(ctx) || ctx->Fs))
+    return S3TTV_OK;
   free_all(ctx);
   ctx->w_stride = ws;
   int rc = ensure_common(ctx);
@@ -220,6 +227,15 @@ int ensure_problem_buffers(s3ttv_ctx *ctx, const Dims &dm, int k) {
     if ((rc = dmalloc(ctx, (void **)b, np * sizeof(float)))) {
       free_all(ctx);
       return rc;
+    }
+  }
+  if (is_ssst(ctx)) {
+    float **ssst[] = {&ctx->Fs, &ctx->Zs[0], &ctx->Zs[1]};
+    for (float **b : ssst) {
+      if ((rc = dmalloc(ctx, (void **)b, np * sizeof(float)))) {
+        free_all(ctx);
+        return rc;
+      }
     }
   }
   if ((rc = dmalloc(ctx, (void **)&ctx->Y, ny * sizeof(float))) ||
@@ -290,9 +306,14 @@ int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, BdShape *sh) {
   sh->v.k = k;
   sh->v.tc = ctx->tensor_cores;
   const bool stacked = ctx->layout == S3TTV_LAYOUT_STACKED;
+  const int parts = row_parts(ctx);
   if (stacked && k > kMaxStackedK)
     return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: the stacked layout supports k <= %d", k, kMaxStackedK);
-  if (stacked || k >= kMinLargeK) {  // one CTA per block at a time; FP32 CUDA cores whatever the option
+  if (parts == 3 && (stacked || ctx->open_s))
+    return fail(ctx, S3TTV_EUNSUPPORTED, "SSST takes the paper layout and the periodic spectral boundary");
+  if (parts == 3 && k > kMaxStackedK)
+    return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: SSST supports k <= %d", k, kMaxStackedK);
+  if (stacked || parts == 3 || k >= kMinLargeK) {  // one CTA per block at a time; FP32 CUDA cores
     sh->large = true;
     sh->smem = block_dual_large_smem_bytes(k, stacked);
     int dev_max = 0;
@@ -300,10 +321,10 @@ int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, BdShape *sh) {
     if (sh->smem > (size_t)dev_max)
       return fail(ctx, S3TTV_EUNSUPPORTED, "a %dx%d block needs %zu bytes of shared memory (device limit %d)", k, k,
                   sh->smem, dev_max);
-    cudaError_t e = block_dual_large_prepare(k, stacked, sh->smem);
+    cudaError_t e = block_dual_large_prepare(k, stacked, sh->smem, parts);
     if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
     int per_sm = 0;
-    e = block_dual_large_occupancy(k, stacked, sh->smem, &per_sm);
+    e = block_dual_large_occupancy(k, stacked, sh->smem, &per_sm, parts);
     if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
     if (per_sm < 1) per_sm = 1;
     long long g = (long long)ctx->num_sms * per_sm;
@@ -377,6 +398,9 @@ void step_sizes(int N1, int N2, int k, int policy, double g[6], int reg = S3TTV_
     g[0] = 1.0 / 9.0;
   } else if (reg == S3TTV_REG_HSSTV1 || reg == S3TTV_REG_HSSTV2) {
     g[0] = 1.0 / (9.0 + 4.0 * omega);  // gamma_Y = 1/4 serves all four dual parts (omega <= 2)
+  } else if (reg == S3TTV_REG_SSST) {
+    g[0] = 1.0 / (6.0 * k * k + 1.0);  // column abs-sum 6k^2 of P_l [D_v; D_h; D_s], plus y3's 1
+    g[3] = 0.5;                          // row abs-sum 2 of a first-order difference
   }
 }
 
@@ -415,7 +439,7 @@ int load_Y(s3ttv_ctx *ctx, const float *src) {
     for (int m = 0; m < ncubes && !rc; ++m) rc = load_cube(ctx, src + m * dm.P * dm.N3, ctx->Y + m * dm.Np, 1.f);
     return rc;
   }
-  const size_t ne = (size_t)dm.P * ctx->k * ctx->k * 2 * dm.N3;
+  const size_t ne = (size_t)dm.P * ctx->k * ctx->k * row_parts(ctx) * dm.N3;
   const float *from = src;
   if (!is_device_ptr(src)) {
     int rc = ensure_stage(ctx, ne);
@@ -423,7 +447,8 @@ int load_Y(s3ttv_ctx *ctx, const float *src) {
     CU(cudaMemcpyAsync(ctx->stage, src, sizeof(float) * ne, cudaMemcpyHostToDevice, ctx->stream));
     from = ctx->stage;
   }
-  CU(launch_Y_to_internal(from, ctx->Y, dm, ctx->k, ctx->stream, ctx->layout == S3TTV_LAYOUT_STACKED));
+  CU(launch_Y_to_internal(from, ctx->Y, dm, ctx->k, ctx->stream, ctx->layout == S3TTV_LAYOUT_STACKED,
+                          row_parts(ctx)));
   return S3TTV_OK;
 }
 
@@ -435,14 +460,16 @@ int store_Y(s3ttv_ctx *ctx, float *dst) {
     for (int m = 0; m < ncubes && !rc; ++m) rc = store_cube(ctx, ctx->Y + m * dm.Np, dst + m * dm.P * dm.N3, nullptr);
     return rc;
   }
-  const size_t ne = (size_t)dm.P * ctx->k * ctx->k * 2 * dm.N3;
+  const size_t ne = (size_t)dm.P * ctx->k * ctx->k * row_parts(ctx) * dm.N3;
   if (is_device_ptr(dst)) {
-    CU(launch_Y_to_external(ctx->Y, dst, dm, ctx->k, ctx->stream, ctx->layout == S3TTV_LAYOUT_STACKED));
+    CU(launch_Y_to_external(ctx->Y, dst, dm, ctx->k, ctx->stream, ctx->layout == S3TTV_LAYOUT_STACKED,
+                            row_parts(ctx)));
     return S3TTV_OK;
   }
   int rc = ensure_stage(ctx, ne);
   if (rc) return rc;
-  CU(launch_Y_to_external(ctx->Y, ctx->stage, dm, ctx->k, ctx->stream, ctx->layout == S3TTV_LAYOUT_STACKED));
+  CU(launch_Y_to_external(ctx->Y, ctx->stage, dm, ctx->k, ctx->stream, ctx->layout == S3TTV_LAYOUT_STACKED,
+                          row_parts(ctx)));
   CU(cudaMemcpyAsync(dst, ctx->stage, sizeof(float) * ne, cudaMemcpyDeviceToHost, ctx->stream));
   return S3TTV_OK;
 }
@@ -488,7 +515,11 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   pa.part = ctx->part;
   pa.hcnt = ctx->hcnt;
   pa.hsum = ctx->hsum;
-  pa.no_ds = ctx->reg == S3TTV_REG_STV;
+  pa.no_ds = ctx->reg == S3TTV_REG_STV || is_ssst(ctx);
+  if (is_ssst(ctx)) {
+    pa.Zs = ctx->Zs[par];
+    pa.Zns = ctx->Zs[par ^ 1];
+  }
   if (is_hsstv(ctx)) {
     pa.Z1v = ctx->Y + 2 * dm.Np;
     pa.Z1h = ctx->Y + 3 * dm.Np;
@@ -519,13 +550,16 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
     CU(launch_hsstv_dual(ctx->ubar, ctx->Y, ctx->Zv[par ^ 1], ctx->Zh[par ^ 1], dm, (float)ctx->gam[3],
                          ctx->hsstv_omega, ctx->reg == S3TTV_REG_HSSTV2, grid_e, st));
   } else {
-  CU(launch_xfield(ctx->ubar, ctx->Fv, ctx->Fh, dm, grid_e, st, ctx->open_s, ctx->reg == S3TTV_REG_STV));
+  CU(launch_xfield(ctx->ubar, ctx->Fv, ctx->Fh, dm, grid_e, st, ctx->open_s,
+                   ctx->reg == S3TTV_REG_STV || is_ssst(ctx), ctx->Fs));
   BlockDualArgs ba;
   ba.Y = ctx->Y;
   ba.Fv = ctx->Fv;
   ba.Fh = ctx->Fh;
+  ba.Fs = ctx->Fs;
   ba.Zv = ctx->Zv[par ^ 1];
   ba.Zh = ctx->Zh[par ^ 1];
+  ba.Zs = ctx->Zs[par ^ 1];
   ba.dm = dm;
   ba.gY = (float)ctx->gam[3];
   ba.rs = bd.rs;
@@ -535,7 +569,9 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   ba.W = ctx->warm_start ? ctx->W : nullptr;
   ba.w_stride = ctx->w_stride;
   ba.warm = ctx->warm_start && ctx->warm_valid;
-  if (bd.large) CU(launch_block_dual_large(ba, ctx->k, ctx->layout == S3TTV_LAYOUT_STACKED, bd.grid, bd.smem, st));
+  if (bd.large)
+    CU(launch_block_dual_large(ba, ctx->k, ctx->layout == S3TTV_LAYOUT_STACKED, bd.grid, bd.smem, st,
+                               row_parts(ctx)));
   else CU(launch_block_dual(ba, bd.v, bd.grid, bd.smem, st));
   if (ctx->warm_start) ctx->warm_valid = true;
   }
@@ -762,7 +798,7 @@ int s3ttv_set_option(s3ttv_ctx *ctx, int key, double value) {
       return S3TTV_OK;
     case S3TTV_OPT_REGULARIZER:
       if (!(value == S3TTV_REG_S3TTV || value == S3TTV_REG_STV || value == S3TTV_REG_SSTV ||
-            value == S3TTV_REG_HSSTV1 || value == S3TTV_REG_HSSTV2))
+            value == S3TTV_REG_HSSTV1 || value == S3TTV_REG_HSSTV2 || value == S3TTV_REG_SSST))
         return fail(ctx, S3TTV_EINVAL, "unknown regularizer %g", value);
       if ((int)value != ctx->reg) {
         ctx->reg = (int)value;
@@ -825,7 +861,9 @@ int s3ttv_setup(s3ttv_ctx *ctx, const float *v, int N1, int N2, int N3, float ep
   float *zero[] = {ctx->s, ctx->t[0], ctx->t[1], ctx->y2, ctx->d, ctx->ubar, ctx->zs, ctx->zt,
                    ctx->Zv[0], ctx->Zv[1], ctx->Zh[0], ctx->Zh[1]};
   for (float *z : zero) CU(cudaMemsetAsync(z, 0, cb, ctx->stream));
-  CU(cudaMemsetAsync(ctx->Y, 0, sizeof(float) * dm.P * k * k * 2 * dm.N3p, ctx->stream));
+  if (is_ssst(ctx))
+    for (float *z : {ctx->Zs[0], ctx->Zs[1]}) CU(cudaMemsetAsync(z, 0, cb, ctx->stream));
+  CU(cudaMemsetAsync(ctx->Y, 0, sizeof(float) * dm.P * k * k * row_parts(ctx) * dm.N3p, ctx->stream));
   CU(cudaMemsetAsync(ctx->hcnt, 0, sizeof(unsigned) * 2 * kHistBins, ctx->stream));
   CU(cudaMemsetAsync(ctx->hsum, 0, sizeof(double) * 2 * kHistBins, ctx->stream));
   CU(launch_init_scalars(ctx->sc, alpha, beta, ctx->stream));
@@ -985,7 +1023,8 @@ int s3ttv_set_state(s3ttv_ctx *ctx, int which, const float *src) {
         CU(cudaMemcpyAsync(ctx->Zh[ctx->parity], ctx->Y + ctx->dm.Np, sizeof(float) * ctx->dm.Np,
                            cudaMemcpyDeviceToDevice, ctx->stream));
       } else if (!rc) {
-        CU(launch_Z_from_Y(ctx->Y, ctx->Zv[ctx->parity], ctx->Zh[ctx->parity], ctx->dm, ctx->k, ctx->stream));
+        CU(launch_Z_from_Y(ctx->Y, ctx->Zv[ctx->parity], ctx->Zh[ctx->parity], ctx->dm, ctx->k, ctx->stream,
+                           is_ssst(ctx) ? ctx->Zs[ctx->parity] : nullptr));
       }
       break;
     default: return fail(ctx, S3TTV_EINVAL, "unknown state %d", which);
@@ -1281,6 +1320,7 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   if (!(gamma_Y > 0.f) || !std::isfinite(gamma_Y)) return fail(ctx, S3TTV_EINVAL, "gamma_Y must be > 0");
   if (ctx->reg == S3TTV_REG_SSTV || is_hsstv(ctx))
     return fail(ctx, S3TTV_EUNSUPPORTED, "SSTV and HSSTV have no block duals");
+  if (is_ssst(ctx)) return fail(ctx, S3TTV_EUNSUPPORTED, "SSST's block duals run inside the solver only");
   if (k > kMaxK) return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: this build supports k <= %d", k, kMaxK);
   DeviceGuard g(ctx->device);
   const Dims dm = make_dims(N1, N2, N3);
@@ -1340,8 +1380,11 @@ int s3ttv_objective(s3ttv_ctx *ctx, const float *u, int N1, int N2, int N3, int 
   if (!u || !value) return fail(ctx, S3TTV_EINVAL, "u and value are required");
   if (k < 1 || N1 < k || N2 < k || N3 < 1) return fail(ctx, S3TTV_EINVAL, "need N1, N2 >= k >= 1 and N3 >= 1");
   const int stacked = ctx->layout == S3TTV_LAYOUT_STACKED;
-  if (k > (stacked ? kMaxStackedK : kMaxK))
-    return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: this build supports k <= %d", k, stacked ? kMaxStackedK : kMaxK);
+  if (k > (stacked || is_ssst(ctx) ? kMaxStackedK : kMaxK))
+    return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: this build supports k <= %d", k,
+                stacked || is_ssst(ctx) ? kMaxStackedK : kMaxK);
+  if (is_ssst(ctx) && (stacked || ctx->open_s))
+    return fail(ctx, S3TTV_EUNSUPPORTED, "SSST takes the paper layout and the periodic spectral boundary");
   DeviceGuard g(ctx->device);
   int rc;
   const long long N = (long long)N1 * N2 * N3;
@@ -1364,8 +1407,8 @@ int s3ttv_objective(s3ttv_ctx *ctx, const float *u, int N1, int N2, int N3, int 
     CU(launch_hsstv_norm(du, N1, N2, N3, ctx->hsstv_omega, ctx->reg == S3TTV_REG_HSSTV2, ctx->macc, ctx->num_sms * 8,
                          ctx->stream));
   else
-    CU(launch_objective(du, N1, N2, N3, k, stacked, ctx->open_s, ctx->reg == S3TTV_REG_STV, ctx->macc, nonconv,
-                        ctx->num_sms * 4, ctx->stream));
+    CU(launch_objective(du, N1, N2, N3, k, stacked, ctx->open_s, ctx->reg == S3TTV_REG_STV || is_ssst(ctx),
+                        ctx->macc, nonconv, ctx->num_sms * 4, ctx->stream, row_parts(ctx)));
   double h[2] = {0.0, 0.0};
   CU(cudaMemcpyAsync(h, ctx->macc, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));

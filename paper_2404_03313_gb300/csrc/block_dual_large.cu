@@ -28,6 +28,10 @@
 //  5. M = I - Ut^T Ut by 4 x 4 tiles; then Y' streams through the chunk again
 //     and every thread forms a 4 x 4 tile of M Y', stored to Y_l and added into
 //     Z with float4 atomics.
+// The PARTS template parameter sets how many N3p-wide parts a paper-layout row
+// has: 2 ([D_v | D_h] differences, S3TTV and STV) or 3 (SSST's first-order
+// [D_v u | D_h u | D_s u], F = (Fv, Fh, Fs), Z = (Zv, Zh, Zs)); SSST's k^2 x 3N3
+// blocks run here for every k <= kMaxStackedK.
 // FP32 throughout (FP32 FMAs on CUDA cores).
 #include <math.h>
 #include "s3ttv_internal.cuh"
@@ -109,13 +113,28 @@ __device__ __forceinline__ void upper_tile(int t, int nt4, int &ti, int &tj) {
 }
 
 // The chunk [c0, c0 + kCW) of Y'_l into shared memory, all 4 nt4 rows (rows
-// >= n and columns >= 2 N3p read as 0).  form: add gamma_Y F and write Y'
+// >= n and columns >= W read as 0).  form: add gamma_Y F and write Y'
 // back over Y_l.
-template <bool ST, int LT>
+// the F cube and band of row r's column c: paper layout, PARTS parts of N3p
+// bands per row ([v | h] or SSST's [v | h | s]); stacked, rows 2r, 2r + 1
+template <bool ST, int PARTS>
+__device__ __forceinline__ const float *f_part(const BlockDualArgs &a, int r, int c, int N3p, int &band) {
+  const int part = ST ? (r & 1) : c / N3p;
+  band = ST ? c : c - part * N3p;
+  return part == 0 ? a.Fv : (part == 1 ? a.Fh : a.Fs);
+}
+template <bool ST, int PARTS>
+__device__ __forceinline__ float *z_part(const BlockDualArgs &a, int r, int c, int N3p, int &band) {
+  const int part = ST ? (r & 1) : c / N3p;
+  band = ST ? c : c - part * N3p;
+  return part == 0 ? a.Zv : (part == 1 ? a.Zh : a.Zs);
+}
+
+template <bool ST, int LT, int PARTS>
 __device__ void stream_chunk(const Layout &L, float *chunk, float *Yl, const BlockDualArgs &a, const int *pix,
                              int c0, bool form) {
   const Dims &dm = a.dm;
-  const int N3p = dm.N3p, W = ST ? N3p : 2 * N3p;
+  const int N3p = dm.N3p, W = ST ? N3p : PARTS * N3p;
   constexpr int Q = kCW / 4;
   for (int it = threadIdx.x; it < 4 * L.nt4 * Q; it += LT) {
     const int r = it / Q, q = it - r * Q, c = c0 + 4 * q;
@@ -124,11 +143,9 @@ __device__ void stream_chunk(const Layout &L, float *chunk, float *Yl, const Blo
       float *g = Yl + (size_t)r * W + c;
       y = *reinterpret_cast<const float4 *>(g);
       if (form) {
-        // paper layout: a row is one pixel, columns [v bands | h bands];
-        // stacked: rows 2r and 2r + 1 are the v and h bands of pixel r
-        const bool hz = ST ? (r & 1) != 0 : c >= N3p;
-        const float4 f = __ldg(reinterpret_cast<const float4 *>((hz ? a.Fh : a.Fv) + (size_t)pix[r] * N3p +
-                                                                (hz && !ST ? c - N3p : c)));
+        int band;
+        const float *F = f_part<ST, PARTS>(a, r, c, N3p, band);
+        const float4 f = __ldg(reinterpret_cast<const float4 *>(F + (size_t)pix[r] * N3p + band));
         y.x = fmaf(a.gY, f.x, y.x);
         y.y = fmaf(a.gY, f.y, y.y);
         y.z = fmaf(a.gY, f.z, y.z);
@@ -142,15 +159,15 @@ __device__ void stream_chunk(const Layout &L, float *chunk, float *Yl, const Blo
 
 // warps per CTA: stacked blocks of up to 64 rows (k <= 5) run four-warp CTAs,
 // four per SM; everything else eight-warp CTAs, two per SM
-template <int K, bool ST>
+template <int K, bool ST, int PARTS>
 __host__ __device__ constexpr int large_warps() {
-  return ST && 2 * K * K <= 64 ? 4 : kLW;
+  return (ST && 2 * K * K <= 64) || (PARTS == 3 && K * K <= 64) ? 4 : kLW;
 }
 
-template <int K, bool ST>
-__global__ void __launch_bounds__(large_warps<K, ST>() * 32, large_warps<K, ST>() == 4 ? 4 : 2)
+template <int K, bool ST, int PARTS>
+__global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32, large_warps<K, ST, PARTS>() == 4 ? 4 : 2)
     block_dual_large_kernel(BlockDualArgs a) {
-  constexpr int LW = large_warps<K, ST>(), LT = LW * 32;
+  constexpr int LW = large_warps<K, ST, PARTS>(), LT = LW * 32;
   constexpr int k = K;
   constexpr int NR = ST ? 2 * K * K : K * K;            // rows of a block matrix
   constexpr int NT4 = (((NR + 1) & ~1) + 3) / 4;
@@ -166,7 +183,7 @@ __global__ void __launch_bounds__(large_warps<K, ST>() * 32, large_warps<K, ST>(
   int *pix = reinterpret_cast<int *>(sm + L.pix);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const Dims dm = a.dm;
-  const int N3p = dm.N3p, W = ST ? N3p : 2 * N3p;
+  const int N3p = dm.N3p, W = ST ? N3p : PARTS * N3p;
   const long long Lb = dm.P;
   if (tid == 0) s_sweeps = 0u;
   const int n_upper = nt4 * (nt4 + 1) / 2;
@@ -192,7 +209,7 @@ __global__ void __launch_bounds__(large_warps<K, ST>() * 32, large_warps<K, ST>(
 #pragma unroll
       for (int e = 0; e < 16; ++e) acc[u][e] = 0.f;
     for (int c0 = 0; c0 < W; c0 += kCW) {
-      stream_chunk<ST, LT>(L, chunk, Yl, a, pix, c0, true);
+      stream_chunk<ST, LT, PARTS>(L, chunk, Yl, a, pix, c0, true);
       __syncthreads();
 #pragma unroll
       for (int u = 0; u < GT; ++u) {
@@ -491,7 +508,7 @@ __global__ void __launch_bounds__(large_warps<K, ST>() * 32, large_warps<K, ST>(
 
     // ---- 5b. Y_l = M Y' by chunks; Z += P_l^T Y_l ----
     for (int c0 = 0; c0 < W; c0 += kCW) {
-      stream_chunk<ST, LT>(L, chunk, Yl, a, pix, c0, false);
+      stream_chunk<ST, LT, PARTS>(L, chunk, Yl, a, pix, c0, false);
       __syncthreads();
       constexpr int Q = kCW / 4;
       for (int t = tid; t < nt4 * Q; t += LT) {
@@ -517,10 +534,10 @@ __global__ void __launch_bounds__(large_warps<K, ST>() * 32, large_warps<K, ST>(
           for (int p = 0; p < 4; ++p) {
             const int r = 4 * ti + p;
             if (r < n) {
-              const bool hz = ST ? (r & 1) != 0 : c >= N3p;
-              float *Zb = (hz ? a.Zh : a.Zv) + (hz && !ST ? c - N3p : c);
+              int band;
+              float *Zb = z_part<ST, PARTS>(a, r, c, N3p, band);
               __stcs(reinterpret_cast<float4 *>(Yl + (size_t)r * W + c), y[p]);
-              atomicAdd(reinterpret_cast<float4 *>(Zb + (size_t)pix[r] * N3p), y[p]);
+              atomicAdd(reinterpret_cast<float4 *>(Zb + (size_t)pix[r] * N3p + band), y[p]);
             }
           }
         }
@@ -544,26 +561,33 @@ long long block_dual_large_w_stride(int k, bool stacked) {
 
 long long block_dual_large_w_stride(int k) { return block_dual_large_w_stride(k, false); }
 
-int block_dual_large_threads(int k, bool stacked) { return stacked && 2 * k * k <= 64 ? 128 : kLT; }
+int block_dual_large_threads(int k, bool stacked, int parts) {
+  return (stacked && 2 * k * k <= 64) || (parts == 3 && k * k <= 64) ? 128 : kLT;
+}
 
 namespace {
 typedef void (*LargeKernel)(BlockDualArgs);
-LargeKernel large_kernel(int k, bool stacked) {
-  static const LargeKernel paper[] = {block_dual_large_kernel<6, false>,  block_dual_large_kernel<7, false>,
-                                      block_dual_large_kernel<8, false>,  block_dual_large_kernel<9, false>,
-                                      block_dual_large_kernel<10, false>, block_dual_large_kernel<11, false>,
-                                      block_dual_large_kernel<12, false>};
-  static const LargeKernel stack[] = {block_dual_large_kernel<1, true>, block_dual_large_kernel<2, true>,
-                                      block_dual_large_kernel<3, true>, block_dual_large_kernel<4, true>,
-                                      block_dual_large_kernel<5, true>, block_dual_large_kernel<6, true>,
-                                      block_dual_large_kernel<7, true>, block_dual_large_kernel<8, true>};
+LargeKernel large_kernel(int k, bool stacked, int parts) {
+  static const LargeKernel paper[] = {block_dual_large_kernel<6, false, 2>,  block_dual_large_kernel<7, false, 2>,
+                                      block_dual_large_kernel<8, false, 2>,  block_dual_large_kernel<9, false, 2>,
+                                      block_dual_large_kernel<10, false, 2>, block_dual_large_kernel<11, false, 2>,
+                                      block_dual_large_kernel<12, false, 2>};
+  static const LargeKernel stack[] = {block_dual_large_kernel<1, true, 2>, block_dual_large_kernel<2, true, 2>,
+                                      block_dual_large_kernel<3, true, 2>, block_dual_large_kernel<4, true, 2>,
+                                      block_dual_large_kernel<5, true, 2>, block_dual_large_kernel<6, true, 2>,
+                                      block_dual_large_kernel<7, true, 2>, block_dual_large_kernel<8, true, 2>};
+  static const LargeKernel three[] = {block_dual_large_kernel<1, false, 3>, block_dual_large_kernel<2, false, 3>,
+                                      block_dual_large_kernel<3, false, 3>, block_dual_large_kernel<4, false, 3>,
+                                      block_dual_large_kernel<5, false, 3>, block_dual_large_kernel<6, false, 3>,
+                                      block_dual_large_kernel<7, false, 3>, block_dual_large_kernel<8, false, 3>};
+  if (parts == 3) return !stacked && k >= 1 && k <= kMaxStackedK ? three[k - 1] : nullptr;
   if (stacked) return k >= 1 && k <= kMaxStackedK ? stack[k - 1] : nullptr;
   return k >= kMinLargeK && k <= kMaxLargeK ? paper[k - kMinLargeK] : nullptr;
 }
 }  // namespace
 
-cudaError_t block_dual_large_prepare(int k, bool stacked, size_t smem) {
-  const LargeKernel f = large_kernel(k, stacked);
+cudaError_t block_dual_large_prepare(int k, bool stacked, size_t smem, int parts) {
+  const LargeKernel f = large_kernel(k, stacked, parts);
   if (!f) return cudaErrorInvalidValue;
   int dev = 0, cap = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -576,17 +600,17 @@ cudaError_t block_dual_large_prepare(int k, bool stacked, size_t smem) {
   return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
 }
 
-cudaError_t block_dual_large_occupancy(int k, bool stacked, size_t smem, int *ctas) {
-  const LargeKernel f = large_kernel(k, stacked);
+cudaError_t block_dual_large_occupancy(int k, bool stacked, size_t smem, int *ctas, int parts) {
+  const LargeKernel f = large_kernel(k, stacked, parts);
   if (!f) return cudaErrorInvalidValue;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, f, block_dual_large_threads(k, stacked), smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, f, block_dual_large_threads(k, stacked, parts), smem);
 }
 
 cudaError_t launch_block_dual_large(const BlockDualArgs &a, int k, bool stacked, int grid, size_t smem,
-                                    cudaStream_t st) {
-  const LargeKernel f = large_kernel(k, stacked);
+                                    cudaStream_t st, int parts) {
+  const LargeKernel f = large_kernel(k, stacked, parts);
   if (!f) return cudaErrorInvalidValue;
-  f<<<grid, block_dual_large_threads(k, stacked), smem, st>>>(a);
+  f<<<grid, block_dual_large_threads(k, stacked, parts), smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(256) primal_kernel(PrimalArgs a) {
     const size_t pjm = ((size_t)i * N2 + (j == 0 ? N2 - 1 : j - 1)) * N3p + b0;
     st4(a.Znv + p0, zero4);
     st4(a.Znh + p0, zero4);
+    if (a.Zns) st4(a.Zns + p0, zero4);
     // w = D_v^T Zv + D_h^T Zh at bands b0..b0+3 and at the band before b0
     // (periodic over the N3 true bands)
     const float4 zv = ld4(a.Zv + p0), zvm = ld4(a.Zv + pim), zh = ld4(a.Zh + p0), zhm = ld4(a.Zh + pjm);
@@ -96,6 +97,8 @@ __global__ void __launch_bounds__(256) primal_kernel(PrimalArgs a) {
         float grad = a.no_ds ? w[e] : (e == 0 ? wbm : w[e - 1]) - w[e];
         if (a.Z1v)  // HSSTV: + omega D^T (Y1v, Y1h), first-order, no D_s
           grad = fmaf(a.w1, (a.Z1v[pim + e] - a.Z1v[p0 + e]) + (a.Z1h[pjm + e] - a.Z1h[p0 + e]), grad);
+        if (a.Zs)  // SSST: + D_s^T Zs, (D_s^T z)[b] = z[b-1] - z[b] (periodic)
+          grad += a.Zs[p0 + (b0 + e == 0 ? dm.N3 - 1 - b0 : e - 1)] - a.Zs[p0 + e];
         const float y3 = c3 * comp(d4, e);
         const float u = comp(u4, e);
         const float x = u - a.gu * (grad + y3);
@@ -245,59 +248,62 @@ __global__ void unpad_cube_kernel(const float *__restrict__ src, float *__restri
 // (v_b, h_b); stacked layout [L][2 k^2][N3] (row 2r + o, band b).  Internal:
 // [L][k^2][2][N3p] for both.
 __global__ void Y_to_internal_kernel(const float *__restrict__ ext, float *__restrict__ in, Dims dm, int n,
-                                     int stacked) {
-  const long long total = dm.P * n * 2 * dm.N3p;
+                                     int stacked, int parts) {
+  const long long total = dm.P * n * parts * dm.N3p;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
-    const long long row = idx / (2 * dm.N3p);
-    const int rem = (int)(idx - row * 2 * dm.N3p);
-    const int o = rem >= dm.N3p;
+    const long long row = idx / (parts * dm.N3p);
+    const int rem = (int)(idx - row * parts * dm.N3p);
+    const int o = rem / dm.N3p;
     const int b = rem - o * dm.N3p;
-    in[idx] = b < dm.N3 ? ext[stacked ? (2 * row + o) * dm.N3 + b : row * 2 * dm.N3 + 2 * b + o] : 0.f;
+    in[idx] = b < dm.N3 ? ext[stacked ? (2 * row + o) * dm.N3 + b : row * parts * dm.N3 + parts * b + o] : 0.f;
   }
 }
 
 __global__ void Y_to_external_kernel(const float *__restrict__ in, float *__restrict__ ext, Dims dm, int n,
-                                     int stacked) {
-  const long long total = dm.P * n * 2 * dm.N3;
+                                     int stacked, int parts) {
+  const long long total = dm.P * n * parts * dm.N3;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
-    const long long row = idx / (2 * dm.N3);
-    const int col = (int)(idx - row * 2 * dm.N3);
-    const int b = stacked ? col % dm.N3 : col >> 1, o = stacked ? col / dm.N3 : col & 1;
-    ext[idx] = in[row * 2 * dm.N3p + (long long)o * dm.N3p + b];
+    const long long row = idx / (parts * dm.N3);
+    const int col = (int)(idx - row * parts * dm.N3);
+    const int b = stacked ? col % dm.N3 : col / parts, o = stacked ? col / dm.N3 : col % parts;
+    ext[idx] = in[row * parts * dm.N3p + (long long)o * dm.N3p + b];
   }
 }
 
 // Z = sum_l P_l^T Y_l by gathering, for each pixel, the rows of the k^2 blocks
 // that cover it (used when a caller replaces Y).
 __global__ void Z_from_Y_kernel(const float *__restrict__ Y, float *__restrict__ Zv, float *__restrict__ Zh,
-                                Dims dm, int k) {
+                                Dims dm, int k, float *__restrict__ Zs) {
+  const int parts = Zs ? 3 : 2;
   const int n = k * k;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < dm.Np; idx += stride) {
     const long long pix = idx / dm.N3p;
     const int b = (int)(idx - pix * dm.N3p);
     const int i = (int)(pix / dm.N2), j = (int)(pix - (long long)i * dm.N2);
-    float zv = 0.f, zh = 0.f;
+    float zv = 0.f, zh = 0.f, zs = 0.f;
     for (int aa = 0; aa < k; ++aa) {
       const int ii = (i - aa + dm.N1) % dm.N1;
       for (int cc = 0; cc < k; ++cc) {
         const int jj = (j - cc + dm.N2) % dm.N2;
-        const long long base = (((long long)ii * dm.N2 + jj) * n + aa * k + cc) * 2 * dm.N3p;
+        const long long base = (((long long)ii * dm.N2 + jj) * n + aa * k + cc) * parts * dm.N3p;
         zv += Y[base + b];
         zh += Y[base + dm.N3p + b];
+        if (Zs) zs += Y[base + 2 * dm.N3p + b];
       }
     }
     Zv[idx] = zv;
     Zh[idx] = zh;
+    if (Zs) Zs[idx] = zs;
   }
 }
 
 // Fv = D_v D_s ubar and Fh = D_h D_s ubar: the second-order differences the
 // structure tensors of eq. (SSST) are cut from, formed once per pass.
 __global__ void xfield_kernel(const float *__restrict__ ubar, float *__restrict__ Fv, float *__restrict__ Fh,
-                              Dims dm, int open_s, int first_order) {
+                              Dims dm, int open_s, int first_order, float *__restrict__ Fs) {
   const int N3p = dm.N3p, C4 = N3p >> 2, N2 = dm.N2;
   const int nch = (int)(dm.P * C4);
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nch; c += gridDim.x * blockDim.x) {
@@ -310,14 +316,16 @@ __global__ void xfield_kernel(const float *__restrict__ ubar, float *__restrict_
     const float4 x0 = ld4(ubar + p0 + b0), xv = ld4(ubar + pv + b0), xh = ld4(ubar + ph + b0);
     const int nb = b0 + 4 < dm.N3 ? b0 + 4 : 0;
     const float n0 = ubar[p0 + nb], nv = ubar[pv + nb], nh = ubar[ph + nb];
-    float fv[4], fh[4];
+    float fv[4], fh[4], fs[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
+      fs[e] = 0.f;
       if (b0 + e < dm.N3 - open_s) {  // open D_s: no difference past the last band
         const bool in = e < 3 && b0 + e + 1 < dm.N3;
-        if (first_order) {  // STV: D_v u, D_h u
+        if (first_order) {  // STV: D_v u, D_h u (SSST: and D_s u)
           fv[e] = comp(xv, e) - comp(x0, e);
           fh[e] = comp(xh, e) - comp(x0, e);
+          fs[e] = (in ? comp(x0, e + 1) : n0) - comp(x0, e);
         } else {
           const float ds0 = (in ? comp(x0, e + 1) : n0) - comp(x0, e);
           fv[e] = ((in ? comp(xv, e + 1) : nv) - comp(xv, e)) - ds0;
@@ -329,6 +337,7 @@ __global__ void xfield_kernel(const float *__restrict__ ubar, float *__restrict_
     }
     st4(Fv + p0 + b0, make_float4(fv[0], fv[1], fv[2], fv[3]));
     st4(Fh + p0 + b0, make_float4(fh[0], fh[1], fh[2], fh[3]));
+    if (Fs) st4(Fs + p0 + b0, make_float4(fs[0], fs[1], fs[2], fs[3]));
   }
 }
 
@@ -478,24 +487,26 @@ cudaError_t launch_unpad_cube(const float *src, float *dst, Dims dm, const doubl
   return cudaGetLastError();
 }
 
-cudaError_t launch_Y_to_internal(const float *ext, float *in, Dims dm, int k, cudaStream_t st, int stacked) {
-  Y_to_internal_kernel<<<grid_for(dm.P * k * k * 2 * dm.N3p), 256, 0, st>>>(ext, in, dm, k * k, stacked);
+cudaError_t launch_Y_to_internal(const float *ext, float *in, Dims dm, int k, cudaStream_t st, int stacked,
+                                 int parts) {
+  Y_to_internal_kernel<<<grid_for(dm.P * k * k * parts * dm.N3p), 256, 0, st>>>(ext, in, dm, k * k, stacked, parts);
   return cudaGetLastError();
 }
 
-cudaError_t launch_Y_to_external(const float *in, float *ext, Dims dm, int k, cudaStream_t st, int stacked) {
-  Y_to_external_kernel<<<grid_for(dm.P * k * k * 2 * dm.N3), 256, 0, st>>>(in, ext, dm, k * k, stacked);
+cudaError_t launch_Y_to_external(const float *in, float *ext, Dims dm, int k, cudaStream_t st, int stacked,
+                                 int parts) {
+  Y_to_external_kernel<<<grid_for(dm.P * k * k * parts * dm.N3), 256, 0, st>>>(in, ext, dm, k * k, stacked, parts);
   return cudaGetLastError();
 }
 
 cudaError_t launch_xfield(const float *ubar, float *Fv, float *Fh, Dims dm, int grid, cudaStream_t st, int open_s,
-                          int first_order) {
-  xfield_kernel<<<grid, 256, 0, st>>>(ubar, Fv, Fh, dm, open_s, first_order);
+                          int first_order, float *Fs) {
+  xfield_kernel<<<grid, 256, 0, st>>>(ubar, Fv, Fh, dm, open_s, first_order, Fs);
   return cudaGetLastError();
 }
 
-cudaError_t launch_Z_from_Y(const float *Y, float *Zv, float *Zh, Dims dm, int k, cudaStream_t st) {
-  Z_from_Y_kernel<<<grid_for(dm.Np), 256, 0, st>>>(Y, Zv, Zh, dm, k);
+cudaError_t launch_Z_from_Y(const float *Y, float *Zv, float *Zh, Dims dm, int k, cudaStream_t st, float *Zs) {
+  Z_from_Y_kernel<<<grid_for(dm.Np), 256, 0, st>>>(Y, Zv, Zh, dm, k, Zs);
   return cudaGetLastError();
 }
 

@@ -127,10 +127,10 @@ __global__ void __launch_bounds__(256) ssim_kernel(const float *u, const float *
 constexpr int kObjCW = 32;
 
 __global__ void __launch_bounds__(256) objective_kernel(const float *u, int N1, int N2, int N3, int k, int stacked,
-                                                       int open_s, int first_order, double tol, int max_sweeps,
-                                                       double *out, unsigned *nonconv) {
+                                                       int open_s, int first_order, int parts, double tol,
+                                                       int max_sweeps, double *out, unsigned *nonconv) {
   extern __shared__ double dsm[];
-  const int n = stacked ? 2 * k * k : k * k, NP = n + (n & 1), W = stacked ? N3 : 2 * N3;
+  const int n = stacked ? 2 * k * k : k * k, NP = n + (n & 1), W = stacked ? N3 : parts * N3;
   double *G = dsm;                 // NP x n
   double *X = dsm + (size_t)NP * n;  // n x kObjCW
   __shared__ double nrm[kMaxLargeK * kMaxLargeK];  // >= 2 kMaxStackedK^2 rows too
@@ -146,16 +146,19 @@ __global__ void __launch_bounds__(256) objective_kernel(const float *u, int N1, 
       for (int e = tid; e < n * kObjCW; e += 256) {
         const int r = e / kObjCW, cc = e - r * kObjCW, col = c0 + cc;
         double x = 0.0;
-        // paper layout: row r is window pixel r, column 2b + o; stacked: row
-        // 2r + o is pixel r, column b; o = 0 vertical, 1 horizontal
-        const int pr = stacked ? r >> 1 : r, o = stacked ? r & 1 : col & 1, b = stacked ? col : col >> 1;
+        // paper layout: row r is window pixel r, column parts * b + o; stacked:
+        // row 2r + o is pixel r, column b; o = 0 vertical, 1 horizontal, 2
+        // spectral (SSST)
+        const int pr = stacked ? r >> 1 : r, o = stacked ? r & 1 : col % parts, b = stacked ? col : col / parts;
         if (col < W && !(open_s && b == N3 - 1)) {
           const int a = pr / k, c = pr - a * k;
           const int i = (p + a) % N1, j = (q + c) % N2;
           const int i1 = i + 1 == N1 ? 0 : i + 1, j1 = j + 1 == N2 ? 0 : j + 1, b1 = b + 1 == N3 ? 0 : b + 1;
           const size_t s00 = ((size_t)i * N2 + j) * N3;
           const size_t s10 = o ? ((size_t)i * N2 + j1) * N3 : ((size_t)i1 * N2 + j) * N3;
-          if (first_order) {  // STV: D_v u or D_h u
+          if (o == 2) {  // SSST: D_s u
+            x = (double)u[s00 + b1] - (double)u[s00 + b];
+          } else if (first_order) {  // STV, SSST: D_v u or D_h u
             x = (double)u[s10 + b] - (double)u[s00 + b];
           } else {
             const double ds0 = (double)u[s00 + b1] - (double)u[s00 + b];
@@ -367,13 +370,14 @@ size_t objective_smem_bytes(int k, int stacked) {
 }
 
 cudaError_t launch_objective(const float *u, int N1, int N2, int N3, int k, int stacked, int open_s,
-                             int first_order, double *out, unsigned *nonconv, int grid, cudaStream_t st) {
+                             int first_order, double *out, unsigned *nonconv, int grid, cudaStream_t st,
+                             int parts) {
   const size_t smem = objective_smem_bytes(k, stacked);
   cudaError_t e = cudaFuncSetAttribute(objective_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long L = (long long)N1 * N2;
   objective_kernel<<<(unsigned)(L < grid ? L : grid), 256, smem, st>>>(u, N1, N2, N3, k, stacked, open_s, first_order,
-                                                                       1e-13, 60, out, nonconv);
+                                                                       parts, 1e-13, 60, out, nonconv);
   return cudaGetLastError();
 }
 

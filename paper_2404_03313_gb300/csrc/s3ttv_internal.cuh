@@ -78,6 +78,8 @@ struct PrimalArgs {
   int no_ds;              // 1: the dual term is D^T Z (STV's first-order tensors), no D_s^T
   const float *Z1v = nullptr, *Z1h = nullptr;  // HSSTV: first-order dual pair, adds w1 D^T Z1
   float w1 = 0.f;
+  const float *Zs = nullptr;  // SSST: the spectral part, adds D_s^T Zs
+  float *Zns = nullptr;       // its next accumulation target, zeroed here
 };
 cudaError_t launch_primal(const PrimalArgs &a, int grid, cudaStream_t st);
 
@@ -131,6 +133,8 @@ struct BlockDualArgs {
   float *W;               // per-block warm-start rows [L][w_stride] (may be null)
   long long w_stride;     // floats per block in W (>= NPOS * k*k)
   int warm;               // 1: start from the rows stored in W
+  const float *Fs = nullptr;  // SSST's third part D_s ubar (per-CTA kernel, three parts)
+  float *Zs = nullptr;        // and its accumulation
 };
 // floats per block of the warm-start rows
 long long block_dual_w_stride(int k);
@@ -157,27 +161,31 @@ bool block_dual_has(const BdVariant &v);  // compiled in this build
 // and 2r + 1 the vertical and horizontal differences of window pixel r) for
 // k = 1..kMaxStackedK; the block memory [L][k^2][2][N3p] is the same.
 constexpr int kMinLargeK = 6, kMaxLargeK = 12, kMaxStackedK = 8;
+// parts = 3: SSST's rows [D_v u, D_h u, D_s u] (paper layout, k <= kMaxStackedK)
 size_t block_dual_large_smem_bytes(int k, bool stacked);
 long long block_dual_large_w_stride(int k, bool stacked);
 long long block_dual_large_w_stride(int k);  // paper layout
-int block_dual_large_threads(int k, bool stacked);
-cudaError_t block_dual_large_prepare(int k, bool stacked, size_t smem_bytes);
-cudaError_t block_dual_large_occupancy(int k, bool stacked, size_t smem_bytes, int *ctas_per_sm);
+int block_dual_large_threads(int k, bool stacked, int parts = 2);
+cudaError_t block_dual_large_prepare(int k, bool stacked, size_t smem_bytes, int parts = 2);
+cudaError_t block_dual_large_occupancy(int k, bool stacked, size_t smem_bytes, int *ctas_per_sm, int parts = 2);
 cudaError_t launch_block_dual_large(const BlockDualArgs &a, int k, bool stacked, int grid, size_t smem,
-                                    cudaStream_t st);
+                                    cudaStream_t st, int parts = 2);
 cudaError_t block_dual_prepare(const BdVariant &v, size_t smem_bytes);
 cudaError_t block_dual_occupancy(const BdVariant &v, size_t smem_bytes, int *ctas_per_sm);
 
 // Layout conversion and small helpers.
 cudaError_t launch_pad_cube(const float *src, float *dst, Dims dm, float scale, cudaStream_t st);
 cudaError_t launch_unpad_cube(const float *src, float *dst, Dims dm, const double *scale_dev, cudaStream_t st);
-cudaError_t launch_Y_to_internal(const float *ext, float *in, Dims dm, int k, cudaStream_t st, int stacked);
-cudaError_t launch_Y_to_external(const float *in, float *ext, Dims dm, int k, cudaStream_t st, int stacked);
+cudaError_t launch_Y_to_internal(const float *ext, float *in, Dims dm, int k, cudaStream_t st, int stacked,
+                                 int parts = 2);
+cudaError_t launch_Y_to_external(const float *in, float *ext, Dims dm, int k, cudaStream_t st, int stacked,
+                                 int parts = 2);
 // Fv = D_v D_s ubar, Fh = D_h D_s ubar (Sec. II-A differences, periodic)
 // open_s: the spectral difference stops at the last band (F's last band is 0)
-// first_order: F = (D_v u, D_h u) (STV) instead of the second-order differences
+// first_order: F = (D_v u, D_h u) (STV) instead of the second-order differences;
+// with Fs as well, SSST's first-order parts (D_v u, D_h u, D_s u)
 cudaError_t launch_xfield(const float *ubar, float *Fv, float *Fh, Dims dm, int grid, cudaStream_t st,
-                         int open_s, int first_order);
+                         int open_s, int first_order, float *Fs = nullptr);
 // SSTV's dual step: Y = clip(Y + gamma_Y D D_s ubar, -1, 1) on the cube pair
 // (Yv, Yh), and Z = Y
 cudaError_t launch_sstv_dual(const float *ubar, float *Yv, float *Yh, float *Zv, float *Zh, Dims dm, float gY,
@@ -186,7 +194,8 @@ cudaError_t launch_sstv_dual(const float *ubar, float *Yv, float *Yh, float *Zv,
 // first-order pair): l1 (l12 = 0) or per-voxel l1,2 (l12 = 1) conjugate prox
 cudaError_t launch_hsstv_dual(const float *ubar, float *Y, float *Zv, float *Zh, Dims dm, float gY, float omega,
                               int l12, int grid, cudaStream_t st);
-cudaError_t launch_Z_from_Y(const float *Y, float *Zv, float *Zh, Dims dm, int k, cudaStream_t st);
+cudaError_t launch_Z_from_Y(const float *Y, float *Zv, float *Zh, Dims dm, int k, cudaStream_t st,
+                            float *Zs = nullptr);
 cudaError_t launch_init_scalars(Scalars *sc, double alpha, double beta, cudaStream_t st);
 
 // evaluation (metrics.cu); plain [N1][N2][N3] cubes, FP64 sums
@@ -197,9 +206,10 @@ cudaError_t launch_sam(const float *u, const float *ref, long long P, int N3, fl
                        cudaStream_t st);
 cudaError_t launch_ssim(const float *u, const float *ref, int N1, int N2, int N3, int b0, int nb, double *out,
                         int grid, cudaStream_t st);
-size_t objective_smem_bytes(int k, int stacked);
+size_t objective_smem_bytes(int k, int stacked);  // rows: k^2 or 2k^2
 cudaError_t launch_objective(const float *u, int N1, int N2, int N3, int k, int stacked, int open_s,
-                             int first_order, double *out, unsigned *nonconv, int grid, cudaStream_t st);
+                             int first_order, double *out, unsigned *nonconv, int grid, cudaStream_t st,
+                             int parts = 2);
 cudaError_t launch_sstv_l1(const float *u, int N1, int N2, int N3, double *out, int grid, cudaStream_t st);
 cudaError_t launch_hsstv_norm(const float *u, int N1, int N2, int N3, double omega, int l12, double *out, int grid,
                               cudaStream_t st);

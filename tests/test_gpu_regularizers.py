@@ -1,8 +1,9 @@
 """GPU parity of the comparison regularisers the paper runs through the same
 P-PDS (Sec. IV): STV (block nuclear norms of first-order spatial differences),
-SSTV (l1 norm of D D_s u) and HSSTV1 / HSSTV2 (SSTV plus omega-weighted
-first-order differences, l1 or per-voxel l1,2), against the FP64 oracle through
-the C ABI.
+SSTV (l1 norm of D D_s u), HSSTV1 / HSSTV2 (SSTV plus omega-weighted
+first-order differences, l1 or per-voxel l1,2) and SSST (block nuclear norms of
+first-order spatial and spectral differences, k^2 x 3N3 blocks), against the
+FP64 oracle through the C ABI.
 
 Tolerances as in test_gpu_parity: one pass from a random state, relative L2
 1e-5 per state (SSTV's clip is exact; STV's blocks have k^2 = 9 rows); after
@@ -17,7 +18,7 @@ from synthetic import WORKLOADS, make_cube, random_state
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-REGS = ["stv", "sstv", "hsstv1", "hsstv2"]
+REGS = ["stv", "sstv", "hsstv1", "hsstv2", "ssst"]
 
 
 def rel(a, b):
@@ -39,7 +40,7 @@ def P():
 def solver_for(P, reg):
     s = P.Solver(0)
     s.set_option(P.OPT_REGULARIZER, {"stv": P.REG_STV, "sstv": P.REG_SSTV, "hsstv1": P.REG_HSSTV1,
-                                      "hsstv2": P.REG_HSSTV2}[reg])
+                                      "hsstv2": P.REG_HSSTV2, "ssst": P.REG_SSST}[reg])
     return s
 
 
@@ -51,6 +52,8 @@ def test_one_pass_from_a_random_state(P, reg):
     v = r.uniform(0, 1, (N1, N2, N3)).astype(np.float32)
     if reg in ("sstv", "hsstv1", "hsstv2"):
         st["Y"] = (0.3 * r.standard_normal((2 if reg == "sstv" else 4, N1, N2, N3))).astype(np.float32)
+    if reg == "ssst":
+        st["Y"] = (0.3 * r.standard_normal((N1 * N2, k * k, 3 * N3))).astype(np.float32)
     eps, alpha, beta = 3.0, 20.0, 10.0
     ref_state = {key: val.astype(np.float64) for key, val in st.items()}
     gam = O.step_sizes(N1, N2, k, "paper", reg)
