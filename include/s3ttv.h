@@ -377,6 +377,16 @@ int s3ttv_radii(long long N, double sigma, double p_s, double p_t, double rho,
  * written to gammas[6] (host). */
 int s3ttv_step_sizes(int N1, int N2, int k, int policy, double gammas[6]);
 
+/* The FP32 arithmetic rate of a device, measured (the denominator of the ALU
+ * roofline of the eigen-solve-bound block-dual kernels): every thread of a full
+ * grid (8 CTAs of 256 threads per SM) runs 8 independent chains of FMAs, scalar
+ * (packed = 0) or packed FP32x2 (packed = 1), sized until one launch takes
+ * 20 ms; *tflops = 2 flops per lane FMA / the CUDA-event time of that launch.
+ * Synchronous, on a stream of its own; changes no device setting.  tflops is a
+ * host pointer.  S3TTV_EINVAL for a NULL pointer or packed not 0/1,
+ * S3TTV_ECUDA when the device cannot run it. */
+int s3ttv_fp32_peak(int device, int packed, double *tflops);
+
 /* ---------------------------------------------------------------------------
  * Learned warm start.  The paper has no network: Alg. 1 starts from u = v,
  * s = t = 0.  These entry points train and run a small 3-D convolutional U-Net

@@ -7,7 +7,7 @@ applies the learned warm start (a 3-D U-Net, also on the library's kernels).  No
 CPU: if the library is not built, calls raise ``S3TTVError``.
 """
 from ._binding import (  # noqa: F401
-    Info, S3TTVError, Solver, WarmStartNet, library, radii, step_sizes, l1_ball_static, LIB_PATH, SIGNATURES, STATE,
+    Info, S3TTVError, Solver, WarmStartNet, library, radii, step_sizes, l1_ball_static, fp32_peak, LIB_PATH, SIGNATURES, STATE,
     L1_STATIC_MAX_N, ETOOBIG,
     STEP_PAPER, STEP_PC_EXACT, OPT_STEP_POLICY, OPT_CHECK_EVERY, OPT_JACOBI_MAX_SWEEPS, OPT_JACOBI_TOL,
     OPT_PROFILE, OPT_WARM_START, OPT_TENSOR_CORES, OPT_LAYOUT, OPT_SPECTRAL_BOUNDARY, LAYOUT_PAPER,

@@ -54,6 +54,7 @@ class Problem(ctypes.Structure):
 _P = ctypes.POINTER
 SIGNATURES = {
     "s3ttv_create": (_c_int, [_P(_vp), _c_int, _vp]),
+    "s3ttv_fp32_peak": (_c_int, [_c_int, _c_int, _P(_c_d)]),
     "s3ttv_destroy": (None, [_vp]),
     "s3ttv_strerror": (ctypes.c_char_p, [_c_int]),
     "s3ttv_last_error": (ctypes.c_char_p, [_vp]),
@@ -187,6 +188,16 @@ def step_sizes(N1, N2, k, policy=STEP_PAPER):
     if rc:
         raise S3TTVError(rc, "s3ttv_step_sizes")
     return dict(zip(("u", "s", "t", "Y", "y2", "y3"), list(g)))
+
+
+def fp32_peak(device=0, packed=False):
+    """Measured FP32 rate of the device in TFLOP/s (s3ttv_fp32_peak): scalar or
+    packed FP32x2 FMA chains over a full grid."""
+    t = ctypes.c_double()
+    rc = library().s3ttv_fp32_peak(int(device), 1 if packed else 0, ctypes.byref(t))
+    if rc:
+        raise S3TTVError(rc, "s3ttv_fp32_peak")
+    return t.value
 
 
 class Solver:

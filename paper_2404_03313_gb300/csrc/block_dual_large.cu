@@ -119,13 +119,13 @@ __device__ __forceinline__ void upper_tile(int t, int nt4, int &ti, int &tj) {
 // bands per row ([v | h] or SSST's [v | h | s]); stacked, rows 2r, 2r + 1
 template <bool ST, int PARTS>
 __device__ __forceinline__ const float *f_part(const BlockDualArgs &a, int r, int c, int N3p, int &band) {
-  const int part = ST ? (r & 1) : c / N3p;
+  const int part = ST ? (r & 1) : (c >= N3p) + (PARTS == 3 && c >= 2 * N3p);
   band = ST ? c : c - part * N3p;
   return part == 0 ? a.Fv : (part == 1 ? a.Fh : a.Fs);
 }
 template <bool ST, int PARTS>
 __device__ __forceinline__ float *z_part(const BlockDualArgs &a, int r, int c, int N3p, int &band) {
-  const int part = ST ? (r & 1) : c / N3p;
+  const int part = ST ? (r & 1) : (c >= N3p) + (PARTS == 3 && c >= 2 * N3p);
   band = ST ? c : c - part * N3p;
   return part == 0 ? a.Zv : (part == 1 ? a.Zh : a.Zs);
 }

@@ -72,6 +72,12 @@ WORKLOADS = {
                                       p_s=0.05, p_t=0.05, k=10, seed=0),
     "paper_120x120x98_k10": CubeSpec(120, 120, 98, regions=8, endmembers=5, sigma=0.1,
                                      p_s=0.05, p_t=0.05, k=10, seed=0),
+    "paper_100x100x128_k10": CubeSpec(100, 100, 128, regions=8, endmembers=5, sigma=0.1,
+                                      p_s=0.05, p_t=0.05, k=10, seed=0),
+    "paper_120x120x198_k10": CubeSpec(120, 120, 198, regions=8, endmembers=5, sigma=0.1,
+                                      p_s=0.05, p_t=0.05, k=10, seed=0),
+    "paper_100x100x360_k10": CubeSpec(100, 100, 360, regions=8, endmembers=5, sigma=0.1,
+                                      p_s=0.05, p_t=0.05, k=10, seed=0),
 }
 
 
