@@ -315,7 +315,7 @@ int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, BdShape *sh) {
     return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: SSST supports k <= %d", k, kMaxStackedK);
   if (stacked || parts == 3 || k >= kMinLargeK) {  // one CTA per block at a time; FP32 CUDA cores
     sh->large = true;
-    sh->smem = block_dual_large_smem_bytes(k, stacked);
+    sh->smem = block_dual_large_smem_bytes(k, stacked, parts);
     int dev_max = 0;
     cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
     if (sh->smem > (size_t)dev_max)

@@ -17,7 +17,8 @@
 //     NaN marker in W starts cold from C0 = G).
 //  3. One-sided (Hestenes) Jacobi on the rows of C, resident in shared memory,
 //     in the round-robin ordering: each of the NPOS - 1 steps of a sweep meets
-//     NPOS / 2 disjoint row pairs, kPG lanes per pair and four pairs per warp
+//     NPOS / 2 disjoint row pairs, a group of 8 lanes per pair (4 where that
+//     lets one round of the warps cover a step) and 32 / group pairs per warp
 //     side by side (a dot product over the group, then the rotation of both
 //     rows, held in registers, written back in place); rows never move, only
 //     the pairing changes.  Rows are scaled by an exact
@@ -43,7 +44,12 @@ constexpr int kLW = 8;         // warps per CTA (two CTAs per SM where shared me
 constexpr int kLT = kLW * 32;  // threads per CTA
 constexpr int kCW = 48;        // columns of Y' per streamed chunk
 constexpr int kSlots = (kMaxLargeK * kMaxLargeK + 31) / 32;  // row elements a lane holds
-constexpr int kPG = 8;                                        // lanes per row pair in the Jacobi
+
+// Lanes per row pair in the Jacobi: 8, or 4 where that lets one round of the
+// CTA's warps cover every pair of a step (n / 2 pairs) and 8 would need more.
+__host__ __device__ constexpr int pair_lanes(int n, int lw) {
+  return ((n + 1) / 2 + lw * 8 - 1) / (lw * 8) < ((n + 1) / 2 + lw * 4 - 1) / (lw * 4) ? 4 : 8;
+}
 
 // Two FP32 values in one 64-bit register pair, and the packed FP32x2
 // arithmetic of sm_100 and later (each lane rounds as its scalar counterpart).
@@ -76,16 +82,16 @@ struct Layout {
 };
 
 // n: rows of a block matrix (k^2 in the paper's layout, 2 k^2 stacked)
-__host__ __device__ inline Layout layout(int n) {
+__host__ __device__ inline Layout layout(int n, int pg) {
   Layout L;
   L.n = n;
   L.npos = (L.n + 1) & ~1;
   L.nt4 = (L.npos + 3) / 4;
   const int w = 4 * L.nt4;  // rows and columns rounded to whole tiles
-  // a multiple of 4 (float4 rows) and 16 mod 32: consecutive rows start 16
-  // banks apart, so the two 8-lane Jacobi groups of a half-warp, which read
-  // neighbouring rows, touch disjoint banks
-  L.gs = w + (16 - w % 32 + 32) % 32;
+  // a multiple of 4 (float4 rows) and 2 pg mod 32: consecutive rows start
+  // 2 pg banks apart, so the pg-lane Jacobi groups of a warp, which read
+  // neighbouring rows (2 pg floats each), fill the 32 banks without conflicts
+  L.gs = w + (2 * pg - w % 32 + 32) % 32;
   L.cs = kCW + 4;
   L.x1 = 0;
   L.x2 = L.x1 + (size_t)w * L.gs;
@@ -165,19 +171,21 @@ __host__ __device__ constexpr int large_warps() {
 }
 
 template <int K, bool ST, int PARTS>
-__global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32, large_warps<K, ST, PARTS>() == 4 ? 4 : 2)
+__global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
+                                  large_warps<K, ST, PARTS>() == 4 ? 4 : ((ST ? 2 * K * K : K * K) > 100 ? 1 : 2))
     block_dual_large_kernel(BlockDualArgs a) {
   constexpr int LW = large_warps<K, ST, PARTS>(), LT = LW * 32;
   constexpr int k = K;
   constexpr int NR = ST ? 2 * K * K : K * K;            // rows of a block matrix
   constexpr int NT4 = (((NR + 1) & ~1) + 3) / 4;
   constexpr int GT = (NT4 * (NT4 + 1) / 2 + LT - 1) / LT;  // upper-triangle Gram tiles per thread
-  constexpr int PE2 = (NR + 2 * kPG - 1) / (2 * kPG);  // float2 pieces of a row a Jacobi lane holds
+  constexpr int PG = pair_lanes(NR, LW);               // lanes per row pair in the Jacobi
+  constexpr int PE2 = (NR + 2 * PG - 1) / (2 * PG);    // float2 pieces of a row a Jacobi lane holds
   extern __shared__ __align__(16) float sm[];
   __shared__ float s_red[LW];
   __shared__ unsigned s_sweeps;
   if (a.sc->done) return;
-  const Layout L = layout(NR);
+  const Layout L = layout(NR, PG);
   const int n = L.n, NP = L.npos, GS = L.gs, nt4 = L.nt4;
   float *X1 = sm + L.x1, *X2 = sm + L.x2, *chunk = sm + L.chunk, *nrm = sm + L.nrm;
   int *pix = reinterpret_cast<int *>(sm + L.pix);
@@ -340,10 +348,10 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32, large_warps<
       if (sw) norms();
       int rotated = 0;
       for (int step = 0; step < NP - 1; ++step) {
-        // kPG lanes per pair, 32 / kPG pairs per warp side by side
-        for (int base = 0; base < NP / 2; base += LW * (32 / kPG)) {
-          if (base + warp * (32 / kPG) >= NP / 2) continue;  // the whole warp has no pair this round
-          const int i = base + warp * (32 / kPG) + (lane / kPG), gl = lane % kPG;
+        // PG lanes per pair, 32 / PG pairs per warp side by side
+        for (int base = 0; base < NP / 2; base += LW * (32 / PG)) {
+          if (base + warp * (32 / PG) >= NP / 2) continue;  // the whole warp has no pair this round
+          const int i = base + warp * (32 / PG) + (lane / PG), gl = lane % PG;
           const bool act = i < NP / 2;
           // round robin: position 0 fixed, positions 1..NP-1 turn by one each step
           const int pa = act ? i : 0, pb = NP - 1 - pa;
@@ -358,7 +366,7 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32, large_warps<
           f32x2 dd = 0ull;
 #pragma unroll
           for (int e = 0; e < PE2; ++e) {
-            const int c = 2 * gl + 2 * kPG * e;
+            const int c = 2 * gl + 2 * PG * e;
             const bool in = act && c < n;
             va[e] = in ? *reinterpret_cast<const f32x2 *>(A + c) : 0ull;
             vb[e] = in ? *reinterpret_cast<const f32x2 *>(B + c) : 0ull;
@@ -367,7 +375,7 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32, large_warps<
           const float2 d2 = up2(dd);
           float d = d2.x + d2.y;
 #pragma unroll
-          for (int o = kPG / 2; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
+          for (int o = PG / 2; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
           const float nA = act ? nrm[ra] : 0.f, nB = act ? nrm[rb] : 0.f;
           if (act && fminf(nA, nB) > floor2 && d * d > tol2 * nA * nB) {
             const float x = nB - nA, y = 2.f * d;
@@ -379,7 +387,7 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32, large_warps<
             const f32x2 cs2 = pk2(cs, cs), sn2 = pk2(sn, sn), ns2 = pk2(-sn, -sn);
 #pragma unroll
             for (int e = 0; e < PE2; ++e) {
-              const int c = 2 * gl + 2 * kPG * e;
+              const int c = 2 * gl + 2 * PG * e;
               if (c < n) {
                 *reinterpret_cast<f32x2 *>(A + c) = fma2(cs2, va[e], mul2(ns2, vb[e]));
                 *reinterpret_cast<f32x2 *>(B + c) = fma2(sn2, va[e], mul2(cs2, vb[e]));
@@ -550,12 +558,13 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32, large_warps<
 
 }  // namespace
 
-size_t block_dual_large_smem_bytes(int k, bool stacked) {
-  return sizeof(float) * layout(stacked ? 2 * k * k : k * k).total;
+size_t block_dual_large_smem_bytes(int k, bool stacked, int parts) {
+  const int n = stacked ? 2 * k * k : k * k;
+  return sizeof(float) * layout(n, pair_lanes(n, block_dual_large_threads(k, stacked, parts) / 32)).total;
 }
 
 long long block_dual_large_w_stride(int k, bool stacked) {
-  const Layout L = layout(stacked ? 2 * k * k : k * k);
+  const Layout L = layout(stacked ? 2 * k * k : k * k, 8);  // npos and n only
   return ((long long)L.npos * L.n + 3) / 4 * 4;
 }
 

@@ -162,7 +162,7 @@ bool block_dual_has(const BdVariant &v);  // compiled in this build
 // k = 1..kMaxStackedK; the block memory [L][k^2][2][N3p] is the same.
 constexpr int kMinLargeK = 6, kMaxLargeK = 12, kMaxStackedK = 8;
 // parts = 3: SSST's rows [D_v u, D_h u, D_s u] (paper layout, k <= kMaxStackedK)
-size_t block_dual_large_smem_bytes(int k, bool stacked);
+size_t block_dual_large_smem_bytes(int k, bool stacked, int parts = 2);
 long long block_dual_large_w_stride(int k, bool stacked);
 long long block_dual_large_w_stride(int k);  // paper layout
 int block_dual_large_threads(int k, bool stacked, int parts = 2);
