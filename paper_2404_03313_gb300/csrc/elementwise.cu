@@ -53,7 +53,9 @@ __device__ __forceinline__ float comp(const float4 &v, int e) { return e == 0 ? 
 //   zs   = s - gs y3,   zt = t - gt (D_v^T y2 + y3)                 (steps 3, 4)
 // with y3 = c3 d and Z = sum_l P_l^T Y_l.  Also: sum (u+ - u)^2 and sum u^2 for
 // the stop rule, the first radix level of |zs| and |zt|, and zeroing of the next
-// Z accumulator.
+// Z accumulator.  EXTRA: 0 S3TTV, STV, SSTV; 1 HSSTV (+ omega D^T of the
+// first-order dual pair); 2 SSST (+ D_s^T Zs, and Zns zeroed).
+template <int EXTRA>
 __global__ void __launch_bounds__(256) primal_kernel(PrimalArgs a) {
   __shared__ unsigned s_cnt[2 * kHistBins];
   __shared__ float s_sum[2 * kHistBins];
@@ -78,7 +80,7 @@ __global__ void __launch_bounds__(256) primal_kernel(PrimalArgs a) {
     const size_t pjm = ((size_t)i * N2 + (j == 0 ? N2 - 1 : j - 1)) * N3p + b0;
     st4(a.Znv + p0, zero4);
     st4(a.Znh + p0, zero4);
-    if (a.Zns) st4(a.Zns + p0, zero4);
+    if (EXTRA == 2) st4(a.Zns + p0, zero4);
     // w = D_v^T Zv + D_h^T Zh at bands b0..b0+3 and at the band before b0
     // (periodic over the N3 true bands)
     const float4 zv = ld4(a.Zv + p0), zvm = ld4(a.Zv + pim), zh = ld4(a.Zh + p0), zhm = ld4(a.Zh + pjm);
@@ -87,6 +89,12 @@ __global__ void __launch_bounds__(256) primal_kernel(PrimalArgs a) {
     const long long o = (b0 == 0 ? dm.N3 - 1 : b0 - 1) - b0;  // to the band before (periodic)
     const float wbm = (a.Zv[(long long)pim + o] - a.Zv[(long long)p0 + o]) +
                       (a.Zh[(long long)pjm + o] - a.Zh[(long long)p0 + o]);
+    float4 zs4 = zero4;
+    float zsm = 0.f;
+    if (EXTRA == 2) {  // SSST's third dual part at bands b0..b0+3 and the band before
+      zs4 = ld4(a.Zs + p0);
+      zsm = a.Zs[(long long)p0 + o];
+    }
     const float4 d4 = ld4(a.d + p0), u4 = ld4(a.u + p0), s4 = ld4(a.s + p0), t4 = ld4(a.t + p0);
     const float4 y2c = ld4(a.y2 + p0), y2m = ld4(a.y2 + pim);
     float un[4], ub[4], zs[4], zt[4];
@@ -95,10 +103,10 @@ __global__ void __launch_bounds__(256) primal_kernel(PrimalArgs a) {
       if (b0 + e < dm.N3) {
         // (D_s^T w)[b] = w[b-1] - w[b]; STV's first-order term has no D_s
         float grad = a.no_ds ? w[e] : (e == 0 ? wbm : w[e - 1]) - w[e];
-        if (a.Z1v)  // HSSTV: + omega D^T (Y1v, Y1h), first-order, no D_s
+        if (EXTRA == 1)  // HSSTV: + omega D^T (Y1v, Y1h), first-order, no D_s
           grad = fmaf(a.w1, (a.Z1v[pim + e] - a.Z1v[p0 + e]) + (a.Z1h[pjm + e] - a.Z1h[p0 + e]), grad);
-        if (a.Zs)  // SSST: + D_s^T Zs, (D_s^T z)[b] = z[b-1] - z[b] (periodic)
-          grad += a.Zs[p0 + (b0 + e == 0 ? dm.N3 - 1 - b0 : e - 1)] - a.Zs[p0 + e];
+        if (EXTRA == 2)  // SSST: + D_s^T Zs, (D_s^T z)[b] = z[b-1] - z[b] (periodic)
+          grad += (e == 0 ? zsm : comp(zs4, e - 1)) - comp(zs4, e);
         const float y3 = c3 * comp(d4, e);
         const float u = comp(u4, e);
         const float x = u - a.gu * (grad + y3);
@@ -358,7 +366,9 @@ int grid_for(long long n) {
 }  // namespace
 
 cudaError_t launch_primal(const PrimalArgs &a, int grid, cudaStream_t st) {
-  primal_kernel<<<grid, 256, 0, st>>>(a);
+  if (a.Zs) primal_kernel<2><<<grid, 256, 0, st>>>(a);
+  else if (a.Z1v) primal_kernel<1><<<grid, 256, 0, st>>>(a);
+  else primal_kernel<0><<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
