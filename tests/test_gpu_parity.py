@@ -109,6 +109,8 @@ BLOCK_CASES = [
     ((12, 10, 13), 4), ((10, 11, 7), 5), ((32, 32, 16), 3), ((20, 24, 33), 5), ((16, 16, 128), 5),
     # the larger blocks of the paper's own setting (one CTA per block): k = 6..12
     ((9, 8, 7), 6), ((8, 9, 33), 7), ((10, 10, 16), 8), ((11, 10, 20), 10), ((10, 12, 70), 10), ((12, 12, 9), 12),
+    # odd row counts with 4 lanes per Jacobi pair (k = 9, 11: 81 and 121 rows)
+    ((10, 9, 12), 9), ((11, 12, 9), 11),
 ]
 
 

@@ -94,3 +94,52 @@ def test_objective(P, reg):
         got = s.objective(v, 3)
     ref = O.objective(v.astype(np.float64), 3, reg=reg)
     assert abs(got - ref) <= 1e-5 * ref, (got, ref)
+
+
+@pytest.mark.parametrize("shape,k", [((9, 8, 7), 1), ((12, 11, 10), 5), ((10, 9, 6), 8)])
+def test_ssst_one_pass_block_sizes(P, shape, k):
+    """SSST's k^2 x 3N3 blocks at the smallest block (one row), at k = 5 and at
+    the largest supported k = 8 (64 rows, 4 lanes per Jacobi pair), one pass
+    from a random state against the oracle."""
+    N1, N2, N3 = shape
+    st = random_state(N1, N2, N3, k, seed=11)
+    r = np.random.default_rng(12)
+    v = r.uniform(0, 1, (N1, N2, N3)).astype(np.float32)
+    scale = r.uniform(0.02, 3.0, size=(N1 * N2, 1, 1)) / np.sqrt(k * k + 3 * N3)
+    st["Y"] = (r.standard_normal((N1 * N2, k * k, 3 * N3)) * scale).astype(np.float32)
+    eps, alpha, beta = 3.0, 20.0, 10.0
+    ref_state = {key: val.astype(np.float64) for key, val in st.items()}
+    gam = O.step_sizes(N1, N2, k, "paper", "ssst")
+    ref, _ = O.iterate(ref_state, v, k, eps, alpha, beta, 0.0, 1.0, gam, reg="ssst")
+    with solver_for(P, "ssst") as s:
+        s.setup(v, eps, alpha, beta, k)
+        for name in ("u", "s", "t", "y2", "y3", "Y"):
+            s.set_state(name, st[name])
+        s.iterate(1)
+        for name in ("u", "s", "t", "y2", "y3", "Y"):
+            got = s.get_state(name)
+            tol = 1e-5 * max(1.0, k * k / 25)
+            assert rel(got, ref[name].reshape(got.shape)) <= tol, (name, rel(got, ref[name].reshape(got.shape)))
+
+
+def test_ssst_unsupported_settings(P):
+    """SSST takes the paper layout, the periodic D_s and k <= 8; it has no
+    stand-alone block-dual entry point."""
+    v = np.random.default_rng(0).uniform(0, 1, (12, 12, 6)).astype(np.float32)
+    with solver_for(P, "ssst") as s:
+        with pytest.raises(P.S3TTVError):
+            s.setup(v, 1.0, 1.0, 1.0, 9)
+        s.set_option(P.OPT_LAYOUT, P.LAYOUT_STACKED)
+        with pytest.raises(P.S3TTVError):
+            s.setup(v, 1.0, 1.0, 1.0, 3)
+        s.set_option(P.OPT_LAYOUT, P.LAYOUT_PAPER)
+        s.set_option(P.OPT_SPECTRAL_BOUNDARY, P.SPECTRAL_OPEN)
+        with pytest.raises(P.S3TTVError):
+            s.setup(v, 1.0, 1.0, 1.0, 3)
+        s.set_option(P.OPT_SPECTRAL_BOUNDARY, P.SPECTRAL_PERIODIC)
+        s.setup(v, 1.0, 1.0, 1.0, 3)
+        info = s.iterate(2)
+        assert info["iters"] == 2
+        Y = np.zeros((144, 9, 12), np.float32)
+        with pytest.raises(P.S3TTVError):
+            s.block_dual(torch.from_numpy(Y).cuda(), torch.from_numpy(v).cuda(), 3)
