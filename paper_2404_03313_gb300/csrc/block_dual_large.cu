@@ -43,6 +43,9 @@ namespace {
 constexpr int kLW = 8;         // warps per CTA (two CTAs per SM where shared memory allows)
 constexpr int kLT = kLW * 32;  // threads per CTA
 constexpr int kCW = 48;        // columns of Y' per streamed chunk
+// The Gram's 4 x 4 tiles read four chunk rows apart (4 (kCW + 4) floats, 16
+// banks mod 32) and rotate their column order within 16-column windows.
+static_assert(kCW % 16 == 0 && (4 * (kCW + 4)) % 32 == 16, "chunk geometry of the Gram's bank rotation");
 constexpr int kSlots = (kMaxLargeK * kMaxLargeK + 31) / 32;  // row elements a lane holds
 
 // Lanes per row pair in the Jacobi: 8, or 4 where that lets one round of the
@@ -226,13 +229,19 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
           int ti, tj;
           upper_tile(t, nt4, ti, tj);
           const float *pa = chunk + (size_t)(4 * ti) * L.cs, *pb = chunk + (size_t)(4 * tj) * L.cs;
+          // the 8 lanes of a quarter-warp hold consecutive tj, whose B rows
+          // start 0 or 16 banks apart: rotating the column order by
+          // 4 ((tj / 2) mod 4) within each 16-column window puts their
+          // float4 loads on 8 distinct 4-bank groups (the sums only reorder)
+          const int rot = 4 * ((tj >> 1) & 3);
 #pragma unroll 2
           for (int c = 0; c < kCW; c += 4) {
+            const int cc = (c & ~15) | ((c + rot) & 15);
             float4 va[4], vb[4];
 #pragma unroll
             for (int x = 0; x < 4; ++x) {
-              va[x] = lds4(pa + (size_t)x * L.cs + c);
-              vb[x] = lds4(pb + (size_t)x * L.cs + c);
+              va[x] = lds4(pa + (size_t)x * L.cs + cc);
+              vb[x] = lds4(pb + (size_t)x * L.cs + cc);
             }
 #pragma unroll
             for (int x = 0; x < 4; ++x)
@@ -271,25 +280,35 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
     // ---- 2. C0 = W G (warm) or G (cold), rows of C into X2 ----
     const float *Wl = a.W ? a.W + (size_t)l * a.w_stride : nullptr;
     const bool warm = a.warm && Wl && !(Wl[0] != Wl[0]);  // NaN marks "start cold"
-    for (int r = warp; r < NP; r += LW) {
-      float acc2[kSlots];
+    // two rows per warp at a time (r0 and r0 + LW), so each G row loaded from
+    // shared memory serves both; per row the sums are those of one row at a time
+    for (int r0 = warp; r0 < NP; r0 += 2 * LW) {
+      const int r1 = r0 + LW;
+      const bool two = r1 < NP;
+      float acc0[kSlots], acc1[kSlots];
       if (warm) {
-        float wr[kSlots];  // lane j holds W[r][j + 32 i]
+        float w0[kSlots], w1[kSlots];  // lane j holds W[r][j + 32 i]
 #pragma unroll
         for (int i = 0; i < kSlots; ++i) {
           const int c = lane + 32 * i;
-          wr[i] = c < n ? __ldg(Wl + (size_t)r * n + c) : 0.f;
-          acc2[i] = 0.f;
+          w0[i] = c < n ? __ldg(Wl + (size_t)r0 * n + c) : 0.f;
+          w1[i] = two && c < n ? __ldg(Wl + (size_t)r1 * n + c) : 0.f;
+          acc0[i] = 0.f;
+          acc1[i] = 0.f;
         }
 #pragma unroll
         for (int kb = 0; kb < kSlots; ++kb) {
           for (int j = 0; j < 32 && kb * 32 + j < n; ++j) {
-            const float w = __shfl_sync(kFull, wr[kb], j);
+            const float wa = __shfl_sync(kFull, w0[kb], j), wb = __shfl_sync(kFull, w1[kb], j);
             const float *g = X1 + (size_t)(kb * 32 + j) * GS;
 #pragma unroll
             for (int i = 0; i < kSlots; ++i) {
               const int c = lane + 32 * i;
-              if (c < n) acc2[i] = fmaf(w, g[c], acc2[i]);
+              if (c < n) {
+                const float gv = g[c];
+                acc0[i] = fmaf(wa, gv, acc0[i]);
+                acc1[i] = fmaf(wb, gv, acc1[i]);
+              }
             }
           }
         }
@@ -297,13 +316,17 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
 #pragma unroll
         for (int i = 0; i < kSlots; ++i) {
           const int c = lane + 32 * i;
-          acc2[i] = r < n && c < n ? X1[(size_t)r * GS + c] : 0.f;
+          acc0[i] = r0 < n && c < n ? X1[(size_t)r0 * GS + c] : 0.f;
+          acc1[i] = r1 < n && c < n ? X1[(size_t)r1 * GS + c] : 0.f;
         }
       }
 #pragma unroll
       for (int i = 0; i < kSlots; ++i) {
         const int c = lane + 32 * i;
-        if (c < GS) X2[(size_t)r * GS + c] = c < n ? acc2[i] : 0.f;
+        if (c < GS) {
+          X2[(size_t)r0 * GS + c] = c < n ? acc0[i] : 0.f;
+          if (two) X2[(size_t)r1 * GS + c] = c < n ? acc1[i] : 0.f;
+        }
       }
     }
     __syncthreads();
@@ -491,9 +514,11 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
       if (cold && tid == 0) a.W[(size_t)l * a.w_stride] = __int_as_float(0x7fc00000);
     }
 
-    // ---- 5a. M = I - Ut^T Ut into X2, 4 x 4 tiles ----
-    for (int t = tid; t < nt4 * nt4; t += LT) {
-      const int ti = t / nt4, tj = t - ti * nt4;
+    // ---- 5a. M = I - Ut^T Ut into X2: upper-triangle 4 x 4 tiles, each
+    // written with its transpose (M is symmetric) ----
+    for (int t = tid; t < n_upper; t += LT) {
+      int ti, tj;
+      upper_tile(t, nt4, ti, tj);
       float m[16];
 #pragma unroll
       for (int e = 0; e < 16; ++e) m[e] = 0.f;
@@ -510,6 +535,11 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
         sts4(X2 + (size_t)r * GS + 4 * tj,
              make_float4((r == 4 * tj ? 1.f : 0.f) - m[4 * p], (r == 4 * tj + 1 ? 1.f : 0.f) - m[4 * p + 1],
                          (r == 4 * tj + 2 ? 1.f : 0.f) - m[4 * p + 2], (r == 4 * tj + 3 ? 1.f : 0.f) - m[4 * p + 3]));
+      }
+      if (ti != tj) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)  // row 4 tj + q of the transpose: off the diagonal, no identity
+          sts4(X2 + (size_t)(4 * tj + q) * GS + 4 * ti, make_float4(-m[q], -m[4 + q], -m[8 + q], -m[12 + q]));
       }
     }
     __syncthreads();
