@@ -81,7 +81,7 @@ __device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
 struct Layout {
   int n, npos, gs, cs;  // block rows, rows padded to even, row strides of the n x n buffers and the chunk
   int nt4;              // 4-row tiles across npos
-  size_t x1, x2, chunk, nrm, pix, total;  // float offsets; total floats
+  size_t x1, x2, chunk, nrm, pix, last, total;  // float offsets; total floats
 };
 
 // n: rows of a block matrix (k^2 in the paper's layout, 2 k^2 stacked)
@@ -101,7 +101,8 @@ __host__ __device__ inline Layout layout(int n, int pg) {
   L.chunk = L.x2 + (size_t)w * L.gs;
   L.nrm = L.chunk + (size_t)w * L.cs;
   L.pix = L.nrm + w;
-  L.total = L.pix + w;
+  L.last = L.pix + w;
+  L.total = L.last + w;
   return L;
 }
 
@@ -184,6 +185,9 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
   constexpr int GT = (NT4 * (NT4 + 1) / 2 + LT - 1) / LT;  // upper-triangle Gram tiles per thread
   constexpr int PG = pair_lanes(NR, LW);               // lanes per row pair in the Jacobi
   constexpr int PE2 = (NR + 2 * PG - 1) / (2 * PG);    // float2 pieces of a row a Jacobi lane holds
+  // skip Jacobi pairs whose rows are unchanged since they last met: pays from
+  // about 64 rows (measured: k = 10 3% faster, SSST's 25 rows 8% slower)
+  constexpr bool SKIP = NR > 64;
   extern __shared__ __align__(16) float sm[];
   __shared__ float s_red[LW];
   __shared__ unsigned s_sweeps;
@@ -192,6 +196,7 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
   const int n = L.n, NP = L.npos, GS = L.gs, nt4 = L.nt4;
   float *X1 = sm + L.x1, *X2 = sm + L.x2, *chunk = sm + L.chunk, *nrm = sm + L.nrm;
   int *pix = reinterpret_cast<int *>(sm + L.pix);
+  int *last = reinterpret_cast<int *>(sm + L.last);  // the last sweep that rotated each Jacobi row
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const Dims dm = a.dm;
   const int N3p = dm.N3p, W = ST ? N3p : PARTS * N3p;
@@ -332,6 +337,8 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
     __syncthreads();
 
     // ---- 3. one-sided Jacobi on the rows of C ----
+    if (SKIP)
+      for (int r = tid; r < NP; r += LT) last[r] = -2;  // published by the barrier in norms()
     // squared row norms (one warp per row)
     auto norms = [&]() {
       for (int r = warp; r < NP; r += LW) {
@@ -383,14 +390,19 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
           xb -= xb >= NP - 1 ? NP - 1 : 0;
           const int ra = pa == 0 ? 0 : 1 + xa, rb = 1 + xb;
           float *A = X2 + (size_t)ra * GS, *B = X2 + (size_t)rb * GS;
-          // lane gl holds the float2 pieces at columns 2 gl + 16 e; columns
+          // a pair whose rows no rotation has touched since the pair last met
+          // (in the previous sweep, with the same rows, and did not rotate
+          // then) would compute the same product: it is skipped
+          const bool chk = act && (!SKIP || sw == 0 || last[ra] >= sw - 1 || last[rb] >= sw - 1);
+          if (SKIP && !__any_sync(kFull, chk)) continue;  // warp-uniform
+          // lane gl holds the float2 pieces at columns 2 gl + 2 PG e; columns
           // n..GS-1 of every row are zero, so a piece starting below n is whole
           f32x2 va[PE2], vb[PE2];
           f32x2 dd = 0ull;
 #pragma unroll
           for (int e = 0; e < PE2; ++e) {
             const int c = 2 * gl + 2 * PG * e;
-            const bool in = act && c < n;
+            const bool in = chk && c < n;
             va[e] = in ? *reinterpret_cast<const f32x2 *>(A + c) : 0ull;
             vb[e] = in ? *reinterpret_cast<const f32x2 *>(B + c) : 0ull;
             dd = fma2(va[e], vb[e], dd);
@@ -399,8 +411,8 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
           float d = d2.x + d2.y;
 #pragma unroll
           for (int o = PG / 2; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
-          const float nA = act ? nrm[ra] : 0.f, nB = act ? nrm[rb] : 0.f;
-          if (act && fminf(nA, nB) > floor2 && d * d > tol2 * nA * nB) {
+          const float nA = chk ? nrm[ra] : 0.f, nB = chk ? nrm[rb] : 0.f;
+          if (chk && fminf(nA, nB) > floor2 && d * d > tol2 * nA * nB) {
             const float x = nB - nA, y = 2.f * d;
             const float rr = rsqrtf(fmaf(x, x, y * y));
             const float hc = fmaf(0.5f * fabsf(x), rr, 0.5f);
@@ -419,6 +431,10 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
             if (gl == 0) {
               nrm[ra] = nA - dn;
               nrm[rb] = nB + dn;
+              if (SKIP) {
+                last[ra] = sw;
+                last[rb] = sw;
+              }
             }
             rotated = 1;
           }
