@@ -63,10 +63,14 @@ typedef struct s3ttv_info {
   int status;              /* the call's return value                                */
   int iters;               /* P-PDS passes completed by this call                    */
   int converged;           /* 1 if ||u+ - u|| / ||u|| < tol fired                    */
-  int jacobi_nonconverged; /* blocks whose eigen-solve reached the sweep cap         */
+  int jacobi_nonconverged; /* blocks left with an unconverged eigen-solve (the FP32
+                              sweep cap without the FP64 re-solve, or the re-solve's
+                              own cap)                                              */
   double rel_change;       /* ||u+ - u||_2 / ||u||_2 of the last pass (eq. StopCri)  */
   double seconds;          /* host wall time of the call                             */
   double jacobi_sweeps;    /* mean eigen-solve sweeps per block and pass             */
+  int jacobi_fallbacks;    /* blocks re-solved in FP64 after their FP32 eigen-solve
+                              reached the sweep cap (S3TTV_OPT_FP64_FALLBACK)      */
 } s3ttv_info;
 
 /* Step-size policies (option S3TTV_OPT_STEP_POLICY).
@@ -108,8 +112,19 @@ enum {
                                       the context (these are passes of the solve; the
                                       forms agree to FP32 rounding).  0 (default): the
                                       occupancy rule and S3TTV_OPT_TENSOR_CORES choose */
-  S3TTV_OPT_HSSTV_OMEGA = 12       /* HSSTV's weight omega of the first-order differences
+  S3TTV_OPT_HSSTV_OMEGA = 12,      /* HSSTV's weight omega of the first-order differences
                                       (default 0.05, (0, 2])                              */
+  S3TTV_OPT_FP64_FALLBACK = 13     /* 1 (default): a block whose FP32 eigen-solve reaches
+                                      S3TTV_OPT_JACOBI_MAX_SWEEPS is re-solved in FP64 in
+                                      the same pass (FP64 Gram and one-sided Jacobi,
+                                      tolerance 1e-13, up to 80 sweeps; one extra launch
+                                      per pass, which returns at once when no block is
+                                      queued; up to 65,536 blocks per pass, the rest are
+                                      applied as they stand and counted in
+                                      jacobi_nonconverged); its warm-start rows start
+                                      cold next pass.  0: such blocks are applied as
+                                      they stand.  info.jacobi_fallbacks counts the
+                                      re-solved blocks                                    */
 };
 /* Regularisers (option S3TTV_OPT_REGULARIZER).  Sec. IV runs its P-PDS-solvable
  * comparison methods by replacing S3TTV in Prob. (S3TTV_denoising) and solving

@@ -26,6 +26,7 @@ SPECTRAL_PERIODIC, SPECTRAL_OPEN = 0, 1
 OPT_REGULARIZER = 10
 OPT_AUTOTUNE = 11
 OPT_HSSTV_OMEGA = 12
+OPT_FP64_FALLBACK = 13
 REG_S3TTV, REG_STV, REG_SSTV, REG_HSSTV1, REG_HSSTV2, REG_SSST = 0, 1, 2, 3, 4, 5
 KERNEL_CLASSES = ("primal", "l1_search", "block_dual", "dual", "finalize")
 STATE = {"u": 0, "s": 1, "t": 2, "y2": 3, "y3": 4, "Y": 5}
@@ -37,7 +38,8 @@ _c_int, _c_ll, _c_f, _c_d, _vp = ctypes.c_int, ctypes.c_longlong, ctypes.c_float
 class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("converged", ctypes.c_int),
                 ("jacobi_nonconverged", ctypes.c_int), ("rel_change", ctypes.c_double),
-                ("seconds", ctypes.c_double), ("jacobi_sweeps", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("jacobi_sweeps", ctypes.c_double),
+                ("jacobi_fallbacks", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -45,6 +45,9 @@ struct s3ttv_ctx {
   float *ubar = nullptr, *zs = nullptr, *zt = nullptr, *Zv[2] = {nullptr, nullptr}, *Zh[2] = {nullptr, nullptr};
   float *Fv = nullptr, *Fh = nullptr;  // D_v D_s ubar, D_h D_s ubar
   float *Fs = nullptr, *Zs[2] = {nullptr, nullptr};  // SSST: D_s ubar and the third part of Z
+  int *fb_list = nullptr;  // FP64 re-solve queue of the block duals
+  int fb_cap = 0;
+  bool fp64_fallback = true;  // option
   float *Y = nullptr, *stage = nullptr;
   float *W = nullptr;      // per-block warm-start rows of the eigen-solve
   long long w_stride = 0;
@@ -72,7 +75,8 @@ namespace {
 
 constexpr int kMaxGrid = 4096;
 constexpr int kMaxK = kMaxLargeK;  // k <= 5: block_dual.cu; 6..12: block_dual_large.cu
-constexpr int kLaunchesPerPass = 10;  // kernels enqueue_pass launches
+constexpr int kLaunchesPerPass = 10;  // kernels enqueue_pass launches (block-dual regularisers, no re-solve)
+constexpr int kFbQueueMax = 1 << 16;  // entries of the FP64 re-solve queue
 
 int fail(s3ttv_ctx *c, int status, const char *fmt, ...) {
   if (c) {
@@ -136,6 +140,9 @@ void free_all(s3ttv_ctx *c) {
     *b = nullptr;
   }
   if (c->sc) cudaFree(c->sc);
+  if (c->fb_list) cudaFree(c->fb_list);
+  c->fb_list = nullptr;
+  c->fb_cap = 0;
   if (c->part) cudaFree(c->part);
   if (c->hcnt) cudaFree(c->hcnt);
   if (c->hsum) cudaFree(c->hsum);
@@ -214,7 +221,9 @@ int ensure_problem_buffers(s3ttv_ctx *ctx, const Dims &dm, int k) {
                                                            : block_dual_w_stride(k);
   const size_t nw = (size_t)dm.P * ws;
   ctx->w_stride = ws;
-  if (np <= ctx->cap_np && ny <= ctx->cap_y && nw <= ctx->cap_w && ctx->sc && (!is_ssst(ctx) || ctx->Fs))
+  const int want_fb = dm.P < kFbQueueMax ? (int)dm.P : kFbQueueMax;
+  if (np <= ctx->cap_np && ny <= ctx->cap_y && nw <= ctx->cap_w && ctx->sc && (!is_ssst(ctx) || ctx->Fs) &&
+      want_fb <= ctx->fb_cap)
     return S3TTV_OK;
   free_all(ctx);
   ctx->w_stride = ws;
@@ -238,11 +247,14 @@ int ensure_problem_buffers(s3ttv_ctx *ctx, const Dims &dm, int k) {
       }
     }
   }
+  const int fb_cap = dm.P < kFbQueueMax ? (int)dm.P : kFbQueueMax;
   if ((rc = dmalloc(ctx, (void **)&ctx->Y, ny * sizeof(float))) ||
-      (rc = dmalloc(ctx, (void **)&ctx->W, nw * sizeof(float)))) {
+      (rc = dmalloc(ctx, (void **)&ctx->W, nw * sizeof(float))) ||
+      (rc = dmalloc(ctx, (void **)&ctx->fb_list, (size_t)fb_cap * sizeof(int)))) {
     free_all(ctx);
     return rc;
   }
+  ctx->fb_cap = fb_cap;
   ctx->cap_np = np;
   ctx->cap_y = ny;
   ctx->cap_w = nw;
@@ -269,6 +281,7 @@ struct BdShape {
   int grid = 0;
   BdVariant v;
   bool large = false;  // block_dual_large.cu (k > 5)
+  size_t fb_smem = 0;  // dynamic shared memory of the FP64 re-solve (0: not available)
 };
 
 // The launch shape of one block-dual form of the k <= 5 kernel: tensor cores
@@ -311,6 +324,17 @@ int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, BdShape *sh) {
     return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: the stacked layout supports k <= %d", k, kMaxStackedK);
   if (parts == 3 && (stacked || ctx->open_s))
     return fail(ctx, S3TTV_EUNSUPPORTED, "SSST takes the paper layout and the periodic spectral boundary");
+  {  // the FP64 re-solve of blocks whose FP32 eigen-solve reaches the sweep cap
+    int dev_max = 0;
+    cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    const size_t fs = fallback_smem_bytes(stacked ? 2 * k * k : k * k);
+    sh->fb_smem = 0;
+    if (fs <= (size_t)dev_max) {
+      cudaError_t e = fallback_prepare(fs);
+      if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+      sh->fb_smem = fs;
+    }
+  }
   if (parts == 3 && k > kMaxStackedK)
     return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: SSST supports k <= %d", k, kMaxStackedK);
   if (stacked || parts == 3 || k >= kMinLargeK) {  // one CTA per block at a time; FP32 CUDA cores
@@ -481,6 +505,7 @@ __global__ void begin_iterate_kernel(Scalars *sc, int n, float tol) {
   sc->tol = tol;
   sc->jacobi_fail = 0u;
   sc->jacobi_sweeps = 0ull;
+  sc->fb_total = 0u;
 }
 
 __global__ void set_c3_kernel(Scalars *sc, double c3) { sc->c3 = c3; }
@@ -569,10 +594,18 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   ba.W = ctx->warm_start ? ctx->W : nullptr;
   ba.w_stride = ctx->w_stride;
   ba.warm = ctx->warm_start && ctx->warm_valid;
+  const bool fb = ctx->fp64_fallback && bd.fb_smem > 0;
+  ba.fb_list = fb ? ctx->fb_list : nullptr;
+  ba.fb_cap = fb ? ctx->fb_cap : 0;
   if (bd.large)
     CU(launch_block_dual_large(ba, ctx->k, ctx->layout == S3TTV_LAYOUT_STACKED, bd.grid, bd.smem, st,
                                row_parts(ctx)));
   else CU(launch_block_dual(ba, bd.v, bd.grid, bd.smem, st));
+  if (fb) {
+    CU(launch_fallback(ba, ctx->k, ctx->layout == S3TTV_LAYOUT_STACKED, row_parts(ctx), ctx->num_sms, bd.fb_smem,
+                       st));
+    ctx->launches += 1;
+  }
   if (ctx->warm_start) ctx->warm_valid = true;
   }
   if (ev) CU(cudaEventRecord(ev[3], st));
@@ -606,7 +639,8 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   fa.g3 = ctx->gam[5];
   CU(launch_finalize(fa, st));
   if (ev) CU(cudaEventRecord(ev[5], st));
-  ctx->launches += kLaunchesPerPass;
+  // SSTV and HSSTV: one elementwise dual kernel in place of xfield + block dual
+  ctx->launches += (ctx->reg == S3TTV_REG_SSTV || is_hsstv(ctx)) ? kLaunchesPerPass - 1 : kLaunchesPerPass;
   return S3TTV_OK;
 }
 
@@ -785,6 +819,10 @@ int s3ttv_set_option(s3ttv_ctx *ctx, int key, double value) {
         ctx->ready = false;
         ctx->warm_valid = false;
       }
+      return S3TTV_OK;
+    case S3TTV_OPT_FP64_FALLBACK:
+      if (value != 0 && value != 1) return fail(ctx, S3TTV_EINVAL, "fp64_fallback must be 0 or 1");
+      ctx->fp64_fallback = value == 1;
       return S3TTV_OK;
     case S3TTV_OPT_HSSTV_OMEGA:
       if (!(value > 0.0 && value <= 2.0)) return fail(ctx, S3TTV_EINVAL, "HSSTV omega must be in (0, 2]");
@@ -969,6 +1007,7 @@ int s3ttv_iterate(s3ttv_ctx *ctx, int n, float tol, s3ttv_info *info) {
     info->iters = done_iters;
     info->converged = hs.status == 1;
     info->jacobi_nonconverged = (int)hs.jacobi_fail;
+    info->jacobi_fallbacks = (int)hs.fb_total;
     info->rel_change = hs.rel;
     info->seconds = now_s() - t0;
     info->jacobi_sweeps = done_iters > 0 ? (double)hs.jacobi_sweeps / ((double)done_iters * ctx->dm.P) : 0.0;
@@ -1145,6 +1184,7 @@ int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, in
     m->open_s = ctx->open_s;
     m->reg = ctx->reg;
     m->hsstv_omega = ctx->hsstv_omega;
+    m->fp64_fallback = ctx->fp64_fallback;
     m->profile = false;
     const s3ttv_problem &p = problems[i];
     int rc = s3ttv_setup(m, p.v, p.N1, p.N2, p.N3, p.eps, p.alpha, p.beta, p.mu_min, p.mu_max, p.k);
@@ -1164,7 +1204,7 @@ int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, in
   ForkJoin fj;
   CU(fj.create(n));
   cudaGraphExec_t exec = nullptr;
-  std::vector<long long> launches0(n);
+  std::vector<long long> launches0(n), per_pass(n, kLaunchesPerPass);
   // the legacy default streams cannot be captured: then every chunk is enqueued
   const bool capturable = ctx->stream != nullptr && ctx->stream != cudaStreamLegacy && ctx->stream != cudaStreamPerThread;
   if (max_iter >= chunk && capturable) {
@@ -1182,7 +1222,10 @@ int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, in
     const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     CU(ei);
-    for (int i = 0; i < n; ++i) ctx->members[i]->launches = launches0[i];  // recorded, not run
+    for (int i = 0; i < n; ++i) {  // recorded, not run
+      per_pass[i] = (ctx->members[i]->launches - launches0[i]) / chunk;
+      ctx->members[i]->launches = launches0[i];
+    }
   }
   std::vector<Scalars> hs(n);
   std::vector<double> finish(n, -1.0);  // host time at which each problem was seen stopped
@@ -1195,7 +1238,7 @@ int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, in
         rc = fail(ctx, S3TTV_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
         break;
       }
-      for (int i = 0; i < n; ++i) ctx->members[i]->launches += (long long)kLaunchesPerPass * chunk;
+      for (int i = 0; i < n; ++i) ctx->members[i]->launches += per_pass[i] * chunk;
     } else {
       if ((rc = enqueue_batch(ctx, n, bd, grid_e, par, step, fj))) break;
       for (int i = 0; i < n; ++i) par[i] ^= step & 1;
@@ -1247,6 +1290,7 @@ int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, in
       infos[i].iters = done_iters;
       infos[i].converged = hs[i].status == 1;
       infos[i].jacobi_nonconverged = (int)hs[i].jacobi_fail;
+      infos[i].jacobi_fallbacks = (int)hs[i].fb_total;
       infos[i].rel_change = hs[i].rel;
       infos[i].jacobi_sweeps =
           done_iters > 0 ? (double)hs[i].jacobi_sweeps / ((double)done_iters * m->dm.P) : 0.0;
@@ -1353,8 +1397,14 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   ba.W = nullptr;
   ba.w_stride = 0;
   ba.warm = 0;
+  const bool fb = ctx->fp64_fallback && bd.fb_smem > 0;
+  ba.fb_list = fb ? ctx->fb_list : nullptr;
+  ba.fb_cap = fb ? ctx->fb_cap : 0;
   if (bd.large) CU(launch_block_dual_large(ba, k, ctx->layout == S3TTV_LAYOUT_STACKED, bd.grid, bd.smem, ctx->stream));
   else CU(launch_block_dual(ba, bd.v, bd.grid, bd.smem, ctx->stream));
+  if (fb)
+    CU(launch_fallback(ba, k, ctx->layout == S3TTV_LAYOUT_STACKED, row_parts(ctx), ctx->num_sms, bd.fb_smem,
+                       ctx->stream));
   if ((rc = store_Y(ctx, Y))) return rc;
   if ((rc = store_cube(ctx, ctx->Zv[0], Zv, nullptr))) return rc;
   if ((rc = store_cube(ctx, ctx->Zh[0], Zh, nullptr))) return rc;
@@ -1363,6 +1413,7 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   CU(cudaStreamSynchronize(ctx->stream));
   if (info) {
     info->jacobi_nonconverged = (int)hs.jacobi_fail;
+    info->jacobi_fallbacks = (int)hs.fb_total;
     info->jacobi_sweeps = (double)hs.jacobi_sweeps / (double)dm.P;
   }
   return S3TTV_OK;

@@ -721,6 +721,7 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
   __shared__ unsigned s_sweeps;
   __shared__ int s_tile_r0[TC ? 1 : 32], s_tile_c0[TC ? 1 : 32];
   __shared__ int s_off[kNW][n];  // pixel (i * N2 + j) of row r of P_l
+  __shared__ int s_queued[kNW];  // block b of the group went to the FP64 re-solve
   if (a.sc->done) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int RS = a.rs;                              // row stride of the block copies
@@ -875,7 +876,18 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
       bool ok;
       const int sweeps = eigen_rows<K>(a, l0 + warp, warm ? Yp + warp * w_floats<K>() : nullptr, Gb, Gb, &ok);
       if (lane == 0) {
-        if (!ok) atomicAdd(&a.sc->jacobi_fail, 1u);
+        int queued = 0;
+        if (!ok) {
+          // to the FP64 re-solve if the queue has room; else applied as it stands
+          const unsigned slot = a.fb_list ? atomicAdd(&a.sc->fb_count, 1u) : 0xffffffffu;
+          if (slot < (unsigned)a.fb_cap) {
+            a.fb_list[slot] = (int)(l0 + warp);
+            queued = 1;
+          } else {
+            atomicAdd(&a.sc->jacobi_fail, 1u);
+          }
+        }
+        s_queued[warp] = queued;
         atomicAdd(&s_sweeps, (unsigned)sweeps);
       }
       __syncwarp();
@@ -886,6 +898,7 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
     // ---- 5. for each block: Y' back into shared memory, Y_l = M Y' in place, then
     //         Y_l stored and P_l^T Y_l added into Z, row by row ----
     for (int b = 0; b < nb; ++b) {
+      if (s_queued[b]) continue;  // CTA-uniform: Y_l keeps Y' for the FP64 re-solve
       const long long l = l0 + b;
       float *Yl = a.Y + (size_t)l * n * 2 * N3p;
       const float *Mg = Gall + b * gm_floats<K, TC>();

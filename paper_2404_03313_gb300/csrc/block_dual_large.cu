@@ -191,6 +191,7 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
   extern __shared__ __align__(16) float sm[];
   __shared__ float s_red[LW];
   __shared__ unsigned s_sweeps;
+  __shared__ int s_queued;  // this block went to the FP64 re-solve
   if (a.sc->done) return;
   const Layout L = layout(NR, PG);
   const int n = L.n, NP = L.npos, GS = L.gs, nt4 = L.nt4;
@@ -448,10 +449,22 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
       }
     }
     if (tid == 0) {
-      if (!converged) atomicAdd(&a.sc->jacobi_fail, 1u);
+      int queued = 0;
+      if (!converged) {
+        // to the FP64 re-solve if the queue has room; else applied as it stands
+        const unsigned slot = a.fb_list ? atomicAdd(&a.sc->fb_count, 1u) : 0xffffffffu;
+        if (slot < (unsigned)a.fb_cap) {
+          a.fb_list[slot] = (int)l;
+          queued = 1;
+        } else {
+          atomicAdd(&a.sc->jacobi_fail, 1u);
+        }
+      }
+      s_queued = queued;
       s_sweeps += (unsigned)sweeps;
     }
-    norms();
+    norms();  // ends with a barrier: s_queued is visible
+    if (s_queued) continue;  // CTA-uniform: Y_l keeps Y' (written back in the Gram pass), no Z
 
     // ---- 4. eigen-rows: Ut (X1), and the unit eigenvectors in place in X2 ----
     for (int r = warp; r < NP; r += LW) {

@@ -61,6 +61,9 @@ __global__ void __launch_bounds__(256) primal_kernel(PrimalArgs a) {
   __shared__ float s_sum[2 * kHistBins];
   __shared__ double s_red[2][32];
   if (a.sc->done) return;
+  // this pass's FP64 re-solve queue starts empty (the block dual runs after this
+  // kernel, the previous pass's re-solve before it)
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.sc->fb_count = 0u;
   for (int i = threadIdx.x; i < 2 * kHistBins; i += blockDim.x) {
     s_cnt[i] = 0u;
     s_sum[i] = 0.f;

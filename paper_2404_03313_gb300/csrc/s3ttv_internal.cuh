@@ -43,9 +43,11 @@ struct Scalars {
   int iter_limit;      // stop when iter reaches this
   int done;            // set once the stop rule or the cap fired
   int status;          // 0 running, 1 converged, 2 cap, -4 numeric
-  unsigned jacobi_fail;
+  unsigned jacobi_fail;  // blocks left with an unconverged eigen-solve
   float tol;
   unsigned long long jacobi_sweeps;  // sweeps summed over blocks (statistics)
+  unsigned fb_count;  // blocks queued for the FP64 re-solve in this pass (reset by the primal step)
+  unsigned fb_total;  // blocks re-solved in FP64 since the last s3ttv_iterate began
 };
 
 // Radix levels over the 31 magnitude bits of a float.
@@ -135,9 +137,19 @@ struct BlockDualArgs {
   int warm;               // 1: start from the rows stored in W
   const float *Fs = nullptr;  // SSST's third part D_s ubar (per-CTA kernel, three parts)
   float *Zs = nullptr;        // and its accumulation
+  // FP64 re-solve queue (fallback.cu): a block whose FP32 eigen-solve reaches
+  // the sweep cap is listed here (up to fb_cap), left as Y' and not added to Z;
+  // null: no queue, such blocks are applied as they stand
+  int *fb_list = nullptr;
+  int fb_cap = 0;
 };
 // floats per block of the warm-start rows
 long long block_dual_w_stride(int k);
+// FP64 re-solve of the queued blocks (fallback.cu); n = rows of a block matrix
+size_t fallback_smem_bytes(int n);
+cudaError_t fallback_prepare(size_t smem_bytes);
+cudaError_t launch_fallback(const BlockDualArgs &a, int k, int stacked, int parts, int grid, size_t smem,
+                            cudaStream_t st);
 // Kernel variant: block side k (1..5), minb = 5 or 4 (CTAs per SM its register
 // budget is sized for), tc = 1 for the Gram and the apply on tensor cores (three
 // TF32 products per FP32 product), 0 for FP32 CUDA cores.
