@@ -114,7 +114,7 @@ enum {
                                       occupancy rule and S3TTV_OPT_TENSOR_CORES choose */
   S3TTV_OPT_HSSTV_OMEGA = 12,      /* HSSTV's weight omega of the first-order differences
                                       (default 0.05, (0, 2])                              */
-  S3TTV_OPT_FP64_FALLBACK = 13     /* 1 (default): a block whose FP32 eigen-solve reaches
+  S3TTV_OPT_FP64_FALLBACK = 13,    /* 1 (default): a block whose FP32 eigen-solve reaches
                                       S3TTV_OPT_JACOBI_MAX_SWEEPS is re-solved in FP64 in
                                       the same pass (FP64 Gram and one-sided Jacobi,
                                       tolerance 1e-13, up to 80 sweeps; one extra launch
@@ -125,6 +125,14 @@ enum {
                                       cold next pass.  0: such blocks are applied as
                                       they stand.  info.jacobi_fallbacks counts the
                                       re-solved blocks                                    */
+  S3TTV_OPT_ALLOC_LIMIT = 14,      /* device bytes the context may hold (0, the default: no
+                                      limit); an allocation past it fails with
+                                      S3TTV_ENOMEM as a failed cudaMalloc would, and the
+                                      context stays usable (host-side fault injection)    */
+  S3TTV_OPT_NVTX = 15              /* 1: NVTX ranges around each API call and each kernel
+                                      class as a pass is enqueued (primal, l1-ball
+                                      thresholds, block dual, dual, finalize), for
+                                      profilers; 0 (default): none                        */
 };
 /* Regularisers (option S3TTV_OPT_REGULARIZER).  Sec. IV runs its P-PDS-solvable
  * comparison methods by replacing S3TTV in Prob. (S3TTV_denoising) and solving

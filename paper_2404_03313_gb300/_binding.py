@@ -27,6 +27,8 @@ OPT_REGULARIZER = 10
 OPT_AUTOTUNE = 11
 OPT_HSSTV_OMEGA = 12
 OPT_FP64_FALLBACK = 13
+OPT_ALLOC_LIMIT = 14
+OPT_NVTX = 15
 REG_S3TTV, REG_STV, REG_SSTV, REG_HSSTV1, REG_HSSTV2, REG_SSST = 0, 1, 2, 3, 4, 5
 KERNEL_CLASSES = ("primal", "l1_search", "block_dual", "dual", "finalize")
 STATE = {"u": 0, "s": 1, "t": 2, "y2": 3, "y3": 4, "Y": 5}

@@ -8,6 +8,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "s3ttv.h"
 #include "s3ttv_internal.cuh"
 
@@ -48,6 +50,8 @@ struct s3ttv_ctx {
   int *fb_list = nullptr;  // FP64 re-solve queue of the block duals
   int fb_cap = 0;
   bool fp64_fallback = true;  // option
+  size_t alloc_limit = 0;     // option: device bytes the context may hold (0: no limit)
+  bool nvtx = false;          // option: NVTX ranges around calls and kernel classes
   float *Y = nullptr, *stage = nullptr;
   float *W = nullptr;      // per-block warm-start rows of the eigen-solve
   long long w_stride = 0;
@@ -117,6 +121,32 @@ bool is_device_ptr(const void *p) {
 
 int round4(int x) { return (x + 3) & ~3; }
 
+// NVTX ranges (option S3TTV_OPT_NVTX): one per API call, and one per kernel
+// class as a pass is enqueued, so a profiler can attribute launches to the steps
+// of Alg. 1.  No-ops unless the option is on (and cheap without a tool attached).
+struct NvtxRange {
+  bool on;
+  NvtxRange(bool enable, const char *name) : on(enable) {
+    if (on) nvtxRangePushA(name);
+  }
+  ~NvtxRange() {
+    if (on) nvtxRangePop();
+  }
+};
+struct NvtxPhase {  // consecutive ranges: next() closes the open one
+  bool on, open = false;
+  explicit NvtxPhase(bool enable) : on(enable) {}
+  void next(const char *name) {
+    if (!on) return;
+    if (open) nvtxRangePop();
+    nvtxRangePushA(name);
+    open = true;
+  }
+  ~NvtxPhase() {
+    if (open) nvtxRangePop();
+  }
+};
+
 bool is_hsstv(const s3ttv_ctx *c) { return c->reg == S3TTV_REG_HSSTV1 || c->reg == S3TTV_REG_HSSTV2; }
 bool is_ssst(const s3ttv_ctx *c) { return c->reg == S3TTV_REG_SSST; }
 // parts of a block row: [D_v | D_h] (S3TTV, STV) or SSST's [D_v | D_h | D_s]
@@ -160,6 +190,11 @@ void free_all(s3ttv_ctx *c) {
 }
 
 int dmalloc(s3ttv_ctx *ctx, void **p, size_t bytes) {
+  if (ctx->alloc_limit && ctx->bytes + bytes > ctx->alloc_limit) {
+    *p = nullptr;
+    return fail(ctx, S3TTV_ENOMEM, "allocating %zu bytes would pass the context's limit of %zu (holding %zu)", bytes,
+                ctx->alloc_limit, ctx->bytes);
+  }
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -516,6 +551,8 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
                  cudaEvent_t *ev) {
   const Dims &dm = ctx->dm;
   cudaStream_t st = ctx->stream;
+  NvtxPhase ph(ctx->nvtx);
+  ph.next("primal (steps 2-7)");
   if (ev) CU(cudaEventRecord(ev[0], st));
   PrimalArgs pa;
   pa.Zv = ctx->Zv[par];
@@ -552,6 +589,7 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   }
   CU(launch_primal(pa, grid_e, st));
   if (ev) CU(cudaEventRecord(ev[1], st));
+  ph.next("l1-ball thresholds (steps 3-4)");
 
   L1Args la;
   la.x[0] = ctx->zs;
@@ -568,6 +606,7 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   CU(launch_l1_scan(la, 3, st));
   if (ev) CU(cudaEventRecord(ev[2], st));
 
+  ph.next("block dual (steps 8-11)");
   if (ctx->reg == S3TTV_REG_SSTV) {
     CU(launch_sstv_dual(ctx->ubar, ctx->Y, ctx->Y + dm.Np, ctx->Zv[par ^ 1], ctx->Zh[par ^ 1], dm,
                         (float)ctx->gam[3], grid_e, st));
@@ -610,6 +649,7 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   }
   if (ev) CU(cudaEventRecord(ev[3], st));
 
+  ph.next("dual (steps 12-13)");
   DualArgs da;
   da.zs = ctx->zs;
   da.zt = ctx->zt;
@@ -637,6 +677,7 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   fa.grid_d = grid_e;
   fa.eps = ctx->eps;
   fa.g3 = ctx->gam[5];
+  ph.next("finalize (step 14, stop rule)");
   CU(launch_finalize(fa, st));
   if (ev) CU(cudaEventRecord(ev[5], st));
   // SSTV and HSSTV: one elementwise dual kernel in place of xfield + block dual
@@ -820,6 +861,14 @@ int s3ttv_set_option(s3ttv_ctx *ctx, int key, double value) {
         ctx->warm_valid = false;
       }
       return S3TTV_OK;
+    case S3TTV_OPT_ALLOC_LIMIT:
+      if (!(value >= 0.0 && value < 1.8e19)) return fail(ctx, S3TTV_EINVAL, "alloc_limit must be >= 0 bytes");
+      ctx->alloc_limit = (size_t)value;
+      return S3TTV_OK;
+    case S3TTV_OPT_NVTX:
+      if (value != 0 && value != 1) return fail(ctx, S3TTV_EINVAL, "nvtx must be 0 or 1");
+      ctx->nvtx = value == 1;
+      return S3TTV_OK;
     case S3TTV_OPT_FP64_FALLBACK:
       if (value != 0 && value != 1) return fail(ctx, S3TTV_EINVAL, "fp64_fallback must be 0 or 1");
       ctx->fp64_fallback = value == 1;
@@ -879,6 +928,7 @@ int s3ttv_setup(s3ttv_ctx *ctx, const float *v, int N1, int N2, int N3, float ep
                 float mu_min, float mu_max, int k) {
   int rc = check_problem(ctx, v, N1, N2, N3, eps, alpha, beta, mu_min, mu_max, k);
   if (rc) return rc;
+  NvtxRange nr(ctx->nvtx, "s3ttv_setup");
   DeviceGuard g(ctx->device);
   ctx->ready = false;
   const Dims dm = make_dims(N1, N2, N3);
@@ -914,6 +964,7 @@ int s3ttv_setup(s3ttv_ctx *ctx, const float *v, int N1, int N2, int N3, float ep
 
 int s3ttv_iterate(s3ttv_ctx *ctx, int n, float tol, s3ttv_info *info) {
   if (!ctx) return S3TTV_EINVAL;
+  NvtxRange nr(ctx->nvtx, "s3ttv_iterate");
   const double t0 = now_s();
   if (info) memset(info, 0, sizeof(*info));
   if (!ctx->ready) return fail(ctx, S3TTV_ESTATE, "s3ttv_iterate before s3ttv_setup");
@@ -1082,6 +1133,7 @@ int s3ttv_solve(s3ttv_ctx *ctx, const float *v, int N1, int N2, int N3, float ep
   if (!u) return fail(ctx, S3TTV_EINVAL, "u is NULL");
   if (max_iter < 1) return fail(ctx, S3TTV_EINVAL, "max_iter = %d must be >= 1", max_iter);
   if (!(tol >= 0.f) || !std::isfinite(tol)) return fail(ctx, S3TTV_EINVAL, "tol must be finite and >= 0");
+  NvtxRange nr(ctx->nvtx, "s3ttv_solve");
   int rc = s3ttv_setup(ctx, v, N1, N2, N3, eps, alpha, beta, mu_min, mu_max, k);
   if (rc) {
     if (info) info->status = rc;
@@ -1154,6 +1206,7 @@ int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, in
                         s3ttv_info *infos) {
   const double t0 = now_s();
   if (!ctx) return S3TTV_EINVAL;
+  NvtxRange nr(ctx->nvtx, "s3ttv_solve_batched");
   if (n < 1) return fail(ctx, S3TTV_EINVAL, "n = %d must be >= 1", n);
   if (infos) memset(infos, 0, sizeof(*infos) * (size_t)n);
   if (!problems) return fail(ctx, S3TTV_EINVAL, "problems is NULL");
@@ -1359,6 +1412,7 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
                      int k, float gamma_Y, s3ttv_info *info) {
   if (info) memset(info, 0, sizeof(*info));
   if (!ctx) return S3TTV_EINVAL;
+  NvtxRange nr(ctx->nvtx, "s3ttv_block_dual");
   if (!Y || !ubar || !Zv || !Zh) return fail(ctx, S3TTV_EINVAL, "Y, ubar, Zv and Zh are required");
   if (k < 1 || N1 < k || N2 < k || N3 < 1) return fail(ctx, S3TTV_EINVAL, "need N1, N2 >= k >= 1 and N3 >= 1");
   if (!(gamma_Y > 0.f) || !std::isfinite(gamma_Y)) return fail(ctx, S3TTV_EINVAL, "gamma_Y must be > 0");
