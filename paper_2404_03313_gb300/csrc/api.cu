@@ -996,6 +996,7 @@ int s3ttv_iterate(s3ttv_ctx *ctx, int n, float tol, s3ttv_info *info) {
         Cand c;
         c.tc = tc;
         c.minb = minb;
+        c.sh.fb_smem = bd.fb_smem;  // the FP64 re-solve stays on while the forms are timed
         if (block_dual_variant_shape(ctx, ctx->dm, ctx->k, tc, minb, &c.sh) == S3TTV_OK) cands.push_back(c);
       }
     ctx->err[0] = 0;
