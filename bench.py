@@ -45,7 +45,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per voxel of one block-dual launch, from an ncu
 # capture of the kernel whose source hashes to `sha` (profiles/block_dual_k5_*.md);
 # traffic is reported only while the kernel source is unchanged.
-BLOCK_DUAL_TRAFFIC = {"sha": "92ee4e96de1c4e70", "k": 5, "bytes_per_voxel": (594.854400e6 + 612.021504e6) / 2097152}
+BLOCK_DUAL_TRAFFIC = {"sha": "7c0b7dc559a0bd7b", "k": 5, "bytes_per_voxel": (592.442368e6 + 610.694400e6) / 2097152}
 
 
 # ---------------------------------------------------------------------------
