@@ -53,7 +53,7 @@ typedef enum s3ttv_status {
   S3TTV_ENOMEM = -2,       /* device allocation failed                               */
   S3TTV_ECUDA = -3,        /* CUDA runtime error                                     */
   S3TTV_ENUMERIC = -4,     /* NaN or Inf appeared in the iterates                    */
-  S3TTV_EUNSUPPORTED = -5, /* valid but outside what this build supports (see each call) */
+  S3TTV_EUNSUPPORTED = -5, /* valid but outside what this library supports (see each call) */
   S3TTV_ESTATE = -6,       /* call made before s3ttv_setup                           */
   S3TTV_ETOOBIG = -7       /* input larger than an allocation-free entry point takes */
 } s3ttv_status;
@@ -249,7 +249,7 @@ int s3ttv_kernel_stats(const s3ttv_ctx *ctx, double *ms, long long *launches);
  * alpha    radius of the l1 ball of the sparse noise s (eq. constraint_sparse), >= 0.
  * beta     radius of the l1 ball of the stripe noise t (eq. constraint_stripe), >= 0.
  * mu_min, mu_max  box of u (eq. constraint_box), mu_min < mu_max.
- * k        block side (k x k x N3 blocks), 1 <= k <= min(N1, N2); this build supports k <= 12
+ * k        block side (k x k x N3 blocks), 1 <= k <= min(N1, N2); this library supports k <= 12
  *          (k <= 5 on the tensor-core or CUDA-core per-warp path, 6..12, the paper's
  *          own 10 x 10 blocks included, on a per-CTA path in FP32) and N1 * N2 < 2^31,
  *          N1 * N2 * N3 < 2^33 (S3TTV_EUNSUPPORTED otherwise).

@@ -348,9 +348,9 @@ int block_dual_variant_shape(s3ttv_ctx *ctx, const Dims &dm, int k, int tc, int 
 
 int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, BdShape *sh) {
   if (dm.P > 2147483647LL)  // the kernels index pixels with 32-bit integers
-    return fail(ctx, S3TTV_EUNSUPPORTED, "N1 * N2 = %lld pixels: this build supports fewer than 2^31", dm.P);
+    return fail(ctx, S3TTV_EUNSUPPORTED, "N1 * N2 = %lld pixels: this library supports fewer than 2^31", dm.P);
   if (dm.Np / 4 > 2147483647LL)  // and float4 chunks of bands with 32-bit integers
-    return fail(ctx, S3TTV_EUNSUPPORTED, "%lld voxels: this build supports fewer than 2^33", dm.Np);
+    return fail(ctx, S3TTV_EUNSUPPORTED, "%lld voxels: this library supports fewer than 2^33", dm.Np);
   sh->v.k = k;
   sh->v.tc = ctx->tensor_cores;
   const bool stacked = ctx->layout == S3TTV_LAYOUT_STACKED;
@@ -434,7 +434,7 @@ int check_problem(s3ttv_ctx *ctx, const float *v, int N1, int N2, int N3, float 
   if (!(std::isfinite(mu_min) && std::isfinite(mu_max) && mu_min < mu_max))
     return fail(ctx, S3TTV_EINVAL, "need finite mu_min < mu_max");
   if ((long long)N1 * N2 * (long long)N3 > (1ll << 40)) return fail(ctx, S3TTV_EINVAL, "cube too large");
-  if (k > kMaxK) return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: this build supports k <= %d", k, kMaxK);
+  if (k > kMaxK) return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: this library supports k <= %d", k, kMaxK);
   return S3TTV_OK;
 }
 
@@ -742,7 +742,7 @@ const char *s3ttv_strerror(int status) {
     case S3TTV_ENOMEM: return "device allocation failed";
     case S3TTV_ECUDA: return "CUDA runtime error";
     case S3TTV_ENUMERIC: return "NaN or Inf in the iterates";
-    case S3TTV_EUNSUPPORTED: return "not supported by this build";
+    case S3TTV_EUNSUPPORTED: return "not supported by this library";
     case S3TTV_ESTATE: return "no problem set up";
     case S3TTV_ETOOBIG: return "input larger than the allocation-free entry point takes";
     default: return "unknown status";
@@ -1420,7 +1420,7 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   if (ctx->reg == S3TTV_REG_SSTV || is_hsstv(ctx))
     return fail(ctx, S3TTV_EUNSUPPORTED, "SSTV and HSSTV have no block duals");
   if (is_ssst(ctx)) return fail(ctx, S3TTV_EUNSUPPORTED, "SSST's block duals run inside the solver only");
-  if (k > kMaxK) return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: this build supports k <= %d", k, kMaxK);
+  if (k > kMaxK) return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: this library supports k <= %d", k, kMaxK);
   DeviceGuard g(ctx->device);
   const Dims dm = make_dims(N1, N2, N3);
   int rc;
@@ -1487,7 +1487,7 @@ int s3ttv_objective(s3ttv_ctx *ctx, const float *u, int N1, int N2, int N3, int 
   if (k < 1 || N1 < k || N2 < k || N3 < 1) return fail(ctx, S3TTV_EINVAL, "need N1, N2 >= k >= 1 and N3 >= 1");
   const int stacked = ctx->layout == S3TTV_LAYOUT_STACKED;
   if (k > (stacked || is_ssst(ctx) ? kMaxStackedK : kMaxK))
-    return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: this build supports k <= %d", k,
+    return fail(ctx, S3TTV_EUNSUPPORTED, "k = %d: this library supports k <= %d", k,
                 stacked || is_ssst(ctx) ? kMaxStackedK : kMaxK);
   if (is_ssst(ctx) && (stacked || ctx->open_s))
     return fail(ctx, S3TTV_EUNSUPPORTED, "SSST takes the paper layout and the periodic spectral boundary");

@@ -166,7 +166,7 @@ int block_dual_threads();
 int block_dual_group();
 // All return cudaErrorInvalidValue for an unsupported variant.
 cudaError_t launch_block_dual(const BlockDualArgs &a, const BdVariant &v, int grid, size_t smem, cudaStream_t st);
-bool block_dual_has(const BdVariant &v);  // compiled in this build
+bool block_dual_has(const BdVariant &v);  // this variant is compiled into the library
 // Larger blocks, k = kMinLargeK..kMaxLargeK (block_dual_large.cu): one CTA of
 // block_dual_large_threads() threads per block at a time, FP32 CUDA cores.
 // The same kernel also runs the stacked layout (2 k^2 rows of N3 bands, rows 2r
