@@ -328,8 +328,10 @@ int s3ttv_l1_ball(s3ttv_ctx *ctx, const float *x, float *out, long long n,
  * (eq. ProxConjugate) clips the singular values of Y'_l at 1; then
  * Z = sum_l P_l^T Y_l is returned split into Zv (column 2b parts) and Zh.
  * Y: [N1*N2][k*k][2*N3], updated in place; ubar: cube; Zv, Zh: output cubes.
- * All host or device.  info (may be NULL) reports jacobi_nonconverged.
- * Uses the context's workspace (replaces any problem set up before). */
+ * All host or device.  info (may be NULL) reports jacobi_nonconverged and
+ * jacobi_fallbacks (blocks re-solved in FP64, S3TTV_OPT_FP64_FALLBACK).
+ * Uses the context's workspace (replaces any problem set up before).
+ * S3TTV_EUNSUPPORTED with the SSTV, HSSTV or SSST regularisers. */
 int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, float *Zh,
                      int N1, int N2, int N3, int k, float gamma_Y, s3ttv_info *info);
 
@@ -344,7 +346,12 @@ int s3ttv_tuned_form(const s3ttv_ctx *ctx, int *tensor_cores, int *ctas_per_sm);
  * value: host double.  Computed in FP64 (the block entries from the FP32 cube,
  * the Gram of each block and a one-sided Jacobi on its rows, sigma =
  * sqrt(eigenvalue)); an evaluation aid, far slower than a solver pass.
- * S3TTV_ENUMERIC if u is not finite or a block does not converge; k <= 12. */
+ * With S3TTV_OPT_REGULARIZER set to a comparison regulariser the value is that
+ * regulariser's (STV, SSST: the same FP64 nuclear norms of their blocks; SSTV,
+ * HSSTV: their l1 or l1,2 norms); the layout and spectral boundary options
+ * apply as in the solver.
+ * S3TTV_ENUMERIC if u is not finite or a block does not converge; k <= 12
+ * (k <= 8 for the stacked layout and SSST). */
 int s3ttv_objective(s3ttv_ctx *ctx, const float *u, int N1, int N2, int N3, int k, double *value);
 
 /* Quality of a restored cube u against a reference cube ref (both host or
