@@ -100,3 +100,29 @@ def test_oracle_and_product_are_independent():
     csrc = os.path.join(ROOT, "paper_2404_03313_gb300", "csrc")
     for f in os.listdir(csrc):
         assert "oracle" not in open(os.path.join(csrc, f)).read().lower(), f
+
+
+def test_header_is_plain_c(lib):
+    """include/s3ttv.h compiles as strict C99 (no C++ or torch types in the
+    boundary), and a C program that takes the address of every entry point it
+    declares links against the library."""
+    import shutil
+    import subprocess
+    import tempfile
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    from paper_2404_03313_gb300 import LIB_PATH
+    fns = _declared_functions()
+    src = '#include "s3ttv.h"\n#include <stdio.h>\ntypedef void (*fn_t)(void);\n'
+    src += "static fn_t table[] = {\n" + "".join(f"  (fn_t)&{name},\n" for name in fns) + "};\n"
+    src += 'int main(void) {\n  printf("%d\\n", (int)(sizeof table / sizeof table[0]));\n  return 0;\n}\n'
+    with tempfile.TemporaryDirectory() as d:
+        c, o, exe = (os.path.join(d, x) for x in ("abi.c", "abi.o", "abi"))
+        with open(c, "w") as f:
+            f.write(src)
+        p = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                            os.path.join(ROOT, "include"), "-c", c, "-o", o], capture_output=True, text=True)
+        assert p.returncode == 0, p.stderr
+        p = subprocess.run([gcc, o, "-o", exe, os.path.abspath(LIB_PATH)], capture_output=True, text=True)
+        assert p.returncode == 0, p.stderr
