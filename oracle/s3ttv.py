@@ -13,7 +13,12 @@ Everything follows the paper's notation and the order of its steps:
   eq. prox_zeroset, eq. prox_l2ball_constraint, eq. prox_nuclear_norm, the
   l1-ball projection) and the step sizes (eq. stepsize_denoising).
 * Sec. IV-A: radii rule (eq. RadiusSet), stopping rule (eq. StopCri_simulated),
-  MPSNR (eq. MPSNR).
+  MPSNR (eq. MPSNR), MSSIM (eq. MSSIM), 2-D SAM (eq. 2D_SAM), the objective of
+  Prob. (S3TTV_denoising).
+* Sec. IV: the comparison regularisers run through the same P-PDS (``reg=``):
+  STV, SSTV, HSSTV1/2 and SSST, with their Lemma 1 step sizes.
+* Layout variants (``layout="stacked"``, ``periodic_s=False``): the (2k^2) x N3
+  stacking of the vertical and horizontal rows and the open spectral boundary.
 
 Readings of passages the paper leaves open:
 D_v differences along the first (vertical, i) axis and D_h along the second (j);
