@@ -699,3 +699,217 @@ def test_ssst_step_sizes_adjoint_and_k1_closed_form():
     dv, dh, ds = (np.roll(u, -1, ax) - u for ax in (0, 1, 2))
     expect = np.sqrt((dv ** 2 + dh ** 2 + ds ** 2).sum(axis=2)).sum()
     assert O.objective(u, 1, reg="ssst") == pytest.approx(expect, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Alg. 1, one whole pass written out by hand (steps 2-14 and the stop rule).
+#
+# Every step is an explicit index loop over the cube, in the order Alg. 1 prints
+# them; the block operator comes from assemble_operator (built entry by entry
+# from the index definitions), step 10 is the clip of the singular values of Y'
+# at 1 (the Moreau form of eq. ProxConjugate, not the oracle's prox route), and
+# the l1-ball projections are a bisection on the threshold (not the oracle's
+# sort).  Steps 12-14 must read the extrapolated t_bar, u_bar, s_bar; the
+# variants that read t+, u+, s+ instead are built too, and must disagree.
+# ---------------------------------------------------------------------------
+def _l1_bisect(x, r):
+    """argmin ||y - x|| over ||y||_1 <= r: soft threshold at the tau with
+    sum max(|x| - tau, 0) = r, found by bisection (r = 0 gives 0)."""
+    a = np.abs(x)
+    if a.sum() <= r:
+        return x.copy()
+    if r <= 0.0:
+        return np.zeros_like(x)
+    lo, hi = 0.0, float(a.max())
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if np.maximum(a - mid, 0.0).sum() > r:
+            lo = mid
+        else:
+            hi = mid
+    tau = 0.5 * (lo + hi)
+    return np.sign(x) * np.maximum(a - tau, 0.0)
+
+
+def _pass_by_hand(st, v, k, eps, alpha, beta, mu_min, mu_max, g, AY, read_bar=(True, True, True)):
+    """One pass of Alg. 1 from state ``st``; ``read_bar`` = whether steps 12-14
+    read (u_bar, s_bar, t_bar) (Alg. 1) or (u+, s+, t+) (a planted mistake)."""
+    N1, N2, N3 = v.shape
+    u, s, t, y2, y3, Y = (st[n] for n in ("u", "s", "t", "y2", "y3", "Y"))
+    # step 2: u+ = P_[mu_min, mu_max](u - gamma_u (L^T Y + y3)), L^T from the assembled operator
+    LtY = (AY.T @ Y.ravel()).reshape(v.shape)
+    u_new = np.empty_like(u)
+    for i in range(N1):
+        for j in range(N2):
+            for b in range(N3):
+                x = u[i, j, b] - g["u"] * (LtY[i, j, b] + y3[i, j, b])
+                u_new[i, j, b] = min(max(x, mu_min), mu_max)
+    # step 3: s+ = P_{B1, alpha}(s - gamma_s y3)
+    zs = np.empty_like(s)
+    for i in range(N1):
+        for j in range(N2):
+            for b in range(N3):
+                zs[i, j, b] = s[i, j, b] - g["s"] * y3[i, j, b]
+    s_new = _l1_bisect(zs, alpha)
+    # step 4: t+ = P_{B1, beta}(t - gamma_t (D_v^T y2 + y3)), (D_v^T y)[i] = y[i-1] - y[i]
+    zt = np.empty_like(t)
+    for i in range(N1):
+        for j in range(N2):
+            for b in range(N3):
+                dvt = y2[(i - 1) % N1, j, b] - y2[i, j, b]
+                zt[i, j, b] = t[i, j, b] - g["t"] * (dvt + y3[i, j, b])
+    t_new = _l1_bisect(zt, beta)
+    # steps 5-7: extrapolation
+    ub, sb, tb = np.empty_like(u), np.empty_like(s), np.empty_like(t)
+    for i in range(N1):
+        for j in range(N2):
+            for b in range(N3):
+                ub[i, j, b] = 2.0 * u_new[i, j, b] - u[i, j, b]
+                sb[i, j, b] = 2.0 * s_new[i, j, b] - s[i, j, b]
+                tb[i, j, b] = 2.0 * t_new[i, j, b] - t[i, j, b]
+    # steps 8-11: Y' = Y + gamma_Y P_l D D_s u_bar; Y+ = U min(Sigma, 1) V^T of Y'
+    X = (AY @ ub.ravel()).reshape(Y.shape)
+    Y_new = np.empty_like(Y)
+    for l in range(Y.shape[0]):
+        Yp = Y[l] + g["Y"] * X[l]
+        U, sv, Vt = np.linalg.svd(Yp, full_matrices=False)
+        Y_new[l] = (U * np.minimum(sv, 1.0)) @ Vt
+    ru, rs, rt = (ub if read_bar[0] else u_new), (sb if read_bar[1] else s_new), (tb if read_bar[2] else t_new)
+    # step 12: y2+ = y2 + gamma_2 D_v t_bar, (D_v x)[i] = x[i+1] - x[i]
+    y2_new = np.empty_like(y2)
+    for i in range(N1):
+        for j in range(N2):
+            for b in range(N3):
+                y2_new[i, j, b] = y2[i, j, b] + g["y2"] * (rt[(i + 1) % N1, j, b] - rt[i, j, b])
+    # step 13: y3' = y3 + gamma_3 (u_bar + s_bar + t_bar)
+    y3p = np.empty_like(y3)
+    for i in range(N1):
+        for j in range(N2):
+            for b in range(N3):
+                y3p[i, j, b] = y3[i, j, b] + g["y3"] * (ru[i, j, b] + rs[i, j, b] + rt[i, j, b])
+    # step 14: y3+ = y3' - gamma_3 P_{B2, eps}^v(y3' / gamma_3)
+    ss = 0.0
+    for i in range(N1):
+        for j in range(N2):
+            for b in range(N3):
+                ss += (y3p[i, j, b] / g["y3"] - v[i, j, b]) ** 2
+    nrm = math.sqrt(ss)
+    y3_new = np.empty_like(y3)
+    for i in range(N1):
+        for j in range(N2):
+            for b in range(N3):
+                w = y3p[i, j, b] / g["y3"]
+                pw = w if nrm <= eps else v[i, j, b] + eps * (w - v[i, j, b]) / nrm
+                y3_new[i, j, b] = y3p[i, j, b] - g["y3"] * pw
+    # eq. StopCri_simulated with the previous iterate's norm (||u+ - u|| alone if ||u|| = 0)
+    du2, nu2 = 0.0, 0.0
+    for i in range(N1):
+        for j in range(N2):
+            for b in range(N3):
+                du2 += (u_new[i, j, b] - u[i, j, b]) ** 2
+                nu2 += u[i, j, b] ** 2
+    relc = math.sqrt(du2) / math.sqrt(nu2) if nu2 > 0 else math.sqrt(du2)
+    return {"u": u_new, "s": s_new, "t": t_new, "y2": y2_new, "y3": y3_new, "Y": Y_new}, relc
+
+
+def _hand_case(policy):
+    from synthetic import CubeSpec, make_cube, random_state
+    N1, N2, N3, k = 4, 5, 3, 2
+    _, v = make_cube(CubeSpec(N1, N2, N3, regions=2, endmembers=2, seed=31))
+    v = v.astype(np.float64)
+    st = {key: val.astype(np.float64) for key, val in random_state(N1, N2, N3, k, seed=32, scale=0.6).items()}
+    st["u"] = st["u"] * 1.4 - 0.2  # some entries outside the box, so step 2's clamp acts
+    g = O.step_sizes(N1, N2, k, policy)
+    AY = O.assemble_operator(N1, N2, N3, k)[("Y", "u")]
+    # radii that make every projection of the pass active: half the l1 norms of
+    # the arguments of steps 3-4, half the distance of step 14's argument
+    big, _ = _pass_by_hand(st, v, k, 1e30, 1e30, 1e30, 0.0, 1.0, g, AY)
+    zs = st["s"] - g["s"] * st["y3"]
+    zt = st["t"] - g["t"] * (np.roll(st["y2"], 1, axis=0) - st["y2"] + st["y3"])
+    alpha, beta = 0.5 * np.abs(zs).sum(), 0.5 * np.abs(zt).sum()
+    probe, _ = _pass_by_hand(st, v, k, 1e30, alpha, beta, 0.0, 1.0, g, AY)
+    bars = [2 * probe[x] - st[x] for x in ("u", "s", "t")]
+    eps = 0.5 * np.linalg.norm((st["y3"] + g["y3"] * sum(bars)) / g["y3"] - v)
+    return st, v, k, eps, alpha, beta, g, AY
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("policy", ["paper", "pc_exact"])
+def test_one_pass_by_hand(policy):
+    st, v, k, eps, alpha, beta, g, AY = _hand_case(policy)
+    want, rel_want = _pass_by_hand(st, v, k, eps, alpha, beta, 0.0, 1.0, g, AY)
+    got, rel_got = O.iterate(st, v, k, eps, alpha, beta, 0.0, 1.0, g)
+    for key in ("u", "s", "t", "y2", "y3", "Y"):
+        assert _rel(got[key], want[key]) <= 1e-11, key
+    assert rel_got == pytest.approx(rel_want, rel=1e-12)
+    # the case is not degenerate: every projection is active and the
+    # extrapolated values differ from the new ones
+    assert np.any(want["u"] == 0.0) or np.any(want["u"] == 1.0)
+    assert np.abs(want["s"]).sum() == pytest.approx(alpha, rel=1e-9)
+    assert np.abs(want["t"]).sum() == pytest.approx(beta, rel=1e-9)
+    for x in ("u", "s", "t"):
+        assert _rel(2 * want[x] - st[x], want[x]) > 0.1
+
+
+@pytest.mark.parametrize("planted", [(False, True, True), (True, False, True), (True, True, False)])
+def test_one_pass_by_hand_detects_unextrapolated_reads(planted):
+    """Steps 12-14 reading u+, s+ or t+ instead of the extrapolated values is a
+    plausible slip; the hand pass built that way must be far from the oracle,
+    so the pin above would catch it."""
+    st, v, k, eps, alpha, beta, g, AY = _hand_case("pc_exact")
+    wrong, _ = _pass_by_hand(st, v, k, eps, alpha, beta, 0.0, 1.0, g, AY, read_bar=planted)
+    got, _ = O.iterate(st, v, k, eps, alpha, beta, 0.0, 1.0, g)
+    keys = ("y3",) if planted[2] else ("y2", "y3")
+    for key in keys:
+        assert _rel(got[key], wrong[key]) > 1e-3, key
+
+
+def test_relative_change_uses_the_previous_iterate():
+    """C7: ||u+ - u|| / ||u|| with u the iterate before the pass.  All duals 0
+    and u = 2 everywhere (outside the box [0, 1]): step 2 only clamps, u+ = 1,
+    so the relative change is |1 - 2| / |2| = 1/2 exactly (1 if the new
+    iterate's norm were used)."""
+    shape = (3, 4, 3)
+    v = np.full(shape, 0.5)
+    st = O.init_state(v, 2)
+    st["u"] = np.full(shape, 2.0)
+    g = O.step_sizes(3, 4, 2, "pc_exact")
+    new, rel = O.iterate(st, v, 2, 1e6, 1e6, 1e6, 0.0, 1.0, g)
+    assert np.all(new["u"] == 1.0)
+    assert rel == 0.5
+
+
+def test_relative_change_at_zero_iterate():
+    """C7 with ||u|| = 0: the change itself.  u = 0, y3 = -c everywhere, all
+    other duals 0: u+ = gamma_u c (inside the box), so the relative change is
+    gamma_u c sqrt(N)."""
+    shape = (3, 4, 3)
+    v = np.full(shape, 0.5)
+    st = O.init_state(v, 2)
+    st["u"] = np.zeros(shape)
+    c = 0.75
+    st["y3"] = np.full(shape, -c)
+    g = O.step_sizes(3, 4, 2, "pc_exact")
+    new, rel = O.iterate(st, v, 2, 1e6, 1e6, 1e6, 0.0, 1.0, g)
+    np.testing.assert_allclose(new["u"], g["u"] * c, rtol=1e-15)
+    assert rel == pytest.approx(g["u"] * c * math.sqrt(v.size), rel=1e-14)
+
+
+def test_solve_counts_completed_passes_and_stops_on_the_first_crossing():
+    """C7: the test runs after every pass; the count is the passes completed."""
+    v = np.full((4, 4, 3), 0.37)  # a fixed point: the first pass already changes nothing
+    st, it, rel = O.solve(v, 2, 1.0, 1.0, 1.0, max_iter=50, tol=1e-5)
+    assert it == 1 and rel == 0.0
+    from synthetic import CubeSpec, make_cube
+    _, v = make_cube(CubeSpec(6, 6, 4, regions=2, endmembers=2, seed=33))
+    trace = []
+    O.solve(v, 2, 0.5, 1.0, 1.0, max_iter=40, tol=0.0, policy="pc_exact", trace=trace)
+    tol = trace[25] * 1.0000001  # first crossing at pass 26 unless an earlier pass is lower
+    first = next(i for i, r in enumerate(trace) if r < tol) + 1
+    st, it, rel = O.solve(v, 2, 0.5, 1.0, 1.0, max_iter=40, tol=tol, policy="pc_exact")
+    assert it == first and rel == trace[first - 1]
+    st, it, rel = O.solve(v, 2, 0.5, 1.0, 1.0, max_iter=7, tol=1e-30, policy="pc_exact")
+    assert it == 7
