@@ -189,8 +189,9 @@ __global__ void __launch_bounds__(1024) l1_scan_kernel(L1Args a, int level) {
   }
 }
 
-__global__ void soft_threshold_kernel(const float *__restrict__ x, float *__restrict__ out, long long n,
-                                      const Scalars *sc, int prob) {
+// x and out may be the same buffer (an in-place projection): each element is
+// read and written by the same thread, and the pointers carry no __restrict__.
+__global__ void soft_threshold_kernel(const float *x, float *out, long long n, const Scalars *sc, int prob) {
   const float tau = sc->l1[prob].tau, tau_lo = sc->l1[prob].tau_lo;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)

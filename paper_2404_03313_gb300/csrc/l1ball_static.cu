@@ -46,13 +46,16 @@ int scratch_address(int dev, unsigned char **out) {
   return S3TTV_OK;
 }
 
-bool on_device(const void *p) {
+// Device memory of device dev itself, or managed memory.  Memory of another
+// GPU is refused: the kernels run on dev, and without peer access such a
+// pointer is not reachable from it.
+bool on_device(const void *p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == dev);
 }
 
 }  // namespace
@@ -68,12 +71,13 @@ extern "C" int s3ttv_l1_ball_static(const float *x, float *out, long long n, dou
     if (tau_out) *tau_out = 0.0;
     return S3TTV_OK;
   }
-  if (!x || !out || !on_device(x) || !on_device(out)) return S3TTV_EINVAL;
+  if (!x || !out) return S3TTV_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return S3TTV_ECUDA;
   }
+  if (!on_device(x, dev) || !on_device(out, dev)) return S3TTV_EINVAL;
   unsigned char *base = nullptr;
   int rc = scratch_address(dev, &base);
   if (rc) return rc;
