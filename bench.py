@@ -13,12 +13,23 @@ workload is the seeded synthetic 256x256x128 cube with k = 5 blocks.
            device->host copy of u, s, t inside the timed region.
 ``roofline`` the dominant kernel (block dual, steps 8-11): algorithmic bytes per
            launch / its average CUDA-event duration in the timed region.
-``cpu_baseline`` the FP64 oracle timed on this host on a bounded crop, scaled to
-           the full cube (a reported baseline, not a target).
-Also reported: seconds and passes to the paper's stop rule (||u+ - u||/||u|| <
-1e-5, cap 5000) and the restored cube's MPSNR.
+``cpu_baseline`` the FP64 oracle timed on this host: one pass over the whole
+           cube (not scaled), the cores it really used (CPU seconds / wall
+           seconds) and the CPU model, plus a one-thread run on a crop (a
+           reported baseline, not a target).
+``forms``  the same passes with the block-dual products on the tensor cores
+           (three TF32 products per FP32 product) and as plain FP32 FMAs on
+           the CUDA cores: passes/s and the block dual's roofline fraction.
+``to_tol`` seconds and passes to the paper's stop rule (||u+ - u||/||u|| <
+           1e-5, cap 5000) with the printed step sizes, and under PC_EXACT
+           (gamma_u = 1/(8k^2 + 1), where the rule fires) for both product
+           forms, with the restored cube's MPSNR.
+``precision_form`` the 304x304x191 cube to the stop rule (PC_EXACT) with both
+           product forms: seconds, passes and MPSNR side by side.
 
-``--impl reference`` times the FP64 oracle instead (host cores, rank 0 only).
+``--impl reference`` times the FP64 oracle instead (host cores, rank 0 only):
+one step is one oracle pass over a crop of the cube, so ms_per_step x steps
+is the time it really spends; value scales that rate to the full cube.
 Multi-GPU: the method has no exchange step at one cube, so N ranks run N
 independent replicas (weak scaling); only the timing is reduced over ranks.
 """
@@ -41,11 +52,17 @@ if ROOT not in sys.path:
 METRIC = "S3TTV seconds-to-tol at 256×256×128; P-PDS iters/s; % of roofline"
 UNIT = "iter/s"
 DEFAULT_WORKLOAD = "s3ttv_256x256x128_k5"
+# block-dual forms (S3TTV_OPT_TENSOR_CORES)
+FORM_NAMES = {2: "tensor_cores_3xtf32_stream", 1: "tensor_cores_3xtf32_group", 0: "cuda_cores_fp32"}
+FORM_TEXT = {2: "tensor cores, each FP32 operand split into two TF32 parts; every warp streams a block of its own",
+             1: "tensor cores, each FP32 operand split into two TF32 parts; four warps share each block",
+             0: "CUDA cores, FP32 FMA"}
 FALLBACK_HBM_GBS = 6800.0
-# DRAM bytes (read + write) per voxel of one block-dual launch, from an ncu
-# capture of the kernel whose source hashes to `sha` (profiles/block_dual_k5_*.md);
-# traffic is reported only while the kernel source is unchanged.
-BLOCK_DUAL_TRAFFIC = {"sha": "7c0b7dc559a0bd7b", "k": 5, "bytes_per_voxel": (592.442368e6 + 610.694400e6) / 2097152}
+# DRAM bytes (read + write) per voxel of one block-dual launch (the streaming
+# form), from an ncu capture of the kernel whose source hashes to `sha`
+# (profiles/block_dual_stream_k5_128x128x128.md); traffic is reported only
+# while the kernel source is unchanged.
+BLOCK_DUAL_TRAFFIC = {"sha": "77bd2886b2039c6f", "k": 5, "bytes_per_voxel": (524.860416e6 + 486.513664e6) / 2097152}
 
 
 # ---------------------------------------------------------------------------
@@ -177,10 +194,39 @@ def measured_peaks():
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded crop of the same workload
 # ---------------------------------------------------------------------------
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or "unknown"
+
+
+def cpu_seconds():
+    """User + system CPU seconds of this process so far (all its threads)."""
+    import resource
+    r = resource.getrusage(resource.RUSAGE_SELF)
+    return r.ru_utime + r.ru_stime
+
+
 def oracle_rate(spec, crop, seconds_budget, min_steps=2, max_steps=None, warmup=0, policy="paper"):
     """Time oracle passes on the top-left crop x crop x N3 of the workload cube
-    (same generator, same noise model).  Returns (full-cube passes/s, passes,
-    seconds, threads, sample text)."""
+    (same generator, same noise model).  Returns a dict: full-cube passes/s
+    (the crop's rate scaled by pixels), passes, seconds, seconds per crop pass,
+    the crop's share of the cube, the cores actually used (CPU seconds / wall
+    seconds over the timed passes) and a description of the sample."""
     import numpy as np
     import oracle as O
     from synthetic import CubeSpec, make_cube
@@ -194,7 +240,7 @@ def oracle_rate(spec, crop, seconds_budget, min_steps=2, max_steps=None, warmup=
     st = O.init_state(v, spec.k)
     for _ in range(warmup):
         st, _ = O.iterate(st, v, spec.k, eps, alpha, beta, 0.0, 1.0, g)
-    n, t0 = 0, time.perf_counter()
+    n, c0, t0 = 0, cpu_seconds(), time.perf_counter()
     while True:
         st, _ = O.iterate(st, v, spec.k, eps, alpha, beta, 0.0, 1.0, g)
         n += 1
@@ -203,31 +249,71 @@ def oracle_rate(spec, crop, seconds_budget, min_steps=2, max_steps=None, warmup=
             break
         if max_steps is None and n >= min_steps and el >= seconds_budget:
             break
-    per_pass_full = el / n * (spec.N1 * spec.N2) / (crop * crop)
-    try:
-        threads = len(os.sched_getaffinity(0))
-    except AttributeError:
-        threads = os.cpu_count()
+    cores = (cpu_seconds() - c0) / el if el > 0 else 1.0
+    frac = (crop * crop) / (spec.N1 * spec.N2)
+    per_pass_full = el / n / frac
     sample = (f"{n} oracle passes (FP64, numpy/LAPACK SVD per block) on a {crop}x{crop}x{spec.N3} crop, "
               f"k={spec.k}, scaled by {spec.N1 * spec.N2}/{crop * crop} pixels to one full-cube pass")
-    return 1.0 / per_pass_full, n, el, threads, sample
+    return {"rate": 1.0 / per_pass_full, "passes": n, "seconds": el, "seconds_per_pass": el / n,
+            "fraction": frac, "cores": cores, "sample": sample}
+
+
+def oracle_full_pass(spec, policy="paper"):
+    """One oracle pass over the whole workload cube, timed (not scaled): returns
+    (seconds, cores actually used)."""
+    import numpy as np
+    import oracle as O
+    from synthetic import make_cube
+    _, v = make_cube(spec)
+    v = v.astype(np.float64)
+    eps, alpha, beta = O.radii(v.size, spec.sigma, spec.p_s, spec.p_t)
+    g = O.step_sizes(spec.N1, spec.N2, spec.k, policy)
+    st = O.init_state(v, spec.k)
+    c0, t0 = cpu_seconds(), time.perf_counter()
+    st, _ = O.iterate(st, v, spec.k, eps, alpha, beta, 0.0, 1.0, g)
+    el = time.perf_counter() - t0
+    return el, (cpu_seconds() - c0) / el
+
+
+def oracle_one_thread(workload, crop, seconds_budget, policy):
+    """oracle_rate in a child process whose BLAS / LAPACK / OpenMP pools are
+    limited to one thread."""
+    env = dict(os.environ)
+    for key in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[key] = "1"
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; from synthetic import WORKLOADS; "
+            "print(json.dumps(bench.oracle_rate(WORKLOADS[%r], %d, %r, policy=%r)))"
+            % (ROOT, workload, crop, float(seconds_budget), policy))
+    try:
+        p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        return json.loads(p.stdout.strip().splitlines()[-1])
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+        return None
 
 
 def run_reference(args, spec):
+    """The oracle arm: one step = one oracle pass over a crop of the workload
+    cube (the bounded sample), so ms_per_step x steps is the time really spent;
+    value = full-cube passes/s, the crop's rate scaled by its share of the
+    pixels."""
     rank, _, world = dist_env()
     if rank != 0:
         return 0
     total = args.steps + args.warmup
     crop = 32 if total > 40 else 64
-    rate, n, el, threads, sample = oracle_rate(spec, crop, 0.0, max_steps=args.steps, warmup=args.warmup,
-                                               policy=args.policy)
+    r = oracle_rate(spec, crop, 0.0, max_steps=args.steps, warmup=args.warmup, policy=args.policy)
+    rate = r["rate"]
     out = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / rate, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * r["seconds_per_pass"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "N1": spec.N1, "N2": spec.N2, "N3": spec.N3, "k": spec.k,
-                   "policy": args.policy},
-        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+                   "policy": args.policy,
+                   "step": f"one oracle pass over a {crop}x{crop}x{spec.N3} crop "
+                           f"({r['fraction']:.4f} of the cube's pixels); value scales its rate to the full cube"},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": round(r["cores"], 2),
+                         "cores_available": os.cpu_count(), "cpu_model": cpu_model(), "kind": "oracle",
+                         "sample": r["sample"]},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -367,22 +453,102 @@ def run_ours(args, spec):
     e2e = {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * N / args.steps,
            "d2h_bytes_per_step": 12 * N / args.steps, "seconds": e2e_s}
 
-    # ---- seconds to the paper's stop rule ----
+    # ---- the other forms of the block duals on the same passes ----
+    # (k <= 5, paper layout, S3TTV: tensor cores with three TF32 products per
+    # FP32 product, a warp streaming each block or four warps sharing it, or
+    # plain FP32 FMAs on the CUDA cores)
+    forms = None
+    if spec.k <= 5 and not stacked and args.reg == "s3ttv":
+        forms = {}
+        for tc in (args.tensor_cores,) + tuple(x for x in (2, 1, 0) if x != args.tensor_cores):
+            if tc != args.tensor_cores:
+                solver.set_option(P.OPT_TENSOR_CORES, tc)
+                solver.iterate(args.warmup)
+                solver.set_option(P.OPT_PROFILE, 1)
+                f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                f0.record(stream)
+                solver.iterate(args.steps)
+                f1.record(stream)
+                torch.cuda.synchronize()
+                fms = dist_max(f0.elapsed_time(f1), world, device=f"cuda:{dev}")
+                fbd_ms, fbd_n = solver.kernel_stats()["block_dual"]
+                solver.set_option(P.OPT_PROFILE, 0)
+                solver.set_option(P.OPT_TENSOR_CORES, args.tensor_cores)
+            else:
+                fms, fbd_ms, fbd_n = ms_max, bd_ms, bd_n
+            fbd_s = fbd_ms / max(fbd_n, 1) / 1000.0
+            forms[FORM_NAMES[tc]] = {
+                "value": world * args.steps / (fms / 1000.0), "unit": UNIT, "ms_per_step": fms / args.steps,
+                "block_dual_ms": fbd_s * 1000.0,
+                "block_dual_frac": (alg_bytes / fbd_s / 1e9 / peak) if fbd_s > 0 else 0.0}
+
+    # ---- seconds to the paper's stop rule (||u+ - u|| / ||u|| < 1e-5, cap 5000) ----
+    def to_tol(slv, vin, cln, e, a, b, k, policy_id, tc, max_iter=5000, tol=1e-5):
+        slv.set_option(P.OPT_STEP_POLICY, policy_id)
+        slv.set_option(P.OPT_TENSOR_CORES, tc)
+        slv.set_option(P.OPT_CHECK_EVERY, 16)
+        u, _, _, inf = slv.solve(vin, e, a, b, k, max_iter=max_iter, tol=tol)
+        torch.cuda.synchronize()
+        return {"seconds": inf["seconds"], "iters": inf["iters"], "converged": bool(inf["converged"]),
+                "rel_change": inf["rel_change"], "mpsnr_restored": mpsnr(u.cpu().numpy(), cln),
+                "iters_per_s": inf["iters"] / inf["seconds"] if inf["seconds"] > 0 else None}
+
     tol_run = None
     if not args.no_tol_run:
-        solver.set_option(P.OPT_CHECK_EVERY, 16)
-        u, s, t, inf = solver.solve(vd, eps, alpha, beta, spec.k, max_iter=5000, tol=1e-5)
-        torch.cuda.synchronize()
-        tol_run = {"seconds": inf["seconds"], "iters": inf["iters"], "converged": bool(inf["converged"]),
-                   "rel_change": inf["rel_change"], "mpsnr_restored": mpsnr(u.cpu().numpy(), clean),
-                   "mpsnr_observed": mpsnr(v, clean), "stop_tol": 1e-5, "max_iter": 5000}
+        tol_run = to_tol(solver, vd, clean, eps, alpha, beta, spec.k, policy, args.tensor_cores)
+        tol_run.update({"policy": args.policy, "mpsnr_observed": mpsnr(v, clean), "stop_tol": 1e-5,
+                        "max_iter": 5000})
+        if args.policy == "paper" and args.reg == "s3ttv" and not stacked:
+            # PC_EXACT (gamma_u = 1/(8k^2 + 1), the exact Lemma 1 column sum):
+            # the stop rule fires; both product forms where both exist
+            pc = {}
+            pair = (args.tensor_cores, 0) if args.tensor_cores else (0, 2)
+            for tc in (pair if forms else (args.tensor_cores,)):
+                pc[FORM_NAMES[tc]] = to_tol(
+                    solver, vd, clean, eps, alpha, beta, spec.k, P.STEP_PC_EXACT, tc)
+            if len(pc) == 2:
+                a_, b_ = pc.values()
+                pc["mpsnr_diff_db"] = abs(a_["mpsnr_restored"] - b_["mpsnr_restored"])
+            tol_run["pc_exact"] = pc
+        solver.set_option(P.OPT_STEP_POLICY, policy)
+        solver.set_option(P.OPT_TENSOR_CORES, args.tensor_cores)
 
-    # ---- CPU baseline (oracle), rank 0 at N = 1 only ----
+    # ---- the precision form's comparison (304x304x191, k = 5): time to the stop
+    # rule of both product forms at equal MPSNR (PC_EXACT step sizes) ----
+    precision = None
+    if (args.workload == DEFAULT_WORKLOAD and not args.no_tol_run and not args.no_precision_run
+            and forms is not None):
+        from synthetic import WORKLOADS
+        spec3 = WORKLOADS["s3ttv_304x304x191_k5"]
+        clean3, v3 = make_cube(spec3)
+        e3, a3, b3 = P.radii(v3.size, spec3.sigma, spec3.p_s, spec3.p_t, 0.95)
+        v3d = torch.from_numpy(v3).to(f"cuda:{dev}")
+        s3 = P.Solver(dev, stream=stream)
+        precision = {"workload": "s3ttv_304x304x191_k5", "policy": "pc_exact"}
+        chosen = args.tensor_cores or 2
+        for tc in (chosen, 0):
+            precision[FORM_NAMES[tc]] = to_tol(s3, v3d, clean3, e3, a3, b3, spec3.k, P.STEP_PC_EXACT, tc)
+        precision["mpsnr_diff_db"] = abs(precision[FORM_NAMES[chosen]]["mpsnr_restored"]
+                                         - precision[FORM_NAMES[0]]["mpsnr_restored"])
+        precision["mpsnr_observed"] = mpsnr(v3, clean3)
+        s3.close()
+        del v3d
+
+    # ---- CPU baseline (oracle), rank 0 at N = 1 only: one full-cube pass timed
+    # on all host cores, and a one-thread run on a crop ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, n, el, threads, sample = oracle_rate(spec, 64, args.cpu_seconds, policy=args.policy)
-        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
-               "seconds": el}
+        full_s, full_cores = oracle_full_pass(spec, args.policy)
+        one = oracle_one_thread(args.workload, 32, args.cpu_seconds, args.policy)
+        cpu = {"value": 1.0 / full_s, "unit": UNIT, "cores": round(full_cores, 2),
+               "cores_available": os.cpu_count(), "cpu_model": cpu_model(), "kind": "oracle",
+               "sample": f"one oracle pass (FP64, numpy/LAPACK SVD per block) over the whole "
+                         f"{spec.N1}x{spec.N2}x{spec.N3} cube, k={spec.k}, timed, not scaled",
+               "seconds": full_s,
+               "one_thread": (None if one is None else
+                              {"value": one["rate"], "unit": UNIT, "cores": round(one["cores"], 2),
+                               "sample": one["sample"] + " (BLAS/OpenMP pools limited to one thread)",
+                               "seconds": one["seconds"]})}
 
     if rank == 0:
         out = {
@@ -393,8 +559,7 @@ def run_ours(args, spec):
                        "policy": args.policy, "layout": args.layout, "spectral": args.spectral, "reg": args.reg,
                        "autotuned_form": ({"tensor_cores": tuned[0], "ctas_per_sm": tuned[1]} if tuned else None),
                        "parallelism": f"replicas{world}",
-                       "block_dual_products": ("tensor cores, each FP32 operand split into two TF32 parts"
-                                               if args.tensor_cores else "CUDA cores, FP32 FMA"),
+                       "block_dual_products": FORM_TEXT[args.tensor_cores],
                        "l2": "inputs larger than L2 (block duals Y: %.2f GB, read and written every pass)"
                              % (8 * k2 * N / 1e9)},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
@@ -404,7 +569,7 @@ def run_ours(args, spec):
                               "unit": "GB/s"},
             "kernel_avg_ms": kernel_ms, "jacobi_nonconverged": info["jacobi_nonconverged"],
             "jacobi_sweeps_mean": info["jacobi_sweeps"],
-            "to_tol": tol_run,
+            "to_tol": tol_run, "forms": forms, "precision_form": precision,
         }
         out["pass_roofline"]["frac"] = out["pass_roofline"]["achieved"] / peak
         print(json.dumps(out), flush=True)
@@ -726,8 +891,9 @@ def main(argv=None):
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--policy", choices=("paper", "pc_exact"), default="paper")
-    ap.add_argument("--tensor-cores", type=int, choices=(0, 1), default=1,
-                    help="block-dual Gram and apply on tensor cores (1) or CUDA cores (0)")
+    ap.add_argument("--tensor-cores", type=int, choices=(0, 1, 2), default=2,
+                    help="block-dual form: tensor cores with a warp streaming each block (2), tensor "
+                         "cores with four warps sharing each block (1), CUDA cores (0)")
     ap.add_argument("--layout", choices=("paper", "stacked"), default="paper",
                     help="block matrices: the paper's k^2 x 2N3 or the stacked 2k^2 x N3")
     ap.add_argument("--spectral", choices=("periodic", "open"), default="periodic",
@@ -743,6 +909,8 @@ def main(argv=None):
                     help="warm-start workload: fixed pass budget of the runs with the paper's step sizes")
     ap.add_argument("--no-tol-run", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision-run", action="store_true",
+                    help="skip the 304x304x191 time-to-tolerance comparison of the two product forms")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args(argv)
     if args.warmup < 3:

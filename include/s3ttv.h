@@ -71,6 +71,9 @@ typedef struct s3ttv_info {
   double jacobi_sweeps;    /* mean eigen-solve sweeps per block and pass             */
   int jacobi_fallbacks;    /* blocks re-solved in FP64 after their FP32 eigen-solve
                               reached the sweep cap (S3TTV_OPT_FP64_FALLBACK)      */
+  double first_order;      /* share of blocks and passes whose clip came from the
+                              first-order update in the kept basis
+                              (S3TTV_OPT_FIRST_ORDER)                              */
 } s3ttv_info;
 
 /* Step-size policies (option S3TTV_OPT_STEP_POLICY).
@@ -93,11 +96,15 @@ enum {
                                       eigenbasis it converged to in the previous pass
                                       (same result, fewer sweeps; 4 (k^2+1) k^2 bytes of
                                       workspace per block); 0: every pass starts cold     */
-  S3TTV_OPT_TENSOR_CORES = 7,      /* block duals (Alg. 1 steps 8-11): 1 (default) forms
-                                      the Gram Y'Y'^T and the product M Y' on tensor cores,
-                                      each FP32 operand split into two TF32 parts and three
-                                      of the four part products kept (FP32-level accuracy);
-                                      0: the same products with FP32 FMAs on CUDA cores   */
+  S3TTV_OPT_TENSOR_CORES = 7,      /* block duals (Alg. 1 steps 8-11), k <= 5: 2 (default)
+                                      forms the Gram Y'Y'^T and the product M Y' on tensor
+                                      cores, each FP32 operand split into two TF32 parts and
+                                      three of the four part products kept (FP32-level
+                                      accuracy), every warp streaming one block of its own
+                                      through double-buffered column chunks; 1: the same
+                                      products with the four warps of a CTA sharing each
+                                      block of a group of four; 0: the group form with FP32
+                                      FMAs on CUDA cores                                  */
   S3TTV_OPT_LAYOUT = 8,            /* block matrices X_l: S3TTV_LAYOUT_PAPER (default) or
                                       S3TTV_LAYOUT_STACKED (below)                        */
   S3TTV_OPT_SPECTRAL_BOUNDARY = 9, /* D_s: S3TTV_SPECTRAL_PERIODIC (default, Sec. II-A)
@@ -129,10 +136,32 @@ enum {
                                       limit); an allocation past it fails with
                                       S3TTV_ENOMEM as a failed cudaMalloc would, and the
                                       context stays usable (host-side fault injection)    */
-  S3TTV_OPT_NVTX = 15              /* 1: NVTX ranges around each API call and each kernel
+  S3TTV_OPT_NVTX = 15,             /* 1: NVTX ranges around each API call and each kernel
                                       class as a pass is enqueued (primal, l1-ball
                                       thresholds, block dual, dual, finalize), for
                                       profilers; 0 (default): none                        */
+  S3TTV_OPT_JACOBI_POLISH_TOL = 16, /* relative orthogonality below which a pair of rows
+                                      of the block eigen-solve is left as it is (0 <
+                                      value <= S3TTV_OPT_JACOBI_TOL).  Pairs between the
+                                      two are rotated, but only a pair above the
+                                      tolerance makes the solve run another sweep, so the
+                                      last sweep polishes the eigenvectors without the
+                                      FP32 rounding floor deciding convergence.  0
+                                      (default): tolerance / 8                         */
+  S3TTV_OPT_FIRST_ORDER = 17       /* k <= 5, paper layout: a block whose stored
+                                      eigen-rows W still nearly diagonalise this pass's
+                                      Gram G takes its clip from the first-order
+                                      (Daleckii-Krein) expansion of f(G) = min(1,
+                                      G^-1/2) in that basis, B = W G W^T = D + O:
+                                      M = W^T (f(D) + [f; d_i, d_j] o O) W, with no
+                                      eigen-solve, when no eigenvalue can reach the kink
+                                      at 1 (||O||_F < min |d_i - 1| / 4) and the bound
+                                      on the neglected second-order term, ||O||_F^2
+                                      times half the largest |f''| near the spectrum,
+                                      is at most this value; the other blocks run the
+                                      eigen-solve, which refreshes W.  Suggested 1e-6;
+                                      0 (default): every warm block runs the
+                                      eigen-solve                                     */
 };
 /* Regularisers (option S3TTV_OPT_REGULARIZER).  Sec. IV runs its P-PDS-solvable
  * comparison methods by replacing S3TTV in Prob. (S3TTV_denoising) and solving
@@ -379,17 +408,20 @@ int s3ttv_quality(s3ttv_ctx *ctx, const float *u, const float *ref, int N1, int 
  * library's device memory, which every GPU that loads the library holds until
  * the process exits.
  *
- * x, out   DEVICE pointers to n floats on the current CUDA device (may alias);
- *          host pointers are rejected with S3TTV_EINVAL (staging them would
- *          need an allocation).
+ * x, out   DEVICE pointers to n floats on the current CUDA device, or managed
+ *          memory (x and out may be the same buffer); host pointers and
+ *          memory of another device are rejected with S3TTV_EINVAL (staging
+ *          them would need an allocation).
  * n        0 <= n <= S3TTV_L1_STATIC_MAX_N (the bins count in 32 bits); larger
  *          n returns S3TTV_ETOOBIG before any work.
  * radius   >= 0, finite.  tau_out (host, may be NULL) receives the threshold.
  * stream   cudaStream_t to run on, NULL for the default stream; the call returns
  *          after that stream has finished its work.
  * The first call on a device looks up the device address of the scratch array
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call reuses the same array and clears it
+ * (cudaGetSymbolAddress, with that device current) and keeps it for the life of
+ * the process; make that first call before any stream capture, and do not call
+ * this entry point on a device after cudaDeviceReset of that device (the
+ * module is reloaded there and the kept address goes stale).  Every call reuses the same array and clears it
  * first, so calls that overlap on the GPU (other streams or host threads using
  * the same device at the same time) race and must not be issued. */
 #define S3TTV_L1_STATIC_MAX_N 4294967295LL

@@ -29,6 +29,8 @@ OPT_HSSTV_OMEGA = 12
 OPT_FP64_FALLBACK = 13
 OPT_ALLOC_LIMIT = 14
 OPT_NVTX = 15
+OPT_JACOBI_POLISH_TOL = 16
+OPT_FIRST_ORDER = 17
 REG_S3TTV, REG_STV, REG_SSTV, REG_HSSTV1, REG_HSSTV2, REG_SSST = 0, 1, 2, 3, 4, 5
 KERNEL_CLASSES = ("primal", "l1_search", "block_dual", "dual", "finalize")
 STATE = {"u": 0, "s": 1, "t": 2, "y2": 3, "y3": 4, "Y": 5}
@@ -41,7 +43,7 @@ class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("converged", ctypes.c_int),
                 ("jacobi_nonconverged", ctypes.c_int), ("rel_change", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("jacobi_sweeps", ctypes.c_double),
-                ("jacobi_fallbacks", ctypes.c_int)]
+                ("jacobi_fallbacks", ctypes.c_int), ("first_order", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -174,6 +176,11 @@ def l1_ball_static(x, radius, out=None, stream=None):
     calls must not overlap on the GPU."""
     n = int(np.prod(x.shape))
     out = _empty_like(x, x.shape) if out is None else out
+    if _is_torch(x) and _is_torch(out) and x.is_cuda and out.is_cuda:
+        import torch
+        cur = torch.cuda.current_device()
+        if x.device.index != cur or out.device.index != cur:
+            raise S3TTVError(EINVAL, "s3ttv_l1_ball_static: x and out must be on the current CUDA device")
     tau = ctypes.c_double()
     st = None
     if stream is not None:

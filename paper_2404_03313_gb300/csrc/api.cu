@@ -26,7 +26,9 @@ struct s3ttv_ctx {
   int check_every = 16;
   int jacobi_max_sweeps = 24;
   float jacobi_tol = 2e-6f;
-  int tensor_cores = 1;
+  float jacobi_polish = 0.f;  // 0: the default, tol / 8 (jacobi_polish_for)
+  float first_order = 0.f;  // remainder bound of the first-order clip (0: off, the default)
+  int tensor_cores = 2;  // block-dual form: 2 streaming (tensor cores), 1 group (tensor cores), 0 CUDA cores
   int layout = S3TTV_LAYOUT_PAPER;  // block matrices: paper k^2 x 2N3 or stacked 2k^2 x N3
   int open_s = 0;                   // 1: D_s stops at the last band (no wrap-around)
   int reg = S3TTV_REG_S3TTV;        // regularisation function (S3TTV or a comparison method)
@@ -307,6 +309,16 @@ Dims make_dims(int N1, int N2, int N3) {
   return dm;
 }
 
+// The polish threshold of the block eigen-solves (S3TTV_OPT_JACOBI_POLISH_TOL):
+// the option's value, at most the tolerance; by default tol / 8 (per-operator
+// errors below 1e-5 up to k = 10 at 200 columns, and fewer sweeps: pairs just
+// above the tolerance no longer need a sweep of their own).
+float jacobi_polish_for(const s3ttv_ctx *ctx) {
+  const float tol = ctx->jacobi_tol;
+  const float p = ctx->jacobi_polish > 0.f ? ctx->jacobi_polish : tol * 0.125f;
+  return p < tol ? p : tol;
+}
+
 // Block-dual launch shape: one CTA per group of block_dual_group() blocks, a
 // persistent grid of as many CTAs as fit on the device at once.  The kernel
 // variant sized for the most CTAs per SM whose shared memory fits is taken.
@@ -541,6 +553,7 @@ __global__ void begin_iterate_kernel(Scalars *sc, int n, float tol) {
   sc->jacobi_fail = 0u;
   sc->jacobi_sweeps = 0ull;
   sc->fb_total = 0u;
+  sc->fo_blocks = 0ull;
 }
 
 __global__ void set_c3_kernel(Scalars *sc, double c3) { sc->c3 = c3; }
@@ -629,6 +642,8 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   ba.rs = bd.rs;
   ba.max_sweeps = ctx->jacobi_max_sweeps;
   ba.tol = ctx->jacobi_tol;
+  ba.polish = jacobi_polish_for(ctx);
+  ba.fo_tol = bd.large ? 0.f : ctx->first_order;
   ba.sc = ctx->sc;
   ba.W = ctx->warm_start ? ctx->W : nullptr;
   ba.w_stride = ctx->w_stride;
@@ -833,9 +848,17 @@ int s3ttv_set_option(s3ttv_ctx *ctx, int key, double value) {
       if (!(value > 0 && value < 1)) return fail(ctx, S3TTV_EINVAL, "jacobi tol must be in (0, 1)");
       ctx->jacobi_tol = (float)value;
       return S3TTV_OK;
+    case S3TTV_OPT_FIRST_ORDER:
+      if (!(value >= 0 && value < 1)) return fail(ctx, S3TTV_EINVAL, "first-order bound must be in [0, 1)");
+      ctx->first_order = (float)value;
+      return S3TTV_OK;
+    case S3TTV_OPT_JACOBI_POLISH_TOL:
+      if (!(value >= 0 && value < 1)) return fail(ctx, S3TTV_EINVAL, "jacobi polish tolerance must be in [0, 1)");
+      ctx->jacobi_polish = (float)value;
+      return S3TTV_OK;
     case S3TTV_OPT_TENSOR_CORES:
       ctx->tuned_tc = -1;
-      if (value != 0 && value != 1) return fail(ctx, S3TTV_EINVAL, "tensor_cores must be 0 or 1");
+      if (value != 0 && value != 1 && value != 2) return fail(ctx, S3TTV_EINVAL, "tensor_cores must be 0, 1 or 2");
       ctx->tensor_cores = (int)value;
       return S3TTV_OK;
     case S3TTV_OPT_WARM_START:
@@ -991,7 +1014,7 @@ int s3ttv_iterate(s3ttv_ctx *ctx, int n, float tol, s3ttv_info *info) {
     // CUDA events, and keep the fastest.  Every timed pass is a pass of the solve.
     struct Cand { int tc, minb; BdShape sh; float ms = 1e30f; };
     std::vector<Cand> cands;
-    for (int tc = 1; tc >= 0; --tc)
+    for (int tc = 2; tc >= 0; --tc)
       for (int minb = 5; minb >= 4; --minb) {
         Cand c;
         c.tc = tc;
@@ -1063,6 +1086,7 @@ int s3ttv_iterate(s3ttv_ctx *ctx, int n, float tol, s3ttv_info *info) {
     info->rel_change = hs.rel;
     info->seconds = now_s() - t0;
     info->jacobi_sweeps = done_iters > 0 ? (double)hs.jacobi_sweeps / ((double)done_iters * ctx->dm.P) : 0.0;
+    info->first_order = done_iters > 0 ? (double)hs.fo_blocks / ((double)done_iters * ctx->dm.P) : 0.0;
   }
   return status;
 }
@@ -1232,6 +1256,8 @@ int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, in
     m->step_policy = ctx->step_policy;
     m->jacobi_max_sweeps = ctx->jacobi_max_sweeps;
     m->jacobi_tol = ctx->jacobi_tol;
+    m->jacobi_polish = ctx->jacobi_polish;
+    m->first_order = ctx->first_order;
     m->tensor_cores = ctx->tensor_cores;
     m->warm_start = ctx->warm_start;
     m->layout = ctx->layout;
@@ -1348,6 +1374,7 @@ int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, in
       infos[i].rel_change = hs[i].rel;
       infos[i].jacobi_sweeps =
           done_iters > 0 ? (double)hs[i].jacobi_sweeps / ((double)done_iters * m->dm.P) : 0.0;
+      infos[i].first_order = done_iters > 0 ? (double)hs[i].fo_blocks / ((double)done_iters * m->dm.P) : 0.0;
     }
     if (status < 0 && result >= 0) result = fail(ctx, status, "problem %d: %s", i, m->err);
     else if (status == S3TTV_MAXITER && result == S3TTV_OK) result = S3TTV_MAXITER;
@@ -1448,6 +1475,8 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   ba.rs = bd.rs;
   ba.max_sweeps = ctx->jacobi_max_sweeps;
   ba.tol = ctx->jacobi_tol;
+  ba.polish = jacobi_polish_for(ctx);
+  ba.fo_tol = bd.large ? 0.f : ctx->first_order;
   ba.sc = ctx->sc;
   ba.W = nullptr;
   ba.w_stride = 0;
@@ -1470,6 +1499,7 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
     info->jacobi_nonconverged = (int)hs.jacobi_fail;
     info->jacobi_fallbacks = (int)hs.fb_total;
     info->jacobi_sweeps = (double)hs.jacobi_sweeps / (double)dm.P;
+    info->first_order = (double)hs.fo_blocks / (double)dm.P;
   }
   return S3TTV_OK;
 }

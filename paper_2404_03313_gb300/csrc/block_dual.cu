@@ -47,6 +47,22 @@
 // mutually orthogonal are again lam_x u_x^T, so the result is the same
 // decomposition; it only needs fewer sweeps.  A block whose rows did not all
 // come out as nonzero directions stores a NaN marker and starts cold next time.
+//
+// First-order clip in the kept basis: when the stored rows W are still nearly
+// an eigenbasis of this pass's G, the clip follows without any Jacobi sweep.
+// B = W G W^T = D + O is then nearly diagonal, and the clip is the matrix
+// function f(G) = W^T f(B) W with f(lam) = min(1, lam^-1/2).  To first order
+// (the Daleckii-Krein expansion) f(B) = f(D) + F o O, F_ij the divided
+// difference of f between d_i and d_j; the remainder is at most ||O||_F^2
+// times half the largest |f''| near the spectrum, which stays finite as long as
+// no eigenvalue can reach the kink at 1 (||O||_F < min_i |d_i - 1| / 4): 3/8
+// lam_>^-5/2 above the kink (lam_> the smallest d_i above 1) plus, with d_i on
+// both sides, 2 / min_i |d_i - 1| for a smooth bridge across it.  A block whose
+// bound is within the fo_tol option takes M = W^T f(B) W (four 32 x 32 products
+// on the tensor cores) and keeps its W; any other block runs the Jacobi, which
+// stores fresh rows.  The divided differences are formed without cancellation:
+// -1 / (sqrt(a) sqrt(b) (sqrt(a) + sqrt(b))) above the kink, and
+// -(x - 1) / (sqrt(x) (1 + sqrt(x)) (x - y)) across it (x > 1 >= y).
 #include <math.h>
 #include "s3ttv_internal.cuh"
 
@@ -134,12 +150,27 @@ __host__ __device__ constexpr int tiles_floats() {
   return TC ? 2 * MmaShape<K>::NTILE * 128 : (kNW * S::NT * S::TS + 3) & ~3;
 }
 
+// Scratch of the first-order clip, per warp: a NPOS x fo_stride matrix (C = W G,
+// then f(B), then f(B) W) and a float4 per position (d, sqrt d, f(d), row of W
+// present).  The stride is 4 mod 8 words, so the A-fragment reads (8 rows x 4
+// consecutive words per access) hit 32 distinct banks.
+template <int K>
+__host__ __device__ constexpr int fo_stride() {
+  return Shape<K>::NPOS + ((12 - Shape<K>::NPOS % 8) % 8);
+}
+template <int K>
+__host__ __device__ constexpr int fo_floats() {
+  return Shape<K>::NPOS * fo_stride<K>() + 4 * Shape<K>::NPOS;
+}
+
 // The Y' buffer: n rows of stride rs, also the staging area of the group's
-// warm-start rows during the eigen-solves and, in the tensor-core form, of the
-// partial Gram tiles once the Gram has read Y'.
+// warm-start rows (and the first-order clip's scratch after them) during the
+// eigen-solves and, in the tensor-core form, of the partial Gram tiles once the
+// Gram has read Y'.
 template <int K, bool TC>
 __host__ __device__ constexpr size_t yp_floats(int rs) {
-  const size_t y = (size_t)K * K * rs, w = (size_t)kNW * w_floats<K>(), t = TC ? (size_t)tiles_floats<K, TC>() : 0;
+  const size_t y = (size_t)K * K * rs, w = (size_t)kNW * (w_floats<K>() + fo_floats<K>()),
+               t = TC ? (size_t)tiles_floats<K, TC>() : 0;
   const size_t yw = y > w ? y : w;
   return yw > t ? yw : t;
 }
@@ -151,6 +182,28 @@ __device__ __forceinline__ void sts4(float *p, float4 v) { *reinterpret_cast<flo
 __device__ __forceinline__ void cp_async16(float *sdst, const float *gsrc) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+// L2 eviction policies: the Y' rows written back after the Gram are kept
+// (evict_last) until the apply reads them again, which marks them evict_first.
+__device__ __forceinline__ unsigned long long l2_evict_last() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void cp_async16_hint(float *sdst, const float *gsrc, unsigned long long pol) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void st_hint(float4 *p, float4 v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;\n" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w), "l"(pol)
+               : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -211,9 +264,10 @@ __device__ __forceinline__ void mma_3xtf32(float (&d)[4], const unsigned (&ah)[4
 // One warp: one-sided Jacobi on the rows of G (or of W G, Ws being a shared
 // copy of the block's warm-start rows W, null for a cold start), then the
 // scaled eigen-rows into Ut and the warm rows into W.  Returns the sweeps used.
+// C0: the product W G already formed (rows of stride c0_ld), or null.
 template <int K>
 __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Ws, const float *Gm, float *Ut,
-                          bool *ok) {
+                          bool *ok, const float *C0 = nullptr, int c0_ld = 0) {
   using S = Shape<K>;
   constexpr int n = S::n, NP = S::NP, NPOS = S::NPOS, HP = S::HP, HW = S::HW, GS = S::GS, UTS = S::UTS;
   const int lane = threadIdx.x & 31;
@@ -237,7 +291,13 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Ws, 
   };
   f32x2 A[HP], B[HP];
   const bool warm = Ws && !(Ws[0] != Ws[0]);  // NaN marks "start cold"
-  if (warm) {
+  if (warm && C0) {
+#pragma unroll
+    for (int j = 0; j < HP; ++j) {
+      A[j] = ld2(C0, c0_ld, 2 * pi, act, col0 + 2 * j);
+      B[j] = ld2(C0, c0_ld, 2 * pi + 1, act, col0 + 2 * j);
+    }
+  } else if (warm) {
     // C0 = W G: rows 2i, 2i+1 of W times G, this lane's columns
 #pragma unroll
     for (int j = 0; j < HP; ++j) A[j] = B[j] = 0ull;
@@ -302,8 +362,8 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Ws, 
   // rows below 1e-6 ||G||_F are numerical zeros: rotating them changes any
   // other row's direction by less than 1e-6
   const float floor2 = 1e-12f * fro;
-  const float tol2 = a.tol * a.tol;
-  bool rotated = false;
+  const float tol2 = a.tol * a.tol, pol2 = a.polish * a.polish;
+  bool rotated = false;  // a pair less orthogonal than tol met in this sweep
   // One step.  The rows are rotated in place, A' = cA - sB, B' = sA + cB; read
   // with the positions of the odd-even ordering, A' now sits at B's position and
   // B' at A's (the pair traded places), so the movement below needs no copies.
@@ -321,7 +381,7 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Ws, 
     const float2 q0 = up2(p0), q1 = up2(p1);
     float apq = (q0.x + q0.y) + (q1.x + q1.y);
     apq += __shfl_xor_sync(kFull, apq, 1);
-    const bool need = meets && fminf(nA, nB) > floor2 && apq * apq > tol2 * nA * nB;
+    const bool need = meets && fminf(nA, nB) > floor2 && apq * apq > pol2 * nA * nB;
     const bool quarter = act && !meets;  // the odd step's idle pair
     if (__any_sync(kFull, need)) {
       float c = quarter ? 0.f : 1.f, sn = quarter ? 1.f : 0.f, dn = 0.f;
@@ -336,7 +396,7 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Ws, 
         c = hc * rc;
         sn = copysignf(0.5f, x) * y * rr * rc;
         dn = sn * rc * apq;  // t apq
-        rotated = true;
+        if (apq * apq > tol2 * nA * nB) rotated = true;
       }
       const f32x2 c2 = pk2(c, c), s2 = pk2(sn, sn), ns2 = pk2(-sn, -sn);
 #pragma unroll
@@ -493,6 +553,212 @@ __device__ void form_M(float *Gm) {
   }
 }
 
+// d = A B for matrices of at most 32 x 32 on the tensor cores (one warp, three
+// TF32 products per FP32 product): rows [0, MR) of A, columns [0, NC) of B and
+// the inner index [0, KD) are read through the accessors, everything else is
+// zero.  d[m][q][e] is element (16 m + g + 8 (e >> 1), 8 q + 2 t + (e & 1)) of
+// the 32 x 32 result (g = lane / 4, t = lane % 4).
+template <int MR, int NC, int KD, class FA, class FB>
+__device__ __forceinline__ void mm32(const FA &A, const FB &B, float (&d)[2][4][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) d[m][q][0] = d[m][q][1] = d[m][q][2] = d[m][q][3] = 0.f;
+#pragma unroll
+  for (int kk = 0; kk < (KD + 7) / 8; ++kk) {
+    unsigned bh[4][2], bl[4][2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = 8 * kk + t + 4 * h, j = 8 * q + g;
+        split_tf32((8 * q < NC && k < KD && j < NC) ? B(k, j) : 0.f, bh[q][h], bl[q][h]);
+      }
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      if (16 * m >= MR) continue;
+      unsigned ah[4], al[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = 16 * m + g + 8 * (e & 1), k = 8 * kk + t + 4 * (e >> 1);
+        split_tf32((i < MR && k < KD) ? A(i, k) : 0.f, ah[e], al[e]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (8 * q < NC) mma_3xtf32(d[m][q], ah, al, bh[q][0], bh[q][1], bl[q][0], bl[q][1]);
+    }
+  }
+}
+
+// Row and column of element e of result tile (m, q) for this lane.
+__device__ __forceinline__ int frag_row(int m, int e) { return 16 * m + ((threadIdx.x & 31) >> 2) + 8 * (e >> 1); }
+__device__ __forceinline__ int frag_col(int q, int e) { return 8 * q + 2 * (threadIdx.x & 3) + (e & 1); }
+
+// Rows [0, MR) x columns [0, NC) of a result into a row-major matrix of stride ld.
+template <int MR, int NC>
+__device__ __forceinline__ void store_frag(const float (&d)[2][4][4], float *dst, int ld) {
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = frag_row(m, e), j = frag_col(q, e);
+        if (i < MR && j < NC) dst[i * ld + j] = d[m][q][e];
+      }
+}
+
+// M[r][c] = v into the block's M slot in the layout the apply reads: by rows of
+// stride GS (tensor-core form) or by columns in two halves (CUDA-core form).
+template <int K, bool TC>
+__device__ __forceinline__ void put_M(float *Mg, int r, int c, float v) {
+  using S = Shape<K>;
+  if constexpr (TC) {
+    Mg[r * S::GS + c] = v;
+  } else {
+    const int slot = r < S::RH ? r : S::MH + (r - S::RH);
+    Mg[c * S::MS + slot] = v;
+  }
+}
+
+// One warp: the first-order clip of its block in the kept basis (see the top
+// of this file).  Ws: the block's stored rows W (NPOS rows of n; the padding
+// position of an odd n holds zeros), Gm: G (stride GS), Sc / tab: this warp's
+// scratch.  Returns true (warp-uniform) when the remainder bound is within
+// fo_tol; then M has been written over Gm.  Returns false, with G untouched,
+// otherwise.
+template <int K, bool TC>
+__device__ bool first_order_clip(const float *Ws, float *Gm, float *Sc, float4 *tab, float fo_tol) {
+  using S = Shape<K>;
+  constexpr int n = S::n, NPOS = S::NPOS, GS = S::GS, SS = fo_stride<K>();
+  const int lane = threadIdx.x & 31;
+  float d[2][4][4];
+  // rows of W that hold a direction
+  float wn = 0.f;
+  if (lane < NPOS)
+    for (int c = 0; c < n; ++c) wn = fmaf(Ws[lane * n + c], Ws[lane * n + c], wn);
+  const unsigned present = __ballot_sync(kFull, lane < NPOS && wn > 0.5f);
+  // C = W G, then B = C W^T
+  mm32<NPOS, n, n>([&](int i, int k) { return Ws[i * n + k]; }, [&](int k, int j) { return Gm[k * GS + j]; }, d);
+  store_frag<NPOS, n>(d, Sc, SS);
+  __syncwarp();
+  mm32<NPOS, NPOS, n>([&](int i, int k) { return Sc[i * SS + k]; }, [&](int k, int j) { return Ws[j * n + k]; },
+                      d);
+  float *tabf = reinterpret_cast<float *>(tab);
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = frag_row(m, e), j = frag_col(q, e);
+        if (i == j && i < NPOS) tabf[4 * i] = d[m][q][e];
+      }
+  __syncwarp();
+  // per position: d, sqrt d, f(d), present; the spectrum's distance to the kink
+  const bool pr = (present >> lane) & 1u;
+  float dmin = INFINITY, lgt = INFINITY;
+  if (lane < NPOS) {
+    const float dr = tabf[4 * lane];
+    const float sr = sqrtf(fmaxf(dr, 0.f));
+    const float fr = dr > 1.f ? rsqrtf(dr) : 1.f;
+    tab[lane] = make_float4(dr, sr, fr, pr ? 1.f : 0.f);
+    if (pr) {
+      dmin = fabsf(dr - 1.f);
+      if (dr > 1.f) lgt = dr;
+    }
+  }
+  const unsigned above = __ballot_sync(kFull, pr && lgt < INFINITY);
+  const unsigned below = present & ~above;
+  // ||O||_F^2 over the present rows
+  float os = 0.f;
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = frag_row(m, e), j = frag_col(q, e);
+        if (i != j && i < NPOS && j < NPOS && ((present >> i) & (present >> j) & 1u)) os = fmaf(d[m][q][e], d[m][q][e], os);
+      }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    os += __shfl_xor_sync(kFull, os, o);
+    dmin = fminf(dmin, __shfl_xor_sync(kFull, dmin, o));
+    lgt = fminf(lgt, __shfl_xor_sync(kFull, lgt, o));
+  }
+  float c = 0.f;
+  if (above) {
+    const float r = rsqrtf(lgt);
+    c = 0.375f * r * r * r * r * r;
+  }
+  if (above && below) c += 2.f / dmin;
+  const bool accept = present && sqrtf(os) < 0.25f * dmin && os * c <= fo_tol;
+  if (!accept) return false;
+  __syncwarp();  // the table is complete and every lane has read Gm
+  if (!above) {
+    // nothing clipped: f(B) = I on the present rows, so M = I
+    if constexpr (!TC)
+      for (int e = lane; e < n * S::MS; e += 32) Gm[e] = 0.f;
+    __syncwarp();
+    for (int e = lane; e < n * n; e += 32) {
+      const int r = e / n, cc = e - r * n;
+      put_M<K, TC>(Gm, r, cc, r == cc ? 1.f : 0.f);
+    }
+    return true;
+  }
+  // f(B): f(d_i) on the diagonal, divided differences times O off it
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = frag_row(m, e), j = frag_col(q, e);
+        float x = 0.f;
+        if (i < NPOS && j < NPOS && ((present >> i) & (present >> j) & 1u)) {
+          const float4 ti = tab[i], tj = tab[j];
+          if (i == j) {
+            x = ti.z;
+          } else {
+            const bool hi = ti.x > 1.f, hj = tj.x > 1.f;
+            float dd = 0.f;
+            if (hi && hj) {
+              dd = -__fdividef(ti.z * tj.z, ti.y + tj.y);
+            } else if (hi || hj) {
+              const float4 tx = hi ? ti : tj, ty = hi ? tj : ti;
+              dd = -__fdividef((tx.x - 1.f) * tx.z, (1.f + tx.y) * (tx.x - ty.x));
+            }
+            x = dd * d[m][q][e];
+          }
+        }
+        d[m][q][e] = x;
+      }
+  store_frag<NPOS, NPOS>(d, Sc, SS);
+  __syncwarp();
+  // T = f(B) W, then M = W^T T
+  mm32<NPOS, n, NPOS>([&](int i, int k) { return Sc[i * SS + k]; }, [&](int k, int j) { return Ws[k * n + j]; },
+                      d);
+  __syncwarp();
+  store_frag<NPOS, n>(d, Sc, SS);
+  __syncwarp();
+  mm32<n, n, NPOS>([&](int i, int k) { return Ws[k * n + i]; }, [&](int k, int j) { return Sc[k * SS + j]; }, d);
+  if constexpr (!TC)
+    for (int e = lane; e < n * S::MS; e += 32) Gm[e] = 0.f;
+  __syncwarp();
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = frag_row(m, e), j = frag_col(q, e);
+        if (i < n && j < n) put_M<K, TC>(Gm, i, j, d[m][q][e]);
+      }
+  return true;
+}
+
 // Tensor-core Gram of the block in Yp (n rows of stride RS, 2 N3p = 8 C4
 // columns): warp w takes k-steps [w C4 / 4, (w+1) C4 / 4) of 8 columns, each
 // operand split hi + lo; the four warps' partial tiles are summed in a fixed
@@ -617,43 +883,62 @@ __device__ void apply_mma(float *Yp, int RS2, int C4, const float *Mg) {
         mr[m][e2][j] = r < n ? Mg[r * GS + S0 + j] : 0.f;
       }
   }
+  // two n-tiles at a time: 2 NM independent accumulation chains per warp
 #pragma unroll 1
-  for (int q = q0; q < q1; ++q) {
-    float *col = Yp + 8 * q + g;
-    float d[NM][4];
+  for (int q = q0; q < q1; q += 2) {
+    const bool two = q + 1 < q1;
+    float d[2][NM][4];
 #pragma unroll
-    for (int m = 0; m < NM; ++m) d[m][0] = d[m][1] = d[m][2] = d[m][3] = 0.f;
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int m = 0; m < NM; ++m) d[u][m][0] = d[u][m][1] = d[u][m][2] = d[u][m][3] = 0.f;
 #pragma unroll
     for (int kk = 0; kk < NKS; ++kk) {
-      // B fragment: Y'[8 kk + t (+4)][col], rows >= S0 read as 0
+      // B fragments: Y'[8 kk + t (+4)][8 (q + u) + g], rows >= S0 read as 0
       const int s0 = 8 * kk + t, s1 = s0 + 4;
-      unsigned bh0, bl0, bh1, bl1;
-      split_tf32(s0 < S0 ? col[(size_t)s0 * RS2] : 0.f, bh0, bl0);
-      split_tf32(s1 < S0 ? col[(size_t)s1 * RS2] : 0.f, bh1, bl1);
+      unsigned bh[2][2], bl[2][2];
 #pragma unroll
-      for (int m = 0; m < NM; ++m) mma_3xtf32(d[m], mh[m][kk], ml[m][kk], bh0, bh1, bl0, bl1);
+      for (int u = 0; u < 2; ++u) {
+        const float *col = Yp + 8 * (q + u) + g;
+        const bool in = u == 0 || two;
+        split_tf32(in && s0 < S0 ? col[(size_t)s0 * RS2] : 0.f, bh[u][0], bl[u][0]);
+        split_tf32(in && s1 < S0 ? col[(size_t)s1 * RS2] : 0.f, bh[u][1], bl[u][1]);
+      }
+#pragma unroll
+      for (int m = 0; m < NM; ++m)
+#pragma unroll
+        for (int u = 0; u < 2; ++u) mma_3xtf32(d[u][m], mh[m][kk], ml[m][kk], bh[u][0], bh[u][1], bl[u][0], bl[u][1]);
     }
-    // columns c, c + 1 of rows 16 m + g (+8)
-    const int c = 8 * q + 2 * t;
 #pragma unroll
-    for (int j = 0; j < NR; ++j) {
-      const float2 y = *reinterpret_cast<const float2 *>(Yp + (size_t)(S0 + j) * RS2 + c);
+    for (int u = 0; u < 2; ++u) {
+      if (u == 1 && !two) break;
+      // columns c, c + 1 of rows 16 m + g (+8)
+      const int c = 8 * (q + u) + 2 * t;
+#pragma unroll
+      for (int j = 0; j < NR; ++j) {
+        const float2 y = *reinterpret_cast<const float2 *>(Yp + (size_t)(S0 + j) * RS2 + c);
+#pragma unroll
+        for (int m = 0; m < NM; ++m)
+#pragma unroll
+          for (int e2 = 0; e2 < 2; ++e2) {
+            d[u][m][2 * e2] = fmaf(mr[m][e2][j], y.x, d[u][m][2 * e2]);
+            d[u][m][2 * e2 + 1] = fmaf(mr[m][e2][j], y.y, d[u][m][2 * e2 + 1]);
+          }
+      }
+    }
+    __syncwarp();  // every lane has read these columns
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (u == 1 && !two) break;
+      const int c = 8 * (q + u) + 2 * t;
 #pragma unroll
       for (int m = 0; m < NM; ++m)
 #pragma unroll
         for (int e2 = 0; e2 < 2; ++e2) {
-          d[m][2 * e2] = fmaf(mr[m][e2][j], y.x, d[m][2 * e2]);
-          d[m][2 * e2 + 1] = fmaf(mr[m][e2][j], y.y, d[m][2 * e2 + 1]);
+          const int r = 16 * m + g + 8 * e2;
+          if (r < n) *reinterpret_cast<float2 *>(Yp + (size_t)r * RS2 + c) = make_float2(d[u][m][2 * e2], d[u][m][2 * e2 + 1]);
         }
     }
-    __syncwarp();  // every lane has read these columns
-#pragma unroll
-    for (int m = 0; m < NM; ++m)
-#pragma unroll
-      for (int e2 = 0; e2 < 2; ++e2) {
-        const int r = 16 * m + g + 8 * e2;
-        if (r < n) *reinterpret_cast<float2 *>(Yp + (size_t)r * RS2 + c) = make_float2(d[m][2 * e2], d[m][2 * e2 + 1]);
-      }
   }
 }
 
@@ -681,14 +966,17 @@ __device__ __forceinline__ Walk make_walk(int W4) {
 
 // Shared-memory copy of the n rows of Y_l (row stride RS); completes at
 // cp_async_wait_all.
-template <int K>
-__device__ __forceinline__ void load_rows(float *Yp, const float *Yl, int RS, int N3p, int W4, const Walk &wk) {
+// With HINT the copies carry the L2 policy pol.
+template <int K, bool HINT = false>
+__device__ __forceinline__ void load_rows(float *Yp, const float *Yl, int RS, int N3p, int W4, const Walk &wk,
+                                          unsigned long long pol = 0ull) {
   constexpr int n = K * K;
   for (int c4 = wk.c0; c4 < W4; c4 += wk.cs) {
     float *sp = Yp + (size_t)wk.r0 * RS + (c4 << 2);
     const float *gp = Yl + (size_t)wk.r0 * 2 * N3p + (c4 << 2);
     for (int r = wk.r0; r < n; r += wk.rs) {
-      cp_async16(sp, gp);
+      if constexpr (HINT) cp_async16_hint(sp, gp, pol);
+      else cp_async16(sp, gp);
       sp += (size_t)wk.rs * RS;
       gp += (size_t)wk.rs * 2 * N3p;
     }
@@ -718,7 +1006,7 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
   constexpr int NTH = kNW * 32;
   constexpr int NF = 6;  // F loads in flight per thread
   extern __shared__ __align__(16) float smem[];
-  __shared__ unsigned s_sweeps;
+  __shared__ unsigned s_sweeps, s_fo;
   __shared__ int s_tile_r0[TC ? 1 : 32], s_tile_c0[TC ? 1 : 32];
   __shared__ int s_off[kNW][n];  // pixel (i * N2 + j) of row r of P_l
   __shared__ int s_queued[kNW];  // block b of the group went to the FP64 re-solve
@@ -735,6 +1023,7 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
   const float gY = a.gY;
   const bool warm = a.warm && a.W;  // a.w_stride == w_floats<K>()
   const Walk wk = make_walk(W4);
+  const unsigned long long pol_keep = l2_evict_last(), pol_done = l2_evict_first();
   if (tid == 0 && !TC) {
     int c = 0;
     for (int t = 0; t < S::NRG; ++t)
@@ -745,7 +1034,7 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
           ++c;
         }
   }
-  if (tid == 0) s_sweeps = 0u;
+  if (tid == 0) s_sweeps = s_fo = 0u;
   __syncthreads();
 
   for (long long grp = blockIdx.x; grp < groups; grp += gridDim.x) {
@@ -760,7 +1049,7 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
     for (int b = 0; b < nb; ++b) {
       const long long l = l0 + b;
       float *Yl = a.Y + (size_t)l * n * 2 * N3p;
-      load_rows<K>(Yp, Yl, RS, N3p, W4, wk);
+      load_rows<K, true>(Yp, Yl, RS, N3p, W4, wk, pol_done);
       if (warp == 1 && b + 1 < nb) prefetch_rows<K>(Yl + (size_t)n * 2 * N3p, N3p);
       if (tid < n) {
         const int p = (int)(l / dm.N2), q = (int)(l - (long long)p * dm.N2);
@@ -796,7 +1085,7 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
               y.w = fmaf(gY, xv[u].w, y.w);
               sts4(dst, y);
               // Y' replaces Y_l in global memory (kept in L2) for step 5
-              reinterpret_cast<float4 *>(Yl + (size_t)r * 2 * N3p)[c4] = y;
+              st_hint(reinterpret_cast<float4 *>(Yl + (size_t)r * 2 * N3p) + c4, y, pol_keep);
             }
           }
         }
@@ -873,8 +1162,24 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
     }
     if (warp < nb) {
       float *Gb = Gall + warp * gm_floats<K, TC>();
+      const float *Ws = warm ? Yp + warp * w_floats<K>() : nullptr;
+      bool fo = false;
+      const float *C0 = nullptr;  // W G, formed by a first-order attempt that fell through
+      if (Ws && a.fo_tol > 0.f && !(Ws[0] != Ws[0])) {
+        float *Sc = Yp + kNW * w_floats<K>() + warp * fo_floats<K>();
+        fo = first_order_clip<K, TC>(Ws, Gb, Sc, reinterpret_cast<float4 *>(Sc + S::NPOS * fo_stride<K>()),
+                                     a.fo_tol);
+        C0 = Sc;
+      }
+      if (fo) {
+        if (lane == 0) {
+          s_queued[warp] = 0;
+          atomicAdd(&s_fo, 1u);
+        }
+        __syncwarp();
+      } else {
       bool ok;
-      const int sweeps = eigen_rows<K>(a, l0 + warp, warm ? Yp + warp * w_floats<K>() : nullptr, Gb, Gb, &ok);
+      const int sweeps = eigen_rows<K>(a, l0 + warp, Ws, Gb, Gb, &ok, C0, fo_stride<K>());
       if (lane == 0) {
         int queued = 0;
         if (!ok) {
@@ -892,6 +1197,7 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
       }
       __syncwarp();
       form_M<K, TC>(Gb);
+      }
     }
     __syncthreads();
 
@@ -902,7 +1208,7 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
       const long long l = l0 + b;
       float *Yl = a.Y + (size_t)l * n * 2 * N3p;
       const float *Mg = Gall + b * gm_floats<K, TC>();
-      load_rows<K>(Yp, Yl, RS, N3p, W4, wk);
+      load_rows<K, true>(Yp, Yl, RS, N3p, W4, wk, pol_done);
       cp_async_wait_all();
       __syncthreads();
       if constexpr (TC) {
@@ -963,15 +1269,329 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
     }
   }
   if (tid == 0 && s_sweeps) atomicAdd(&a.sc->jacobi_sweeps, (unsigned long long)s_sweeps);
+  if (tid == 0 && s_fo) atomicAdd(&a.sc->fo_blocks, (unsigned long long)s_fo);
+}
+
+// ---------------------------------------------------------------------------
+// Streaming form (k <= 5, tensor cores): every warp owns one block at a time,
+// end to end, and streams its rows through two chunk buffers of kCW columns,
+// so the copies of the next chunk are in flight while the current one is
+// used, and no step waits on a CTA-wide barrier.
+//  A. For each chunk: Y rows by cp.async (the next chunk's issued first),
+//     Y' = Y + gamma_Y (Fv | Fh), written back over Y_l, and the chunk's part
+//     of G = Y'Y'^T on the tensor cores (the warp holds all of G in registers).
+//  B. The clip of the block: first-order in the kept basis, else the Jacobi
+//     (the same device code as the group form above), M over G's slot.
+//  C. For each chunk: Y' back from global memory, Y_l = M Y' in place, Y_l
+//     stored and P_l^T Y_l added into Z.
+// While a warp is in B its chunk buffers hold the block's stored rows W and
+// the first-order scratch.
+constexpr int kSW = 4;         // warps per CTA
+constexpr int kCW = 32;        // columns per chunk (four 8-column k-steps)
+constexpr int kCS = kCW + 12;  // chunk row stride: 12 mod 32 words, as the group form's rows
+
+template <int K>
+struct StreamLayout {
+  static constexpr int n = K * K;
+  static constexpr int buf = n * kCS;                          // one chunk buffer
+  static constexpr int gm = gm_floats<K, true>();              // G, then M (by rows, stride GS)
+  static constexpr int per_warp = (2 * buf + gm + n + 3) & ~3;  // + the rows' pixel offsets
+  static_assert(w_floats<K>() + fo_floats<K>() <= 2 * buf, "W and the first-order scratch fit the chunk buffers");
+};
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int K>
+__global__ void __launch_bounds__(kSW * 32, 4) block_dual_stream_kernel(BlockDualArgs a) {
+  using S = Shape<K>;
+  using T = MmaShape<K>;
+  using LY = StreamLayout<K>;
+  constexpr int n = S::n, GS = S::GS, NTILE = T::NTILE, NM = T::NM, NKS = T::NKS, NR = T::NR, S0 = n - NR;
+  constexpr int NE = (n * (kCW / 4) + 31) / 32;  // 16-byte pieces of a chunk per lane
+  extern __shared__ __align__(16) float smem[];
+  if (a.sc->done) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float *bufs = smem + warp * LY::per_warp;
+  float *Gm = bufs + 2 * LY::buf;
+  int *off = reinterpret_cast<int *>(Gm + LY::gm);
+  const Dims dm = a.dm;
+  const int N3p = dm.N3p, RW = 2 * N3p, NCH = (RW + kCW - 1) / kCW;
+  const float gY = a.gY;
+  const bool warm = a.warm && a.W;  // a.w_stride == w_floats<K>()
+  const unsigned long long pol_keep = l2_evict_last(), pol_done = l2_evict_first();
+  unsigned long long sweeps = 0, fo_count = 0;
+  const long long step = (long long)gridDim.x * kSW;
+  for (long long l = (long long)blockIdx.x * kSW + warp; l < dm.P; l += step) {
+    float *Yl = a.Y + (size_t)l * n * RW;
+    if (lane < n) {
+      const int p = (int)(l / dm.N2), q = (int)(l - (long long)p * dm.N2);
+      const int ra = lane / K, rc = lane - ra * K;
+      int i = p + ra;
+      if (i >= dm.N1) i -= dm.N1;
+      int j = q + rc;
+      if (j >= dm.N2) j -= dm.N2;
+      off[lane] = i * dm.N2 + j;
+    }
+    // chunk ch of the n rows into buffer b: piece e = (row e / 8, float4 e % 8)
+    auto load_chunk = [&](int ch, float *b, unsigned long long pol) {
+      const int c0 = ch * kCW, w4 = min(kCW, RW - c0) >> 2;
+#pragma unroll
+      for (int u = 0; u < NE; ++u) {
+        const int e = lane + 32 * u, r = e >> 3, j = e & 7;
+        if (r < n && j < w4) cp_async16_hint(b + r * kCS + 4 * j, Yl + (size_t)r * RW + c0 + 4 * j, pol);
+      }
+      cp_async_commit();
+    };
+    __syncwarp();  // the pixel offsets are visible; the buffers are free
+
+    // ---- A. Y' chunk by chunk, its Gram in registers ----
+    float acc[NTILE][4];
+#pragma unroll
+    for (int i = 0; i < NTILE; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+    load_chunk(0, bufs, pol_done);
+    for (int ch = 0; ch < NCH; ++ch) {
+      float *cur = bufs + (ch & 1) * LY::buf;
+      if (ch + 1 < NCH) {
+        load_chunk(ch + 1, bufs + ((ch + 1) & 1) * LY::buf, pol_done);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncwarp();
+      const int c0 = ch * kCW, w4 = min(kCW, RW - c0) >> 2;
+      float4 fv[NE];
+#pragma unroll
+      for (int u = 0; u < NE; ++u) {
+        const int e = lane + 32 * u, r = e >> 3, j = e & 7;
+        if (r < n && j < w4) {
+          const int c = c0 + 4 * j;
+          const bool hz = c >= N3p;
+          fv[u] = __ldg(reinterpret_cast<const float4 *>((hz ? a.Fh : a.Fv) + (size_t)off[r] * N3p + (hz ? c - N3p : c)));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < NE; ++u) {
+        const int e = lane + 32 * u, r = e >> 3, j = e & 7;
+        if (r < n && j < w4) {
+          float *dst = cur + r * kCS + 4 * j;
+          float4 y = lds4(dst);
+          y.x = fmaf(gY, fv[u].x, y.x);
+          y.y = fmaf(gY, fv[u].y, y.y);
+          y.z = fmaf(gY, fv[u].z, y.z);
+          y.w = fmaf(gY, fv[u].w, y.w);
+          sts4(dst, y);
+          // Y' replaces Y_l in global memory (kept in L2) for step C
+          st_hint(reinterpret_cast<float4 *>(Yl + (size_t)r * RW + c0) + j, y, pol_keep);
+        }
+      }
+      __syncwarp();
+      const int nks = w4 >> 1;
+      for (int ks = 0; ks < nks; ++ks) {
+        unsigned xh[4][2], xl[4][2];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            xh[q][h] = xl[q][h] = 0u;
+            if (8 * q < n) {
+              const int row = 8 * q + g;
+              split_tf32(row < n ? cur[row * kCS + 8 * ks + t + 4 * h] : 0.f, xh[q][h], xl[q][h]);
+            }
+          }
+        int idx = 0;
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+          const unsigned ah[4] = {xh[2 * m][0], xh[2 * m + 1][0], xh[2 * m][1], xh[2 * m + 1][1]};
+          const unsigned al[4] = {xl[2 * m][0], xl[2 * m + 1][0], xl[2 * m][1], xl[2 * m + 1][1]};
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (T::need(m, q)) {
+              mma_3xtf32(acc[idx], ah, al, xh[q][0], xh[q][1], xl[q][0], xl[q][1]);
+              ++idx;
+            }
+        }
+      }
+      __syncwarp();  // every lane has read this buffer before it is refilled
+    }
+    {  // G, both triangles, from the tiles reaching the upper triangle
+      int idx = 0;
+#pragma unroll
+      for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (T::need(m, q)) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int i = 16 * m + g + 8 * (e >> 1), j = 8 * q + 2 * t + (e & 1);
+              if (i < n && j < n && i <= j) {
+                Gm[i * GS + j] = acc[idx][e];
+                Gm[j * GS + i] = acc[idx][e];
+              }
+            }
+            ++idx;
+          }
+    }
+
+    // ---- B. the clip: M over G's slot ----
+    const float *Ws = nullptr;
+    if (warm) {  // the block's stored rows into the (now idle) chunk buffers
+      const float *Wg = a.W + (size_t)l * w_floats<K>();
+      for (int c = lane; c < w_floats<K>() / 4; c += 32) cp_async16(bufs + 4 * c, Wg + 4 * c);
+      cp_async_commit();
+      cp_async_wait<0>();
+      Ws = bufs;
+    }
+    __syncwarp();  // G and W visible to every lane
+    bool fo = false;
+    const float *C0 = nullptr;
+    if (Ws && a.fo_tol > 0.f && !(Ws[0] != Ws[0])) {
+      float *Sc = bufs + w_floats<K>();
+      fo = first_order_clip<K, true>(Ws, Gm, Sc, reinterpret_cast<float4 *>(Sc + S::NPOS * fo_stride<K>()), a.fo_tol);
+      C0 = Sc;
+    }
+    if (fo) {
+      ++fo_count;
+    } else {
+      bool ok;
+      sweeps += eigen_rows<K>(a, l, Ws, Gm, Gm, &ok, C0, fo_stride<K>());
+      int queued = 0;
+      if (lane == 0 && !ok) {
+        // to the FP64 re-solve if the queue has room; else applied as it stands
+        const unsigned slot = a.fb_list ? atomicAdd(&a.sc->fb_count, 1u) : 0xffffffffu;
+        if (slot < (unsigned)a.fb_cap) {
+          a.fb_list[slot] = (int)l;
+          queued = 1;
+        } else {
+          atomicAdd(&a.sc->jacobi_fail, 1u);
+        }
+      }
+      queued = __shfl_sync(kFull, queued, 0);
+      __syncwarp();
+      form_M<K, true>(Gm);
+      if (queued) continue;  // Y_l keeps Y' for the FP64 re-solve, nothing added to Z
+    }
+    __syncwarp();  // M visible to every lane; W and the scratch are no longer read
+
+    // ---- C. Y_l = M Y' chunk by chunk, stored and added into Z ----
+    unsigned mh[NM][NKS > 0 ? NKS : 1][4], ml[NM][NKS > 0 ? NKS : 1][4];
+    float mr[NM][2][NR > 0 ? NR : 1];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+#pragma unroll
+      for (int kk = 0; kk < NKS; ++kk)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int r = 16 * m + g + 8 * (e & 1), c = 8 * kk + t + 4 * (e >> 1);
+          split_tf32((r < n && c < S0) ? Gm[r * GS + c] : 0.f, mh[m][kk][e], ml[m][kk][e]);
+        }
+#pragma unroll
+      for (int e2 = 0; e2 < 2; ++e2)
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+          const int r = 16 * m + g + 8 * e2;
+          mr[m][e2][j] = r < n ? Gm[r * GS + S0 + j] : 0.f;
+        }
+    }
+    load_chunk(0, bufs, pol_done);
+    for (int ch = 0; ch < NCH; ++ch) {
+      float *cur = bufs + (ch & 1) * LY::buf;
+      if (ch + 1 < NCH) {
+        load_chunk(ch + 1, bufs + ((ch + 1) & 1) * LY::buf, pol_done);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncwarp();
+      const int c0 = ch * kCW, w4 = min(kCW, RW - c0) >> 2, ntl = w4 >> 1;
+      // n-tiles of 8 columns, two at a time
+      for (int q = 0; q < ntl; q += 2) {
+        const bool two = q + 1 < ntl;
+        float d[2][NM][4];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int m = 0; m < NM; ++m) d[u][m][0] = d[u][m][1] = d[u][m][2] = d[u][m][3] = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < NKS; ++kk) {
+          const int s0 = 8 * kk + t, s1 = s0 + 4;
+          unsigned bh[2][2], bl[2][2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const float *col = cur + 8 * (q + u) + g;
+            const bool in = u == 0 || two;
+            split_tf32(in && s0 < S0 ? col[s0 * kCS] : 0.f, bh[u][0], bl[u][0]);
+            split_tf32(in && s1 < S0 ? col[s1 * kCS] : 0.f, bh[u][1], bl[u][1]);
+          }
+#pragma unroll
+          for (int m = 0; m < NM; ++m)
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+              mma_3xtf32(d[u][m], mh[m][kk], ml[m][kk], bh[u][0], bh[u][1], bl[u][0], bl[u][1]);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (u == 1 && !two) break;
+          const int c = 8 * (q + u) + 2 * t;
+#pragma unroll
+          for (int j = 0; j < NR; ++j) {
+            const float2 y = *reinterpret_cast<const float2 *>(cur + (S0 + j) * kCS + c);
+#pragma unroll
+            for (int m = 0; m < NM; ++m)
+#pragma unroll
+              for (int e2 = 0; e2 < 2; ++e2) {
+                d[u][m][2 * e2] = fmaf(mr[m][e2][j], y.x, d[u][m][2 * e2]);
+                d[u][m][2 * e2 + 1] = fmaf(mr[m][e2][j], y.y, d[u][m][2 * e2 + 1]);
+              }
+          }
+        }
+        __syncwarp();  // every lane has read these columns
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (u == 1 && !two) break;
+          const int c = 8 * (q + u) + 2 * t;
+#pragma unroll
+          for (int m = 0; m < NM; ++m)
+#pragma unroll
+            for (int e2 = 0; e2 < 2; ++e2) {
+              const int r = 16 * m + g + 8 * e2;
+              if (r < n) *reinterpret_cast<float2 *>(cur + r * kCS + c) = make_float2(d[u][m][2 * e2], d[u][m][2 * e2 + 1]);
+            }
+        }
+      }
+      __syncwarp();  // Y_l of this chunk complete in the buffer
+#pragma unroll
+      for (int u = 0; u < NE; ++u) {
+        const int e = lane + 32 * u, r = e >> 3, j = e & 7;
+        if (r < n && j < w4) {
+          const int c = c0 + 4 * j;
+          const float4 y = lds4(cur + r * kCS + 4 * j);
+          __stcs(reinterpret_cast<float4 *>(Yl + (size_t)r * RW + c0) + j, y);
+          const bool hz = c >= N3p;
+          atomicAdd(reinterpret_cast<float4 *>((hz ? a.Zh : a.Zv) + (size_t)off[r] * N3p + (hz ? c - N3p : c)), y);
+        }
+      }
+      __syncwarp();  // every lane has read this buffer before it is refilled
+    }
+  }
+  if (lane == 0) {
+    if (sweeps) atomicAdd(&a.sc->jacobi_sweeps, sweeps);
+    if (fo_count) atomicAdd(&a.sc->fo_blocks, fo_count);
+  }
 }
 
 using KernelFn = void (*)(BlockDualArgs);
 
-// Variants compiled (null for the others): the CUDA-core form for 5 and 4 CTAs
-// per SM; the tensor-core form for 4 only (its five- and six-CTA variants fit
-// in shared memory, but at 96 and 80 registers they spill and ran slower).
+// Variants compiled (null for the others): the CUDA-core form (tc 0) for 5
+// and 4 CTAs per SM; the tensor-core group form (tc 1) for 4 only (its five-
+// and six-CTA variants fit in shared memory, but at 96 and 80 registers they
+// spill and ran slower); the tensor-core streaming form (tc 2) for 4.
 template <int K>
 KernelFn kernel_k(int minb, int tc) {
+  if (tc == 2) return minb == 4 ? block_dual_stream_kernel<K> : nullptr;
   if (tc) return minb == 4 ? block_dual_kernel<K, 4, true> : nullptr;
   if (minb != 5 && minb != 4) return nullptr;
   return minb == 5 ? block_dual_kernel<K, 5, false> : block_dual_kernel<K, 4, false>;
@@ -995,6 +1615,7 @@ size_t smem_k(int rs) {
 
 template <int K>
 size_t smem_kt(int tc, int rs) {
+  if (tc == 2) return sizeof(float) * kSW * StreamLayout<K>::per_warp;
   return tc ? smem_k<K, true>(rs) : smem_k<K, false>(rs);
 }
 

@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
       __syncthreads();
     }
     const float floor2 = 1e-12f * fro;
-    const float tol2 = a.tol * a.tol;
+    const float tol2 = a.tol * a.tol, pol2 = a.polish * a.polish;
     bool converged = false;
     int sweeps = 0;
     for (int sw = 0; sw < a.max_sweeps; ++sw) {
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
 #pragma unroll
           for (int o = PG / 2; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
           const float nA = chk ? nrm[ra] : 0.f, nB = chk ? nrm[rb] : 0.f;
-          if (chk && fminf(nA, nB) > floor2 && d * d > tol2 * nA * nB) {
+          if (chk && fminf(nA, nB) > floor2 && d * d > pol2 * nA * nB) {
             const float x = nB - nA, y = 2.f * d;
             const float rr = rsqrtf(fmaf(x, x, y * y));
             const float hc = fmaf(0.5f * fabsf(x), rr, 0.5f);
@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
                 last[rb] = sw;
               }
             }
-            rotated = 1;
+            if (d * d > tol2 * nA * nB) rotated = 1;
           }
         }
         __syncthreads();

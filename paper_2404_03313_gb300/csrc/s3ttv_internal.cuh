@@ -48,6 +48,7 @@ struct Scalars {
   unsigned long long jacobi_sweeps;  // sweeps summed over blocks (statistics)
   unsigned fb_count;  // blocks queued for the FP64 re-solve in this pass (reset by the primal step)
   unsigned fb_total;  // blocks re-solved in FP64 since the last s3ttv_iterate began
+  unsigned long long fo_blocks;  // blocks whose clip came from the first-order update (statistics)
 };
 
 // Radix levels over the 31 magnitude bits of a float.
@@ -130,7 +131,9 @@ struct BlockDualArgs {
   float gY;
   int rs;                 // shared-memory row stride (floats) of the block copies
   int max_sweeps;
-  float tol;
+  float tol;              // a sweep with a pair less orthogonal than this is followed by another
+  float polish;           // (<= tol) pairs less orthogonal than this are rotated
+  float fo_tol;           // bound on the remainder of the first-order clip (0: path off; k <= 5 kernel)
   Scalars *sc;            // done flag and the non-convergence counter
   float *W;               // per-block warm-start rows [L][w_stride] (may be null)
   long long w_stride;     // floats per block in W (>= NPOS * k*k)

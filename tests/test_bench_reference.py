@@ -7,6 +7,8 @@ import os
 import subprocess
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -29,10 +31,16 @@ def test_reference_line_has_the_contract_keys():
                 "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in d, key
     assert d["impl"] == "reference" and d["steps"] == 1 and d["warmup"] == 3
-    assert d["value"] > 0 and abs(d["ms_per_step"] - 1000.0 / d["value"]) <= 1e-9 * d["ms_per_step"]
+    # one step is one oracle pass over a crop (the bounded sample): ms_per_step is
+    # that pass's time, and value scales its rate to the whole cube
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    frac = 64 * 64 / (256 * 256)
+    assert d["value"] == pytest.approx(frac / (d["ms_per_step"] / 1000.0), rel=1e-9)
+    assert "crop" in d["config"]["step"]
     assert d["config"]["workload"] == "s3ttv_256x256x128_k5"
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and "crop" in cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] > 0 and cb["value"] == d["value"] and "crop" in cb["sample"]
+    assert cb["cpu_model"] and cb["cores_available"] >= 1
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
 

@@ -19,11 +19,12 @@ OP_TOL = 1e-5
 
 
 def op_tol(k):
-    """Per-operator bound: 1e-5 for blocks of up to 25 rows (k <= 5); beyond,
-    scaled by n / 25 for n = k^2 rows, the growth of the worst-case rounding of
-    the n-term sums of the FP32 Gram route (G = Y'Y'^T, M = I - sum of n
-    rank-one terms, M Y')."""
-    return OP_TOL * max(1.0, k * k / 25.0)
+    """Per-operator bound: 1e-5 for every block size.  The eigen-solves of the
+    one-CTA-per-block kernel (k = 6..12) rotate pairs down to a polish
+    threshold of tol / 8 while only pairs above tol keep a sweep going; at the
+    default tol = 2e-6 without it the measured error reached 1.4e-5 at k = 10
+    and 1.8e-5 at k = 12 (random blocks of 140 and 120 columns)."""
+    return OP_TOL
 
 
 def rel(a, b):
@@ -42,9 +43,11 @@ def P():
     return P
 
 
-# Both forms of the block-dual products: tensor cores (three TF32 products per
-# FP32 product) and FP32 FMAs on CUDA cores.
-FORMS = [pytest.param(1, id="tc"), pytest.param(0, id="fp32")]
+# The forms of the block-dual products: tensor cores (three TF32 products per
+# FP32 product) with the four warps of a CTA sharing each block, the same
+# products with every warp streaming a block of its own, and FP32 FMAs on CUDA
+# cores.  (k >= 6 has one form; its cases run three times.)
+FORMS = [pytest.param(1, id="tc"), pytest.param(2, id="tc_stream"), pytest.param(0, id="fp32")]
 
 
 @pytest.fixture(params=FORMS)
@@ -111,6 +114,8 @@ BLOCK_CASES = [
     ((9, 8, 7), 6), ((8, 9, 33), 7), ((10, 10, 16), 8), ((11, 10, 20), 10), ((10, 12, 70), 10), ((12, 12, 9), 12),
     # odd row counts with 4 lanes per Jacobi pair (k = 9, 11: 81 and 121 rows)
     ((10, 9, 12), 9), ((11, 12, 9), 11),
+    # many columns per block (the measured error grows with them)
+    ((10, 10, 100), 10),
 ]
 
 
@@ -137,6 +142,29 @@ def test_block_dual_matches_oracle(solver, shape, k):
     # error: eigenvalues of G = Y'Y'^T near 1 carry an absolute error of order
     # eps * lambda_max, and these random blocks reach lambda_max ~ 100
     assert np.linalg.norm(got.astype(np.float64), 2, axis=(1, 2)).max() <= 1 + 1e-4
+
+
+@pytest.mark.parametrize("shape,k,floor", [((11, 11, 50), 11, 1.01e-5), ((12, 12, 60), 12, 1.24e-5)])
+def test_block_dual_large_blocks_many_columns_floor(solver, shape, k, floor):
+    """k = 11 and 12 with 100 and 120 columns per block: 121- and 144-row Grams
+    whose FP32 one-sided Jacobi leaves rounding in the rows of the small
+    eigenvalues of order eps * lambda_max / lambda.  Measured per-operator
+    errors: 1.01e-5 and 1.24e-5 (``floor``), and a lower polish threshold
+    (1.25e-7) does not lower them: the FP32 floor of the Gram route at these
+    sizes.  These two cases alone are held to their measured floor plus 20%;
+    every other case holds 1e-5."""
+    N1, N2, N3 = shape
+    rng = np.random.default_rng(N1 * 1000 + N2 * 10 + k)
+    L = N1 * N2
+    scale = rng.uniform(0.02, 3.0, size=(L, 1, 1)) / math.sqrt(k * k + 2 * N3)
+    Y = (rng.standard_normal((L, k * k, 2 * N3)) * scale).astype(np.float32)
+    Y[rng.uniform(size=L) < 0.1] = 0.0
+    ubar = rng.uniform(-0.5, 1.5, size=shape).astype(np.float32)
+    Yd = torch.from_numpy(Y).cuda()
+    Zv, Zh, info = solver.block_dual(Yd, torch.from_numpy(ubar).cuda(), k)
+    assert info["jacobi_nonconverged"] == 0
+    Yref = O.block_dual_update(Y.astype(np.float64), O.structure_tensors(ubar.astype(np.float64), k), 0.25)
+    assert rel(Yd.cpu().numpy(), Yref) <= 1.2 * floor, rel(Yd.cpu().numpy(), Yref)
 
 
 def test_block_dual_identity_when_inside_ball(solver):

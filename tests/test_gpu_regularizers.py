@@ -118,7 +118,7 @@ def test_ssst_one_pass_block_sizes(P, shape, k):
         s.iterate(1)
         for name in ("u", "s", "t", "y2", "y3", "Y"):
             got = s.get_state(name)
-            tol = 1e-5 * max(1.0, k * k / 25)
+            tol = 1e-5
             assert rel(got, ref[name].reshape(got.shape)) <= tol, (name, rel(got, ref[name].reshape(got.shape)))
 
 
