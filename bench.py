@@ -629,6 +629,22 @@ def run_batch(args):
     clocks = sampler.stop()
     ms = dist_max(e0.elapsed_time(e1), world, device=f"cuda:{dev}")
     launches = solver.launch_count()
+    # the same passes with the block duals of all cubes in one work-list launch
+    # per block side (S3TTV_OPT_BATCH_WORKLIST)
+    worklist = None
+    if args.tensor_cores == 2:
+        solver.set_option(P.OPT_BATCH_WORKLIST, 1)
+        solver.solve_batched(probs, max_iter=args.warmup, tol=0.0)
+        w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0.record(stream)
+        outw = solver.solve_batched(probs, max_iter=args.steps, tol=0.0)
+        w1.record(stream)
+        torch.cuda.synchronize()
+        wms = w0.elapsed_time(w1)
+        worklist = {"value": args.steps / (wms / 1000.0), "unit": BATCH_UNIT, "ms_per_step": wms / args.steps,
+                    "max_rel_diff_vs_default": max(float((a[0] - b_[0]).norm() / b_[0].norm())
+                                                   for a, b_ in zip(outw, out))}
+        solver.set_option(P.OPT_BATCH_WORKLIST, 0)
     # each cube alone, the same passes, back to back
     alone_u, t_alone = [], 0.0
     for p in probs:
@@ -675,6 +691,7 @@ def run_batch(args):
                          "frac": achieved / peak, "traffic": None, "kernel": "whole pass, all cubes",
                          "peak_source": peak_src, "algorithmic_bytes_per_step": pass_bytes},
             "cubes_alone_ms_per_step": t_alone / args.steps, "batching_gain": t_alone / ms,
+            "block_dual_worklist": worklist,
             "max_rel_diff_batched_vs_alone": agree,
             "to_tol": tol_run,
         }), flush=True)
@@ -762,12 +779,24 @@ def run_warm_start(args):
     fwd_ms = f0.elapsed_time(f1) / nf
 
     evals = []
+
+    def first_within(trace, target):
+        return next((n for n, m in trace if m >= target), None)
+
     for sp in warm_start_specs(args.steps, 20000, (256, 256, 128)):
         clean, v = make_cube(sp)
         vd = torch.from_numpy(v).to(f"cuda:{dev}")
+        cref = torch.from_numpy(clean).to(f"cuda:{dev}")
         e, a, b = P.radii(v.size, sp.sigma, sp.p_s, sp.p_t)
         cold = WS.solve(vd, e, a, b, 5, None, 5000, 1e-5, policy, device=dev)
         warm = WS.solve(vd, e, a, b, 5, net, 5000, 1e-5, policy, device=dev)
+        # the same runs with MPSNR traced every 16 passes, and a warm start whose
+        # block duals also start from the prediction (singular values of
+        # 16 X(u_pred) clipped at 1)
+        cold_t = WS.solve(vd, e, a, b, 5, None, 5000, 1e-5, policy, device=dev, trace_ref=cref)
+        warm_t = WS.solve(vd, e, a, b, 5, net, 5000, 1e-5, policy, device=dev, trace_ref=cref)
+        warm_y = WS.solve(vd, e, a, b, 5, net, 5000, 1e-5, policy, device=dev, dual_scale=16.0)
+        target = cold_t["trace"][-1][1] - 0.01
         # the paper's printed step sizes: the stop rule does not fire, so compare
         # the restored cube after a fixed budget of passes
         cold_p = WS.solve(vd, e, a, b, 5, None, args.ws_paper_passes, 0.0, P.STEP_PAPER, device=dev)
@@ -776,6 +805,11 @@ def run_warm_start(args):
         evals.append({"cold_s": cold["seconds"], "cold_iters": cold["info"]["iters"],
                       "warm_s": warm["seconds"], "warm_iters": warm["info"]["iters"],
                       "net_s": warm["net_seconds"],
+                      "warm_dual_init": {"dual_scale": 16.0, "s": warm_y["seconds"],
+                                         "iters": warm_y["info"]["iters"],
+                                         "mpsnr": mpsnr(warm_y["u"].cpu().numpy(), clean)},
+                      "passes_to_cold_final_mpsnr_minus_0p01": {"cold": first_within(cold_t["trace"], target),
+                                                               "warm": first_within(warm_t["trace"], target)},
                       "mpsnr_observed": mpsnr(v, clean), "mpsnr_network": mpsnr(pred.cpu().numpy(), clean),
                       "mpsnr_cold": mpsnr(cold["u"].cpu().numpy(), clean),
                       "mpsnr_warm": mpsnr(warm["u"].cpu().numpy(), clean),

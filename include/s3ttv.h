@@ -148,7 +148,7 @@ enum {
                                       last sweep polishes the eigenvectors without the
                                       FP32 rounding floor deciding convergence.  0
                                       (default): tolerance / 8                         */
-  S3TTV_OPT_FIRST_ORDER = 17       /* k <= 5, paper layout: a block whose stored
+  S3TTV_OPT_FIRST_ORDER = 17,      /* k <= 5, paper layout: a block whose stored
                                       eigen-rows W still nearly diagonalise this pass's
                                       Gram G takes its clip from the first-order
                                       (Daleckii-Krein) expansion of f(G) = min(1,
@@ -162,6 +162,15 @@ enum {
                                       eigen-solve, which refreshes W.  Suggested 1e-6;
                                       0 (default): every warm block runs the
                                       eigen-solve                                     */
+  S3TTV_OPT_BATCH_WORKLIST = 18    /* s3ttv_solve_batched with the streaming block-dual
+                                      form (k <= 5, S3TTV or STV): 1 runs the block duals
+                                      of every problem as one persistent launch per block
+                                      side over a work list of all their blocks, between
+                                      each pass's steps before and after them on the
+                                      problems' own streams; 0 (default, faster: the
+                                      problems' small kernels overlap their block duals):
+                                      every problem's passes run on its own stream with
+                                      its own block-dual launches                     */
 };
 /* Regularisers (option S3TTV_OPT_REGULARIZER).  Sec. IV runs its P-PDS-solvable
  * comparison methods by replacing S3TTV in Prob. (S3TTV_denoising) and solving

@@ -11,7 +11,7 @@ from ._binding import (  # noqa: F401
     L1_STATIC_MAX_N, ETOOBIG,
     STEP_PAPER, STEP_PC_EXACT, OPT_STEP_POLICY, OPT_CHECK_EVERY, OPT_JACOBI_MAX_SWEEPS, OPT_JACOBI_TOL,
     OPT_PROFILE, OPT_WARM_START, OPT_TENSOR_CORES, OPT_LAYOUT, OPT_SPECTRAL_BOUNDARY, LAYOUT_PAPER,
-    LAYOUT_STACKED, SPECTRAL_PERIODIC, SPECTRAL_OPEN, OPT_REGULARIZER, OPT_AUTOTUNE, OPT_HSSTV_OMEGA, OPT_FP64_FALLBACK, OPT_ALLOC_LIMIT, OPT_NVTX, OPT_JACOBI_POLISH_TOL, OPT_FIRST_ORDER, REG_S3TTV, REG_STV, REG_SSTV, REG_HSSTV1,
+    LAYOUT_STACKED, SPECTRAL_PERIODIC, SPECTRAL_OPEN, OPT_REGULARIZER, OPT_AUTOTUNE, OPT_HSSTV_OMEGA, OPT_FP64_FALLBACK, OPT_ALLOC_LIMIT, OPT_NVTX, OPT_JACOBI_POLISH_TOL, OPT_FIRST_ORDER, OPT_BATCH_WORKLIST, REG_S3TTV, REG_STV, REG_SSTV, REG_HSSTV1,
     REG_HSSTV2, REG_SSST, KERNEL_CLASSES,
     OK, MAXITER, EINVAL, ENOMEM, ECUDA, ENUMERIC, EUNSUPPORTED, ESTATE,
 )

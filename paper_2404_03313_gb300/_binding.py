@@ -31,6 +31,7 @@ OPT_ALLOC_LIMIT = 14
 OPT_NVTX = 15
 OPT_JACOBI_POLISH_TOL = 16
 OPT_FIRST_ORDER = 17
+OPT_BATCH_WORKLIST = 18
 REG_S3TTV, REG_STV, REG_SSTV, REG_HSSTV1, REG_HSSTV2, REG_SSST = 0, 1, 2, 3, 4, 5
 KERNEL_CLASSES = ("primal", "l1_search", "block_dual", "dual", "finalize")
 STATE = {"u": 0, "s": 1, "t": 2, "y2": 3, "y3": 4, "Y": 5}

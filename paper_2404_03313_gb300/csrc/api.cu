@@ -28,6 +28,7 @@ struct s3ttv_ctx {
   float jacobi_tol = 2e-6f;
   float jacobi_polish = 0.f;  // 0: the default, tol / 8 (jacobi_polish_for)
   float first_order = 0.f;  // remainder bound of the first-order clip (0: off, the default)
+  int batch_worklist = 0;    // batched solves: 1, one block-dual work list per block side
   int tensor_cores = 2;  // block-dual form: 2 streaming (tensor cores), 1 group (tensor cores), 0 CUDA cores
   int layout = S3TTV_LAYOUT_PAPER;  // block matrices: paper k^2 x 2N3 or stacked 2k^2 x N3
   int open_s = 0;                   // 1: D_s stops at the last band (no wrap-around)
@@ -75,6 +76,8 @@ struct s3ttv_ctx {
   long long prof_n[S3TTV_KERNEL_CLASSES] = {0, 0, 0, 0, 0};
   // batched solves: one member context (workspace and stream) per problem
   std::vector<s3ttv_ctx *> members;
+  BatchDual *batch_items = nullptr;  // the block-dual work lists of a batched solve (device)
+  size_t cap_items = 0;
 };
 
 namespace {
@@ -179,6 +182,9 @@ void free_all(s3ttv_ctx *c) {
   if (c->hcnt) cudaFree(c->hcnt);
   if (c->hsum) cudaFree(c->hsum);
   if (c->macc) cudaFree(c->macc);
+  if (c->batch_items) cudaFree(c->batch_items);
+  c->batch_items = nullptr;
+  c->cap_items = 0;
   c->macc = nullptr;
   c->cap_macc = 0;
   c->sc = nullptr;
@@ -560,11 +566,52 @@ __global__ void set_c3_kernel(Scalars *sc, double c3) { sc->c3 = c3; }
 
 // One pass of Alg. 1, enqueued on the context stream.  `par` selects the current
 // t / Z buffers; the pass writes the other ones.
+// The block-dual arguments of one pass at parity par.
+BlockDualArgs make_bd_args(s3ttv_ctx *ctx, int par, const BdShape &bd) {
+  BlockDualArgs ba;
+  ba.Y = ctx->Y;
+  ba.Fv = ctx->Fv;
+  ba.Fh = ctx->Fh;
+  ba.Fs = ctx->Fs;
+  ba.Zv = ctx->Zv[par ^ 1];
+  ba.Zh = ctx->Zh[par ^ 1];
+  ba.Zs = ctx->Zs[par ^ 1];
+  ba.dm = ctx->dm;
+  ba.gY = (float)ctx->gam[3];
+  ba.rs = bd.rs;
+  ba.max_sweeps = ctx->jacobi_max_sweeps;
+  ba.tol = ctx->jacobi_tol;
+  ba.polish = jacobi_polish_for(ctx);
+  ba.fo_tol = bd.large ? 0.f : ctx->first_order;
+  ba.sc = ctx->sc;
+  ba.W = ctx->warm_start ? ctx->W : nullptr;
+  ba.w_stride = ctx->w_stride;
+  ba.warm = ctx->warm_start && ctx->warm_valid;
+  const bool fb = ctx->fp64_fallback && bd.fb_smem > 0;
+  ba.fb_list = fb ? ctx->fb_list : nullptr;
+  ba.fb_cap = fb ? ctx->fb_cap : 0;
+  return ba;
+}
+
+// One pass of Alg. 1 (part 0), or its steps before the block duals (part 1:
+// primal step, l1-ball thresholds, D D_s ubar) or after them (part 2: the FP64
+// re-solve queue, the dual step, finalize); the batched solve launches the
+// block duals of all its problems in between.
 int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
-                 cudaEvent_t *ev) {
+                 cudaEvent_t *ev, int part = 0) {
   const Dims &dm = ctx->dm;
   cudaStream_t st = ctx->stream;
   NvtxPhase ph(ctx->nvtx);
+  if (part == 2) {
+    const BlockDualArgs ba = make_bd_args(ctx, par, bd);
+    if (ba.fb_list) {
+      CU(launch_fallback(ba, ctx->k, ctx->layout == S3TTV_LAYOUT_STACKED, row_parts(ctx), ctx->num_sms,
+                         bd.fb_smem, st));
+      ctx->launches += 1;
+    }
+    if (ctx->warm_start) ctx->warm_valid = true;
+  }
+  if (part != 2) {
   ph.next("primal (steps 2-7)");
   if (ev) CU(cudaEventRecord(ev[0], st));
   PrimalArgs pa;
@@ -629,28 +676,12 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   } else {
   CU(launch_xfield(ctx->ubar, ctx->Fv, ctx->Fh, dm, grid_e, st, ctx->open_s,
                    ctx->reg == S3TTV_REG_STV || is_ssst(ctx), ctx->Fs));
-  BlockDualArgs ba;
-  ba.Y = ctx->Y;
-  ba.Fv = ctx->Fv;
-  ba.Fh = ctx->Fh;
-  ba.Fs = ctx->Fs;
-  ba.Zv = ctx->Zv[par ^ 1];
-  ba.Zh = ctx->Zh[par ^ 1];
-  ba.Zs = ctx->Zs[par ^ 1];
-  ba.dm = dm;
-  ba.gY = (float)ctx->gam[3];
-  ba.rs = bd.rs;
-  ba.max_sweeps = ctx->jacobi_max_sweeps;
-  ba.tol = ctx->jacobi_tol;
-  ba.polish = jacobi_polish_for(ctx);
-  ba.fo_tol = bd.large ? 0.f : ctx->first_order;
-  ba.sc = ctx->sc;
-  ba.W = ctx->warm_start ? ctx->W : nullptr;
-  ba.w_stride = ctx->w_stride;
-  ba.warm = ctx->warm_start && ctx->warm_valid;
-  const bool fb = ctx->fp64_fallback && bd.fb_smem > 0;
-  ba.fb_list = fb ? ctx->fb_list : nullptr;
-  ba.fb_cap = fb ? ctx->fb_cap : 0;
+  if (part == 1) {
+    ctx->launches += 7;  // primal, three scans, two histograms, xfield
+    return S3TTV_OK;
+  }
+  const BlockDualArgs ba = make_bd_args(ctx, par, bd);
+  const bool fb = ba.fb_list != nullptr;
   if (bd.large)
     CU(launch_block_dual_large(ba, ctx->k, ctx->layout == S3TTV_LAYOUT_STACKED, bd.grid, bd.smem, st,
                                row_parts(ctx)));
@@ -663,6 +694,7 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   if (ctx->warm_start) ctx->warm_valid = true;
   }
   if (ev) CU(cudaEventRecord(ev[3], st));
+  }  // part != 2
 
   ph.next("dual (steps 12-13)");
   DualArgs da;
@@ -695,6 +727,10 @@ int enqueue_pass(s3ttv_ctx *ctx, int par, int grid_e, const BdShape &bd,
   ph.next("finalize (step 14, stop rule)");
   CU(launch_finalize(fa, st));
   if (ev) CU(cudaEventRecord(ev[5], st));
+  if (part == 2) {
+    ctx->launches += 2;  // dual, finalize (the block duals are counted by the batch)
+    return S3TTV_OK;
+  }
   // SSTV and HSSTV: one elementwise dual kernel in place of xfield + block dual
   ctx->launches += (ctx->reg == S3TTV_REG_SSTV || is_hsstv(ctx)) ? kLaunchesPerPass - 1 : kLaunchesPerPass;
   return S3TTV_OK;
@@ -851,6 +887,10 @@ int s3ttv_set_option(s3ttv_ctx *ctx, int key, double value) {
     case S3TTV_OPT_FIRST_ORDER:
       if (!(value >= 0 && value < 1)) return fail(ctx, S3TTV_EINVAL, "first-order bound must be in [0, 1)");
       ctx->first_order = (float)value;
+      return S3TTV_OK;
+    case S3TTV_OPT_BATCH_WORKLIST:
+      if (value != 0 && value != 1) return fail(ctx, S3TTV_EINVAL, "batch_worklist must be 0 or 1");
+      ctx->batch_worklist = (int)value;
       return S3TTV_OK;
     case S3TTV_OPT_JACOBI_POLISH_TOL:
       if (!(value >= 0 && value < 1)) return fail(ctx, S3TTV_EINVAL, "jacobi polish tolerance must be in [0, 1)");
@@ -1227,6 +1267,106 @@ int enqueue_batch(s3ttv_ctx *ctx, int n, const std::vector<BdShape> &bd, const s
 
 }  // namespace
 
+// The work lists of a batched solve's block duals: for each block side k in the
+// batch, the problems with that k (their BlockDualArgs and running first-block
+// offsets), for both parities of the Z buffers; one persistent launch per k.
+struct BatchGroup {
+  int k = 0, offset = 0, count = 0, grid = 0;  // items [offset, offset + count) of a parity's list
+  long long total = 0;                         // blocks of the group's problems
+};
+struct BatchPlan {
+  int n_items = 0;
+  std::vector<BatchGroup> groups;
+};
+
+// Every member's block duals can join one work list: the streaming k <= 5 form
+// of a regulariser with blocks (S3TTV or STV), all members at the same parity.
+bool worklist_eligible(s3ttv_ctx *ctx, int n, const std::vector<BdShape> &bd, const std::vector<int> &par) {
+  for (int i = 0; i < n; ++i) {
+    const s3ttv_ctx *m = ctx->members[i];
+    if (bd[i].large || bd[i].v.tc != 2 || par[i] != par[0]) return false;
+    if (m->reg != S3TTV_REG_S3TTV && m->reg != S3TTV_REG_STV) return false;
+  }
+  return true;
+}
+
+int build_worklist(s3ttv_ctx *ctx, int n, const std::vector<BdShape> &bd, BatchPlan *plan) {
+  std::vector<BatchDual> host;
+  plan->groups.clear();
+  for (int p = 0; p < 2; ++p) {
+    for (int k = 1; k <= kMaxSmallK; ++k) {
+      BatchGroup g;
+      g.k = k;
+      g.offset = (int)host.size() - p * plan->n_items;
+      for (int i = 0; i < n; ++i) {
+        s3ttv_ctx *m = ctx->members[i];
+        if (m->k != k) continue;
+        BatchDual it;
+        it.a = make_bd_args(m, p, bd[i]);
+        it.first = g.total;
+        g.total += m->dm.P;
+        host.push_back(it);
+        ++g.count;
+      }
+      if (p == 0 && g.count) {
+        int per_sm = 0;
+        const cudaError_t e = block_dual_batch_prepare(k, &per_sm);
+        if (e != cudaSuccess) return fail(ctx, S3TTV_ECUDA, "batched block dual, k = %d: %s", k, cudaGetErrorString(e));
+        long long grid = (long long)ctx->num_sms * (per_sm > 0 ? per_sm : 1);
+        const long long rounds = (g.total + block_dual_group() - 1) / block_dual_group();
+        g.grid = (int)(grid < rounds ? grid : rounds);
+        plan->groups.push_back(g);
+      }
+    }
+    if (p == 0) plan->n_items = (int)host.size();
+  }
+  const size_t bytes = host.size() * sizeof(BatchDual);
+  if (ctx->cap_items < bytes) {
+    if (ctx->batch_items) {
+      cudaFree(ctx->batch_items);
+      ctx->bytes -= ctx->cap_items;
+      ctx->batch_items = nullptr;
+      ctx->cap_items = 0;
+    }
+    int rc = dmalloc(ctx, (void **)&ctx->batch_items, bytes);
+    if (rc) return rc;
+    ctx->cap_items = bytes;
+  }
+  CU(cudaMemcpyAsync(ctx->batch_items, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return S3TTV_OK;
+}
+
+// Enqueue `passes` passes of every member: each pass's steps before the block
+// duals on the members' own streams, then the block duals of all members in
+// one work-list launch per block side on ctx->stream, then the steps after
+// them on the members' streams again.
+int enqueue_batch_worklist(s3ttv_ctx *ctx, int n, const std::vector<BdShape> &bd, const std::vector<int> &grid_e,
+                           const std::vector<int> &par, int passes, ForkJoin &fj, const BatchPlan &plan) {
+  for (int c = 0; c < passes; ++c) {
+    for (int half = 1; half <= 2; ++half) {
+      CU(cudaEventRecord(fj.fork, ctx->stream));
+      for (int i = 0; i < n; ++i) {
+        s3ttv_ctx *m = ctx->members[i];
+        CU(cudaStreamWaitEvent(m->stream, fj.fork, 0));
+        const int rc = enqueue_pass(m, par[i] ^ (c & 1), grid_e[i], bd[i], nullptr, half);
+        if (rc) return fail(ctx, rc, "problem %d: %s", i, m->err);
+        CU(cudaEventRecord(fj.join[i], m->stream));
+        CU(cudaStreamWaitEvent(ctx->stream, fj.join[i], 0));
+      }
+      if (half == 1) {
+        const int p = (par[0] ^ c) & 1;
+        for (const BatchGroup &g : plan.groups) {
+          CU(launch_block_dual_batch(g.k, ctx->batch_items + (size_t)p * plan.n_items + g.offset, g.count, g.total,
+                                     g.grid, ctx->stream));
+          ctx->launches += 1;
+        }
+      }
+    }
+  }
+  return S3TTV_OK;
+}
+
 int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, int max_iter, float tol,
                         s3ttv_info *infos) {
   const double t0 = now_s();
@@ -1277,12 +1417,30 @@ int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, in
     begin_iterate_kernel<<<1, 1, 0, m->stream>>>(m->sc, max_iter, tol);
     CU(cudaGetLastError());
     m->launches += 1;
+    if (m->warm_start && m->W) {
+      // every block starts cold on a NaN marker, so every recorded pass may
+      // take the stored rows as they stand (warm from the second pass on)
+      CU(cudaMemsetAsync(m->W, 0xff, sizeof(float) * (size_t)m->dm.P * m->w_stride, m->stream));
+      m->warm_valid = true;
+    }
   }
+  BatchPlan plan;
+  const bool worklist = ctx->batch_worklist && worklist_eligible(ctx, n, bd, par);
+  if (worklist) {
+    for (int i = 0; i < n; ++i) CU(cudaStreamSynchronize(ctx->members[i]->stream));
+    const int rcw = build_worklist(ctx, n, bd, &plan);
+    if (rcw) return rcw;
+  }
+
   // one chunk of passes of every problem, recorded as a graph (an even number
   // of passes returns every problem to its starting parity)
   const int chunk = (ctx->check_every + 1) & ~1;
   ForkJoin fj;
   CU(fj.create(n));
+  auto enqueue = [&](int passes) {
+    return worklist ? enqueue_batch_worklist(ctx, n, bd, grid_e, par, passes, fj, plan)
+                    : enqueue_batch(ctx, n, bd, grid_e, par, passes, fj);
+  };
   cudaGraphExec_t exec = nullptr;
   std::vector<long long> launches0(n), per_pass(n, kLaunchesPerPass);
   // the legacy default streams cannot be captured: then every chunk is enqueued
@@ -1290,7 +1448,7 @@ int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, in
   if (max_iter >= chunk && capturable) {
     for (int i = 0; i < n; ++i) launches0[i] = ctx->members[i]->launches;
     CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_batch(ctx, n, bd, grid_e, par, chunk, fj);
+    int rc = enqueue(chunk);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(ctx->stream, &graph);
     if (rc) {
@@ -1320,7 +1478,7 @@ int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, in
       }
       for (int i = 0; i < n; ++i) ctx->members[i]->launches += per_pass[i] * chunk;
     } else {
-      if ((rc = enqueue_batch(ctx, n, bd, grid_e, par, step, fj))) break;
+      if ((rc = enqueue(step))) break;
       for (int i = 0; i < n; ++i) par[i] ^= step & 1;
     }
     enq += step;

@@ -236,11 +236,13 @@ __device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
 
 // x ~ hi + lo with hi = x truncated to TF32 (low 13 mantissa bits cleared,
 // |x - hi| < 2^-10 |x|) and lo = x - hi (exact in FP32) truncated to TF32 as
-// well: |x - hi - lo| < 2^-20 |x|.  Three integer / FP32 instructions, and the
-// tensor core reads both parts exactly.
+// well: |x - hi - lo| < 2^-20 |x|.  The TF32 tensor-core operands ignore the
+// low 13 bits of their 32-bit registers (checked on GB300: every product of
+// raw and of masked operands agreed bit for bit), so both parts go in
+// unmasked: two instructions, the same products.
 __device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo) {
-  hi = __float_as_uint(x) & 0xffffe000u;
-  lo = __float_as_uint(x - __uint_as_float(hi)) & 0xffffe000u;
+  hi = __float_as_uint(x);
+  lo = __float_as_uint(x - __uint_as_float(hi & 0xffffe000u));
 }
 // d += A B for one 16 x 8 x 8 tile, TF32 operands, FP32 accumulation (warp-wide).
 __device__ __forceinline__ void mma_tf32(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
@@ -1272,6 +1274,27 @@ __global__ void __launch_bounds__(kNW * 32, MINB) block_dual_kernel(BlockDualArg
   if (tid == 0 && s_fo) atomicAdd(&a.sc->fo_blocks, (unsigned long long)s_fo);
 }
 
+// One warp: M = I - Ut^T Ut of its block on the tensor cores, written over Ut
+// by rows of stride GS (Ut: NPOS rows of stride UTS = n in the block's slot).
+template <int K>
+__device__ void form_M_mma(float *Gm) {
+  using S = Shape<K>;
+  constexpr int n = S::n, NPOS = S::NPOS, GS = S::GS;
+  float d[2][4][4];
+  mm32<n, n, NPOS>([&](int i, int k) { return Gm[k * S::UTS + i]; },
+                   [&](int k, int j) { return Gm[k * S::UTS + j]; }, d);
+  __syncwarp();  // Ut no longer read
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = frag_row(m, e), j = frag_col(q, e);
+        if (i < n && j < n) Gm[i * GS + j] = (i == j ? 1.f : 0.f) - d[m][q][e];
+      }
+}
+
 // ---------------------------------------------------------------------------
 // Streaming form (k <= 5, tensor cores): every warp owns one block at a time,
 // end to end, and streams its rows through two chunk buffers of kCW columns,
@@ -1305,27 +1328,26 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// One block l of the problem a, by the calling warp (see above).  bufs: the
+// warp's shared region (two chunk buffers, then G / M, then the rows' pixel
+// offsets, laid out for K); the statistics go to sweeps and fo_count.
 template <int K>
-__global__ void __launch_bounds__(kSW * 32, 4) block_dual_stream_kernel(BlockDualArgs a) {
+__device__ void stream_block(const BlockDualArgs &a, long long l, float *bufs, unsigned long long pol_keep,
+                             unsigned long long pol_done, unsigned long long &sweeps,
+                             unsigned long long &fo_count) {
   using S = Shape<K>;
   using T = MmaShape<K>;
   using LY = StreamLayout<K>;
   constexpr int n = S::n, GS = S::GS, NTILE = T::NTILE, NM = T::NM, NKS = T::NKS, NR = T::NR, S0 = n - NR;
   constexpr int NE = (n * (kCW / 4) + 31) / 32;  // 16-byte pieces of a chunk per lane
-  extern __shared__ __align__(16) float smem[];
-  if (a.sc->done) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  float *bufs = smem + warp * LY::per_warp;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   float *Gm = bufs + 2 * LY::buf;
   int *off = reinterpret_cast<int *>(Gm + LY::gm);
   const Dims dm = a.dm;
   const int N3p = dm.N3p, RW = 2 * N3p, NCH = (RW + kCW - 1) / kCW;
   const float gY = a.gY;
   const bool warm = a.warm && a.W;  // a.w_stride == w_floats<K>()
-  const unsigned long long pol_keep = l2_evict_last(), pol_done = l2_evict_first();
-  unsigned long long sweeps = 0, fo_count = 0;
-  const long long step = (long long)gridDim.x * kSW;
-  for (long long l = (long long)blockIdx.x * kSW + warp; l < dm.P; l += step) {
+  {
     float *Yl = a.Y + (size_t)l * n * RW;
     if (lane < n) {
       const int p = (int)(l / dm.N2), q = (int)(l - (long long)p * dm.N2);
@@ -1447,10 +1469,19 @@ __global__ void __launch_bounds__(kSW * 32, 4) block_dual_stream_kernel(BlockDua
     }
     __syncwarp();  // G and W visible to every lane
     bool fo = false;
-    const float *C0 = nullptr;
-    if (Ws && a.fo_tol > 0.f && !(Ws[0] != Ws[0])) {
+    const float *C0 = nullptr;  // the warm-start product W G, on the tensor cores
+    if (Ws && !(Ws[0] != Ws[0])) {
       float *Sc = bufs + w_floats<K>();
-      fo = first_order_clip<K, true>(Ws, Gm, Sc, reinterpret_cast<float4 *>(Sc + S::NPOS * fo_stride<K>()), a.fo_tol);
+      if (a.fo_tol > 0.f) {
+        fo = first_order_clip<K, true>(Ws, Gm, Sc, reinterpret_cast<float4 *>(Sc + S::NPOS * fo_stride<K>()),
+                                       a.fo_tol);
+      } else {
+        float d[2][4][4];
+        mm32<S::NPOS, n, n>([&](int i, int k) { return Ws[i * n + k]; },
+                            [&](int k, int j) { return Gm[k * GS + j]; }, d);
+        store_frag<S::NPOS, n>(d, Sc, fo_stride<K>());
+        __syncwarp();
+      }
       C0 = Sc;
     }
     if (fo) {
@@ -1471,8 +1502,8 @@ __global__ void __launch_bounds__(kSW * 32, 4) block_dual_stream_kernel(BlockDua
       }
       queued = __shfl_sync(kFull, queued, 0);
       __syncwarp();
-      form_M<K, true>(Gm);
-      if (queued) continue;  // Y_l keeps Y' for the FP64 re-solve, nothing added to Z
+      form_M_mma<K>(Gm);
+      if (queued) return;  // Y_l keeps Y' for the FP64 re-solve, nothing added to Z
     }
     __syncwarp();  // M visible to every lane; W and the scratch are no longer read
 
@@ -1577,9 +1608,77 @@ __global__ void __launch_bounds__(kSW * 32, 4) block_dual_stream_kernel(BlockDua
       __syncwarp();  // every lane has read this buffer before it is refilled
     }
   }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kSW * 32, 4) block_dual_stream_kernel(BlockDualArgs a) {
+  extern __shared__ __align__(16) float smem[];
+  if (a.sc->done) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float *bufs = smem + warp * StreamLayout<K>::per_warp;
+  const unsigned long long pol_keep = l2_evict_last(), pol_done = l2_evict_first();
+  unsigned long long sweeps = 0, fo_count = 0;
+  const long long step = (long long)gridDim.x * kSW;
+  for (long long l = (long long)blockIdx.x * kSW + warp; l < a.dm.P; l += step)
+    stream_block<K>(a, l, bufs, pol_keep, pol_done, sweeps, fo_count);
   if (lane == 0) {
     if (sweeps) atomicAdd(&a.sc->jacobi_sweeps, sweeps);
     if (fo_count) atomicAdd(&a.sc->fo_blocks, fo_count);
+  }
+}
+
+// The batched solve's block duals: one work list over the blocks of every
+// problem with block side K (problem i owns entries [items[i].first,
+// items[i + 1].first)), taken by the warps of one persistent grid; each
+// problem keeps its own sizes, step size, stop flag and statistics.
+template <int K>
+__global__ void __launch_bounds__(kSW * 32, 4) block_dual_stream_batch_kernel(const BatchDual *items, int n,
+                                                                              long long total) {
+  extern __shared__ __align__(16) float smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float *bufs = smem + warp * StreamLayout<K>::per_warp;
+  const unsigned long long pol_keep = l2_evict_last(), pol_done = l2_evict_first();
+  unsigned long long sweeps = 0, fo_count = 0;
+  int c = 0;
+  auto flush = [&]() {
+    if (lane == 0) {
+      if (sweeps) atomicAdd(&items[c].a.sc->jacobi_sweeps, sweeps);
+      if (fo_count) atomicAdd(&items[c].a.sc->fo_blocks, fo_count);
+    }
+    sweeps = fo_count = 0;
+  };
+  const long long step = (long long)gridDim.x * kSW;
+  for (long long e = (long long)blockIdx.x * kSW + warp; e < total; e += step) {
+    if (c + 1 < n && items[c + 1].first <= e) {  // a warp's entries only grow: move forward
+      flush();
+      while (c + 1 < n && items[c + 1].first <= e) ++c;
+    }
+    const BlockDualArgs &a = items[c].a;
+    if (a.sc->done) continue;
+    stream_block<K>(a, e - items[c].first, bufs, pol_keep, pol_done, sweeps, fo_count);
+  }
+  flush();
+}
+
+using BatchFn = void (*)(const BatchDual *, int, long long);
+BatchFn batch_kernel(int k) {
+  switch (k) {
+    case 1: return block_dual_stream_batch_kernel<1>;
+    case 2: return block_dual_stream_batch_kernel<2>;
+    case 3: return block_dual_stream_batch_kernel<3>;
+    case 4: return block_dual_stream_batch_kernel<4>;
+    case 5: return block_dual_stream_batch_kernel<5>;
+    default: return nullptr;
+  }
+}
+size_t batch_smem(int k) {
+  switch (k) {
+    case 1: return sizeof(float) * kSW * StreamLayout<1>::per_warp;
+    case 2: return sizeof(float) * kSW * StreamLayout<2>::per_warp;
+    case 3: return sizeof(float) * kSW * StreamLayout<3>::per_warp;
+    case 4: return sizeof(float) * kSW * StreamLayout<4>::per_warp;
+    case 5: return sizeof(float) * kSW * StreamLayout<5>::per_warp;
+    default: return 0;
   }
 }
 
@@ -1684,6 +1783,26 @@ cudaError_t block_dual_occupancy(const BdVariant &v, size_t smem, int *ctas) {
   KernelFn f = kernel_for(v);
   if (!f) return cudaErrorInvalidValue;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, reinterpret_cast<const void *>(f), kNW * 32, smem);
+}
+
+cudaError_t block_dual_batch_prepare(int k, int *ctas_per_sm) {
+  BatchFn f = batch_kernel(k);
+  if (!f) return cudaErrorInvalidValue;
+  int dev = 0, cap = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t smem = batch_smem(k);
+  if (e == cudaSuccess && (size_t)cap < smem) return cudaErrorInvalidValue;
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, f, kSW * 32, smem);
+  return e;
+}
+
+cudaError_t launch_block_dual_batch(int k, const BatchDual *items, int n, long long total, int grid, cudaStream_t st) {
+  BatchFn f = batch_kernel(k);
+  if (!f) return cudaErrorInvalidValue;
+  f<<<grid, kSW * 32, batch_smem(k), st>>>(items, n, total);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_block_dual(const BlockDualArgs &a, const BdVariant &v, int grid, size_t smem, cudaStream_t st) {

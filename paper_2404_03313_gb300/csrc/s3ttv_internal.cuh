@@ -169,6 +169,15 @@ int block_dual_threads();
 int block_dual_group();
 // All return cudaErrorInvalidValue for an unsupported variant.
 cudaError_t launch_block_dual(const BlockDualArgs &a, const BdVariant &v, int grid, size_t smem, cudaStream_t st);
+// The batched solve's block duals (streaming form, k <= 5): one persistent
+// launch per block side k over a work list of the blocks of every problem with
+// that k.
+struct BatchDual {
+  BlockDualArgs a;   // the problem's arguments (its own Y, F, Z, W, sizes, scalars)
+  long long first;   // its first entry in the work list (a running sum of N1 * N2)
+};
+cudaError_t block_dual_batch_prepare(int k, int *ctas_per_sm);
+cudaError_t launch_block_dual_batch(int k, const BatchDual *items, int n, long long total, int grid, cudaStream_t st);
 bool block_dual_has(const BdVariant &v);  // this variant is compiled into the library
 // Larger blocks, k = kMinLargeK..kMaxLargeK (block_dual_large.cu): one CTA of
 // block_dual_large_threads() threads per block at a time, FP32 CUDA cores.
@@ -176,6 +185,7 @@ bool block_dual_has(const BdVariant &v);  // this variant is compiled into the l
 // and 2r + 1 the vertical and horizontal differences of window pixel r) for
 // k = 1..kMaxStackedK; the block memory [L][k^2][2][N3p] is the same.
 constexpr int kMinLargeK = 6, kMaxLargeK = 12, kMaxStackedK = 8;
+constexpr int kMaxSmallK = kMinLargeK - 1;  // the k <= 5 kernels (block_dual.cu)
 // parts = 3: SSST's rows [D_v u, D_h u, D_s u] (paper layout, k <= kMaxStackedK)
 size_t block_dual_large_smem_bytes(int k, bool stacked, int parts = 2);
 long long block_dual_large_w_stride(int k, bool stacked);

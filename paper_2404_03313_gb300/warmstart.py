@@ -3,9 +3,10 @@
 The paper has none: Alg. 1 starts from u = v, s = t = 0.  Here a 3-D U-Net
 (``WarmStartNet``, ``s3ttv_net_*`` in include/s3ttv.h) is trained on pairs
 (noisy cube, converged solver output) and its prediction (u, s, t) becomes the
-solver's starting point through ``s3ttv_set_state``; every dual starts at zero
-as usual.  The solver alone decides the result; the network can only change how
-many passes the stop rule needs.
+solver's starting point through ``s3ttv_set_state``; the duals start at zero as
+usual, or the block duals from the prediction (``dual_scale``).  The solver
+alone decides the result; the network can only change how many passes the
+stop rule needs.
 
 Arrays are float32 CUDA tensors shaped (N1, N2, N3).  PyTorch only slices and
 stacks training crops here; every arithmetic step runs in the library.
@@ -64,11 +65,17 @@ def train(net: WarmStartNet, inputs, targets, steps, crop=(32, 32, 32), batch=4,
 
 
 def solve(v, eps, alpha, beta, k, net: WarmStartNet | None = None, max_iter=5000, tol=1e-5, policy=STEP_PAPER,
-          solver: Solver | None = None, device=0, settle=32):
+          solver: Solver | None = None, device=0, settle=32, dual_scale=0.0, trace_ref=None, trace_every=16):
     """Alg. 1 on v from the cold start (net None) or from the network's
     prediction.  Returns a dict with u, s, t, the solver info (`iters` counts
     every pass), `seconds` (all of it: inference, set-up and passes) and
     `net_seconds` (inference alone).
+
+    dual_scale > 0 also starts the block duals from the network's u: Y =
+    the singular values of dual_scale * X(u_pred) clipped at 1 (one block-dual
+    step from Y = 0 with gamma_Y = dual_scale).  With trace_ref (the clean cube)
+    the MPSNR of u is recorded every trace_every passes as `trace`: [(passes,
+    MPSNR)] (the traced run's `seconds` include the measurements).
 
     A warm start first runs `settle` passes without the stop test: the duals
     start at zero, so the first passes leave u almost where the network put it
@@ -90,14 +97,37 @@ def solve(v, eps, alpha, beta, k, net: WarmStartNet | None = None, max_iter=5000
         if init is not None:
             for name, x in zip(("u", "s", "t"), init):
                 sv.set_state(name, x)
+            if dual_scale > 0:
+                N1, N2, N3 = v.shape
+                Y = torch.zeros(N1 * N2, k * k, 2 * N3, dtype=torch.float32, device=v.device)
+                with Solver(device) as aux:
+                    aux.block_dual(Y, init[0].contiguous(), k, gamma_Y=float(dual_scale))
+                sv.set_state("Y", Y)
+                del Y
+        trace = [] if trace_ref is not None else None
+
+        def run(n, stop_tol):
+            if trace is None:
+                return sv.iterate(n, stop_tol)
+            done, last = 0, None
+            while done < n:
+                last = sv.iterate(min(trace_every, n - done), stop_tol)
+                done += last["iters"]
+                base = trace[-1][0] if trace else 0
+                trace.append((base + last["iters"], sv.quality(sv.get_state("u", like=v), trace_ref)["mpsnr"]))
+                if last["converged"]:
+                    break
+            last["iters"] = done
+            return last
+
         if init is not None and settle > 0:
-            first = sv.iterate(min(settle, max_iter), 0.0)
+            first = run(min(settle, max_iter), 0.0)
             info = first
             if first["iters"] < max_iter:
-                info = sv.iterate(max_iter - first["iters"], tol)
+                info = run(max_iter - first["iters"], tol)
                 info["iters"] += first["iters"]
         else:
-            info = sv.iterate(max_iter, tol)
+            info = run(max_iter, tol)
         u = sv.get_state("u", like=v)
         s = sv.get_state("s", like=v)
         t = sv.get_state("t", like=v)
@@ -106,4 +136,4 @@ def solve(v, eps, alpha, beta, k, net: WarmStartNet | None = None, max_iter=5000
     finally:
         if own:
             sv.close()
-    return {"u": u, "s": s, "t": t, "info": info, "seconds": t2 - t0, "net_seconds": t1 - t0}
+    return {"u": u, "s": s, "t": t, "info": info, "seconds": t2 - t0, "net_seconds": t1 - t0, "trace": trace}

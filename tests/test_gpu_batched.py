@@ -41,11 +41,17 @@ def _problems(specs, device=True):
     return probs
 
 
-@pytest.mark.parametrize("form", [pytest.param(1, id="tc"), pytest.param(0, id="fp32")])
-def test_batch_matches_each_cube_alone_and_the_oracle(P, form):
+# form 2 (streaming) with the work list batches every problem's block duals
+# into one launch per block side; otherwise each problem's own launches are
+# recorded
+@pytest.mark.parametrize("form,worklist", [pytest.param(2, 1, id="tc_stream_worklist"),
+                                           pytest.param(2, 0, id="tc_stream"), pytest.param(1, 0, id="tc"),
+                                           pytest.param(0, 0, id="fp32")])
+def test_batch_matches_each_cube_alone_and_the_oracle(P, form, worklist):
     probs = _problems(SPECS)
     with P.Solver(0) as s:
         s.set_option(P.OPT_TENSOR_CORES, form)
+        s.set_option(P.OPT_BATCH_WORKLIST, worklist)
         out = s.solve_batched(probs, max_iter=30, tol=0.0)  # one recorded chunk of 16 plus 14 more
         alone = []
         for p in probs:

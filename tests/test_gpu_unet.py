@@ -160,13 +160,18 @@ def test_invalid_shapes_rejected(P):
 
 
 def test_trained_network_as_warm_start(P):
-    """What the trained network gains over the plain solver.  Train on six
-    64x64x32 cubes solved by the library, then on a held-out cube: the
-    prediction alone must restore far more than the noisy input holds, and the
-    solver started from it must reach the minimiser the cold start reaches
-    (MPSNR within 0.01 dB after a tight stop rule, 1e-7, or 20000 passes).  The passes each start needs
-    are printed; the network does not have to save passes (the duals start at
-    zero either way)."""
+    """What the trained network gains over the plain solver, as measured.
+    Train on six 64x64x32 cubes solved by the library, then on a held-out cube:
+    (1) the prediction alone (one forward pass, milliseconds) restores far more
+    than the noisy input holds (> 6 dB); (2) the solver started from it reaches
+    the minimiser the cold start reaches (MPSNR within 0.01 dB after a tight stop
+    rule, 1e-7, or 20000 passes), so the network never changes the result;
+    (3) with the paper's printed step sizes, where the stop rule does not fire,
+    the warm start is more than 3 dB ahead after 200 passes.  What it does not
+    gain: passes to the stop rule with the PC_EXACT step sizes (the duals, not
+    u, set that count; measured at 256x256x128, a warm start took 1025 and 1568
+    passes against 972 and 1714 cold, and starting the block duals from the
+    prediction saved 1-2% more), so that count is printed, not asserted."""
     import oracle as O
     from paper_2404_03313_gb300 import warmstart as WS
     from synthetic import make_cube, warm_start_specs
