@@ -534,6 +534,12 @@ def run_ours(args, spec):
         s3.close()
         del v3d
 
+    # ---- cost per pass against the block side (the paper's block-size study,
+    # Fig. Param_Anal, runs k up to 16 on 100x100x198-sized cubes) ----
+    sweep = None
+    if args.workload == DEFAULT_WORKLOAD and not args.no_block_sweep:
+        sweep = block_size_sweep(P, dev, stream)
+
     # ---- CPU baseline (oracle), rank 0 at N = 1 only: one full-cube pass timed
     # on all host cores, and a one-thread run on a crop ----
     cpu = None
@@ -569,7 +575,7 @@ def run_ours(args, spec):
                               "unit": "GB/s"},
             "kernel_avg_ms": kernel_ms, "jacobi_nonconverged": info["jacobi_nonconverged"],
             "jacobi_sweeps_mean": info["jacobi_sweeps"],
-            "to_tol": tol_run, "forms": forms, "precision_form": precision,
+            "to_tol": tol_run, "forms": forms, "precision_form": precision, "block_size_sweep": sweep,
         }
         out["pass_roofline"]["frac"] = out["pass_roofline"]["achieved"] / peak
         print(json.dumps(out), flush=True)
@@ -578,6 +584,39 @@ def run_ours(args, spec):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def block_size_sweep(P, dev, stream, ks=(5, 6, 8, 10, 12, 13, 14, 16), warm=3, timed=4):
+    """ms per pass at block side k on the 100x100x198 cube of the paper's
+    simulated experiments (its noise recipe, seeded), k = 5..16: warm passes,
+    then `timed` passes between CUDA events on the solver's stream, with the
+    block-dual kernel's own average from the solver's profile."""
+    import torch
+    from synthetic import WORKLOADS, CubeSpec, make_cube
+    base = WORKLOADS["paper_100x100x198_k10"]
+    rows = []
+    for k in ks:
+        spec = CubeSpec(base.N1, base.N2, base.N3, regions=base.regions, endmembers=base.endmembers,
+                        sigma=base.sigma, p_s=base.p_s, p_t=base.p_t, k=k, seed=base.seed)
+        _, v = make_cube(spec)
+        e, a, b = P.radii(v.size, spec.sigma, spec.p_s, spec.p_t, 0.95)
+        s = P.Solver(dev, stream=stream)
+        s.setup(torch.from_numpy(v).to(f"cuda:{dev}"), e, a, b, k)
+        s.set_option(P.OPT_CHECK_EVERY, 1000)
+        s.iterate(warm)
+        s.set_option(P.OPT_PROFILE, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = s.iterate(timed)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bd_ms, bd_n = s.kernel_stats()["block_dual"]
+        rows.append({"k": k, "ms_per_pass": e0.elapsed_time(e1) / timed, "block_dual_ms": bd_ms / max(bd_n, 1),
+                     "jacobi_sweeps_mean": info["jacobi_sweeps"],
+                     "jacobi_nonconverged": info["jacobi_nonconverged"]})
+        s.close()
+    return {"workload": "100x100x198 (paper_100x100x198 recipe), block side k", "warm_passes": warm,
+            "timed_passes": timed, "rows": rows}
 
 
 BATCH_WORKLOAD = "batch_64_uneven"
@@ -943,6 +982,8 @@ def main(argv=None):
                     help="warm-start workload: fixed pass budget of the runs with the paper's step sizes")
     ap.add_argument("--no-tol-run", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-block-sweep", action="store_true",
+                    help="skip the ms-per-pass sweep over block sides k = 5..16 (100x100x198)")
     ap.add_argument("--no-precision-run", action="store_true",
                     help="skip the 304x304x191 time-to-tolerance comparison of the two product forms")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

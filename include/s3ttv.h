@@ -287,10 +287,13 @@ int s3ttv_kernel_stats(const s3ttv_ctx *ctx, double *ms, long long *launches);
  * alpha    radius of the l1 ball of the sparse noise s (eq. constraint_sparse), >= 0.
  * beta     radius of the l1 ball of the stripe noise t (eq. constraint_stripe), >= 0.
  * mu_min, mu_max  box of u (eq. constraint_box), mu_min < mu_max.
- * k        block side (k x k x N3 blocks), 1 <= k <= min(N1, N2); this library supports k <= 12
- *          (k <= 5 on the tensor-core or CUDA-core per-warp path, 6..12, the paper's
- *          own 10 x 10 blocks included, on a per-CTA path in FP32) and N1 * N2 < 2^31,
- *          N1 * N2 * N3 < 2^33 (S3TTV_EUNSUPPORTED otherwise).
+ * k        block side (k x k x N3 blocks), 1 <= k <= min(N1, N2); this library supports k <= 16
+ *          (k <= 5 on the tensor-core or CUDA-core per-warp path, 6..16, the paper's
+ *          own 10 x 10 blocks included, on a per-CTA path in FP32; from k = 13 the
+ *          two k^2 x k^2 matrices of each block live in an L2-resident global
+ *          scratch of the context, and the FP64 re-solve of blocks at the sweep cap
+ *          is not available) and N1 * N2 < 2^31, N1 * N2 * N3 < 2^33
+ *          (S3TTV_EUNSUPPORTED otherwise).
  * max_iter iteration cap, >= 1.
  * tol      stop when ||u+ - u||_2 / ||u||_2 < tol (eq. StopCri_simulated), >= 0;
  *          0 runs exactly max_iter passes.
@@ -389,7 +392,9 @@ int s3ttv_tuned_form(const s3ttv_ctx *ctx, int *tensor_cores, int *ctas_per_sm);
  * HSSTV: their l1 or l1,2 norms); the layout and spectral boundary options
  * apply as in the solver.
  * S3TTV_ENUMERIC if u is not finite or a block does not converge; k <= 12
- * (k <= 8 for the stacked layout and SSST). */
+ * (each block's FP64 k^2 x k^2 Gram in shared memory; k = 13..16, which the
+ * solver takes, return S3TTV_EUNSUPPORTED here) and k <= 8 for the stacked
+ * layout and SSST. */
 int s3ttv_objective(s3ttv_ctx *ctx, const float *u, int N1, int N2, int N3, int k, double *value);
 
 /* Quality of a restored cube u against a reference cube ref (both host or

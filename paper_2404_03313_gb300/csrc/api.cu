@@ -78,12 +78,14 @@ struct s3ttv_ctx {
   std::vector<s3ttv_ctx *> members;
   BatchDual *batch_items = nullptr;  // the block-dual work lists of a batched solve (device)
   size_t cap_items = 0;
+  float *rows = nullptr;  // blocks above 12 x 12: the per-CTA n x n matrices of the block duals
+  size_t cap_rows = 0;    // bytes
 };
 
 namespace {
 
 constexpr int kMaxGrid = 4096;
-constexpr int kMaxK = kMaxLargeK;  // k <= 5: block_dual.cu; 6..12: block_dual_large.cu
+constexpr int kMaxK = kMaxLargeK;  // k <= 5: block_dual.cu; 6..16: block_dual_large.cu
 constexpr int kLaunchesPerPass = 10;  // kernels enqueue_pass launches (block-dual regularisers, no re-solve)
 constexpr int kFbQueueMax = 1 << 16;  // entries of the FP64 re-solve queue
 
@@ -185,6 +187,9 @@ void free_all(s3ttv_ctx *c) {
   if (c->batch_items) cudaFree(c->batch_items);
   c->batch_items = nullptr;
   c->cap_items = 0;
+  if (c->rows) cudaFree(c->rows);
+  c->rows = nullptr;
+  c->cap_rows = 0;
   c->macc = nullptr;
   c->cap_macc = 0;
   c->sc = nullptr;
@@ -335,7 +340,24 @@ struct BdShape {
   BdVariant v;
   bool large = false;  // block_dual_large.cu (k > 5)
   size_t fb_smem = 0;  // dynamic shared memory of the FP64 re-solve (0: not available)
+  size_t rows_bytes = 0;  // global scratch of the large kernel's grid (ensure_rows)
 };
+
+// The large kernel's global scratch for shape sh.  Call it after
+// ensure_problem_buffers, whose reallocation frees every buffer of the context.
+int ensure_rows(s3ttv_ctx *ctx, const BdShape &sh) {
+  if (sh.rows_bytes <= ctx->cap_rows) return S3TTV_OK;
+  if (ctx->rows) {
+    cudaFree(ctx->rows);
+    ctx->bytes -= ctx->cap_rows;
+    ctx->rows = nullptr;
+    ctx->cap_rows = 0;
+  }
+  int rc = dmalloc(ctx, (void **)&ctx->rows, sh.rows_bytes);
+  if (rc) return rc;
+  ctx->cap_rows = sh.rows_bytes;
+  return S3TTV_OK;
+}
 
 // The launch shape of one block-dual form of the k <= 5 kernel: tensor cores
 // (tc) or CUDA cores, compiled for minb CTAs per SM.  Fails (S3TTV_EUNSUPPORTED)
@@ -407,6 +429,8 @@ int block_dual_shape(s3ttv_ctx *ctx, const Dims &dm, int k, BdShape *sh) {
     long long g = (long long)ctx->num_sms * per_sm;
     if (g > dm.P) g = dm.P;
     sh->grid = (int)g;
+    // blocks above kMaxSmemRows rows: their two n x n matrices per CTA in global memory
+    sh->rows_bytes = block_dual_large_rows_floats(k, stacked, parts) * sizeof(float) * (size_t)g;
     return S3TTV_OK;
   }
   sh->rs = block_dual_row_stride(dm.N3p);
@@ -590,6 +614,8 @@ BlockDualArgs make_bd_args(s3ttv_ctx *ctx, int par, const BdShape &bd) {
   const bool fb = ctx->fp64_fallback && bd.fb_smem > 0;
   ba.fb_list = fb ? ctx->fb_list : nullptr;
   ba.fb_cap = fb ? ctx->fb_cap : 0;
+  ba.rows = ctx->rows;
+  ba.rows_cap = ctx->cap_rows / sizeof(float);
   return ba;
 }
 
@@ -1036,6 +1062,7 @@ int s3ttv_iterate(s3ttv_ctx *ctx, int n, float tol, s3ttv_info *info) {
   DeviceGuard g(ctx->device);
   BdShape bd;
   int rc = block_dual_shape(ctx, ctx->dm, ctx->k, &bd);
+  if (!rc) rc = ensure_rows(ctx, bd);
   if (rc) return rc;
   const int grid_e = elementwise_grid(ctx, ctx->dm.Np);
   Scalars hs;
@@ -1409,6 +1436,7 @@ int s3ttv_solve_batched(s3ttv_ctx *ctx, int n, const s3ttv_problem *problems, in
     const s3ttv_problem &p = problems[i];
     int rc = s3ttv_setup(m, p.v, p.N1, p.N2, p.N3, p.eps, p.alpha, p.beta, p.mu_min, p.mu_max, p.k);
     if (!rc) rc = block_dual_shape(m, m->dm, m->k, &bd[i]);
+    if (!rc) rc = ensure_rows(m, bd[i]);
     if (rc) {
       if (infos) infos[i].status = rc;
       return fail(ctx, rc, "problem %d: %s", i, m->err);
@@ -1613,6 +1641,7 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   if ((rc = block_dual_shape(ctx, dm, k, &bd))) return rc;
   ctx->ready = false;
   if ((rc = ensure_problem_buffers(ctx, dm, k))) return rc;
+  if ((rc = ensure_rows(ctx, bd))) return rc;
   ctx->dm = dm;
   ctx->k = k;
   if ((rc = load_Y(ctx, Y))) return rc;
@@ -1642,6 +1671,8 @@ int s3ttv_block_dual(s3ttv_ctx *ctx, float *Y, const float *ubar, float *Zv, flo
   const bool fb = ctx->fp64_fallback && bd.fb_smem > 0;
   ba.fb_list = fb ? ctx->fb_list : nullptr;
   ba.fb_cap = fb ? ctx->fb_cap : 0;
+  ba.rows = ctx->rows;
+  ba.rows_cap = ctx->cap_rows / sizeof(float);
   if (bd.large) CU(launch_block_dual_large(ba, k, ctx->layout == S3TTV_LAYOUT_STACKED, bd.grid, bd.smem, ctx->stream));
   else CU(launch_block_dual(ba, bd.v, bd.grid, bd.smem, ctx->stream));
   if (fb)

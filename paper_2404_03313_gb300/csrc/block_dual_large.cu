@@ -1,5 +1,5 @@
 // Alg. 1 steps 8-11 for the larger blocks the paper itself uses (Sec. IV sets
-// the block to 10 x 10 pixels; this file takes k = 6..12, n = k^2 = 36..144
+// the block to 10 x 10 pixels; this file takes k = 6..16, n = k^2 = 36..256
 // block rows).  The mathematics is that of block_dual.cu: with
 // Y'_l = Y_l + gamma_Y P_l D D_s ubar and G = Y' Y'^T = sum_x lam_x u_x u_x^T,
 //
@@ -33,6 +33,11 @@
 // has: 2 ([D_v | D_h] differences, S3TTV and STV) or 3 (SSST's first-order
 // [D_v u | D_h u | D_s u], F = (Fv, Fh, Fs), Z = (Zv, Zh, Zs)); SSST's k^2 x 3N3
 // blocks run here for every k <= kMaxStackedK.
+// Above kMaxSmemRows rows (k = 13..16) the two n x n buffers no longer fit
+// shared memory: they live in a per-CTA slice of a global scratch (up to
+// 2 x 256 x 272 floats, 557 KB per CTA, 85 MB for 152 CTAs, so L2-resident),
+// the Gram accumulates its upper-triangle tiles over several passes of the
+// chunks (3 tiles a thread per pass) and the Jacobi uses 8-lane groups.
 // FP32 throughout (FP32 FMAs on CUDA cores).
 #include <math.h>
 #include "s3ttv_internal.cuh"
@@ -46,12 +51,12 @@ constexpr int kCW = 48;        // columns of Y' per streamed chunk
 // The Gram's 4 x 4 tiles read four chunk rows apart (4 (kCW + 4) floats, 16
 // banks mod 32) and rotate their column order within 16-column windows.
 static_assert(kCW % 16 == 0 && (4 * (kCW + 4)) % 32 == 16, "chunk geometry of the Gram's bank rotation");
-constexpr int kSlots = (kMaxLargeK * kMaxLargeK + 31) / 32;  // row elements a lane holds
-
 // Lanes per row pair in the Jacobi: 8, or 4 where that lets one round of the
-// CTA's warps cover every pair of a step (n / 2 pairs) and 8 would need more.
+// CTA's warps cover every pair of a step (n / 2 pairs) and 8 would need more;
+// blocks above kMaxSmemRows rows always 8 (at most 32 floats of a row per lane).
 __host__ __device__ constexpr int pair_lanes(int n, int lw) {
-  return ((n + 1) / 2 + lw * 8 - 1) / (lw * 8) < ((n + 1) / 2 + lw * 4 - 1) / (lw * 4) ? 4 : 8;
+  return n > kMaxSmemRows ? 8
+                          : (((n + 1) / 2 + lw * 8 - 1) / (lw * 8) < ((n + 1) / 2 + lw * 4 - 1) / (lw * 4) ? 4 : 8);
 }
 
 // Two FP32 values in one 64-bit register pair, and the packed FP32x2
@@ -81,10 +86,13 @@ __device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
 struct Layout {
   int n, npos, gs, cs;  // block rows, rows padded to even, row strides of the n x n buffers and the chunk
   int nt4;              // 4-row tiles across npos
-  size_t x1, x2, chunk, nrm, pix, last, total;  // float offsets; total floats
+  size_t x1, x2, chunk, nrm, pix, last, total;  // float offsets; total floats of shared memory
+  size_t rows;          // floats of the n x n buffers in global memory per CTA (0: in shared memory)
 };
 
-// n: rows of a block matrix (k^2 in the paper's layout, 2 k^2 stacked)
+// n: rows of a block matrix (k^2 in the paper's layout, 2 k^2 stacked).  Above
+// kMaxSmemRows rows the two n x n buffers x1, x2 are offsets into the CTA's
+// global rows instead of shared memory.
 __host__ __device__ inline Layout layout(int n, int pg) {
   Layout L;
   L.n = n;
@@ -98,7 +106,9 @@ __host__ __device__ inline Layout layout(int n, int pg) {
   L.cs = kCW + 4;
   L.x1 = 0;
   L.x2 = L.x1 + (size_t)w * L.gs;
-  L.chunk = L.x2 + (size_t)w * L.gs;
+  const bool glb = n > kMaxSmemRows;
+  L.rows = glb ? L.x2 + (size_t)w * L.gs : 0;
+  L.chunk = glb ? 0 : L.x2 + (size_t)w * L.gs;
   L.nrm = L.chunk + (size_t)w * L.cs;
   L.pix = L.nrm + w;
   L.last = L.pix + w;
@@ -183,6 +193,9 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
   constexpr int NR = ST ? 2 * K * K : K * K;            // rows of a block matrix
   constexpr int NT4 = (((NR + 1) & ~1) + 3) / 4;
   constexpr int GT = (NT4 * (NT4 + 1) / 2 + LT - 1) / LT;  // upper-triangle Gram tiles per thread
+  // tiles a thread accumulates per pass over the chunks (more passes above 3)
+  constexpr int GTP = GT > 3 ? 3 : GT, NPASS = (GT + GTP - 1) / GTP;
+  constexpr int SL = (NR + 31) / 32;                   // row elements a lane holds
   constexpr int PG = pair_lanes(NR, LW);               // lanes per row pair in the Jacobi
   constexpr int PE2 = (NR + 2 * PG - 1) / (2 * PG);    // float2 pieces of a row a Jacobi lane holds
   // skip Jacobi pairs whose rows are unchanged since they last met: pays from
@@ -195,7 +208,8 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
   if (a.sc->done) return;
   const Layout L = layout(NR, PG);
   const int n = L.n, NP = L.npos, GS = L.gs, nt4 = L.nt4;
-  float *X1 = sm + L.x1, *X2 = sm + L.x2, *chunk = sm + L.chunk, *nrm = sm + L.nrm;
+  float *rb = L.rows ? a.rows + (size_t)blockIdx.x * L.rows : sm;  // where the n x n buffers live
+  float *X1 = rb + L.x1, *X2 = rb + L.x2, *chunk = sm + L.chunk, *nrm = sm + L.nrm;
   int *pix = reinterpret_cast<int *>(sm + L.pix);
   int *last = reinterpret_cast<int *>(sm + L.last);  // the last sweep that rotated each Jacobi row
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -219,18 +233,21 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
     }
     __syncthreads();
 
-    // ---- 1. Gram of Y', streamed by column chunks ----
-    float acc[GT][16];
+    // ---- 1. Gram of Y', streamed by column chunks (Y' = Y + gamma_Y F is
+    // formed and written back on the first of the NPASS passes; each pass
+    // accumulates GTP of a thread's GT upper-triangle tiles) ----
+    for (int ps = 0; ps < NPASS; ++ps) {
+    float acc[GTP][16];
 #pragma unroll
-    for (int u = 0; u < GT; ++u)
+    for (int u = 0; u < GTP; ++u)
 #pragma unroll
       for (int e = 0; e < 16; ++e) acc[u][e] = 0.f;
     for (int c0 = 0; c0 < W; c0 += kCW) {
-      stream_chunk<ST, LT, PARTS>(L, chunk, Yl, a, pix, c0, true);
+      stream_chunk<ST, LT, PARTS>(L, chunk, Yl, a, pix, c0, ps == 0);
       __syncthreads();
 #pragma unroll
-      for (int u = 0; u < GT; ++u) {
-        const int t = tid + u * LT;
+      for (int u = 0; u < GTP; ++u) {
+        const int t = tid + (ps * GTP + u) * LT;
         if (t < n_upper) {
           int ti, tj;
           upper_tile(t, nt4, ti, tj);
@@ -266,8 +283,8 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
       __syncthreads();
     }
 #pragma unroll
-    for (int u = 0; u < GT; ++u) {
-      const int t = tid + u * LT;
+    for (int u = 0; u < GTP; ++u) {
+      const int t = tid + (ps * GTP + u) * LT;
       if (t < n_upper) {
         int ti, tj;
         upper_tile(t, nt4, ti, tj);
@@ -281,6 +298,7 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
           }
       }
     }
+    }  // passes
     __syncthreads();
 
     // ---- 2. C0 = W G (warm) or G (cold), rows of C into X2 ----
@@ -291,11 +309,11 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
     for (int r0 = warp; r0 < NP; r0 += 2 * LW) {
       const int r1 = r0 + LW;
       const bool two = r1 < NP;
-      float acc0[kSlots], acc1[kSlots];
+      float acc0[SL], acc1[SL];
       if (warm) {
-        float w0[kSlots], w1[kSlots];  // lane j holds W[r][j + 32 i]
+        float w0[SL], w1[SL];  // lane j holds W[r][j + 32 i]
 #pragma unroll
-        for (int i = 0; i < kSlots; ++i) {
+        for (int i = 0; i < SL; ++i) {
           const int c = lane + 32 * i;
           w0[i] = c < n ? __ldg(Wl + (size_t)r0 * n + c) : 0.f;
           w1[i] = two && c < n ? __ldg(Wl + (size_t)r1 * n + c) : 0.f;
@@ -303,12 +321,12 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
           acc1[i] = 0.f;
         }
 #pragma unroll
-        for (int kb = 0; kb < kSlots; ++kb) {
+        for (int kb = 0; kb < SL; ++kb) {
           for (int j = 0; j < 32 && kb * 32 + j < n; ++j) {
             const float wa = __shfl_sync(kFull, w0[kb], j), wb = __shfl_sync(kFull, w1[kb], j);
             const float *g = X1 + (size_t)(kb * 32 + j) * GS;
 #pragma unroll
-            for (int i = 0; i < kSlots; ++i) {
+            for (int i = 0; i < SL; ++i) {
               const int c = lane + 32 * i;
               if (c < n) {
                 const float gv = g[c];
@@ -320,14 +338,14 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
         }
       } else {
 #pragma unroll
-        for (int i = 0; i < kSlots; ++i) {
+        for (int i = 0; i < SL; ++i) {
           const int c = lane + 32 * i;
           acc0[i] = r0 < n && c < n ? X1[(size_t)r0 * GS + c] : 0.f;
           acc1[i] = r1 < n && c < n ? X1[(size_t)r1 * GS + c] : 0.f;
         }
       }
 #pragma unroll
-      for (int i = 0; i < kSlots; ++i) {
+      for (int i = 0; i < SL; ++i) {
         const int c = lane + 32 * i;
         if (c < GS) {
           X2[(size_t)r0 * GS + c] = c < n ? acc0[i] : 0.f;
@@ -622,6 +640,11 @@ size_t block_dual_large_smem_bytes(int k, bool stacked, int parts) {
   return sizeof(float) * layout(n, pair_lanes(n, block_dual_large_threads(k, stacked, parts) / 32)).total;
 }
 
+size_t block_dual_large_rows_floats(int k, bool stacked, int parts) {
+  const int n = stacked ? 2 * k * k : k * k;
+  return layout(n, pair_lanes(n, block_dual_large_threads(k, stacked, parts) / 32)).rows;
+}
+
 long long block_dual_large_w_stride(int k, bool stacked) {
   const Layout L = layout(stacked ? 2 * k * k : k * k, 8);  // npos and n only
   return ((long long)L.npos * L.n + 3) / 4 * 4;
@@ -639,7 +662,9 @@ LargeKernel large_kernel(int k, bool stacked, int parts) {
   static const LargeKernel paper[] = {block_dual_large_kernel<6, false, 2>,  block_dual_large_kernel<7, false, 2>,
                                       block_dual_large_kernel<8, false, 2>,  block_dual_large_kernel<9, false, 2>,
                                       block_dual_large_kernel<10, false, 2>, block_dual_large_kernel<11, false, 2>,
-                                      block_dual_large_kernel<12, false, 2>};
+                                      block_dual_large_kernel<12, false, 2>, block_dual_large_kernel<13, false, 2>,
+                                      block_dual_large_kernel<14, false, 2>, block_dual_large_kernel<15, false, 2>,
+                                      block_dual_large_kernel<16, false, 2>};
   static const LargeKernel stack[] = {block_dual_large_kernel<1, true, 2>, block_dual_large_kernel<2, true, 2>,
                                       block_dual_large_kernel<3, true, 2>, block_dual_large_kernel<4, true, 2>,
                                       block_dual_large_kernel<5, true, 2>, block_dual_large_kernel<6, true, 2>,
@@ -678,6 +703,8 @@ cudaError_t launch_block_dual_large(const BlockDualArgs &a, int k, bool stacked,
                                     cudaStream_t st, int parts) {
   const LargeKernel f = large_kernel(k, stacked, parts);
   if (!f) return cudaErrorInvalidValue;
+  const size_t rows = block_dual_large_rows_floats(k, stacked, parts);
+  if (rows && (!a.rows || rows * (size_t)grid > a.rows_cap)) return cudaErrorInvalidValue;
   f<<<grid, block_dual_large_threads(k, stacked, parts), smem, st>>>(a);
   return cudaGetLastError();
 }

@@ -145,6 +145,11 @@ struct BlockDualArgs {
   // null: no queue, such blocks are applied as they stand
   int *fb_list = nullptr;
   int fb_cap = 0;
+  // blocks above kMaxSmemRows rows: the per-CTA global rows of the two n x n
+  // matrices (block_dual_large_rows_floats() floats per CTA of the grid);
+  // rows_cap floats in all (the launcher refuses a grid they do not cover)
+  float *rows = nullptr;
+  size_t rows_cap = 0;
 };
 // floats per block of the warm-start rows
 long long block_dual_w_stride(int k);
@@ -183,14 +188,17 @@ bool block_dual_has(const BdVariant &v);  // this variant is compiled into the l
 // block_dual_large_threads() threads per block at a time, FP32 CUDA cores.
 // The same kernel also runs the stacked layout (2 k^2 rows of N3 bands, rows 2r
 // and 2r + 1 the vertical and horizontal differences of window pixel r) for
-// k = 1..kMaxStackedK; the block memory [L][k^2][2][N3p] is the same.
-constexpr int kMinLargeK = 6, kMaxLargeK = 12, kMaxStackedK = 8;
+// k = 1..kMaxStackedK; the block memory [L][k^2][2][N3p] is the same.  Blocks
+// of more than kMaxSmemRows rows (k = 13..16) keep their two n x n matrices in a
+// global scratch of block_dual_large_rows_floats() floats per CTA (L2-resident).
+constexpr int kMinLargeK = 6, kMaxLargeK = 16, kMaxStackedK = 8, kMaxSmemRows = 144;
 constexpr int kMaxSmallK = kMinLargeK - 1;  // the k <= 5 kernels (block_dual.cu)
 // parts = 3: SSST's rows [D_v u, D_h u, D_s u] (paper layout, k <= kMaxStackedK)
 size_t block_dual_large_smem_bytes(int k, bool stacked, int parts = 2);
 long long block_dual_large_w_stride(int k, bool stacked);
 long long block_dual_large_w_stride(int k);  // paper layout
 int block_dual_large_threads(int k, bool stacked, int parts = 2);
+size_t block_dual_large_rows_floats(int k, bool stacked, int parts = 2);
 cudaError_t block_dual_large_prepare(int k, bool stacked, size_t smem_bytes, int parts = 2);
 cudaError_t block_dual_large_occupancy(int k, bool stacked, size_t smem_bytes, int *ctas_per_sm, int parts = 2);
 cudaError_t launch_block_dual_large(const BlockDualArgs &a, int k, bool stacked, int grid, size_t smem,

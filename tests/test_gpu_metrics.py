@@ -69,3 +69,14 @@ def test_quality_host_buffers_and_identity(solver):
     q = solver.quality(ref, ref.copy(), trim=1, sam_map=True)
     assert q["mpsnr"] == float("inf") and q["mssim"] == pytest.approx(1.0, abs=1e-12) and q["sam"] < 1e-6
     assert isinstance(q["sam_map"], np.ndarray) and q["sam_map"].shape == (12, 12)
+
+
+def test_objective_refuses_blocks_above_12(solver):
+    """The solver takes k = 13..16; the FP64 objective keeps each block's
+    k^2 x k^2 Gram in shared memory and refuses those sizes with a status."""
+    import paper_2404_03313_gb300 as P
+    u = np.random.default_rng(3).uniform(0, 1, (14, 14, 4)).astype(np.float32)
+    with pytest.raises(P.S3TTVError) as e:
+        solver.objective(torch.from_numpy(u).cuda(), 13)
+    assert e.value.status == P.EUNSUPPORTED
+    assert solver.objective(u, 2) > 0.0  # the context stays usable
