@@ -64,6 +64,7 @@
 // -1 / (sqrt(a) sqrt(b) (sqrt(a) + sqrt(b))) above the kink, and
 // -(x - 1) / (sqrt(x) (1 + sqrt(x)) (x - y)) across it (x > 1 >= y).
 #include <math.h>
+#include <type_traits>
 #include "s3ttv_internal.cuh"
 
 namespace s3ttv {
@@ -255,12 +256,24 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], unsigned a0, unsigned a1
 }
 // d += A B with both operands split hi + lo: lo*hi + hi*lo + hi*hi (the lo*lo
 // term, below 2^-20 of the product, is dropped), so the tile product keeps
-// FP32-level accuracy (a few 2^-20 relative).
-__device__ __forceinline__ void mma_3xtf32(float (&d)[4], const unsigned (&ah)[4], const unsigned (&al)[4],
-                                           unsigned bh0, unsigned bh1, unsigned bl0, unsigned bl1) {
-  mma_tf32(d, al[0], al[1], al[2], al[3], bh0, bh1);
-  mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bl0, bl1);
-  mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+// FP32-level accuracy (a few 2^-20 relative).  Product p of the three (0: lo*hi,
+// 1: hi*lo, 2: hi*hi), in that order on every accumulator.  The call sites run
+// p as their outermost loop over independent tiles, so consecutive products on
+// one accumulator are several instructions apart instead of waiting out each
+// other's latency (the same sums in the same order).
+template <int p>
+__device__ __forceinline__ void mma_3xtf32_part(float (&d)[4], const unsigned (&ah)[4], const unsigned (&al)[4],
+                                                unsigned bh0, unsigned bh1, unsigned bl0, unsigned bl1) {
+  if constexpr (p == 0) mma_tf32(d, al[0], al[1], al[2], al[3], bh0, bh1);
+  else if constexpr (p == 1) mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+  else mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+}
+// F(integral_constant<int, p>) for p = 0, 1, 2
+template <class F>
+__device__ __forceinline__ void three_parts(const F &f) {
+  f(std::integral_constant<int, 0>());
+  f(std::integral_constant<int, 1>());
+  f(std::integral_constant<int, 2>());
 }
 
 // One warp: one-sided Jacobi on the rows of G (or of W G, Ws being a shared
@@ -577,19 +590,22 @@ __device__ __forceinline__ void mm32(const FA &A, const FB &B, float (&d)[2][4][
         const int k = 8 * kk + t + 4 * h, j = 8 * q + g;
         split_tf32((8 * q < NC && k < KD && j < NC) ? B(k, j) : 0.f, bh[q][h], bl[q][h]);
       }
+    unsigned ah[2][4], al[2][4];
 #pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      if (16 * m >= MR) continue;
-      unsigned ah[4], al[4];
+    for (int m = 0; m < 2; ++m)
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int i = 16 * m + g + 8 * (e & 1), k = 8 * kk + t + 4 * (e >> 1);
-        split_tf32((i < MR && k < KD) ? A(i, k) : 0.f, ah[e], al[e]);
+        split_tf32((16 * m < MR && i < MR && k < KD) ? A(i, k) : 0.f, ah[m][e], al[m][e]);
       }
+    three_parts([&](auto P) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (8 * q < NC) mma_3xtf32(d[m][q], ah, al, bh[q][0], bh[q][1], bl[q][0], bl[q][1]);
-    }
+      for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (16 * m < MR && 8 * q < NC)
+            mma_3xtf32_part<decltype(P)::value>(d[m][q], ah[m], al[m], bh[q][0], bh[q][1], bl[q][0], bl[q][1]);
+    });
   }
 }
 
@@ -791,18 +807,19 @@ __device__ void gram_mma(const float *Yp, int RS, int C4, float *Part, float *Gb
           split_tf32(x, xh[q][h], xl[q][h]);
         }
       }
-    int idx = 0;
+    const unsigned ah[2][4] = {{xh[0][0], xh[1][0], xh[0][1], xh[1][1]}, {xh[2][0], xh[3][0], xh[2][1], xh[3][1]}};
+    const unsigned al[2][4] = {{xl[0][0], xl[1][0], xl[0][1], xl[1][1]}, {xl[2][0], xl[3][0], xl[2][1], xl[3][1]}};
+    three_parts([&](auto P) {
+      int idx = 0;
 #pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      const unsigned ah[4] = {xh[2 * m][0], xh[2 * m + 1][0], xh[2 * m][1], xh[2 * m + 1][1]};
-      const unsigned al[4] = {xl[2 * m][0], xl[2 * m + 1][0], xl[2 * m][1], xl[2 * m + 1][1]};
+      for (int m = 0; m < 2; ++m)
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (T::need(m, q)) {
-          mma_3xtf32(acc[idx], ah, al, xh[q][0], xh[q][1], xl[q][0], xl[q][1]);
-          ++idx;
-        }
-    }
+        for (int q = 0; q < 4; ++q)
+          if (T::need(m, q)) {
+            mma_3xtf32_part<decltype(P)::value>(acc[idx], ah[m], al[m], xh[q][0], xh[q][1], xl[q][0], xl[q][1]);
+            ++idx;
+          }
+    });
   }
   float *P2 = Part, *P3 = Part + NTILE * 128;
   __syncthreads();  // the partials take the place of Y', which every warp has read
@@ -906,10 +923,14 @@ __device__ void apply_mma(float *Yp, int RS2, int C4, const float *Mg) {
         split_tf32(in && s0 < S0 ? col[(size_t)s0 * RS2] : 0.f, bh[u][0], bl[u][0]);
         split_tf32(in && s1 < S0 ? col[(size_t)s1 * RS2] : 0.f, bh[u][1], bl[u][1]);
       }
+      three_parts([&](auto P) {
 #pragma unroll
-      for (int m = 0; m < NM; ++m)
+        for (int m = 0; m < NM; ++m)
 #pragma unroll
-        for (int u = 0; u < 2; ++u) mma_3xtf32(d[u][m], mh[m][kk], ml[m][kk], bh[u][0], bh[u][1], bl[u][0], bl[u][1]);
+          for (int u = 0; u < 2; ++u)
+            mma_3xtf32_part<decltype(P)::value>(d[u][m], mh[m][kk], ml[m][kk], bh[u][0], bh[u][1], bl[u][0],
+                                                bl[u][1]);
+      });
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
@@ -1424,18 +1445,19 @@ __device__ void stream_block(const BlockDualArgs &a, long long l, float *bufs, u
               split_tf32(row < n ? cur[row * kCS + 8 * ks + t + 4 * h] : 0.f, xh[q][h], xl[q][h]);
             }
           }
-        int idx = 0;
+        const unsigned ah[2][4] = {{xh[0][0], xh[1][0], xh[0][1], xh[1][1]}, {xh[2][0], xh[3][0], xh[2][1], xh[3][1]}};
+        const unsigned al[2][4] = {{xl[0][0], xl[1][0], xl[0][1], xl[1][1]}, {xl[2][0], xl[3][0], xl[2][1], xl[3][1]}};
+        three_parts([&](auto P) {
+          int idx = 0;
 #pragma unroll
-        for (int m = 0; m < 2; ++m) {
-          const unsigned ah[4] = {xh[2 * m][0], xh[2 * m + 1][0], xh[2 * m][1], xh[2 * m + 1][1]};
-          const unsigned al[4] = {xl[2 * m][0], xl[2 * m + 1][0], xl[2 * m][1], xl[2 * m + 1][1]};
+          for (int m = 0; m < 2; ++m)
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (T::need(m, q)) {
-              mma_3xtf32(acc[idx], ah, al, xh[q][0], xh[q][1], xl[q][0], xl[q][1]);
-              ++idx;
-            }
-        }
+            for (int q = 0; q < 4; ++q)
+              if (T::need(m, q)) {
+                mma_3xtf32_part<decltype(P)::value>(acc[idx], ah[m], al[m], xh[q][0], xh[q][1], xl[q][0], xl[q][1]);
+                ++idx;
+              }
+        });
       }
       __syncwarp();  // every lane has read this buffer before it is refilled
     }
@@ -1557,11 +1579,14 @@ __device__ void stream_block(const BlockDualArgs &a, long long l, float *bufs, u
             split_tf32(in && s0 < S0 ? col[s0 * kCS] : 0.f, bh[u][0], bl[u][0]);
             split_tf32(in && s1 < S0 ? col[s1 * kCS] : 0.f, bh[u][1], bl[u][1]);
           }
+          three_parts([&](auto P) {
 #pragma unroll
-          for (int m = 0; m < NM; ++m)
+            for (int m = 0; m < NM; ++m)
 #pragma unroll
-            for (int u = 0; u < 2; ++u)
-              mma_3xtf32(d[u][m], mh[m][kk], ml[m][kk], bh[u][0], bh[u][1], bl[u][0], bl[u][1]);
+              for (int u = 0; u < 2; ++u)
+                mma_3xtf32_part<decltype(P)::value>(d[u][m], mh[m][kk], ml[m][kk], bh[u][0], bh[u][1], bl[u][0],
+                                                    bl[u][1]);
+          });
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
