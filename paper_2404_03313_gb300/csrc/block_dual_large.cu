@@ -499,57 +499,174 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
     __syncthreads();
 
     // ---- 4b. the warm rows W: the eigenvectors completed to an orthonormal basis ----
-    // Rows below the numerical-zero floor carry no reliable direction.  Each is
-    // replaced by a unit vector e_j orthogonalized (classical Gram-Schmidt,
-    // twice) against every unit row so far, taking the first j whose remainder
-    // keeps more than 1 / (2 n) of its squared norm (the largest remainder is
-    // at least 1 / n while the rows span less than R^n).  The next pass starts
-    // from this complete basis; a block is marked cold only if that fails.
+    // Rows below the numerical-zero floor carry no reliable direction; each
+    // needs a unit vector that completes the converged rows to an orthonormal
+    // basis.  A warm pass takes the block's stored W rows at those positions
+    // and finishes with Jacobi sweeps over the same round-robin ordering with
+    // the converged rows frozen: a pair of a frozen row and a candidate
+    // projects the candidate off the frozen row, two candidates rotate as in
+    // step 3, two frozen rows are skipped (the eigen-rows, and so M, are those
+    // of step 3).  The rank deficiency is often structural and the same every
+    // pass (the stacked blocks of k x k windows have the (k - 1)^2 discrete
+    // curl relations of their vertical and horizontal differences), so the
+    // stored rows already complete the basis.  A cold pass, a candidate left
+    // with no more than 1 / (2 n) of its squared norm, or sweeps that do not
+    // converge fall back to Gram-Schmidt: each missing row is the first unit
+    // vector e_j whose remainder against every unit row so far (classical
+    // Gram-Schmidt, twice) keeps more than 1 / (2 n) of its squared norm (the
+    // largest remainder is at least 1 / n while the rows span less than R^n).
+    // The block is marked cold only if that fails too.
     if (a.W) {
       float *xv = chunk, *coef = chunk + GS;  // the chunk is free until the apply
+      int below = 0;
+      for (int r = tid; r < n; r += LT) below |= nrm[r] <= floor2 ? 1 : 0;
       bool cold = false;
-      int next_e = 0;
-      for (int r = 0; r < n && !cold; ++r) {
-        if (nrm[r] > floor2) continue;  // block-uniform: shared memory read after a barrier
-        bool placed = false;
-        while (!placed && next_e < n) {
-          const int j = next_e++;
-          for (int c = tid; c < n; c += LT) xv[c] = c == j ? 1.f : 0.f;
+      if (__syncthreads_or(below)) {  // block-uniform
+        for (int r = tid; r < NP; r += LT) last[r] = r >= n || nrm[r] > floor2 ? 1 : 0;
+        __syncthreads();
+        bool ok = false;
+        if (warm) {
+          for (int r = warp; r < NP; r += LW)
+            if (!last[r])
+              for (int c = lane; c < GS; c += 32) X2[(size_t)r * GS + c] = c < n ? __ldg(Wl + (size_t)r * n + c) : 0.f;
           __syncthreads();
-          for (int pass = 0; pass < 2; ++pass) {
-            for (int s2 = warp; s2 < n; s2 += LW) {
-              float d = 0.f;
-              if (nrm[s2] > floor2)
-                for (int c = lane; c < n; c += 32) d = fmaf(X2[(size_t)s2 * GS + c], xv[c], d);
+          norms();  // frozen rows 1 (0 for a padding row), candidates their own
+          bool done = false;
+          for (int sw = 0; sw < a.max_sweeps && !done; ++sw) {
+            if (sw) norms();
+            int rotated = 0;
+            for (int step = 0; step < NP - 1; ++step) {
+              for (int base = 0; base < NP / 2; base += LW * (32 / PG)) {
+                if (base + warp * (32 / PG) >= NP / 2) continue;
+                const int i = base + warp * (32 / PG) + (lane / PG), gl = lane % PG;
+                const bool act = i < NP / 2;
+                const int pa = act ? i : 0, pb = NP - 1 - pa;
+                int xa = pa - 1 + step, xb = pb - 1 + step;
+                xa -= xa >= NP - 1 ? NP - 1 : 0;
+                xb -= xb >= NP - 1 ? NP - 1 : 0;
+                const int ra = pa == 0 ? 0 : 1 + xa, rb = 1 + xb;
+                const int fa = act ? last[ra] : 1, fb = act ? last[rb] : 1;
+                const bool chk = !(fa && fb);
+                if (!__any_sync(kFull, chk)) continue;  // warp-uniform
+                float *A = X2 + (size_t)ra * GS, *B = X2 + (size_t)rb * GS;
+                f32x2 va[PE2], vb[PE2];
+                f32x2 dd = 0ull;
 #pragma unroll
-              for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
-              if (lane == 0) coef[s2] = d;
-            }
-            __syncthreads();
-            for (int c = tid; c < n; c += LT) {
-              float x = xv[c];
-              for (int s2 = 0; s2 < n; ++s2) x = fmaf(-coef[s2], X2[(size_t)s2 * GS + c], x);
-              xv[c] = x;
-            }
-            __syncthreads();
-          }
-          float q = 0.f;
-          for (int c = tid; c < n; c += LT) q = fmaf(xv[c], xv[c], q);
+                for (int e = 0; e < PE2; ++e) {
+                  const int c = 2 * gl + 2 * PG * e;
+                  const bool in = chk && c < n;
+                  va[e] = in ? *reinterpret_cast<const f32x2 *>(A + c) : 0ull;
+                  vb[e] = in ? *reinterpret_cast<const f32x2 *>(B + c) : 0ull;
+                  dd = fma2(va[e], vb[e], dd);
+                }
+                const float2 d2 = up2(dd);
+                float d = d2.x + d2.y;
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(kFull, q, o);
-          if (lane == 0) s_red[warp] = q;
-          __syncthreads();
-          q = 0.f;
-          for (int w = 0; w < LW; ++w) q += s_red[w];
-          if (q * (float)(2 * n) > 1.f) {
-            const float iq = rsqrtf(q);
-            for (int c = tid; c < GS; c += LT) X2[(size_t)r * GS + c] = c < n ? xv[c] * iq : 0.f;
-            if (tid == 0) nrm[r] = 1.f;  // a unit row from now on
-            placed = true;
+                for (int o = PG / 2; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
+                const float nA = chk ? nrm[ra] : 0.f, nB = chk ? nrm[rb] : 0.f;
+                if (chk && fminf(nA, nB) > 1e-12f && d * d > pol2 * nA * nB) {
+                  if (fa || fb) {  // the candidate minus its component along the frozen row
+                    float *Cr = fa ? B : A;
+                    const float nf = fa ? nA : nB, m = -d / nf;
+                    const f32x2 m2 = pk2(m, m);
+#pragma unroll
+                    for (int e = 0; e < PE2; ++e) {
+                      const int c = 2 * gl + 2 * PG * e;
+                      if (c < n) *reinterpret_cast<f32x2 *>(Cr + c) = fa ? fma2(m2, va[e], vb[e]) : fma2(m2, vb[e], va[e]);
+                    }
+                    if (gl == 0) nrm[fa ? rb : ra] = (fa ? nB : nA) + m * d;
+                  } else {
+                    const float x = nB - nA, y = 2.f * d;
+                    const float rr = rsqrtf(fmaf(x, x, y * y));
+                    const float hc = fmaf(0.5f * fabsf(x), rr, 0.5f);
+                    const float rc = rsqrtf(hc);
+                    const float cs = hc * rc, sn = copysignf(0.5f, x) * y * rr * rc;
+                    const float dn = sn * rc * d;
+                    const f32x2 cs2 = pk2(cs, cs), sn2 = pk2(sn, sn), ns2 = pk2(-sn, -sn);
+#pragma unroll
+                    for (int e = 0; e < PE2; ++e) {
+                      const int c = 2 * gl + 2 * PG * e;
+                      if (c < n) {
+                        *reinterpret_cast<f32x2 *>(A + c) = fma2(cs2, va[e], mul2(ns2, vb[e]));
+                        *reinterpret_cast<f32x2 *>(B + c) = fma2(sn2, va[e], mul2(cs2, vb[e]));
+                      }
+                    }
+                    if (gl == 0) {
+                      nrm[ra] = nA - dn;
+                      nrm[rb] = nB + dn;
+                    }
+                  }
+                  if (d * d > tol2 * nA * nB) rotated = 1;
+                }
+              }
+              __syncthreads();
+            }
+            done = !__syncthreads_or(rotated);
           }
-          __syncthreads();
+          norms();
+          ok = done;  // block-uniform: every thread reads the same norms after the barrier
+          for (int r = 0; r < n; ++r)
+            if (!last[r] && nrm[r] * (float)(2 * n) <= 1.f) ok = false;
+          if (ok) {
+            for (int r = warp; r < n; r += LW) {
+              if (last[r]) continue;
+              const float sc = rsqrtf(nrm[r]);
+              for (int c = lane; c < n; c += 32) X2[(size_t)r * GS + c] *= sc;
+            }
+          }
         }
-        if (!placed) cold = true;
+        if (!ok) {  // Gram-Schmidt from unit vectors: missing rows zero, unit rows marked by nrm
+          for (int r = warp; r < NP; r += LW) {
+            if (!last[r])
+              for (int c = lane; c < GS; c += 32) X2[(size_t)r * GS + c] = 0.f;
+            if (lane == 0) nrm[r] = last[r] && r < n ? 1.f : 0.f;
+          }
+          __syncthreads();
+          int next_e = 0;
+          for (int r = 0; r < n && !cold; ++r) {
+            if (nrm[r] > floor2) continue;  // block-uniform: shared memory read after a barrier
+            bool placed = false;
+            while (!placed && next_e < n) {
+              const int j = next_e++;
+              for (int c = tid; c < n; c += LT) xv[c] = c == j ? 1.f : 0.f;
+              __syncthreads();
+              for (int pass = 0; pass < 2; ++pass) {
+                for (int s2 = warp; s2 < n; s2 += LW) {
+                  float d = 0.f;
+                  if (nrm[s2] > floor2)
+                    for (int c = lane; c < n; c += 32) d = fmaf(X2[(size_t)s2 * GS + c], xv[c], d);
+#pragma unroll
+                  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
+                  if (lane == 0) coef[s2] = d;
+                }
+                __syncthreads();
+                for (int c = tid; c < n; c += LT) {
+                  float x = xv[c];
+                  for (int s2 = 0; s2 < n; ++s2) x = fmaf(-coef[s2], X2[(size_t)s2 * GS + c], x);
+                  xv[c] = x;
+                }
+                __syncthreads();
+              }
+              float q = 0.f;
+              for (int c = tid; c < n; c += LT) q = fmaf(xv[c], xv[c], q);
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(kFull, q, o);
+              if (lane == 0) s_red[warp] = q;
+              __syncthreads();
+              q = 0.f;
+              for (int w = 0; w < LW; ++w) q += s_red[w];
+              if (q * (float)(2 * n) > 1.f) {
+                const float iq = rsqrtf(q);
+                for (int c = tid; c < GS; c += LT) X2[(size_t)r * GS + c] = c < n ? xv[c] * iq : 0.f;
+                if (tid == 0) nrm[r] = 1.f;  // a unit row from now on
+                placed = true;
+              }
+              __syncthreads();
+            }
+            if (!placed) cold = true;
+          }
+        }
+        __syncthreads();
       }
       if (!cold) {
         for (int r = warp; r < NP; r += LW) {
@@ -557,7 +674,7 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
           for (int c = lane; c < n; c += 32) ww[c] = X2[(size_t)r * GS + c];
         }
       }
-      __syncthreads();  // every W row written before the marker may overwrite W[0]
+      __syncthreads();  // every W row written (and X2 read) before the marker and before M takes X2's place
       if (cold && tid == 0) a.W[(size_t)l * a.w_stride] = __int_as_float(0x7fc00000);
     }
 
