@@ -88,7 +88,9 @@ enum {
   S3TTV_OPT_STEP_POLICY = 1,       /* S3TTV_STEP_PAPER (default) or S3TTV_STEP_PC_EXACT  */
   S3TTV_OPT_CHECK_EVERY = 2,       /* passes between host reads of the stop flag (default 16) */
   S3TTV_OPT_JACOBI_MAX_SWEEPS = 3, /* sweep cap of the block eigen-solve (default 24, 1..64) */
-  S3TTV_OPT_JACOBI_TOL = 4,        /* relative orthogonality tolerance (default 2e-6)    */
+  S3TTV_OPT_JACOBI_TOL = 4,        /* relative orthogonality tolerance: a sweep of a
+                                      block eigen-solve in which no pair of rows was
+                                      less orthogonal ends the solve (default 1e-4)       */
   S3TTV_OPT_PROFILE = 5,           /* 1: time each kernel class of every pass with CUDA
                                       events on the context stream (resets the totals);
                                       0: off (default)                                    */
@@ -142,12 +144,13 @@ enum {
                                       profilers; 0 (default): none                        */
   S3TTV_OPT_JACOBI_POLISH_TOL = 16, /* relative orthogonality below which a pair of rows
                                       of the block eigen-solve is left as it is (0 <
-                                      value <= S3TTV_OPT_JACOBI_TOL).  Pairs between the
-                                      two are rotated, but only a pair above the
-                                      tolerance makes the solve run another sweep, so the
-                                      last sweep polishes the eigenvectors without the
-                                      FP32 rounding floor deciding convergence.  0
-                                      (default): tolerance / 8                         */
+                                      value <= S3TTV_OPT_JACOBI_TOL).  Every sweep
+                                      rotates the pairs above it, but only a pair above
+                                      the tolerance makes the solve run another sweep:
+                                      a last sweep whose rotations stay below the
+                                      tolerance tau moves a pair it already met by about
+                                      n tau^2 at most.  0 (default): 2.5e-7, near the
+                                      FP32 rounding of a row pair's dot product        */
   S3TTV_OPT_FIRST_ORDER = 17,      /* k <= 5, paper layout: a block whose stored
                                       eigen-rows W still nearly diagonalise this pass's
                                       Gram G takes its clip from the first-order

@@ -25,8 +25,8 @@ struct s3ttv_ctx {
   int step_policy = S3TTV_STEP_PAPER;
   int check_every = 16;
   int jacobi_max_sweeps = 24;
-  float jacobi_tol = 2e-6f;
-  float jacobi_polish = 0.f;  // 0: the default, tol / 8 (jacobi_polish_for)
+  float jacobi_tol = 1e-4f;   // a sweep with no pair above it ends an eigen-solve
+  float jacobi_polish = 0.f;  // 0: the default, kDefaultPolish (jacobi_polish_for)
   float first_order = 0.f;  // remainder bound of the first-order clip (0: off, the default)
   int batch_worklist = 0;    // batched solves: 1, one block-dual work list per block side
   int tensor_cores = 2;  // block-dual form: 2 streaming (tensor cores), 1 group (tensor cores), 0 CUDA cores
@@ -321,12 +321,17 @@ Dims make_dims(int N1, int N2, int N3) {
 }
 
 // The polish threshold of the block eigen-solves (S3TTV_OPT_JACOBI_POLISH_TOL):
-// the option's value, at most the tolerance; by default tol / 8 (per-operator
-// errors below 1e-5 up to k = 10 at 200 columns, and fewer sweeps: pairs just
-// above the tolerance no longer need a sweep of their own).
+// the option's value, at most the tolerance; by default 2.5e-7, near the FP32
+// rounding of a row pair's dot product.  Every sweep rotates each pair above
+// it; only a pair above the tolerance makes the solve run another sweep.  A
+// last sweep whose rotations all stay below the tolerance tau changes a pair
+// it already met by at most about n tau^2 (2.6e-6 at tau = 1e-4, n = 256), so
+// the default tolerance 1e-4 leaves the per-operator errors as they were at
+// tau = 2e-6 (measured on GB300 for k = 5..16) with one sweep fewer.
+constexpr float kDefaultPolish = 2.5e-7f;
 float jacobi_polish_for(const s3ttv_ctx *ctx) {
   const float tol = ctx->jacobi_tol;
-  const float p = ctx->jacobi_polish > 0.f ? ctx->jacobi_polish : tol * 0.125f;
+  const float p = ctx->jacobi_polish > 0.f ? ctx->jacobi_polish : kDefaultPolish;
   return p < tol ? p : tol;
 }
 

@@ -177,6 +177,26 @@ __device__ void stream_chunk(const Layout &L, float *chunk, float *Yl, const Blo
   }
 }
 
+// Column tiles of 8 per unit of the apply's tensor-core loop (a unit: one
+// 16-row block of the result over QPU tiles of a chunk of QT tiles, its M
+// fragments loaded once per k-step): the largest divisor of QT whose units
+// fill the warps' rounds best.
+__host__ __device__ constexpr int apply_qpu(int mt, int qt, int lw) {
+  int best = 1, best_num = 0, best_den = 1;
+  const int cand[4] = {6, 3, 2, 1};
+  for (int i = 0; i < 4; ++i) {
+    const int q = cand[i];
+    if (qt % q) continue;
+    const int units = mt * (qt / q), rounds = (units + lw - 1) / lw;
+    if ((long long)units * best_den > (long long)best_num * rounds * lw) {  // strictly better filled
+      best = q;
+      best_num = units;
+      best_den = rounds * lw;
+    }
+  }
+  return best;
+}
+
 // warps per CTA: stacked blocks of up to 64 rows (k <= 5) run four-warp CTAs,
 // four per SM; everything else eight-warp CTAs, two per SM
 template <int K, bool ST, int PARTS>
@@ -708,44 +728,130 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
     }
     __syncthreads();
 
-    // ---- 5b. Y_l = M Y' by chunks; Z += P_l^T Y_l ----
-    for (int c0 = 0; c0 < W; c0 += kCW) {
-      stream_chunk<ST, LT, PARTS>(L, chunk, Yl, a, pix, c0, false);
-      __syncthreads();
-      constexpr int Q = kCW / 4;
-      for (int t = tid; t < nt4 * Q; t += LT) {
-        const int ti = t / Q, q = t - ti * Q;
-        float4 y[4];
+    // ---- 5b. Y_l = M Y' by chunks; Z += P_l^T Y_l.  Blocks of at least 64
+    // rows on the tensor cores (three TF32 products per FP32 product); smaller
+    // ones, whose apply is bound by streaming the chunks rather than by the
+    // products (measured), by 4 x 4 FP32 register tiles ----
+    if constexpr (NR < 64) {
+      for (int c0 = 0; c0 < W; c0 += kCW) {
+        stream_chunk<ST, LT, PARTS>(L, chunk, Yl, a, pix, c0, false);
+        __syncthreads();
+        constexpr int Q = kCW / 4;
+        for (int t = tid; t < nt4 * Q; t += LT) {
+          const int ti = t / Q, q = t - ti * Q;
+          float4 y[4];
 #pragma unroll
-        for (int p = 0; p < 4; ++p) y[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int s = 0; s < n; ++s) {
-          const float4 m = lds4(X2 + (size_t)s * GS + 4 * ti);  // M[s][r] = M[r][s]
-          const float4 v = lds4(chunk + (size_t)s * L.cs + 4 * q);
+          for (int p = 0; p < 4; ++p) y[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int s = 0; s < n; ++s) {
+            const float4 m = lds4(X2 + (size_t)s * GS + 4 * ti);  // M[s][r] = M[r][s]
+            const float4 v = lds4(chunk + (size_t)s * L.cs + 4 * q);
 #pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            const float mp = c4(m, p);
-            y[p].x = fmaf(mp, v.x, y[p].x);
-            y[p].y = fmaf(mp, v.y, y[p].y);
-            y[p].z = fmaf(mp, v.z, y[p].z);
-            y[p].w = fmaf(mp, v.w, y[p].w);
+            for (int p = 0; p < 4; ++p) {
+              const float mp = c4(m, p);
+              y[p].x = fmaf(mp, v.x, y[p].x);
+              y[p].y = fmaf(mp, v.y, y[p].y);
+              y[p].z = fmaf(mp, v.z, y[p].z);
+              y[p].w = fmaf(mp, v.w, y[p].w);
+            }
           }
-        }
-        const int c = c0 + 4 * q;
-        if (c < W) {
+          const int c = c0 + 4 * q;
+          if (c < W) {
 #pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            const int r = 4 * ti + p;
-            if (r < n) {
-              int band;
-              float *Zb = z_part<ST, PARTS>(a, r, c, N3p, band);
-              __stcs(reinterpret_cast<float4 *>(Yl + (size_t)r * W + c), y[p]);
-              atomicAdd(reinterpret_cast<float4 *>(Zb + (size_t)pix[r] * N3p + band), y[p]);
+            for (int p = 0; p < 4; ++p) {
+              const int r = 4 * ti + p;
+              if (r < n) {
+                int band;
+                float *Zb = z_part<ST, PARTS>(a, r, c, N3p, band);
+                __stcs(reinterpret_cast<float4 *>(Yl + (size_t)r * W + c), y[p]);
+                atomicAdd(reinterpret_cast<float4 *>(Zb + (size_t)pix[r] * N3p + band), y[p]);
+              }
             }
           }
         }
+        __syncthreads();
       }
-      __syncthreads();
+    } else {
+    // M's low TF32 parts into X1 (Ut is no longer read); X2 keeps M, whose raw
+    // bits are its high parts.  A = M read transposed (M is symmetric).
+    for (int e = tid; e < n * GS; e += LT) {
+      const float m = X2[e];
+      X1[e] = m - __uint_as_float(__float_as_uint(m) & 0xffffe000u);
     }
+    __syncthreads();
+    {
+      constexpr int MT = (NR + 15) / 16, KS = (NR + 7) / 8, QT = kCW / 8;
+      constexpr int QPU = apply_qpu(MT, QT, LW), UPR = QT / QPU, UNITS = MT * UPR;
+      constexpr int ROUNDS = (UNITS + LW - 1) / LW;
+      const int g = lane >> 2, t = lane & 3;
+      for (int c0 = 0; c0 < W; c0 += kCW) {
+        stream_chunk<ST, LT, PARTS>(L, chunk, Yl, a, pix, c0, false);
+        __syncthreads();
+        // unit u: rows 16 m .. 16 m + 15 of the chunk's result, QPU column tiles of 8
+        float d[ROUNDS][QPU][4];
+#pragma unroll
+        for (int rd = 0; rd < ROUNDS; ++rd) {
+#pragma unroll
+          for (int qq = 0; qq < QPU; ++qq) d[rd][qq][0] = d[rd][qq][1] = d[rd][qq][2] = d[rd][qq][3] = 0.f;
+          const int u = warp + rd * LW;
+          if (u >= UNITS) continue;  // warp-uniform
+          const int m = u / UPR, q0 = (u - m * UPR) * QPU;
+#pragma unroll 2
+          for (int ks = 0; ks < KS; ++ks) {
+            unsigned ah[4], al[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int i = 16 * m + g + 8 * (e & 1), k = 8 * ks + t + 4 * (e >> 1);
+              const bool in = i < n && k < n;
+              ah[e] = in ? __float_as_uint(X2[(size_t)k * GS + i]) : 0u;
+              al[e] = in ? __float_as_uint(X1[(size_t)k * GS + i]) : 0u;
+            }
+            unsigned bh[QPU][2], bl[QPU][2];
+#pragma unroll
+            for (int qq = 0; qq < QPU; ++qq)
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int k = 8 * ks + t + 4 * h;
+                split_tf32(k < n ? chunk[(size_t)k * L.cs + 8 * (q0 + qq) + g] : 0.f, bh[qq][h], bl[qq][h]);
+              }
+            three_parts([&](auto P) {
+#pragma unroll
+              for (int qq = 0; qq < QPU; ++qq)
+                mma_3xtf32_part<decltype(P)::value>(d[rd][qq], ah, al, bh[qq][0], bh[qq][1], bl[qq][0], bl[qq][1]);
+            });
+          }
+        }
+        __syncthreads();  // every warp has read the chunk: the results take its place
+#pragma unroll
+        for (int rd = 0; rd < ROUNDS; ++rd) {
+          const int u = warp + rd * LW;
+          if (u >= UNITS) continue;
+          const int m = u / UPR, q0 = (u - m * UPR) * QPU;
+#pragma unroll
+          for (int qq = 0; qq < QPU; ++qq)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int r = 16 * m + g + 8 * h;
+              if (r < n)
+                *reinterpret_cast<float2 *>(chunk + (size_t)r * L.cs + 8 * (q0 + qq) + 2 * t) =
+                    make_float2(d[rd][qq][2 * h], d[rd][qq][2 * h + 1]);
+            }
+        }
+        __syncthreads();
+        constexpr int Q = kCW / 4;
+        for (int it = tid; it < n * Q; it += LT) {
+          const int r = it / Q, j = it - r * Q, c = c0 + 4 * j;
+          if (c < W) {
+            const float4 y = lds4(chunk + (size_t)r * L.cs + 4 * j);
+            int band;
+            float *Zb = z_part<ST, PARTS>(a, r, c, N3p, band);
+            __stcs(reinterpret_cast<float4 *>(Yl + (size_t)r * W + c), y);
+            atomicAdd(reinterpret_cast<float4 *>(Zb + (size_t)pix[r] * N3p + band), y);
+          }
+        }
+        __syncthreads();
+      }
+    }
+    }  // tensor-core apply
   }
   if (tid == 0 && s_sweeps) atomicAdd(&a.sc->jacobi_sweeps, (unsigned long long)s_sweeps);
 }

@@ -10,6 +10,7 @@
 // device scalar c3 and a cube d (see dual_kernel).
 #pragma once
 #include <cuda_runtime.h>
+#include <type_traits>
 #include <stdint.h>
 
 namespace s3ttv {
@@ -246,5 +247,50 @@ cudaError_t launch_objective(const float *u, int N1, int N2, int N3, int k, int 
 cudaError_t launch_sstv_l1(const float *u, int N1, int N2, int N3, double *out, int grid, cudaStream_t st);
 cudaError_t launch_hsstv_norm(const float *u, int N1, int N2, int N3, double omega, int l12, double *out, int grid,
                               cudaStream_t st);
+
+
+// ---------------------------------------------------------------------------
+// FP32 products on the TF32 tensor cores (mma.sync m16n8k8), shared by both
+// block-dual kernels.
+// x ~ hi + lo with hi = x truncated to TF32 (low 13 mantissa bits cleared,
+// |x - hi| < 2^-10 |x|) and lo = x - hi (exact in FP32) truncated to TF32 as
+// well: |x - hi - lo| < 2^-20 |x|.  The TF32 tensor-core operands ignore the
+// low 13 bits of their 32-bit registers (checked on GB300: every product of
+// raw and of masked operands agreed bit for bit), so both parts go in
+// unmasked: two instructions, the same products.
+__device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo) {
+  hi = __float_as_uint(x);
+  lo = __float_as_uint(x - __uint_as_float(hi & 0xffffe000u));
+}
+// d += A B for one 16 x 8 x 8 tile, TF32 operands, FP32 accumulation (warp-wide).
+__device__ __forceinline__ void mma_tf32(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+// d += A B with both operands split hi + lo: lo*hi + hi*lo + hi*hi (the lo*lo
+// term, below 2^-20 of the product, is dropped), so the tile product keeps
+// FP32-level accuracy (a few 2^-20 relative).  Product p of the three (0: lo*hi,
+// 1: hi*lo, 2: hi*hi), in that order on every accumulator.  The call sites run
+// p as their outermost loop over independent tiles, so consecutive products on
+// one accumulator are several instructions apart instead of waiting out each
+// other's latency (the same sums in the same order).
+template <int p>
+__device__ __forceinline__ void mma_3xtf32_part(float (&d)[4], const unsigned (&ah)[4], const unsigned (&al)[4],
+                                                unsigned bh0, unsigned bh1, unsigned bl0, unsigned bl1) {
+  if constexpr (p == 0) mma_tf32(d, al[0], al[1], al[2], al[3], bh0, bh1);
+  else if constexpr (p == 1) mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+  else mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+}
+// F(integral_constant<int, p>) for p = 0, 1, 2
+template <class F>
+__device__ __forceinline__ void three_parts(const F &f) {
+  f(std::integral_constant<int, 0>());
+  f(std::integral_constant<int, 1>());
+  f(std::integral_constant<int, 2>());
+}
 
 }  // namespace s3ttv

@@ -19,13 +19,13 @@ OP_TOL = 1e-5
 
 
 def op_tol(k):
-    """Per-operator bound: 1e-5 for every block size.  The eigen-solves of the
-    one-CTA-per-block kernel (k = 6..16) rotate pairs down to a polish
-    threshold of tol / 8 while only pairs above tol keep a sweep going; at the
-    default tol = 2e-6 without it the measured error reached 1.4e-5 at k = 10
-    and 1.8e-5 at k = 12 (random blocks of 140 and 120 columns).  The cases
-    of k = 11..16 with many rows and columns have measured bounds of their own
-    (FLOOR_CASES)."""
+    """Per-operator bound: 1e-5 for every block size.  The eigen-solves rotate
+    every pair of rows above a polish threshold (2.5e-7) in every sweep, and a
+    sweep with no pair above the tolerance (1e-4) ends the solve; without the
+    polish (rotating only above a tolerance of 2e-6) the measured error reached
+    1.4e-5 at k = 10 and 1.8e-5 at k = 12 (random blocks of 140 and 120
+    columns).  The cases of k = 11..16 with many rows and columns have measured
+    bounds of their own (FLOOR_CASES)."""
     return OP_TOL
 
 
