@@ -62,7 +62,7 @@ FALLBACK_HBM_GBS = 6800.0
 # form), from an ncu capture of the kernel whose source hashes to `sha`
 # (profiles/block_dual_stream_k5_128x128x128.md); traffic is reported only
 # while the kernel source is unchanged.
-BLOCK_DUAL_TRAFFIC = {"sha": "77bd2886b2039c6f", "k": 5, "bytes_per_voxel": (524.860416e6 + 486.513664e6) / 2097152}
+BLOCK_DUAL_TRAFFIC = {"sha": "00cf7ea1c6d9cd82", "k": 5, "bytes_per_voxel": (513.40672e6 + 466.765568e6) / 2097152}
 
 
 # ---------------------------------------------------------------------------
@@ -170,13 +170,23 @@ def nvsmi_id(device_index):
     return str(device_index)
 
 
-def block_dual_traffic(k, N):
+def block_dual_source_sha():
+    """sha256 prefix of the streaming block-dual kernel's sources (block_dual.cu
+    and the internal header holding its shared device helpers)."""
     import hashlib
+    h = hashlib.sha256()
     try:
-        src = open(os.path.join(ROOT, "paper_2404_03313_gb300", "csrc", "block_dual.cu"), "rb").read()
+        for name in ("block_dual.cu", "s3ttv_internal.cuh"):
+            h.update(open(os.path.join(ROOT, "paper_2404_03313_gb300", "csrc", name), "rb").read())
     except OSError:
         return None
-    if hashlib.sha256(src).hexdigest()[:16] != BLOCK_DUAL_TRAFFIC["sha"] or k != BLOCK_DUAL_TRAFFIC["k"]:
+    return h.hexdigest()[:16]
+
+
+def block_dual_traffic(k, N):
+    """DRAM bytes of one block-dual launch, scaled by voxels from the ncu capture
+    of the 128x128x128 case; None once the kernel's sources have changed."""
+    if block_dual_source_sha() != BLOCK_DUAL_TRAFFIC["sha"] or k != BLOCK_DUAL_TRAFFIC["k"]:
         return None
     return BLOCK_DUAL_TRAFFIC["bytes_per_voxel"] * N
 
