@@ -1290,14 +1290,16 @@ __device__ void form_M_mma(float *Gm) {
 // the first-order scratch.
 constexpr int kSW = 4;         // warps per CTA
 constexpr int kCW = 32;        // columns per chunk (four 8-column k-steps)
-constexpr int kCS = kCW + 12;  // chunk row stride: 12 mod 32 words, as the group form's rows
+constexpr int kCS = kCW + 4;   // chunk row stride: 4 mod 32 words (conflict-free Gram fragments)
 
 template <int K>
 struct StreamLayout {
   static constexpr int n = K * K;
   static constexpr int buf = n * kCS;                          // one chunk buffer
   static constexpr int gm = gm_floats<K, true>();              // G, then M (by rows, stride GS)
-  static constexpr int per_warp = (2 * buf + gm + n + 3) & ~3;  // + the rows' pixel offsets
+  static constexpr int off = 2 * buf + gm;                     // the rows' pixel offsets (n ints)
+  static constexpr int fb = (off + n + 3) & ~3;                // the chunk's F rows (n x kCW), step A
+  static constexpr int per_warp = fb + n * kCW;
   static_assert(w_floats<K>() + fo_floats<K>() <= 2 * buf, "W and the first-order scratch fit the chunk buffers");
 };
 
@@ -1321,7 +1323,8 @@ __device__ void stream_block(const BlockDualArgs &a, long long l, float *bufs, u
   constexpr int NE = (n * (kCW / 4) + 31) / 32;  // 16-byte pieces of a chunk per lane
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   float *Gm = bufs + 2 * LY::buf;
-  int *off = reinterpret_cast<int *>(Gm + LY::gm);
+  int *off = reinterpret_cast<int *>(bufs + LY::off);
+  float *fb = bufs + LY::fb;
   const Dims dm = a.dm;
   const int N3p = dm.N3p, RW = 2 * N3p, NCH = (RW + kCW - 1) / kCW;
   const float gY = a.gY;
@@ -1347,13 +1350,32 @@ __device__ void stream_block(const BlockDualArgs &a, long long l, float *bufs, u
       }
       cp_async_commit();
     };
+    // the F rows of chunk ch (F = (Fv | Fh) at the rows' pixels) into fb, the
+    // same pieces as load_chunk; its own commit group
+    auto load_f = [&](int ch) {
+      const int c0 = ch * kCW, w4 = min(kCW, RW - c0) >> 2;
+#pragma unroll
+      for (int u = 0; u < NE; ++u) {
+        const int e = lane + 32 * u, r = e >> 3, j = e & 7;
+        if (r < n && j < w4) {
+          const int c = c0 + 4 * j;
+          const bool hz = c >= N3p;
+          cp_async16(fb + r * kCW + 4 * j, (hz ? a.Fh : a.Fv) + (size_t)off[r] * N3p + (hz ? c - N3p : c));
+        }
+      }
+      cp_async_commit();
+    };
     __syncwarp();  // the pixel offsets are visible; the buffers are free
 
     // ---- A. Y' chunk by chunk, its Gram in registers ----
     float acc[NTILE][4];
 #pragma unroll
     for (int i = 0; i < NTILE; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+    // Commit groups in order: Y(0), F(0), then per chunk ch: Y(ch + 1) before
+    // the wait, F(ch + 1) once F(ch) has been used, so waiting for all but the
+    // newest group leaves Y(ch) and F(ch) complete.
     load_chunk(0, bufs, pol_done);
+    load_f(0);
     for (int ch = 0; ch < NCH; ++ch) {
       float *cur = bufs + (ch & 1) * LY::buf;
       if (ch + 1 < NCH) {
@@ -1364,32 +1386,24 @@ __device__ void stream_block(const BlockDualArgs &a, long long l, float *bufs, u
       }
       __syncwarp();
       const int c0 = ch * kCW, w4 = min(kCW, RW - c0) >> 2;
-      float4 fv[NE];
-#pragma unroll
-      for (int u = 0; u < NE; ++u) {
-        const int e = lane + 32 * u, r = e >> 3, j = e & 7;
-        if (r < n && j < w4) {
-          const int c = c0 + 4 * j;
-          const bool hz = c >= N3p;
-          fv[u] = __ldg(reinterpret_cast<const float4 *>((hz ? a.Fh : a.Fv) + (size_t)off[r] * N3p + (hz ? c - N3p : c)));
-        }
-      }
 #pragma unroll
       for (int u = 0; u < NE; ++u) {
         const int e = lane + 32 * u, r = e >> 3, j = e & 7;
         if (r < n && j < w4) {
           float *dst = cur + r * kCS + 4 * j;
+          const float4 f = lds4(fb + r * kCW + 4 * j);
           float4 y = lds4(dst);
-          y.x = fmaf(gY, fv[u].x, y.x);
-          y.y = fmaf(gY, fv[u].y, y.y);
-          y.z = fmaf(gY, fv[u].z, y.z);
-          y.w = fmaf(gY, fv[u].w, y.w);
+          y.x = fmaf(gY, f.x, y.x);
+          y.y = fmaf(gY, f.y, y.y);
+          y.z = fmaf(gY, f.z, y.z);
+          y.w = fmaf(gY, f.w, y.w);
           sts4(dst, y);
           // Y' replaces Y_l in global memory (kept in L2) for step C
           st_hint(reinterpret_cast<float4 *>(Yl + (size_t)r * RW + c0) + j, y, pol_keep);
         }
       }
-      __syncwarp();
+      __syncwarp();  // every lane has read fb: the next chunk's F may replace it
+      if (ch + 1 < NCH) load_f(ch + 1);
       const int nks = w4 >> 1;
       for (int ks = 0; ks < nks; ++ks) {
         unsigned xh[4][2], xl[4][2];
