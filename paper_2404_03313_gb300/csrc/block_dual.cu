@@ -238,9 +238,12 @@ __device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
 // copy of the block's warm-start rows W, null for a cold start), then the
 // scaled eigen-rows into Ut and the warm rows into W.  Returns the sweeps used.
 // C0: the product W G already formed (rows of stride c0_ld), or null.
+// wstage: shared memory of w_floats<K>() floats, free by the time the rows are
+// final (it may be Ws or C0): the new W rows are assembled there and written
+// out with coalesced 16-byte streaming stores; null: stored row by row.
 template <int K>
 __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Ws, const float *Gm, float *Ut,
-                          bool *ok, const float *C0 = nullptr, int c0_ld = 0) {
+                          bool *ok, const float *C0 = nullptr, int c0_ld = 0, float *wstage = nullptr) {
   using S = Shape<K>;
   constexpr int n = S::n, NP = S::NP, NPOS = S::NPOS, HP = S::HP, HW = S::HW, GS = S::GS, UTS = S::UTS;
   const int lane = threadIdx.x & 31;
@@ -450,20 +453,29 @@ __device__ int eigen_rows(const BlockDualArgs &a, long long l, const float *Ws, 
     float *Ww = a.W + (size_t)l * a.w_stride;
     if (zero_rows > (unsigned)(NPOS - n)) {
       if (lane == 0) Ww[0] = __int_as_float(0x7fc00000);
-    } else if (act) {
-      const float iA = nA > floor2 ? rsqrtf(nA) : 0.f, iB = nB > floor2 ? rsqrtf(nB) : 0.f;
+    } else {
+      float *Wd = wstage ? wstage : Ww;
+      if (act) {
+        const float iA = nA > floor2 ? rsqrtf(nA) : 0.f, iB = nB > floor2 ? rsqrtf(nB) : 0.f;
 #pragma unroll
-      for (int j = 0; j < HP; ++j) {
-        const float2 x = up2(A[j]), y = up2(B[j]);
-        const int col = col0 + 2 * j;
-        if (col < n) {
-          Ww[(2 * pi) * n + col] = x.x * iA;
-          Ww[(2 * pi + 1) * n + col] = y.x * iB;
+        for (int j = 0; j < HP; ++j) {
+          const float2 x = up2(A[j]), y = up2(B[j]);
+          const int col = col0 + 2 * j;
+          if (col < n) {
+            Wd[(2 * pi) * n + col] = x.x * iA;
+            Wd[(2 * pi + 1) * n + col] = y.x * iB;
+          }
+          if (col + 1 < n) {
+            Wd[(2 * pi) * n + col + 1] = x.y * iA;
+            Wd[(2 * pi + 1) * n + col + 1] = y.y * iB;
+          }
         }
-        if (col + 1 < n) {
-          Ww[(2 * pi) * n + col + 1] = x.y * iA;
-          Ww[(2 * pi + 1) * n + col + 1] = y.y * iB;
-        }
+      }
+      if (wstage) {
+        __syncwarp();
+        for (int c = lane; c < w_floats<K>() / 4; c += 32)
+          __stcs(reinterpret_cast<float4 *>(Ww) + c, reinterpret_cast<const float4 *>(wstage)[c]);
+        __syncwarp();  // wstage read before its next use
       }
     }
   }
@@ -1482,7 +1494,7 @@ __device__ void stream_block(const BlockDualArgs &a, long long l, float *bufs, u
       ++fo_count;
     } else {
       bool ok;
-      sweeps += eigen_rows<K>(a, l, Ws, Gm, Gm, &ok, C0, fo_stride<K>());
+      sweeps += eigen_rows<K>(a, l, Ws, Gm, Gm, &ok, C0, fo_stride<K>(), bufs);
       int queued = 0;
       if (lane == 0 && !ok) {
         // to the FP64 re-solve if the queue has room; else applied as it stands
