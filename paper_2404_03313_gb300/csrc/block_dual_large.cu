@@ -324,9 +324,64 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
     // ---- 2. C0 = W G (warm) or G (cold), rows of C into X2 ----
     const float *Wl = a.W ? a.W + (size_t)l * a.w_stride : nullptr;
     const bool warm = a.warm && Wl && !(Wl[0] != Wl[0]);  // NaN marks "start cold"
+    bool c0_done = false;
+    if constexpr (NR >= 64) {
+      if (warm) {  // block-uniform
+        // C0 = W G on the tensor cores (three TF32 products per FP32 product):
+        // unit u = rows 16 m .. 16 m + 15 of C0 over Q0 column tiles of 8, W's
+        // fragments (from global memory) loaded once per k-step for all of them
+        constexpr int NPC = (NR + 1) & ~1, MT0 = (NPC + 15) / 16, QT0 = (NR + 7) / 8, KS0 = (NR + 7) / 8;
+        constexpr int G0 = (QT0 + 6) / 7, Q0 = (QT0 + G0 - 1) / G0, UNITS0 = MT0 * G0;
+        const int g = lane >> 2, t = lane & 3;
+        for (int e = tid; e < NP * (GS - 8 * QT0); e += LT) {  // columns beyond the tiles
+          const int r = e / (GS - 8 * QT0);
+          X2[(size_t)r * GS + 8 * QT0 + (e - r * (GS - 8 * QT0))] = 0.f;
+        }
+        for (int u = warp; u < UNITS0; u += LW) {
+          const int m = u / G0, q0 = (u - m * G0) * Q0;
+          float d[Q0][4];
+#pragma unroll
+          for (int qq = 0; qq < Q0; ++qq) d[qq][0] = d[qq][1] = d[qq][2] = d[qq][3] = 0.f;
+#pragma unroll 2
+          for (int ks = 0; ks < KS0; ++ks) {
+            unsigned ah[4], al[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int i = 16 * m + g + 8 * (e & 1), k = 8 * ks + t + 4 * (e >> 1);
+              split_tf32(i < NP && k < n ? __ldg(Wl + (size_t)i * n + k) : 0.f, ah[e], al[e]);
+            }
+            unsigned bh[Q0][2], bl[Q0][2];
+#pragma unroll
+            for (int qq = 0; qq < Q0; ++qq)
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int k = 8 * ks + t + 4 * h, j = 8 * (q0 + qq) + g;
+                split_tf32(k < n && j < n && q0 + qq < QT0 ? X1[(size_t)k * GS + j] : 0.f, bh[qq][h], bl[qq][h]);
+              }
+            three_parts([&](auto P) {
+#pragma unroll
+              for (int qq = 0; qq < Q0; ++qq)
+                mma_3xtf32_part<decltype(P)::value>(d[qq], ah, al, bh[qq][0], bh[qq][1], bl[qq][0], bl[qq][1]);
+            });
+          }
+#pragma unroll
+          for (int qq = 0; qq < Q0; ++qq) {
+            if (q0 + qq >= QT0) break;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int r = 16 * m + g + 8 * h;
+              if (r < NP)
+                *reinterpret_cast<float2 *>(X2 + (size_t)r * GS + 8 * (q0 + qq) + 2 * t) =
+                    make_float2(d[qq][2 * h], d[qq][2 * h + 1]);
+            }
+          }
+        }
+        c0_done = true;
+      }
+    }
     // two rows per warp at a time (r0 and r0 + LW), so each G row loaded from
     // shared memory serves both; per row the sums are those of one row at a time
-    for (int r0 = warp; r0 < NP; r0 += 2 * LW) {
+    for (int r0 = warp; r0 < NP && !c0_done; r0 += 2 * LW) {
       const int r1 = r0 + LW;
       const bool two = r1 < NP;
       float acc0[SL], acc1[SL];
