@@ -177,6 +177,52 @@ __device__ void stream_chunk(const Layout &L, float *chunk, float *Yl, const Blo
   }
 }
 
+// The same chunk as stream_chunk in two halves, so the next chunk's global
+// loads are in flight while the current one is used: fetch_chunk loads this
+// thread's PC pieces (Y, and F when forming) into registers, place_chunk forms
+// Y' = Y + gamma_Y F, writes it back over Y_l (form) and stores the pieces in
+// the chunk (rows >= n and columns >= W as 0).
+template <bool ST, int LT, int PARTS, int PC>
+__device__ __forceinline__ void fetch_chunk(const Layout &L, const float *Yl, const BlockDualArgs &a, const int *pix,
+                                            int c0, bool form, float4 (&y)[PC], float4 (&f)[PC]) {
+  const int N3p = a.dm.N3p, W = ST ? N3p : PARTS * N3p;
+  constexpr int Q = kCW / 4;
+#pragma unroll
+  for (int p = 0; p < PC; ++p) {
+    const int it = threadIdx.x + p * LT, r = it / Q, q = it - r * Q, c = c0 + 4 * q;
+    y[p] = f[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (it < 4 * L.nt4 * Q && r < L.n && c < W) {
+      y[p] = *reinterpret_cast<const float4 *>(Yl + (size_t)r * W + c);
+      if (form) {
+        int band;
+        const float *F = f_part<ST, PARTS>(a, r, c, N3p, band);
+        f[p] = __ldg(reinterpret_cast<const float4 *>(F + (size_t)pix[r] * N3p + band));
+      }
+    }
+  }
+}
+template <bool ST, int LT, int PARTS, int PC>
+__device__ __forceinline__ void place_chunk(const Layout &L, float *chunk, float *Yl, const BlockDualArgs &a, int c0,
+                                            bool form, const float4 (&y)[PC], const float4 (&f)[PC]) {
+  const int N3p = a.dm.N3p, W = ST ? N3p : PARTS * N3p;
+  constexpr int Q = kCW / 4;
+#pragma unroll
+  for (int p = 0; p < PC; ++p) {
+    const int it = threadIdx.x + p * LT, r = it / Q, q = it - r * Q, c = c0 + 4 * q;
+    if (it < 4 * L.nt4 * Q) {
+      float4 v = y[p];
+      if (form) {
+        v.x = fmaf(a.gY, f[p].x, v.x);
+        v.y = fmaf(a.gY, f[p].y, v.y);
+        v.z = fmaf(a.gY, f[p].z, v.z);
+        v.w = fmaf(a.gY, f[p].w, v.w);
+        if (r < L.n && c < W) *reinterpret_cast<float4 *>(Yl + (size_t)r * W + c) = v;
+      }
+      sts4(chunk + (size_t)r * L.cs + 4 * q, v);
+    }
+  }
+}
+
 // Column tiles of 8 per unit of the apply's tensor-core loop (a unit: one
 // 16-row block of the result over QPU tiles of a chunk of QT tiles, its M
 // fragments loaded once per k-step): the largest divisor of QT whose units
@@ -262,9 +308,23 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
     for (int u = 0; u < GTP; ++u)
 #pragma unroll
       for (int e = 0; e < 16; ++e) acc[u][e] = 0.f;
+    // Blocks of fewer than 64 rows (their Gram is bound by streaming the
+    // chunks, measured) fetch the next chunk into registers while this one's
+    // products run; larger ones would spill (two CTAs per SM) and stream as is.
+    constexpr int PC = (4 * NT4 * (kCW / 4) + LT - 1) / LT;
+    constexpr bool PREF = PC <= 6 && NR < 64;
+    constexpr int PCR = PREF ? PC : 1;
+    float4 ry[PCR], rf[PCR];
+    if constexpr (PREF) fetch_chunk<ST, LT, PARTS, PCR>(L, Yl, a, pix, 0, ps == 0, ry, rf);
     for (int c0 = 0; c0 < W; c0 += kCW) {
-      stream_chunk<ST, LT, PARTS>(L, chunk, Yl, a, pix, c0, ps == 0);
+      if constexpr (PREF) {
+        place_chunk<ST, LT, PARTS, PCR>(L, chunk, Yl, a, c0, ps == 0, ry, rf);
+      } else {
+        stream_chunk<ST, LT, PARTS>(L, chunk, Yl, a, pix, c0, ps == 0);
+      }
       __syncthreads();
+      if constexpr (PREF)
+        if (c0 + kCW < W) fetch_chunk<ST, LT, PARTS, PCR>(L, Yl, a, pix, c0 + kCW, ps == 0, ry, rf);
 #pragma unroll
       for (int u = 0; u < GTP; ++u) {
         const int t = tid + (ps * GTP + u) * LT;
