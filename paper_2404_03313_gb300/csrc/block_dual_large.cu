@@ -848,9 +848,21 @@ __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
     // ones, whose apply is bound by streaming the chunks rather than by the
     // products (measured), by 4 x 4 FP32 register tiles ----
     if constexpr (NR < 64) {
+      // the next chunk of Y' is fetched into registers while this one is applied
+      constexpr int PC = (4 * NT4 * (kCW / 4) + LT - 1) / LT;
+      constexpr bool PREF = PC <= 6;
+      constexpr int PCR = PREF ? PC : 1;
+      float4 ry[PCR], rf[PCR];
+      if constexpr (PREF) fetch_chunk<ST, LT, PARTS, PCR>(L, Yl, a, pix, 0, false, ry, rf);
       for (int c0 = 0; c0 < W; c0 += kCW) {
-        stream_chunk<ST, LT, PARTS>(L, chunk, Yl, a, pix, c0, false);
+        if constexpr (PREF) {
+          place_chunk<ST, LT, PARTS, PCR>(L, chunk, Yl, a, c0, false, ry, rf);
+        } else {
+          stream_chunk<ST, LT, PARTS>(L, chunk, Yl, a, pix, c0, false);
+        }
         __syncthreads();
+        if constexpr (PREF)
+          if (c0 + kCW < W) fetch_chunk<ST, LT, PARTS, PCR>(L, Yl, a, pix, c0 + kCW, false, ry, rf);
         constexpr int Q = kCW / 4;
         for (int t = tid; t < nt4 * Q; t += LT) {
           const int ti = t / Q, q = t - ti * Q;
