@@ -62,7 +62,7 @@ FALLBACK_HBM_GBS = 6800.0
 # form), from an ncu capture of the kernel whose source hashes to `sha`
 # (profiles/block_dual_stream_k5_128x128x128.md); traffic is reported only
 # while the kernel source is unchanged.
-BLOCK_DUAL_TRAFFIC = {"sha": "00cf7ea1c6d9cd82", "k": 5, "bytes_per_voxel": (513.40672e6 + 466.765568e6) / 2097152}
+BLOCK_DUAL_TRAFFIC = {"sha": "8e1bfef7d4d9cdec", "k": 5, "bytes_per_voxel": (526.2528e6 + 495.520768e6) / 2097152}
 
 
 # ---------------------------------------------------------------------------
