@@ -436,8 +436,8 @@ int s3ttv_quality(s3ttv_ctx *ctx, const float *u, const float *ref, int N1, int 
  *          after that stream has finished its work.
  * The first call on a device looks up the device address of the scratch array
  * (cudaGetSymbolAddress, with that device current) and keeps it for the life of
- * the process; make that first call before any stream capture, and do not call
- * this entry point on a device after cudaDeviceReset of that device (the
+ * the process; do not call this entry point on a device after
+ * cudaDeviceReset of that device (the
  * module is reloaded there and the kept address goes stale).  Every call reuses the same array and clears it
  * first, so calls that overlap on the GPU (other streams or host threads using
  * the same device at the same time) race and must not be issued. */
