@@ -104,3 +104,31 @@ def test_stacked_objective_and_state_round_trip(P, open_s):
             assert not Y[:, :, -1].any()
         s.set_state("Y", Y)
         np.testing.assert_array_equal(s.get_state("Y"), Y)
+
+
+@pytest.mark.parametrize("case", ["stacked_k6", "ssst_k8"])
+def test_warm_start_matches_cold_start_64_rows_and_more(P, case):
+    """Blocks of 64 rows or more form the warm-start product C0 = W G on the
+    tensor cores; the stacked 72-row (k = 6) and SSST 64-row (k = 8) blocks
+    take that path on every warm pass.  Warm and cold solves must agree (the
+    eigenbasis carried between passes only changes where the sweeps start), and
+    the warm one must take fewer sweeps."""
+    from synthetic import CubeSpec
+    k = 6 if case == "stacked_k6" else 8
+    spec = CubeSpec(16, 16, 24, regions=4, k=k, seed=5)
+    _, v = make_cube(spec)
+    eps, alpha, beta = O.radii(v.size, spec.sigma, spec.p_s, spec.p_t)
+    res = {}
+    for warm in (1, 0):
+        with P.Solver(0) as s:
+            if case == "stacked_k6":
+                s.set_option(P.OPT_LAYOUT, P.LAYOUT_STACKED)
+            else:
+                s.set_option(P.OPT_REGULARIZER, P.REG_SSST)
+            s.set_option(P.OPT_WARM_START, warm)
+            u, sp, t, info = s.solve(v, eps, alpha, beta, k, max_iter=40, tol=0.0)
+            assert info["jacobi_nonconverged"] == 0
+            res[warm] = (u, sp, t, info["jacobi_sweeps"])
+    for i in range(3):
+        assert rel(res[1][i], res[0][i]) <= 1e-5, i
+    assert res[1][3] < res[0][3]
