@@ -55,3 +55,20 @@ def test_reference_other_ranks_exit_without_work():
 def test_fewer_than_three_warmup_steps_rejected():
     p = run(["--impl", "reference", "--steps", "1", "--warmup", "0"], timeout=60)
     assert p.returncode != 0 and "warmup" in p.stderr
+
+
+def test_traffic_figure_follows_the_kernel_sources(monkeypatch):
+    """The DRAM traffic bench.py reports comes from an ncu capture of one
+    version of the streaming block-dual kernel; it is reported only while
+    block_dual.cu and the internal header hash to that capture, and only for
+    the block side it was taken at."""
+    import bench
+    N = 256 * 256 * 128
+    sha = bench.block_dual_source_sha()
+    assert sha is not None and len(sha) == 16
+    monkeypatch.setitem(bench.BLOCK_DUAL_TRAFFIC, "sha", sha)
+    got = bench.block_dual_traffic(bench.BLOCK_DUAL_TRAFFIC["k"], N)
+    assert got == bench.BLOCK_DUAL_TRAFFIC["bytes_per_voxel"] * N
+    assert bench.block_dual_traffic(bench.BLOCK_DUAL_TRAFFIC["k"] + 1, N) is None
+    monkeypatch.setitem(bench.BLOCK_DUAL_TRAFFIC, "sha", "0" * 16)
+    assert bench.block_dual_traffic(bench.BLOCK_DUAL_TRAFFIC["k"], N) is None
