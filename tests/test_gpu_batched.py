@@ -112,3 +112,20 @@ def test_problems_that_need_different_shared_memory(P):
         alone = [s.solve(p["v"], p["eps"], p["alpha"], p["beta"], p["k"], max_iter=4, tol=0.0) for p in probs]
     for o, a in zip(out, alone):
         assert rel(o[0].cpu().numpy(), a[0].cpu().numpy()) <= 1e-6
+
+
+def test_batch_with_blocks_of_10_and_14(P):
+    """Members whose block side takes the per-CTA kernel: k = 10 (rows in
+    shared memory) and k = 14 (196 rows: the n x n matrices in the member's own
+    global row scratch, allocated after its workspace) batched with a k = 5
+    cube give what each gives alone."""
+    specs = [CubeSpec(14, 15, 10, regions=3, k=14, seed=6), CubeSpec(12, 11, 12, regions=3, k=10, seed=7),
+             CubeSpec(16, 18, 8, regions=3, k=5, seed=2)]
+    probs = _problems(specs)
+    with P.Solver(0) as s:
+        out = s.solve_batched(probs, max_iter=20, tol=0.0)
+        alone = [s.solve(p["v"], p["eps"], p["alpha"], p["beta"], p["k"], max_iter=20, tol=0.0) for p in probs]
+    for (u, sp_, t, info), (ua, sa, ta, ia) in zip(out, alone):
+        assert info["iters"] == 20 and info["jacobi_nonconverged"] == 0
+        assert rel(u.cpu().numpy(), ua.cpu().numpy()) <= 1e-6
+        assert rel(t.cpu().numpy(), ta.cpu().numpy()) <= 1e-6
