@@ -35,7 +35,8 @@
 // blocks run here for every k <= kMaxStackedK.
 // Above kMaxSmemRows rows (k = 13..16) the two n x n buffers no longer fit
 // shared memory: they live in a per-CTA slice of a global scratch (up to
-// 2 x 256 x 272 floats, 557 KB per CTA, 85 MB for 152 CTAs, so L2-resident),
+// 2 x 256 x 272 floats, 557 KB per CTA; two CTAs per SM, 72 MB in all at
+// k = 13 and 165 MB at k = 16, mostly L2-resident),
 // the Gram accumulates its upper-triangle tiles over several passes of the
 // chunks (3 tiles a thread per pass) and the Jacobi uses 8-lane groups.
 // FP32 throughout (FP32 FMAs on CUDA cores).
@@ -252,7 +253,7 @@ __host__ __device__ constexpr int large_warps() {
 
 template <int K, bool ST, int PARTS>
 __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
-                                  large_warps<K, ST, PARTS>() == 4 ? 4 : ((ST ? 2 * K * K : K * K) > 100 ? 1 : 2))
+                                  large_warps<K, ST, PARTS>() == 4 ? 4 : ((ST ? 2 * K * K : K * K) > 100 && (ST ? 2 * K * K : K * K) <= kMaxSmemRows ? 1 : 2))
     block_dual_large_kernel(BlockDualArgs a) {
   constexpr int LW = large_warps<K, ST, PARTS>(), LT = LW * 32;
   constexpr int k = K;
