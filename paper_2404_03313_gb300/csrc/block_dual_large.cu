@@ -244,16 +244,21 @@ __host__ __device__ constexpr int apply_qpu(int mt, int qt, int lw) {
   return best;
 }
 
-// warps per CTA: stacked blocks of up to 64 rows (k <= 5) run four-warp CTAs,
-// four per SM; everything else eight-warp CTAs, two per SM
+// warps per CTA: stacked blocks of up to 64 rows (k <= 5) and SSST's blocks
+// run four-warp CTAs, four per SM; blocks of 101..144 rows, whose two n x n
+// matrices fill one SM's shared memory, one sixteen-warp CTA per SM;
+// everything else eight-warp CTAs, two per SM
+__host__ __device__ constexpr int large_warps_for(int n_rows, bool small) {
+  return small ? 4 : (n_rows > 100 && n_rows <= kMaxSmemRows ? 16 : kLW);
+}
 template <int K, bool ST, int PARTS>
 __host__ __device__ constexpr int large_warps() {
-  return (ST && 2 * K * K <= 64) || (PARTS == 3 && K * K <= 64) ? 4 : kLW;
+  return large_warps_for(ST ? 2 * K * K : K * K, (ST && 2 * K * K <= 64) || (PARTS == 3 && K * K <= 64));
 }
 
 template <int K, bool ST, int PARTS>
 __global__ void __launch_bounds__(large_warps<K, ST, PARTS>() * 32,
-                                  large_warps<K, ST, PARTS>() == 4 ? 4 : ((ST ? 2 * K * K : K * K) > 100 && (ST ? 2 * K * K : K * K) <= kMaxSmemRows ? 1 : 2))
+                                  large_warps<K, ST, PARTS>() == 4 ? 4 : (large_warps<K, ST, PARTS>() == 16 ? 1 : 2))
     block_dual_large_kernel(BlockDualArgs a) {
   constexpr int LW = large_warps<K, ST, PARTS>(), LT = LW * 32;
   constexpr int k = K;
@@ -1004,7 +1009,8 @@ long long block_dual_large_w_stride(int k, bool stacked) {
 long long block_dual_large_w_stride(int k) { return block_dual_large_w_stride(k, false); }
 
 int block_dual_large_threads(int k, bool stacked, int parts) {
-  return (stacked && 2 * k * k <= 64) || (parts == 3 && k * k <= 64) ? 128 : kLT;
+  const int n = stacked ? 2 * k * k : k * k;
+  return 32 * large_warps_for(n, (stacked && n <= 64) || (parts == 3 && k * k <= 64));
 }
 
 namespace {
